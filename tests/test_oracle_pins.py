@@ -1,0 +1,424 @@
+"""Pins of the FP64 oracle against values the method and the mathematics fix.
+
+None of these compares the oracle with itself: the expected values are hand
+evaluations (40-digit decimal arithmetic of Eq. 3-5 written out by hand, the
+literals below), closed forms (Manning normal depth, uniform inflow split),
+exact invariants (lake at rest, mass ledger, mirror symmetry), library
+routines (numpy.interp, scipy's brentq) and finite differences.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+from inputs import INFLOW, OUTFLOW, XMAX, XMIN, YMAX, YMIN, Options, Problem, Section
+import oracle
+
+
+def closed_box(z, h0, dx=1.0, n=0.03, sections=(), **opt):
+    ny, nx = z.shape
+    o = dict(dt_mode=1, dt_const=0.1)
+    o.update(opt)
+    return Problem("case", nx, ny, dx, np.asarray(z, float), np.full((ny, nx), n), list(sections),
+                   Options(**o), h0=np.asarray(h0, float))
+
+
+# ---------------------------------------------------------------- P1: 2 cells
+def test_p1_two_cell_hand_values():
+    """Flat bed, dx = 1, dt = 0.1, n = 0.03, h = (1, 0.5), closed walls.
+
+    Step 1: h_f = 1, q' = g dt h_f (1 - 0.5)/dx = 0.4905 (no friction at q = 0),
+            h = (1 - 0.04905, 0.5 + 0.04905).
+    Step 2: h_f = 0.95095, slope 0.4019,
+            q' = (0.4905 + 0.981*0.95095*0.4019) / (1 + 0.981*0.0009*0.4905*0.95095^(-7/3)).
+    Step 3: same with the step-2 state.  Decimal (40-digit) evaluations below.
+    """
+    p = closed_box(np.zeros((1, 2)), [[1.0, 0.5]])
+    o = oracle.Oracle(p)
+    expect = [
+        (0.4905, 0.95095, 0.54905),
+        (0.8650040113860357304, 0.8644495988613964270, 0.6355504011386035730),
+        (1.0579812164048227008, 0.7586514772209141569, 0.7413485227790858431),
+    ]
+    for q, h0, h1 in expect:
+        o.run(1)
+        assert o.qx[0, 1] == pytest.approx(q, rel=1e-14, abs=1e-15)
+        assert o.h[0, 0] == pytest.approx(h0, rel=1e-14)
+        assert o.h[0, 1] == pytest.approx(h1, rel=1e-14)
+        assert o.qx[0, 0] == 0.0 and o.qx[0, 2] == 0.0
+
+
+# ---------------------------------------------------------------- P2: 4x4
+def test_p2_four_by_four_hand_values():
+    """Step in the bed: columns 0-1 at z = 0 with h = 1, columns 2-3 at z = 0.6 dry.
+
+    Outflow (S = 1e-3) at the xmax face of row 0 (a dry cell) and at the xmin
+    face of row 1 (a wet cell); walls elsewhere; dx = 1, dt = 0.1, n = 0.03.
+    Step 1 by hand: faces 1|2 have h_f = max(1, 0.6) - max(0, 0.6) = 0.4 and
+    q' = g dt 0.4 (1 - 0.6) = 0.15696; the wet outflow face carries
+    -1^(5/3) sqrt(1e-3)/0.03 = -1.05409255338946; everything else is 0.
+    Step 2 values are 40-digit decimal evaluations of the same formulas.
+    """
+    z = np.array([[0.0, 0.0, 0.6, 0.6]] * 4)
+    h0 = np.array([[1.0, 1.0, 0.0, 0.0]] * 4)
+    secs = [Section.cells(XMAX, 0, 1, OUTFLOW, 1e-3, 4, 4), Section.cells(XMIN, 1, 2, OUTFLOW, 1e-3, 4, 4)]
+    o = oracle.Oracle(closed_box(z, h0, sections=secs))
+    o.run(1)
+    h1 = np.array([[1.0, 0.984304, 0.015696, 0.0],
+                   [0.8945907446610540, 0.984304, 0.015696, 0.0],
+                   [1.0, 0.984304, 0.015696, 0.0],
+                   [1.0, 0.984304, 0.015696, 0.0]])
+    np.testing.assert_allclose(o.h, h1, rtol=1e-14, atol=1e-15)
+    qx1 = np.zeros((4, 5))
+    qx1[:, 2] = 0.15696
+    qx1[1, 0] = -1.054092553389460
+    np.testing.assert_allclose(o.qx, qx1, rtol=1e-14, atol=1e-15)
+    assert np.all(o.qy == 0.0)
+    o.run(1)
+    h2 = np.array([[9.881195744512494e-1, 9.562893170728781e-1, 4.522629217791231e-2, 2.416834920960000e-5],
+                   [8.363854586562135e-1, 9.460868075851215e-1, 4.522629217791231e-2, 2.416834920960000e-5],
+                   [9.881195744512494e-1, 9.562893170728781e-1, 4.522629217791231e-2, 2.416834920960000e-5],
+                   [9.984602224000000e-1, 9.562893170728781e-1, 4.522629217791231e-2, 2.416834920960000e-5]])
+    np.testing.assert_allclose(o.h, h2, rtol=1e-13, atol=1e-16)
+    qx2 = np.array([[0.0, 1.539777600000000e-2, 2.955446052712191e-1, 2.416834920960000e-4, 0.0],
+                    [-8.754931379009831e-1, -8.662731887756611e-2, 2.955446052712191e-1, 2.416834920960000e-4, 0.0],
+                    [0.0, 1.539777600000000e-2, 2.955446052712191e-1, 2.416834920960000e-4, 0.0],
+                    [0.0, 1.539777600000000e-2, 2.955446052712191e-1, 2.416834920960000e-4, 0.0]])
+    np.testing.assert_allclose(o.qx, qx2, rtol=1e-13, atol=1e-16)
+    qy2 = np.zeros((5, 4))
+    qy2[1, 0] = 1.034064794875060e-1
+    qy2[2, 0] = -1.034064794875060e-1
+    np.testing.assert_allclose(o.qy, qy2, rtol=1e-13, atol=1e-16)
+
+
+# ---------------------------------------------------------------- P3: lake at rest
+@pytest.mark.parametrize("shape", [(16, 16), (7, 5), (33, 17)])
+def test_p3_lake_at_rest_is_exact(shape):
+    """Flat water surface over dyadic terrain with dry islands stays bitwise at rest."""
+    nx, ny = shape
+    p = inputs.lake_at_rest(nx, ny)
+    assert (p.z > 2.0).any() and (p.z < 2.0).any()   # both wet and dry cells
+    o = oracle.Oracle(p)
+    h0 = o.h.copy()
+    o.run(200)
+    assert np.array_equal(o.h, h0)
+    assert not o.qx.any() and not o.qy.any()
+
+
+def test_p3_lake_at_rest_fractal_cfl():
+    p = inputs.c2_fractal(nx=64, ny=48, steps=10)
+    z = p.z
+    eta0 = float(np.quantile(z, 0.4))
+    lake = Problem("lake_fractal", p.nx, p.ny, p.dx, z, p.n, [], Options(dt_cap=0.5),
+                   h0=np.maximum(eta0 - z, 0.0))
+    o = oracle.Oracle(lake)
+    o.run(100)
+    assert np.abs(o.qx).max() < 1e-12 and np.abs(o.qy).max() < 1e-12
+
+
+# ---------------------------------------------------------------- P4: mass ledger
+def test_p4_mass_ledger_c1():
+    """V(T) - V(0) = V_in - V_out + V_clip on the 128^2 channel run; V_in = sum dt Q."""
+    p = inputs.c1_tilted_channel()
+    o = oracle.Oracle(p)
+    V0 = o.volume()
+    _, dts = o.run(1000, dt_log=True)
+    L = o.ledger_dict()
+    assert L["V_in"] == pytest.approx(float(np.sum(dts * 50.0)), rel=1e-15)
+    bal = o.volume() - V0 - (L["V_in"] - L["V_out"] + L["V_clip"])
+    assert abs(bal) <= 1e-12 * L["V_in"]
+    assert L["V_out"] > 0.0
+
+
+def test_p4_mass_ledger_with_clipping():
+    """Thin water at an outflow edge drains below zero; the clip volume closes the ledger."""
+    z = np.zeros((6, 8))
+    h0 = np.full((6, 8), 0.002)
+    secs = [Section.cells(XMAX, 0, 6, OUTFLOW, 0.5, 8, 6), Section.cells(YMIN, 0, 8, OUTFLOW, 0.5, 8, 6)]
+    o = oracle.Oracle(closed_box(z, h0, dx=0.1, n=0.01, sections=secs, dt_const=0.05))
+    V0 = o.volume()
+    o.run(20)
+    L = o.ledger_dict()
+    assert L["V_clip"] > 0.0
+    assert np.all(o.h >= 0.0)
+    bal = o.volume() - V0 - (L["V_in"] - L["V_out"] + L["V_clip"])
+    assert abs(bal) <= 1e-12 * max(V0, L["V_out"])
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_p4_mass_ledger_random(seed):
+    p = inputs.random_small(23, 17, seed)
+    o = oracle.Oracle(p)
+    V0 = o.volume()
+    o.run(150)
+    L = o.ledger_dict()
+    assert L["V_in"] > 0 and L["V_out"] > 0
+    bal = o.volume() - V0 - (L["V_in"] - L["V_out"] + L["V_clip"])
+    assert abs(bal) <= 1e-12 * (V0 + L["V_in"])
+
+
+# ---------------------------------------------------------------- P5: normal depth
+def test_p5_uniform_channel_reaches_manning_normal_depth():
+    """At steady state Eq. 3 reduces to q = h^(5/3) sqrt(S0) / n (Manning)."""
+    p = inputs.normal_depth_channel(h_n=1.0)
+    o = oracle.Oracle(p)
+    for _ in range(60):
+        prev = o.h.copy()
+        o.run(500)
+        if np.abs(o.h - prev).max() < 1e-13:
+            break
+    assert np.abs(o.h - 1.0).max() < 1e-6
+    q_manning = math.sqrt(1e-3) / 0.03      # h_n = 1
+    np.testing.assert_allclose(o.qx[:, 1:], q_manning, rtol=1e-9)
+    assert np.abs(o.qy).max() < 1e-12
+
+
+def test_p5_normal_depth_other_depth():
+    h_n = 0.37
+    p = inputs.normal_depth_channel(nx=40, ny=3, dx=5.0, S0=4e-3, n=0.05, h_n=h_n)
+    p.h0 = np.full((3, 40), 0.5)
+    o = oracle.Oracle(p)
+    for _ in range(80):
+        prev = o.h.copy()
+        o.run(500)
+        if np.abs(o.h - prev).max() < 1e-13:
+            break
+    assert np.abs(o.h - h_n).max() < 1e-6
+
+
+# ---------------------------------------------------------------- P6: symmetry
+def _mirror_y(p):
+    ny = p.ny
+    secs = []
+    flip = {YMIN: YMAX, YMAX: YMIN, XMIN: XMIN, XMAX: XMAX}
+    for s in p.sections:
+        if s.side in (XMIN, XMAX):
+            a, b = round(s.frac_start * ny), round(s.frac_end * ny)
+            secs.append(Section.cells(s.side, ny - b, ny - a, s.kind, s.slope, p.nx, ny, s.t_s, s.q_m3s))
+        else:
+            secs.append(Section(flip[s.side], s.frac_start, s.frac_end, s.kind, s.slope, s.t_s, s.q_m3s))
+    return Problem(p.name + "_my", p.nx, ny, p.dx, p.z[::-1].copy(), p.n[::-1].copy(), secs, p.opts,
+                   h0=p.h0[::-1].copy(), qx0=p.qx0[::-1].copy(), qy0=-p.qy0[::-1].copy())
+
+
+def _transpose(p):
+    secs = []
+    swap = {XMIN: YMIN, XMAX: YMAX, YMIN: XMIN, YMAX: XMAX}
+    for s in p.sections:
+        secs.append(Section(swap[s.side], s.frac_start, s.frac_end, s.kind, s.slope, s.t_s, s.q_m3s))
+    return Problem(p.name + "_T", p.ny, p.nx, p.dx, p.z.T.copy(), p.n.T.copy(), secs, p.opts,
+                   h0=p.h0.T.copy(), qx0=p.qy0.T.copy(), qy0=p.qx0.T.copy())
+
+
+def _outflow_only(seed):
+    p = inputs.random_small(19, 14, seed)
+    p.sections = [s for s in p.sections if s.kind == OUTFLOW]
+    return p
+
+
+def test_p6_mirror_y_is_bitwise():
+    """Reflecting y negates every y-face exactly and leaves Eq. 4's sums unchanged."""
+    p = _outflow_only(3)
+    a, b = oracle.Oracle(p), oracle.Oracle(_mirror_y(p))
+    a.run(60)
+    b.run(60)
+    assert np.array_equal(a.h, b.h[::-1])
+    assert np.array_equal(a.qx, b.qx[::-1])
+    assert np.array_equal(a.qy, -b.qy[::-1])
+
+
+def test_p6_transpose_with_inflow():
+    """Swapping the axes swaps qx and qy; with inflow the Eq. 6 sums only reorder."""
+    p = inputs.random_small(19, 14, 4)
+    a, b = oracle.Oracle(p), oracle.Oracle(_transpose(p))
+    a.run(60)
+    b.run(60)
+    np.testing.assert_allclose(a.h, b.h.T, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(a.qx, b.qy.T, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(a.qy, b.qx.T, rtol=0, atol=1e-12)
+
+
+def test_p6_transpose_outflow_only_bitwise():
+    p = _outflow_only(5)
+    a, b = oracle.Oracle(p), oracle.Oracle(_transpose(p))
+    a.run(40)
+    b.run(40)
+    assert np.array_equal(a.h, b.h.T)
+    assert np.array_equal(a.qx, b.qy.T)
+
+
+# ---------------------------------------------------------------- P8 and the dt rule
+def test_p8_constant_dt_two_simulated_days():
+    """0.1 s constant steps: 1.728 M steps make two simulated days (172 800 s)."""
+    p = closed_box(np.zeros((1, 1)), [[0.0]], dt_const=0.1)
+    o = oracle.Oracle(p)
+    o.run(1_728_000)
+    assert o.ledger.step == 1_728_000
+    assert o.ledger.t == pytest.approx(172_800.0, rel=1e-9)
+
+
+def test_cfl_rule_and_epochs():
+    p = inputs.random_small(20, 12, 2)
+    p.opts.epoch_steps = 5
+    o = oracle.Oracle(p)
+    hmax0 = o.h.max()
+    _, dts = o.run(23, dt_log=True)
+    # held constant inside each epoch of 5 steps
+    for e in range(0, 23, 5):
+        assert np.all(dts[e:e + 5] == dts[e])
+    # Courant number alpha at the first epoch (unless capped)
+    c = dts[0] * math.sqrt(9.81 * hmax0) / p.dx
+    assert c == pytest.approx(0.7, rel=1e-14) or dts[0] == p.opts.dt_cap
+    dry = oracle.Oracle(closed_box(np.zeros((3, 3)), np.zeros((3, 3)), dt_mode=0, dt_cap=1.5))
+    assert dry.dt() == 1.5
+
+
+# ---------------------------------------------------------------- boundary conditions
+def test_section_fraction_rule():
+    p = inputs.random_small(20, 12, 0)
+    o = oracle.Oracle(p)
+    ny, nx = 12, 20
+    assert o.section_range(0) == (ny // 4, 3 * ny // 4)
+    assert o.section_range(1) == (nx // 3, 2 * nx // 3)
+    assert o.section_range(2) == (0, ny)
+
+
+def test_hydrograph_matches_numpy_interp():
+    p = inputs.random_small(10, 10, 0)
+    o = oracle.Oracle(p)
+    s = p.sections[0]
+    for t in [-5.0, 0.0, 12.5, 50.0, 77.7, 200.0, 1e6]:
+        assert o.hydrograph(0, t) == pytest.approx(np.interp(t, s.t_s, s.q_m3s), rel=1e-15, abs=1e-15)
+
+
+@pytest.mark.parametrize("bc_form", [0, 1])
+def test_inflow_uniform_section_splits_evenly(bc_form):
+    """Equal bed levels and roughness: every section cell carries Q / (m dx)."""
+    z = np.full((9, 5), 3.0)
+    secs = [Section.cells(XMIN, 2, 7, INFLOW, 1e-3, 5, 9, [0, 1], [12.0, 12.0])]
+    o = oracle.Oracle(closed_box(z, np.zeros((9, 5)), dx=2.0, sections=secs, bc_form=bc_form))
+    W, q = o.inflow_faces(0, 12.0)
+    np.testing.assert_allclose(q, 12.0 / (5 * 2.0), rtol=1e-14)
+    # Eq. 5 at that level gives the same per-cell discharge (closed form)
+    hh = W - 3.0
+    per_cell = (2.0 * hh ** (5 / 3) if bc_form == 0 else 4.0 * hh ** (2 / 3)) * math.sqrt(1e-3) / 0.03
+    assert per_cell == pytest.approx(12.0 / 5, rel=1e-9)
+
+
+@pytest.mark.parametrize("bc_form", [0, 1])
+def test_inflow_level_matches_brentq(bc_form):
+    """W solves sum_c Q_c(W) = Q_in (Eq. 6); check against scipy's root finder."""
+    from scipy.optimize import brentq
+    rng = np.random.default_rng(11)
+    z = rng.uniform(0.0, 2.0, (10, 6))
+    n = rng.uniform(0.02, 0.08, (10, 6))
+    p = closed_box(z, np.zeros((10, 6)), dx=3.0, sections=[
+        Section.cells(YMAX, 1, 5, INFLOW, 2e-3, 6, 10, [0, 1], [7.0, 7.0])], bc_form=bc_form)
+    p.n = n
+    o = oracle.Oracle(p)
+    W, q = o.inflow_faces(0, 7.0)
+    zc, nc = z[-1, 1:5], n[-1, 1:5]
+    pe = 5 / 3 if bc_form == 0 else 2 / 3
+    A = 3.0 if bc_form == 0 else 9.0
+
+    def F(w):
+        return np.sum(A * np.maximum(w - zc, 0.0) ** pe * math.sqrt(2e-3) / nc) - 7.0
+    Wref = brentq(F, zc.min(), zc.min() + 100.0, xtol=1e-14, rtol=1e-15)
+    assert W == pytest.approx(Wref, abs=2e-12)
+    assert np.sum(q) * 3.0 == pytest.approx(7.0, rel=1e-14)
+    assert np.all(q[zc >= W] == 0.0)
+
+
+def test_outflow_literal_form_hand_value():
+    """bc_form 1 (A = dx^2 in Eq. 5): unit-width flux dx h^(2/3) sqrt(S)/n."""
+    z = np.zeros((1, 1))
+    secs = [Section.cells(XMAX, 0, 1, OUTFLOW, 4e-4, 1, 1)]
+    o = oracle.Oracle(closed_box(z, [[0.512]], dx=2.0, n=0.04, sections=secs, bc_form=1, dt_const=0.01))
+    o.run(1)
+    # 2 * 0.512^(2/3) * 0.02 / 0.04 = 2 * 0.64 * 0.5 = 0.64 m^2/s
+    assert o.qx[0, 1] == pytest.approx(0.64, rel=1e-14)
+    assert o.h[0, 0] == pytest.approx(0.512 - 0.01 * 0.64 / 2.0, rel=1e-14)
+
+
+# ---------------------------------------------------------------- adjoint
+def wet_case(nx=12, ny=9, seed=0, bc_form=0):
+    rng = np.random.default_rng(500 + seed)
+    dx = 4.0
+    xm = (np.arange(nx) + 0.5) * dx
+    z = 1.0 - 2e-3 * xm[None, :] + rng.uniform(-0.05, 0.05, (ny, nx))
+    h0 = 0.6 + rng.uniform(0.0, 0.2, (ny, nx))
+    n = rng.uniform(0.03, 0.06, (ny, nx))
+    so = 2e-3 if bc_form == 0 else 2e-5      # the literal form drains ~dx/h times faster
+    secs = [Section.cells(XMIN, 2, 7, INFLOW, 2e-3, nx, ny, [0.0, 30.0], [1.0, 3.0]),
+            Section.cells(XMAX, 0, ny, OUTFLOW, so, nx, ny),
+            Section.cells(YMAX, 3, 8, OUTFLOW, so / 2, nx, ny)]
+    p = Problem("wet", nx, ny, dx, z, n, secs, Options(dt_mode=1, dt_const=0.4, bc_form=bc_form), h0=h0,
+                qx0=np.zeros((ny, nx + 1)), qy0=np.zeros((ny + 1, nx)))
+    return p
+
+
+def _loss(p, n, steps, gauges, w):
+    p2 = Problem(p.name, p.nx, p.ny, p.dx, p.z, n, p.sections, p.opts, h0=p.h0, qx0=p.qx0, qy0=p.qy0)
+    o = oracle.Oracle(p2)
+    series, _ = o.run(steps, gauges=gauges)
+    assert o.h.min() > 0.05
+    return float(np.sum(series * w))
+
+
+@pytest.mark.parametrize("bc_form", [0, 1])
+def test_adjoint_dn_matches_central_differences(bc_form):
+    """dL/dn by the reverse sweep equals central finite differences of the forward run."""
+    p = wet_case(bc_form=bc_form)
+    steps = 40
+    rng = np.random.default_rng(3)
+    gauges = np.array([[3, 4], [8, 2], [10, 7], [0, 4], [11, 0]])
+    w = rng.standard_normal((steps, len(gauges)))
+    o = oracle.Oracle(p)
+    gn = o.adjoint(steps, gauges, w)
+    cells = [(0, 3), (0, 5), (4, 4), (11, 2), (6, 8), (3, 0), (7, 6), (11, 8)]  # incl. inflow + outflow cells
+    for (i, j) in cells:
+        eps = 1e-4 * p.n[j, i]      # the W bisection's 1e-12 m bracket is FD noise below ~1e-5
+        npl, nmi = p.n.copy(), p.n.copy()
+        npl[j, i] += eps
+        nmi[j, i] -= eps
+        fd = (_loss(p, npl, steps, gauges, w) - _loss(p, nmi, steps, gauges, w)) / (2 * eps)
+        assert gn[j, i] == pytest.approx(fd, rel=1e-5, abs=1e-9 * np.abs(gn).max())
+
+
+def test_adjoint_dh0_matches_central_differences():
+    p = wet_case(seed=1)
+    steps = 30
+    gauges = np.array([[5, 5], [9, 3]])
+    w = np.ones((steps, 2))
+    o = oracle.Oracle(p)
+    gn, lh, lqx, lqy = o.adjoint(steps, gauges, w, want_state=True)
+    for (i, j) in [(5, 5), (2, 2), (10, 6), (0, 0)]:
+        eps = 1e-6
+        lo = []
+        for sgn in (1, -1):
+            p2 = wet_case(seed=1)
+            p2.h0 = p.h0.copy()
+            p2.h0[j, i] += sgn * eps
+            o2 = oracle.Oracle(p2)
+            s, _ = o2.run(steps, gauges=gauges)
+            lo.append(np.sum(s * w))
+        fd = (lo[0] - lo[1]) / (2 * eps)
+        assert lh[j, i] == pytest.approx(fd, rel=2e-5, abs=1e-8)
+    # and one interior x-face discharge
+    eps = 1e-6
+    vals = []
+    for sgn in (1, -1):
+        p2 = wet_case(seed=1)
+        p2.qx0 = p.qx0.copy()
+        p2.qx0[4, 6] += sgn * eps
+        s, _ = oracle.Oracle(p2).run(steps, gauges=gauges)
+        vals.append(np.sum(s * w))
+    assert lqx[4, 6] == pytest.approx((vals[0] - vals[1]) / (2 * eps), rel=2e-5, abs=1e-8)
+
+
+def test_adjoint_zero_seed_gives_zero():
+    p = wet_case()
+    o = oracle.Oracle(p)
+    gn = o.adjoint(10, np.array([[1, 1]]), np.zeros((10, 1)))
+    assert not gn.any()
