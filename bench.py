@@ -1,0 +1,291 @@
+"""Benchmark of the GB300 flood-model step: Gcell-updates/s and HBM roofline.
+
+Default workload: the 16384 x 16384 single-grid step (268 M cells, FP32
+state h, qx, qy with DEM z and Manning n, ~5.4 GB resident, far larger than
+the 129 MB L2), fractal terrain with a carved channel, two inflow sections and
+an outflow edge, primed to ~30 % wet.  One benchmark "step" is one time step
+of the whole grid: epoch bookkeeping (CFL dt, Eq. 6 inflow) when due, the
+face update (Eq. 3), depth update (Eq. 4), boundary faces and ledgers.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle (the
+independent definition used by the tests) on the host cores over a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL = 32          # read h, qx, qy, z, n (20 B) + write h, qx, qy (12 B), FP32
+METRIC = "Gcell-updates/s and % of HBM roofline (FP32, 1 GB300); adjoint/forward time ratio"
+UNIT = "Gcell-updates/s"
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(name: str):
+    import inputs
+    if name == "c3":
+        return inputs.c3_large(), "fractal_16384x16384_1m_two_inflows_fp32"
+    if name == "c2":
+        return inputs.c2_fractal(), "fractal_2048x2048_5m_fp32"
+    if name.startswith("c3:"):
+        n = int(name.split(":")[1])
+        return inputs.c3_large(nx=n, ny=n), f"fractal_{n}x{n}_1m_two_inflows_fp32"
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, power, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(prob, seconds_target: float = 15.0):
+    """Time the FP64 oracle on a bounded sample (a full-width strip of the grid)."""
+    import oracle
+    from inputs import Problem
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    rows = max(16, min(prob.ny, 1024))
+    sub = Problem(prob.name + "_strip", prob.nx, rows, prob.dx, prob.z[:rows].copy(), prob.n[:rows].copy(),
+                  [s for s in prob.sections if s.side in (0, 1)], prob.opts,
+                  h0=None if prob.h0 is None else prob.h0[:rows].copy())
+    # fractions along x sides refer to the full height; re-express for the strip
+    from inputs import Section
+    secs = []
+    for s in sub.sections:
+        a, b = int(np.floor(s.frac_start * prob.ny + 0.5)), int(np.floor(s.frac_end * prob.ny + 0.5))
+        a, b = min(a, rows), min(b, rows)
+        if b > a:
+            secs.append(Section(s.side, a / rows, b / rows, s.kind, s.slope, s.t_s, s.q_m3s))
+    sub.sections = secs
+    o = oracle.Oracle(sub)
+    o.run(1)                      # warm (page-in)
+    steps, elapsed = 0, 0.0
+    while elapsed < seconds_target:
+        t0 = time.perf_counter()
+        o.run(1)
+        elapsed += time.perf_counter() - t0
+        steps += 1
+    v = sub.nx * sub.ny * steps / elapsed / 1e9
+    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"FP64 C oracle, {sub.nx}x{rows} full-width strip of the workload, {steps} steps, "
+                      f"{elapsed:.1f} s, OpenMP {threads} threads"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    prob, wname = workload(args.workload)
+    cb = cpu_baseline(prob, seconds_target=max(5.0, min(30.0, 4.0 * args.steps)))
+    line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wname, "nx": prob.nx, "ny": prob.ny, "sample": cb["sample"]},
+            "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import paper_2204_10323_gb300 as F
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    prob, wname = workload(args.workload)
+    ncell = prob.nx * prob.ny
+    kernel = {"rows": F.KERNEL_ROWS, "tiled": F.KERNEL_TILED, "reference": F.KERNEL_REFERENCE}[args.kernel]
+    sim = F.Sim(prob, precision=F.F32, kernel=kernel, steps_per_launch=args.k, use_graph=args.graph)
+    E = prob.opts.epoch_steps
+    h0, qx0, qy0 = prob.initial_state(np.float32)
+    stream = torch.cuda.current_stream()
+
+    # warm-up (also moves the clock past one epoch start)
+    for _ in range(args.warmup):
+        sim.step(1)
+    sim.sync()
+
+    # timed region: K steps, one event pair per step on the library's stream
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    step0 = int(sim.ledger()["step"])
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        sim.step(1)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    sim.sync()
+    L = sim.ledger()
+    # steps that did not start an epoch launch the step kernel alone
+    kern = [per[k] for k in range(args.steps) if (step0 + k) % E != 0]
+    kern_ms = statistics.mean(kern) if kern else statistics.mean(per)
+    n_epochs = sum(1 for k in range(args.steps) if (step0 + k) % E == 0)
+    launches = args.steps * (1 if args.kernel != "tiled" else 1) + n_epochs * (1 + (1 if sim_inflows(prob) else 0))
+
+    value = world * ncell * args.steps / (total_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_CELL * ncell / (kern_ms * 1e-3) / 1e9
+    traffic = None
+    if args.traffic_bytes:
+        traffic = float(args.traffic_bytes)
+
+    # end to end through the C ABI with host buffers: upload state, K steps, read depth + ledger
+    pin_h = torch.from_numpy(h0).pin_memory()
+    pin_qx = torch.from_numpy(qx0).pin_memory()
+    pin_qy = torch.from_numpy(qy0).pin_memory()
+    out_h = torch.empty_like(pin_h).pin_memory()
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.write_state(pin_h.numpy(), pin_qx.numpy(), pin_qy.numpy())
+    sim.step(e2e_steps)
+    F.flood_read(sim.h, F.FIELD_H, __import__("ctypes").c_void_p(out_h.data_ptr()), out_h.numel() * 4, 0)
+    led = sim.ledger()
+    e2e_s = time.perf_counter() - t0
+    h2d = (pin_h.numel() + pin_qx.numel() + pin_qy.numel()) * 4
+    d2h = out_h.numel() * 4 + 9 * 8
+    e2e = {"value": ncell * e2e_steps / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+           "what": f"flood_write_state from pinned host (h, qx, qy), flood_step({e2e_steps}), "
+                   f"flood_read(depth) + ledger to host"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wname, "nx": prob.nx, "ny": prob.ny, "kernel": args.kernel,
+                       "steps_per_launch": args.k, "epoch_steps": E, "l2": "inputs larger than L2 (5.4 GB state)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "bytes_per_cell": BYTES_PER_CELL, "kernel_ms": kern_ms},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "ledger": {k: L[k] for k in ("t", "dt", "V_in", "V_out", "V_clip", "volume")}}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob, seconds_target=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def sim_inflows(prob):
+    return any(s.kind == 0 for s in prob.sections)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c3")
+    ap.add_argument("--kernel", default="rows", choices=["rows", "tiled", "reference"])
+    ap.add_argument("--k", type=int, default=0, help="steps per launch (tiled kernel)")
+    ap.add_argument("--graph", action="store_true")
+    ap.add_argument("--traffic-bytes", type=float, default=None)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

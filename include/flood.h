@@ -1,0 +1,231 @@
+/*
+ * flood.h -- C ABI of the GB300 (sm_103a) local-inertial shallow-water
+ * flood model of Pierce et al., "Accelerating Physics Simulations with TPUs:
+ * An Inundation Modeling Example" (Methods, "Shallow Water Equations").
+ *
+ * One time step (Eq. 3-4 with the boundary conditions of Eq. 5-6):
+ *   1. boundary faces: inflow sections get the Eq. 6 distribution of the
+ *      hydrograph discharge Q_in(t), outflow sections the Eq. 5 discharge of
+ *      each boundary cell, every other border face is a closed wall (q = 0);
+ *   2. every interior face: q' = (q - g dt h_f (eta_R - eta_L)/dx)
+ *                                / (1 + g dt n_f^2 |q| h_f^(-7/3))          (Eq. 3)
+ *      with eta = h + z, h_f = max(eta_L, eta_R) - max(z_L, z_R),
+ *      n_f = (n_L + n_R)/2, and q' = 0 when h_f <= h_dry;
+ *   3. every cell: h' = h + dt ((qx_W - qx_E) + (qy_S - qy_N)) / dx       (Eq. 4)
+ *      and h' < 0 is set to 0 with the removed volume booked as V_clip.
+ * The time step is constant, or chosen every E steps by the CFL rule
+ * dt = min(dt_cap, alpha dx / sqrt(g h_max)).
+ *
+ * Layout (device and host arrays alike): row-major, x fastest; cell (i, j)
+ * at j*nx + i (host) for i < nx, j < ny.  Depth h, bed z and roughness n are
+ * ny x nx; the x-face array qx is ny x (nx+1) with qx[j][i] the west face of
+ * cell i; the y-face array qy is (ny+1) x nx with qy[j][i] the south face of
+ * cell (i, j).  Face fluxes are per unit width (m^2/s), positive towards +x
+ * or +y.  Element type of every grid array passed in or out: float for
+ * FLOOD_F32 handles, double for FLOOD_F64 handles.  Hydrograph tables,
+ * fractions, slopes and ledger values are always double.
+ *
+ * Every function returns a flood_status (0 = FLOOD_OK, < 0 = error) and never
+ * aborts or traps.  Errors are sticky per handle: after FLOOD_ERR_NONFINITE,
+ * FLOOD_ERR_CUDA or FLOOD_ERR_TIMEOUT, stepping calls return FLOOD_ERR_STATE
+ * until flood_write_state() installs a new state.  The message of the last
+ * error is available from flood_last_error().
+ *
+ * Memory and streams: the handle owns all device memory (taken from the
+ * PyTorch CUDA caching allocator) and issues all work on the stream given in
+ * flood_opts (or the current PyTorch stream of the current device at
+ * creation).  Input arrays are copied at the call; output arrays are
+ * caller-owned.  A handle must not be used by two threads at once.
+ */
+#ifndef FLOOD_H
+#define FLOOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FLOOD_OK = 0,
+    FLOOD_ERR_ARG = -1,          /* invalid argument (sizes, pointers, options, sections) */
+    FLOOD_ERR_OOM = -2,          /* device allocation failed */
+    FLOOD_ERR_CUDA = -3,         /* a CUDA call or kernel launch failed */
+    FLOOD_ERR_NONFINITE = -4,    /* NaN or Inf depth detected at an epoch start */
+    FLOOD_ERR_CFL = -5,          /* reserved: CFL limit exceeded (counted in the ledger) */
+    FLOOD_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
+    FLOOD_ERR_STATE = -7,        /* handle is in an error state */
+    FLOOD_ERR_UNSUPPORTED = -8   /* option not available for this precision or size */
+} flood_status;
+
+typedef enum { FLOOD_F32 = 0, FLOOD_F64 = 1 } flood_precision;
+
+/* BoundarySide and the inflow/outflow kinds (Appendix, "Inputs"; Methods). */
+typedef enum { FLOOD_XMIN = 0, FLOOD_XMAX = 1, FLOOD_YMIN = 2, FLOOD_YMAX = 3 } flood_side;
+typedef enum { FLOOD_INFLOW = 0, FLOOD_OUTFLOW = 1 } flood_bc_kind;
+
+/* Grid: nx x ny square cells of size dx (m) (Appendix "Inputs": unpadded_dem, resolution). */
+typedef struct {
+    int32_t nx, ny;
+    double dx;
+    int32_t precision;           /* flood_precision */
+} flood_grid;
+
+/*
+ * One boundary section (Methods, inflow/outflow boundary conditions): the
+ * contiguous cells [floor(frac_start L + 1/2), floor(frac_end L + 1/2)) along
+ * `side` (L = ny for x sides, nx for y sides).  Inflow sections carry the
+ * hydrograph Q_in(t) (m^3/s) as n_pts points (t_s ascending), interpolated
+ * linearly and held constant past both ends, and the channel slope S_in.
+ * Outflow sections carry S_out.  Sections must not share a boundary face.
+ * The tables are copied at flood_create.
+ */
+typedef struct {
+    int32_t side;                /* flood_side */
+    int32_t kind;                /* flood_bc_kind */
+    double frac_start, frac_end;
+    double slope;
+    const double *t_s, *q_m3s;   /* inflow only; host arrays of n_pts */
+    int32_t n_pts;
+} flood_bc_section;
+
+/* Kernel families for the forward step (FLOOD_F32; FLOOD_F64 always uses REFERENCE). */
+typedef enum {
+    FLOOD_KERNEL_AUTO = 0,
+    FLOOD_KERNEL_REFERENCE = 1,  /* one thread per cell, IEEE ops in the oracle's order */
+    FLOOD_KERNEL_ROWS = 2,       /* one warp per 128-column strip, float4 row streaming */
+    FLOOD_KERNEL_TILED = 3       /* shared-memory tiles, K steps per launch (temporal blocking) */
+} flood_kernel;
+
+typedef struct {
+    double g;                    /* 9.81 m/s^2 */
+    double h_dry;                /* dry-face threshold on h_f (m), 1e-3 */
+    double cfl_alpha;            /* 0.7 */
+    double dt_cap;               /* upper bound of the CFL time step (s) */
+    double dt_const;             /* constant time step (s), the paper's 0.1 */
+    int32_t dt_mode;             /* 0 CFL epochs, 1 constant dt */
+    int32_t epoch_steps;         /* E: steps per CFL epoch (1..1024) */
+    int32_t bc_form;             /* 0 cell discharge dx h^(5/3) sqrt(S)/n, 1 literal dx^2 h^(2/3) sqrt(S)/n */
+    int32_t kernel;              /* flood_kernel */
+    int32_t steps_per_launch;    /* K for FLOOD_KERNEL_TILED (must divide E; 0 = auto) */
+    int32_t tile_x, tile_y;      /* tile shape for FLOOD_KERNEL_TILED (0 = auto) */
+    int32_t use_graph;           /* 1: replay whole epochs from a captured CUDA graph */
+    void *stream;                /* cudaStream_t, NULL = current PyTorch stream */
+} flood_opts;
+
+typedef struct flood_handle flood_handle;
+
+/* Fields for flood_read. */
+typedef enum {
+    FLOOD_FIELD_H = 0, FLOOD_FIELD_QX = 1, FLOOD_FIELD_QY = 2, FLOOD_FIELD_Z = 3,
+    FLOOD_FIELD_N = 4,
+    FLOOD_FIELD_LEDGER = 5       /* FLOOD_LEDGER_LEN doubles, see flood_ledger_index */
+} flood_field;
+
+/* Ledger entries (doubles) returned by flood_read(FLOOD_FIELD_LEDGER). */
+typedef enum {
+    FLOOD_LEDGER_T = 0,          /* simulated time (s) */
+    FLOOD_LEDGER_DT = 1,         /* time step in force (s) */
+    FLOOD_LEDGER_V_IN = 2,       /* cumulative inflow volume sum dt Q_in (m^3) */
+    FLOOD_LEDGER_V_OUT = 3,      /* cumulative outflow volume (m^3) */
+    FLOOD_LEDGER_V_CLIP = 4,     /* cumulative volume added by the depth clip (m^3) */
+    FLOOD_LEDGER_VOLUME = 5,     /* stored volume sum h dx^2 now (m^3) */
+    FLOOD_LEDGER_H_MAX = 6,      /* max depth at the last epoch start (m) */
+    FLOOD_LEDGER_STEP = 7,       /* steps taken */
+    FLOOD_LEDGER_CFL_EXCEED = 8, /* epochs whose dt exceeded dx/sqrt(g h_max) at their end */
+    FLOOD_LEDGER_LEN = 9
+} flood_ledger_index;
+
+/* Fill *o with the defaults listed beside each flood_opts field. */
+void flood_default_opts(flood_opts *o);
+
+/*
+ * Create a simulation (Appendix "Inputs"; Methods "Data": the DEM grid).
+ * dem, manning: host arrays of ny*nx elements of the grid's precision; manning
+ * may be NULL for a uniform n = 0.03.  sections: n_sections descriptors (may
+ * be 0).  opts may be NULL for defaults.  The initial state is dry (h = q = 0)
+ * at t = 0.  On success *out receives the handle; on failure *out is NULL and
+ * the error text is available from flood_last_error(NULL).
+ */
+flood_status flood_create(const flood_grid *grid, const void *dem, const void *manning,
+                          const flood_bc_section *sections, int32_t n_sections,
+                          const flood_opts *opts, flood_handle **out);
+
+/* Advance n_steps >= 0 steps (Eq. 3-6, the time-step rule).  Asynchronous on the
+ * handle's stream: a NaN/Inf found at an epoch start is reported by the next
+ * flood_sync or flood_read. */
+flood_status flood_step(flood_handle *h, int64_t n_steps);
+
+/* Wait for the handle's stream and return its sticky status. */
+flood_status flood_sync(flood_handle *h);
+
+/*
+ * Copy a field out.  dst holds `bytes` bytes (must equal the field's size:
+ * ny*nx, ny*(nx+1) or (ny+1)*nx elements, or FLOOD_LEDGER_LEN doubles);
+ * dst_on_device != 0 means a device pointer on the handle's device.
+ * Synchronous on the handle's stream.
+ */
+flood_status flood_read(flood_handle *h, int32_t field, void *dst, size_t bytes, int32_t dst_on_device);
+
+/*
+ * Install a state (initial condition or resume from a checkpoint): depth
+ * (ny*nx), qx (ny*(nx+1)) and qy ((ny+1)*nx), host or device (src_on_device).
+ * qx or qy may be NULL for zero fluxes.  Clears an error state.  The time,
+ * step count and volumes are not changed (see flood_set_clock).
+ */
+flood_status flood_write_state(flood_handle *h, const void *depth, const void *qx, const void *qy,
+                               int32_t src_on_device);
+
+/* Set time, step count and cumulative volumes (a checkpoint's ledger).  The
+ * next step starts a new CFL epoch when step % E == 0. */
+flood_status flood_set_clock(flood_handle *h, double t, int64_t step, double dt, double v_in,
+                             double v_out, double v_clip);
+
+/* Replace the per-cell Manning field (ny*nx, host or device). */
+flood_status flood_set_manning(flood_handle *h, const void *manning, int32_t src_on_device);
+
+/*
+ * Advance n_steps and record the depth at n_gauges gauge cells after every
+ * step: out[k*n_gauges + g] = h(gauge g) after step k, as doubles.  gauge_cells
+ * are flat cell indices j*nx + i (host array).  out is host or device memory.
+ */
+flood_status flood_run_gauges(flood_handle *h, int64_t n_steps, const int64_t *gauge_cells,
+                              int32_t n_gauges, double *out, int32_t out_on_device);
+
+/*
+ * Reverse-mode gradient (not in the paper; for the calibration use it names as
+ * future work) of L = sum_k sum_g dLdh[k*n_gauges+g] * h_g(after step k) over
+ * the next n_steps steps from the current state, with the time-step schedule
+ * held fixed (chosen by the forward sweep).  Binomial checkpointing keeps at
+ * most n_checkpoints states on the device (>= 1).  dLdh: host doubles.
+ * dLdn_out: ny*nx elements of the grid's precision, host (out_on_device = 0)
+ * or device.  dLdh0_out: optional (NULL) gradient with respect to the
+ * starting depth.  The handle's state, clock and ledger are unchanged.
+ * Branch conventions at non-smooth points: max() sends its derivative to the
+ * lower-index cell on ties, d|q|/dq = 0 at q = 0, and the dry-face test, the
+ * outflow dry test and the depth clip are held as constant masks; the Eq. 6
+ * inflow level is differentiated exactly (implicit function theorem).
+ */
+flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const int64_t *gauge_cells,
+                           int32_t n_gauges, const double *dLdh, int32_t n_checkpoints,
+                           void *dLdn_out, void *dLdh0_out, int32_t out_on_device);
+
+/* Number of forward steps the last flood_adjoint call recomputed (revolve cost). */
+int64_t flood_adjoint_forward_steps(const flood_handle *h);
+
+/* Release all device memory of the handle (NULL is accepted). */
+flood_status flood_destroy(flood_handle *h);
+
+/* Text of the handle's last error ("" if none); with NULL, the calling thread's
+ * last flood_create error. */
+const char *flood_last_error(const flood_handle *h);
+
+/* Library version string. */
+const char *flood_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLOOD_H */

@@ -1,0 +1,294 @@
+"""GB300 (sm_103a) local-inertial shallow-water flood model behind a C ABI.
+
+Python binding of ``include/flood.h``: argument marshalling only.  Every step
+of the method (Eq. 3-6 of Pierce et al., the CFL rule, the ledgers, the
+adjoint) runs in the CUDA kernels of ``libflood_gb300.so``; PyTorch provides
+the device memory allocator and streams.  Importing this package loads the
+library and fails loudly if it is missing or cannot be built; there is no CPU
+fallback.
+
+The functions ``flood_create``, ``flood_step``, ``flood_read``, ... mirror the
+C entry points one to one; :class:`Sim` wraps a handle for NumPy / torch users.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_CFL, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+F32, F64 = 0, 1
+XMIN, XMAX, YMIN, YMAX = 0, 1, 2, 3
+INFLOW, OUTFLOW = 0, 1
+KERNEL_AUTO, KERNEL_REFERENCE, KERNEL_ROWS, KERNEL_TILED = 0, 1, 2, 3
+FIELD_H, FIELD_QX, FIELD_QY, FIELD_Z, FIELD_N, FIELD_LEDGER = 0, 1, 2, 3, 4, 5
+LEDGER_KEYS = ("t", "dt", "V_in", "V_out", "V_clip", "volume", "h_max", "step", "cfl_exceed")
+
+
+class FloodError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"flood status {status}: {msg}")
+        self.status = status
+
+
+class flood_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("dx", C.c_double), ("precision", C.c_int32)]
+
+
+class flood_bc_section(C.Structure):
+    _fields_ = [("side", C.c_int32), ("kind", C.c_int32), ("frac_start", C.c_double),
+                ("frac_end", C.c_double), ("slope", C.c_double),
+                ("t_s", C.POINTER(C.c_double)), ("q_m3s", C.POINTER(C.c_double)), ("n_pts", C.c_int32)]
+
+
+class flood_opts(C.Structure):
+    _fields_ = [("g", C.c_double), ("h_dry", C.c_double), ("cfl_alpha", C.c_double), ("dt_cap", C.c_double),
+                ("dt_const", C.c_double), ("dt_mode", C.c_int32), ("epoch_steps", C.c_int32),
+                ("bc_form", C.c_int32), ("kernel", C.c_int32), ("steps_per_launch", C.c_int32),
+                ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("use_graph", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+_lib = None
+LIB_PATH = None
+
+
+def _load():
+    global _lib, LIB_PATH
+    if _lib is not None:
+        return _lib
+    import torch  # loads c10 / c10_cuda / cudart before the library
+    if torch.cuda.is_available():
+        torch.cuda.init()        # the caching allocator must be initialised before the library allocates
+    path = _build.build()
+    L = C.CDLL(path, mode=C.RTLD_GLOBAL)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    H = C.c_void_p
+    L.flood_default_opts.argtypes = [C.POINTER(flood_opts)]
+    L.flood_default_opts.restype = None
+    L.flood_create.argtypes = [C.POINTER(flood_grid), vp, vp, C.POINTER(flood_bc_section), i32,
+                               C.POINTER(flood_opts), C.POINTER(H)]
+    L.flood_step.argtypes = [H, i64]
+    L.flood_sync.argtypes = [H]
+    L.flood_read.argtypes = [H, i32, vp, C.c_size_t, i32]
+    L.flood_write_state.argtypes = [H, vp, vp, vp, i32]
+    L.flood_set_clock.argtypes = [H, dbl, i64, dbl, dbl, dbl, dbl]
+    L.flood_set_manning.argtypes = [H, vp, i32]
+    L.flood_run_gauges.argtypes = [H, i64, C.POINTER(C.c_int64), i32, vp, i32]
+    L.flood_adjoint.argtypes = [H, i64, C.POINTER(C.c_int64), i32, C.POINTER(C.c_double), i32, vp, vp, i32]
+    L.flood_adjoint_forward_steps.argtypes = [H]
+    L.flood_adjoint_forward_steps.restype = i64
+    L.flood_destroy.argtypes = [H]
+    L.flood_last_error.argtypes = [H]
+    L.flood_last_error.restype = C.c_char_p
+    L.flood_version.restype = C.c_char_p
+    for name in ("flood_create", "flood_step", "flood_sync", "flood_read", "flood_write_state",
+                 "flood_set_clock", "flood_set_manning", "flood_run_gauges", "flood_adjoint", "flood_destroy"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    LIB_PATH = path
+    return L
+
+
+def lib():
+    return _load()
+
+
+def _check(st: int, handle=None):
+    if st != OK:
+        msg = lib().flood_last_error(handle).decode(errors="replace")
+        raise FloodError(st, msg)
+
+
+def default_opts() -> flood_opts:
+    o = flood_opts()
+    lib().flood_default_opts(C.byref(o))
+    return o
+
+
+# ------------------------------------------------------------------ C-ABI mirrors
+def flood_create(grid: flood_grid, dem, manning, sections, n_sections: int, opts: Optional[flood_opts]):
+    h = C.c_void_p()
+    st = lib().flood_create(C.byref(grid), dem, manning, sections, n_sections,
+                            None if opts is None else C.byref(opts), C.byref(h))
+    _check(st, None)
+    return h
+
+
+def flood_step(h, n_steps: int):
+    _check(lib().flood_step(h, int(n_steps)), h)
+
+
+def flood_sync(h):
+    return lib().flood_sync(h)
+
+
+def flood_read(h, field: int, dst_ptr, nbytes: int, dst_on_device: int):
+    _check(lib().flood_read(h, int(field), dst_ptr, int(nbytes), int(dst_on_device)), h)
+
+
+def flood_write_state(h, depth, qx, qy, src_on_device: int):
+    _check(lib().flood_write_state(h, depth, qx, qy, int(src_on_device)), h)
+
+
+def flood_set_clock(h, t, step, dt, v_in, v_out, v_clip):
+    _check(lib().flood_set_clock(h, float(t), int(step), float(dt), float(v_in), float(v_out), float(v_clip)), h)
+
+
+def flood_set_manning(h, manning, src_on_device: int):
+    _check(lib().flood_set_manning(h, manning, int(src_on_device)), h)
+
+
+def flood_run_gauges(h, n_steps, gauge_cells, n_gauges, out, out_on_device):
+    _check(lib().flood_run_gauges(h, int(n_steps), gauge_cells, int(n_gauges), out, int(out_on_device)), h)
+
+
+def flood_adjoint(h, n_steps, gauge_cells, n_gauges, dLdh, n_checkpoints, dLdn_out, dLdh0_out, out_on_device):
+    _check(lib().flood_adjoint(h, int(n_steps), gauge_cells, int(n_gauges), dLdh, int(n_checkpoints), dLdn_out,
+                               dLdh0_out, int(out_on_device)), h)
+
+
+def flood_destroy(h):
+    lib().flood_destroy(h)
+
+
+def flood_last_error(h=None) -> str:
+    return lib().flood_last_error(h).decode(errors="replace")
+
+
+def flood_version() -> str:
+    return lib().flood_version().decode()
+
+
+# ------------------------------------------------------------------ convenience wrapper
+def _ptr(a):
+    """(pointer, on_device) of a contiguous NumPy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return C.c_void_p(a.ctypes.data), 0
+    import torch
+    if isinstance(a, torch.Tensor):
+        assert a.is_contiguous()
+        return C.c_void_p(a.data_ptr()), int(a.is_cuda)
+    raise TypeError(type(a))
+
+
+class Sim:
+    """One simulation handle.  ``problem`` is an ``inputs.Problem``-like object
+    (nx, ny, dx, z, n, sections, opts, h0/qx0/qy0)."""
+
+    def __init__(self, problem, precision: int = F32, kernel: int = KERNEL_AUTO, steps_per_launch: int = 0,
+                 tile=(0, 0), use_graph: bool = False, stream=None):
+        self.prob = problem
+        self.precision = precision
+        self.dtype = np.float32 if precision == F32 else np.float64
+        self.nx, self.ny = problem.nx, problem.ny
+        po = problem.opts
+        o = default_opts()
+        o.g, o.h_dry, o.cfl_alpha, o.dt_cap, o.dt_const = po.g, po.h_dry, po.cfl_alpha, po.dt_cap, po.dt_const
+        o.dt_mode, o.epoch_steps, o.bc_form = po.dt_mode, po.epoch_steps, po.bc_form
+        o.kernel, o.steps_per_launch = kernel, steps_per_launch
+        o.tile_x, o.tile_y = tile
+        o.use_graph = int(use_graph)
+        o.stream = None if stream is None else C.c_void_p(stream.cuda_stream)
+        self.opts = o
+        secs = (flood_bc_section * max(1, len(problem.sections)))()
+        self._keep = []
+        for k, s in enumerate(problem.sections):
+            t = np.ascontiguousarray(s.t_s if s.t_s is not None else np.zeros(1), np.float64)
+            q = np.ascontiguousarray(s.q_m3s if s.q_m3s is not None else np.zeros(1), np.float64)
+            self._keep += [t, q]
+            secs[k] = flood_bc_section(s.side, s.kind, s.frac_start, s.frac_end, s.slope,
+                                       t.ctypes.data_as(C.POINTER(C.c_double)),
+                                       q.ctypes.data_as(C.POINTER(C.c_double)),
+                                       t.size if s.kind == INFLOW else 0)
+        z = np.ascontiguousarray(problem.z, self.dtype)
+        n = np.ascontiguousarray(problem.n, self.dtype)
+        self.grid = flood_grid(self.nx, self.ny, float(problem.dx), precision)
+        self.h = flood_create(self.grid, C.c_void_p(z.ctypes.data), C.c_void_p(n.ctypes.data), secs,
+                              len(problem.sections), o)
+        if problem.h0 is not None or problem.qx0 is not None or problem.qy0 is not None:
+            h0, qx0, qy0 = problem.initial_state(self.dtype)
+            self.write_state(h0, qx0, qy0)
+
+    # -- state
+    def write_state(self, h, qx=None, qy=None):
+        arrs = [None if a is None else (np.ascontiguousarray(a, self.dtype) if isinstance(a, np.ndarray) else a)
+                for a in (h, qx, qy)]
+        ptrs = [_ptr(a) for a in arrs]
+        dev = max(p[1] for p in ptrs if p[0] is not None)
+        flood_write_state(self.h, ptrs[0][0], ptrs[1][0], ptrs[2][0], dev)
+
+    def read(self, field: int):
+        shape = {FIELD_H: (self.ny, self.nx), FIELD_QX: (self.ny, self.nx + 1), FIELD_QY: (self.ny + 1, self.nx),
+                 FIELD_Z: (self.ny, self.nx), FIELD_N: (self.ny, self.nx)}[field]
+        out = np.empty(shape, self.dtype)
+        flood_read(self.h, field, C.c_void_p(out.ctypes.data), out.nbytes, 0)
+        return out
+
+    def state(self):
+        return self.read(FIELD_H), self.read(FIELD_QX), self.read(FIELD_QY)
+
+    def ledger(self):
+        out = np.zeros(len(LEDGER_KEYS), np.float64)
+        flood_read(self.h, FIELD_LEDGER, C.c_void_p(out.ctypes.data), out.nbytes, 0)
+        return dict(zip(LEDGER_KEYS, out.tolist()))
+
+    def set_clock(self, t, step, dt, v_in=0.0, v_out=0.0, v_clip=0.0):
+        flood_set_clock(self.h, t, step, dt, v_in, v_out, v_clip)
+
+    def set_manning(self, n):
+        a = np.ascontiguousarray(n, self.dtype) if isinstance(n, np.ndarray) else n
+        p, dev = _ptr(a)
+        flood_set_manning(self.h, p, dev)
+
+    # -- stepping
+    def step(self, n_steps: int = 1, check: bool = False):
+        flood_step(self.h, n_steps)
+        if check:
+            self.sync()
+
+    def sync(self):
+        st = flood_sync(self.h)
+        _check(st, self.h)
+
+    def run_gauges(self, n_steps: int, gauges: np.ndarray, out=None):
+        cells = np.ascontiguousarray(gauges[:, 1].astype(np.int64) * self.nx + gauges[:, 0], np.int64)
+        if out is None:
+            out = np.zeros((n_steps, cells.size), np.float64)
+        p, dev = _ptr(out)
+        flood_run_gauges(self.h, n_steps, cells.ctypes.data_as(C.POINTER(C.c_int64)), cells.size, p, dev)
+        return out
+
+    def adjoint(self, n_steps: int, gauges: np.ndarray, dLdh: np.ndarray, n_checkpoints: int = 40,
+                want_dh0: bool = False):
+        cells = np.ascontiguousarray(gauges[:, 1].astype(np.int64) * self.nx + gauges[:, 0], np.int64)
+        seed = np.ascontiguousarray(dLdh, np.float64)
+        assert seed.shape == (n_steps, cells.size)
+        gn = np.zeros((self.ny, self.nx), self.dtype)
+        gh = np.zeros((self.ny, self.nx), self.dtype) if want_dh0 else None
+        flood_adjoint(self.h, n_steps, cells.ctypes.data_as(C.POINTER(C.c_int64)), cells.size,
+                      seed.ctypes.data_as(C.POINTER(C.c_double)), n_checkpoints, C.c_void_p(gn.ctypes.data),
+                      None if gh is None else C.c_void_p(gh.ctypes.data), 0)
+        return (gn, gh) if want_dh0 else gn
+
+    def adjoint_forward_steps(self) -> int:
+        return int(lib().flood_adjoint_forward_steps(self.h))
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            flood_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

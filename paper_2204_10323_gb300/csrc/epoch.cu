@@ -1,0 +1,218 @@
+// epoch.cu -- per-epoch and bookkeeping kernels: the time-step rule, the
+// Eq. 6 inflow distribution, and deterministic reductions (h_max, volume,
+// gauge gathers).
+#include <cfloat>
+
+#include "device_common.cuh"
+
+namespace flood {
+
+namespace {
+
+// Time-step rule at an epoch start: constant, frozen (adjoint replays), or
+// dt = min(dt_cap, alpha dx / sqrt(g h_max)); h_max = 0 gives dt_cap.
+__global__ void epoch_begin_kernel(Geom G, Ctrl *ctrl, double *t_list, int E, const double *fixed_dt)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double hmax = __longlong_as_double((long long)ctrl->hmax_bits);
+    if (!isfinite(hmax)) ctrl->status |= kStatusNonfinite;
+    if (ctrl->dt > 0.0 && hmax > 0.0 && ctrl->dt * sqrt(G.g * hmax) > G.dx) ctrl->cfl_exceed += 1.0;
+    double dt;
+    if (fixed_dt) dt = *fixed_dt;
+    else if (G.dt_mode == 1) dt = G.dt_const;
+    else if (!(hmax > 0.0)) dt = G.dt_cap;
+    else dt = fmin(G.dt_cap, G.cfl_alpha * G.dx / sqrt(G.g * hmax));
+    ctrl->dt = dt;
+    ctrl->h_max = hmax;
+    ctrl->hmax_bits = 0ull;
+    double t = ctrl->t;
+    t_list[0] = t;
+    for (int s = 0; s < E; s++) {
+        t = t + dt;
+        t_list[s + 1] = t;
+    }
+}
+
+// Linear interpolation in the hydrograph table, constant past both ends.
+__device__ double hydrograph(const double *ts, const double *qs, int n, double t)
+{
+    if (n <= 0) return 0.0;
+    if (t <= ts[0]) return qs[0];
+    for (int k = 1; k < n; k++)
+        if (t <= ts[k]) {
+            double w = (t - ts[k - 1]) / (ts[k] - ts[k - 1]);
+            return qs[k - 1] + w * (qs[k] - qs[k - 1]);
+        }
+    return qs[n - 1];
+}
+
+// Eq. 5 discharge of one cell (m^3/s) at depth hh.
+__device__ __forceinline__ double manning_cell(double hh, double sqrtS, double n, double dx, int form)
+{
+    if (form == 0) return dx * pow(hh, 5.0 / 3.0) * sqrtS / n;
+    return dx * dx * pow(hh, 2.0 / 3.0) * sqrtS / n;
+}
+
+template <typename T>
+__device__ double section_total(const InflowSec &S, const int64_t *cells, const T *z, const T *n,
+                                double W, double dx, int form)
+{
+    double s = 0.0;
+    for (int c = threadIdx.x; c < S.ncell; c += 32) {
+        int64_t idx = cells[S.cell0 + c];
+        double hh = W - (double)z[idx];
+        if (hh > 0.0) s += manning_cell(hh, S.sqrtS, (double)n[idx], dx, form);
+    }
+    return warp_sum(s);
+}
+
+// Eq. 6 for (step s of the epoch, inflow section k), one warp: bisection for
+// the level W with sum_c Q_c(W) = Q_in(t_s) on [min z, min z + H] (H doubled
+// from 1 m), 200 halvings at most or a bracket below 1e-12 m, W = upper end;
+// then each cell's discharge scaled by Q_in / sum, stored as unit-width flux.
+template <typename T>
+__global__ void inflow_kernel(Geom G, const InflowSec *secs, int nsec, const int64_t *cells,
+                              const double *tab_t, const double *tab_q, const T *z, const T *n,
+                              const double *t_list, T *inflow_q, int n_slots, double *inflow_Q)
+{
+    const int s = blockIdx.x, k = blockIdx.y, lane = threadIdx.x;
+    const InflowSec S = secs[k];
+    const double t = t_list[s];
+    const double Q = hydrograph(tab_t + S.tab0, tab_q + S.tab0, S.ntab, t);
+    T *out = inflow_q + (size_t)s * n_slots + S.slot0;
+    if (lane == 0) inflow_Q[(size_t)s * nsec + k] = Q;
+    double zmin = DBL_MAX;
+    for (int c = lane; c < S.ncell; c += 32) zmin = fmin(zmin, (double)z[cells[S.cell0 + c]]);
+    for (int o = 16; o > 0; o >>= 1) zmin = fmin(zmin, __shfl_xor_sync(0xffffffffu, zmin, o));
+    if (!(Q > 0.0) || S.ncell == 0) {
+        for (int c = lane; c < S.ncell; c += 32) out[c] = T(0);
+        return;
+    }
+    const double dx = G.dx;
+    const int form = G.bc_form;
+    double Hb = 1.0;
+    while (section_total(S, cells, z, n, zmin + Hb, dx, form) < Q && Hb < 1e12) Hb *= 2.0;
+    double lo = zmin, hi = zmin + Hb;
+    for (int it = 0; it < 200 && hi - lo >= 1e-12; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (section_total(S, cells, z, n, mid, dx, form) < Q) lo = mid;
+        else hi = mid;
+    }
+    const double W = hi;
+    const double total = section_total(S, cells, z, n, W, dx, form);
+    for (int c = lane; c < S.ncell; c += 32) {
+        int64_t idx = cells[S.cell0 + c];
+        double hh = W - (double)z[idx];
+        double w = hh > 0.0 ? manning_cell(hh, S.sqrtS, (double)n[idx], dx, form) : 0.0;
+        out[c] = T((w * (Q / total)) / dx);
+    }
+}
+
+template <typename T>
+__global__ void hmax_kernel(Geom G, const T *h, Ctrl *ctrl)
+{
+    __shared__ double red[32];
+    double m = 0.0;
+    const size_t N = (size_t)G.nx * G.ny;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+        size_t j = c / G.nx, i = c % G.nx;
+        double v = (double)h[j * G.pitch + i];
+        m = (v > m || v != v) ? v : m;
+    }
+    m = block_reduce<true>(m, red);
+    if (threadIdx.x == 0) atomic_max_nonneg(&ctrl->hmax_bits, m);
+}
+
+// Pass 1: block b sums rows b, b + nb, ... (fixed order for a fixed launch shape).
+template <typename T>
+__global__ void volume_partial_kernel(Geom G, const T *h, double *partials)
+{
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int j = blockIdx.x; j < G.ny; j += gridDim.x)
+        for (int i = threadIdx.x; i < G.nx; i += blockDim.x) s += (double)h[(size_t)j * G.pitch + i];
+    s = block_reduce<false>(s, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void volume_final_kernel(const double *partials, int np, double area, double *out)
+{
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) s += partials[k];
+    s = block_reduce<false>(s, red);
+    if (threadIdx.x == 0) *out = s * area;
+}
+
+template <typename T>
+__global__ void gauges_kernel(Geom G, const T *h, const int64_t *cells, int ng, double *out)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ng) return;
+    int64_t c = cells[k];
+    out[k] = (double)h[(c / G.nx) * G.pitch + (c % G.nx)];
+}
+
+}  // namespace
+
+cudaError_t launch_epoch_begin(const Geom &g, Ctrl *ctrl, double *t_list, int E, int /*unused*/,
+                               const double *fixed_dt, cudaStream_t st)
+{
+    epoch_begin_kernel<<<1, 32, 0, st>>>(g, ctrl, t_list, E, fixed_dt);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_inflow(const Geom &g, const InflowSec *secs, int nsec, const int64_t *sec_cells,
+                          const int8_t * /*sec_side*/, const double *tab_t, const double *tab_q,
+                          const T *z, const T *n, const double *t_list, int E, T *inflow_q, int n_slots,
+                          double *inflow_Q, cudaStream_t st)
+{
+    if (nsec == 0) return cudaSuccess;
+    dim3 grid(E, nsec);
+    inflow_kernel<T><<<grid, 32, 0, st>>>(g, secs, nsec, sec_cells, tab_t, tab_q, z, n, t_list, inflow_q,
+                                          n_slots, inflow_Q);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_hmax(const Geom &g, const T *h, Ctrl *ctrl, cudaStream_t st)
+{
+    size_t N = (size_t)g.nx * g.ny;
+    int blocks = (int)((N + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    hmax_kernel<T><<<blocks, 256, 0, st>>>(g, h, ctrl);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_volume(const Geom &g, const T *h, double *partials, int n_partials, double *out,
+                          cudaStream_t st)
+{
+    volume_partial_kernel<T><<<n_partials, 256, 0, st>>>(g, h, partials);
+    volume_final_kernel<<<1, 256, 0, st>>>(partials, n_partials, g.dx * g.dx, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gauges(const Geom &g, const T *h, const int64_t *cells, int G, double *out,
+                          cudaStream_t st)
+{
+    if (G <= 0) return cudaSuccess;
+    gauges_kernel<T><<<(G + 127) / 128, 128, 0, st>>>(g, h, cells, G, out);
+    return cudaGetLastError();
+}
+
+#define FLOOD_INST(T)                                                                                      \
+    template cudaError_t launch_inflow<T>(const Geom &, const InflowSec *, int, const int64_t *,             \
+                                          const int8_t *, const double *, const double *, const T *,       \
+                                          const T *, const double *, int, T *, int, double *, cudaStream_t); \
+    template cudaError_t launch_hmax<T>(const Geom &, const T *, Ctrl *, cudaStream_t);                     \
+    template cudaError_t launch_volume<T>(const Geom &, const T *, double *, int, double *, cudaStream_t);   \
+    template cudaError_t launch_gauges<T>(const Geom &, const T *, const int64_t *, int, double *, cudaStream_t);
+FLOOD_INST(float)
+FLOOD_INST(double)
+#undef FLOOD_INST
+
+}  // namespace flood

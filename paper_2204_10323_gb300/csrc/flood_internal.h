@@ -1,0 +1,110 @@
+// flood_internal.h -- plain structs shared by the runtime (flood_api.cpp) and
+// the CUDA kernels.  No PyTorch types; included by host C++ and by nvcc.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace flood {
+
+constexpr int kMaxEpoch = 1024;       // largest E (steps per CFL epoch)
+constexpr int kBcWall = 0, kBcInflow = 1, kBcOutflow = 2;
+
+// Device status bits (sticky, OR-ed by kernels).
+constexpr int kStatusNonfinite = 1;
+constexpr int kStatusTimeout = 2;
+
+// Device-resident control block of one simulation.
+struct Ctrl {
+    double t;                     // time at the start of the next step
+    double dt;                    // time step of the current epoch
+    double V_in, V_out, V_clip;   // cumulative volumes (m^3)
+    double h_max;                 // depth maximum measured at the current epoch start
+    double cfl_exceed;            // epochs whose dt broke dx / sqrt(g h_max) at their end
+    unsigned long long hmax_bits; // running max of h (bits of a non-negative double)
+    int status;                   // kStatus* bits
+    int pad;
+};
+
+// One inflow section as seen by the Eq. 6 solver.
+struct InflowSec {
+    int ncell;                    // cells along the section
+    int cell0;                    // offset into the section cell-index array
+    int slot0;                    // first column of this section in the per-step flux rows
+    int tab0, ntab;               // hydrograph table offset / length
+    int pad;
+    double sqrtS;                 // sqrt(S_in)
+};
+
+// Geometry and physical constants (both precisions keep them in double here;
+// kernels cast to their working type).
+struct Geom {
+    int nx, ny;
+    int pitch;                    // elements per row of every grid array
+    int bc_form;
+    double dx, g, h_dry;
+    double cfl_alpha, dt_cap, dt_const;
+    int dt_mode, epoch_steps;
+};
+
+// Boundary description, one entry per boundary cell: sides laid out as
+// [xmin: ny][xmax: ny][ymin: nx][ymax: nx].
+struct Boundary {
+    const int8_t *type;           // kBcWall / kBcInflow / kBcOutflow
+    const int32_t *slot;          // inflow: column in the per-step inflow flux row
+    const double *sqrtS;          // outflow: sqrt(S_out)
+};
+
+template <typename T>
+struct StepArgs {
+    Geom geo;
+    const T *h, *qx, *qy, *z, *n;
+    T *h_out, *qx_out, *qy_out;
+    Boundary bc;
+    const T *inflow_q;            // E x n_slots unit-width inflow fluxes (into the domain)
+    int n_slots;
+    const double *inflow_Q;       // E x n_inflow_sections discharges (for V_in)
+    int n_inflow_sec;
+    const double *t_list;         // E + 1 start times of the epoch's steps
+    Ctrl *ctrl;
+    int s;                        // step index inside the epoch (first step of the launch)
+    int k_steps;                  // steps done by this launch (1 except the tiled kernel)
+    int want_hmax;                // 1: record max depth after the launch's last step
+    const int64_t *gauge_cells;   // flat j*nx+i; h after each step -> gauge_out
+    int n_gauges;
+    double *gauge_out;            // (k_steps) x n_gauges rows for this launch, or null
+    int tile_x, tile_y;           // tiled kernel only
+};
+
+// ---------------------------------------------------------------- launchers
+// Each returns the cudaError_t of the launch.
+template <typename T>
+cudaError_t launch_step_reference(const StepArgs<T> &a, cudaStream_t st);
+cudaError_t launch_step_rows(const StepArgs<float> &a, cudaStream_t st);
+cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st);
+size_t tiled_smem_bytes(int tile_x, int tile_y, int k);
+
+// Epoch start: choose dt from h_max (or constant), fill t_list, reset the
+// running maximum, count CFL exceedances, flag NaN/Inf.
+cudaError_t launch_epoch_begin(const Geom &g, Ctrl *ctrl, double *t_list, int E, int fixed_dt_mode,
+                               const double *fixed_dt, cudaStream_t st);
+// Eq. 6 for every (step of the epoch, inflow section) pair.
+template <typename T>
+cudaError_t launch_inflow(const Geom &g, const InflowSec *secs, int nsec, const int64_t *sec_cells,
+                          const int8_t *sec_side, const double *tab_t, const double *tab_q,
+                          const T *z, const T *n, const double *t_list, int E, T *inflow_q,
+                          int n_slots, double *inflow_Q, cudaStream_t st);
+// h_max of a state into ctrl->hmax_bits (max with what is there).
+template <typename T>
+cudaError_t launch_hmax(const Geom &g, const T *h, Ctrl *ctrl, cudaStream_t st);
+// Deterministic two-pass sum of h * dx^2 into *out (double, device).
+template <typename T>
+cudaError_t launch_volume(const Geom &g, const T *h, double *partials, int n_partials, double *out,
+                          cudaStream_t st);
+// Gather h at gauge cells into out[0..G).
+template <typename T>
+cudaError_t launch_gauges(const Geom &g, const T *h, const int64_t *cells, int G, double *out,
+                          cudaStream_t st);
+
+}  // namespace flood

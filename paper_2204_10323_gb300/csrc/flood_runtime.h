@@ -1,0 +1,93 @@
+// flood_runtime.h -- the handle behind the C ABI and the runtime's internal
+// functions (host C++ only; uses no PyTorch types in its interface).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "flood.h"
+#include "flood_internal.h"
+
+struct flood_adjoint_state;   // adjoint work buffers (flood_adjoint.cpp)
+
+struct flood_handle {
+    flood::Geom geo{};
+    int prec = 0;                 // flood_precision
+    size_t esz = 4;               // bytes per grid element
+    flood_opts opts{};
+    int kernel = FLOOD_KERNEL_REFERENCE;
+    int k_per_launch = 1;
+    int tile_x = 128, tile_y = 32;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+
+    // state (ping-pong) and static fields, pitched rows of geo.pitch elements
+    void *h[2] = {nullptr, nullptr}, *qx[2] = {nullptr, nullptr}, *qy[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *z = nullptr, *n = nullptr;
+
+    // boundary description and the per-epoch inflow solution
+    int8_t *bc_type = nullptr;
+    int32_t *bc_slot = nullptr;
+    double *bc_sqrtS = nullptr;
+    flood::InflowSec *secs_dev = nullptr;
+    int n_in = 0, n_slots = 1;
+    int64_t *sec_cells = nullptr;
+    double *tab_t = nullptr, *tab_q = nullptr;
+    void *inflow_q = nullptr;     // E x n_slots
+    double *inflow_Q = nullptr;   // E x n_in
+    double *t_list = nullptr;     // E + 1
+    flood::Ctrl *ctrl = nullptr;
+
+    // reductions and gauges
+    double *vol_partials = nullptr, *vol_out = nullptr;
+    int n_partials = 1024;
+    int64_t *gauge_dev = nullptr;
+    int gauge_cap = 0;
+    double *gauge_buf = nullptr;
+    size_t gauge_buf_cap = 0;
+
+    int64_t step = 0;             // steps taken (host copy; defines the epoch position)
+    int sticky = 0;               // flood_status of a sticky error
+    std::string err;
+    std::vector<void *> allocations;
+
+    // captured epochs (use_graph): [parity of cur at the epoch start]
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+
+    flood_adjoint_state *adj = nullptr;
+    int64_t adj_forward_steps = 0;
+};
+
+namespace flood {
+
+void *dev_alloc(flood_handle *h, size_t bytes);
+void dev_free(flood_handle *h, void *p);
+flood_status fail(flood_handle *h, flood_status st, const std::string &msg);
+flood_status cuda_fail(flood_handle *h, cudaError_t e, const char *where);
+
+void section_range(const flood_bc_section &s, int nx, int ny, int *i0, int *i1);
+size_t plane_elems(const flood_handle *h, int field);
+void field_shape(const flood_handle *h, int field, int *rows, int *cols);
+flood_status copy_in(flood_handle *h, void *dst_pitched, const void *src, int rows, int cols, int src_on_device);
+flood_status copy_out(flood_handle *h, void *dst, const void *src_pitched, int rows, int cols, int dst_on_device);
+flood_status refresh_hmax(flood_handle *h);
+flood_status launch_inflow_epoch(flood_handle *h);
+flood_status launch_steps(flood_handle *h, int s, int k, int want_hmax, const int64_t *gcells, int ng,
+                          double *gout);
+flood_status advance(flood_handle *h, int64_t n, const int64_t *gcells, int ng, double *gbuf,
+                     const double *fixed_dt_log);
+flood_status check_device_status(flood_handle *h);
+flood_status ensure_gauge_buffers(flood_handle *h, int ng, size_t n_values);
+
+// CUDA-graph epochs (flood_graph.cpp)
+flood_status advance_graph(flood_handle *h, int64_t n);
+void invalidate_graphs(flood_handle *h);
+void destroy_graphs(flood_handle *h);
+
+// adjoint (flood_adjoint.cpp)
+void destroy_adjoint(flood_handle *h);
+
+}  // namespace flood

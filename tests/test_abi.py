@@ -1,0 +1,139 @@
+"""C-ABI library checks that need no GPU: it builds for sm_103a, loads, exports
+every entry point that include/flood.h declares, and rejects bad arguments in
+host code before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "flood.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(
+        r"^\s*(?:flood_status|void|int64_t|const\s+char\s*\*)\s*\**\s*(flood_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_lists_the_boundary():
+    names = header_functions()
+    for n in ("flood_create", "flood_step", "flood_read", "flood_adjoint", "flood_destroy", "flood_last_error",
+              "flood_write_state"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2204_10323_gb300 as F
+    L = F.lib()
+    missing = [n for n in header_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    assert "sm_103a" in F.flood_version()
+
+
+def test_objects_are_built_for_sm_103a_only():
+    import paper_2204_10323_gb300 as F
+    F.lib()
+    import subprocess
+    objs = [os.path.join(F._build.BUILD, f) for f in os.listdir(F._build.BUILD) if f.endswith(".cu.o")]
+    assert objs
+    out = subprocess.run(["cuobjdump", "--list-elf", objs[0]], capture_output=True, text=True).stdout
+    assert "sm_103a" in out
+
+
+def _grid(nx, ny, dx=1.0, prec=0):
+    import paper_2204_10323_gb300 as F
+    return F.flood_grid(nx, ny, dx, prec)
+
+
+def _create(grid, dem, secs=None, opts=None):
+    import paper_2204_10323_gb300 as F
+    h = C.c_void_p()
+    ns = 0 if secs is None else len(secs)
+    arr = None
+    if secs:
+        arr = (F.flood_bc_section * ns)(*secs)
+    st = F.lib().flood_create(C.byref(grid), C.c_void_p(dem.ctypes.data), None, arr, ns,
+                              None if opts is None else C.byref(opts), C.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("nx,ny,dx", [(0, 4, 1.0), (4, 0, 1.0), (4, 4, 0.0), (4, 4, -1.0), (4, 4, float("nan"))])
+def test_create_rejects_bad_grid(nx, ny, dx):
+    import paper_2204_10323_gb300 as F
+    st, h = _create(_grid(nx, ny, dx), np.zeros(16, np.float32))
+    assert st == F.ERR_ARG and not h.value
+    assert F.flood_last_error(None)
+
+
+def test_create_rejects_overlapping_sections():
+    import paper_2204_10323_gb300 as F
+    t = np.array([0.0, 1.0])
+    q = np.array([1.0, 1.0])
+    tp, qp = t.ctypes.data_as(C.POINTER(C.c_double)), q.ctypes.data_as(C.POINTER(C.c_double))
+    a = F.flood_bc_section(F.XMIN, F.INFLOW, 0.0, 0.5, 1e-3, tp, qp, 2)
+    b = F.flood_bc_section(F.XMIN, F.OUTFLOW, 0.25, 1.0, 1e-3, None, None, 0)
+    st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), [a, b])
+    assert st == F.ERR_ARG and "overlap" in F.flood_last_error(None)
+
+
+@pytest.mark.parametrize("field,value", [("slope", 0.0), ("side", 7), ("kind", 3), ("frac_end", 1.5)])
+def test_create_rejects_bad_section(field, value):
+    import paper_2204_10323_gb300 as F
+    s = F.flood_bc_section(F.XMAX, F.OUTFLOW, 0.0, 1.0, 1e-3, None, None, 0)
+    setattr(s, field, value)
+    st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), [s])
+    assert st == F.ERR_ARG
+
+
+def test_create_rejects_descending_hydrograph_and_nan_dem():
+    import paper_2204_10323_gb300 as F
+    t = np.array([0.0, 2.0, 1.0])
+    q = np.array([1.0, 1.0, 1.0])
+    s = F.flood_bc_section(F.XMIN, F.INFLOW, 0.0, 1.0, 1e-3, t.ctypes.data_as(C.POINTER(C.c_double)),
+                           q.ctypes.data_as(C.POINTER(C.c_double)), 3)
+    st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), [s])
+    assert st == F.ERR_ARG
+    dem = np.zeros(64, np.float32)
+    dem[5] = np.nan
+    st, _ = _create(_grid(8, 8), dem)
+    assert st == F.ERR_ARG and "NaN" in F.flood_last_error(None)
+
+
+def test_create_rejects_bad_options():
+    import paper_2204_10323_gb300 as F
+    o = F.default_opts()
+    o.epoch_steps = 0
+    st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
+    assert st == F.ERR_ARG
+    o = F.default_opts()
+    o.kernel = F.KERNEL_TILED
+    o.epoch_steps = 16
+    o.steps_per_launch = 3        # must divide E
+    st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
+    assert st == F.ERR_ARG
+
+
+def test_default_opts_values():
+    import paper_2204_10323_gb300 as F
+    o = F.default_opts()
+    assert (o.g, o.h_dry, o.cfl_alpha, o.epoch_steps, o.dt_const) == (9.81, 1e-3, 0.7, 16, 0.1)
+
+
+def test_null_handle_calls_fail_cleanly():
+    import paper_2204_10323_gb300 as F
+    L = F.lib()
+    assert L.flood_step(None, 1) == F.ERR_ARG
+    assert L.flood_sync(None) == F.ERR_ARG
+    assert L.flood_destroy(None) == F.OK
+
+
+def test_create_without_gpu_reports_cuda_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2204_10323_gb300 as F
+    st, h = _create(_grid(8, 8), np.zeros(64, np.float32))
+    assert st == F.ERR_CUDA and not h.value

@@ -1,0 +1,233 @@
+"""GPU forward step vs the FP64 oracle, through the C ABI.
+
+Tolerances (written here, derived from the arithmetic): the FP64 GPU path
+evaluates every operation IEEE-rounded in the oracle's order, so it differs
+only by CUDA's cbrt/pow versus the C library's (about 1 ulp) and by the order
+of the Eq. 6 and ledger sums; 1e-10 m after 1000 steps.  The FP32 path
+carries a relative rounding of about 6e-8 per operation on water levels of
+10-100 m (a few micrometres per step) and may flip wet/dry decisions at
+fronts; 1e-3 m max-abs depth and 1e-5 relative volume after 1000 steps.
+Both sides get the same inputs: for FP32 the oracle runs on the float32
+rounding of the DEM, roughness and initial state.
+"""
+import numpy as np
+import pytest
+
+import inputs
+from inputs import INFLOW, OUTFLOW, XMAX, XMIN, YMAX, YMIN, Options, Problem, Section
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32_H = 1e-3
+TOL32_MASS = 1e-5
+
+
+def F():
+    import paper_2204_10323_gb300 as F
+    return F
+
+
+def as_f32_problem(p):
+    """Same problem with every grid input rounded to float32 (then held as float64)."""
+    r = lambda a: None if a is None else a.astype(np.float32).astype(np.float64)
+    return Problem(p.name, p.nx, p.ny, p.dx, r(p.z), r(p.n), p.sections, p.opts, h0=r(p.h0), qx0=r(p.qx0),
+                   qy0=r(p.qy0), steps=p.steps, gauges=p.gauges)
+
+
+def run_pair(p, steps, precision, kernel=0, **kw):
+    Fm = F()
+    q = as_f32_problem(p) if precision == Fm.F32 else p
+    o = oracle.Oracle(q)
+    V0 = o.volume()
+    o.run(steps)
+    s = Fm.Sim(q, precision=precision, kernel=kernel, **kw)
+    s.step(steps)
+    s.sync()
+    h, qx, qy = s.state()
+    L = s.ledger()
+    s.close()
+    return o, V0, h.astype(np.float64), qx.astype(np.float64), qy.astype(np.float64), L
+
+
+def check_ledger(o, L, rel):
+    Lo = o.ledger_dict()
+    scale = max(Lo["V_in"], o.volume(), 1e-300)
+    for k in ("V_in", "V_out", "V_clip"):
+        assert abs(L[k] - Lo[k]) <= rel * scale, (k, L[k], Lo[k])
+    assert abs(L["volume"] - o.volume()) <= rel * scale
+    assert L["t"] == pytest.approx(Lo["t"], rel=1e-12)
+    assert L["step"] == Lo["step"]
+
+
+# ---------------------------------------------------------------- FP64 parity
+def test_c1_fp64_matches_oracle_1000_steps():
+    p = inputs.c1_tilted_channel()
+    o, V0, h, qx, qy, L = run_pair(p, 1000, F().F64)
+    assert np.abs(h - o.h).max() < TOL64
+    assert np.abs(qx - o.qx).max() < TOL64
+    assert np.abs(qy - o.qy).max() < TOL64
+    check_ledger(o, L, 1e-12)
+
+
+@pytest.mark.parametrize("shape,seed", [((33, 17), 0), ((7, 5), 1), ((130, 70), 2), ((1, 9), 3), ((9, 1), 4)])
+def test_random_fp64_matches_oracle(shape, seed):
+    p = inputs.random_small(shape[0], shape[1], seed)
+    o, V0, h, qx, qy, L = run_pair(p, 120, F().F64)
+    assert np.abs(h - o.h).max() < TOL64
+    assert np.abs(qx - o.qx).max() < TOL64
+    assert np.abs(qy - o.qy).max() < TOL64
+    check_ledger(o, L, 1e-12)
+
+
+@pytest.mark.parametrize("bc_form,dt_mode", [(1, 0), (0, 1), (1, 1)])
+def test_options_fp64_match_oracle(bc_form, dt_mode):
+    p = inputs.random_small(40, 23, 5, bc_form=bc_form, dt_mode=dt_mode)
+    o, V0, h, qx, qy, L = run_pair(p, 80, F().F64)
+    assert np.abs(h - o.h).max() < TOL64
+    check_ledger(o, L, 1e-12)
+
+
+# ---------------------------------------------------------------- FP32 parity
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_c1_fp32_matches_oracle_1000_steps(kernel):
+    p = inputs.c1_tilted_channel()
+    o, V0, h, qx, qy, L = run_pair(p, 1000, F().F32, kernel=kernel)
+    assert np.abs(h - o.h).max() < TOL32_H
+    Vo = o.volume()
+    assert abs(L["volume"] - Vo) / Vo < TOL32_MASS
+    # the FP32 run's own ledger closes too
+    bal = L["volume"] - V0 - (L["V_in"] - L["V_out"] + L["V_clip"])
+    assert abs(bal) / L["V_in"] < TOL32_MASS
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("shape,seed", [((33, 17), 0), ((7, 5), 1), ((130, 70), 2), ((257, 129), 6),
+                                        ((1, 1), 7), ((1, 40), 3), ((40, 1), 4), ((128, 32), 8), ((129, 33), 9)])
+def test_random_fp32_matches_oracle(kernel, shape, seed):
+    p = inputs.random_small(shape[0], shape[1], seed)
+    o, V0, h, qx, qy, L = run_pair(p, 100, F().F32, kernel=kernel)
+    assert np.abs(h - o.h).max() < TOL32_H
+    assert np.abs(qx - o.qx).max() < 10 * TOL32_H
+    assert np.abs(qy - o.qy).max() < 10 * TOL32_H
+
+
+def test_c2_fp32_parity_1000_steps():
+    """The 2048^2 fractal workload at reduced size (256^2 crop of the same generator)."""
+    p = inputs.c2_fractal(nx=256, ny=256, steps=1000)
+    o, V0, h, qx, qy, L = run_pair(p, 1000, F().F32)
+    assert np.abs(h - o.h).max() < TOL32_H
+    Vo = o.volume()
+    assert abs(L["volume"] - Vo) / max(Vo, 1.0) < TOL32_MASS
+
+
+# ---------------------------------------------------------------- invariants on the GPU
+@pytest.mark.parametrize("precision,kernel", [(0, 1), (0, 2), (1, 1)])
+def test_lake_at_rest_is_exact_on_gpu(precision, kernel):
+    p = inputs.lake_at_rest(67, 45)
+    s = F().Sim(p, precision=precision, kernel=kernel)
+    h0 = s.read(F().FIELD_H).copy()
+    s.step(300)
+    h, qx, qy = s.state()
+    assert np.array_equal(h, h0)
+    assert not qx.any() and not qy.any()
+
+
+def test_fp32_run_is_deterministic_and_resumable():
+    Fm = F()
+    p = as_f32_problem(inputs.random_small(150, 90, 11))
+    a = Fm.Sim(p)
+    a.step(100)
+    ha, qxa, qya = a.state()
+    b = Fm.Sim(p)
+    b.step(37)                         # mid-epoch stop (E = 4)
+    hb, qxb, qyb = b.state()
+    Lb = b.ledger()
+    c = Fm.Sim(p)
+    c.write_state(hb, qxb, qyb)
+    c.set_clock(Lb["t"], int(Lb["step"]), Lb["dt"], Lb["V_in"], Lb["V_out"], Lb["V_clip"])
+    c.step(63)
+    hc, qxc, qyc = c.state()
+    a2 = Fm.Sim(p)
+    a2.step(100)
+    assert np.array_equal(ha, a2.read(Fm.FIELD_H))
+    assert np.array_equal(ha, hc) and np.array_equal(qxa, qxc) and np.array_equal(qya, qyc)
+
+
+def test_inflow_distribution_matches_oracle_eq6():
+    """First-step boundary faces equal the oracle's Eq. 6 split (FP64)."""
+    Fm = F()
+    p = inputs.random_small(30, 24, 4)
+    o = oracle.Oracle(p)
+    s = Fm.Sim(p, precision=Fm.F64)
+    s.step(1)
+    qx = s.read(Fm.FIELD_QX)
+    a, b = o.section_range(0)
+    W, q = o.inflow_faces(0, o.hydrograph(0, 0.0))
+    np.testing.assert_allclose(qx[a:b, 0], q, rtol=1e-12, atol=1e-15)
+
+
+def test_graph_replay_equals_direct_launches():
+    Fm = F()
+    p = as_f32_problem(inputs.random_small(200, 120, 12))
+    a = Fm.Sim(p)
+    a.step(64)
+    b = Fm.Sim(p, use_graph=True)
+    b.step(10)
+    b.step(54)
+    assert np.array_equal(a.read(Fm.FIELD_H), b.read(Fm.FIELD_H))
+    assert np.array_equal(a.read(Fm.FIELD_QX), b.read(Fm.FIELD_QX))
+
+
+def test_gauge_series_matches_state_reads():
+    Fm = F()
+    p = as_f32_problem(inputs.random_small(60, 40, 13))
+    g = np.array([[3, 4], [59, 39], [0, 0], [30, 20]])
+    a = Fm.Sim(p)
+    series = a.run_gauges(9, g)
+    b = Fm.Sim(p)
+    for k in range(9):
+        b.step(1)
+        h = b.read(Fm.FIELD_H)
+        np.testing.assert_array_equal(series[k], h[g[:, 1], g[:, 0]].astype(np.float64))
+
+
+def test_nonfinite_depth_is_reported_and_sticky():
+    Fm = F()
+    p = inputs.random_small(20, 12, 2)
+    s = Fm.Sim(p)
+    h = s.read(Fm.FIELD_H)
+    h[3, 4] = np.inf
+    # write_state rejects non-finite host input
+    with pytest.raises(Fm.FloodError):
+        s.write_state(h)
+    import torch
+    hd = torch.from_numpy(h).cuda()          # device input is not scanned on the host
+    s.write_state(hd)
+    s.step(8)
+    with pytest.raises(Fm.FloodError) as e:
+        s.sync()
+    assert e.value.status == Fm.ERR_NONFINITE
+    with pytest.raises(Fm.FloodError) as e:
+        s.step(1)
+    assert e.value.status == Fm.ERR_STATE
+    s.write_state(np.zeros_like(h))          # clears the error
+    s.step(4)
+    s.sync()
+
+
+def test_empty_section_and_zero_inflow():
+    Fm = F()
+    nx, ny = 20, 10
+    z = np.zeros((ny, nx))
+    secs = [Section(XMIN, 0.3, 0.3, INFLOW, 1e-3, np.array([0.0, 1.0]), np.array([5.0, 5.0])),
+            Section.cells(YMAX, 2, 9, INFLOW, 1e-3, nx, ny, [0.0, 1.0], [0.0, 0.0]),
+            Section.cells(XMAX, 0, ny, OUTFLOW, 1e-3, nx, ny)]
+    p = Problem("empty", nx, ny, 1.0, z, np.full((ny, nx), 0.03), secs, Options(dt_mode=1), h0=np.full((ny, nx), 0.1))
+    o = oracle.Oracle(p)
+    o.run(20)
+    s = Fm.Sim(p, precision=Fm.F64)
+    s.step(20)
+    assert np.abs(s.read(Fm.FIELD_H) - o.h).max() < TOL64
+    assert s.ledger()["V_in"] == 0.0
