@@ -346,15 +346,20 @@ def normal_depth_channel(nx: int = 96, ny: int = 8, dx: float = 10.0, S0: float 
 
 def random_small(nx: int, ny: int, seed: int, wet: float = 0.5, inflow: float = 5.0,
                  bc_form: int = 0, dt_mode: int = 0) -> Problem:
-    """Small seeded case with rough terrain, partial wetting and every boundary kind."""
+    """Small seeded case with rough terrain, partial wetting and every boundary kind.
+
+    Kept in the well-conditioned regime of the scheme (no depth clipping, a
+    1e-15 perturbation stays below 1e-14 after 120 steps) so that it compares
+    arithmetic, not the amplification of rounding by an unstable run.
+    """
     rng = np.random.default_rng(SEED_BASE + 100 + seed)
     dx = 2.0
     xm = (np.arange(nx) + 0.5) * dx
-    z = 5.0 - 0.01 * xm[None, :] + rng.uniform(-0.3, 0.3, (ny, nx))
+    z = 5.0 - 0.01 * xm[None, :] + rng.uniform(-0.05, 0.05, (ny, nx))
     h0 = np.maximum(wet_start(z, dx, wet, 1e-3) * rng.uniform(0.5, 1.0, (ny, nx)), 0.0)
     n = rng.uniform(0.02, 0.06, (ny, nx))
-    qx0 = rng.uniform(-0.05, 0.05, (ny, nx + 1))
-    qy0 = rng.uniform(-0.05, 0.05, (ny + 1, nx))
+    qx0 = rng.uniform(-0.01, 0.01, (ny, nx + 1))
+    qy0 = rng.uniform(-0.01, 0.01, (ny + 1, nx))
     qx0[:, 0] = qx0[:, -1] = 0.0
     qy0[0, :] = qy0[-1, :] = 0.0
     a, b = ny // 4, max(ny // 4 + 1, 3 * ny // 4)
@@ -364,5 +369,5 @@ def random_small(nx: int, ny: int, seed: int, wet: float = 0.5, inflow: float = 
             Section.cells(XMAX, 0, ny, OUTFLOW, 2e-3, nx, ny),
             Section.cells(YMIN, 0, max(1, nx // 2), OUTFLOW, 1e-3, nx, ny)]
     return Problem(f"random_{nx}x{ny}_{seed}", nx, ny, dx, z, n, secs,
-                   Options(dt_cap=0.5, epoch_steps=4, bc_form=bc_form, dt_mode=dt_mode, dt_const=0.1),
+                   Options(dt_cap=0.2, epoch_steps=4, bc_form=bc_form, dt_mode=dt_mode, dt_const=0.1),
                    h0=h0, qx0=qx0, qy0=qy0)

@@ -80,7 +80,8 @@ __global__ void inflow_kernel(Geom G, const InflowSec *secs, int nsec, const int
     const double t = t_list[s];
     const double Q = hydrograph(tab_t + S.tab0, tab_q + S.tab0, S.ntab, t);
     T *out = inflow_q + (size_t)s * n_slots + S.slot0;
-    if (lane == 0) inflow_Q[(size_t)s * nsec + k] = Q;
+    // a section that covers no cell carries no discharge
+    if (lane == 0) inflow_Q[(size_t)s * nsec + k] = S.ncell > 0 ? Q : 0.0;
     double zmin = DBL_MAX;
     for (int c = lane; c < S.ncell; c += 32) zmin = fmin(zmin, (double)z[cells[S.cell0 + c]]);
     for (int o = 16; o > 0; o >>= 1) zmin = fmin(zmin, __shfl_xor_sync(0xffffffffu, zmin, o));

@@ -217,6 +217,21 @@ def test_nonfinite_depth_is_reported_and_sticky():
     s.sync()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_depth_clip_matches_oracle(precision):
+    """Thin water drained through two outflow edges goes negative and is clipped."""
+    Fm = F()
+    z = np.zeros((6, 8))
+    secs = [Section.cells(XMAX, 0, 6, OUTFLOW, 0.5, 8, 6), Section.cells(YMIN, 0, 8, OUTFLOW, 0.5, 8, 6)]
+    p = Problem("clip", 8, 6, 0.1, z, np.full((6, 8), 0.01), secs, Options(dt_mode=1, dt_const=0.05),
+                h0=np.full((6, 8), 0.002))
+    o, V0, h, qx, qy, L = run_pair(p, 20, precision, kernel=2 if precision == 0 else 1)
+    assert o.ledger.V_clip > 0
+    tol = TOL64 if precision == 1 else 1e-6
+    assert np.abs(h - o.h).max() < tol
+    assert L["V_clip"] == pytest.approx(o.ledger.V_clip, rel=1e-12 if precision == 1 else 1e-4)
+
+
 def test_empty_section_and_zero_inflow():
     Fm = F()
     nx, ny = 20, 10
