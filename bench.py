@@ -173,7 +173,8 @@ def run_gpu(args):
 
     prob, wname = workload(args.workload)
     ncell = prob.nx * prob.ny
-    kernel = {"rows": F.KERNEL_ROWS, "tiled": F.KERNEL_TILED, "reference": F.KERNEL_REFERENCE}[args.kernel]
+    kernel = {"rows": F.KERNEL_ROWS, "tiled": F.KERNEL_TILED, "reference": F.KERNEL_REFERENCE,
+              "stream": F.KERNEL_STREAM}[args.kernel]
     sim = F.Sim(prob, precision=F.F32, kernel=kernel, steps_per_launch=args.k, use_graph=args.graph)
     E = prob.opts.epoch_steps
     h0, qx0, qy0 = prob.initial_state(np.float32)
@@ -273,7 +274,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c3")
-    ap.add_argument("--kernel", default="rows", choices=["rows", "tiled", "reference"])
+    ap.add_argument("--kernel", default="stream", choices=["stream", "rows", "tiled", "reference"])
     ap.add_argument("--k", type=int, default=0, help="steps per launch (tiled kernel)")
     ap.add_argument("--graph", action="store_true")
     ap.add_argument("--traffic-bytes", type=float, default=None)

@@ -53,17 +53,41 @@ __device__ __forceinline__ double manning_cell(double hh, double sqrtS, double n
     return dx * dx * pow(hh, 2.0 / 3.0) * sqrtS / n;
 }
 
+// FP32 handles evaluate Eq. 5 in single precision inside the solve (the
+// final rescale makes the section total exact either way); FP64 handles keep
+// the double-precision evaluation of the plain definition.
+__device__ __forceinline__ double manning_cell_t(double hh, double sqrtS, float n, double dx, int form)
+{
+    float h = (float)hh, p = form == 0 ? 5.0f / 3.0f : 2.0f / 3.0f;
+    float a = form == 0 ? (float)dx : (float)(dx * dx);
+    return (double)(a * powf(h, p) * (float)sqrtS / n);
+}
+
+__device__ __forceinline__ double manning_cell_t(double hh, double sqrtS, double n, double dx, int form)
+{
+    return manning_cell(hh, sqrtS, n, dx, form);
+}
+
+constexpr int kInflowThreads = 128;
+
+// Block-wide sum of the section's Eq. 5 discharges at level W (all threads get it).
 template <typename T>
 __device__ double section_total(const InflowSec &S, const int64_t *cells, const T *z, const T *n,
-                                double W, double dx, int form)
+                                double W, double dx, int form, double *red)
 {
     double s = 0.0;
-    for (int c = threadIdx.x; c < S.ncell; c += 32) {
+    for (int c = threadIdx.x; c < S.ncell; c += kInflowThreads) {
         int64_t idx = cells[S.cell0 + c];
         double hh = W - (double)z[idx];
-        if (hh > 0.0) s += manning_cell(hh, S.sqrtS, (double)n[idx], dx, form);
+        if (hh > 0.0) s += manning_cell_t(hh, S.sqrtS, n[idx], dx, form);
     }
-    return warp_sum(s);
+    s = warp_sum(s);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < kInflowThreads / 32; w++) t += red[w];
+    return t;
 }
 
 // Eq. 6 for (step s of the epoch, inflow section k), one warp: bisection for
@@ -75,36 +99,40 @@ __global__ void inflow_kernel(Geom G, const InflowSec *secs, int nsec, const int
                               const double *tab_t, const double *tab_q, const T *z, const T *n,
                               const double *t_list, T *inflow_q, int n_slots, double *inflow_Q)
 {
-    const int s = blockIdx.x, k = blockIdx.y, lane = threadIdx.x;
+    __shared__ double red[kInflowThreads / 32];
+    const int s = blockIdx.x, k = blockIdx.y, tid = threadIdx.x;
     const InflowSec S = secs[k];
     const double t = t_list[s];
     const double Q = hydrograph(tab_t + S.tab0, tab_q + S.tab0, S.ntab, t);
     T *out = inflow_q + (size_t)s * n_slots + S.slot0;
     // a section that covers no cell carries no discharge
-    if (lane == 0) inflow_Q[(size_t)s * nsec + k] = S.ncell > 0 ? Q : 0.0;
+    if (tid == 0) inflow_Q[(size_t)s * nsec + k] = S.ncell > 0 ? Q : 0.0;
     double zmin = DBL_MAX;
-    for (int c = lane; c < S.ncell; c += 32) zmin = fmin(zmin, (double)z[cells[S.cell0 + c]]);
+    for (int c = tid; c < S.ncell; c += kInflowThreads) zmin = fmin(zmin, (double)z[cells[S.cell0 + c]]);
     for (int o = 16; o > 0; o >>= 1) zmin = fmin(zmin, __shfl_xor_sync(0xffffffffu, zmin, o));
+    if ((tid & 31) == 0) red[tid >> 5] = zmin;
+    __syncthreads();
+    for (int w = 0; w < kInflowThreads / 32; w++) zmin = fmin(zmin, red[w]);
     if (!(Q > 0.0) || S.ncell == 0) {
-        for (int c = lane; c < S.ncell; c += 32) out[c] = T(0);
+        for (int c = tid; c < S.ncell; c += kInflowThreads) out[c] = T(0);
         return;
     }
     const double dx = G.dx;
     const int form = G.bc_form;
     double Hb = 1.0;
-    while (section_total(S, cells, z, n, zmin + Hb, dx, form) < Q && Hb < 1e12) Hb *= 2.0;
+    while (section_total(S, cells, z, n, zmin + Hb, dx, form, red) < Q && Hb < 1e12) Hb *= 2.0;
     double lo = zmin, hi = zmin + Hb;
     for (int it = 0; it < 200 && hi - lo >= 1e-12; it++) {
         double mid = 0.5 * (lo + hi);
-        if (section_total(S, cells, z, n, mid, dx, form) < Q) lo = mid;
+        if (section_total(S, cells, z, n, mid, dx, form, red) < Q) lo = mid;
         else hi = mid;
     }
     const double W = hi;
-    const double total = section_total(S, cells, z, n, W, dx, form);
-    for (int c = lane; c < S.ncell; c += 32) {
+    const double total = section_total(S, cells, z, n, W, dx, form, red);
+    for (int c = tid; c < S.ncell; c += kInflowThreads) {
         int64_t idx = cells[S.cell0 + c];
         double hh = W - (double)z[idx];
-        double w = hh > 0.0 ? manning_cell(hh, S.sqrtS, (double)n[idx], dx, form) : 0.0;
+        double w = hh > 0.0 ? manning_cell_t(hh, S.sqrtS, n[idx], dx, form) : 0.0;
         out[c] = T((w * (Q / total)) / dx);
     }
 }
@@ -171,7 +199,7 @@ cudaError_t launch_inflow(const Geom &g, const InflowSec *secs, int nsec, const 
 {
     if (nsec == 0) return cudaSuccess;
     dim3 grid(E, nsec);
-    inflow_kernel<T><<<grid, 32, 0, st>>>(g, secs, nsec, sec_cells, tab_t, tab_q, z, n, t_list, inflow_q,
+    inflow_kernel<T><<<grid, kInflowThreads, 0, st>>>(g, secs, nsec, sec_cells, tab_t, tab_q, z, n, t_list, inflow_q,
                                           n_slots, inflow_Q);
     return cudaGetLastError();
 }

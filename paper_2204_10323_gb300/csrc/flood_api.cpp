@@ -229,6 +229,7 @@ flood_status launch_steps(flood_handle *h, int s, int k, int want_hmax, const in
         switch (h->kernel) {
         case FLOOD_KERNEL_REFERENCE: e = launch_step_reference<float>(a, h->stream); break;
         case FLOOD_KERNEL_TILED: e = launch_step_tiled(a, h->stream); break;
+        case FLOOD_KERNEL_STREAM: e = launch_step_stream(a, h->stream); break;
         default: e = launch_step_rows(a, h->stream); break;
         }
     }
@@ -292,7 +293,7 @@ static flood_status validate(const flood_grid *grid, const flood_bc_section *sec
         return fail(nullptr, FLOOD_ERR_ARG, "g, h_dry, cfl_alpha, dt_cap, dt_const must be > 0");
     if (o.dt_mode != 0 && o.dt_mode != 1) return fail(nullptr, FLOOD_ERR_ARG, "dt_mode must be 0 or 1");
     if (o.bc_form != 0 && o.bc_form != 1) return fail(nullptr, FLOOD_ERR_ARG, "bc_form must be 0 or 1");
-    if (o.kernel < 0 || o.kernel > 3) return fail(nullptr, FLOOD_ERR_ARG, "unknown kernel");
+    if (o.kernel < 0 || o.kernel > 4) return fail(nullptr, FLOOD_ERR_ARG, "unknown kernel");
     if (o.kernel == FLOOD_KERNEL_TILED) {
         int K = o.steps_per_launch > 0 ? o.steps_per_launch : 4;
         if (K > 16 || o.epoch_steps % K != 0)
@@ -389,7 +390,7 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
     const int E = o.epoch_steps;
 
     // kernel family and temporal-blocking depth
-    h->kernel = o.kernel == FLOOD_KERNEL_AUTO ? FLOOD_KERNEL_ROWS : o.kernel;
+    h->kernel = o.kernel == FLOOD_KERNEL_AUTO ? FLOOD_KERNEL_STREAM : o.kernel;
     if (h->prec == FLOOD_F64) h->kernel = FLOOD_KERNEL_REFERENCE;
     h->k_per_launch = 1;
     h->tile_x = o.tile_x > 0 ? o.tile_x : 128;

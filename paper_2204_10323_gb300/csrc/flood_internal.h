@@ -82,6 +82,7 @@ struct StepArgs {
 template <typename T>
 cudaError_t launch_step_reference(const StepArgs<T> &a, cudaStream_t st);
 cudaError_t launch_step_rows(const StepArgs<float> &a, cudaStream_t st);
+cudaError_t launch_step_stream(const StepArgs<float> &a, cudaStream_t st);
 cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st);
 size_t tiled_smem_bytes(int tile_x, int tile_y, int k);
 

@@ -14,7 +14,7 @@
 // All face arithmetic uses explicitly rounded intrinsics, so the faces that
 // two warps both evaluate (strip and chunk edges) come out bit-identical and
 // the update conserves mass.
-#include "device_common.cuh"
+#include "fast_face.cuh"
 
 namespace flood {
 
@@ -22,54 +22,6 @@ namespace {
 
 constexpr int kWarps = 4;       // warps (strips) per block
 constexpr int kRows = 32;       // rows per chunk
-
-struct FastConst {
-    float a1;       // g dt / dx   (slope term factor)
-    float gdt;      // g dt        (friction factor)
-    float h_dry;
-    float dtdx;     // dt / dx
-};
-
-// Eq. 3 at one face: eta_L, eta_R water levels, zmax = max(z_L, z_R),
-// nsum = n_L + n_R.  h_f^(-7/3) is evaluated as (h_f^(-1/3))^7.
-__device__ __forceinline__ float face_fast(float q, float etaL, float etaR, float zmax, float nsum,
-                                           const FastConst &k)
-{
-    float hf = __fsub_rn(fmaxf(etaL, etaR), zmax);
-    if (!(hf > k.h_dry)) return 0.0f;
-    float r = rcbrtf(hf);
-    float r2 = __fmul_rn(r, r);
-    float r4 = __fmul_rn(r2, r2);
-    float r7 = __fmul_rn(__fmul_rn(r4, r2), r);
-    float nf = __fmul_rn(0.5f, nsum);
-    float fric = __fmul_rn(__fmul_rn(__fmul_rn(k.gdt, __fmul_rn(nf, nf)), fabsf(q)), r7);
-    float num = __fsub_rn(q, __fmul_rn(__fmul_rn(k.a1, hf), __fsub_rn(etaR, etaL)));
-    return __fdividef(num, __fadd_rn(1.0f, fric));
-}
-
-// Eq. 5 boundary flux magnitude (m^2/s) of a cell of depth h.
-__device__ __forceinline__ float outflow_fast(float h, float sqrtS, float n, float dx, float h_dry, int form)
-{
-    if (!(h > h_dry)) return 0.0f;
-    float c = cbrtf(h);
-    float p = form == 0 ? __fmul_rn(h, __fmul_rn(c, c)) : __fmul_rn(dx, __fmul_rn(c, c));
-    return __fdividef(__fmul_rn(p, sqrtS), n);
-}
-
-// Boundary face value on `side` at index k along it, for the adjacent cell (h, n).
-__device__ __forceinline__ float boundary_fast(const StepArgs<float> &a, int side, int k, float h, float n,
-                                               double &vout)
-{
-    const Geom &G = a.geo;
-    int off = side == 0 ? 0 : side == 1 ? G.ny : side == 2 ? 2 * G.ny : 2 * G.ny + G.nx;
-    int type = a.bc.type[off + k];
-    if (type == kBcWall) return 0.0f;
-    float inward = (side == 0 || side == 2) ? 1.0f : -1.0f;
-    if (type == kBcInflow) return inward * a.inflow_q[(size_t)a.s * a.n_slots + a.bc.slot[off + k]];
-    float q = outflow_fast(h, (float)a.bc.sqrtS[off + k], n, (float)G.dx, (float)G.h_dry, G.bc_form);
-    vout += (double)q * G.dx;
-    return -inward * q;
-}
 
 struct Row {
     float4 h, z, n, qx, qy;

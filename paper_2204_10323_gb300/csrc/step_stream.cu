@@ -1,0 +1,307 @@
+// step_stream.cu -- FP32 single-step kernel fed by the bulk-copy engine.
+//
+// Same work split and arithmetic as the row-streaming kernel (one warp per
+// 128-column strip and a chunk of rows, south to north, previous row in
+// registers), but the rows arrive through a per-warp ring of kDepth shared
+// memory stages filled by 1D bulk copies (cp.async.bulk, one per field and
+// row, completion counted on an mbarrier per stage).  Lane 0 keeps kDepth
+// rows in flight while the warp computes, so memory latency is hidden by
+// copies in flight instead of by registers or extra warps.  Each staged row
+// segment covers columns x0-4 .. x0+131, so the west and east neighbour
+// columns of the strip come from shared memory as well.
+//
+// Waits are bounded: a stage that does not complete within ~2 s sets the
+// timeout status bit, the warp waits (bounded) for its copies in flight and
+// leaves without storing.
+#include "fast_face.cuh"
+#include "tma_util.cuh"
+
+namespace flood {
+
+namespace {
+
+constexpr int kWarps = 4;        // warps (strips) per block
+constexpr int kRows = 64;        // rows per chunk
+constexpr int kDepth = 4;        // rows in flight per warp
+constexpr int kSeg = 136;        // floats per staged row segment (x0-4 .. x0+131)
+constexpr int kFields = 5;       // h, z, n, qx, qy
+constexpr uint64_t kBudgetNs = 2000000000ull;
+
+struct WarpRing {
+    float buf[kDepth][kFields][kSeg];
+    uint64_t bar[kDepth];
+};
+
+constexpr size_t kSmemBytes = sizeof(WarpRing) * kWarps;
+
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
+__device__ __forceinline__ float get(const float4 &v, int k)
+{
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+
+__device__ __forceinline__ void set(float4 &v, int k, float x)
+{
+    if (k == 0) v.x = x;
+    else if (k == 1) v.y = x;
+    else if (k == 2) v.z = x;
+    else v.w = x;
+}
+
+__global__ void __launch_bounds__(kWarps * 32, 5) step_stream_kernel(const StepArgs<float> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    const Geom &G = a.geo;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nx = G.nx, ny = G.ny;
+    const int P = G.pitch;
+    const int x0 = (blockIdx.x * kWarps + warp) * 128;
+    const int c0 = x0 + 4 * lane;
+    const bool active = x0 < nx;
+    const int y0 = blockIdx.y * kRows;
+    const int y1 = min(y0 + kRows, ny);
+    const int jstart = y0 > 0 ? y0 - 1 : 0;
+    const int jlast = min(y1, ny - 1);             // last row that is staged
+    const int nload = jlast - jstart + 1;
+    WarpRing &ring = reinterpret_cast<WarpRing *>(smem_raw)[warp];
+
+    const double dtd = a.ctrl->dt;
+    FastConst K;
+    const float dt = (float)dtd, dx = (float)G.dx, g = (float)G.g;
+    K.gdt = g * dt;
+    K.a1 = K.gdt / dx;
+    K.h_dry = (float)G.h_dry;
+    K.dtdx = dt / dx;
+
+    double vout = 0.0, vclip = 0.0;
+    float hmax = 0.0f;
+    bool nan_seen = false;
+
+    // staged segment: global columns [cs, ce) land at ring offset so
+    const int cs = max(x0 - 4, 0);
+    const int ce = min(x0 + 132, P);
+    const int so = cs - (x0 - 4);
+    const uint32_t seg_bytes = (uint32_t)(ce - cs) * 4u;
+    const float *fields[kFields] = {a.h, a.z, a.n, a.qx, a.qy};
+
+    if (active && lane == 0) {
+        for (int s = 0; s < kDepth; s++) mbar_init(&ring.bar[s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    auto issue = [&](int idx) {
+        const int s = idx % kDepth;
+        const size_t row = (size_t)(jstart + idx) * P + cs;
+        mbar_arrive_expect_tx(&ring.bar[s], seg_bytes * kFields);
+#pragma unroll
+        for (int f = 0; f < kFields; f++) bulk_copy_g2s(&ring.buf[s][f][so], fields[f] + row, seg_bytes, &ring.bar[s]);
+    };
+    int issued = 0, consumed = 0;
+    bool abort = false;
+    if (active && lane == 0) {
+        for (; issued < min(kDepth, nload); issued++) issue(issued);
+    }
+
+    float4 hp = make_float4(0, 0, 0, 0), zp = hp, np_ = hp;
+    float4 qxw_p = hp, qys_p = hp;
+    float qxe_p3 = 0.0f;
+    if (active) {
+        for (int j = jstart; j <= y1; j++) {
+            const int idx = j - jstart;
+            float4 ch = make_float4(0, 0, 0, 0), cz = ch, cn = ch, cqx = ch, cqy = ch;
+            float hW = 0.f, zW = 0.f, nW = 0.f, hE = 0.f, zE = 0.f, nE = 0.f, qxE = 0.f;
+            if (j < ny) {
+                const int s = idx % kDepth;
+                bool ok = mbar_wait_bounded(&ring.bar[s], (uint32_t)((idx / kDepth) & 1), kBudgetNs);
+                if (__any_sync(0xffffffffu, !ok)) {
+                    abort = true;
+                    break;
+                }
+                consumed = idx + 1;
+                const int o = 4 + 4 * lane;
+                ch = lds4(&ring.buf[s][0][o]);
+                cz = lds4(&ring.buf[s][1][o]);
+                cn = lds4(&ring.buf[s][2][o]);
+                cqx = lds4(&ring.buf[s][3][o]);
+                cqy = lds4(&ring.buf[s][4][o]);
+                if (lane == 0) {
+                    hW = ring.buf[s][0][3];
+                    zW = ring.buf[s][1][3];
+                    nW = ring.buf[s][2][3];
+                }
+                if (lane == 31) {
+                    hE = ring.buf[s][0][132];
+                    zE = ring.buf[s][1][132];
+                    nE = ring.buf[s][2][132];
+                    qxE = ring.buf[s][3][132];
+                }
+                __syncwarp();
+                if (lane == 0 && issued < nload) {
+                    fence_proxy_async();
+                    issue(issued);
+                    issued++;
+                }
+            }
+            if (j < y0) {                 // halo row south of the chunk
+                hp = ch;
+                zp = cz;
+                np_ = cn;
+                continue;
+            }
+            // ---- new south faces of row j
+            float4 qys;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                int c = c0 + k;
+                float v = 0.0f;
+                if (c < nx) {
+                    if (j == 0) v = boundary_fast(a, 2, c, get(ch, k), get(cn, k), vout);
+                    else if (j == ny) v = boundary_fast(a, 3, c, get(hp, k), get(np_, k), vout);
+                    else {
+                        float zl = get(zp, k), zr = get(cz, k);
+                        v = face_fast(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr, fmaxf(zl, zr),
+                                      get(np_, k) + get(cn, k), K);
+                    }
+                }
+                set(qys, k, v);
+            }
+            // ---- finish row j-1
+            if (j > y0) {
+                const int jr = j - 1;
+                const size_t r = (size_t)jr * P + c0;
+                float4 hn;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    float qe = k < 3 ? get(qxw_p, k + 1) : qxe_p3;
+                    float dv = __fadd_rn(__fsub_rn(get(qxw_p, k), qe), __fsub_rn(get(qys_p, k), get(qys, k)));
+                    float v = __fmaf_rn(K.dtdx, dv, get(hp, k));
+                    if (c0 + k < nx) {
+                        if (v < 0.0f) {
+                            vclip += -(double)v * G.dx * G.dx;
+                            v = 0.0f;
+                        }
+                        hmax = fmaxf(hmax, v);
+                        nan_seen |= (v != v);
+                    }
+                    set(hn, k, v);
+                }
+                if (c0 + 3 < nx) {
+                    *reinterpret_cast<float4 *>(a.h_out + r) = hn;
+                    *reinterpret_cast<float4 *>(a.qy_out + r) = qys_p;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        if (c0 + k < nx) {
+                            a.h_out[r + k] = get(hn, k);
+                            a.qy_out[r + k] = get(qys_p, k);
+                        }
+                }
+                if (c0 + 3 <= nx) *reinterpret_cast<float4 *>(a.qx_out + r) = qxw_p;
+                else {
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        if (c0 + k <= nx) a.qx_out[r + k] = get(qxw_p, k);
+                }
+                if (lane == 31 && x0 + 128 == nx) a.qx_out[(size_t)jr * P + nx] = qxe_p3;
+                if (jr == ny - 1) {
+                    const size_t rn = (size_t)ny * P + c0;
+                    if (c0 + 3 < nx) *reinterpret_cast<float4 *>(a.qy_out + rn) = qys;
+                    else {
+#pragma unroll
+                        for (int k = 0; k < 4; k++)
+                            if (c0 + k < nx) a.qy_out[rn + k] = get(qys, k);
+                    }
+                }
+            }
+            if (j == y1) break;
+            // ---- new west faces of row j
+            float hl0 = __shfl_up_sync(0xffffffffu, ch.w, 1);
+            float zl0 = __shfl_up_sync(0xffffffffu, cz.w, 1);
+            float nl0 = __shfl_up_sync(0xffffffffu, cn.w, 1);
+            if (lane == 0) {
+                hl0 = hW;
+                zl0 = zW;
+                nl0 = nW;
+            }
+            float4 qxw;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                int c = c0 + k;
+                float hl = k == 0 ? hl0 : get(ch, k - 1);
+                float zl = k == 0 ? zl0 : get(cz, k - 1);
+                float nl = k == 0 ? nl0 : get(cn, k - 1);
+                float v = 0.0f;
+                if (c == 0) v = boundary_fast(a, 0, j, get(ch, 0), get(cn, 0), vout);
+                else if (c == nx) v = boundary_fast(a, 1, j, hl, nl, vout);
+                else if (c < nx) {
+                    float zr = get(cz, k);
+                    v = face_fast(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), K);
+                }
+                set(qxw, k, v);
+            }
+            float qe = __shfl_down_sync(0xffffffffu, qxw.x, 1);
+            if (lane == 31) {
+                const int c = x0 + 128;
+                qe = 0.0f;
+                if (c == nx) qe = boundary_fast(a, 1, j, ch.w, cn.w, vout);
+                else if (c < nx) qe = face_fast(qxE, ch.w + cz.w, hE + zE, fmaxf(cz.w, zE), cn.w + nE, K);
+            }
+            hp = ch;
+            zp = cz;
+            np_ = cn;
+            qxw_p = qxw;
+            qxe_p3 = qe;
+            qys_p = qys;
+        }
+        if (abort) {
+            // leave no bulk copy writing into shared memory after exit
+            if (lane == 0) {
+                for (int k = consumed; k < issued; k++)
+                    mbar_wait_bounded(&ring.bar[k % kDepth], (uint32_t)((k / kDepth) & 1), kBudgetNs);
+                atomicOr(&a.ctrl->status, kStatusTimeout);
+            }
+            __syncwarp();
+        }
+    }
+    double bo = block_reduce<false>(vout, red);
+    if (threadIdx.x == 0 && bo != 0.0) atomicAdd(&a.ctrl->V_out, dtd * bo);
+    double bc = block_reduce<false>(vclip, red);
+    if (threadIdx.x == 0 && bc != 0.0) atomicAdd(&a.ctrl->V_clip, bc);
+    if (a.want_hmax) {
+        double bm = block_reduce<true>(nan_seen ? (double)NAN : (double)hmax, red);
+        if (threadIdx.x == 0) atomic_max_nonneg(&a.ctrl->hmax_bits, bm);
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        double vin = a.ctrl->V_in;
+        for (int k = 0; k < a.n_inflow_sec; k++) {
+            double Q = a.inflow_Q[(size_t)a.s * a.n_inflow_sec + k];
+            if (Q > 0.0) vin += dtd * Q;
+        }
+        a.ctrl->V_in = vin;
+        a.ctrl->t = a.t_list[a.s + 1];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_step_stream(const StepArgs<float> &a, cudaStream_t st)
+{
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(step_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int strips = (a.geo.nx + 127) / 128;
+    dim3 grid((strips + kWarps - 1) / kWarps, (a.geo.ny + kRows - 1) / kRows);
+    step_stream_kernel<<<grid, kWarps * 32, kSmemBytes, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.gauge_out) return launch_gauges<float>(a.geo, a.h_out, a.gauge_cells, a.n_gauges, a.gauge_out, st);
+    return cudaSuccess;
+}
+
+}  // namespace flood

@@ -90,7 +90,7 @@ def test_options_fp64_match_oracle(bc_form, dt_mode):
 
 
 # ---------------------------------------------------------------- FP32 parity
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 4])
 def test_c1_fp32_matches_oracle_1000_steps(kernel):
     p = inputs.c1_tilted_channel()
     o, V0, h, qx, qy, L = run_pair(p, 1000, F().F32, kernel=kernel)
@@ -102,7 +102,7 @@ def test_c1_fp32_matches_oracle_1000_steps(kernel):
     assert abs(bal) / L["V_in"] < TOL32_MASS
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 4])
 @pytest.mark.parametrize("shape,seed", [((33, 17), 0), ((7, 5), 1), ((130, 70), 2), ((257, 129), 6),
                                         ((1, 1), 7), ((1, 40), 3), ((40, 1), 4), ((128, 32), 8), ((129, 33), 9)])
 def test_random_fp32_matches_oracle(kernel, shape, seed):
@@ -123,7 +123,7 @@ def test_c2_fp32_parity_1000_steps():
 
 
 # ---------------------------------------------------------------- invariants on the GPU
-@pytest.mark.parametrize("precision,kernel", [(0, 1), (0, 2), (1, 1)])
+@pytest.mark.parametrize("precision,kernel", [(0, 1), (0, 2), (0, 4), (1, 1)])
 def test_lake_at_rest_is_exact_on_gpu(precision, kernel):
     p = inputs.lake_at_rest(67, 45)
     s = F().Sim(p, precision=precision, kernel=kernel)
