@@ -109,7 +109,7 @@ typedef struct {
     int32_t epoch_steps;         /* E: steps per CFL epoch (1..1024) */
     int32_t bc_form;             /* 0 cell discharge dx h^(5/3) sqrt(S)/n, 1 literal dx^2 h^(2/3) sqrt(S)/n */
     int32_t kernel;              /* flood_kernel */
-    int32_t steps_per_launch;    /* K for FLOOD_KERNEL_TILED (must divide E; 0 = auto) */
+    int32_t steps_per_launch;    /* K for FLOOD_KERNEL_TILED: 1..4, must divide E (0 = 4) */
     int32_t tile_x, tile_y;      /* tile shape for FLOOD_KERNEL_TILED (0 = auto) */
     int32_t use_graph;           /* 1: replay whole epochs from a captured CUDA graph */
     void *stream;                /* cudaStream_t, NULL = current PyTorch stream */

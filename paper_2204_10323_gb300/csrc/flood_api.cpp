@@ -228,7 +228,10 @@ flood_status launch_steps(flood_handle *h, int s, int k, int want_hmax, const in
         StepArgs<float> a = make_args<float>(h, s, k, want_hmax, gcells, ng, gout);
         switch (h->kernel) {
         case FLOOD_KERNEL_REFERENCE: e = launch_step_reference<float>(a, h->stream); break;
-        case FLOOD_KERNEL_TILED: e = launch_step_tiled(a, h->stream); break;
+        case FLOOD_KERNEL_TILED:
+            // gauge recording needs the depth after every step: single steps there
+            e = gout ? launch_step_stream(a, h->stream) : launch_step_tiled(a, h->stream);
+            break;
         case FLOOD_KERNEL_STREAM: e = launch_step_stream(a, h->stream); break;
         default: e = launch_step_rows(a, h->stream); break;
         }
@@ -253,7 +256,7 @@ flood_status advance(flood_handle *h, int64_t n, const int64_t *gcells, int ng, 
             if (st) return st;
         }
         int k = 1;
-        if (h->prec == FLOOD_F32 && h->kernel == FLOOD_KERNEL_TILED) {
+        if (h->prec == FLOOD_F32 && h->kernel == FLOOD_KERNEL_TILED && !gcells) {
             k = std::min<int64_t>(h->k_per_launch, std::min<int64_t>(E - s, n - done));
         }
         int want = (s + k == E) ? 1 : 0;
@@ -296,8 +299,8 @@ static flood_status validate(const flood_grid *grid, const flood_bc_section *sec
     if (o.kernel < 0 || o.kernel > 4) return fail(nullptr, FLOOD_ERR_ARG, "unknown kernel");
     if (o.kernel == FLOOD_KERNEL_TILED) {
         int K = o.steps_per_launch > 0 ? o.steps_per_launch : 4;
-        if (K > 16 || o.epoch_steps % K != 0)
-            return fail(nullptr, FLOOD_ERR_ARG, "steps_per_launch must divide epoch_steps and be <= 16");
+        if (K > 4 || o.epoch_steps % K != 0)
+            return fail(nullptr, FLOOD_ERR_ARG, "steps_per_launch must divide epoch_steps and be <= 4");
     }
     std::vector<int> used(2 * (size_t)grid->nx + 2 * (size_t)grid->ny, 0);
     for (int k = 0; k < nsec; k++) {

@@ -246,3 +246,51 @@ def test_empty_section_and_zero_inflow():
     s.step(20)
     assert np.abs(s.read(Fm.FIELD_H) - o.h).max() < TOL64
     assert s.ledger()["V_in"] == 0.0
+
+
+# ---------------------------------------------------------------- temporal blocking
+@pytest.mark.parametrize("K", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape,seed", [((130, 70), 2), ((257, 129), 6), ((241, 50), 14), ((120, 33), 15),
+                                        ((7, 5), 1), ((1, 40), 3), ((40, 1), 4), ((361, 97), 16)])
+def test_tiled_equals_single_steps_bitwise(K, shape, seed):
+    """K time levels per launch give the same bits and ledger as K single steps."""
+    Fm = F()
+    p = as_f32_problem(inputs.random_small(shape[0], shape[1], seed))
+    p.opts.epoch_steps = 4 if K in (1, 2, 4) else 3
+    a = Fm.Sim(p, kernel=Fm.KERNEL_STREAM)
+    b = Fm.Sim(p, kernel=Fm.KERNEL_TILED, steps_per_launch=K)
+    for n in (5, 12, 1, 30):              # stops inside and at the ends of epochs
+        a.step(n)
+        b.step(n)
+    for f in (Fm.FIELD_H, Fm.FIELD_QX, Fm.FIELD_QY):
+        assert np.array_equal(a.read(f), b.read(f)), f
+    La, Lb = a.ledger(), b.ledger()
+    for k in ("V_in", "V_out", "V_clip", "volume", "t", "h_max"):
+        assert Lb[k] == pytest.approx(La[k], rel=1e-12, abs=1e-12), k
+
+
+def test_tiled_c1_matches_oracle_and_lake_at_rest():
+    Fm = F()
+    p = inputs.c1_tilted_channel()
+    o, V0, h, qx, qy, L = run_pair(p, 1000, Fm.F32, kernel=Fm.KERNEL_TILED, steps_per_launch=4)
+    assert np.abs(h - o.h).max() < TOL32_H
+    assert abs(L["volume"] - o.volume()) / o.volume() < TOL32_MASS
+    lake = inputs.lake_at_rest(300, 170)
+    s = Fm.Sim(lake, kernel=Fm.KERNEL_TILED, steps_per_launch=4)
+    h0 = s.read(Fm.FIELD_H).copy()
+    s.step(64)
+    assert np.array_equal(s.read(Fm.FIELD_H), h0)
+    assert not s.read(Fm.FIELD_QX).any() and not s.read(Fm.FIELD_QY).any()
+
+
+def test_tiled_large_grid_many_chunks_bitwise():
+    """A grid large enough for many strips and chunks per strip (persistent split)."""
+    Fm = F()
+    p = as_f32_problem(inputs.c2_fractal(nx=1100, ny=2300, steps=100))
+    p.h0 = inputs.wet_start(p.z, p.dx, 0.3)
+    a = Fm.Sim(p, kernel=Fm.KERNEL_STREAM)
+    b = Fm.Sim(p, kernel=Fm.KERNEL_TILED, steps_per_launch=4)
+    a.step(40)
+    b.step(40)
+    for f in (Fm.FIELD_H, Fm.FIELD_QX, Fm.FIELD_QY):
+        assert np.array_equal(a.read(f), b.read(f)), f
