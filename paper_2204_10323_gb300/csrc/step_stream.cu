@@ -27,11 +27,14 @@ constexpr int kSeg = 136;        // floats per staged row segment (x0-4 .. x0+13
 constexpr int kFields = 5;       // h, z, n, qx, qy
 constexpr uint64_t kBudgetNs = 2000000000ull;
 
-struct WarpRing {
+// 16-byte aligned size: every warp's ring (bulk-copy destinations, float4
+// loads) must start on a 16-byte boundary.
+struct alignas(16) WarpRing {
     float buf[kDepth][kFields][kSeg];
     uint64_t bar[kDepth];
 };
 
+static_assert(sizeof(WarpRing) % 16 == 0, "per-warp ring must keep 16-byte alignment");
 constexpr size_t kSmemBytes = sizeof(WarpRing) * kWarps;
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }

@@ -32,12 +32,15 @@ constexpr int kPF = 3;                      // rows in flight
 constexpr int kDZ = kPF + kHalo + 1;        // z,n ring depth: rows still read by lagging levels
 constexpr uint64_t kBudgetNs = 2000000000ull;
 
-struct WarpRing {
+// 16-byte aligned size: every warp's ring (bulk-copy destinations, float4
+// loads) must start on a 16-byte boundary.
+struct alignas(16) WarpRing {
     float hq[kPF][3][128];                  // h, qx, qy of staged rows
     float zn[kDZ][2][128];                  // z, n of the last kDZ rows
     uint64_t bar[kPF];
 };
 
+static_assert(sizeof(WarpRing) % 16 == 0, "per-warp ring must keep 16-byte alignment");
 constexpr size_t kSmemBytes = sizeof(WarpRing) * kWarps;
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
