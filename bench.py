@@ -180,28 +180,36 @@ def run_gpu(args):
     h0, qx0, qy0 = prob.initial_state(np.float32)
     stream = torch.cuda.current_stream()
 
-    # warm-up (also moves the clock past one epoch start)
-    for _ in range(args.warmup):
-        sim.step(1)
+    # steps per launch: K for the temporal-blocked kernel, else 1; time whole epochs
+    per_launch = (args.k or 4) if args.kernel == "tiled" else 1
+    n_launch_total = max(E // per_launch, (args.steps + per_launch - 1) // per_launch)
+    n_launch_total = (n_launch_total + (E // per_launch) - 1) // (E // per_launch) * (E // per_launch)
+    steps = n_launch_total * per_launch
+
+    # warm-up: whole epochs so the timed region starts at an epoch start
+    warm = max(args.warmup, E)
+    warm = (warm + E - 1) // E * E
+    for _ in range(warm // per_launch):
+        sim.step(per_launch)
     sim.sync()
 
-    # timed region: K steps, one event pair per step on the library's stream
+    # timed region: one event per launch on the library's stream
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch_total + 1)]
     step0 = int(sim.ledger()["step"])
     torch.cuda.synchronize()
     ev[0].record(stream)
-    for k in range(args.steps):
-        sim.step(1)
+    for k in range(n_launch_total):
+        sim.step(per_launch)
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(n_launch_total)]
     total_ms = ev[0].elapsed_time(ev[-1])
     if dist:
         t = torch.tensor([total_ms], device="cuda")
@@ -209,15 +217,17 @@ def run_gpu(args):
         total_ms = float(t.item())
     sim.sync()
     L = sim.ledger()
-    # steps that did not start an epoch launch the step kernel alone
-    kern = [per[k] for k in range(args.steps) if (step0 + k) % E != 0]
+    # launches that did not start an epoch run the step kernel alone
+    starts = [(step0 + k * per_launch) % E == 0 for k in range(n_launch_total)]
+    kern = [per[k] for k in range(n_launch_total) if not starts[k]]
     kern_ms = statistics.mean(kern) if kern else statistics.mean(per)
-    n_epochs = sum(1 for k in range(args.steps) if (step0 + k) % E == 0)
-    launches = args.steps * (1 if args.kernel != "tiled" else 1) + n_epochs * (1 + (1 if sim_inflows(prob) else 0))
+    n_epochs = sum(starts)
+    launches = n_launch_total + n_epochs * (1 + (1 if sim_inflows(prob) else 0))
+    args.steps = steps
 
-    value = world * ncell * args.steps / (total_ms * 1e-3) / 1e9
+    value = world * ncell * steps / (total_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    achieved = BYTES_PER_CELL * ncell / (kern_ms * 1e-3) / 1e9
+    achieved = BYTES_PER_CELL * ncell * per_launch / (kern_ms * 1e-3) / 1e9
     traffic = None
     if args.traffic_bytes:
         traffic = float(args.traffic_bytes)
@@ -250,7 +260,7 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "bytes_per_cell": BYTES_PER_CELL, "kernel_ms": kern_ms},
+                         "bytes_per_cell": BYTES_PER_CELL, "kernel_ms": kern_ms, "steps_per_launch": per_launch},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "ledger": {k: L[k] for k in ("t", "dt", "V_in", "V_out", "V_clip", "volume")}}
     if rank == 0 and not args.no_cpu_baseline:
