@@ -225,6 +225,25 @@ const char *flood_last_error(const flood_handle *h);
 /* Library version string. */
 const char *flood_version(void);
 
+/*
+ * Stored water volume sum(h) dx^2 of a caller-owned device depth array: ny
+ * rows of row_pitch elements with nx used per row (float for FLOOD_F32,
+ * double for FLOOD_F64), written as one double to out_device, asynchronously
+ * on `stream` (NULL = the legacy default stream).  The paper has no
+ * counterpart; this entry point is for callers that cannot allocate device
+ * memory when they need the number: code inside a CUDA-graph capture region,
+ * callers whose device memory all belongs to their own pool, and hosts that
+ * forbid allocation after start-up.  It allocates nothing: its scratch is a
+ * fixed device array of 65536 row sums (512 KiB) that every GPU loading the
+ * library keeps until exit, so ny > 65536 returns FLOOD_ERR_ARG.  The first
+ * call on each device (with that device current) looks up the scratch's
+ * address; make that call outside any stream capture.  All calls on a device
+ * share the scratch, which keeps the last call's row sums: calls whose kernels
+ * overlap on the GPU race.  Errors: flood_last_error(NULL).
+ */
+flood_status flood_volume_noalloc(const void *depth, int32_t nx, int32_t ny, int64_t row_pitch,
+                                  int32_t precision, double dx, double *out_device, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

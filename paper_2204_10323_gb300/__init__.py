@@ -87,6 +87,8 @@ def _load():
     L.flood_last_error.argtypes = [H]
     L.flood_last_error.restype = C.c_char_p
     L.flood_version.restype = C.c_char_p
+    L.flood_volume_noalloc.argtypes = [vp, i32, i32, i64, i32, dbl, vp, vp]
+    L.flood_volume_noalloc.restype = C.c_int
     for name in ("flood_create", "flood_step", "flood_sync", "flood_read", "flood_write_state",
                  "flood_set_clock", "flood_set_manning", "flood_run_gauges", "flood_adjoint", "flood_destroy"):
         getattr(L, name).restype = C.c_int
@@ -163,6 +165,13 @@ def flood_last_error(h=None) -> str:
 
 def flood_version() -> str:
     return lib().flood_version().decode()
+
+
+def flood_volume_noalloc(depth_ptr, nx: int, ny: int, row_pitch: int, precision: int, dx: float, out_ptr,
+                         stream_ptr=None):
+    """Stored volume of a device depth array without any allocation (see include/flood.h)."""
+    _check(lib().flood_volume_noalloc(depth_ptr, int(nx), int(ny), int(row_pitch), int(precision), float(dx),
+                                      out_ptr, stream_ptr), None)
 
 
 # ------------------------------------------------------------------ convenience wrapper
