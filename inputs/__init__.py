@@ -313,8 +313,10 @@ def c5_calibration(nx: int = 1024, ny: int = 1024, truth: bool = False, steps: i
             Section.cells(XMAX, 0, ny, OUTFLOW, bed_slope(bed, dx, False), nx, ny)]
     gi = np.round(np.linspace(2, min(nx - 3, 2 + steps // 8), n_gauges)).astype(int)
     gj = np.clip(np.floor(yc[gi]).astype(int), 0, ny - 1)
+    # a fixed step: the gradient holds the time-step schedule fixed, so finite
+    # differences of the loss are comparable only without the CFL rule
     return Problem(f"c5_calibration_{nx}x{ny}", nx, ny, dx, z, n, secs,
-                   Options(dt_cap=0.5, epoch_steps=16), steps=steps,
+                   Options(dt_cap=0.5, dt_mode=1, dt_const=0.25, epoch_steps=16), steps=steps,
                    gauges=np.stack([gi, gj], 1))
 
 

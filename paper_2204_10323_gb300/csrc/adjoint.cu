@@ -1,0 +1,403 @@
+// adjoint.cu -- reverse of one time step (not in the paper; its calibration
+// use is named as future work).  Given the forward state x_k and the adjoint
+// lambda_{k+1} of the state after the step, produce lambda_k and accumulate
+// dL/dn.  The forward step is h' = max(h + dt/dx div q'(x_k, n), 0) with q'
+// from Eq. 3 on interior faces and Eq. 5-6 on boundary faces, so
+//
+//   lambda_hu(c) = lambda_h'(c) * [h'_unclipped(c) >= 0]
+//   mu_f         = lambda_q'(f) + dt/dx (lambda_hu(R) - lambda_hu(L))     (face f between L and R)
+//   lambda_h(c)  = lambda_hu(c) + sum_f mu_f dq'_f/dh_c
+//   lambda_q(f)  = mu_f dq'_f/dq_f                                          (interior faces)
+//   dL/dn(c)    += sum_f mu_f dq'_f/dn_c
+//
+// Branch conventions: max(eta_L, eta_R) sends its derivative to L on ties;
+// d|q|/dq = 0 at q = 0; the dry-face test, the outflow dry test and the clip
+// are held as masks; the Eq. 6 level is differentiated exactly through the
+// implicit function theorem.  Each cell gathers the contributions of its
+// four faces (both cells of a face evaluate its derivatives), so no atomics
+// are needed and the result is deterministic.
+//
+// Pass 1 recomputes the forward faces with the same arithmetic as the
+// forward kernels (IEEE order for FP64, the fast FP32 face for FP32), so the
+// clip mask and the wet/dry decisions are the forward's own.
+#include "fast_face.cuh"
+
+namespace flood {
+
+namespace {
+
+constexpr int BX = 32, BY = 8;
+
+// ---------------------------------------------------------------- forward faces per precision
+template <typename T> struct Fwd;
+
+template <> struct Fwd<double> {
+    double g, dt, dx, hd, dtdx_unused;
+    __device__ Fwd(const Geom &G, double dt_) : g(G.g), dt(dt_), dx(G.dx), hd(G.h_dry), dtdx_unused(0) {}
+    __device__ double face(double q, double hL, double zL, double nL, double hR, double zR, double nR) const
+    {
+        return face_update_ieee<double>(q, hL, zL, nL, hR, zR, nR, g, dt, dx, hd);
+    }
+    __device__ double hf(double hL, double zL, double hR, double zR) const
+    {
+        using O = R<double>;
+        return O::sub(O::max(O::add(hL, zL), O::add(hR, zR)), O::max(zL, zR));
+    }
+    __device__ double outflow(double h, double sqrtS, double n, int form) const
+    {
+        return outflow_flux_ieee<double>(h, sqrtS, n, dx, hd, form);
+    }
+    __device__ double update(double h, double qW, double qE, double qS, double qN) const
+    {
+        using O = R<double>;
+        double dv = O::add(O::sub(qW, qE), O::sub(qS, qN));
+        return O::add(h, O::div(O::mul(dt, dv), dx));
+    }
+    __device__ static double rcbrt_(double x) { return ::rcbrt(x); }
+};
+
+template <> struct Fwd<float> {
+    FastConst K;
+    float dx, hd;
+    __device__ Fwd(const Geom &G, double dt_)
+    {
+        const float dt = (float)dt_;
+        dx = (float)G.dx;
+        K.gdt = (float)G.g * dt;
+        K.a1 = K.gdt / dx;
+        K.h_dry = (float)G.h_dry;
+        K.dtdx = dt / dx;
+        hd = K.h_dry;
+    }
+    __device__ float face(float q, float hL, float zL, float nL, float hR, float zR, float nR) const
+    {
+        return face_fast(q, hL + zL, hR + zR, fmaxf(zL, zR), nL + nR, K);
+    }
+    __device__ float hf(float hL, float zL, float hR, float zR) const
+    {
+        return __fsub_rn(fmaxf(hL + zL, hR + zR), fmaxf(zL, zR));
+    }
+    __device__ float outflow(float h, float sqrtS, float n, int form) const
+    {
+        return outflow_fast(h, sqrtS, n, dx, hd, form);
+    }
+    __device__ float update(float h, float qW, float qE, float qS, float qN) const
+    {
+        float dv = __fadd_rn(__fsub_rn(qW, qE), __fsub_rn(qS, qN));
+        return __fmaf_rn(K.dtdx, dv, h);
+    }
+    __device__ static float rcbrt_(float x) { return rcbrtf(x); }
+};
+
+// Partial derivatives of one wet face's Eq. 3 value.
+template <typename T> struct FaceLin {
+    T dq, dhL, dhR, dn;     // dn = dq'/dn_L = dq'/dn_R
+};
+
+template <typename T>
+__device__ __forceinline__ FaceLin<T> face_lin(T q, T hL, T zL, T nL, T hR, T zR, T nR, T hf, T g, T dt, T dx)
+{
+    FaceLin<T> r;
+    const T etaL = hL + zL, etaR = hR + zR;
+    const T nf = T(0.5) * (nL + nR);
+    const T gdt = g * dt, a1 = gdt / dx;
+    const T m13 = Fwd<T>::rcbrt_(hf);
+    const T hf_m73 = m13 / (hf * hf);
+    const T c0 = gdt * nf * nf * hf_m73;     // friction per |q|
+    const T fric = c0 * (q < T(0) ? -q : q);
+    const T den = T(1) + fric;
+    const T slope = etaR - etaL;
+    const T F = (q - a1 * hf * slope) / den;
+    const T sg = q > T(0) ? T(1) : (q < T(0) ? T(-1) : T(0));
+    r.dq = (T(1) - F * c0 * sg) / den;
+    const T dF_dhf = (-a1 * slope + F * (T(7) / T(3)) * fric / hf) / den;
+    const T d_expl = a1 * hf / den;
+    const bool left = etaL >= etaR;
+    r.dhL = d_expl + (left ? dF_dhf : T(0));
+    r.dhR = -d_expl + (left ? T(0) : dF_dhf);
+    r.dn = -F * fric / (nf * den);
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ int bc_off(const Geom &G, int side)
+{
+    return side == 0 ? 0 : side == 1 ? G.ny : side == 2 ? 2 * G.ny : 2 * G.ny + G.nx;
+}
+
+// Forward boundary face value (same rules as the forward kernels).
+template <typename T>
+__device__ __forceinline__ T bface(const StepArgs<T> &a, const Fwd<T> &F, int side, int k, T h, T n)
+{
+    const Geom &G = a.geo;
+    const int off = bc_off<T>(G, side);
+    const int type = a.bc.type[off + k];
+    if (type == kBcWall) return T(0);
+    const T inward = T(inward_sign(side));
+    if (type == kBcInflow) return inward * a.inflow_q[(size_t)a.s * a.n_slots + a.bc.slot[off + k]];
+    return -inward * F.outflow(h, T(a.bc.sqrtS[off + k]), n, G.bc_form);
+}
+
+// Pass 1: recompute the step for each cell; lhu = lambda_h' where the depth was not clipped.
+template <typename T>
+__global__ void __launch_bounds__(BX *BY) adj_mask_kernel(const AdjArgs<T> A)
+{
+    const StepArgs<T> &a = A.fwd;
+    const Geom &G = a.geo;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    const Fwd<T> F(G, a.ctrl->dt);
+    const size_t P = (size_t)G.pitch, c = (size_t)j * P + i;
+    const T hC = a.h[c], zC = a.z[c], nC = a.n[c];
+    T qW, qE, qS, qN;
+    if (i == 0) qW = bface(a, F, 0, j, hC, nC);
+    else qW = F.face(a.qx[c], a.h[c - 1], a.z[c - 1], a.n[c - 1], hC, zC, nC);
+    if (i == G.nx - 1) qE = bface(a, F, 1, j, hC, nC);
+    else qE = F.face(a.qx[c + 1], hC, zC, nC, a.h[c + 1], a.z[c + 1], a.n[c + 1]);
+    if (j == 0) qS = bface(a, F, 2, i, hC, nC);
+    else qS = F.face(a.qy[c], a.h[c - P], a.z[c - P], a.n[c - P], hC, zC, nC);
+    if (j == G.ny - 1) qN = bface(a, F, 3, i, hC, nC);
+    else qN = F.face(a.qy[c + P], hC, zC, nC, a.h[c + P], a.z[c + P], a.n[c + P]);
+    const T hu = F.update(hC, qW, qE, qS, qN);
+    A.lhu[c] = hu < T(0) ? T(0) : A.lh[c];
+}
+
+// Adjoint of an outflow boundary face: contributions to lambda_h(c) and dL/dn(c).
+template <typename T>
+__device__ __forceinline__ void outflow_adj(const StepArgs<T> &a, const Fwd<T> &F, int side, int k, T h, T n,
+                                            T mu, T &lh, double &gn)
+{
+    const Geom &G = a.geo;
+    const int off = bc_off<T>(G, side);
+    if (a.bc.type[off + k] != kBcOutflow) return;
+    const T q = F.outflow(h, T(a.bc.sqrtS[off + k]), n, G.bc_form);
+    if (!(q > T(0))) return;                    // dry boundary cell: held at zero
+    const T nu = -T(inward_sign(side)) * mu;   // adjoint of the outflow magnitude
+    const T pe = G.bc_form == 0 ? T(5.0 / 3.0) : T(2.0 / 3.0);
+    lh += nu * pe * q / h;
+    gn += (double)(-nu * q / n);
+}
+
+// Pass 2: gather the adjoint of each cell and of its own west and south faces.
+template <typename T>
+__global__ void __launch_bounds__(BX *BY) adj_step_kernel(const AdjArgs<T> A)
+{
+    const StepArgs<T> &a = A.fwd;
+    const Geom &G = a.geo;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    const double dtd = a.ctrl->dt;
+    const Fwd<T> F(G, dtd);
+    const T dt = T(dtd), dx = T(G.dx), g = T(G.g), hd = T(G.h_dry), dtdx = dt / dx;
+    const size_t P = (size_t)G.pitch, c = (size_t)j * P + i;
+    const T hC = a.h[c], zC = a.z[c], nC = a.n[c];
+    const T lu = A.lhu[c];
+    T lh = lu;
+    double gn = 0.0;
+    // west face (this cell is R)
+    {
+        if (i == 0) {
+            const T mu = A.lqx[c] + dtdx * lu;
+            outflow_adj(a, F, 0, j, hC, nC, mu, lh, gn);
+            A.lqx_out[c] = T(0);
+        } else {
+            const T hL = a.h[c - 1], zL = a.z[c - 1], nL = a.n[c - 1];
+            const T mu = A.lqx[c] + dtdx * (lu - A.lhu[c - 1]);
+            const T hf = F.hf(hL, zL, hC, zC);
+            T lq = T(0);
+            if (hf > hd && mu != T(0)) {
+                FaceLin<T> d = face_lin<T>(a.qx[c], hL, zL, nL, hC, zC, nC, hf, g, dt, dx);
+                lh += mu * d.dhR;
+                gn += (double)(mu * d.dn);
+                lq = mu * d.dq;
+            }
+            A.lqx_out[c] = lq;
+        }
+    }
+    // east face (this cell is L)
+    {
+        if (i == G.nx - 1) {
+            const T mu = A.lqx[c + 1] - dtdx * lu;
+            outflow_adj(a, F, 1, j, hC, nC, mu, lh, gn);
+            A.lqx_out[c + 1] = T(0);
+        } else {
+            const T hR = a.h[c + 1], zR = a.z[c + 1], nR = a.n[c + 1];
+            const T mu = A.lqx[c + 1] + dtdx * (A.lhu[c + 1] - lu);
+            const T hf = F.hf(hC, zC, hR, zR);
+            if (hf > hd && mu != T(0)) {
+                FaceLin<T> d = face_lin<T>(a.qx[c + 1], hC, zC, nC, hR, zR, nR, hf, g, dt, dx);
+                lh += mu * d.dhL;
+                gn += (double)(mu * d.dn);
+            }
+        }
+    }
+    // south face (this cell is R)
+    {
+        if (j == 0) {
+            const T mu = A.lqy[c] + dtdx * lu;
+            outflow_adj(a, F, 2, i, hC, nC, mu, lh, gn);
+            A.lqy_out[c] = T(0);
+        } else {
+            const T hL = a.h[c - P], zL = a.z[c - P], nL = a.n[c - P];
+            const T mu = A.lqy[c] + dtdx * (lu - A.lhu[c - P]);
+            const T hf = F.hf(hL, zL, hC, zC);
+            T lq = T(0);
+            if (hf > hd && mu != T(0)) {
+                FaceLin<T> d = face_lin<T>(a.qy[c], hL, zL, nL, hC, zC, nC, hf, g, dt, dx);
+                lh += mu * d.dhR;
+                gn += (double)(mu * d.dn);
+                lq = mu * d.dq;
+            }
+            A.lqy_out[c] = lq;
+        }
+    }
+    // north face (this cell is L)
+    {
+        if (j == G.ny - 1) {
+            const T mu = A.lqy[c + P] - dtdx * lu;
+            outflow_adj(a, F, 3, i, hC, nC, mu, lh, gn);
+            A.lqy_out[c + P] = T(0);
+        } else {
+            const T hR = a.h[c + P], zR = a.z[c + P], nR = a.n[c + P];
+            const T mu = A.lqy[c + P] + dtdx * (A.lhu[c + P] - lu);
+            const T hf = F.hf(hC, zC, hR, zR);
+            if (hf > hd && mu != T(0)) {
+                FaceLin<T> d = face_lin<T>(a.qy[c + P], hC, zC, nC, hR, zR, nR, hf, g, dt, dx);
+                lh += mu * d.dhL;
+                gn += (double)(mu * d.dn);
+            }
+        }
+    }
+    A.lh_out[c] = lh;
+    A.gn[c] += gn;
+}
+
+// Pass 3: the inflow faces of each section depend on every section cell's n
+// through the Eq. 6 level W: with w_c the cell discharge (sum_c w_c = Q),
+// pe its depth exponent and hh_c = W - z_c,
+//   dw_c/dn_j = -delta_cj w_c/n_c + (pe w_c/hh_c) dW/dn_j,
+//   dW/dn_j   = (w_j/n_j) / sum_c (pe w_c/hh_c),
+// so dL/dn_j += (w_j/n_j) (sum_c nu_c pe w_c/hh_c / sum_c pe w_c/hh_c - nu_j).
+template <typename T>
+__global__ void adj_inflow_kernel(const AdjArgs<T> A)
+{
+    __shared__ double red[32];
+    const StepArgs<T> &a = A.fwd;
+    const Geom &G = a.geo;
+    const int k = blockIdx.x;
+    const InflowSec S = A.secs[k];
+    const double Q = a.inflow_Q[(size_t)a.s * a.n_inflow_sec + k];
+    if (!(Q > 0.0) || S.ncell == 0) return;
+    const double W = A.inflow_W[(size_t)a.s * a.n_inflow_sec + k];
+    const double dx = G.dx, dtdx = a.ctrl->dt / G.dx;
+    const double pe = G.bc_form == 0 ? 5.0 / 3.0 : 2.0 / 3.0;
+    const double inward = (double)inward_sign(S.side);
+    const size_t P = (size_t)G.pitch;
+    double D = 0.0, Nn = 0.0;
+    for (int c = threadIdx.x; c < S.ncell; c += blockDim.x) {
+        const int64_t idx = A.sec_cells[S.cell0 + c];
+        const double hh = W - (double)a.z[idx];
+        if (!(hh > 0.0)) continue;
+        const double w = (double)a.inflow_q[(size_t)a.s * a.n_slots + S.slot0 + c] * dx;
+        size_t face;
+        double lq;
+        switch (S.side) {
+        case 0: face = idx; lq = (double)A.lqx[face]; break;
+        case 1: face = idx + 1; lq = (double)A.lqx[face]; break;
+        case 2: face = idx; lq = (double)A.lqy[face]; break;
+        default: face = idx + P; lq = (double)A.lqy[face]; break;
+        }
+        const double mu = lq + inward * dtdx * (double)A.lhu[idx];
+        const double nu = inward * mu / dx;
+        D += pe * w / hh;
+        Nn += nu * pe * w / hh;
+    }
+    D = block_reduce<false>(D, red);
+    __syncthreads();
+    if (threadIdx.x == 0) red[31] = D;
+    __syncthreads();
+    D = red[31];
+    __syncthreads();
+    Nn = block_reduce<false>(Nn, red);
+    __syncthreads();
+    if (threadIdx.x == 0) red[30] = Nn;
+    __syncthreads();
+    Nn = red[30];
+    if (!(D > 0.0)) return;
+    for (int c = threadIdx.x; c < S.ncell; c += blockDim.x) {
+        const int64_t idx = A.sec_cells[S.cell0 + c];
+        const double hh = W - (double)a.z[idx];
+        if (!(hh > 0.0)) continue;
+        const double w = (double)a.inflow_q[(size_t)a.s * a.n_slots + S.slot0 + c] * dx;
+        double lq;
+        switch (S.side) {
+        case 0: lq = (double)A.lqx[idx]; break;
+        case 1: lq = (double)A.lqx[idx + 1]; break;
+        case 2: lq = (double)A.lqy[idx]; break;
+        default: lq = (double)A.lqy[idx + P]; break;
+        }
+        const double mu = lq + inward * dtdx * (double)A.lhu[idx];
+        const double nu = inward * mu / dx;
+        A.gn[idx] += (w / (double)a.n[idx]) * (Nn / D - nu);
+    }
+}
+
+template <typename T>
+__global__ void add_seed_kernel(Geom G, T *lh, const int64_t *cells, int ng, const double *seed)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int k = 0; k < ng; k++) {       // one thread: repeated gauge cells add up in order
+        const int64_t c = cells[k];
+        const size_t idx = (size_t)(c / G.nx) * G.pitch + (size_t)(c % G.nx);
+        lh[idx] = lh[idx] + T(seed[k]);
+    }
+}
+
+template <typename T>
+__global__ void gn_out_kernel(Geom G, const double *gn, T *dst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    const size_t c = (size_t)j * G.pitch + i;
+    dst[c] = T(gn[c]);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_gn_out(const Geom &g, const double *gn, T *dst, cudaStream_t st)
+{
+    dim3 grid((g.nx + 255) / 256, g.ny);
+    gn_out_kernel<T><<<grid, 256, 0, st>>>(g, gn, dst);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_gn_out<float>(const Geom &, const double *, float *, cudaStream_t);
+template cudaError_t launch_gn_out<double>(const Geom &, const double *, double *, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_adjoint_step(const AdjArgs<T> &A, cudaStream_t st)
+{
+    dim3 block(BX, BY);
+    dim3 grid((A.fwd.geo.nx + BX - 1) / BX, (A.fwd.geo.ny + BY - 1) / BY);
+    adj_mask_kernel<T><<<grid, block, 0, st>>>(A);
+    adj_step_kernel<T><<<grid, block, 0, st>>>(A);
+    if (A.fwd.n_inflow_sec > 0) adj_inflow_kernel<T><<<A.fwd.n_inflow_sec, 256, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_add_seed(const Geom &g, T *lh, const int64_t *cells, int G, const double *seed, cudaStream_t st)
+{
+    if (G <= 0) return cudaSuccess;
+    add_seed_kernel<T><<<1, 32, 0, st>>>(g, lh, cells, G, seed);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_adjoint_step<float>(const AdjArgs<float> &, cudaStream_t);
+template cudaError_t launch_adjoint_step<double>(const AdjArgs<double> &, cudaStream_t);
+template cudaError_t launch_add_seed<float>(const Geom &, float *, const int64_t *, int, const double *, cudaStream_t);
+template cudaError_t launch_add_seed<double>(const Geom &, double *, const int64_t *, int, const double *,
+                                             cudaStream_t);
+
+}  // namespace flood

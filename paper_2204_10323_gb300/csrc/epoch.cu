@@ -97,7 +97,7 @@ __device__ double section_total(const InflowSec &S, const int64_t *cells, const 
 template <typename T>
 __global__ void inflow_kernel(Geom G, const InflowSec *secs, int nsec, const int64_t *cells,
                               const double *tab_t, const double *tab_q, const T *z, const T *n,
-                              const double *t_list, T *inflow_q, int n_slots, double *inflow_Q)
+                              const double *t_list, T *inflow_q, int n_slots, double *inflow_Q, double *W_out)
 {
     __shared__ double red[kInflowThreads / 32];
     const int s = blockIdx.x, k = blockIdx.y, tid = threadIdx.x;
@@ -128,6 +128,7 @@ __global__ void inflow_kernel(Geom G, const InflowSec *secs, int nsec, const int
         else hi = mid;
     }
     const double W = hi;
+    if (tid == 0 && W_out) W_out[(size_t)s * nsec + k] = W;
     const double total = section_total(S, cells, z, n, W, dx, form, red);
     for (int c = tid; c < S.ncell; c += kInflowThreads) {
         int64_t idx = cells[S.cell0 + c];
@@ -195,12 +196,12 @@ template <typename T>
 cudaError_t launch_inflow(const Geom &g, const InflowSec *secs, int nsec, const int64_t *sec_cells,
                           const int8_t * /*sec_side*/, const double *tab_t, const double *tab_q,
                           const T *z, const T *n, const double *t_list, int E, T *inflow_q, int n_slots,
-                          double *inflow_Q, cudaStream_t st)
+                          double *inflow_Q, double *W_out, cudaStream_t st)
 {
     if (nsec == 0) return cudaSuccess;
     dim3 grid(E, nsec);
     inflow_kernel<T><<<grid, kInflowThreads, 0, st>>>(g, secs, nsec, sec_cells, tab_t, tab_q, z, n, t_list, inflow_q,
-                                          n_slots, inflow_Q);
+                                          n_slots, inflow_Q, W_out);
     return cudaGetLastError();
 }
 
@@ -236,7 +237,8 @@ cudaError_t launch_gauges(const Geom &g, const T *h, const int64_t *cells, int G
 #define FLOOD_INST(T)                                                                                      \
     template cudaError_t launch_inflow<T>(const Geom &, const InflowSec *, int, const int64_t *,             \
                                           const int8_t *, const double *, const double *, const T *,       \
-                                          const T *, const double *, int, T *, int, double *, cudaStream_t); \
+                                          const T *, const double *, int, T *, int, double *, double *,      \
+                                          cudaStream_t);                                                    \
     template cudaError_t launch_hmax<T>(const Geom &, const T *, Ctrl *, cudaStream_t);                     \
     template cudaError_t launch_volume<T>(const Geom &, const T *, double *, int, double *, cudaStream_t);   \
     template cudaError_t launch_gauges<T>(const Geom &, const T *, const int64_t *, int, double *, cudaStream_t);

@@ -1,17 +1,425 @@
-// flood_adjoint.cpp -- reverse sweep driver (binomial checkpointing).
-// Placeholder until the adjoint kernels land.
+// flood_adjoint.cpp -- reverse sweep driver of flood_adjoint: binomial
+// checkpointing (Griewank & Walther, "Algorithm 799: revolve") over device
+// resident snapshots, frozen time-step schedule, per-step adjoint kernels.
+//
+// Cost model: reversing l steps with the start state stored and s free
+// snapshot slots takes F(l, s) forward steps, F(1, s) = 0, F(l, 0) =
+// l(l-1)/2, F(l, s) = min_j [j + F(l-j, s-1) + F(j, s)]; the minimum equals
+// the binomial closed form r l - C(c + r, c + 1) with c = s + 1 and r the
+// least integer with C(c + r, c) >= l.  The schedule below places each
+// snapshot at a split j attaining that minimum.
+#include "flood.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "flood_internal.h"
 #include "flood_runtime.h"
 
 using namespace flood;
 
-namespace flood {
-void destroy_adjoint(flood_handle *) {}
-}  // namespace flood
+struct flood_adjoint_state {
+    int dummy = 0;
+};
 
-extern "C" flood_status flood_adjoint(flood_handle *h, int64_t, const int64_t *, int32_t, const double *, int32_t,
-                                      void *, void *, int32_t)
+namespace flood {
+
+void destroy_adjoint(flood_handle *h)
 {
-    return fail(h, FLOOD_ERR_UNSUPPORTED, "adjoint not built yet");
+    delete h->adj;
+    h->adj = nullptr;
 }
 
+// C(c + r, c) with saturation.
+static int64_t beta(int64_t c, int64_t r)
+{
+    double v = 1.0;
+    for (int64_t k = 1; k <= r; k++) {
+        v = v * (double)(c + k) / (double)k;
+        if (v > 4e18) return (int64_t)4e18;
+    }
+    return (int64_t)(v + 0.5);
+}
+
+// Forward steps needed to reverse l steps with c snapshots including the start state's.
+int64_t revolve_cost(int64_t l, int64_t c)
+{
+    if (l <= 1) return 0;
+    if (c <= 1) return l * (l - 1) / 2;
+    int64_t r = 0;
+    while (beta(c, r) < l) r++;
+    return r * l - beta(c + 1, r - 1);
+}
+
+namespace {
+
+#define CKA(expr)                                                     \
+    do {                                                              \
+        cudaError_t e_ = (expr);                                      \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #expr);        \
+    } while (0)
+
+struct Planes {
+    void *h = nullptr, *qx = nullptr, *qy = nullptr;
+};
+
+struct Sweep {
+    flood_handle *h = nullptr;
+    int64_t g0 = 0, N = 0;           // first global step, steps to reverse
+    int E = 16;
+    size_t plane = 0, plane_y = 0;
+    std::vector<Planes> slots;
+    std::vector<int> free_slots;
+    int64_t work_step = -1;          // local index of the state in the handle's buffers
+    // epoch logs (device): dt and the E+1 start times of each epoch touched
+    double *dt_log = nullptr, *tl_log = nullptr;
+    std::vector<char> logged;
+    int64_t e0 = 0;
+    int64_t loaded = -1;             // epoch whose inflow buffers are loaded
+    // adjoint buffers
+    void *lh[2] = {nullptr, nullptr}, *lqx[2] = {nullptr, nullptr}, *lqy[2] = {nullptr, nullptr};
+    void *lhu = nullptr;
+    double *gn = nullptr;
+    int cur_l = 0;
+    const int64_t *cells = nullptr;
+    int G = 0;
+    const double *seed = nullptr;    // device, N x G
+    int64_t fwd_steps = 0;
+};
+
+flood_status copy_planes(flood_handle *h, const Planes &dst, const Planes &src, size_t plane, size_t plane_y)
+{
+    CKA(cudaMemcpyAsync(dst.h, src.h, plane, cudaMemcpyDeviceToDevice, h->stream));
+    CKA(cudaMemcpyAsync(dst.qx, src.qx, plane, cudaMemcpyDeviceToDevice, h->stream));
+    CKA(cudaMemcpyAsync(dst.qy, src.qy, plane_y, cudaMemcpyDeviceToDevice, h->stream));
+    return FLOOD_OK;
+}
+
+Planes working(flood_handle *h)
+{
+    Planes p;
+    p.h = h->h[h->cur];
+    p.qx = h->qx[h->cur];
+    p.qy = h->qy[h->cur];
+    return p;
+}
+
+// Make the inflow buffers and dt of epoch e current (logging it the first time).
+flood_status ensure_epoch(Sweep &S, int64_t e)
+{
+    flood_handle *h = S.h;
+    if (S.loaded == e) return FLOOD_OK;
+    const int64_t ie = e - S.e0;
+    const int E = S.E;
+    double *dtl = S.dt_log + ie;
+    double *tll = S.tl_log + ie * (E + 1);
+    if (!S.logged[ie]) {
+        // first visit: the working state is the epoch's first state; choose dt by the rule
+        flood_status st = refresh_hmax(h);
+        if (st) return st;
+        CKA(launch_epoch_begin(h->geo, h->ctrl, h->t_list, E, 0, nullptr, h->stream));
+        CKA(cudaMemcpyAsync(dtl, &h->ctrl->dt, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        CKA(cudaMemcpyAsync(tll, h->t_list, (E + 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        S.logged[ie] = 1;
+    } else {
+        CKA(cudaMemcpyAsync(h->t_list, tll, (E + 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        CKA(cudaMemcpyAsync(&h->ctrl->dt, dtl, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    flood_status st = launch_inflow_epoch(h);
+    if (st) return st;
+    S.loaded = e;
+    return FLOOD_OK;
+}
+
+flood_status forward_step(Sweep &S)
+{
+    flood_handle *h = S.h;
+    const int64_t g = S.g0 + S.work_step;
+    const int64_t e = g / S.E;
+    const int s = (int)(g % S.E);
+    if (s == 0 && !S.logged[e - S.e0]) S.loaded = -1;
+    flood_status st = ensure_epoch(S, e);
+    if (st) return st;
+    st = launch_steps(h, s, 1, s == S.E - 1 ? 1 : 0, nullptr, 0, nullptr);
+    if (st) return st;
+    S.work_step += 1;
+    S.fwd_steps += 1;
+    return FLOOD_OK;
+}
+
+flood_status restore(Sweep &S, int slot, int64_t step)
+{
+    if (S.work_step == step) return FLOOD_OK;
+    flood_status st = copy_planes(S.h, working(S.h), S.slots[slot], S.plane, S.plane_y);
+    if (st) return st;
+    S.work_step = step;
+    return FLOOD_OK;
+}
+
+flood_status advance_to(Sweep &S, int64_t step)
+{
+    while (S.work_step < step) {
+        flood_status st = forward_step(S);
+        if (st) return st;
+    }
+    return FLOOD_OK;
+}
+
+template <typename T>
+flood_status reverse_step_t(Sweep &S)
+{
+    flood_handle *h = S.h;
+    const int64_t k = S.work_step;
+    const int64_t g = S.g0 + k;
+    const int64_t e = g / S.E;
+    const int s = (int)(g % S.E);
+    if (s == 0 && !S.logged[e - S.e0]) S.loaded = -1;
+    flood_status st = ensure_epoch(S, e);
+    if (st) return st;
+    const int c = S.cur_l, o = 1 - S.cur_l;
+    CKA(launch_add_seed<T>(h->geo, (T *)S.lh[c], S.cells, S.G, S.seed + (size_t)k * S.G, h->stream));
+    AdjArgs<T> A;
+    std::memset(&A, 0, sizeof(A));
+    StepArgs<T> &a = A.fwd;
+    a.geo = h->geo;
+    a.h = (const T *)h->h[h->cur];
+    a.qx = (const T *)h->qx[h->cur];
+    a.qy = (const T *)h->qy[h->cur];
+    a.z = (const T *)h->z;
+    a.n = (const T *)h->n;
+    a.bc.type = h->bc_type;
+    a.bc.slot = h->bc_slot;
+    a.bc.sqrtS = h->bc_sqrtS;
+    a.inflow_q = (const T *)h->inflow_q;
+    a.n_slots = h->n_slots;
+    a.inflow_Q = h->inflow_Q;
+    a.n_inflow_sec = h->n_in;
+    a.t_list = h->t_list;
+    a.ctrl = h->ctrl;
+    a.s = s;
+    a.k_steps = 1;
+    A.lh = (const T *)S.lh[c];
+    A.lqx = (const T *)S.lqx[c];
+    A.lqy = (const T *)S.lqy[c];
+    A.lh_out = (T *)S.lh[o];
+    A.lqx_out = (T *)S.lqx[o];
+    A.lqy_out = (T *)S.lqy[o];
+    A.lhu = (T *)S.lhu;
+    A.gn = S.gn;
+    A.secs = h->secs_dev;
+    A.sec_cells = h->sec_cells;
+    A.inflow_W = h->inflow_W;
+    CKA(launch_adjoint_step<T>(A, h->stream));
+    S.cur_l = o;
+    return FLOOD_OK;
+}
+
+flood_status reverse_step(Sweep &S)
+{
+    return S.h->prec == FLOOD_F32 ? reverse_step_t<float>(S) : reverse_step_t<double>(S);
+}
+
+// Reverse steps [a, b) with the state of step a in slot sa and S.free_slots free.
+flood_status reverse_range(Sweep &S, int64_t a, int64_t b, int sa)
+{
+    flood_status st;
+    if (b - a == 1) {
+        if ((st = restore(S, sa, a))) return st;
+        return reverse_step(S);
+    }
+    const int64_t s = (int64_t)S.free_slots.size();
+    if (s == 0) {
+        for (int64_t k = b - 1; k >= a; k--) {
+            if (S.work_step > k || S.work_step < a)
+                if ((st = restore(S, sa, a))) return st;
+            if ((st = advance_to(S, k))) return st;
+            if ((st = reverse_step(S))) return st;
+        }
+        return FLOOD_OK;
+    }
+    const int64_t l = b - a;
+    int64_t best_j = 1, best = -1;
+    for (int64_t j = 1; j < l; j++) {
+        int64_t cst = j + revolve_cost(l - j, s) + revolve_cost(j, s + 1);
+        if (best < 0 || cst < best) {
+            best = cst;
+            best_j = j;
+        }
+    }
+    const int64_t m = a + best_j;
+    if (S.work_step > m || S.work_step < a) {
+        if ((st = restore(S, sa, a))) return st;
+    }
+    if ((st = advance_to(S, m))) return st;
+    const int sm = S.free_slots.back();
+    S.free_slots.pop_back();
+    if ((st = copy_planes(S.h, S.slots[sm], working(S.h), S.plane, S.plane_y))) return st;
+    if ((st = reverse_range(S, m, b, sm))) return st;
+    S.free_slots.push_back(sm);
+    return reverse_range(S, a, m, sa);
+}
+
+}  // namespace
+
+}  // namespace flood
+
 extern "C" int64_t flood_adjoint_forward_steps(const flood_handle *h) { return h ? h->adj_forward_steps : 0; }
+
+extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const int64_t *gauge_cells,
+                                      int32_t n_gauges, const double *dLdh, int32_t n_checkpoints,
+                                      void *dLdn_out, void *dLdh0_out, int32_t out_on_device)
+{
+    if (!h) return fail(nullptr, FLOOD_ERR_ARG, "handle is NULL");
+    if (n_steps < 1 || n_gauges < 0 || n_checkpoints < 1 || !dLdn_out || (n_gauges > 0 && (!gauge_cells || !dLdh)))
+        return fail(h, FLOOD_ERR_ARG, "bad adjoint arguments");
+    if (h->sticky) return fail(h, FLOOD_ERR_STATE, "handle is in an error state; write a new state first");
+    const int64_t nc = (int64_t)h->geo.nx * h->geo.ny;
+    for (int g = 0; g < n_gauges; g++)
+        if (gauge_cells[g] < 0 || gauge_cells[g] >= nc) return fail(h, FLOOD_ERR_ARG, "gauge cell out of range");
+    const size_t esz = h->esz;
+    const size_t P = (size_t)h->geo.pitch;
+    Sweep S;
+    S.h = h;
+    S.g0 = h->step;
+    S.N = n_steps;
+    S.E = h->geo.epoch_steps;
+    S.plane = P * h->geo.ny * esz;
+    S.plane_y = P * (h->geo.ny + 1) * esz;
+    const int C = (int)std::min<int64_t>(n_checkpoints, n_steps);
+    std::vector<void *> mine;
+    auto alloc = [&](size_t bytes) {
+        void *p = dev_alloc(h, bytes);
+        if (p) mine.push_back(p);
+        return p;
+    };
+    auto release = [&]() {
+        for (void *p : mine) dev_free(h, p);
+        mine.clear();
+    };
+    S.slots.resize(C);
+    for (int c = 0; c < C; c++) {
+        S.slots[c].h = alloc(S.plane);
+        S.slots[c].qx = alloc(S.plane);
+        S.slots[c].qy = alloc(S.plane_y);
+        if (!S.slots[c].h || !S.slots[c].qx || !S.slots[c].qy) {
+            release();
+            return fail(h, FLOOD_ERR_OOM, "checkpoint allocation");
+        }
+    }
+    for (int c = C - 1; c >= 1; c--) S.free_slots.push_back(c);
+    S.e0 = S.g0 / S.E;
+    const int64_t n_ep = (S.g0 + n_steps - 1) / S.E - S.e0 + 1;
+    S.logged.assign(n_ep, 0);
+    S.dt_log = (double *)alloc(n_ep * sizeof(double));
+    S.tl_log = (double *)alloc(n_ep * (S.E + 1) * sizeof(double));
+    for (int b = 0; b < 2; b++) {
+        S.lh[b] = alloc(S.plane);
+        S.lqx[b] = alloc(S.plane);
+        S.lqy[b] = alloc(S.plane_y);
+    }
+    S.lhu = alloc(S.plane);
+    S.gn = (double *)alloc(P * h->geo.ny * sizeof(double));
+    double *seed_dev = (double *)alloc(std::max<size_t>((size_t)n_steps * n_gauges, 1) * sizeof(double));
+    int64_t *cells_dev = (int64_t *)alloc(std::max(n_gauges, 1) * sizeof(int64_t));
+    // saved handle state: control block, epoch buffers
+    Ctrl saved_ctrl;
+    const int E = S.E;
+    void *saved_inflow_q = alloc((size_t)E * h->n_slots * esz);
+    double *saved_inflow_Q = (double *)alloc((size_t)E * std::max(h->n_in, 1) * sizeof(double));
+    double *saved_inflow_W = (double *)alloc((size_t)E * std::max(h->n_in, 1) * sizeof(double));
+    double *saved_tlist = (double *)alloc((E + 1) * sizeof(double));
+    for (void *p : {(void *)S.dt_log, (void *)S.tl_log, S.lh[0], S.lh[1], S.lqx[0], S.lqx[1], S.lqy[0], S.lqy[1],
+                    S.lhu, (void *)S.gn, (void *)seed_dev, (void *)cells_dev, saved_inflow_q,
+                    (void *)saved_inflow_Q, (void *)saved_inflow_W, (void *)saved_tlist})
+        if (!p) {
+            release();
+            return fail(h, FLOOD_ERR_OOM, "adjoint buffer allocation");
+        }
+    const int saved_kernel = h->kernel;
+    const int saved_cur = h->cur;
+    const int64_t saved_step = h->step;
+    auto finish = [&](flood_status st) {
+        h->kernel = saved_kernel;
+        release();
+        return st;
+    };
+#define CKF(expr)                                                                   \
+    do {                                                                            \
+        cudaError_t e_ = (expr);                                                    \
+        if (e_ != cudaSuccess) return finish(cuda_fail(h, e_, #expr));              \
+    } while (0)
+    CKF(cudaMemcpyAsync(&saved_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CKF(cudaMemcpyAsync(saved_inflow_q, h->inflow_q, (size_t)E * h->n_slots * esz, cudaMemcpyDeviceToDevice, h->stream));
+    CKF(cudaMemcpyAsync(saved_inflow_Q, h->inflow_Q, (size_t)E * std::max(h->n_in, 1) * sizeof(double),
+                        cudaMemcpyDeviceToDevice, h->stream));
+    CKF(cudaMemcpyAsync(saved_inflow_W, h->inflow_W, (size_t)E * std::max(h->n_in, 1) * sizeof(double),
+                        cudaMemcpyDeviceToDevice, h->stream));
+    CKF(cudaMemcpyAsync(saved_tlist, h->t_list, (E + 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    // the epoch in progress at the start is logged from the handle
+    if (S.g0 % E != 0) {
+        CKF(cudaMemcpyAsync(S.dt_log, &h->ctrl->dt, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        CKF(cudaMemcpyAsync(S.tl_log, h->t_list, (E + 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        S.logged[0] = 1;
+        S.loaded = S.e0;
+    }
+    if (n_gauges > 0) {
+        CKF(cudaMemcpyAsync(seed_dev, dLdh, (size_t)n_steps * n_gauges * sizeof(double), cudaMemcpyHostToDevice,
+                            h->stream));
+        CKF(cudaMemcpyAsync(cells_dev, gauge_cells, n_gauges * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+    }
+    for (int b = 0; b < 2; b++) {
+        CKF(cudaMemsetAsync(S.lh[b], 0, S.plane, h->stream));
+        CKF(cudaMemsetAsync(S.lqx[b], 0, S.plane, h->stream));
+        CKF(cudaMemsetAsync(S.lqy[b], 0, S.plane_y, h->stream));
+    }
+    CKF(cudaMemsetAsync(S.lhu, 0, S.plane, h->stream));
+    CKF(cudaMemsetAsync(S.gn, 0, P * h->geo.ny * sizeof(double), h->stream));
+    S.cells = cells_dev;
+    S.G = n_gauges;
+    S.seed = seed_dev;
+    // FP32 forward replays use the row-streaming arithmetic the adjoint linearises
+    if (h->prec == FLOOD_F32) h->kernel = FLOOD_KERNEL_STREAM;
+    {
+        flood_status st = copy_planes(h, S.slots[0], working(h), S.plane, S.plane_y);
+        if (st) return finish(st);
+    }
+    S.work_step = 0;
+    {
+        flood_status st = reverse_range(S, 0, n_steps, 0);
+        if (st) return finish(st);
+    }
+    h->adj_forward_steps = S.fwd_steps;
+    // outputs
+    {
+        flood_status st = FLOOD_OK;
+        if (h->prec == FLOOD_F32) st = (flood_status)(launch_gn_out<float>(h->geo, S.gn, (float *)S.lhu, h->stream) ? FLOOD_ERR_CUDA : FLOOD_OK);
+        else st = (flood_status)(launch_gn_out<double>(h->geo, S.gn, (double *)S.lhu, h->stream) ? FLOOD_ERR_CUDA : FLOOD_OK);
+        if (st) return finish(fail(h, FLOOD_ERR_CUDA, "gradient conversion"));
+        st = copy_out(h, dLdn_out, S.lhu, h->geo.ny, h->geo.nx, out_on_device);
+        if (st) return finish(st);
+        if (dLdh0_out) {
+            st = copy_out(h, dLdh0_out, S.lh[S.cur_l], h->geo.ny, h->geo.nx, out_on_device);
+            if (st) return finish(st);
+        }
+    }
+    // put the handle back as it was
+    h->cur = saved_cur;
+    {
+        flood_status st = copy_planes(h, working(h), S.slots[0], S.plane, S.plane_y);
+        if (st) return finish(st);
+    }
+    h->step = saved_step;
+    CKF(cudaMemcpyAsync(h->ctrl, &saved_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+    CKF(cudaMemcpyAsync(h->inflow_q, saved_inflow_q, (size_t)E * h->n_slots * esz, cudaMemcpyDeviceToDevice, h->stream));
+    CKF(cudaMemcpyAsync(h->inflow_Q, saved_inflow_Q, (size_t)E * std::max(h->n_in, 1) * sizeof(double),
+                        cudaMemcpyDeviceToDevice, h->stream));
+    CKF(cudaMemcpyAsync(h->inflow_W, saved_inflow_W, (size_t)E * std::max(h->n_in, 1) * sizeof(double),
+                        cudaMemcpyDeviceToDevice, h->stream));
+    CKF(cudaMemcpyAsync(h->t_list, saved_tlist, (E + 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CKF(cudaStreamSynchronize(h->stream));
+#undef CKF
+    return finish(FLOOD_OK);
+}

@@ -173,11 +173,11 @@ flood_status launch_inflow_epoch(flood_handle *h)
     if (h->prec == FLOOD_F32)
         CK(launch_inflow<float>(h->geo, h->secs_dev, h->n_in, h->sec_cells, nullptr, h->tab_t, h->tab_q,
                                 (const float *)h->z, (const float *)h->n, h->t_list, E, (float *)h->inflow_q,
-                                h->n_slots, h->inflow_Q, h->stream));
+                                h->n_slots, h->inflow_Q, h->inflow_W, h->stream));
     else
         CK(launch_inflow<double>(h->geo, h->secs_dev, h->n_in, h->sec_cells, nullptr, h->tab_t, h->tab_q,
                                  (const double *)h->z, (const double *)h->n, h->t_list, E, (double *)h->inflow_q,
-                                 h->n_slots, h->inflow_Q, h->stream));
+                                 h->n_slots, h->inflow_Q, h->inflow_W, h->stream));
     return FLOOD_OK;
 }
 
@@ -465,6 +465,7 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
             InflowSec S;
             std::memset(&S, 0, sizeof(S));
             S.ncell = i1 - i0;
+            S.side = s.side;
             S.cell0 = (int)icells.size();
             S.slot0 = slots;
             S.tab0 = (int)tt.size();
@@ -494,6 +495,7 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
     ALLOC(h->tab_q, double *, std::max<size_t>(tq.size(), 1) * sizeof(double));
     ALLOC(h->inflow_q, void *, (size_t)E * h->n_slots * esz);
     ALLOC(h->inflow_Q, double *, (size_t)E * std::max(h->n_in, 1) * sizeof(double));
+    ALLOC(h->inflow_W, double *, (size_t)E * std::max(h->n_in, 1) * sizeof(double));
     ALLOC(h->t_list, double *, (E + 1) * sizeof(double));
     ALLOC(h->ctrl, Ctrl *, sizeof(Ctrl));
     h->n_partials = 1024;

@@ -33,7 +33,7 @@ struct InflowSec {
     int cell0;                    // offset into the section cell-index array
     int slot0;                    // first column of this section in the per-step flux rows
     int tab0, ntab;               // hydrograph table offset / length
-    int pad;
+    int side;                     // flood_side of the section
     double sqrtS;                 // sqrt(S_in)
 };
 
@@ -95,7 +95,7 @@ template <typename T>
 cudaError_t launch_inflow(const Geom &g, const InflowSec *secs, int nsec, const int64_t *sec_cells,
                           const int8_t *sec_side, const double *tab_t, const double *tab_q,
                           const T *z, const T *n, const double *t_list, int E, T *inflow_q,
-                          int n_slots, double *inflow_Q, cudaStream_t st);
+                          int n_slots, double *inflow_Q, double *W_out, cudaStream_t st);
 // h_max of a state into ctrl->hmax_bits (max with what is there).
 template <typename T>
 cudaError_t launch_hmax(const Geom &g, const T *h, Ctrl *ctrl, cudaStream_t st);
@@ -103,6 +103,28 @@ cudaError_t launch_hmax(const Geom &g, const T *h, Ctrl *ctrl, cudaStream_t st);
 template <typename T>
 cudaError_t launch_volume(const Geom &g, const T *h, double *partials, int n_partials, double *out,
                           cudaStream_t st);
+// ---------------------------------------------------------------- adjoint
+// Buffers of one reverse step (all pitched like the state; gn in double).
+template <typename T>
+struct AdjArgs {
+    StepArgs<T> fwd;              // forward state x_k (h, qx, qy, z, n), BCs, inflow row, ctrl (dt)
+    const T *lh, *lqx, *lqy;      // adjoint of x_{k+1}
+    T *lh_out, *lqx_out, *lqy_out;   // adjoint of x_k
+    T *lhu;                       // scratch: adjoint of the unclipped depth
+    double *gn;                   // dL/dn accumulator
+    const InflowSec *secs;        // inflow sections (for the Eq. 6 derivative)
+    const int64_t *sec_cells;
+    const double *inflow_W;       // E x n_sec levels of this epoch
+};
+template <typename T>
+cudaError_t launch_adjoint_step(const AdjArgs<T> &a, cudaStream_t st);
+// dst (pitched, precision T) = gn (pitched doubles).
+template <typename T>
+cudaError_t launch_gn_out(const Geom &g, const double *gn, T *dst, cudaStream_t st);
+// lh[gauge g] += seed[g] for g < G (seed: device doubles).
+template <typename T>
+cudaError_t launch_add_seed(const Geom &g, T *lh, const int64_t *cells, int G, const double *seed, cudaStream_t st);
+
 // Gather h at gauge cells into out[0..G).
 template <typename T>
 cudaError_t launch_gauges(const Geom &g, const T *h, const int64_t *cells, int G, double *out,

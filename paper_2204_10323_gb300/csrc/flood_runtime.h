@@ -38,6 +38,7 @@ struct flood_handle {
     double *tab_t = nullptr, *tab_q = nullptr;
     void *inflow_q = nullptr;     // E x n_slots
     double *inflow_Q = nullptr;   // E x n_in
+    double *inflow_W = nullptr;   // E x n_in Eq. 6 water levels (for the adjoint)
     double *t_list = nullptr;     // E + 1
     flood::Ctrl *ctrl = nullptr;
 
