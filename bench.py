@@ -263,14 +263,95 @@ def run_gpu(args):
                          "bytes_per_cell": BYTES_PER_CELL, "kernel_ms": kern_ms, "steps_per_launch": per_launch},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "ledger": {k: L[k] for k in ("t", "dt", "V_in", "V_out", "V_clip", "volume")}}
+    sim.close()
+    del sim
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_ratio(F, torch)
+    if not args.no_ensemble:
+        line["ensemble"] = ensemble_throughput(F, torch, value)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, seconds_target=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line))
-    sim.close()
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def adjoint_ratio(F, torch, steps: int = 2000, checkpoints: int = 40):
+    """Adjoint/forward time on the 1024^2 calibration workload (16 gauges, FP32).
+
+    per_step: (store-all adjoint time - its N-1 forward replays) / N, divided
+    by the forward step time; end_to_end: the gradient with 40 snapshots
+    (binomial checkpointing) divided by the forward run.  CUDA events bracket
+    whole library calls on the library's stream."""
+    import inputs
+    p = inputs.c5_calibration(truth=False, steps=steps)
+    g = p.gauges
+    seed = np.ones((steps, len(g)))
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    s = F.Sim(p)
+    s.step(32)                       # warm-up
+    s2 = F.Sim(p)
+    t_fwd = timed(lambda: s2.step(steps))
+    s3 = F.Sim(p)
+    s3.adjoint(64, g, seed[:64], n_checkpoints=64)          # warm-up of the adjoint path
+    t_all = timed(lambda: s3.adjoint(steps, g, seed, n_checkpoints=steps))
+    t_rev = timed(lambda: s3.adjoint(steps, g, seed, n_checkpoints=checkpoints))
+    fwd_steps = s3.adjoint_forward_steps()
+    per_fwd = t_fwd / steps
+    per_rev = (t_all - (steps - 1) * per_fwd) / steps
+    for x in (s, s2, s3):
+        x.close()
+    return {"workload": f"calibration_{p.nx}x{p.ny}_{steps}_steps_{len(g)}_gauges_fp32",
+            "forward_ms_per_step": per_fwd, "adjoint_ms_per_step": per_rev,
+            "per_step_ratio": per_rev / per_fwd, "end_to_end_ratio": t_rev / t_fwd,
+            "checkpoints": checkpoints, "forward_replays": fwd_steps,
+            "gradient_ms": t_rev, "forward_run_ms": t_fwd}
+
+
+def ensemble_throughput(F, torch, single_value: float, n: int = 96, steps: int = 1024):
+    """96 uneven scenarios (256^2 .. 2048^2, own terrain seed, n ~ U(0.02, 0.08),
+    hydrograph peak ~ U(100, 1000) m^3/s), primed ~30 % wet, stepped together
+    with the autotuned launch shape; Gcell-updates/s over all scenarios."""
+    import inputs
+    from paper_2204_10323_gb300 import autotune
+    probs = []
+    for s in range(n):
+        p = inputs.c4_scenario(s, steps=5000)
+        p.h0 = inputs.wet_start(p.z, p.dx, 0.3)
+        probs.append(p)
+    ens = F.Ensemble(probs)
+    tune = autotune.tune_ensemble(ens, use_cache=False)
+    spg = tune["shape"][2]
+    steps = max(spg, steps // spg * spg)
+    ens.step(spg)
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    ens.step(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    value = ens.cells * steps / (ms * 1e-3) / 1e9
+    shapes = sorted({(p.nx, p.ny) for p in probs})
+    out = {"workload": f"{n}_scenarios_uneven_{'_'.join(f'{x}x{y}' for x, y in shapes)}_fp32",
+           "scenarios": n, "cells": ens.cells, "steps": steps, "value": value, "unit": UNIT,
+           "ratio_to_single_grid": value / single_value, "launch_shape": tune["shape"],
+           "autotune_ms_per_step": [[s, round(t, 4)] for s, t in tune["trials"]]}
+    ens.close()
+    return out
 
 
 def sim_inflows(prob):
@@ -290,6 +371,8 @@ def main():
     ap.add_argument("--traffic-bytes", type=float, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -110,7 +110,7 @@ typedef struct {
     int32_t bc_form;             /* 0 cell discharge dx h^(5/3) sqrt(S)/n, 1 literal dx^2 h^(2/3) sqrt(S)/n */
     int32_t kernel;              /* flood_kernel */
     int32_t steps_per_launch;    /* K for FLOOD_KERNEL_TILED: 1..4, must divide E (0 = 4) */
-    int32_t tile_x, tile_y;      /* tile shape for FLOOD_KERNEL_TILED (0 = auto) */
+    int32_t tile_x, tile_y;      /* stream kernel launch shape: warps per block (1..4), rows per chunk (0 = 4, 64) */
     int32_t use_graph;           /* 1: replay whole epochs from a captured CUDA graph */
     void *stream;                /* cudaStream_t, NULL = current PyTorch stream */
 } flood_opts;
@@ -221,6 +221,32 @@ flood_status flood_destroy(flood_handle *h);
 /* Text of the handle's last error ("" if none); with NULL, the calling thread's
  * last flood_create error. */
 const char *flood_last_error(const flood_handle *h);
+
+/*
+ * Ensembles (not in the paper; its scenario sweeps over discharges, dam
+ * release policies and climate scenarios are the use): n independent FP32
+ * scenarios, each with its own grid, DEM, Manning field and boundary
+ * sections (arguments as for flood_create, element k of each array), advanced
+ * together.  Every step is one launch of the stream kernel over the blocks of
+ * all scenarios, largest grid first; each scenario keeps its own CFL time
+ * step, Eq. 6 inflow and ledger.  Whole epochs are captured once into a CUDA
+ * graph (steps_per_graph steps, a multiple of epoch_steps) and replayed.
+ * opts applies to every scenario (kernel and use_graph are set by the
+ * ensemble); all scenarios share its stream.  flood_ensemble_member returns
+ * scenario k's handle for flood_read / flood_write_state / flood_set_clock
+ * (do not destroy it or step it alone).  Errors: flood_ensemble_last_error.
+ */
+typedef struct flood_ensemble flood_ensemble;
+flood_status flood_ensemble_create(int32_t n, const flood_grid *grids, const void *const *dems,
+                                   const void *const *mannings, const flood_bc_section *const *sections,
+                                   const int32_t *n_sections, const flood_opts *opts, flood_ensemble **out);
+/* Launch shape: warps per block (1..4), rows per chunk, steps per graph replay, graph on/off. */
+flood_status flood_ensemble_set_launch(flood_ensemble *e, int32_t warps, int32_t rows, int32_t steps_per_graph,
+                                       int32_t use_graph);
+flood_status flood_ensemble_step(flood_ensemble *e, int64_t n_steps);
+flood_handle *flood_ensemble_member(flood_ensemble *e, int32_t k);
+flood_status flood_ensemble_destroy(flood_ensemble *e);
+const char *flood_ensemble_last_error(const flood_ensemble *e);
 
 /* Library version string. */
 const char *flood_version(void);

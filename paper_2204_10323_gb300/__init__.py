@@ -89,6 +89,19 @@ def _load():
     L.flood_version.restype = C.c_char_p
     L.flood_volume_noalloc.argtypes = [vp, i32, i32, i64, i32, dbl, vp, vp]
     L.flood_volume_noalloc.restype = C.c_int
+    L.flood_ensemble_create.argtypes = [i32, C.POINTER(flood_grid), C.POINTER(vp), C.POINTER(vp),
+                                        C.POINTER(C.POINTER(flood_bc_section)), C.POINTER(i32),
+                                        C.POINTER(flood_opts), C.POINTER(vp)]
+    L.flood_ensemble_set_launch.argtypes = [vp, i32, i32, i32, i32]
+    L.flood_ensemble_step.argtypes = [vp, i64]
+    L.flood_ensemble_member.argtypes = [vp, i32]
+    L.flood_ensemble_member.restype = vp
+    L.flood_ensemble_destroy.argtypes = [vp]
+    L.flood_ensemble_last_error.argtypes = [vp]
+    L.flood_ensemble_last_error.restype = C.c_char_p
+    for name in ("flood_ensemble_create", "flood_ensemble_set_launch", "flood_ensemble_step",
+                 "flood_ensemble_destroy"):
+        getattr(L, name).restype = C.c_int
     for name in ("flood_create", "flood_step", "flood_sync", "flood_read", "flood_write_state",
                  "flood_set_clock", "flood_set_manning", "flood_run_gauges", "flood_adjoint", "flood_destroy"):
         getattr(L, name).restype = C.c_int
@@ -295,6 +308,111 @@ class Sim:
         if getattr(self, "h", None) is not None:
             flood_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ ensembles
+def _ens_check(st: int, ens=None):
+    if st != OK:
+        raise FloodError(st, lib().flood_ensemble_last_error(ens).decode(errors="replace"))
+
+
+def flood_ensemble_create(n, grids, dems, mannings, sections, n_sections, opts):
+    e = C.c_void_p()
+    _ens_check(lib().flood_ensemble_create(n, grids, dems, mannings, sections, n_sections, C.byref(opts),
+                                           C.byref(e)))
+    return e
+
+
+def flood_ensemble_set_launch(e, warps, rows, steps_per_graph, use_graph):
+    _ens_check(lib().flood_ensemble_set_launch(e, int(warps), int(rows), int(steps_per_graph), int(use_graph)), e)
+
+
+def flood_ensemble_step(e, n_steps):
+    _ens_check(lib().flood_ensemble_step(e, int(n_steps)), e)
+
+
+def flood_ensemble_member(e, k):
+    return C.c_void_p(lib().flood_ensemble_member(e, int(k)))
+
+
+def flood_ensemble_destroy(e):
+    lib().flood_ensemble_destroy(e)
+
+
+class _Member(Sim):
+    """View of one ensemble scenario's handle (owned by the ensemble)."""
+
+    def __init__(self, handle, problem):
+        self.prob = problem
+        self.precision = F32
+        self.dtype = np.float32
+        self.nx, self.ny = problem.nx, problem.ny
+        self.h = handle
+
+    def close(self):
+        self.h = None
+
+
+class Ensemble:
+    """FP32 scenarios of different sizes stepped together (see include/flood.h)."""
+
+    def __init__(self, problems, stream=None):
+        self.problems = list(problems)
+        n = len(self.problems)
+        po = self.problems[0].opts
+        o = default_opts()
+        o.g, o.h_dry, o.cfl_alpha, o.dt_cap, o.dt_const = po.g, po.h_dry, po.cfl_alpha, po.dt_cap, po.dt_const
+        o.dt_mode, o.epoch_steps, o.bc_form = po.dt_mode, po.epoch_steps, po.bc_form
+        o.stream = None if stream is None else C.c_void_p(stream.cuda_stream)
+        self._keep = []
+        grids = (flood_grid * n)()
+        dems = (C.c_void_p * n)()
+        mans = (C.c_void_p * n)()
+        secs = (C.POINTER(flood_bc_section) * n)()
+        nsec = (C.c_int32 * n)()
+        for k, p in enumerate(self.problems):
+            grids[k] = flood_grid(p.nx, p.ny, float(p.dx), F32)
+            z = np.ascontiguousarray(p.z, np.float32)
+            m = np.ascontiguousarray(p.n, np.float32)
+            self._keep += [z, m]
+            dems[k] = z.ctypes.data
+            mans[k] = m.ctypes.data
+            arr = (flood_bc_section * max(1, len(p.sections)))()
+            for i, s in enumerate(p.sections):
+                t = np.ascontiguousarray(s.t_s if s.t_s is not None else np.zeros(1), np.float64)
+                q = np.ascontiguousarray(s.q_m3s if s.q_m3s is not None else np.zeros(1), np.float64)
+                self._keep += [t, q]
+                arr[i] = flood_bc_section(s.side, s.kind, s.frac_start, s.frac_end, s.slope,
+                                          t.ctypes.data_as(C.POINTER(C.c_double)),
+                                          q.ctypes.data_as(C.POINTER(C.c_double)),
+                                          t.size if s.kind == INFLOW else 0)
+            self._keep.append(arr)
+            secs[k] = C.cast(arr, C.POINTER(flood_bc_section))
+            nsec[k] = len(p.sections)
+        self.e = flood_ensemble_create(n, grids, dems, mans, secs, nsec, o)
+        self.members = [_Member(flood_ensemble_member(self.e, k), p) for k, p in enumerate(self.problems)]
+        for mb, p in zip(self.members, self.problems):
+            if p.h0 is not None or p.qx0 is not None or p.qy0 is not None:
+                mb.write_state(*p.initial_state(np.float32))
+        self.cells = sum(p.nx * p.ny for p in self.problems)
+
+    def set_launch(self, warps=4, rows=64, steps_per_graph=None, use_graph=True):
+        E = self.problems[0].opts.epoch_steps
+        flood_ensemble_set_launch(self.e, warps, rows, steps_per_graph or E, int(use_graph))
+
+    def step(self, n_steps: int):
+        flood_ensemble_step(self.e, n_steps)
+
+    def close(self):
+        if getattr(self, "e", None) is not None:
+            flood_ensemble_destroy(self.e)
+            self.e = None
 
     def __del__(self):
         try:

@@ -1,0 +1,87 @@
+"""Launch-shape autotuner for ensembles (and single grids).
+
+Times each candidate (warps per block, rows per chunk, steps per graph
+replay) on the live ensemble with CUDA events, keeps the fastest, and caches
+the choice in a JSON file keyed by the device name and the scenario shapes
+(``$FLOOD_AUTOTUNE_CACHE`` or ``~/.cache/paper_2204_10323_gb300/autotune.json``).
+Every launch shape computes bit-identical results, so tuning on the live run
+does not change its trajectory; it only advances it.
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Iterable, Optional, Sequence, Tuple
+
+import torch
+
+Shape = Tuple[int, int, int]
+
+
+def cache_path() -> str:
+    return os.environ.get("FLOOD_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "paper_2204_10323_gb300",
+                                       "autotune.json"))
+
+
+def _load(path: str) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(path: str, data: dict) -> None:
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def ensemble_key(ens) -> str:
+    shapes = ",".join(f"{p.nx}x{p.ny}" for p in ens.problems)
+    return f"{torch.cuda.get_device_name()}|E{ens.problems[0].opts.epoch_steps}|{shapes}"
+
+
+def default_candidates(E: int) -> Sequence[Shape]:
+    return [(w, r, g) for w in (2, 4) for r in (32, 64, 128) for g in (E, 4 * E)]
+
+
+def tune_ensemble(ens, candidates: Optional[Iterable[Shape]] = None, trial_steps: Optional[int] = None,
+                  use_cache: bool = True) -> dict:
+    """Pick and set the fastest launch shape; returns {shape, ms_per_step, trials}."""
+    E = ens.problems[0].opts.epoch_steps
+    key = ensemble_key(ens)
+    path = cache_path()
+    cache = _load(path) if use_cache else {}
+    if use_cache and key in cache:
+        w, r, g = cache[key]["shape"]
+        ens.set_launch(w, r, g)
+        return dict(cache[key], cached=True)
+    cands = list(candidates or default_candidates(E))
+    stream = torch.cuda.current_stream()
+    trials = []
+    for (w, r, g) in cands:
+        ens.set_launch(w, r, g)
+        steps = trial_steps or 2 * g
+        steps = max(g, (steps // g) * g)
+        ens.step(g)                        # capture + warm
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        ens.step(steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        trials.append(((w, r, g), a.elapsed_time(b) / steps))
+    best, ms = min(trials, key=lambda t: t[1])
+    ens.set_launch(*best)
+    result = {"shape": list(best), "ms_per_step": ms, "trials": [[list(s), t] for s, t in trials]}
+    if use_cache:
+        cache[key] = result
+        _save(path, cache)
+    return dict(result, cached=False)

@@ -182,7 +182,7 @@ flood_status launch_inflow_epoch(flood_handle *h)
 }
 
 template <typename T>
-static StepArgs<T> make_args(flood_handle *h, int s, int k_steps, int want_hmax, const int64_t *gcells,
+StepArgs<T> make_args(flood_handle *h, int s, int k_steps, int want_hmax, const int64_t *gcells,
                              int ng, double *gout)
 {
     StepArgs<T> a;
@@ -216,6 +216,8 @@ static StepArgs<T> make_args(flood_handle *h, int s, int k_steps, int want_hmax,
     a.tile_y = h->tile_y;
     return a;
 }
+
+StepArgs<float> step_args_f32(flood_handle *h, int s) { return make_args<float>(h, s, 1, 0, nullptr, 0, nullptr); }
 
 // One launch of k steps starting at step-in-epoch s.
 flood_status launch_steps(flood_handle *h, int s, int k, int want_hmax, const int64_t *gcells, int ng,
@@ -396,8 +398,8 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
     h->kernel = o.kernel == FLOOD_KERNEL_AUTO ? FLOOD_KERNEL_STREAM : o.kernel;
     if (h->prec == FLOOD_F64) h->kernel = FLOOD_KERNEL_REFERENCE;
     h->k_per_launch = 1;
-    h->tile_x = o.tile_x > 0 ? o.tile_x : 128;
-    h->tile_y = o.tile_y > 0 ? o.tile_y : 32;
+    h->tile_x = o.tile_x;
+    h->tile_y = o.tile_y;
     if (h->kernel == FLOOD_KERNEL_TILED) {
         h->k_per_launch = o.steps_per_launch > 0 ? o.steps_per_launch : 4;
     }

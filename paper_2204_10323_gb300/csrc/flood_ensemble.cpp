@@ -1,0 +1,287 @@
+// flood_ensemble.cpp -- many independent scenarios (own grid size, terrain,
+// roughness, hydrograph) advanced together: per step one launch of the
+// stream kernel covers the blocks of every scenario (largest first), and
+// whole CFL epochs (per-scenario time step and Eq. 6 inflow, then the steps)
+// are captured once into a CUDA graph and replayed.  Each scenario is an
+// ordinary FP32 handle, so flood_read / flood_write_state work on it.
+#include "flood.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "flood_internal.h"
+#include "flood_runtime.h"
+
+using namespace flood;
+
+struct flood_ensemble {
+    std::vector<flood_handle *> members;   // creation order
+    std::vector<int> order;                // block order: largest grid first
+    int E = 16;
+    int64_t step = 0;
+    cudaStream_t stream = nullptr;
+    int warps = 4, rows = 64, steps_per_graph = 16;
+    StepArgs<float> *table[2] = {nullptr, nullptr};   // per parity of the ping-pong buffers
+    int *base = nullptr;                   // block prefix, n + 1
+    int total_blocks = 0;
+    std::vector<cudaGraphExec_t> graphs;   // [parity]
+    int use_graph = 1;
+    std::string err;
+    flood_handle *owner = nullptr;         // member 0: allocations for the tables
+};
+
+namespace {
+
+thread_local std::string g_ens_error;
+
+flood_status efail(flood_ensemble *e, flood_status st, const std::string &m)
+{
+    if (e) e->err = m;
+    else g_ens_error = m;
+    return st;
+}
+
+void drop_graphs(flood_ensemble *e)
+{
+    for (auto &g : e->graphs)
+        if (g) cudaGraphExecDestroy(g);
+    e->graphs.assign(2, nullptr);
+}
+
+flood_status build_tables(flood_ensemble *e)
+{
+    const int n = (int)e->members.size();
+    std::vector<int> base(n + 1, 0);
+    for (int k = 0; k < n; k++)
+        base[k + 1] = base[k] + stream_blocks(e->members[e->order[k]]->geo, e->warps, e->rows);
+    e->total_blocks = base[n];
+    for (int p = 0; p < 2; p++) {
+        std::vector<StepArgs<float>> t(n);
+        for (int k = 0; k < n; k++) {
+            flood_handle *h = e->members[e->order[k]];
+            const int cur = h->cur;
+            h->cur = p;
+            t[k] = step_args_f32(h, 0);
+            h->cur = cur;
+        }
+        cudaError_t c = cudaMemcpyAsync(e->table[p], t.data(), n * sizeof(StepArgs<float>), cudaMemcpyHostToDevice,
+                                        e->stream);
+        if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+    }
+    cudaError_t c = cudaMemcpyAsync(e->base, base.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, e->stream);
+    if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+    c = cudaStreamSynchronize(e->stream);
+    if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+    drop_graphs(e);
+    return FLOOD_OK;
+}
+
+// One step of every member (epoch bookkeeping per member when due).
+flood_status ensemble_step(flood_ensemble *e, cudaStream_t st)
+{
+    const int E = e->E;
+    const int s = (int)(e->step % E);
+    if (s == 0) {
+        for (flood_handle *h : e->members) {
+            cudaError_t c = launch_epoch_begin(h->geo, h->ctrl, h->t_list, E, 0, nullptr, st);
+            if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+            cudaStream_t keep = h->stream;
+            h->stream = st;
+            flood_status fs = launch_inflow_epoch(h);
+            h->stream = keep;
+            if (fs) return efail(e, fs, "inflow: " + h->err);
+        }
+    }
+    const int parity = e->members[0]->cur;
+    cudaError_t c = launch_step_stream_ensemble(e->table[parity], e->base, (int)e->members.size(), e->total_blocks,
+                                                e->warps, e->rows, s, s == E - 1 ? 1 : 0, st);
+    if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+    for (flood_handle *h : e->members) {
+        h->cur = 1 - h->cur;
+        h->step += 1;
+    }
+    e->step += 1;
+    return FLOOD_OK;
+}
+
+flood_status capture(flood_ensemble *e, int parity)
+{
+    cudaStream_t cap = nullptr;
+    cudaError_t c = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+    const int64_t step0 = e->step;
+    std::vector<int> cur0;
+    std::vector<int64_t> st0;
+    for (flood_handle *h : e->members) {
+        cur0.push_back(h->cur);
+        st0.push_back(h->step);
+    }
+    c = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    flood_status fs = FLOOD_OK;
+    if (c == cudaSuccess)
+        for (int k = 0; k < e->steps_per_graph && !fs; k++) fs = ensemble_step(e, cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t c2 = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    e->step = step0;
+    for (size_t k = 0; k < e->members.size(); k++) {
+        e->members[k]->cur = cur0[k];
+        e->members[k]->step = st0[k];
+    }
+    if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+    if (fs) {
+        if (graph) cudaGraphDestroy(graph);
+        return fs;
+    }
+    if (c2 != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c2));
+    c = cudaGraphInstantiate(&e->graphs[parity], graph, 0);
+    cudaGraphDestroy(graph);
+    if (c != cudaSuccess) {
+        e->graphs[parity] = nullptr;
+        return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+    }
+    return FLOOD_OK;
+}
+
+}  // namespace
+
+extern "C" flood_status flood_ensemble_create(int32_t n, const flood_grid *grids, const void *const *dems,
+                                              const void *const *mannings, const flood_bc_section *const *sections,
+                                              const int32_t *n_sections, const flood_opts *opts,
+                                              flood_ensemble **out)
+{
+    if (!out) return efail(nullptr, FLOOD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !grids || !dems || !n_sections) return efail(nullptr, FLOOD_ERR_ARG, "bad ensemble arguments");
+    flood_opts o;
+    if (opts) o = *opts;
+    else flood_default_opts(&o);
+    o.kernel = FLOOD_KERNEL_STREAM;
+    o.use_graph = 0;
+    flood_ensemble *e = new flood_ensemble();
+    e->E = o.epoch_steps;
+    e->graphs.assign(2, nullptr);
+    for (int k = 0; k < n; k++) {
+        if (grids[k].precision != FLOOD_F32) {
+            flood_ensemble_destroy(e);
+            return efail(nullptr, FLOOD_ERR_UNSUPPORTED, "ensembles are FP32");
+        }
+        flood_handle *h = nullptr;
+        flood_status st = flood_create(&grids[k], dems[k], mannings ? mannings[k] : nullptr,
+                                       sections ? sections[k] : nullptr, n_sections[k], &o, &h);
+        if (st) {
+            std::string m = std::string("member ") + std::to_string(k) + ": " + flood_last_error(nullptr);
+            flood_ensemble_destroy(e);
+            return efail(nullptr, st, m);
+        }
+        e->members.push_back(h);
+    }
+    e->stream = e->members[0]->stream;
+    e->owner = e->members[0];
+    for (flood_handle *h : e->members)
+        if (h->stream != e->stream) {
+            flood_ensemble_destroy(e);
+            return efail(nullptr, FLOOD_ERR_ARG, "members must share one stream");
+        }
+    e->order.resize(n);
+    std::iota(e->order.begin(), e->order.end(), 0);
+    std::stable_sort(e->order.begin(), e->order.end(), [&](int a, int b) {
+        return (int64_t)e->members[a]->geo.nx * e->members[a]->geo.ny >
+               (int64_t)e->members[b]->geo.nx * e->members[b]->geo.ny;
+    });
+    for (int p = 0; p < 2; p++) {
+        e->table[p] = (StepArgs<float> *)dev_alloc(e->owner, n * sizeof(StepArgs<float>));
+        if (!e->table[p]) {
+            flood_ensemble_destroy(e);
+            return efail(nullptr, FLOOD_ERR_OOM, "ensemble table");
+        }
+    }
+    e->base = (int *)dev_alloc(e->owner, (n + 1) * sizeof(int));
+    if (!e->base) {
+        flood_ensemble_destroy(e);
+        return efail(nullptr, FLOOD_ERR_OOM, "ensemble table");
+    }
+    flood_status st = build_tables(e);
+    if (st) {
+        std::string m = e->err;
+        flood_ensemble_destroy(e);
+        return efail(nullptr, st, m);
+    }
+    *out = e;
+    return FLOOD_OK;
+}
+
+extern "C" flood_status flood_ensemble_set_launch(flood_ensemble *e, int32_t warps, int32_t rows,
+                                                  int32_t steps_per_graph, int32_t use_graph)
+{
+    if (!e) return efail(nullptr, FLOOD_ERR_ARG, "ensemble is NULL");
+    if (warps < 1 || warps > 4 || rows < 1 || steps_per_graph < 1 || steps_per_graph % e->E != 0)
+        return efail(e, FLOOD_ERR_ARG, "warps 1..4, rows >= 1, steps_per_graph a multiple of epoch_steps");
+    e->warps = warps;
+    e->rows = rows;
+    e->steps_per_graph = steps_per_graph;
+    e->use_graph = use_graph ? 1 : 0;
+    return build_tables(e);
+}
+
+extern "C" flood_status flood_ensemble_step(flood_ensemble *e, int64_t n_steps)
+{
+    if (!e) return efail(nullptr, FLOOD_ERR_ARG, "ensemble is NULL");
+    if (n_steps < 0) return efail(e, FLOOD_ERR_ARG, "n_steps must be >= 0");
+    for (flood_handle *h : e->members)
+        if (h->sticky) return efail(e, FLOOD_ERR_STATE, "a member is in an error state");
+    while (n_steps > 0) {
+        const int s = (int)(e->step % e->E);
+        if (e->use_graph && s == 0 && n_steps >= e->steps_per_graph) {
+            const int parity = e->members[0]->cur;
+            if (!e->graphs[parity]) {
+                flood_status st = capture(e, parity);
+                if (st) return st;
+            }
+            cudaError_t c = cudaGraphLaunch(e->graphs[parity], e->stream);
+            if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+            const int flips = e->steps_per_graph & 1;
+            for (flood_handle *h : e->members) {
+                h->cur ^= flips;
+                h->step += e->steps_per_graph;
+            }
+            e->step += e->steps_per_graph;
+            n_steps -= e->steps_per_graph;
+            continue;
+        }
+        flood_status st = ensemble_step(e, e->stream);
+        if (st) return st;
+        n_steps -= 1;
+    }
+    return FLOOD_OK;
+}
+
+extern "C" flood_handle *flood_ensemble_member(flood_ensemble *e, int32_t k)
+{
+    if (!e || k < 0 || k >= (int32_t)e->members.size()) return nullptr;
+    return e->members[k];
+}
+
+extern "C" flood_status flood_ensemble_destroy(flood_ensemble *e)
+{
+    if (!e) return FLOOD_OK;
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    drop_graphs(e);
+    if (e->owner) {
+        for (int p = 0; p < 2; p++)
+            if (e->table[p]) dev_free(e->owner, e->table[p]);
+        if (e->base) dev_free(e->owner, e->base);
+    }
+    for (flood_handle *h : e->members) flood_destroy(h);
+    delete e;
+    return FLOOD_OK;
+}
+
+extern "C" const char *flood_ensemble_last_error(const flood_ensemble *e)
+{
+    return e ? e->err.c_str() : g_ens_error.c_str();
+}

@@ -83,6 +83,13 @@ template <typename T>
 cudaError_t launch_step_reference(const StepArgs<T> &a, cudaStream_t st);
 cudaError_t launch_step_rows(const StepArgs<float> &a, cudaStream_t st);
 cudaError_t launch_step_stream(const StepArgs<float> &a, cudaStream_t st);
+// Stream kernel over many grids: table of per-grid arguments (device), block
+// prefix base[n+1] (device), one launch of total_blocks blocks.
+cudaError_t launch_step_stream_ensemble(const StepArgs<float> *table, const int *base, int n, int total_blocks,
+                                        int warps, int rows, int step, int want_hmax, cudaStream_t st);
+// Blocks of one grid for the stream kernel, and the (warps, rows) a tile pair selects.
+int stream_blocks(const Geom &g, int warps, int rows);
+void stream_launch_shape(int tile_x, int tile_y, int *warps, int *rows);
 cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st);
 size_t tiled_smem_bytes(int tile_x, int tile_y, int k);
 

@@ -19,7 +19,7 @@ struct flood_handle {
     flood_opts opts{};
     int kernel = FLOOD_KERNEL_REFERENCE;
     int k_per_launch = 1;
-    int tile_x = 128, tile_y = 32;
+    int tile_x = 0, tile_y = 0;   // stream kernel: warps per block, rows per chunk (0 = default)
     int device = 0;
     cudaStream_t stream = nullptr;
 
@@ -81,6 +81,7 @@ flood_status launch_steps(flood_handle *h, int s, int k, int want_hmax, const in
 flood_status advance(flood_handle *h, int64_t n, const int64_t *gcells, int ng, double *gbuf,
                      const double *fixed_dt_log);
 flood_status check_device_status(flood_handle *h);
+StepArgs<float> step_args_f32(flood_handle *h, int s);
 flood_status ensure_gauge_buffers(flood_handle *h, int ng, size_t n_values);
 
 // CUDA-graph epochs (flood_graph.cpp)

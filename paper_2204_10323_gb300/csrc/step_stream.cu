@@ -20,8 +20,9 @@ namespace flood {
 
 namespace {
 
-constexpr int kWarps = 4;        // warps (strips) per block
-constexpr int kRows = 64;        // rows per chunk
+constexpr int kMaxWarps = 4;     // warps (strips) per block at most
+constexpr int kDefaultWarps = 4;
+constexpr int kDefaultRows = 64; // rows per chunk unless tuned
 constexpr int kDepth = 4;        // rows in flight per warp
 constexpr int kSeg = 136;        // floats per staged row segment (x0-4 .. x0+131)
 constexpr int kFields = 5;       // h, z, n, qx, qy
@@ -35,7 +36,6 @@ struct alignas(16) WarpRing {
 };
 
 static_assert(sizeof(WarpRing) % 16 == 0, "per-warp ring must keep 16-byte alignment");
-constexpr size_t kSmemBytes = sizeof(WarpRing) * kWarps;
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
@@ -52,19 +52,20 @@ __device__ __forceinline__ void set(float4 &v, int k, float x)
     else v.w = x;
 }
 
-__global__ void __launch_bounds__(kWarps * 32, 5) step_stream_kernel(const StepArgs<float> a)
+// One block's work: warps cover consecutive 128-column strips of strip block
+// bx, all on the row chunk by of `rows` rows; step is the step inside the epoch.
+__device__ __forceinline__ void stream_body(const StepArgs<float> &a, const int step, const int want_hmax, const int bx,
+                                            const int by, const int rows, unsigned char *smem_raw, double *red)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
     const Geom &G = a.geo;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nx = G.nx, ny = G.ny;
     const int P = G.pitch;
-    const int x0 = (blockIdx.x * kWarps + warp) * 128;
+    const int x0 = (bx * nwarps + warp) * 128;
     const int c0 = x0 + 4 * lane;
     const bool active = x0 < nx;
-    const int y0 = blockIdx.y * kRows;
-    const int y1 = min(y0 + kRows, ny);
+    const int y0 = by * rows;
+    const int y1 = min(y0 + rows, ny);
     const int jstart = y0 > 0 ? y0 - 1 : 0;
     const int jlast = min(y1, ny - 1);             // last row that is staged
     const int nload = jlast - jstart + 1;
@@ -160,8 +161,8 @@ __global__ void __launch_bounds__(kWarps * 32, 5) step_stream_kernel(const StepA
                 int c = c0 + k;
                 float v = 0.0f;
                 if (c < nx) {
-                    if (j == 0) v = boundary_fast(a, 2, c, get(ch, k), get(cn, k), vout);
-                    else if (j == ny) v = boundary_fast(a, 3, c, get(hp, k), get(np_, k), vout);
+                    if (j == 0) v = boundary_fast_at(a, step, 2, c, get(ch, k), get(cn, k), vout);
+                    else if (j == ny) v = boundary_fast_at(a, step, 3, c, get(hp, k), get(np_, k), vout);
                     else {
                         float zl = get(zp, k), zr = get(cz, k);
                         v = face_fast(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr, fmaxf(zl, zr),
@@ -236,8 +237,8 @@ __global__ void __launch_bounds__(kWarps * 32, 5) step_stream_kernel(const StepA
                 float zl = k == 0 ? zl0 : get(cz, k - 1);
                 float nl = k == 0 ? nl0 : get(cn, k - 1);
                 float v = 0.0f;
-                if (c == 0) v = boundary_fast(a, 0, j, get(ch, 0), get(cn, 0), vout);
-                else if (c == nx) v = boundary_fast(a, 1, j, hl, nl, vout);
+                if (c == 0) v = boundary_fast_at(a, step, 0, j, get(ch, 0), get(cn, 0), vout);
+                else if (c == nx) v = boundary_fast_at(a, step, 1, j, hl, nl, vout);
                 else if (c < nx) {
                     float zr = get(cz, k);
                     v = face_fast(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), K);
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kWarps * 32, 5) step_stream_kernel(const StepA
             if (lane == 31) {
                 const int c = x0 + 128;
                 qe = 0.0f;
-                if (c == nx) qe = boundary_fast(a, 1, j, ch.w, cn.w, vout);
+                if (c == nx) qe = boundary_fast_at(a, step, 1, j, ch.w, cn.w, vout);
                 else if (c < nx) qe = face_fast(qxE, ch.w + cz.w, hE + zE, fmaxf(cz.w, zE), cn.w + nE, K);
             }
             hp = ch;
@@ -272,39 +273,103 @@ __global__ void __launch_bounds__(kWarps * 32, 5) step_stream_kernel(const StepA
     if (threadIdx.x == 0 && bo != 0.0) atomicAdd(&a.ctrl->V_out, dtd * bo);
     double bc = block_reduce<false>(vclip, red);
     if (threadIdx.x == 0 && bc != 0.0) atomicAdd(&a.ctrl->V_clip, bc);
-    if (a.want_hmax) {
+    if (want_hmax) {
         double bm = block_reduce<true>(nan_seen ? (double)NAN : (double)hmax, red);
         if (threadIdx.x == 0) atomic_max_nonneg(&a.ctrl->hmax_bits, bm);
     }
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    if (bx == 0 && by == 0 && threadIdx.x == 0) {
         double vin = a.ctrl->V_in;
         for (int k = 0; k < a.n_inflow_sec; k++) {
-            double Q = a.inflow_Q[(size_t)a.s * a.n_inflow_sec + k];
+            double Q = a.inflow_Q[(size_t)step * a.n_inflow_sec + k];
             if (Q > 0.0) vin += dtd * Q;
         }
         a.ctrl->V_in = vin;
-        a.ctrl->t = a.t_list[a.s + 1];
+        a.ctrl->t = a.t_list[step + 1];
     }
+}
+
+__global__ void __launch_bounds__(kMaxWarps * 32, 5) step_stream_kernel(const StepArgs<float> a, const int rows)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    stream_body(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, smem_raw, red);
+}
+
+// Many grids in one launch: block b belongs to the scenario whose block range
+// [base[k], base[k+1]) holds it (scenarios ordered largest first).
+__global__ void __launch_bounds__(kMaxWarps * 32, 5)
+    step_stream_ensemble_kernel(const StepArgs<float> *table, const int *base, const int n, const int rows,
+                                const int step, const int want_hmax)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    const int b = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const StepArgs<float> &a = table[lo];
+    const int nwarps = blockDim.x >> 5;
+    const int strips = (a.geo.nx + 127) / 128;
+    const int nbx = (strips + nwarps - 1) / nwarps;
+    const int local = b - base[lo];
+    stream_body(a, step, want_hmax, local % nbx, local / nbx, rows, smem_raw, red);
+}
+
+cudaError_t configure(int warps)
+{
+    static bool configured = false;
+    if (configured) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(step_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(WarpRing) * kMaxWarps));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(step_stream_ensemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(WarpRing) * kMaxWarps));
+    if (e != cudaSuccess) return e;
+    configured = true;
+    (void)warps;
+    return cudaSuccess;
 }
 
 }  // namespace
 
+int stream_blocks(const Geom &g, int warps, int rows)
+{
+    const int strips = (g.nx + 127) / 128;
+    return ((strips + warps - 1) / warps) * ((g.ny + rows - 1) / rows);
+}
+
+void stream_launch_shape(int tile_x, int tile_y, int *warps, int *rows)
+{
+    *warps = (tile_x >= 1 && tile_x <= kMaxWarps) ? tile_x : kDefaultWarps;
+    *rows = tile_y >= 1 ? tile_y : kDefaultRows;
+}
+
 cudaError_t launch_step_stream(const StepArgs<float> &a, cudaStream_t st)
 {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(step_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kSmemBytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    int warps, rows;
+    stream_launch_shape(a.tile_x, a.tile_y, &warps, &rows);
+    cudaError_t e = configure(warps);
+    if (e != cudaSuccess) return e;
     const int strips = (a.geo.nx + 127) / 128;
-    dim3 grid((strips + kWarps - 1) / kWarps, (a.geo.ny + kRows - 1) / kRows);
-    step_stream_kernel<<<grid, kWarps * 32, kSmemBytes, st>>>(a);
-    cudaError_t e = cudaGetLastError();
+    dim3 grid((strips + warps - 1) / warps, (a.geo.ny + rows - 1) / rows);
+    step_stream_kernel<<<grid, warps * 32, sizeof(WarpRing) * warps, st>>>(a, rows);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.gauge_out) return launch_gauges<float>(a.geo, a.h_out, a.gauge_cells, a.n_gauges, a.gauge_out, st);
     return cudaSuccess;
+}
+
+cudaError_t launch_step_stream_ensemble(const StepArgs<float> *table, const int *base, int n, int total_blocks,
+                                        int warps, int rows, int step, int want_hmax, cudaStream_t st)
+{
+    cudaError_t e = configure(warps);
+    if (e != cudaSuccess) return e;
+    step_stream_ensemble_kernel<<<total_blocks, warps * 32, sizeof(WarpRing) * warps, st>>>(table, base, n, rows,
+                                                                                          step, want_hmax);
+    return cudaGetLastError();
 }
 
 }  // namespace flood

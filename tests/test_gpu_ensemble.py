@@ -1,0 +1,75 @@
+"""Ensembles: many uneven scenarios in one launch per step must give exactly
+what each scenario gives alone (the same stream-kernel arithmetic, bit for
+bit), for every launch shape, with and without graph replay."""
+import numpy as np
+import pytest
+
+import inputs
+from inputs import Problem
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def F():
+    import paper_2204_10323_gb300 as F
+    return F
+
+
+def scenarios():
+    shapes = [(130, 70, 2), (257, 129, 6), (64, 300, 17), (500, 40, 18), (33, 17, 0)]
+    out = []
+    for nx, ny, seed in shapes:
+        p = inputs.random_small(nx, ny, seed)
+        r = lambda a: None if a is None else a.astype(np.float32).astype(np.float64)
+        p = Problem(p.name, p.nx, p.ny, p.dx, r(p.z), r(p.n), p.sections, p.opts, h0=r(p.h0), qx0=r(p.qx0),
+                    qy0=r(p.qy0))
+        out.append(p)
+    return out
+
+
+@pytest.mark.parametrize("warps,rows,spg,graph", [(4, 64, 4, True), (2, 16, 8, True), (1, 128, 4, False),
+                                                  (4, 7, 12, True)])
+def test_ensemble_equals_members_alone(warps, rows, spg, graph):
+    Fm = F()
+    probs = scenarios()
+    ens = Fm.Ensemble(probs)
+    ens.set_launch(warps, rows, spg, use_graph=graph)
+    ens.step(3)
+    ens.step(spg * 2)
+    ens.step(5)
+    n = 3 + 2 * spg + 5
+    for mb, p in zip(ens.members, probs):
+        s = Fm.Sim(p, kernel=Fm.KERNEL_STREAM)
+        s.step(n)
+        for f in (Fm.FIELD_H, Fm.FIELD_QX, Fm.FIELD_QY):
+            assert np.array_equal(mb.read(f), s.read(f)), (p.name, f)
+        La, Lb = mb.ledger(), s.ledger()
+        for k in ("t", "dt", "V_in", "V_out", "V_clip", "volume", "step"):
+            assert La[k] == pytest.approx(Lb[k], rel=1e-12, abs=1e-12), (p.name, k)
+    ens.close()
+
+
+def test_ensemble_member_matches_oracle():
+    Fm = F()
+    probs = scenarios()
+    ens = Fm.Ensemble(probs)
+    ens.set_launch(4, 64, 4)
+    ens.step(100)
+    p = probs[1]
+    o = oracle.Oracle(p)
+    o.run(100)
+    assert np.abs(ens.members[1].read(Fm.FIELD_H).astype(np.float64) - o.h).max() < 1e-3
+    ens.close()
+
+
+def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
+    from paper_2204_10323_gb300 import autotune
+    Fm = F()
+    monkeypatch.setenv("FLOOD_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    ens = Fm.Ensemble(scenarios())
+    r = autotune.tune_ensemble(ens, candidates=[(4, 64, 4), (2, 32, 8)], trial_steps=8)
+    assert not r["cached"] and len(r["trials"]) == 2 and tuple(r["shape"]) in [(4, 64, 4), (2, 32, 8)]
+    r2 = autotune.tune_ensemble(ens)
+    assert r2["cached"] and r2["shape"] == r["shape"]
+    ens.close()
