@@ -11,9 +11,8 @@ namespace {
 
 // Time-step rule at an epoch start: constant, frozen (adjoint replays), or
 // dt = min(dt_cap, alpha dx / sqrt(g h_max)); h_max = 0 gives dt_cap.
-__global__ void epoch_begin_kernel(Geom G, Ctrl *ctrl, double *t_list, int E, const double *fixed_dt)
+__device__ void epoch_begin_body(const Geom &G, Ctrl *ctrl, double *t_list, int E, const double *fixed_dt)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double hmax = __longlong_as_double((long long)ctrl->hmax_bits);
     if (!isfinite(hmax)) ctrl->status |= kStatusNonfinite;
     if (ctrl->dt > 0.0 && hmax > 0.0 && ctrl->dt * sqrt(G.g * hmax) > G.dx) ctrl->cfl_exceed += 1.0;
@@ -31,6 +30,21 @@ __global__ void epoch_begin_kernel(Geom G, Ctrl *ctrl, double *t_list, int E, co
         t = t + dt;
         t_list[s + 1] = t;
     }
+}
+
+__global__ void epoch_begin_kernel(Geom G, Ctrl *ctrl, double *t_list, int E, const double *fixed_dt)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    epoch_begin_body(G, ctrl, t_list, E, fixed_dt);
+}
+
+// One thread per simulation of a batch.
+template <typename T>
+__global__ void epoch_begin_batched_kernel(const EpochArgs<T> *tab, int n, int E)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    epoch_begin_body(tab[k].geo, tab[k].ctrl, tab[k].t_list, E, nullptr);
 }
 
 // Linear interpolation in the hydrograph table, constant past both ends.
@@ -95,12 +109,12 @@ __device__ double section_total(const InflowSec &S, const int64_t *cells, const 
 // from 1 m), 200 halvings at most or a bracket below 1e-12 m, W = upper end;
 // then each cell's discharge scaled by Q_in / sum, stored as unit-width flux.
 template <typename T>
-__global__ void inflow_kernel(Geom G, const InflowSec *secs, int nsec, const int64_t *cells,
-                              const double *tab_t, const double *tab_q, const T *z, const T *n,
-                              const double *t_list, T *inflow_q, int n_slots, double *inflow_Q, double *W_out)
+__device__ void inflow_body(const Geom &G, const InflowSec *secs, int nsec, const int64_t *cells,
+                            const double *tab_t, const double *tab_q, const T *z, const T *n,
+                            const double *t_list, T *inflow_q, int n_slots, double *inflow_Q, double *W_out,
+                            const int s, const int k, double *red)
 {
-    __shared__ double red[kInflowThreads / 32];
-    const int s = blockIdx.x, k = blockIdx.y, tid = threadIdx.x;
+    const int tid = threadIdx.x;
     const InflowSec S = secs[k];
     const double t = t_list[s];
     const double Q = hydrograph(tab_t + S.tab0, tab_q + S.tab0, S.ntab, t);
@@ -136,6 +150,27 @@ __global__ void inflow_kernel(Geom G, const InflowSec *secs, int nsec, const int
         double w = hh > 0.0 ? manning_cell_t(hh, S.sqrtS, n[idx], dx, form) : 0.0;
         out[c] = T((w * (Q / total)) / dx);
     }
+}
+
+template <typename T>
+__global__ void inflow_kernel(Geom G, const InflowSec *secs, int nsec, const int64_t *cells,
+                              const double *tab_t, const double *tab_q, const T *z, const T *n,
+                              const double *t_list, T *inflow_q, int n_slots, double *inflow_Q, double *W_out)
+{
+    __shared__ double red[kInflowThreads / 32];
+    inflow_body<T>(G, secs, nsec, cells, tab_t, tab_q, z, n, t_list, inflow_q, n_slots, inflow_Q, W_out, blockIdx.x,
+                   blockIdx.y, red);
+}
+
+// Eq. 6 for every (step, section) of a batch of simulations: block (s, task).
+template <typename T>
+__global__ void inflow_batched_kernel(const EpochArgs<T> *tab, const int2 *tasks)
+{
+    __shared__ double red[kInflowThreads / 32];
+    const int2 t = tasks[blockIdx.y];
+    const EpochArgs<T> &A = tab[t.x];
+    inflow_body<T>(A.geo, A.secs, A.nsec, A.cells, A.tab_t, A.tab_q, A.z, A.n, A.t_list, A.inflow_q, A.n_slots,
+                   A.inflow_Q, A.inflow_W, blockIdx.x, t.y, red);
 }
 
 template <typename T>
@@ -191,6 +226,19 @@ cudaError_t launch_epoch_begin(const Geom &g, Ctrl *ctrl, double *t_list, int E,
     epoch_begin_kernel<<<1, 32, 0, st>>>(g, ctrl, t_list, E, fixed_dt);
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_epoch_batched(const EpochArgs<T> *tab, int n, const int2 *tasks, int n_tasks, int E,
+                                 cudaStream_t st)
+{
+    epoch_begin_batched_kernel<T><<<(n + 127) / 128, 128, 0, st>>>(tab, n, E);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || n_tasks == 0) return e;
+    inflow_batched_kernel<T><<<dim3(E, n_tasks), kInflowThreads, 0, st>>>(tab, tasks);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_epoch_batched<float>(const EpochArgs<float> *, int, const int2 *, int, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_inflow(const Geom &g, const InflowSec *secs, int nsec, const int64_t *sec_cells,

@@ -28,6 +28,9 @@ struct flood_ensemble {
     StepArgs<float> *table[2] = {nullptr, nullptr};   // per parity of the ping-pong buffers
     int *base = nullptr;                   // block prefix, n + 1
     int total_blocks = 0;
+    EpochArgs<float> *etab = nullptr;      // per member: epoch bookkeeping arguments
+    int2 *tasks = nullptr;                 // (member, inflow section) pairs
+    int n_tasks = 0;
     std::vector<cudaGraphExec_t> graphs;   // [parity]
     int use_graph = 1;
     std::string err;
@@ -86,15 +89,8 @@ flood_status ensemble_step(flood_ensemble *e, cudaStream_t st)
     const int E = e->E;
     const int s = (int)(e->step % E);
     if (s == 0) {
-        for (flood_handle *h : e->members) {
-            cudaError_t c = launch_epoch_begin(h->geo, h->ctrl, h->t_list, E, 0, nullptr, st);
-            if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
-            cudaStream_t keep = h->stream;
-            h->stream = st;
-            flood_status fs = launch_inflow_epoch(h);
-            h->stream = keep;
-            if (fs) return efail(e, fs, "inflow: " + h->err);
-        }
+        cudaError_t c = launch_epoch_batched<float>(e->etab, (int)e->members.size(), e->tasks, e->n_tasks, E, st);
+        if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
     }
     const int parity = e->members[0]->cur;
     cudaError_t c = launch_step_stream_ensemble(e->table[parity], e->base, (int)e->members.size(), e->total_blocks,
@@ -201,7 +197,34 @@ extern "C" flood_status flood_ensemble_create(int32_t n, const flood_grid *grids
         }
     }
     e->base = (int *)dev_alloc(e->owner, (n + 1) * sizeof(int));
-    if (!e->base) {
+    e->etab = (EpochArgs<float> *)dev_alloc(e->owner, n * sizeof(EpochArgs<float>));
+    std::vector<EpochArgs<float>> et(n);
+    std::vector<int2> tk;
+    for (int k = 0; k < n; k++) {
+        flood_handle *h = e->members[k];
+        EpochArgs<float> &A = et[k];
+        A.geo = h->geo;
+        A.ctrl = h->ctrl;
+        A.t_list = h->t_list;
+        A.secs = h->secs_dev;
+        A.nsec = h->n_in;
+        A.cells = h->sec_cells;
+        A.tab_t = h->tab_t;
+        A.tab_q = h->tab_q;
+        A.z = (const float *)h->z;
+        A.n = (const float *)h->n;
+        A.inflow_q = (float *)h->inflow_q;
+        A.n_slots = h->n_slots;
+        A.inflow_Q = h->inflow_Q;
+        A.inflow_W = h->inflow_W;
+        for (int sct = 0; sct < h->n_in; sct++) tk.push_back(make_int2(k, sct));
+    }
+    e->n_tasks = (int)tk.size();
+    e->tasks = (int2 *)dev_alloc(e->owner, std::max<size_t>(tk.size(), 1) * sizeof(int2));
+    if (!e->base || !e->etab || !e->tasks ||
+        cudaMemcpyAsync(e->etab, et.data(), n * sizeof(EpochArgs<float>), cudaMemcpyHostToDevice, e->stream) ||
+        (tk.size() &&
+         cudaMemcpyAsync(e->tasks, tk.data(), tk.size() * sizeof(int2), cudaMemcpyHostToDevice, e->stream))) {
         flood_ensemble_destroy(e);
         return efail(nullptr, FLOOD_ERR_OOM, "ensemble table");
     }
@@ -275,6 +298,8 @@ extern "C" flood_status flood_ensemble_destroy(flood_ensemble *e)
         for (int p = 0; p < 2; p++)
             if (e->table[p]) dev_free(e->owner, e->table[p]);
         if (e->base) dev_free(e->owner, e->base);
+        if (e->etab) dev_free(e->owner, e->etab);
+        if (e->tasks) dev_free(e->owner, e->tasks);
     }
     for (flood_handle *h : e->members) flood_destroy(h);
     delete e;

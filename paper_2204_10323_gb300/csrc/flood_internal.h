@@ -89,7 +89,7 @@ cudaError_t launch_step_stream_ensemble(const StepArgs<float> *table, const int 
                                         int warps, int rows, int step, int want_hmax, cudaStream_t st);
 // Blocks of one grid for the stream kernel, and the (warps, rows) a tile pair selects.
 int stream_blocks(const Geom &g, int warps, int rows);
-void stream_launch_shape(int tile_x, int tile_y, int *warps, int *rows);
+void stream_launch_shape(const Geom &g, int tile_x, int tile_y, int *warps, int *rows);
 cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st);
 size_t tiled_smem_bytes(int tile_x, int tile_y, int k);
 
@@ -103,6 +103,26 @@ cudaError_t launch_inflow(const Geom &g, const InflowSec *secs, int nsec, const 
                           const int8_t *sec_side, const double *tab_t, const double *tab_q,
                           const T *z, const T *n, const double *t_list, int E, T *inflow_q,
                           int n_slots, double *inflow_Q, double *W_out, cudaStream_t st);
+// Epoch bookkeeping of a batch of simulations in two launches: the time-step
+// rule for each (one thread each), then Eq. 6 for every (step, section) task
+// (task = {simulation, section}).
+template <typename T>
+struct EpochArgs {
+    Geom geo;
+    Ctrl *ctrl;
+    double *t_list;
+    const InflowSec *secs;
+    int nsec;
+    const int64_t *cells;
+    const double *tab_t, *tab_q;
+    const T *z, *n;
+    T *inflow_q;
+    int n_slots;
+    double *inflow_Q, *inflow_W;
+};
+template <typename T>
+cudaError_t launch_epoch_batched(const EpochArgs<T> *tab, int n, const int2 *tasks, int n_tasks, int E,
+                                 cudaStream_t st);
 // h_max of a state into ctrl->hmax_bits (max with what is there).
 template <typename T>
 cudaError_t launch_hmax(const Geom &g, const T *h, Ctrl *ctrl, cudaStream_t st);

@@ -341,16 +341,32 @@ int stream_blocks(const Geom &g, int warps, int rows)
     return ((strips + warps - 1) / warps) * ((g.ny + rows - 1) / rows);
 }
 
-void stream_launch_shape(int tile_x, int tile_y, int *warps, int *rows)
+// Launch shape: the caller's (tile_x warps, tile_y rows) when given, else the
+// tallest chunk and widest block that still give about two waves of blocks
+// (152 SMs x 5 resident blocks), so small grids keep every SM busy.
+void stream_launch_shape(const Geom &g, int tile_x, int tile_y, int *warps, int *rows)
 {
-    *warps = (tile_x >= 1 && tile_x <= kMaxWarps) ? tile_x : kDefaultWarps;
-    *rows = tile_y >= 1 ? tile_y : kDefaultRows;
+    if (tile_x >= 1 && tile_x <= kMaxWarps && tile_y >= 1) {
+        *warps = tile_x;
+        *rows = tile_y;
+        return;
+    }
+    const int want = 2 * 152 * 5;
+    for (int w : {kDefaultWarps, 2, 1})
+        for (int r : {kDefaultRows, 32, 16, 8})
+            if (stream_blocks(g, w, r) >= want) {
+                *warps = (tile_x >= 1 && tile_x <= kMaxWarps) ? tile_x : w;
+                *rows = tile_y >= 1 ? tile_y : r;
+                return;
+            }
+    *warps = (tile_x >= 1 && tile_x <= kMaxWarps) ? tile_x : 1;
+    *rows = tile_y >= 1 ? tile_y : 8;
 }
 
 cudaError_t launch_step_stream(const StepArgs<float> &a, cudaStream_t st)
 {
     int warps, rows;
-    stream_launch_shape(a.tile_x, a.tile_y, &warps, &rows);
+    stream_launch_shape(a.geo, a.tile_x, a.tile_y, &warps, &rows);
     cudaError_t e = configure(warps);
     if (e != cudaSuccess) return e;
     const int strips = (a.geo.nx + 127) / 128;
