@@ -17,9 +17,9 @@
 // four faces (both cells of a face evaluate its derivatives), so no atomics
 // are needed and the result is deterministic.
 //
-// Pass 1 recomputes the forward faces with the same arithmetic as the
-// forward kernels (IEEE order for FP64, the fast FP32 face for FP32), so the
-// clip mask and the wet/dry decisions are the forward's own.
+// The clip mask is recomputed with the forward kernels' own arithmetic (IEEE
+// order for FP64, the fast FP32 face for FP32), so the clip and wet/dry
+// decisions are exactly the forward's.
 #include "fast_face.cuh"
 
 namespace flood {
@@ -54,6 +54,7 @@ template <> struct Fwd<double> {
         return O::add(h, O::div(O::mul(dt, dv), dx));
     }
     __device__ static double rcbrt_(double x) { return ::rcbrt(x); }
+    __device__ static double rcp_(double x) { return 1.0 / x; }
 };
 
 template <> struct Fwd<float> {
@@ -87,6 +88,7 @@ template <> struct Fwd<float> {
         return __fmaf_rn(K.dtdx, dv, h);
     }
     __device__ static float rcbrt_(float x) { return rcbrtf(x); }
+    __device__ static float rcp_(float x) { return __frcp_rn(x); }
 };
 
 // Partial derivatives of one wet face's Eq. 3 value.
@@ -102,20 +104,21 @@ __device__ __forceinline__ FaceLin<T> face_lin(T q, T hL, T zL, T nL, T hR, T zR
     const T nf = T(0.5) * (nL + nR);
     const T gdt = g * dt, a1 = gdt / dx;
     const T m13 = Fwd<T>::rcbrt_(hf);
-    const T hf_m73 = m13 / (hf * hf);
+    const T inv_hf = Fwd<T>::rcp_(hf);
+    const T hf_m73 = m13 * inv_hf * inv_hf;
     const T c0 = gdt * nf * nf * hf_m73;     // friction per |q|
     const T fric = c0 * (q < T(0) ? -q : q);
-    const T den = T(1) + fric;
+    const T inv_den = Fwd<T>::rcp_(T(1) + fric);
     const T slope = etaR - etaL;
-    const T F = (q - a1 * hf * slope) / den;
+    const T F = (q - a1 * hf * slope) * inv_den;
     const T sg = q > T(0) ? T(1) : (q < T(0) ? T(-1) : T(0));
-    r.dq = (T(1) - F * c0 * sg) / den;
-    const T dF_dhf = (-a1 * slope + F * (T(7) / T(3)) * fric / hf) / den;
-    const T d_expl = a1 * hf / den;
+    r.dq = (T(1) - F * c0 * sg) * inv_den;
+    const T dF_dhf = (-a1 * slope + F * (T(7) / T(3)) * fric * inv_hf) * inv_den;
+    const T d_expl = a1 * hf * inv_den;
     const bool left = etaL >= etaR;
     r.dhL = d_expl + (left ? dF_dhf : T(0));
     r.dhR = -d_expl + (left ? T(0) : dF_dhf);
-    r.dn = -F * fric / (nf * den);
+    r.dn = -F * fric * inv_den * Fwd<T>::rcp_(nf);
     return r;
 }
 
@@ -138,15 +141,13 @@ __device__ __forceinline__ T bface(const StepArgs<T> &a, const Fwd<T> &F, int si
     return -inward * F.outflow(h, T(a.bc.sqrtS[off + k]), n, G.bc_form);
 }
 
-// Pass 1: recompute the step for each cell; lhu = lambda_h' where the depth was not clipped.
+// Adjoint of cell (i, j)'s unclipped depth: lambda_h'(c) plus the loss's
+// seeds at gauge cells, where the recomputed forward depth was not clipped.
 template <typename T>
-__global__ void __launch_bounds__(BX *BY) adj_mask_kernel(const AdjArgs<T> A)
+__device__ __forceinline__ T unclipped_adjoint(const AdjArgs<T> &A, const Fwd<T> &F, const int i, const int j)
 {
     const StepArgs<T> &a = A.fwd;
     const Geom &G = a.geo;
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    if (i >= G.nx || j >= G.ny) return;
-    const Fwd<T> F(G, a.ctrl->dt);
     const size_t P = (size_t)G.pitch, c = (size_t)j * P + i;
     const T hC = a.h[c], zC = a.z[c], nC = a.n[c];
     T qW, qE, qS, qN;
@@ -159,7 +160,12 @@ __global__ void __launch_bounds__(BX *BY) adj_mask_kernel(const AdjArgs<T> A)
     if (j == G.ny - 1) qN = bface(a, F, 3, i, hC, nC);
     else qN = F.face(a.qy[c + P], hC, zC, nC, a.h[c + P], a.z[c + P], a.n[c + P]);
     const T hu = F.update(hC, qW, qE, qS, qN);
-    A.lhu[c] = hu < T(0) ? T(0) : A.lh[c];
+    if (hu < T(0)) return T(0);
+    T lam = A.lh[c];
+    const int64_t flat = (int64_t)j * G.nx + i;
+    for (int g = 0; g < A.n_gauges; g++)          // repeated gauges add up in order
+        if (A.gauge_cells[g] == flat) lam = lam + T(A.seed[g]);
+    return lam;
 }
 
 // Adjoint of an outflow boundary face: contributions to lambda_h(c) and dL/dn(c).
@@ -178,20 +184,37 @@ __device__ __forceinline__ void outflow_adj(const StepArgs<T> &a, const Fwd<T> &
     gn += (double)(-nu * q / n);
 }
 
-// Pass 2: gather the adjoint of each cell and of its own west and south faces.
+// One launch per reverse step: the block first recomputes the clip mask (and
+// adds the gauge seeds) for its tile plus a one-cell halo into shared memory,
+// then every cell gathers its own adjoint and that of its west and south faces.
 template <typename T>
 __global__ void __launch_bounds__(BX *BY) adj_step_kernel(const AdjArgs<T> A)
 {
+    __shared__ T s_lhu[BY + 2][BX + 2];
     const StepArgs<T> &a = A.fwd;
     const Geom &G = a.geo;
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    if (i >= G.nx || j >= G.ny) return;
     const double dtd = a.ctrl->dt;
     const Fwd<T> F(G, dtd);
+    {
+        const int tid = threadIdx.y * BX + threadIdx.x;
+        const int i0 = blockIdx.x * BX - 1, j0 = blockIdx.y * BY - 1;
+        for (int t = tid; t < (BX + 2) * (BY + 2); t += BX * BY) {
+            const int li = t % (BX + 2), lj = t / (BX + 2);
+            const int ii = i0 + li, jj = j0 + lj;
+            T v = T(0);
+            if (ii >= 0 && ii < G.nx && jj >= 0 && jj < G.ny) v = unclipped_adjoint(A, F, ii, jj);
+            s_lhu[lj][li] = v;
+        }
+    }
+    __syncthreads();
+    const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
     const T dt = T(dtd), dx = T(G.dx), g = T(G.g), hd = T(G.h_dry), dtdx = dt / dx;
     const size_t P = (size_t)G.pitch, c = (size_t)j * P + i;
     const T hC = a.h[c], zC = a.z[c], nC = a.n[c];
-    const T lu = A.lhu[c];
+    const T lu = s_lhu[ty][tx];
+    if (i == 0 || j == 0 || i == G.nx - 1 || j == G.ny - 1) A.lhu[c] = lu;   // read by the inflow pass
     T lh = lu;
     double gn = 0.0;
     // west face (this cell is R)
@@ -202,7 +225,7 @@ __global__ void __launch_bounds__(BX *BY) adj_step_kernel(const AdjArgs<T> A)
             A.lqx_out[c] = T(0);
         } else {
             const T hL = a.h[c - 1], zL = a.z[c - 1], nL = a.n[c - 1];
-            const T mu = A.lqx[c] + dtdx * (lu - A.lhu[c - 1]);
+            const T mu = A.lqx[c] + dtdx * (lu - s_lhu[ty][tx - 1]);
             const T hf = F.hf(hL, zL, hC, zC);
             T lq = T(0);
             if (hf > hd && mu != T(0)) {
@@ -222,7 +245,7 @@ __global__ void __launch_bounds__(BX *BY) adj_step_kernel(const AdjArgs<T> A)
             A.lqx_out[c + 1] = T(0);
         } else {
             const T hR = a.h[c + 1], zR = a.z[c + 1], nR = a.n[c + 1];
-            const T mu = A.lqx[c + 1] + dtdx * (A.lhu[c + 1] - lu);
+            const T mu = A.lqx[c + 1] + dtdx * (s_lhu[ty][tx + 1] - lu);
             const T hf = F.hf(hC, zC, hR, zR);
             if (hf > hd && mu != T(0)) {
                 FaceLin<T> d = face_lin<T>(a.qx[c + 1], hC, zC, nC, hR, zR, nR, hf, g, dt, dx);
@@ -239,7 +262,7 @@ __global__ void __launch_bounds__(BX *BY) adj_step_kernel(const AdjArgs<T> A)
             A.lqy_out[c] = T(0);
         } else {
             const T hL = a.h[c - P], zL = a.z[c - P], nL = a.n[c - P];
-            const T mu = A.lqy[c] + dtdx * (lu - A.lhu[c - P]);
+            const T mu = A.lqy[c] + dtdx * (lu - s_lhu[ty - 1][tx]);
             const T hf = F.hf(hL, zL, hC, zC);
             T lq = T(0);
             if (hf > hd && mu != T(0)) {
@@ -259,7 +282,7 @@ __global__ void __launch_bounds__(BX *BY) adj_step_kernel(const AdjArgs<T> A)
             A.lqy_out[c + P] = T(0);
         } else {
             const T hR = a.h[c + P], zR = a.z[c + P], nR = a.n[c + P];
-            const T mu = A.lqy[c + P] + dtdx * (A.lhu[c + P] - lu);
+            const T mu = A.lqy[c + P] + dtdx * (s_lhu[ty + 1][tx] - lu);
             const T hf = F.hf(hC, zC, hR, zR);
             if (hf > hd && mu != T(0)) {
                 FaceLin<T> d = face_lin<T>(a.qy[c + P], hC, zC, nC, hR, zR, nR, hf, g, dt, dx);
@@ -343,17 +366,6 @@ __global__ void adj_inflow_kernel(const AdjArgs<T> A)
 }
 
 template <typename T>
-__global__ void add_seed_kernel(Geom G, T *lh, const int64_t *cells, int ng, const double *seed)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int k = 0; k < ng; k++) {       // one thread: repeated gauge cells add up in order
-        const int64_t c = cells[k];
-        const size_t idx = (size_t)(c / G.nx) * G.pitch + (size_t)(c % G.nx);
-        lh[idx] = lh[idx] + T(seed[k]);
-    }
-}
-
-template <typename T>
 __global__ void gn_out_kernel(Geom G, const double *gn, T *dst)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
@@ -380,24 +392,12 @@ cudaError_t launch_adjoint_step(const AdjArgs<T> &A, cudaStream_t st)
 {
     dim3 block(BX, BY);
     dim3 grid((A.fwd.geo.nx + BX - 1) / BX, (A.fwd.geo.ny + BY - 1) / BY);
-    adj_mask_kernel<T><<<grid, block, 0, st>>>(A);
     adj_step_kernel<T><<<grid, block, 0, st>>>(A);
     if (A.fwd.n_inflow_sec > 0) adj_inflow_kernel<T><<<A.fwd.n_inflow_sec, 256, 0, st>>>(A);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_add_seed(const Geom &g, T *lh, const int64_t *cells, int G, const double *seed, cudaStream_t st)
-{
-    if (G <= 0) return cudaSuccess;
-    add_seed_kernel<T><<<1, 32, 0, st>>>(g, lh, cells, G, seed);
-    return cudaGetLastError();
-}
-
 template cudaError_t launch_adjoint_step<float>(const AdjArgs<float> &, cudaStream_t);
 template cudaError_t launch_adjoint_step<double>(const AdjArgs<double> &, cudaStream_t);
-template cudaError_t launch_add_seed<float>(const Geom &, float *, const int64_t *, int, const double *, cudaStream_t);
-template cudaError_t launch_add_seed<double>(const Geom &, double *, const int64_t *, int, const double *,
-                                             cudaStream_t);
 
 }  // namespace flood

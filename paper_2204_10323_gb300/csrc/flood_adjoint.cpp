@@ -180,7 +180,6 @@ flood_status reverse_step_t(Sweep &S)
     flood_status st = ensure_epoch(S, e);
     if (st) return st;
     const int c = S.cur_l, o = 1 - S.cur_l;
-    CKA(launch_add_seed<T>(h->geo, (T *)S.lh[c], S.cells, S.G, S.seed + (size_t)k * S.G, h->stream));
     AdjArgs<T> A;
     std::memset(&A, 0, sizeof(A));
     StepArgs<T> &a = A.fwd;
@@ -212,6 +211,9 @@ flood_status reverse_step_t(Sweep &S)
     A.secs = h->secs_dev;
     A.sec_cells = h->sec_cells;
     A.inflow_W = h->inflow_W;
+    A.gauge_cells = S.cells;
+    A.n_gauges = S.G;
+    A.seed = S.seed + (size_t)k * S.G;      // dL/dh after step k, added to lambda_{k+1}
     CKA(launch_adjoint_step<T>(A, h->stream));
     S.cur_l = o;
     return FLOOD_OK;

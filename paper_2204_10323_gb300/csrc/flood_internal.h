@@ -142,15 +142,15 @@ struct AdjArgs {
     const InflowSec *secs;        // inflow sections (for the Eq. 6 derivative)
     const int64_t *sec_cells;
     const double *inflow_W;       // E x n_sec levels of this epoch
+    const int64_t *gauge_cells;   // flat j*nx+i of the loss's gauges
+    int n_gauges;
+    const double *seed;           // dL/d(depth at gauge g after this step), n_gauges values (device)
 };
 template <typename T>
 cudaError_t launch_adjoint_step(const AdjArgs<T> &a, cudaStream_t st);
 // dst (pitched, precision T) = gn (pitched doubles).
 template <typename T>
 cudaError_t launch_gn_out(const Geom &g, const double *gn, T *dst, cudaStream_t st);
-// lh[gauge g] += seed[g] for g < G (seed: device doubles).
-template <typename T>
-cudaError_t launch_add_seed(const Geom &g, T *lh, const int64_t *cells, int G, const double *seed, cudaStream_t st);
 
 // Gather h at gauge cells into out[0..G).
 template <typename T>
