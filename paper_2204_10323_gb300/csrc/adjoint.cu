@@ -141,33 +141,6 @@ __device__ __forceinline__ T bface(const StepArgs<T> &a, const Fwd<T> &F, int si
     return -inward * F.outflow(h, T(a.bc.sqrtS[off + k]), n, G.bc_form);
 }
 
-// Adjoint of cell (i, j)'s unclipped depth: lambda_h'(c) plus the loss's
-// seeds at gauge cells, where the recomputed forward depth was not clipped.
-template <typename T>
-__device__ __forceinline__ T unclipped_adjoint(const AdjArgs<T> &A, const Fwd<T> &F, const int i, const int j)
-{
-    const StepArgs<T> &a = A.fwd;
-    const Geom &G = a.geo;
-    const size_t P = (size_t)G.pitch, c = (size_t)j * P + i;
-    const T hC = a.h[c], zC = a.z[c], nC = a.n[c];
-    T qW, qE, qS, qN;
-    if (i == 0) qW = bface(a, F, 0, j, hC, nC);
-    else qW = F.face(a.qx[c], a.h[c - 1], a.z[c - 1], a.n[c - 1], hC, zC, nC);
-    if (i == G.nx - 1) qE = bface(a, F, 1, j, hC, nC);
-    else qE = F.face(a.qx[c + 1], hC, zC, nC, a.h[c + 1], a.z[c + 1], a.n[c + 1]);
-    if (j == 0) qS = bface(a, F, 2, i, hC, nC);
-    else qS = F.face(a.qy[c], a.h[c - P], a.z[c - P], a.n[c - P], hC, zC, nC);
-    if (j == G.ny - 1) qN = bface(a, F, 3, i, hC, nC);
-    else qN = F.face(a.qy[c + P], hC, zC, nC, a.h[c + P], a.z[c + P], a.n[c + P]);
-    const T hu = F.update(hC, qW, qE, qS, qN);
-    if (hu < T(0)) return T(0);
-    T lam = A.lh[c];
-    const int64_t flat = (int64_t)j * G.nx + i;
-    for (int g = 0; g < A.n_gauges; g++)          // repeated gauges add up in order
-        if (A.gauge_cells[g] == flat) lam = lam + T(A.seed[g]);
-    return lam;
-}
-
 // Adjoint of an outflow boundary face: contributions to lambda_h(c) and dL/dn(c).
 template <typename T>
 __device__ __forceinline__ void outflow_adj(const StepArgs<T> &a, const Fwd<T> &F, int side, int k, T h, T n,
@@ -184,115 +157,171 @@ __device__ __forceinline__ void outflow_adj(const StepArgs<T> &a, const Fwd<T> &
     gn += (double)(-nu * q / n);
 }
 
-// One launch per reverse step: the block first recomputes the clip mask (and
-// adds the gauge seeds) for its tile plus a one-cell halo into shared memory,
-// then every cell gathers its own adjoint and that of its west and south faces.
+// One launch per reverse step, face-centric within a BX x BY tile:
+//  A. every face around the tile and its one-cell halo gets its new value q'
+//     (the forward arithmetic) in shared memory;
+//  B. the tile and halo cells get the adjoint of their unclipped depth
+//     (lambda_h' plus the gauge seeds, zero where the depth was clipped);
+//  C. every face touching a tile cell gets mu and its derivatives once,
+//     leaving its contributions to the two cells and the adjoint of its old q;
+//  D. every tile cell gathers the contributions of its four faces.
 template <typename T>
 __global__ void __launch_bounds__(BX *BY) adj_step_kernel(const AdjArgs<T> A)
 {
-    __shared__ T s_lhu[BY + 2][BX + 2];
+    __shared__ T sX[BY + 2][BX + 3];          // q' of x-faces: columns I0-1 .. I0+BX+1, rows J0-1 .. J0+BY
+    __shared__ T sY[BY + 3][BX + 2];          // q' of y-faces: rows J0-1 .. J0+BY+1, columns I0-1 .. I0+BX
+    __shared__ T sL[BY + 2][BX + 2];          // lambda of the unclipped depth, cells I0-1.., J0-1..
+    __shared__ T cXl[BY][BX + 1], cXr[BY][BX + 1], cXn[BY][BX + 1];   // x-face contributions
+    __shared__ T cYl[BY + 1][BX], cYr[BY + 1][BX], cYn[BY + 1][BX];   // y-face contributions
     const StepArgs<T> &a = A.fwd;
     const Geom &G = a.geo;
+    const int nx = G.nx, ny = G.ny;
+    const size_t P = (size_t)G.pitch;
     const double dtd = a.ctrl->dt;
     const Fwd<T> F(G, dtd);
-    {
-        const int tid = threadIdx.y * BX + threadIdx.x;
-        const int i0 = blockIdx.x * BX - 1, j0 = blockIdx.y * BY - 1;
-        for (int t = tid; t < (BX + 2) * (BY + 2); t += BX * BY) {
-            const int li = t % (BX + 2), lj = t / (BX + 2);
-            const int ii = i0 + li, jj = j0 + lj;
-            T v = T(0);
-            if (ii >= 0 && ii < G.nx && jj >= 0 && jj < G.ny) v = unclipped_adjoint(A, F, ii, jj);
-            s_lhu[lj][li] = v;
+    const T dt = T(dtd), dx = T(G.dx), g = T(G.g), hd = T(G.h_dry), dtdx = dt / dx;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    const int I0 = blockIdx.x * BX, J0 = blockIdx.y * BY;
+
+    // A. new face values (zero outside the domain)
+    for (int t = tid; t < (BY + 2) * (BX + 3); t += BX * BY) {
+        const int lj = t / (BX + 3), li = t % (BX + 3);
+        const int j = J0 - 1 + lj, fi = I0 - 1 + li;
+        T v = T(0);
+        if (j >= 0 && j < ny && fi >= 0 && fi <= nx) {
+            const size_t r = (size_t)j * P;
+            if (fi == 0) v = bface(a, F, 0, j, a.h[r], a.n[r]);
+            else if (fi == nx) v = bface(a, F, 1, j, a.h[r + nx - 1], a.n[r + nx - 1]);
+            else v = F.face(a.qx[r + fi], a.h[r + fi - 1], a.z[r + fi - 1], a.n[r + fi - 1], a.h[r + fi],
+                            a.z[r + fi], a.n[r + fi]);
         }
+        sX[lj][li] = v;
+    }
+    for (int t = tid; t < (BY + 3) * (BX + 2); t += BX * BY) {
+        const int lj = t / (BX + 2), li = t % (BX + 2);
+        const int fj = J0 - 1 + lj, i = I0 - 1 + li;
+        T v = T(0);
+        if (i >= 0 && i < nx && fj >= 0 && fj <= ny) {
+            if (fj == 0) v = bface(a, F, 2, i, a.h[i], a.n[i]);
+            else if (fj == ny) v = bface(a, F, 3, i, a.h[(size_t)(ny - 1) * P + i], a.n[(size_t)(ny - 1) * P + i]);
+            else {
+                const size_t c = (size_t)fj * P + i;
+                v = F.face(a.qy[c], a.h[c - P], a.z[c - P], a.n[c - P], a.h[c], a.z[c], a.n[c]);
+            }
+        }
+        sY[lj][li] = v;
     }
     __syncthreads();
-    const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    if (i >= G.nx || j >= G.ny) return;
-    const T dt = T(dtd), dx = T(G.dx), g = T(G.g), hd = T(G.h_dry), dtdx = dt / dx;
-    const size_t P = (size_t)G.pitch, c = (size_t)j * P + i;
-    const T hC = a.h[c], zC = a.z[c], nC = a.n[c];
-    const T lu = s_lhu[ty][tx];
-    if (i == 0 || j == 0 || i == G.nx - 1 || j == G.ny - 1) A.lhu[c] = lu;   // read by the inflow pass
-    T lh = lu;
-    double gn = 0.0;
-    // west face (this cell is R)
-    {
-        if (i == 0) {
-            const T mu = A.lqx[c] + dtdx * lu;
-            outflow_adj(a, F, 0, j, hC, nC, mu, lh, gn);
-            A.lqx_out[c] = T(0);
-        } else {
-            const T hL = a.h[c - 1], zL = a.z[c - 1], nL = a.n[c - 1];
-            const T mu = A.lqx[c] + dtdx * (lu - s_lhu[ty][tx - 1]);
-            const T hf = F.hf(hL, zL, hC, zC);
-            T lq = T(0);
-            if (hf > hd && mu != T(0)) {
-                FaceLin<T> d = face_lin<T>(a.qx[c], hL, zL, nL, hC, zC, nC, hf, g, dt, dx);
-                lh += mu * d.dhR;
-                gn += (double)(mu * d.dn);
-                lq = mu * d.dq;
-            }
-            A.lqx_out[c] = lq;
-        }
-    }
-    // east face (this cell is L)
-    {
-        if (i == G.nx - 1) {
-            const T mu = A.lqx[c + 1] - dtdx * lu;
-            outflow_adj(a, F, 1, j, hC, nC, mu, lh, gn);
-            A.lqx_out[c + 1] = T(0);
-        } else {
-            const T hR = a.h[c + 1], zR = a.z[c + 1], nR = a.n[c + 1];
-            const T mu = A.lqx[c + 1] + dtdx * (s_lhu[ty][tx + 1] - lu);
-            const T hf = F.hf(hC, zC, hR, zR);
-            if (hf > hd && mu != T(0)) {
-                FaceLin<T> d = face_lin<T>(a.qx[c + 1], hC, zC, nC, hR, zR, nR, hf, g, dt, dx);
-                lh += mu * d.dhL;
-                gn += (double)(mu * d.dn);
+    // B. adjoint of the unclipped depth (gauge seeds included)
+    for (int t = tid; t < (BY + 2) * (BX + 2); t += BX * BY) {
+        const int lj = t / (BX + 2), li = t % (BX + 2);
+        const int j = J0 - 1 + lj, i = I0 - 1 + li;
+        T v = T(0);
+        if (i >= 0 && i < nx && j >= 0 && j < ny) {
+            const size_t c = (size_t)j * P + i;
+            const T hu = F.update(a.h[c], sX[lj][li], sX[lj][li + 1], sY[lj][li], sY[lj + 1][li]);
+            if (!(hu < T(0))) {
+                v = A.lh[c];
+                const int64_t flat = (int64_t)j * nx + i;
+                for (int gk = 0; gk < A.n_gauges; gk++)   // repeated gauges add up in order
+                    if (A.gauge_cells[gk] == flat) v = v + T(A.seed[gk]);
             }
         }
+        sL[lj][li] = v;
     }
-    // south face (this cell is R)
-    {
-        if (j == 0) {
-            const T mu = A.lqy[c] + dtdx * lu;
-            outflow_adj(a, F, 2, i, hC, nC, mu, lh, gn);
-            A.lqy_out[c] = T(0);
-        } else {
-            const T hL = a.h[c - P], zL = a.z[c - P], nL = a.n[c - P];
-            const T mu = A.lqy[c] + dtdx * (lu - s_lhu[ty - 1][tx]);
-            const T hf = F.hf(hL, zL, hC, zC);
-            T lq = T(0);
-            if (hf > hd && mu != T(0)) {
-                FaceLin<T> d = face_lin<T>(a.qy[c], hL, zL, nL, hC, zC, nC, hf, g, dt, dx);
-                lh += mu * d.dhR;
-                gn += (double)(mu * d.dn);
-                lq = mu * d.dq;
+    __syncthreads();
+    // C. each face touching the tile once
+    for (int t = tid; t < BY * (BX + 1); t += BX * BY) {
+        const int lj = t / (BX + 1), li = t % (BX + 1);
+        const int j = J0 + lj, fi = I0 + li;
+        T cl = T(0), cr = T(0), cn = T(0);
+        if (j < ny && fi <= nx) {
+            const size_t r = (size_t)j * P;
+            const T lR = sL[lj + 1][li + 1], lL = sL[lj + 1][li];
+            if (fi == 0) {
+                const T mu = A.lqx[r] + dtdx * lR;
+                double gnv = 0.0;
+                outflow_adj(a, F, 0, j, a.h[r], a.n[r], mu, cr, gnv);
+                cn = T(gnv);
+                A.lqx_out[r] = T(0);
+            } else if (fi == nx) {
+                const T mu = A.lqx[r + nx] - dtdx * lL;
+                double gnv = 0.0;
+                outflow_adj(a, F, 1, j, a.h[r + nx - 1], a.n[r + nx - 1], mu, cl, gnv);
+                cn = T(gnv);
+                A.lqx_out[r + nx] = T(0);
+            } else {
+                const T mu = A.lqx[r + fi] + dtdx * (lR - lL);
+                const T hL = a.h[r + fi - 1], zL = a.z[r + fi - 1], nL = a.n[r + fi - 1];
+                const T hR = a.h[r + fi], zR = a.z[r + fi], nR = a.n[r + fi];
+                const T hf = F.hf(hL, zL, hR, zR);
+                T lq = T(0);
+                if (hf > hd && mu != T(0)) {
+                    FaceLin<T> d = face_lin<T>(a.qx[r + fi], hL, zL, nL, hR, zR, nR, hf, g, dt, dx);
+                    cl = mu * d.dhL;
+                    cr = mu * d.dhR;
+                    cn = mu * d.dn;
+                    lq = mu * d.dq;
+                }
+                if (li < BX) A.lqx_out[r + fi] = lq;        // the tile owns the west faces of its cells
             }
-            A.lqy_out[c] = lq;
         }
+        cXl[lj][li] = cl;
+        cXr[lj][li] = cr;
+        cXn[lj][li] = cn;
     }
-    // north face (this cell is L)
-    {
-        if (j == G.ny - 1) {
-            const T mu = A.lqy[c + P] - dtdx * lu;
-            outflow_adj(a, F, 3, i, hC, nC, mu, lh, gn);
-            A.lqy_out[c + P] = T(0);
-        } else {
-            const T hR = a.h[c + P], zR = a.z[c + P], nR = a.n[c + P];
-            const T mu = A.lqy[c + P] + dtdx * (s_lhu[ty + 1][tx] - lu);
-            const T hf = F.hf(hC, zC, hR, zR);
-            if (hf > hd && mu != T(0)) {
-                FaceLin<T> d = face_lin<T>(a.qy[c + P], hC, zC, nC, hR, zR, nR, hf, g, dt, dx);
-                lh += mu * d.dhL;
-                gn += (double)(mu * d.dn);
+    for (int t = tid; t < (BY + 1) * BX; t += BX * BY) {
+        const int lj = t / BX, li = t % BX;
+        const int fj = J0 + lj, i = I0 + li;
+        T cl = T(0), cr = T(0), cn = T(0);
+        if (i < nx && fj <= ny) {
+            const T lR = sL[lj + 1][li + 1], lL = sL[lj][li + 1];
+            if (fj == 0) {
+                const T mu = A.lqy[i] + dtdx * lR;
+                double gnv = 0.0;
+                outflow_adj(a, F, 2, i, a.h[i], a.n[i], mu, cr, gnv);
+                cn = T(gnv);
+                A.lqy_out[i] = T(0);
+            } else if (fj == ny) {
+                const size_t c = (size_t)(ny - 1) * P + i;
+                const T mu = A.lqy[c + P] - dtdx * lL;
+                double gnv = 0.0;
+                outflow_adj(a, F, 3, i, a.h[c], a.n[c], mu, cl, gnv);
+                cn = T(gnv);
+                A.lqy_out[c + P] = T(0);
+            } else {
+                const size_t c = (size_t)fj * P + i;
+                const T mu = A.lqy[c] + dtdx * (lR - lL);
+                const T hL = a.h[c - P], zL = a.z[c - P], nL = a.n[c - P];
+                const T hR = a.h[c], zR = a.z[c], nR = a.n[c];
+                const T hf = F.hf(hL, zL, hR, zR);
+                T lq = T(0);
+                if (hf > hd && mu != T(0)) {
+                    FaceLin<T> d = face_lin<T>(a.qy[c], hL, zL, nL, hR, zR, nR, hf, g, dt, dx);
+                    cl = mu * d.dhL;
+                    cr = mu * d.dhR;
+                    cn = mu * d.dn;
+                    lq = mu * d.dq;
+                }
+                if (lj < BY) A.lqy_out[c] = lq;             // the tile owns the south faces of its cells
             }
         }
+        cYl[lj][li] = cl;
+        cYr[lj][li] = cr;
+        cYn[lj][li] = cn;
     }
+    __syncthreads();
+    // D. gather per tile cell
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = I0 + tx, j = J0 + ty;
+    if (i >= nx || j >= ny) return;
+    const size_t c = (size_t)j * P + i;
+    const T lu = sL[ty + 1][tx + 1];
+    const T lh = lu + cXr[ty][tx] + cXl[ty][tx + 1] + cYr[ty][tx] + cYl[ty + 1][tx];
+    const double gn = (double)cXn[ty][tx] + (double)cXn[ty][tx + 1] + (double)cYn[ty][tx] + (double)cYn[ty + 1][tx];
     A.lh_out[c] = lh;
     A.gn[c] += gn;
+    if (i == 0 || j == 0 || i == nx - 1 || j == ny - 1) A.lhu[c] = lu;   // read by the inflow pass
 }
 
 // Pass 3: the inflow faces of each section depend on every section cell's n
