@@ -215,6 +215,13 @@ flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const int64_t *gaug
 /* Number of forward steps the last flood_adjoint call recomputed (revolve cost). */
 int64_t flood_adjoint_forward_steps(const flood_handle *h);
 
+/* Profiling of flood_adjoint (off by default): when enabled, the next calls
+ * bracket every reverse step and every forward replay with CUDA events, and
+ * flood_adjoint_times reports their summed device time (ms) and counts. */
+flood_status flood_adjoint_profile(flood_handle *h, int32_t enable);
+flood_status flood_adjoint_times(const flood_handle *h, double *reverse_ms, int64_t *reverse_steps,
+                                 double *forward_ms, int64_t *forward_steps);
+
 /* Release all device memory of the handle (NULL is accepted). */
 flood_status flood_destroy(flood_handle *h);
 

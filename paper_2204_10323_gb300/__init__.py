@@ -87,6 +87,10 @@ def _load():
     L.flood_last_error.argtypes = [H]
     L.flood_last_error.restype = C.c_char_p
     L.flood_version.restype = C.c_char_p
+    L.flood_adjoint_profile.argtypes = [H, i32]
+    L.flood_adjoint_profile.restype = C.c_int
+    L.flood_adjoint_times.argtypes = [H, C.POINTER(dbl), C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64)]
+    L.flood_adjoint_times.restype = C.c_int
     L.flood_volume_noalloc.argtypes = [vp, i32, i32, i64, i32, dbl, vp, vp]
     L.flood_volume_noalloc.restype = C.c_int
     L.flood_ensemble_create.argtypes = [i32, C.POINTER(flood_grid), C.POINTER(vp), C.POINTER(vp),
@@ -303,6 +307,16 @@ class Sim:
 
     def adjoint_forward_steps(self) -> int:
         return int(lib().flood_adjoint_forward_steps(self.h))
+
+    def adjoint_profile(self, enable: bool = True) -> None:
+        _check(lib().flood_adjoint_profile(self.h, int(enable)), self.h)
+
+    def adjoint_times(self) -> dict:
+        """Device time (ms) of the last profiled flood_adjoint call's reverse steps and forward replays."""
+        rm, fm = C.c_double(), C.c_double()
+        rn, fn = C.c_int64(), C.c_int64()
+        _check(lib().flood_adjoint_times(self.h, C.byref(rm), C.byref(rn), C.byref(fm), C.byref(fn)), self.h)
+        return {"reverse_ms": rm.value, "reverse_steps": rn.value, "forward_ms": fm.value, "forward_steps": fn.value}
 
     def close(self):
         if getattr(self, "h", None) is not None:

@@ -88,7 +88,7 @@ template <> struct Fwd<float> {
         return __fmaf_rn(K.dtdx, dv, h);
     }
     __device__ static float rcbrt_(float x) { return rcbrtf(x); }
-    __device__ static float rcp_(float x) { return __frcp_rn(x); }
+    __device__ static float rcp_(float x) { return __fdividef(1.0f, x); }
 };
 
 // Partial derivatives of one wet face's Eq. 3 value.
@@ -157,22 +157,31 @@ __device__ __forceinline__ void outflow_adj(const StepArgs<T> &a, const Fwd<T> &
     gn += (double)(-nu * q / n);
 }
 
-// One launch per reverse step, face-centric within a BX x BY tile:
+// One launch per reverse step, face-centric within a BX x by tile (by = 16
+// rows in FP32, 8 in FP64 to stay inside static shared memory):
+//  0. the tile's cells with a two-cell halo (h, z, n) and the faces around it
+//     (old q) are staged in shared memory;
 //  A. every face around the tile and its one-cell halo gets its new value q'
-//     (the forward arithmetic) in shared memory;
+//     (the forward arithmetic);
 //  B. the tile and halo cells get the adjoint of their unclipped depth
 //     (lambda_h' plus the gauge seeds, zero where the depth was clipped);
 //  C. every face touching a tile cell gets mu and its derivatives once,
 //     leaving its contributions to the two cells and the adjoint of its old q;
 //  D. every tile cell gathers the contributions of its four faces.
+template <typename T> struct TileRows { static constexpr int v = 16; };
+template <> struct TileRows<double> { static constexpr int v = 8; };
+
 template <typename T>
-__global__ void __launch_bounds__(BX *BY) adj_step_kernel(const AdjArgs<T> A)
+__global__ void __launch_bounds__(BX * TileRows<T>::v) adj_step_kernel(const AdjArgs<T> A)
 {
-    __shared__ T sX[BY + 2][BX + 3];          // q' of x-faces: columns I0-1 .. I0+BX+1, rows J0-1 .. J0+BY
-    __shared__ T sY[BY + 3][BX + 2];          // q' of y-faces: rows J0-1 .. J0+BY+1, columns I0-1 .. I0+BX
-    __shared__ T sL[BY + 2][BX + 2];          // lambda of the unclipped depth, cells I0-1.., J0-1..
-    __shared__ T cXl[BY][BX + 1], cXr[BY][BX + 1], cXn[BY][BX + 1];   // x-face contributions
-    __shared__ T cYl[BY + 1][BX], cYr[BY + 1][BX], cYn[BY + 1][BX];   // y-face contributions
+    constexpr int BYT = TileRows<T>::v;
+    constexpr int NT = BX * BYT;
+    __shared__ T sh[BYT + 4][BX + 4], sz[BYT + 4][BX + 4], sn[BYT + 4][BX + 4];   // cells I0-2.., J0-2..
+    __shared__ T sqx[BYT + 2][BX + 3], sX[BYT + 2][BX + 3];   // x-faces: columns I0-1 .., rows J0-1 ..
+    __shared__ T sqy[BYT + 3][BX + 2], sY[BYT + 3][BX + 2];   // y-faces: rows J0-1 .., columns I0-1 ..
+    __shared__ T sL[BYT + 2][BX + 2];                          // cells I0-1 .., J0-1 ..
+    __shared__ T cXl[BYT][BX + 1], cXr[BYT][BX + 1], cXn[BYT][BX + 1];
+    __shared__ T cYl[BYT + 1][BX], cYr[BYT + 1][BX], cYn[BYT + 1][BX];
     const StepArgs<T> &a = A.fwd;
     const Geom &G = a.geo;
     const int nx = G.nx, ny = G.ny;
@@ -181,47 +190,70 @@ __global__ void __launch_bounds__(BX *BY) adj_step_kernel(const AdjArgs<T> A)
     const Fwd<T> F(G, dtd);
     const T dt = T(dtd), dx = T(G.dx), g = T(G.g), hd = T(G.h_dry), dtdx = dt / dx;
     const int tid = threadIdx.y * BX + threadIdx.x;
-    const int I0 = blockIdx.x * BX, J0 = blockIdx.y * BY;
+    const int I0 = blockIdx.x * BX, J0 = blockIdx.y * BYT;
 
-    // A. new face values (zero outside the domain)
-    for (int t = tid; t < (BY + 2) * (BX + 3); t += BX * BY) {
+    // 0. stage cells and old face fluxes (zeros outside the domain)
+    for (int t = tid; t < (BYT + 4) * (BX + 4); t += NT) {
+        const int lj = t / (BX + 4), li = t % (BX + 4);
+        const int j = J0 - 2 + lj, i = I0 - 2 + li;
+        T hv = T(0), zv = T(0), nv = T(0);
+        if (i >= 0 && i < nx && j >= 0 && j < ny) {
+            const size_t c = (size_t)j * P + i;
+            hv = a.h[c];
+            zv = a.z[c];
+            nv = a.n[c];
+        }
+        sh[lj][li] = hv;
+        sz[lj][li] = zv;
+        sn[lj][li] = nv;
+    }
+    for (int t = tid; t < (BYT + 2) * (BX + 3); t += NT) {
+        const int lj = t / (BX + 3), li = t % (BX + 3);
+        const int j = J0 - 1 + lj, fi = I0 - 1 + li;
+        sqx[lj][li] = (j >= 0 && j < ny && fi >= 0 && fi <= nx) ? a.qx[(size_t)j * P + fi] : T(0);
+    }
+    for (int t = tid; t < (BYT + 3) * (BX + 2); t += NT) {
+        const int lj = t / (BX + 2), li = t % (BX + 2);
+        const int fj = J0 - 1 + lj, i = I0 - 1 + li;
+        sqy[lj][li] = (i >= 0 && i < nx && fj >= 0 && fj <= ny) ? a.qy[(size_t)fj * P + i] : T(0);
+    }
+    __syncthreads();
+    // A. new face values.  x-face (lj, li) lies between cells (lj+1, li) and (lj+1, li+1) of the staging.
+    for (int t = tid; t < (BYT + 2) * (BX + 3); t += NT) {
         const int lj = t / (BX + 3), li = t % (BX + 3);
         const int j = J0 - 1 + lj, fi = I0 - 1 + li;
         T v = T(0);
         if (j >= 0 && j < ny && fi >= 0 && fi <= nx) {
-            const size_t r = (size_t)j * P;
-            if (fi == 0) v = bface(a, F, 0, j, a.h[r], a.n[r]);
-            else if (fi == nx) v = bface(a, F, 1, j, a.h[r + nx - 1], a.n[r + nx - 1]);
-            else v = F.face(a.qx[r + fi], a.h[r + fi - 1], a.z[r + fi - 1], a.n[r + fi - 1], a.h[r + fi],
-                            a.z[r + fi], a.n[r + fi]);
+            const int sj = lj + 1, sl = li, sr = li + 1;
+            if (fi == 0) v = bface(a, F, 0, j, sh[sj][sr], sn[sj][sr]);
+            else if (fi == nx) v = bface(a, F, 1, j, sh[sj][sl], sn[sj][sl]);
+            else v = F.face(sqx[lj][li], sh[sj][sl], sz[sj][sl], sn[sj][sl], sh[sj][sr], sz[sj][sr], sn[sj][sr]);
         }
         sX[lj][li] = v;
     }
-    for (int t = tid; t < (BY + 3) * (BX + 2); t += BX * BY) {
+    // y-face (lj, li) lies between cells (lj, li+1) and (lj+1, li+1) of the staging.
+    for (int t = tid; t < (BYT + 3) * (BX + 2); t += NT) {
         const int lj = t / (BX + 2), li = t % (BX + 2);
         const int fj = J0 - 1 + lj, i = I0 - 1 + li;
         T v = T(0);
         if (i >= 0 && i < nx && fj >= 0 && fj <= ny) {
-            if (fj == 0) v = bface(a, F, 2, i, a.h[i], a.n[i]);
-            else if (fj == ny) v = bface(a, F, 3, i, a.h[(size_t)(ny - 1) * P + i], a.n[(size_t)(ny - 1) * P + i]);
-            else {
-                const size_t c = (size_t)fj * P + i;
-                v = F.face(a.qy[c], a.h[c - P], a.z[c - P], a.n[c - P], a.h[c], a.z[c], a.n[c]);
-            }
+            const int sc = li + 1, sb = lj, st = lj + 1;
+            if (fj == 0) v = bface(a, F, 2, i, sh[st][sc], sn[st][sc]);
+            else if (fj == ny) v = bface(a, F, 3, i, sh[sb][sc], sn[sb][sc]);
+            else v = F.face(sqy[lj][li], sh[sb][sc], sz[sb][sc], sn[sb][sc], sh[st][sc], sz[st][sc], sn[st][sc]);
         }
         sY[lj][li] = v;
     }
     __syncthreads();
     // B. adjoint of the unclipped depth (gauge seeds included)
-    for (int t = tid; t < (BY + 2) * (BX + 2); t += BX * BY) {
+    for (int t = tid; t < (BYT + 2) * (BX + 2); t += NT) {
         const int lj = t / (BX + 2), li = t % (BX + 2);
         const int j = J0 - 1 + lj, i = I0 - 1 + li;
         T v = T(0);
         if (i >= 0 && i < nx && j >= 0 && j < ny) {
-            const size_t c = (size_t)j * P + i;
-            const T hu = F.update(a.h[c], sX[lj][li], sX[lj][li + 1], sY[lj][li], sY[lj + 1][li]);
+            const T hu = F.update(sh[lj + 1][li + 1], sX[lj][li], sX[lj][li + 1], sY[lj][li], sY[lj + 1][li]);
             if (!(hu < T(0))) {
-                v = A.lh[c];
+                v = A.lh[(size_t)j * P + i];
                 const int64_t flat = (int64_t)j * nx + i;
                 for (int gk = 0; gk < A.n_gauges; gk++)   // repeated gauges add up in order
                     if (A.gauge_cells[gk] == flat) v = v + T(A.seed[gk]);
@@ -230,34 +262,35 @@ __global__ void __launch_bounds__(BX *BY) adj_step_kernel(const AdjArgs<T> A)
         sL[lj][li] = v;
     }
     __syncthreads();
-    // C. each face touching the tile once
-    for (int t = tid; t < BY * (BX + 1); t += BX * BY) {
+    // C. each face touching the tile once.  x-face column li = fi - I0, row lj = j - J0.
+    for (int t = tid; t < BYT * (BX + 1); t += NT) {
         const int lj = t / (BX + 1), li = t % (BX + 1);
         const int j = J0 + lj, fi = I0 + li;
         T cl = T(0), cr = T(0), cn = T(0);
         if (j < ny && fi <= nx) {
             const size_t r = (size_t)j * P;
             const T lR = sL[lj + 1][li + 1], lL = sL[lj + 1][li];
+            const int sj = lj + 2, sl = li + 1, sr = li + 2;     // staging coordinates of L and R
             if (fi == 0) {
                 const T mu = A.lqx[r] + dtdx * lR;
                 double gnv = 0.0;
-                outflow_adj(a, F, 0, j, a.h[r], a.n[r], mu, cr, gnv);
+                outflow_adj(a, F, 0, j, sh[sj][sr], sn[sj][sr], mu, cr, gnv);
                 cn = T(gnv);
                 A.lqx_out[r] = T(0);
             } else if (fi == nx) {
                 const T mu = A.lqx[r + nx] - dtdx * lL;
                 double gnv = 0.0;
-                outflow_adj(a, F, 1, j, a.h[r + nx - 1], a.n[r + nx - 1], mu, cl, gnv);
+                outflow_adj(a, F, 1, j, sh[sj][sl], sn[sj][sl], mu, cl, gnv);
                 cn = T(gnv);
                 A.lqx_out[r + nx] = T(0);
             } else {
                 const T mu = A.lqx[r + fi] + dtdx * (lR - lL);
-                const T hL = a.h[r + fi - 1], zL = a.z[r + fi - 1], nL = a.n[r + fi - 1];
-                const T hR = a.h[r + fi], zR = a.z[r + fi], nR = a.n[r + fi];
+                const T hL = sh[sj][sl], zL = sz[sj][sl], nL = sn[sj][sl];
+                const T hR = sh[sj][sr], zR = sz[sj][sr], nR = sn[sj][sr];
                 const T hf = F.hf(hL, zL, hR, zR);
                 T lq = T(0);
                 if (hf > hd && mu != T(0)) {
-                    FaceLin<T> d = face_lin<T>(a.qx[r + fi], hL, zL, nL, hR, zR, nR, hf, g, dt, dx);
+                    FaceLin<T> d = face_lin<T>(sqx[lj + 1][li + 1], hL, zL, nL, hR, zR, nR, hf, g, dt, dx);
                     cl = mu * d.dhL;
                     cr = mu * d.dhR;
                     cn = mu * d.dn;
@@ -270,40 +303,42 @@ __global__ void __launch_bounds__(BX *BY) adj_step_kernel(const AdjArgs<T> A)
         cXr[lj][li] = cr;
         cXn[lj][li] = cn;
     }
-    for (int t = tid; t < (BY + 1) * BX; t += BX * BY) {
+    // y-face row lj = fj - J0, column li = i - I0.
+    for (int t = tid; t < (BYT + 1) * BX; t += NT) {
         const int lj = t / BX, li = t % BX;
         const int fj = J0 + lj, i = I0 + li;
         T cl = T(0), cr = T(0), cn = T(0);
         if (i < nx && fj <= ny) {
             const T lR = sL[lj + 1][li + 1], lL = sL[lj][li + 1];
+            const int sc = li + 2, sb = lj + 1, st = lj + 2;     // staging coordinates of L (below) and R
             if (fj == 0) {
                 const T mu = A.lqy[i] + dtdx * lR;
                 double gnv = 0.0;
-                outflow_adj(a, F, 2, i, a.h[i], a.n[i], mu, cr, gnv);
+                outflow_adj(a, F, 2, i, sh[st][sc], sn[st][sc], mu, cr, gnv);
                 cn = T(gnv);
                 A.lqy_out[i] = T(0);
             } else if (fj == ny) {
                 const size_t c = (size_t)(ny - 1) * P + i;
                 const T mu = A.lqy[c + P] - dtdx * lL;
                 double gnv = 0.0;
-                outflow_adj(a, F, 3, i, a.h[c], a.n[c], mu, cl, gnv);
+                outflow_adj(a, F, 3, i, sh[sb][sc], sn[sb][sc], mu, cl, gnv);
                 cn = T(gnv);
                 A.lqy_out[c + P] = T(0);
             } else {
                 const size_t c = (size_t)fj * P + i;
                 const T mu = A.lqy[c] + dtdx * (lR - lL);
-                const T hL = a.h[c - P], zL = a.z[c - P], nL = a.n[c - P];
-                const T hR = a.h[c], zR = a.z[c], nR = a.n[c];
+                const T hL = sh[sb][sc], zL = sz[sb][sc], nL = sn[sb][sc];
+                const T hR = sh[st][sc], zR = sz[st][sc], nR = sn[st][sc];
                 const T hf = F.hf(hL, zL, hR, zR);
                 T lq = T(0);
                 if (hf > hd && mu != T(0)) {
-                    FaceLin<T> d = face_lin<T>(a.qy[c], hL, zL, nL, hR, zR, nR, hf, g, dt, dx);
+                    FaceLin<T> d = face_lin<T>(sqy[lj + 1][li + 1], hL, zL, nL, hR, zR, nR, hf, g, dt, dx);
                     cl = mu * d.dhL;
                     cr = mu * d.dhR;
                     cn = mu * d.dn;
                     lq = mu * d.dq;
                 }
-                if (lj < BY) A.lqy_out[c] = lq;             // the tile owns the south faces of its cells
+                if (lj < BYT) A.lqy_out[c] = lq;            // the tile owns the south faces of its cells
             }
         }
         cYl[lj][li] = cl;
@@ -419,8 +454,9 @@ template cudaError_t launch_gn_out<double>(const Geom &, const double *, double 
 template <typename T>
 cudaError_t launch_adjoint_step(const AdjArgs<T> &A, cudaStream_t st)
 {
-    dim3 block(BX, BY);
-    dim3 grid((A.fwd.geo.nx + BX - 1) / BX, (A.fwd.geo.ny + BY - 1) / BY);
+    constexpr int BYT = TileRows<T>::v;
+    dim3 block(BX, BYT);
+    dim3 grid((A.fwd.geo.nx + BX - 1) / BX, (A.fwd.geo.ny + BYT - 1) / BYT);
     adj_step_kernel<T><<<grid, block, 0, st>>>(A);
     if (A.fwd.n_inflow_sec > 0) adj_inflow_kernel<T><<<A.fwd.n_inflow_sec, 256, 0, st>>>(A);
     return cudaGetLastError();

@@ -68,6 +68,8 @@ struct Planes {
 
 struct Sweep {
     flood_handle *h = nullptr;
+    bool profile = false;            // time every reverse step and forward replay with events
+    std::vector<cudaEvent_t> ev_rev, ev_fwd;   // start/end pairs
     int64_t g0 = 0, N = 0;           // first global step, steps to reverse
     int E = 16;
     size_t plane = 0, plane_y = 0;
@@ -107,6 +109,33 @@ Planes working(flood_handle *h)
     return p;
 }
 
+// Run fn between two events recorded on the handle's stream (profiling only).
+template <typename Fn>
+flood_status timed(Sweep &S, std::vector<cudaEvent_t> &evs, Fn fn)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+        return fail(S.h, FLOOD_ERR_CUDA, "event create");
+    evs.push_back(a);
+    evs.push_back(b);
+    cudaEventRecord(a, S.h->stream);
+    flood_status st = fn();
+    cudaEventRecord(b, S.h->stream);
+    return st;
+}
+
+double sum_pairs(std::vector<cudaEvent_t> &evs)
+{
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < evs.size(); k += 2) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, evs[k], evs[k + 1]) == cudaSuccess) total += ms;
+    }
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    evs.clear();
+    return total;
+}
+
 // Make the inflow buffers and dt of epoch e current (logging it the first time).
 flood_status ensure_epoch(Sweep &S, int64_t e)
 {
@@ -143,7 +172,8 @@ flood_status forward_step(Sweep &S)
     if (s == 0 && !S.logged[e - S.e0]) S.loaded = -1;
     flood_status st = ensure_epoch(S, e);
     if (st) return st;
-    st = launch_steps(h, s, 1, s == S.E - 1 ? 1 : 0, nullptr, 0, nullptr);
+    if (S.profile) st = timed(S, S.ev_fwd, [&] { return launch_steps(h, s, 1, s == S.E - 1 ? 1 : 0, nullptr, 0, nullptr); });
+    else st = launch_steps(h, s, 1, s == S.E - 1 ? 1 : 0, nullptr, 0, nullptr);
     if (st) return st;
     S.work_step += 1;
     S.fwd_steps += 1;
@@ -214,7 +244,15 @@ flood_status reverse_step_t(Sweep &S)
     A.gauge_cells = S.cells;
     A.n_gauges = S.G;
     A.seed = S.seed + (size_t)k * S.G;      // dL/dh after step k, added to lambda_{k+1}
-    CKA(launch_adjoint_step<T>(A, h->stream));
+    if (S.profile) {
+        flood_status ts = timed(S, S.ev_rev, [&] {
+            cudaError_t e = launch_adjoint_step<T>(A, h->stream);
+            return e == cudaSuccess ? FLOOD_OK : cuda_fail(h, e, "adjoint step");
+        });
+        if (ts) return ts;
+    } else {
+        CKA(launch_adjoint_step<T>(A, h->stream));
+    }
     S.cur_l = o;
     return FLOOD_OK;
 }
@@ -270,6 +308,25 @@ flood_status reverse_range(Sweep &S, int64_t a, int64_t b, int sa)
 
 extern "C" int64_t flood_adjoint_forward_steps(const flood_handle *h) { return h ? h->adj_forward_steps : 0; }
 
+extern "C" flood_status flood_adjoint_profile(flood_handle *h, int32_t enable)
+{
+    if (!h) return fail(nullptr, FLOOD_ERR_ARG, "handle is NULL");
+    h->adj_profile = enable ? 1 : 0;
+    return FLOOD_OK;
+}
+
+extern "C" flood_status flood_adjoint_times(const flood_handle *h, double *reverse_ms, int64_t *reverse_steps,
+                                            double *forward_ms, int64_t *forward_steps)
+{
+    if (!h || !reverse_ms || !reverse_steps || !forward_ms || !forward_steps)
+        return fail(nullptr, FLOOD_ERR_ARG, "NULL argument");
+    *reverse_ms = h->adj_prof_rev_ms;
+    *reverse_steps = h->adj_prof_rev_steps;
+    *forward_ms = h->adj_prof_fwd_ms;
+    *forward_steps = h->adj_prof_fwd_steps;
+    return FLOOD_OK;
+}
+
 extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const int64_t *gauge_cells,
                                       int32_t n_gauges, const double *dLdh, int32_t n_checkpoints,
                                       void *dLdn_out, void *dLdh0_out, int32_t out_on_device)
@@ -285,6 +342,7 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     const size_t P = (size_t)h->geo.pitch;
     Sweep S;
     S.h = h;
+    S.profile = h->adj_profile != 0;
     S.g0 = h->step;
     S.N = n_steps;
     S.E = h->geo.epoch_steps;
@@ -394,6 +452,13 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
         if (st) return finish(st);
     }
     h->adj_forward_steps = S.fwd_steps;
+    if (S.profile) {
+        CKF(cudaStreamSynchronize(h->stream));
+        h->adj_prof_rev_steps = (int64_t)S.ev_rev.size() / 2;
+        h->adj_prof_fwd_steps = (int64_t)S.ev_fwd.size() / 2;
+        h->adj_prof_rev_ms = sum_pairs(S.ev_rev);
+        h->adj_prof_fwd_ms = sum_pairs(S.ev_fwd);
+    }
     // outputs
     {
         flood_status st = FLOOD_OK;

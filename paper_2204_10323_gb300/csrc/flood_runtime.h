@@ -60,6 +60,9 @@ struct flood_handle {
 
     flood_adjoint_state *adj = nullptr;
     int64_t adj_forward_steps = 0;
+    int adj_profile = 0;                      // flood_adjoint_profile
+    double adj_prof_rev_ms = 0.0, adj_prof_fwd_ms = 0.0;
+    int64_t adj_prof_rev_steps = 0, adj_prof_fwd_steps = 0;
 };
 
 namespace flood {
