@@ -175,7 +175,8 @@ def run_gpu(args):
     ncell = prob.nx * prob.ny
     kernel = {"rows": F.KERNEL_ROWS, "tiled": F.KERNEL_TILED, "reference": F.KERNEL_REFERENCE,
               "stream": F.KERNEL_STREAM}[args.kernel]
-    sim = F.Sim(prob, precision=F.F32, kernel=kernel, steps_per_launch=args.k, use_graph=args.graph)
+    tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else (0, 0)
+    sim = F.Sim(prob, precision=F.F32, kernel=kernel, steps_per_launch=args.k, tile=tile, use_graph=args.graph)
     E = prob.opts.epoch_steps
     h0, qx0, qy0 = prob.initial_state(np.float32)
     stream = torch.cuda.current_stream()
@@ -372,6 +373,7 @@ def main():
     ap.add_argument("--kernel", default="stream", choices=["stream", "rows", "tiled", "reference"])
     ap.add_argument("--k", type=int, default=0, help="steps per launch (tiled kernel)")
     ap.add_argument("--graph", action="store_true")
+    ap.add_argument("--tile", default="", help="stream kernel launch shape: warps,rows")
     ap.add_argument("--traffic-bytes", type=float, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
