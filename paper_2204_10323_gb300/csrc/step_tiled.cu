@@ -1,23 +1,25 @@
 // step_tiled.cu -- FP32 temporal blocking: K <= 4 time steps per launch.
 //
-// Persistent, time-skewed row streaming.  Each warp owns one output strip of
-// 120 columns and one chunk of rows; it stages 128 columns (4 halo columns on
-// each side, held by lanes 0 and 31) row by row through shared memory with
-// bulk copies (cp.async.bulk + mbarrier), and advances the rows through K
-// time levels in a pipeline: when input row j arrives, level 1 finishes row
-// j-1, level 2 finishes row j-2 from level 1's output of the same iteration,
-// ..., and level K finishes row j-K, which is stored.  The dependency cone of
-// K steps is K columns wide on each side, so the strip's 120 inner columns
-// are exact after K levels; in y the skew only needs K extra rows at the two
-// ends of a chunk, and chunks are as tall as the SM count allows.  HBM
-// traffic per cell and step is about (20 B read + 12 B written) / K.
+// One block is a pipeline of K warps over one output strip of 120 columns
+// (128 staged, 4 halo columns on each side held by lanes 0 and 31) and one
+// chunk of rows; warp s-1 advances the strip by time level s.  The warps move
+// in lockstep ticks: at tick j, level s works on row r = j - 2(s-1), i.e. it
+// computes the new south faces of row r, finishes row r-1 (Eq. 4) and
+// computes the new west faces of row r, exactly like the single-step row
+// kernels.  Level 1 reads its rows from a shared-memory ring filled by bulk
+// copies (cp.async.bulk + mbarrier, a few rows ahead); level s > 1 reads the
+// row that level s-1 finished at the previous tick from a double-buffered
+// hand-off slot; only level K stores.  The dependency cone of K steps is K
+// columns wide on each side, so the 120 inner columns are exact; in y the
+// chunk needs K extra rows at each end.  HBM traffic per cell and step is
+// about (20 B read + 12 B written) / K plus the 8/120 column overlap.
 //
 // Per cell and level the arithmetic is the single-step kernels' (the same
 // explicitly rounded face function and depth update), so K levels give the
-// same bits as K single steps.  Boundary faces (Eq. 5-6) are applied at every
-// level with that level's inflow row; ledger volumes are booked only by the
-// warp that owns the cell or boundary face.  Waits are bounded like the
-// stream kernel's.
+// same bits as K single steps.  Boundary faces (Eq. 5-6) use that level's
+// inflow row; ledger volumes are booked only by the pipeline that owns the
+// cell or boundary face.  Waits on the copies are bounded (about 2 s), after
+// which the status word gets the timeout bit and the pipeline stops storing.
 #include "fast_face.cuh"
 #include "tma_util.cuh"
 
@@ -25,25 +27,22 @@ namespace flood {
 
 namespace {
 
-constexpr int kWarps = 4;                   // warps per block
 constexpr int kHalo = 4;                    // halo columns per side (= largest K)
 constexpr int kOut = 128 - 2 * kHalo;       // output columns per strip
-constexpr int kPF = 3;                      // rows in flight
-constexpr int kDZ = kPF + kHalo + 1;        // z,n ring depth: rows still read by lagging levels
+constexpr int kPF = 3;                      // level-1 rows in flight
 constexpr uint64_t kBudgetNs = 2000000000ull;
 
-// 16-byte aligned size: every warp's ring (bulk-copy destinations, float4
-// loads) must start on a 16-byte boundary.
-struct alignas(16) WarpRing {
-    float hq[kPF][3][128];                  // h, qx, qy of staged rows
-    float zn[kDZ][2][128];                  // z, n of the last kDZ rows
+template <int K>
+struct alignas(16) PipeSmem {
+    static constexpr int kDZ = kPF + 2 * K; // z,n rows kept: the lagging levels read 2(K-1)+1 rows back
+    float hq[kPF][3][128];                  // level-1 input rows: h, qx, qy
+    float zn[kDZ][2][128];                  // z, n of recent rows
+    float ho[K > 1 ? K - 1 : 1][2][3][128]; // hand-off: level s -> s+1, double buffered by tick parity
     uint64_t bar[kPF];
 };
 
-static_assert(sizeof(WarpRing) % 16 == 0, "per-warp ring must keep 16-byte alignment");
-constexpr size_t kSmemBytes = sizeof(WarpRing) * kWarps;
-
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void sts4(float *p, const float4 &v) { *reinterpret_cast<float4 *>(p) = v; }
 
 __device__ __forceinline__ float get(const float4 &v, int k)
 {
@@ -58,43 +57,42 @@ __device__ __forceinline__ void set(float4 &v, int k, float x)
     else v.w = x;
 }
 
-// One level's pending row r-1: its input depth and the new faces computed for it.
-struct Level {
-    float4 hp, qxw, qys;
-    float qxe;
-};
-
 template <int K>
-__global__ void __launch_bounds__(kWarps * 32, 4) step_tiled_kernel(const StepArgs<float> a)
+__global__ void __launch_bounds__(K * 32) step_tiled_kernel(const StepArgs<float> a)
 {
+    using Smem = PipeSmem<K>;
+    constexpr int kDZ = Smem::kDZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const Geom &G = a.geo;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lvl = warp + 1;                         // this warp's time level
     const int nx = G.nx, ny = G.ny, P = G.pitch;
     const int n_strips = a.tile_x, chunk_rows = a.tile_y;
-    const int gw = blockIdx.x * kWarps + warp;
-    const int strip = gw % n_strips, chunk = gw / n_strips;
+    const int strip = blockIdx.x % n_strips, chunk = blockIdx.x / n_strips;
     const int y0 = chunk * chunk_rows;
-    const bool active = y0 < ny;
+    const bool active = y0 < ny;                      // uniform over the block
     const int y1 = min(y0 + chunk_rows, ny);
-    const int x0 = strip * kOut - kHalo;              // first staged column
+    const int x0 = strip * kOut - kHalo;
     const int c0 = x0 + 4 * lane;
     const int own_lo = strip * kOut, own_hi = min(strip * kOut + kOut, nx);
     const int jb = max(y0 - K, 0);
-    const int jend = y1 + K - 1;                      // last iteration (level K reaches row y1)
     const int jload_hi = min(y1 + K - 1, ny - 1);     // last staged row
     const int nload = jload_hi - jb + 1;
-    WarpRing &ring = reinterpret_cast<WarpRing *>(smem_raw)[warp];
+    const int jlast = min(y1, ny) + 2 * (K - 1);      // last tick: level K reaches row min(y1, ny)
+    const int step = a.s + (lvl - 1);                 // this level's step in the epoch
+    const int rstart = jb == 0 ? 0 : jb + (lvl - 1);  // first row this level sees (halo row if jb > 0)
 
     const double dtd = a.ctrl->dt;
     FastConst Kc;
-    const float dt = (float)dtd, dx = (float)G.dx, g = (float)G.g;
-    Kc.gdt = g * dt;
-    Kc.a1 = Kc.gdt / dx;
-    Kc.h_dry = (float)G.h_dry;
-    Kc.dtdx = dt / dx;
-
+    {
+        const float dt = (float)dtd, dx = (float)G.dx, g = (float)G.g;
+        Kc.gdt = g * dt;
+        Kc.a1 = Kc.gdt / dx;
+        Kc.h_dry = (float)G.h_dry;
+        Kc.dtdx = dt / dx;
+    }
     double vout = 0.0, vclip = 0.0;
     float hmax = 0.0f;
     bool nan_seen = false;
@@ -103,19 +101,18 @@ __global__ void __launch_bounds__(kWarps * 32, 4) step_tiled_kernel(const StepAr
     const int ce = min(x0 + 128, P);
     const int so = cs - x0;
     const uint32_t seg_bytes = (uint32_t)(ce - cs) * 4u;
-
-    if (active && lane == 0) {
-        for (int s = 0; s < kPF; s++) mbar_init(&ring.bar[s], 1);
+    if (active && threadIdx.x == 0) {
+        for (int s = 0; s < kPF; s++) mbar_init(&sm.bar[s], 1);
         fence_mbar_init();
     }
-    __syncwarp();
+    __syncthreads();
     auto issue = [&](int idx) {
         const int j = jb + idx;
         const size_t row = (size_t)j * P + cs;
-        uint64_t *bar = &ring.bar[idx % kPF];
+        uint64_t *bar = &sm.bar[idx % kPF];
         mbar_arrive_expect_tx(bar, seg_bytes * 5u);
-        float *hq = &ring.hq[idx % kPF][0][0];
-        float *zn = &ring.zn[j % kDZ][0][0];
+        float *hq = &sm.hq[idx % kPF][0][0];
+        float *zn = &sm.zn[j % kDZ][0][0];
         bulk_copy_g2s(hq + 0 * 128 + so, a.h + row, seg_bytes, bar);
         bulk_copy_g2s(hq + 1 * 128 + so, a.qx + row, seg_bytes, bar);
         bulk_copy_g2s(hq + 2 * 128 + so, a.qy + row, seg_bytes, bar);
@@ -123,181 +120,178 @@ __global__ void __launch_bounds__(kWarps * 32, 4) step_tiled_kernel(const StepAr
         bulk_copy_g2s(zn + 1 * 128 + so, a.n + row, seg_bytes, bar);
     };
     int issued = 0, consumed = 0;
-    bool abort = false;
-    if (active && lane == 0)
+    if (active && threadIdx.x == 0)
         for (; issued < min(kPF, nload); issued++) issue(issued);
 
-    Level L[K];
-#pragma unroll
-    for (int s = 0; s < K; s++) {
-        L[s].hp = L[s].qxw = L[s].qys = make_float4(0, 0, 0, 0);
-        L[s].qxe = 0.0f;
-    }
     bool own_cell[4], own_wface[4], all_cell = true, all_wface = true;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        int c = c0 + k;
+        const int c = c0 + k;
         own_cell[k] = c >= own_lo && c < own_hi;
         own_wface[k] = c >= own_lo && (c < own_hi || (c == nx && own_hi == nx));
         all_cell &= own_cell[k];
         all_wface &= own_wface[k];
     }
 
+    // this level's previous row: input depth and the new faces computed for it
+    float4 hp = make_float4(0, 0, 0, 0), qxw_p = hp, qys_p = hp;
+    float qxe_p = 0.0f;
+    bool abort = false;
     if (active) {
-        for (int j = jb; j <= jend; j++) {
-            // ---- input row j (level 0) from the ring
-            float4 ho_h = make_float4(0, 0, 0, 0), ho_qx = ho_h, ho_qy = ho_h;   // hand-off to the next level
-            bool ho_valid = false;
-            if (j <= jload_hi) {
-                const int idx = j - jb;
-                bool ok = mbar_wait_bounded(&ring.bar[idx % kPF], (uint32_t)((idx / kPF) & 1), kBudgetNs);
-                if (__any_sync(0xffffffffu, !ok)) {
-                    abort = true;
-                    break;
+        for (int j = jb; j <= jlast; j++) {
+            const int r = j - 2 * (lvl - 1);
+            // ---- level 1: wait for the staged row (the block shares the outcome)
+            int ok = 1;
+            if (lvl == 1 && r >= jb && r <= jload_hi) {
+                const int idx = r - jb;
+                ok = mbar_wait_bounded(&sm.bar[idx % kPF], (uint32_t)((idx / kPF) & 1), kBudgetNs) ? 1 : 0;
+                ok = __all_sync(0xffffffffu, ok);
+            }
+            if (!__syncthreads_and(ok)) {
+                abort = true;
+                break;
+            }
+            if (r >= rstart && r <= ny && r <= y1 + K - lvl) {
+                // current row inputs
+                float4 ch = make_float4(0, 0, 0, 0), cqx = ch, cqy = ch, cz = ch, cn = ch, pz = ch, pn = ch;
+                if (r < ny) {
+                    if (lvl == 1) {
+                        const float *hq = &sm.hq[(r - jb) % kPF][0][0];
+                        ch = lds4(hq + 0 * 128 + 4 * lane);
+                        cqx = lds4(hq + 1 * 128 + 4 * lane);
+                        cqy = lds4(hq + 2 * 128 + 4 * lane);
+                    } else {
+                        const float *ho = &sm.ho[lvl - 2][(j - 1) & 1][0][0];
+                        ch = lds4(ho + 0 * 128 + 4 * lane);
+                        cqx = lds4(ho + 1 * 128 + 4 * lane);
+                        cqy = lds4(ho + 2 * 128 + 4 * lane);
+                    }
+                    cz = lds4(&sm.zn[r % kDZ][0][4 * lane]);
+                    cn = lds4(&sm.zn[r % kDZ][1][4 * lane]);
                 }
-                consumed = idx + 1;
-                const float *hq = &ring.hq[idx % kPF][0][0];
-                ho_h = lds4(hq + 0 * 128 + 4 * lane);
-                ho_qx = lds4(hq + 1 * 128 + 4 * lane);
-                ho_qy = lds4(hq + 2 * 128 + 4 * lane);
-                ho_valid = true;
-                __syncwarp();
-                if (lane == 0 && issued < nload) {
+                if (r > 0) {
+                    pz = lds4(&sm.zn[(r - 1) % kDZ][0][4 * lane]);
+                    pn = lds4(&sm.zn[(r - 1) % kDZ][1][4 * lane]);
+                }
+                if (r == rstart && jb > 0) {
+                    hp = ch;                          // halo row: only becomes the previous row
+                } else {
+                    // ---- new south faces of row r
+                    float4 qys;
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const int c = c0 + k;
+                        float v = 0.0f;
+                        if (c >= 0 && c < nx) {
+                            double vo = 0.0;
+                            if (r == 0) v = boundary_fast_at(a, step, 2, c, get(ch, k), get(cn, k), vo);
+                            else if (r == ny) v = boundary_fast_at(a, step, 3, c, get(hp, k), get(pn, k), vo);
+                            else {
+                                const float zl = get(pz, k), zr = get(cz, k);
+                                v = face_fast(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr, fmaxf(zl, zr),
+                                              get(pn, k) + get(cn, k), Kc);
+                            }
+                            if (own_cell[k] && ((r == 0 && y0 == 0) || (r == ny && y1 == ny))) vout += vo;
+                        }
+                        set(qys, k, v);
+                    }
+                    // ---- finish row r-1: Eq. 4 and the clip; hand it on (or store it at level K)
+                    const bool has_prev = jb == 0 ? r > 0 : r > rstart + 1;
+                    if (has_prev) {
+                        const int rr = r - 1;
+                        const bool own_row = rr >= y0 && rr < y1;
+                        float4 fin;
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            const float qe = k < 3 ? get(qxw_p, k + 1) : qxe_p;
+                            const float dv = __fadd_rn(__fsub_rn(get(qxw_p, k), qe), __fsub_rn(get(qys_p, k), get(qys, k)));
+                            float v = __fmaf_rn(Kc.dtdx, dv, get(hp, k));
+                            if (v < 0.0f) {
+                                if (own_row && own_cell[k]) vclip += -(double)v * G.dx * G.dx;
+                                v = 0.0f;
+                            }
+                            if (lvl == K && own_row && own_cell[k]) {
+                                hmax = fmaxf(hmax, v);
+                                nan_seen |= (v != v);
+                            }
+                            set(fin, k, v);
+                        }
+                        if (lvl < K) {
+                            float *ho = &sm.ho[lvl - 1][j & 1][0][0];
+                            sts4(ho + 0 * 128 + 4 * lane, fin);
+                            sts4(ho + 1 * 128 + 4 * lane, qxw_p);
+                            sts4(ho + 2 * 128 + 4 * lane, qys_p);
+                        } else if (own_row) {
+                            const size_t ro = (size_t)rr * P + c0;
+                            if (all_cell) {
+                                *reinterpret_cast<float4 *>(a.h_out + ro) = fin;
+                                *reinterpret_cast<float4 *>(a.qy_out + ro) = qys_p;
+                                if (rr == ny - 1) *reinterpret_cast<float4 *>(a.qy_out + ro + P) = qys;
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < 4; k++)
+                                    if (own_cell[k]) {
+                                        a.h_out[ro + k] = get(fin, k);
+                                        a.qy_out[ro + k] = get(qys_p, k);
+                                        if (rr == ny - 1) a.qy_out[ro + P + k] = get(qys, k);
+                                    }
+                            }
+                            if (all_wface) *reinterpret_cast<float4 *>(a.qx_out + ro) = qxw_p;
+                            else {
+#pragma unroll
+                                for (int k = 0; k < 4; k++)
+                                    if (own_wface[k]) a.qx_out[ro + k] = get(qxw_p, k);
+                            }
+                        }
+                    }
+                    // ---- new west faces of row r; row r becomes this level's previous row
+                    if (r < ny) {
+                        const bool own_row_r = r >= y0 && r < y1;
+                        const float hl0 = __shfl_up_sync(0xffffffffu, ch.w, 1);
+                        const float zl0 = __shfl_up_sync(0xffffffffu, cz.w, 1);
+                        const float nl0 = __shfl_up_sync(0xffffffffu, cn.w, 1);
+                        float4 qxw;
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            const int c = c0 + k;
+                            const float hl = k == 0 ? hl0 : get(ch, k - 1);
+                            const float zl = k == 0 ? zl0 : get(cz, k - 1);
+                            const float nl = k == 0 ? nl0 : get(cn, k - 1);
+                            float v = 0.0f;
+                            double vo = 0.0;
+                            if (c == 0) v = boundary_fast_at(a, step, 0, r, get(ch, 0), get(cn, 0), vo);
+                            else if (c == nx) v = boundary_fast_at(a, step, 1, r, hl, nl, vo);
+                            else if (c > 0 && c < nx) {
+                                const float zr = get(cz, k);
+                                v = face_fast(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), Kc);
+                            }
+                            if (own_row_r && own_wface[k]) vout += vo;
+                            set(qxw, k, v);
+                        }
+                        qxe_p = __shfl_down_sync(0xffffffffu, qxw.x, 1);
+                        hp = ch;
+                        qxw_p = qxw;
+                        qys_p = qys;
+                    }
+                }
+            }
+            // ---- level 1 refills the ring once every level is done with the tick's rows
+            __syncthreads();
+            if (lvl == 1 && lane == 0 && r >= jb && r <= jload_hi) {
+                consumed = r - jb + 1;
+                if (issued < nload) {
                     fence_proxy_async();
                     issue(issued);
                     issued++;
                 }
             }
-#pragma unroll
-            for (int s = 1; s <= K; s++) {
-                const int r = j - (s - 1);                 // this level's current row
-                const int rstart = jb == 0 ? 0 : jb + (s - 1);
-                Level &S = L[s - 1];
-                const float4 ch = ho_h, cqx = ho_qx, cqy = ho_qy;
-                const bool cur_valid = ho_valid;
-                ho_valid = false;
-                if (r < rstart || r > ny) continue;
-                if (r < ny && !cur_valid) continue;        // no input for this row (cannot happen)
-                if (r == rstart && jb > 0) {               // halo row: only becomes the previous row
-                    S.hp = ch;
-                    continue;
-                }
-                const int step = a.s + (s - 1);
-                float4 cz = make_float4(0, 0, 0, 0), cn = cz, pz = cz, pn = cz;
-                if (r < ny) {
-                    cz = lds4(&ring.zn[r % kDZ][0][4 * lane]);
-                    cn = lds4(&ring.zn[r % kDZ][1][4 * lane]);
-                }
-                if (r > 0) {
-                    pz = lds4(&ring.zn[(r - 1) % kDZ][0][4 * lane]);
-                    pn = lds4(&ring.zn[(r - 1) % kDZ][1][4 * lane]);
-                }
-                // ---- new south faces of row r
-                float4 qys;
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const int c = c0 + k;
-                    float v = 0.0f;
-                    if (c >= 0 && c < nx) {
-                        double vo = 0.0;
-                        if (r == 0) v = boundary_fast_at(a, step, 2, c, get(ch, k), get(cn, k), vo);
-                        else if (r == ny) v = boundary_fast_at(a, step, 3, c, get(S.hp, k), get(pn, k), vo);
-                        else {
-                            float zl = get(pz, k), zr = get(cz, k);
-                            v = face_fast(get(cqy, k), get(S.hp, k) + zl, get(ch, k) + zr, fmaxf(zl, zr),
-                                          get(pn, k) + get(cn, k), Kc);
-                        }
-                        if (own_cell[k] && ((r == 0 && y0 == 0) || (r == ny && y1 == ny))) vout += vo;
-                    }
-                    set(qys, k, v);
-                }
-                // ---- finish row r-1 (Eq. 4, clip); hand it to the next level
-                const bool has_prev = jb == 0 ? r > 0 : r > rstart + 1;
-                if (has_prev) {
-                    const int rr = r - 1;
-                    const bool own_row = rr >= y0 && rr < y1;
-                    float4 fin;
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        float qe = k < 3 ? get(S.qxw, k + 1) : S.qxe;
-                        float dv = __fadd_rn(__fsub_rn(get(S.qxw, k), qe), __fsub_rn(get(S.qys, k), get(qys, k)));
-                        float v = __fmaf_rn(Kc.dtdx, dv, get(S.hp, k));
-                        if (v < 0.0f) {
-                            if (own_row && own_cell[k]) vclip += -(double)v * G.dx * G.dx;
-                            v = 0.0f;
-                        }
-                        if (s == K && own_row && own_cell[k]) {
-                            hmax = fmaxf(hmax, v);
-                            nan_seen |= (v != v);
-                        }
-                        set(fin, k, v);
-                    }
-                    if (s == K && own_row) {
-                        const size_t ro = (size_t)rr * P + c0;
-                        if (all_cell) {
-                            *reinterpret_cast<float4 *>(a.h_out + ro) = fin;
-                            *reinterpret_cast<float4 *>(a.qy_out + ro) = S.qys;
-                            if (rr == ny - 1) *reinterpret_cast<float4 *>(a.qy_out + ro + P) = qys;
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < 4; k++)
-                                if (own_cell[k]) {
-                                    a.h_out[ro + k] = get(fin, k);
-                                    a.qy_out[ro + k] = get(S.qys, k);
-                                    if (rr == ny - 1) a.qy_out[ro + P + k] = get(qys, k);
-                                }
-                        }
-                        if (all_wface) *reinterpret_cast<float4 *>(a.qx_out + ro) = S.qxw;
-                        else {
-#pragma unroll
-                            for (int k = 0; k < 4; k++)
-                                if (own_wface[k]) a.qx_out[ro + k] = get(S.qxw, k);
-                        }
-                    }
-                    ho_h = fin;
-                    ho_qx = S.qxw;
-                    ho_qy = S.qys;
-                    ho_valid = true;
-                }
-                // ---- new west faces of row r, then row r becomes this level's previous row
-                if (r < ny) {
-                    const bool own_row_r = r >= y0 && r < y1;
-                    float hl0 = __shfl_up_sync(0xffffffffu, ch.w, 1);
-                    float zl0 = __shfl_up_sync(0xffffffffu, cz.w, 1);
-                    float nl0 = __shfl_up_sync(0xffffffffu, cn.w, 1);
-                    float4 qxw;
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        const int c = c0 + k;
-                        float hl = k == 0 ? hl0 : get(ch, k - 1);
-                        float zl = k == 0 ? zl0 : get(cz, k - 1);
-                        float nl = k == 0 ? nl0 : get(cn, k - 1);
-                        float v = 0.0f;
-                        double vo = 0.0;
-                        if (c == 0) v = boundary_fast_at(a, step, 0, r, get(ch, 0), get(cn, 0), vo);
-                        else if (c == nx) v = boundary_fast_at(a, step, 1, r, hl, nl, vo);
-                        else if (c > 0 && c < nx) {
-                            float zr = get(cz, k);
-                            v = face_fast(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), Kc);
-                        }
-                        if (own_row_r && own_wface[k]) vout += vo;
-                        set(qxw, k, v);
-                    }
-                    S.qxe = __shfl_down_sync(0xffffffffu, qxw.x, 1);
-                    S.hp = ch;
-                    S.qxw = qxw;
-                    S.qys = qys;
-                }
-            }
         }
-        if (abort) {
-            if (lane == 0) {
-                for (int k = consumed; k < issued; k++)
-                    mbar_wait_bounded(&ring.bar[k % kPF], (uint32_t)((k / kPF) & 1), kBudgetNs);
-                atomicOr(&a.ctrl->status, kStatusTimeout);
-            }
-            __syncwarp();
-        }
+    }
+    if (abort && threadIdx.x == 0) {
+        // leave no bulk copy writing into shared memory after exit
+        for (int k = consumed; k < issued; k++)
+            mbar_wait_bounded(&sm.bar[k % kPF], (uint32_t)((k / kPF) & 1), kBudgetNs);
+        atomicOr(&a.ctrl->status, kStatusTimeout);
     }
     double bo = block_reduce<false>(vout, red);
     if (threadIdx.x == 0 && bo != 0.0) atomicAdd(&a.ctrl->V_out, dtd * bo);
@@ -311,7 +305,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) step_tiled_kernel(const StepAr
         double vin = a.ctrl->V_in;
         for (int s = 0; s < K; s++)
             for (int k = 0; k < a.n_inflow_sec; k++) {
-                double Q = a.inflow_Q[(size_t)(a.s + s) * a.n_inflow_sec + k];
+                const double Q = a.inflow_Q[(size_t)(a.s + s) * a.n_inflow_sec + k];
                 if (Q > 0.0) vin += dtd * Q;
             }
         a.ctrl->V_in = vin;
@@ -323,40 +317,38 @@ template <int K>
 cudaError_t launch_k(const StepArgs<float> &a0, cudaStream_t st)
 {
     static int blocks_per_sm = 0, num_sms = 0;
+    const size_t smem = sizeof(PipeSmem<K>);
     if (!blocks_per_sm) {
         cudaError_t e = cudaFuncSetAttribute(step_tiled_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kSmemBytes);
+                                             (int)smem);
         if (e != cudaSuccess) return e;
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, step_tiled_kernel<K>, kWarps * 32,
-                                                          kSmemBytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, step_tiled_kernel<K>, K * 32, smem);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     StepArgs<float> a = a0;
     const int nx = a.geo.nx, ny = a.geo.ny;
     const int n_strips = (nx + kOut - 1) / kOut;
-    const int resident_warps = num_sms * blocks_per_sm * kWarps;
-    // one chunk per resident warp, but no chunk shorter than 32 rows (the K-row skew overhead)
-    int chunks = resident_warps / n_strips;
+    // one chunk per resident pipeline, chunks no shorter than 32 rows
+    const int resident = num_sms * blocks_per_sm;
+    int chunks = resident / n_strips;
     chunks = chunks < 1 ? 1 : chunks;
-    int max_chunks = (ny + 31) / 32;
+    const int max_chunks = (ny + 31) / 32;
     if (chunks > max_chunks) chunks = max_chunks;
     const int chunk_rows = (ny + chunks - 1) / chunks;
     chunks = (ny + chunk_rows - 1) / chunk_rows;
     a.tile_x = n_strips;
     a.tile_y = chunk_rows;
-    const int warps = n_strips * chunks;
-    const int blocks = (warps + kWarps - 1) / kWarps;
-    step_tiled_kernel<K><<<blocks, kWarps * 32, kSmemBytes, st>>>(a);
+    step_tiled_kernel<K><<<n_strips * chunks, K * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t tiled_smem_bytes(int, int, int) { return kSmemBytes; }
+size_t tiled_smem_bytes(int, int, int k) { return k >= 4 ? sizeof(PipeSmem<4>) : sizeof(PipeSmem<2>); }
 
 cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st)
 {
