@@ -29,7 +29,7 @@ namespace {
 
 constexpr int kHalo = 4;                    // halo columns per side (= largest K)
 constexpr int kOut = 128 - 2 * kHalo;       // output columns per strip
-constexpr int kPF = 3;                      // level-1 rows in flight
+constexpr int kPF = 8;                      // level-1 rows in flight
 constexpr uint64_t kBudgetNs = 2000000000ull;
 
 template <int K>
@@ -140,18 +140,15 @@ __global__ void __launch_bounds__(K * 32) step_tiled_kernel(const StepArgs<float
     if (active) {
         for (int j = jb; j <= jlast; j++) {
             const int r = j - 2 * (lvl - 1);
-            // ---- level 1: wait for the staged row (the block shares the outcome)
-            int ok = 1;
+            // ---- level 1 waits for its staged row; the other levels only read rows that
+            // level 1 waited for at earlier ticks (ordered by the end-of-tick barrier)
+            bool stop = false;
             if (lvl == 1 && r >= jb && r <= jload_hi) {
                 const int idx = r - jb;
-                ok = mbar_wait_bounded(&sm.bar[idx % kPF], (uint32_t)((idx / kPF) & 1), kBudgetNs) ? 1 : 0;
-                ok = __all_sync(0xffffffffu, ok);
+                const int ok = mbar_wait_bounded(&sm.bar[idx % kPF], (uint32_t)((idx / kPF) & 1), kBudgetNs) ? 1 : 0;
+                stop = !__all_sync(0xffffffffu, ok);
             }
-            if (!__syncthreads_and(ok)) {
-                abort = true;
-                break;
-            }
-            if (r >= rstart && r <= ny && r <= y1 + K - lvl) {
+            if (!stop && r >= rstart && r <= ny && r <= y1 + K - lvl) {
                 // current row inputs
                 float4 ch = make_float4(0, 0, 0, 0), cqx = ch, cqy = ch, cz = ch, cn = ch, pz = ch, pn = ch;
                 if (r < ny) {
@@ -275,8 +272,11 @@ __global__ void __launch_bounds__(K * 32) step_tiled_kernel(const StepArgs<float
                     }
                 }
             }
-            // ---- level 1 refills the ring once every level is done with the tick's rows
-            __syncthreads();
+            // ---- end of tick (shares a timeout); then level 1 refills the ring
+            if (__syncthreads_or(stop ? 1 : 0)) {
+                abort = true;
+                break;
+            }
             if (lvl == 1 && lane == 0 && r >= jb && r <= jload_hi) {
                 consumed = r - jb + 1;
                 if (issued < nload) {
