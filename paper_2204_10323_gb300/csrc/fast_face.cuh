@@ -16,21 +16,56 @@ struct FastConst {
     float dtdx;     // dt / dx
 };
 
+// x^(-7/3) for x > 0 as 2^(-7/3 log2 x) with the hardware base-2 logarithm
+// and exponential (relative error below 1e-6 for the depths of a flood).
+__device__ __forceinline__ float pow_m73(float x)
+{
+    float l, r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+    l = __fmul_rn(l, -7.0f / 3.0f);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(l));
+    return r;
+}
+
+// 1/x by the hardware reciprocal approximation (about 1 ulp); Eq. 3 divides
+// by 1 + friction >= 1 only.
+__device__ __forceinline__ float rcp_fast(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Eq. 3 for a wet face of flow depth hf.  Called with hf <= 0 the result is
+// NaN or garbage, never a trap; face_fast_sel discards it.
+__device__ __forceinline__ float face_wet(float q, float etaL, float etaR, float hf, float nsum, const FastConst &k)
+{
+    float r7 = pow_m73(hf);
+    float nf = __fmul_rn(0.5f, nsum);
+    float fric = __fmul_rn(__fmul_rn(__fmul_rn(k.gdt, __fmul_rn(nf, nf)), fabsf(q)), r7);
+    float num = __fsub_rn(q, __fmul_rn(__fmul_rn(k.a1, hf), __fsub_rn(etaR, etaL)));
+    return __fmul_rn(num, rcp_fast(__fadd_rn(1.0f, fric)));
+}
+
 // Eq. 3 at one face: eta_L, eta_R water levels, zmax = max(z_L, z_R),
-// nsum = n_L + n_R.  h_f^(-7/3) is evaluated as (h_f^(-1/3))^7.
+// nsum = n_L + n_R.
 __device__ __forceinline__ float face_fast(float q, float etaL, float etaR, float zmax, float nsum,
                                            const FastConst &k)
 {
     float hf = __fsub_rn(fmaxf(etaL, etaR), zmax);
     if (!(hf > k.h_dry)) return 0.0f;
-    float r = rcbrtf(hf);
-    float r2 = __fmul_rn(r, r);
-    float r4 = __fmul_rn(r2, r2);
-    float r7 = __fmul_rn(__fmul_rn(r4, r2), r);
-    float nf = __fmul_rn(0.5f, nsum);
-    float fric = __fmul_rn(__fmul_rn(__fmul_rn(k.gdt, __fmul_rn(nf, nf)), fabsf(q)), r7);
-    float num = __fsub_rn(q, __fmul_rn(__fmul_rn(k.a1, hf), __fsub_rn(etaR, etaL)));
-    return __fdividef(num, __fadd_rn(1.0f, fric));
+    return face_wet(q, etaL, etaR, hf, nsum, k);
+}
+
+// The same value as face_fast without a branch: a dry face is evaluated too
+// and its result discarded, so that the faces of a lane can be interleaved by
+// the compiler.
+__device__ __forceinline__ float face_fast_sel(float q, float etaL, float etaR, float zmax, float nsum,
+                                               const FastConst &k)
+{
+    float hf = __fsub_rn(fmaxf(etaL, etaR), zmax);
+    float v = face_wet(q, etaL, etaR, hf, nsum, k);
+    return hf > k.h_dry ? v : 0.0f;
 }
 
 // Eq. 5 boundary flux magnitude (m^2/s) of a cell of depth h.

@@ -63,6 +63,7 @@ __device__ __forceinline__ void stream_body(const StepArgs<float> &a, const int 
     const int P = G.pitch;
     const int x0 = (bx * nwarps + warp) * 128;
     const int c0 = x0 + 4 * lane;
+    const bool full = c0 + 3 < nx;                  // all four columns of the lane inside the grid
     const bool active = x0 < nx;
     const int y0 = by * rows;
     const int y1 = min(y0 + rows, ny);
@@ -155,41 +156,62 @@ __device__ __forceinline__ void stream_body(const StepArgs<float> &a, const int 
                 continue;
             }
             // ---- new south faces of row j
+            // (interior rows branch-free; the boundary rows, uniform over the warp, take Eq. 5-6)
             float4 qys;
+            if (j > 0 && j < ny) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                int c = c0 + k;
-                float v = 0.0f;
-                if (c < nx) {
-                    if (j == 0) v = boundary_fast_at(a, step, 2, c, get(ch, k), get(cn, k), vout);
-                    else if (j == ny) v = boundary_fast_at(a, step, 3, c, get(hp, k), get(np_, k), vout);
-                    else {
-                        float zl = get(zp, k), zr = get(cz, k);
-                        v = face_fast(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr, fmaxf(zl, zr),
-                                      get(np_, k) + get(cn, k), K);
-                    }
+                for (int k = 0; k < 4; k++) {
+                    const float zl = get(zp, k), zr = get(cz, k);
+                    set(qys, k, face_fast_sel(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr, fmaxf(zl, zr),
+                                              get(np_, k) + get(cn, k), K));
                 }
-                set(qys, k, v);
+                if (!full) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        if (c0 + k >= nx) set(qys, k, 0.0f);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    int c = c0 + k;
+                    float v = 0.0f;
+                    if (c < nx)
+                        v = j == 0 ? boundary_fast_at(a, step, 2, c, get(ch, k), get(cn, k), vout)
+                                   : boundary_fast_at(a, step, 3, c, get(hp, k), get(np_, k), vout);
+                    set(qys, k, v);
+                }
             }
             // ---- finish row j-1
             if (j > y0) {
                 const int jr = j - 1;
                 const size_t r = (size_t)jr * P + c0;
                 float4 hn;
+                bool neg = false;
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     float qe = k < 3 ? get(qxw_p, k + 1) : qxe_p3;
                     float dv = __fadd_rn(__fsub_rn(get(qxw_p, k), qe), __fsub_rn(get(qys_p, k), get(qys, k)));
                     float v = __fmaf_rn(K.dtdx, dv, get(hp, k));
-                    if (c0 + k < nx) {
+                    neg |= v < 0.0f;
+                    set(hn, k, v);
+                }
+                if (neg) {                        // rare: clip to zero, book the removed volume
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const float v = get(hn, k);
                         if (v < 0.0f) {
-                            vclip += -(double)v * G.dx * G.dx;
-                            v = 0.0f;
+                            if (c0 + k < nx) vclip += -(double)v * G.dx * G.dx;
+                            set(hn, k, 0.0f);
                         }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float v = get(hn, k);
+                    if (full || c0 + k < nx) {
                         hmax = fmaxf(hmax, v);
                         nan_seen |= (v != v);
                     }
-                    set(hn, k, v);
                 }
                 if (c0 + 3 < nx) {
                     *reinterpret_cast<float4 *>(a.h_out + r) = hn;
@@ -232,18 +254,22 @@ __device__ __forceinline__ void stream_body(const StepArgs<float> &a, const int 
             float4 qxw;
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                int c = c0 + k;
-                float hl = k == 0 ? hl0 : get(ch, k - 1);
-                float zl = k == 0 ? zl0 : get(cz, k - 1);
-                float nl = k == 0 ? nl0 : get(cn, k - 1);
-                float v = 0.0f;
-                if (c == 0) v = boundary_fast_at(a, step, 0, j, get(ch, 0), get(cn, 0), vout);
-                else if (c == nx) v = boundary_fast_at(a, step, 1, j, hl, nl, vout);
-                else if (c < nx) {
-                    float zr = get(cz, k);
-                    v = face_fast(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), K);
+                const float hl = k == 0 ? hl0 : get(ch, k - 1);
+                const float zl = k == 0 ? zl0 : get(cz, k - 1);
+                const float nl = k == 0 ? nl0 : get(cn, k - 1);
+                const float zr = get(cz, k);
+                set(qxw, k, face_fast_sel(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), K));
+            }
+            if (c0 == 0 || !full) {               // lanes holding x = 0 or x >= nx: Eq. 5-6, or no face
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int c = c0 + k;
+                    const float hl = k == 0 ? hl0 : get(ch, k - 1);
+                    const float nl = k == 0 ? nl0 : get(cn, k - 1);
+                    if (c == 0) set(qxw, k, boundary_fast_at(a, step, 0, j, get(ch, 0), get(cn, 0), vout));
+                    else if (c == nx) set(qxw, k, boundary_fast_at(a, step, 1, j, hl, nl, vout));
+                    else if (c > nx) set(qxw, k, 0.0f);
                 }
-                set(qxw, k, v);
             }
             float qe = __shfl_down_sync(0xffffffffu, qxw.x, 1);
             if (lane == 31) {

@@ -123,10 +123,13 @@ __global__ void __launch_bounds__(K * 32) step_tiled_kernel(const StepArgs<float
     if (active && threadIdx.x == 0)
         for (; issued < min(kPF, nload); issued++) issue(issued);
 
-    bool own_cell[4], own_wface[4], all_cell = true, all_wface = true;
+    bool own_cell[4], own_wface[4], in_col[4], in_wface[4], all_cell = true, all_wface = true;
+    const bool edge_lane = c0 <= 0 || c0 + 3 >= nx;   // holds a column outside (0, nx)
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const int c = c0 + k;
+        in_col[k] = c >= 0 && c < nx;                 // a cell of the grid (its south face exists)
+        in_wface[k] = c > 0 && c < nx;                // an interior west face
         own_cell[k] = c >= own_lo && c < own_hi;
         own_wface[k] = c >= own_lo && (c < own_hi || (c == nx && own_hi == nx));
         all_cell &= own_cell[k];
@@ -173,24 +176,35 @@ __global__ void __launch_bounds__(K * 32) step_tiled_kernel(const StepArgs<float
                 if (r == rstart && jb > 0) {
                     hp = ch;                          // halo row: only becomes the previous row
                 } else {
-                    // ---- new south faces of row r
+                    // ---- new south faces of row r (interior rows branch-free; the boundary
+                    // rows, uniform over the warp, take the Eq. 5-6 path)
                     float4 qys;
+                    if (r > 0 && r < ny) {
 #pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        const int c = c0 + k;
-                        float v = 0.0f;
-                        if (c >= 0 && c < nx) {
-                            double vo = 0.0;
-                            if (r == 0) v = boundary_fast_at(a, step, 2, c, get(ch, k), get(cn, k), vo);
-                            else if (r == ny) v = boundary_fast_at(a, step, 3, c, get(hp, k), get(pn, k), vo);
-                            else {
-                                const float zl = get(pz, k), zr = get(cz, k);
-                                v = face_fast(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr, fmaxf(zl, zr),
-                                              get(pn, k) + get(cn, k), Kc);
-                            }
-                            if (own_cell[k] && ((r == 0 && y0 == 0) || (r == ny && y1 == ny))) vout += vo;
+                        for (int k = 0; k < 4; k++) {
+                            const float zl = get(pz, k), zr = get(cz, k);
+                            const float v = face_fast_sel(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr,
+                                                          fmaxf(zl, zr), get(pn, k) + get(cn, k), Kc);
+                            set(qys, k, v);
                         }
-                        set(qys, k, v);
+                        if (edge_lane) {
+#pragma unroll
+                            for (int k = 0; k < 4; k++)
+                                if (!in_col[k]) set(qys, k, 0.0f);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            const int c = c0 + k;
+                            float v = 0.0f;
+                            if (in_col[k]) {
+                                double vo = 0.0;
+                                v = r == 0 ? boundary_fast_at(a, step, 2, c, get(ch, k), get(cn, k), vo)
+                                           : boundary_fast_at(a, step, 3, c, get(hp, k), get(pn, k), vo);
+                                if (own_cell[k] && ((r == 0 && y0 == 0) || (r == ny && y1 == ny))) vout += vo;
+                            }
+                            set(qys, k, v);
+                        }
                     }
                     // ---- finish row r-1: Eq. 4 and the clip; hand it on (or store it at level K)
                     const bool has_prev = jb == 0 ? r > 0 : r > rstart + 1;
@@ -198,20 +212,34 @@ __global__ void __launch_bounds__(K * 32) step_tiled_kernel(const StepArgs<float
                         const int rr = r - 1;
                         const bool own_row = rr >= y0 && rr < y1;
                         float4 fin;
+                        bool neg = false;
 #pragma unroll
                         for (int k = 0; k < 4; k++) {
                             const float qe = k < 3 ? get(qxw_p, k + 1) : qxe_p;
                             const float dv = __fadd_rn(__fsub_rn(get(qxw_p, k), qe), __fsub_rn(get(qys_p, k), get(qys, k)));
-                            float v = __fmaf_rn(Kc.dtdx, dv, get(hp, k));
-                            if (v < 0.0f) {
-                                if (own_row && own_cell[k]) vclip += -(double)v * G.dx * G.dx;
-                                v = 0.0f;
-                            }
-                            if (lvl == K && own_row && own_cell[k]) {
-                                hmax = fmaxf(hmax, v);
-                                nan_seen |= (v != v);
-                            }
+                            const float v = __fmaf_rn(Kc.dtdx, dv, get(hp, k));
+                            neg |= v < 0.0f;
                             set(fin, k, v);
+                        }
+                        if (neg) {                    // rare: clip to zero, book the removed volume
+#pragma unroll
+                            for (int k = 0; k < 4; k++) {
+                                const float v = get(fin, k);
+                                if (v < 0.0f) {
+                                    if (own_row && own_cell[k]) vclip += -(double)v * G.dx * G.dx;
+                                    set(fin, k, 0.0f);
+                                }
+                            }
+                        }
+                        if (lvl == K && own_row) {
+#pragma unroll
+                            for (int k = 0; k < 4; k++) {
+                                const float v = get(fin, k);
+                                if (own_cell[k]) {
+                                    hmax = fmaxf(hmax, v);
+                                    nan_seen |= (v != v);
+                                }
+                            }
                         }
                         if (lvl < K) {
                             float *ho = &sm.ho[lvl - 1][j & 1][0][0];
@@ -250,20 +278,29 @@ __global__ void __launch_bounds__(K * 32) step_tiled_kernel(const StepArgs<float
                         float4 qxw;
 #pragma unroll
                         for (int k = 0; k < 4; k++) {
-                            const int c = c0 + k;
                             const float hl = k == 0 ? hl0 : get(ch, k - 1);
                             const float zl = k == 0 ? zl0 : get(cz, k - 1);
                             const float nl = k == 0 ? nl0 : get(cn, k - 1);
-                            float v = 0.0f;
-                            double vo = 0.0;
-                            if (c == 0) v = boundary_fast_at(a, step, 0, r, get(ch, 0), get(cn, 0), vo);
-                            else if (c == nx) v = boundary_fast_at(a, step, 1, r, hl, nl, vo);
-                            else if (c > 0 && c < nx) {
-                                const float zr = get(cz, k);
-                                v = face_fast(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), Kc);
-                            }
-                            if (own_row_r && own_wface[k]) vout += vo;
+                            const float zr = get(cz, k);
+                            const float v = face_fast_sel(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr),
+                                                          nl + get(cn, k), Kc);
                             set(qxw, k, v);
+                        }
+                        if (edge_lane) {              // lanes at or beyond x = 0 or x = nx: Eq. 5-6, or no face
+#pragma unroll
+                            for (int k = 0; k < 4; k++) {
+                                const int c = c0 + k;
+                                if (!in_wface[k]) set(qxw, k, 0.0f);
+                                if (c == 0 || c == nx) {
+                                    double vo = 0.0;
+                                    const float hl = k == 0 ? hl0 : get(ch, k - 1);
+                                    const float nl = k == 0 ? nl0 : get(cn, k - 1);
+                                    const float v = c == 0 ? boundary_fast_at(a, step, 0, r, get(ch, 0), get(cn, 0), vo)
+                                                           : boundary_fast_at(a, step, 1, r, hl, nl, vo);
+                                    if (own_row_r && own_wface[k]) vout += vo;
+                                    set(qxw, k, v);
+                                }
+                            }
                         }
                         qxe_p = __shfl_down_sync(0xffffffffu, qxw.x, 1);
                         hp = ch;
