@@ -110,7 +110,9 @@ typedef struct {
     int32_t bc_form;             /* 0 cell discharge dx h^(5/3) sqrt(S)/n, 1 literal dx^2 h^(2/3) sqrt(S)/n */
     int32_t kernel;              /* flood_kernel */
     int32_t steps_per_launch;    /* K for FLOOD_KERNEL_TILED: 1..4, must divide E (0 = 4) */
-    int32_t tile_x, tile_y;      /* stream kernel launch shape: warps per block (1..4), rows per chunk (0 = 4, 64) */
+    int32_t tile_x, tile_y;      /* launch shape, 0 = chosen by the library.  STREAM: warps per block (1..4),
+                                    rows per chunk.  TILED: at most tile_x pipelines (blocks), tile_y rows
+                                    per work item (a chunk of one 120-column strip).  Negative: invalid. */
     int32_t use_graph;           /* 1: replay whole epochs from a captured CUDA graph */
     void *stream;                /* cudaStream_t, NULL = current PyTorch stream */
 } flood_opts;

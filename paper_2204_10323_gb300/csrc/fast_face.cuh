@@ -93,6 +93,23 @@ __device__ __forceinline__ float boundary_fast_at(const StepArgs<float> &a, int 
     return -inward * q;
 }
 
+// As boundary_fast_at, booking the outflow flux magnitude (m^2/s, not yet
+// times dx) into a float partial sum that the caller folds into its double
+// ledger every few rows.
+__device__ __forceinline__ float boundary_fast_flux(const StepArgs<float> &a, int step, int side, int k, float h,
+                                                    float n, float &qout)
+{
+    const Geom &G = a.geo;
+    int off = side == 0 ? 0 : side == 1 ? G.ny : side == 2 ? 2 * G.ny : 2 * G.ny + G.nx;
+    int type = a.bc.type[off + k];
+    if (type == kBcWall) return 0.0f;
+    float inward = (side == 0 || side == 2) ? 1.0f : -1.0f;
+    if (type == kBcInflow) return inward * a.inflow_q[(size_t)step * a.n_slots + a.bc.slot[off + k]];
+    float q = outflow_fast(h, (float)a.bc.sqrtS[off + k], n, (float)G.dx, (float)G.h_dry, G.bc_form);
+    qout += q;
+    return -inward * q;
+}
+
 // Boundary face value on `side` at index k along it, for the adjacent cell (h, n).
 __device__ __forceinline__ float boundary_fast(const StepArgs<float> &a, int side, int k, float h, float n,
                                                double &vout)

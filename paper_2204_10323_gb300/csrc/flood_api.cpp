@@ -232,7 +232,13 @@ flood_status launch_steps(flood_handle *h, int s, int k, int want_hmax, const in
         case FLOOD_KERNEL_REFERENCE: e = launch_step_reference<float>(a, h->stream); break;
         case FLOOD_KERNEL_TILED:
             // gauge recording needs the depth after every step: single steps there
-            e = gout ? launch_step_stream(a, h->stream) : launch_step_tiled(a, h->stream);
+            if (gout) {
+                StepArgs<float> b = a;
+                b.tile_x = b.tile_y = 0;
+                e = launch_step_stream(b, h->stream);
+            } else {
+                e = launch_step_tiled(a, h->stream);
+            }
             break;
         case FLOOD_KERNEL_STREAM: e = launch_step_stream(a, h->stream); break;
         default: e = launch_step_rows(a, h->stream); break;
@@ -299,6 +305,7 @@ static flood_status validate(const flood_grid *grid, const flood_bc_section *sec
     if (o.dt_mode != 0 && o.dt_mode != 1) return fail(nullptr, FLOOD_ERR_ARG, "dt_mode must be 0 or 1");
     if (o.bc_form != 0 && o.bc_form != 1) return fail(nullptr, FLOOD_ERR_ARG, "bc_form must be 0 or 1");
     if (o.kernel < 0 || o.kernel > 4) return fail(nullptr, FLOOD_ERR_ARG, "unknown kernel");
+    if (o.tile_x < 0 || o.tile_y < 0) return fail(nullptr, FLOOD_ERR_ARG, "tile_x and tile_y must be >= 0");
     if (o.kernel == FLOOD_KERNEL_TILED) {
         int K = o.steps_per_launch > 0 ? o.steps_per_launch : 4;
         if (K > 4 || o.epoch_steps % K != 0)

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(kWarps * 32) step_rows_kernel(const StepArgs<f
     const size_t P = (size_t)G.pitch;
     const int x0 = (blockIdx.x * kWarps + warp) * 128;
     const int c0 = x0 + 4 * lane;
+    const bool full = c0 + 3 < nx;                       // all four columns of the lane inside the grid
     const bool active = x0 < nx;
     const bool lane_in = active && c0 < (int)P;        // float4 lies inside the row pitch
     const int y0 = blockIdx.y * kRows;
@@ -105,41 +106,62 @@ __global__ void __launch_bounds__(kWarps * 32) step_rows_kernel(const StepArgs<f
                 if (j + 1 < y1) nxt.qx = ld4(QX + r);
             }
             // ---- new south faces of row j (between rows j-1 and j)
+            // (interior rows branch-free; the boundary rows, uniform over the warp, take Eq. 5-6)
             float4 qys;
-            #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                int c = c0 + k;
-                float v = 0.0f;
-                if (c < nx) {
-                    if (j == 0) v = boundary_fast(a, 2, c, get(cur.h, k), get(cur.n, k), vout);
-                    else if (j == ny) v = boundary_fast(a, 3, c, get(hp, k), get(np_, k), vout);
-                    else {
-                        float zl = get(zp, k), zr = get(cur.z, k);
-                        v = face_fast(get(cur.qy, k), get(hp, k) + zl, get(cur.h, k) + zr, fmaxf(zl, zr),
-                                      get(np_, k) + get(cur.n, k), K);
-                    }
+            if (j > 0 && j < ny) {
+                #pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float zl = get(zp, k), zr = get(cur.z, k);
+                    set(qys, k, face_fast_sel(get(cur.qy, k), get(hp, k) + zl, get(cur.h, k) + zr, fmaxf(zl, zr),
+                                              get(np_, k) + get(cur.n, k), K));
                 }
-                set(qys, k, v);
+                if (!full) {
+                    #pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        if (c0 + k >= nx) set(qys, k, 0.0f);
+                }
+            } else {
+                #pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    int c = c0 + k;
+                    float v = 0.0f;
+                    if (c < nx)
+                        v = j == 0 ? boundary_fast(a, 2, c, get(cur.h, k), get(cur.n, k), vout)
+                                   : boundary_fast(a, 3, c, get(hp, k), get(np_, k), vout);
+                    set(qys, k, v);
+                }
             }
             // ---- finish row j-1: Eq. 4, clip, stores
             if (j > y0) {
                 const int jr = j - 1;
                 const size_t r = (size_t)jr * P + c0;
                 float4 hn;
+                bool neg = false;
                 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     float qe = k < 3 ? get(qxw_p, k + 1) : qxe_p3;
                     float dv = __fadd_rn(__fsub_rn(get(qxw_p, k), qe), __fsub_rn(get(qys_p, k), get(qys, k)));
                     float v = __fmaf_rn(K.dtdx, dv, get(hp, k));
-                    if (c0 + k < nx) {
+                    neg |= v < 0.0f;
+                    set(hn, k, v);
+                }
+                if (neg) {                        // rare: clip to zero, book the removed volume
+                    #pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const float v = get(hn, k);
                         if (v < 0.0f) {
-                            vclip += -(double)v * G.dx * G.dx;
-                            v = 0.0f;
+                            if (c0 + k < nx) vclip += -(double)v * G.dx * G.dx;
+                            set(hn, k, 0.0f);
                         }
+                    }
+                }
+                #pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float v = get(hn, k);
+                    if (full || c0 + k < nx) {
                         hmax = fmaxf(hmax, v);
                         nan_seen |= (v != v);
                     }
-                    set(hn, k, v);
                 }
                 if (c0 + 3 < nx) {
                     *reinterpret_cast<float4 *>(a.h_out + r) = hn;
@@ -185,18 +207,23 @@ __global__ void __launch_bounds__(kWarps * 32) step_rows_kernel(const StepArgs<f
             float4 qxw;
             #pragma unroll
             for (int k = 0; k < 4; k++) {
-                int c = c0 + k;
-                float hl = k == 0 ? hW : get(cur.h, k - 1);
-                float zl = k == 0 ? zW : get(cur.z, k - 1);
-                float nl = k == 0 ? nW : get(cur.n, k - 1);
-                float v = 0.0f;
-                if (c == 0) v = boundary_fast(a, 0, j, get(cur.h, 0), get(cur.n, 0), vout);
-                else if (c == nx) v = boundary_fast(a, 1, j, hl, nl, vout);
-                else if (c < nx) {
-                    float zr = get(cur.z, k);
-                    v = face_fast(get(cur.qx, k), hl + zl, get(cur.h, k) + zr, fmaxf(zl, zr), nl + get(cur.n, k), K);
+                const float hl = k == 0 ? hW : get(cur.h, k - 1);
+                const float zl = k == 0 ? zW : get(cur.z, k - 1);
+                const float nl = k == 0 ? nW : get(cur.n, k - 1);
+                const float zr = get(cur.z, k);
+                set(qxw, k, face_fast_sel(get(cur.qx, k), hl + zl, get(cur.h, k) + zr, fmaxf(zl, zr),
+                                          nl + get(cur.n, k), K));
+            }
+            if (c0 == 0 || !full) {               // lanes holding x = 0 or x >= nx: Eq. 5-6, or no face
+                #pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int c = c0 + k;
+                    const float hl = k == 0 ? hW : get(cur.h, k - 1);
+                    const float nl = k == 0 ? nW : get(cur.n, k - 1);
+                    if (c == 0) set(qxw, k, boundary_fast(a, 0, j, get(cur.h, 0), get(cur.n, 0), vout));
+                    else if (c == nx) set(qxw, k, boundary_fast(a, 1, j, hl, nl, vout));
+                    else if (c > nx) set(qxw, k, 0.0f);
                 }
-                set(qxw, k, v);
             }
             // east face of the lane's last column = next lane's first west face
             float qe = __shfl_down_sync(0xffffffffu, qxw.x, 1);

@@ -1,8 +1,11 @@
 // step_tiled.cu -- FP32 temporal blocking: K <= 4 time steps per launch.
 //
-// One block is a pipeline of K warps over one output strip of 120 columns
-// (128 staged, 4 halo columns on each side held by lanes 0 and 31) and one
-// chunk of rows; warp s-1 advances the strip by time level s.  The warps move
+// One block is a pipeline of K warps over output strips of 120 columns (128
+// staged, 4 halo columns on each side held by lanes 0 and 31); warp s-1
+// advances the strip by time level s.  The grid is persistent, one block per
+// resident pipeline, and each block takes an equal contiguous share of the
+// strip-major sequence of (strip, row) units, running the pipeline once per
+// strip segment of its share, so that every SM gets the same work.  The warps move
 // in lockstep ticks: at tick j, level s works on row r = j - 2(s-1), i.e. it
 // computes the new south faces of row r, finishes row r-1 (Eq. 4) and
 // computes the new west faces of row r, exactly like the single-step row
@@ -58,7 +61,7 @@ __device__ __forceinline__ void set(float4 &v, int k, float x)
 }
 
 template <int K>
-__global__ void __launch_bounds__(K * 32) step_tiled_kernel(const StepArgs<float> a)
+__global__ void __launch_bounds__(K * 32, K == 4 ? 5 : 1) step_tiled_kernel(const StepArgs<float> a)
 {
     using Smem = PipeSmem<K>;
     constexpr int kDZ = Smem::kDZ;
@@ -69,20 +72,10 @@ __global__ void __launch_bounds__(K * 32) step_tiled_kernel(const StepArgs<float
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lvl = warp + 1;                         // this warp's time level
     const int nx = G.nx, ny = G.ny, P = G.pitch;
+    // work items (chunk, strip) in chunk-major order, block b takes items b, b + grid, ...
     const int n_strips = a.tile_x, chunk_rows = a.tile_y;
-    const int strip = blockIdx.x % n_strips, chunk = blockIdx.x / n_strips;
-    const int y0 = chunk * chunk_rows;
-    const bool active = y0 < ny;                      // uniform over the block
-    const int y1 = min(y0 + chunk_rows, ny);
-    const int x0 = strip * kOut - kHalo;
-    const int c0 = x0 + 4 * lane;
-    const int own_lo = strip * kOut, own_hi = min(strip * kOut + kOut, nx);
-    const int jb = max(y0 - K, 0);
-    const int jload_hi = min(y1 + K - 1, ny - 1);     // last staged row
-    const int nload = jload_hi - jb + 1;
-    const int jlast = min(y1, ny) + 2 * (K - 1);      // last tick: level K reaches row min(y1, ny)
+    const int n_items = n_strips * ((ny + chunk_rows - 1) / chunk_rows);
     const int step = a.s + (lvl - 1);                 // this level's step in the epoch
-    const int rstart = jb == 0 ? 0 : jb + (lvl - 1);  // first row this level sees (halo row if jb > 0)
 
     const double dtd = a.ctrl->dt;
     FastConst Kc;
@@ -93,241 +86,271 @@ __global__ void __launch_bounds__(K * 32) step_tiled_kernel(const StepArgs<float
         Kc.h_dry = (float)G.h_dry;
         Kc.dtdx = dt / dx;
     }
-    double vout = 0.0, vclip = 0.0;
+    double vout = 0.0, vclip = 0.0;                   // folded from the float runs below
     float hmax = 0.0f;
     bool nan_seen = false;
 
-    const int cs = max(x0, 0);
-    const int ce = min(x0 + 128, P);
-    const int so = cs - x0;
-    const uint32_t seg_bytes = (uint32_t)(ce - cs) * 4u;
-    if (active && threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
         for (int s = 0; s < kPF; s++) mbar_init(&sm.bar[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    auto issue = [&](int idx) {
-        const int j = jb + idx;
-        const size_t row = (size_t)j * P + cs;
-        uint64_t *bar = &sm.bar[idx % kPF];
-        mbar_arrive_expect_tx(bar, seg_bytes * 5u);
-        float *hq = &sm.hq[idx % kPF][0][0];
-        float *zn = &sm.zn[j % kDZ][0][0];
-        bulk_copy_g2s(hq + 0 * 128 + so, a.h + row, seg_bytes, bar);
-        bulk_copy_g2s(hq + 1 * 128 + so, a.qx + row, seg_bytes, bar);
-        bulk_copy_g2s(hq + 2 * 128 + so, a.qy + row, seg_bytes, bar);
-        bulk_copy_g2s(zn + 0 * 128 + so, a.z + row, seg_bytes, bar);
-        bulk_copy_g2s(zn + 1 * 128 + so, a.n + row, seg_bytes, bar);
-    };
+    // rows staged by earlier segments: ring slot and phase of staged row idx of
+    // this segment are those of the running count base + idx
+    uint32_t base = 0;
     int issued = 0, consumed = 0;
-    if (active && threadIdx.x == 0)
-        for (; issued < min(kPF, nload); issued++) issue(issued);
-
-    bool own_cell[4], own_wface[4], in_col[4], in_wface[4], all_cell = true, all_wface = true;
-    const bool edge_lane = c0 <= 0 || c0 + 3 >= nx;   // holds a column outside (0, nx)
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const int c = c0 + k;
-        in_col[k] = c >= 0 && c < nx;                 // a cell of the grid (its south face exists)
-        in_wface[k] = c > 0 && c < nx;                // an interior west face
-        own_cell[k] = c >= own_lo && c < own_hi;
-        own_wface[k] = c >= own_lo && (c < own_hi || (c == nx && own_hi == nx));
-        all_cell &= own_cell[k];
-        all_wface &= own_wface[k];
-    }
-
-    // this level's previous row: input depth and the new faces computed for it
-    float4 hp = make_float4(0, 0, 0, 0), qxw_p = hp, qys_p = hp;
-    float qxe_p = 0.0f;
     bool abort = false;
-    if (active) {
-        for (int j = jb; j <= jlast; j++) {
-            const int r = j - 2 * (lvl - 1);
-            // ---- level 1 waits for its staged row; the other levels only read rows that
-            // level 1 waited for at earlier ticks (ordered by the end-of-tick barrier)
-            bool stop = false;
-            if (lvl == 1 && r >= jb && r <= jload_hi) {
-                const int idx = r - jb;
-                const int ok = mbar_wait_bounded(&sm.bar[idx % kPF], (uint32_t)((idx / kPF) & 1), kBudgetNs) ? 1 : 0;
-                stop = !__all_sync(0xffffffffu, ok);
-            }
-            if (!stop && r >= rstart && r <= ny && r <= y1 + K - lvl) {
-                // current row inputs
-                float4 ch = make_float4(0, 0, 0, 0), cqx = ch, cqy = ch, cz = ch, cn = ch, pz = ch, pn = ch;
-                if (r < ny) {
-                    if (lvl == 1) {
-                        const float *hq = &sm.hq[(r - jb) % kPF][0][0];
-                        ch = lds4(hq + 0 * 128 + 4 * lane);
-                        cqx = lds4(hq + 1 * 128 + 4 * lane);
-                        cqy = lds4(hq + 2 * 128 + 4 * lane);
-                    } else {
-                        const float *ho = &sm.ho[lvl - 2][(j - 1) & 1][0][0];
-                        ch = lds4(ho + 0 * 128 + 4 * lane);
-                        cqx = lds4(ho + 1 * 128 + 4 * lane);
-                        cqy = lds4(ho + 2 * 128 + 4 * lane);
-                    }
-                    cz = lds4(&sm.zn[r % kDZ][0][4 * lane]);
-                    cn = lds4(&sm.zn[r % kDZ][1][4 * lane]);
+    for (int item = blockIdx.x; item < n_items && !abort; item += gridDim.x) {
+        const int strip = item % n_strips;
+        const int y0 = (item / n_strips) * chunk_rows;
+        const int y1 = min(y0 + chunk_rows, ny);
+        const int x0 = strip * kOut - kHalo;
+        const int c0 = x0 + 4 * lane;
+        const int own_lo = strip * kOut, own_hi = min(strip * kOut + kOut, nx);
+        const int jb = max(y0 - K, 0);
+        const int jload_hi = min(y1 + K - 1, ny - 1);     // last staged row
+        const int nload = jload_hi - jb + 1;
+        const int jlast = min(y1, ny) + 2 * (K - 1);      // last tick: level K reaches row min(y1, ny)
+        const int rstart = jb == 0 ? 0 : jb + (lvl - 1);  // first row this level sees (halo row if jb > 0)
+        const int cs = max(x0, 0);
+        const int ce = min(x0 + 128, P);
+        const int so = cs - x0;
+        const uint32_t seg_bytes = (uint32_t)(ce - cs) * 4u;
+        auto issue = [&](int idx) {
+            const int j = jb + idx;
+            const uint32_t slot = (base + (uint32_t)idx) % kPF;
+            const size_t row = (size_t)j * P + cs;
+            uint64_t *bar = &sm.bar[slot];
+            mbar_arrive_expect_tx(bar, seg_bytes * 5u);
+            float *hq = &sm.hq[slot][0][0];
+            float *zn = &sm.zn[j % kDZ][0][0];
+            bulk_copy_g2s(hq + 0 * 128 + so, a.h + row, seg_bytes, bar);
+            bulk_copy_g2s(hq + 1 * 128 + so, a.qx + row, seg_bytes, bar);
+            bulk_copy_g2s(hq + 2 * 128 + so, a.qy + row, seg_bytes, bar);
+            bulk_copy_g2s(zn + 0 * 128 + so, a.z + row, seg_bytes, bar);
+            bulk_copy_g2s(zn + 1 * 128 + so, a.n + row, seg_bytes, bar);
+        };
+        issued = 0;
+        consumed = 0;
+        if (threadIdx.x == 0) {
+            fence_proxy_async();                          // earlier segments' reads of the rings come first
+            for (; issued < min(kPF, nload); issued++) issue(issued);
+        }
+
+        bool own_cell[4], own_wface[4], in_col[4], in_wface[4], all_cell = true, all_wface = true;
+        const bool edge_lane = c0 <= 0 || c0 + 3 >= nx;   // holds a column outside (0, nx)
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int c = c0 + k;
+            in_col[k] = c >= 0 && c < nx;                 // a cell of the grid (its south face exists)
+            in_wface[k] = c > 0 && c < nx;                // an interior west face
+            own_cell[k] = c >= own_lo && c < own_hi;
+            own_wface[k] = c >= own_lo && (c < own_hi || (c == nx && own_hi == nx));
+            all_cell &= own_cell[k];
+            all_wface &= own_wface[k];
+        }
+
+        // this level's previous row: input depth and the new faces computed for it
+        float4 hp = make_float4(0, 0, 0, 0), qxw_p = hp, qys_p = hp;
+        float qxe_p = 0.0f;
+        // runs of up to 32 ticks; the float partial sums of the boundary outflow (fq)
+        // and the clipped depth (fc) are folded into the double ledger after each run
+        for (int j0 = jb; j0 <= jlast && !abort; j0 += 32) {
+            float fq = 0.0f, fc = 0.0f;
+            const int jend = min(j0 + 31, jlast);
+            for (int j = j0; j <= jend; j++) {
+                const int r = j - 2 * (lvl - 1);
+                // ---- level 1 waits for its staged row; the other levels only read rows that
+                // level 1 waited for at earlier ticks (ordered by the end-of-tick barrier)
+                bool stop = false;
+                if (lvl == 1 && r >= jb && r <= jload_hi) {
+                    const uint32_t g = base + (uint32_t)(r - jb);
+                    const int ok = mbar_wait_bounded(&sm.bar[g % kPF], (g / kPF) & 1u, kBudgetNs) ? 1 : 0;
+                    stop = !__all_sync(0xffffffffu, ok);
                 }
-                if (r > 0) {
-                    pz = lds4(&sm.zn[(r - 1) % kDZ][0][4 * lane]);
-                    pn = lds4(&sm.zn[(r - 1) % kDZ][1][4 * lane]);
-                }
-                if (r == rstart && jb > 0) {
-                    hp = ch;                          // halo row: only becomes the previous row
-                } else {
-                    // ---- new south faces of row r (interior rows branch-free; the boundary
-                    // rows, uniform over the warp, take the Eq. 5-6 path)
-                    float4 qys;
-                    if (r > 0 && r < ny) {
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            const float zl = get(pz, k), zr = get(cz, k);
-                            const float v = face_fast_sel(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr,
-                                                          fmaxf(zl, zr), get(pn, k) + get(cn, k), Kc);
-                            set(qys, k, v);
-                        }
-                        if (edge_lane) {
-#pragma unroll
-                            for (int k = 0; k < 4; k++)
-                                if (!in_col[k]) set(qys, k, 0.0f);
-                        }
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            const int c = c0 + k;
-                            float v = 0.0f;
-                            if (in_col[k]) {
-                                double vo = 0.0;
-                                v = r == 0 ? boundary_fast_at(a, step, 2, c, get(ch, k), get(cn, k), vo)
-                                           : boundary_fast_at(a, step, 3, c, get(hp, k), get(pn, k), vo);
-                                if (own_cell[k] && ((r == 0 && y0 == 0) || (r == ny && y1 == ny))) vout += vo;
-                            }
-                            set(qys, k, v);
-                        }
-                    }
-                    // ---- finish row r-1: Eq. 4 and the clip; hand it on (or store it at level K)
-                    const bool has_prev = jb == 0 ? r > 0 : r > rstart + 1;
-                    if (has_prev) {
-                        const int rr = r - 1;
-                        const bool own_row = rr >= y0 && rr < y1;
-                        float4 fin;
-                        bool neg = false;
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            const float qe = k < 3 ? get(qxw_p, k + 1) : qxe_p;
-                            const float dv = __fadd_rn(__fsub_rn(get(qxw_p, k), qe), __fsub_rn(get(qys_p, k), get(qys, k)));
-                            const float v = __fmaf_rn(Kc.dtdx, dv, get(hp, k));
-                            neg |= v < 0.0f;
-                            set(fin, k, v);
-                        }
-                        if (neg) {                    // rare: clip to zero, book the removed volume
-#pragma unroll
-                            for (int k = 0; k < 4; k++) {
-                                const float v = get(fin, k);
-                                if (v < 0.0f) {
-                                    if (own_row && own_cell[k]) vclip += -(double)v * G.dx * G.dx;
-                                    set(fin, k, 0.0f);
-                                }
-                            }
-                        }
-                        if (lvl == K && own_row) {
-#pragma unroll
-                            for (int k = 0; k < 4; k++) {
-                                const float v = get(fin, k);
-                                if (own_cell[k]) {
-                                    hmax = fmaxf(hmax, v);
-                                    nan_seen |= (v != v);
-                                }
-                            }
-                        }
-                        if (lvl < K) {
-                            float *ho = &sm.ho[lvl - 1][j & 1][0][0];
-                            sts4(ho + 0 * 128 + 4 * lane, fin);
-                            sts4(ho + 1 * 128 + 4 * lane, qxw_p);
-                            sts4(ho + 2 * 128 + 4 * lane, qys_p);
-                        } else if (own_row) {
-                            const size_t ro = (size_t)rr * P + c0;
-                            if (all_cell) {
-                                *reinterpret_cast<float4 *>(a.h_out + ro) = fin;
-                                *reinterpret_cast<float4 *>(a.qy_out + ro) = qys_p;
-                                if (rr == ny - 1) *reinterpret_cast<float4 *>(a.qy_out + ro + P) = qys;
-                            } else {
-#pragma unroll
-                                for (int k = 0; k < 4; k++)
-                                    if (own_cell[k]) {
-                                        a.h_out[ro + k] = get(fin, k);
-                                        a.qy_out[ro + k] = get(qys_p, k);
-                                        if (rr == ny - 1) a.qy_out[ro + P + k] = get(qys, k);
-                                    }
-                            }
-                            if (all_wface) *reinterpret_cast<float4 *>(a.qx_out + ro) = qxw_p;
-                            else {
-#pragma unroll
-                                for (int k = 0; k < 4; k++)
-                                    if (own_wface[k]) a.qx_out[ro + k] = get(qxw_p, k);
-                            }
-                        }
-                    }
-                    // ---- new west faces of row r; row r becomes this level's previous row
+                if (!stop && r >= rstart && r <= ny && r <= y1 + K - lvl) {
+                    // current row inputs
+                    float4 ch = make_float4(0, 0, 0, 0), cqx = ch, cqy = ch, cz = ch, cn = ch, pz = ch, pn = ch;
                     if (r < ny) {
-                        const bool own_row_r = r >= y0 && r < y1;
-                        const float hl0 = __shfl_up_sync(0xffffffffu, ch.w, 1);
-                        const float zl0 = __shfl_up_sync(0xffffffffu, cz.w, 1);
-                        const float nl0 = __shfl_up_sync(0xffffffffu, cn.w, 1);
-                        float4 qxw;
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            const float hl = k == 0 ? hl0 : get(ch, k - 1);
-                            const float zl = k == 0 ? zl0 : get(cz, k - 1);
-                            const float nl = k == 0 ? nl0 : get(cn, k - 1);
-                            const float zr = get(cz, k);
-                            const float v = face_fast_sel(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr),
-                                                          nl + get(cn, k), Kc);
-                            set(qxw, k, v);
+                        if (lvl == 1) {
+                            const float *hq = &sm.hq[(base + (uint32_t)(r - jb)) % kPF][0][0];
+                            ch = lds4(hq + 0 * 128 + 4 * lane);
+                            cqx = lds4(hq + 1 * 128 + 4 * lane);
+                            cqy = lds4(hq + 2 * 128 + 4 * lane);
+                        } else {
+                            const float *ho = &sm.ho[lvl - 2][(j - 1) & 1][0][0];
+                            ch = lds4(ho + 0 * 128 + 4 * lane);
+                            cqx = lds4(ho + 1 * 128 + 4 * lane);
+                            cqy = lds4(ho + 2 * 128 + 4 * lane);
                         }
-                        if (edge_lane) {              // lanes at or beyond x = 0 or x = nx: Eq. 5-6, or no face
+                        cz = lds4(&sm.zn[r % kDZ][0][4 * lane]);
+                        cn = lds4(&sm.zn[r % kDZ][1][4 * lane]);
+                    }
+                    if (r > 0) {
+                        pz = lds4(&sm.zn[(r - 1) % kDZ][0][4 * lane]);
+                        pn = lds4(&sm.zn[(r - 1) % kDZ][1][4 * lane]);
+                    }
+                    if (r == rstart && jb > 0) {
+                        hp = ch;                          // halo row: only becomes the previous row
+                    } else {
+                        // ---- new south faces of row r (interior rows branch-free; the boundary
+                        // rows, uniform over the warp, take the Eq. 5-6 path)
+                        float4 qys;
+                        if (r > 0 && r < ny) {
+#pragma unroll
+                            for (int k = 0; k < 4; k++) {
+                                const float zl = get(pz, k), zr = get(cz, k);
+                                const float v = face_fast_sel(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr,
+                                                              fmaxf(zl, zr), get(pn, k) + get(cn, k), Kc);
+                                set(qys, k, v);
+                            }
+                            if (edge_lane) {
+#pragma unroll
+                                for (int k = 0; k < 4; k++)
+                                    if (!in_col[k]) set(qys, k, 0.0f);
+                            }
+                        } else {
 #pragma unroll
                             for (int k = 0; k < 4; k++) {
                                 const int c = c0 + k;
-                                if (!in_wface[k]) set(qxw, k, 0.0f);
-                                if (c == 0 || c == nx) {
-                                    double vo = 0.0;
-                                    const float hl = k == 0 ? hl0 : get(ch, k - 1);
-                                    const float nl = k == 0 ? nl0 : get(cn, k - 1);
-                                    const float v = c == 0 ? boundary_fast_at(a, step, 0, r, get(ch, 0), get(cn, 0), vo)
-                                                           : boundary_fast_at(a, step, 1, r, hl, nl, vo);
-                                    if (own_row_r && own_wface[k]) vout += vo;
-                                    set(qxw, k, v);
+                                float v = 0.0f;
+                                if (in_col[k]) {
+                                    float qo = 0.0f;
+                                    v = r == 0 ? boundary_fast_flux(a, step, 2, c, get(ch, k), get(cn, k), qo)
+                                               : boundary_fast_flux(a, step, 3, c, get(hp, k), get(pn, k), qo);
+                                    if (own_cell[k] && ((r == 0 && y0 == 0) || (r == ny && y1 == ny))) fq += qo;
+                                }
+                                set(qys, k, v);
+                            }
+                        }
+                        // ---- finish row r-1: Eq. 4 and the clip; hand it on (or store it at level K)
+                        const bool has_prev = jb == 0 ? r > 0 : r > rstart + 1;
+                        if (has_prev) {
+                            const int rr = r - 1;
+                            const bool own_row = rr >= y0 && rr < y1;
+                            float4 fin;
+                            bool neg = false;
+#pragma unroll
+                            for (int k = 0; k < 4; k++) {
+                                const float qe = k < 3 ? get(qxw_p, k + 1) : qxe_p;
+                                const float dv = __fadd_rn(__fsub_rn(get(qxw_p, k), qe), __fsub_rn(get(qys_p, k), get(qys, k)));
+                                const float v = __fmaf_rn(Kc.dtdx, dv, get(hp, k));
+                                neg |= v < 0.0f;
+                                set(fin, k, v);
+                            }
+                            if (neg) {                    // rare: clip to zero, book the removed volume
+#pragma unroll
+                                for (int k = 0; k < 4; k++) {
+                                    const float v = get(fin, k);
+                                    if (v < 0.0f) {
+                                        if (own_row && own_cell[k]) fc -= v;
+                                        set(fin, k, 0.0f);
+                                    }
+                                }
+                            }
+                            if (lvl == K && own_row) {
+#pragma unroll
+                                for (int k = 0; k < 4; k++) {
+                                    const float v = get(fin, k);
+                                    if (own_cell[k]) {
+                                        hmax = fmaxf(hmax, v);
+                                        nan_seen |= (v != v);
+                                    }
+                                }
+                            }
+                            if (lvl < K) {
+                                float *ho = &sm.ho[lvl - 1][j & 1][0][0];
+                                sts4(ho + 0 * 128 + 4 * lane, fin);
+                                sts4(ho + 1 * 128 + 4 * lane, qxw_p);
+                                sts4(ho + 2 * 128 + 4 * lane, qys_p);
+                            } else if (own_row) {
+                                const size_t ro = (size_t)rr * P + c0;
+                                if (all_cell) {
+                                    *reinterpret_cast<float4 *>(a.h_out + ro) = fin;
+                                    *reinterpret_cast<float4 *>(a.qy_out + ro) = qys_p;
+                                    if (rr == ny - 1) *reinterpret_cast<float4 *>(a.qy_out + ro + P) = qys;
+                                } else {
+#pragma unroll
+                                    for (int k = 0; k < 4; k++)
+                                        if (own_cell[k]) {
+                                            a.h_out[ro + k] = get(fin, k);
+                                            a.qy_out[ro + k] = get(qys_p, k);
+                                            if (rr == ny - 1) a.qy_out[ro + P + k] = get(qys, k);
+                                        }
+                                }
+                                if (all_wface) *reinterpret_cast<float4 *>(a.qx_out + ro) = qxw_p;
+                                else {
+#pragma unroll
+                                    for (int k = 0; k < 4; k++)
+                                        if (own_wface[k]) a.qx_out[ro + k] = get(qxw_p, k);
                                 }
                             }
                         }
-                        qxe_p = __shfl_down_sync(0xffffffffu, qxw.x, 1);
-                        hp = ch;
-                        qxw_p = qxw;
-                        qys_p = qys;
+                        // ---- new west faces of row r; row r becomes this level's previous row
+                        if (r < ny) {
+                            const bool own_row_r = r >= y0 && r < y1;
+                            const float hl0 = __shfl_up_sync(0xffffffffu, ch.w, 1);
+                            const float zl0 = __shfl_up_sync(0xffffffffu, cz.w, 1);
+                            const float nl0 = __shfl_up_sync(0xffffffffu, cn.w, 1);
+                            float4 qxw;
+#pragma unroll
+                            for (int k = 0; k < 4; k++) {
+                                const float hl = k == 0 ? hl0 : get(ch, k - 1);
+                                const float zl = k == 0 ? zl0 : get(cz, k - 1);
+                                const float nl = k == 0 ? nl0 : get(cn, k - 1);
+                                const float zr = get(cz, k);
+                                const float v = face_fast_sel(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr),
+                                                              nl + get(cn, k), Kc);
+                                set(qxw, k, v);
+                            }
+                            if (edge_lane) {              // lanes at or beyond x = 0 or x = nx: Eq. 5-6, or no face
+#pragma unroll
+                                for (int k = 0; k < 4; k++) {
+                                    const int c = c0 + k;
+                                    if (!in_wface[k]) set(qxw, k, 0.0f);
+                                    if (c == 0 || c == nx) {
+                                        float qo = 0.0f;
+                                        const float hl = k == 0 ? hl0 : get(ch, k - 1);
+                                        const float nl = k == 0 ? nl0 : get(cn, k - 1);
+                                        const float v = c == 0 ? boundary_fast_flux(a, step, 0, r, get(ch, 0), get(cn, 0), qo)
+                                                               : boundary_fast_flux(a, step, 1, r, hl, nl, qo);
+                                        if (own_row_r && own_wface[k]) fq += qo;
+                                        set(qxw, k, v);
+                                    }
+                                }
+                            }
+                            qxe_p = __shfl_down_sync(0xffffffffu, qxw.x, 1);
+                            hp = ch;
+                            qxw_p = qxw;
+                            qys_p = qys;
+                        }
+                    }
+                }
+                // ---- end of tick (shares a timeout); then level 1 refills the ring
+                if (__syncthreads_or(stop ? 1 : 0)) {
+                    abort = true;
+                    break;
+                }
+                if (lvl == 1 && lane == 0 && r >= jb && r <= jload_hi) {
+                    consumed = r - jb + 1;
+                    if (issued < nload) {
+                        fence_proxy_async();
+                        issue(issued);
+                        issued++;
                     }
                 }
             }
-            // ---- end of tick (shares a timeout); then level 1 refills the ring
-            if (__syncthreads_or(stop ? 1 : 0)) {
-                abort = true;
-                break;
-            }
-            if (lvl == 1 && lane == 0 && r >= jb && r <= jload_hi) {
-                consumed = r - jb + 1;
-                if (issued < nload) {
-                    fence_proxy_async();
-                    issue(issued);
-                    issued++;
-                }
-            }
+            vout += (double)fq * G.dx;
+            vclip += (double)fc * G.dx * G.dx;
         }
-    }
+        if (!abort) base += (uint32_t)nload;
+    }   // segments
     if (abort && threadIdx.x == 0) {
         // leave no bulk copy writing into shared memory after exit
-        for (int k = consumed; k < issued; k++)
-            mbar_wait_bounded(&sm.bar[k % kPF], (uint32_t)((k / kPF) & 1), kBudgetNs);
+        for (int k = consumed; k < issued; k++) {
+            const uint32_t g = base + (uint32_t)k;
+            mbar_wait_bounded(&sm.bar[g % kPF], (g / kPF) & 1u, kBudgetNs);
+        }
         atomicOr(&a.ctrl->status, kStatusTimeout);
     }
     double bo = block_reduce<false>(vout, red);
@@ -350,6 +373,48 @@ __global__ void __launch_bounds__(K * 32) step_tiled_kernel(const StepArgs<float
     }
 }
 
+}  // namespace
+
+// Row chunks for the (chunk, strip) work items of a grid of n_strips strips and
+// ny rows on `resident` pipelines: the chunk count minimises the ticks of the
+// busiest pipeline, (items per pipeline) x (chunk rows + 3K - 1), an item
+// costing its rows plus 2K - 1 staged halo rows and the 2(K - 1) ticks by
+// which level K lags level 1.
+void tiled_split(int n_strips, int ny, int resident, int K, int *chunk_rows, int *blocks)
+{
+    static int memo[4] = {-1, -1, -1, -1}, memo_rows = 0;
+    if (memo[0] == n_strips && memo[1] == ny && memo[2] == resident && memo[3] == K) {
+        const long long items = (long long)n_strips * ((ny + memo_rows - 1) / memo_rows);
+        *chunk_rows = memo_rows;
+        *blocks = (int)(items < resident ? items : resident);
+        return;
+    }
+    long long best = -1;
+    int best_rows = ny;
+    const int max_chunks = (ny + 15) / 16;            // chunks of at least 16 rows
+    for (int c = 1; c <= max_chunks; c++) {
+        const int rows = (ny + c - 1) / c;
+        const int chunks = (ny + rows - 1) / rows;
+        const long long items = (long long)n_strips * chunks;
+        const long long waves = (items + resident - 1) / resident;
+        const long long ticks = waves * (rows + 3 * K - 1);
+        if (best < 0 || ticks < best) {
+            best = ticks;
+            best_rows = rows;
+        }
+    }
+    memo[0] = n_strips;
+    memo[1] = ny;
+    memo[2] = resident;
+    memo[3] = K;
+    memo_rows = best_rows;
+    const long long items = (long long)n_strips * ((ny + best_rows - 1) / best_rows);
+    *chunk_rows = best_rows;
+    *blocks = (int)(items < resident ? items : resident);
+}
+
+namespace {
+
 template <int K>
 cudaError_t launch_k(const StepArgs<float> &a0, cudaStream_t st)
 {
@@ -369,17 +434,19 @@ cudaError_t launch_k(const StepArgs<float> &a0, cudaStream_t st)
     StepArgs<float> a = a0;
     const int nx = a.geo.nx, ny = a.geo.ny;
     const int n_strips = (nx + kOut - 1) / kOut;
-    // one chunk per resident pipeline, chunks no shorter than 32 rows
-    const int resident = num_sms * blocks_per_sm;
-    int chunks = resident / n_strips;
-    chunks = chunks < 1 ? 1 : chunks;
-    const int max_chunks = (ny + 31) / 32;
-    if (chunks > max_chunks) chunks = max_chunks;
-    const int chunk_rows = (ny + chunks - 1) / chunks;
-    chunks = (ny + chunk_rows - 1) / chunk_rows;
+    int resident = num_sms * blocks_per_sm;
+    if (a0.tile_x > 0 && a0.tile_x < resident) resident = a0.tile_x;   // caller's cap on pipelines
+    int chunk_rows = 0, blocks = 0;
+    if (a0.tile_y > 0) {                                                // caller's rows per work item
+        chunk_rows = a0.tile_y < ny ? a0.tile_y : ny;
+        const long long items = (long long)n_strips * ((ny + chunk_rows - 1) / chunk_rows);
+        blocks = (int)(items < resident ? items : resident);
+    } else {
+        tiled_split(n_strips, ny, resident, K, &chunk_rows, &blocks);
+    }
     a.tile_x = n_strips;
     a.tile_y = chunk_rows;
-    step_tiled_kernel<K><<<n_strips * chunks, K * 32, smem, st>>>(a);
+    step_tiled_kernel<K><<<blocks, K * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 

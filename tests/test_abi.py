@@ -114,6 +114,10 @@ def test_create_rejects_bad_options():
     o.steps_per_launch = 3        # must divide E
     st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
     assert st == F.ERR_ARG
+    o = F.default_opts()
+    o.tile_y = -1
+    st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
+    assert st == F.ERR_ARG and "tile" in F.flood_last_error(None)
 
 
 def test_default_opts_values():
