@@ -53,8 +53,8 @@ template <> struct Fwd<double> {
         double dv = O::add(O::sub(qW, qE), O::sub(qS, qN));
         return O::add(h, O::div(O::mul(dt, dv), dx));
     }
-    __device__ static double rcbrt_(double x) { return ::rcbrt(x); }
     __device__ static double rcp_(double x) { return 1.0 / x; }
+    __device__ static double pow_m73_(double x) { const double m = ::rcbrt(x), r = 1.0 / x; return m * r * r; }
 };
 
 template <> struct Fwd<float> {
@@ -87,8 +87,8 @@ template <> struct Fwd<float> {
         float dv = __fadd_rn(__fsub_rn(qW, qE), __fsub_rn(qS, qN));
         return __fmaf_rn(K.dtdx, dv, h);
     }
-    __device__ static float rcbrt_(float x) { return rcbrtf(x); }
-    __device__ static float rcp_(float x) { return __fdividef(1.0f, x); }
+    __device__ static float rcp_(float x) { return rcp_fast(x); }
+    __device__ static float pow_m73_(float x) { return pow_m73(x); }
 };
 
 // Partial derivatives of one wet face's Eq. 3 value.
@@ -103,9 +103,8 @@ __device__ __forceinline__ FaceLin<T> face_lin(T q, T hL, T zL, T nL, T hR, T zR
     const T etaL = hL + zL, etaR = hR + zR;
     const T nf = T(0.5) * (nL + nR);
     const T gdt = g * dt, a1 = gdt / dx;
-    const T m13 = Fwd<T>::rcbrt_(hf);
     const T inv_hf = Fwd<T>::rcp_(hf);
-    const T hf_m73 = m13 * inv_hf * inv_hf;
+    const T hf_m73 = Fwd<T>::pow_m73_(hf);
     const T c0 = gdt * nf * nf * hf_m73;     // friction per |q|
     const T fric = c0 * (q < T(0) ? -q : q);
     const T inv_den = Fwd<T>::rcp_(T(1) + fric);
@@ -144,7 +143,7 @@ __device__ __forceinline__ T bface(const StepArgs<T> &a, const Fwd<T> &F, int si
 // Adjoint of an outflow boundary face: contributions to lambda_h(c) and dL/dn(c).
 template <typename T>
 __device__ __forceinline__ void outflow_adj(const StepArgs<T> &a, const Fwd<T> &F, int side, int k, T h, T n,
-                                            T mu, T &lh, double &gn)
+                                            T mu, T &lh, T &gn)
 {
     const Geom &G = a.geo;
     const int off = bc_off<T>(G, side);
@@ -154,7 +153,7 @@ __device__ __forceinline__ void outflow_adj(const StepArgs<T> &a, const Fwd<T> &
     const T nu = -T(inward_sign(side)) * mu;   // adjoint of the outflow magnitude
     const T pe = G.bc_form == 0 ? T(5.0 / 3.0) : T(2.0 / 3.0);
     lh += nu * pe * q / h;
-    gn += (double)(-nu * q / n);
+    gn += -nu * q / n;
 }
 
 // One launch per reverse step, face-centric within a BX x by tile (by = 16
@@ -169,6 +168,7 @@ __device__ __forceinline__ void outflow_adj(const StepArgs<T> &a, const Fwd<T> &
 //     leaving its contributions to the two cells and the adjoint of its old q;
 //  D. every tile cell gathers the contributions of its four faces.
 template <typename T> struct TileRows { static constexpr int v = 16; };
+constexpr int kTileGauges = 32;
 template <> struct TileRows<double> { static constexpr int v = 8; };
 
 template <typename T>
@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(BX * TileRows<T>::v) adj_step_kernel(const Adj
     __shared__ T sL[BYT + 2][BX + 2];                          // cells I0-1 .., J0-1 ..
     __shared__ T cXl[BYT][BX + 1], cXr[BYT][BX + 1], cXn[BYT][BX + 1];
     __shared__ T cYl[BYT + 1][BX], cYr[BYT + 1][BX], cYn[BYT + 1][BX];
+    __shared__ int s_ng, s_gk[kTileGauges];                     // gauges inside the tile and its halo
     const StepArgs<T> &a = A.fwd;
     const Geom &G = a.geo;
     const int nx = G.nx, ny = G.ny;
@@ -245,7 +246,30 @@ __global__ void __launch_bounds__(BX * TileRows<T>::v) adj_step_kernel(const Adj
         sY[lj][li] = v;
     }
     __syncthreads();
-    // B. adjoint of the unclipped depth (gauge seeds included)
+    // B. adjoint of the unclipped depth (gauge seeds included).  The gauges inside
+    // the tile and its halo are listed first (flags in gauge order), so that a
+    // cell scans only those; a tile holding more than kTileGauges scans them all.
+    if (tid == 0) s_ng = 0;
+    __syncthreads();
+    for (int gk = tid; gk < A.n_gauges; gk += NT) {
+        const int64_t flat = A.gauge_cells[gk];
+        const int gj = (int)(flat / nx), gi = (int)(flat - (int64_t)gj * nx);
+        if (gj >= J0 - 1 && gj <= J0 + BYT && gi >= I0 - 1 && gi <= I0 + BX) {
+            const int slot = atomicAdd(&s_ng, 1);
+            if (slot < kTileGauges) s_gk[slot] = gk;
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && s_ng > 1 && s_ng <= kTileGauges) {   // restore gauge order: repeated gauges add up in order
+        for (int x = 1; x < s_ng; x++)
+            for (int y = x; y > 0 && s_gk[y - 1] > s_gk[y]; y--) {
+                const int tmp = s_gk[y];
+                s_gk[y] = s_gk[y - 1];
+                s_gk[y - 1] = tmp;
+            }
+    }
+    __syncthreads();
+    const int ng_tile = s_ng;
     for (int t = tid; t < (BYT + 2) * (BX + 2); t += NT) {
         const int lj = t / (BX + 2), li = t % (BX + 2);
         const int j = J0 - 1 + lj, i = I0 - 1 + li;
@@ -254,9 +278,16 @@ __global__ void __launch_bounds__(BX * TileRows<T>::v) adj_step_kernel(const Adj
             const T hu = F.update(sh[lj + 1][li + 1], sX[lj][li], sX[lj][li + 1], sY[lj][li], sY[lj + 1][li]);
             if (!(hu < T(0))) {
                 v = A.lh[(size_t)j * P + i];
-                const int64_t flat = (int64_t)j * nx + i;
-                for (int gk = 0; gk < A.n_gauges; gk++)   // repeated gauges add up in order
-                    if (A.gauge_cells[gk] == flat) v = v + T(A.seed[gk]);
+                if (ng_tile > 0) {
+                    const int64_t flat = (int64_t)j * nx + i;
+                    if (ng_tile <= kTileGauges) {
+                        for (int x = 0; x < ng_tile; x++)
+                            if (A.gauge_cells[s_gk[x]] == flat) v = v + T(A.seed[s_gk[x]]);
+                    } else {
+                        for (int gk = 0; gk < A.n_gauges; gk++)
+                            if (A.gauge_cells[gk] == flat) v = v + T(A.seed[gk]);
+                    }
+                }
             }
         }
         sL[lj][li] = v;
@@ -273,15 +304,11 @@ __global__ void __launch_bounds__(BX * TileRows<T>::v) adj_step_kernel(const Adj
             const int sj = lj + 2, sl = li + 1, sr = li + 2;     // staging coordinates of L and R
             if (fi == 0) {
                 const T mu = A.lqx[r] + dtdx * lR;
-                double gnv = 0.0;
-                outflow_adj(a, F, 0, j, sh[sj][sr], sn[sj][sr], mu, cr, gnv);
-                cn = T(gnv);
+                outflow_adj(a, F, 0, j, sh[sj][sr], sn[sj][sr], mu, cr, cn);
                 A.lqx_out[r] = T(0);
             } else if (fi == nx) {
                 const T mu = A.lqx[r + nx] - dtdx * lL;
-                double gnv = 0.0;
-                outflow_adj(a, F, 1, j, sh[sj][sl], sn[sj][sl], mu, cl, gnv);
-                cn = T(gnv);
+                outflow_adj(a, F, 1, j, sh[sj][sl], sn[sj][sl], mu, cl, cn);
                 A.lqx_out[r + nx] = T(0);
             } else {
                 const T mu = A.lqx[r + fi] + dtdx * (lR - lL);
@@ -313,16 +340,12 @@ __global__ void __launch_bounds__(BX * TileRows<T>::v) adj_step_kernel(const Adj
             const int sc = li + 2, sb = lj + 1, st = lj + 2;     // staging coordinates of L (below) and R
             if (fj == 0) {
                 const T mu = A.lqy[i] + dtdx * lR;
-                double gnv = 0.0;
-                outflow_adj(a, F, 2, i, sh[st][sc], sn[st][sc], mu, cr, gnv);
-                cn = T(gnv);
+                outflow_adj(a, F, 2, i, sh[st][sc], sn[st][sc], mu, cr, cn);
                 A.lqy_out[i] = T(0);
             } else if (fj == ny) {
                 const size_t c = (size_t)(ny - 1) * P + i;
                 const T mu = A.lqy[c + P] - dtdx * lL;
-                double gnv = 0.0;
-                outflow_adj(a, F, 3, i, sh[sb][sc], sn[sb][sc], mu, cl, gnv);
-                cn = T(gnv);
+                outflow_adj(a, F, 3, i, sh[sb][sc], sn[sb][sc], mu, cl, cn);
                 A.lqy_out[c + P] = T(0);
             } else {
                 const size_t c = (size_t)fj * P + i;
@@ -353,9 +376,11 @@ __global__ void __launch_bounds__(BX * TileRows<T>::v) adj_step_kernel(const Adj
     const size_t c = (size_t)j * P + i;
     const T lu = sL[ty + 1][tx + 1];
     const T lh = lu + cXr[ty][tx] + cXl[ty][tx + 1] + cYr[ty][tx] + cYl[ty + 1][tx];
-    const double gn = (double)cXn[ty][tx] + (double)cXn[ty][tx + 1] + (double)cYn[ty][tx] + (double)cYn[ty + 1][tx];
+    // this step's dL/dn of the cell in the working precision, then one add into the
+    // double accumulator over the sweep
+    const T gs = (cXn[ty][tx] + cXn[ty][tx + 1]) + (cYn[ty][tx] + cYn[ty + 1][tx]);
     A.lh_out[c] = lh;
-    A.gn[c] += gn;
+    A.gn[c] += (double)gs;
     if (i == 0 || j == 0 || i == nx - 1 || j == ny - 1) A.lhu[c] = lu;   // read by the inflow pass
 }
 

@@ -54,8 +54,15 @@ __device__ __forceinline__ void set(float4 &v, int k, float x)
 
 // One block's work: warps cover consecutive 128-column strips of strip block
 // bx, all on the row chunk by of `rows` rows; step is the step inside the epoch.
-__device__ __forceinline__ void stream_body(const StepArgs<float> &a, const int step, const int want_hmax, const int bx,
-                                            const int by, const int rows, unsigned char *smem_raw, double *red)
+//
+// ring_base counts the rows this warp staged in earlier calls (a persistent
+// block calls it once per work item): the slot and phase of staged row idx are
+// those of ring_base + idx.  fresh: the ring's barriers still need their
+// initialisation.  Returns true if a wait on a copy timed out (the status word
+// then has the timeout bit).
+__device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int step, const int want_hmax, const int bx,
+                                            const int by, const int rows, unsigned char *smem_raw, double *red,
+                                            uint32_t &ring_base, const bool fresh)
 {
     const Geom &G = a.geo;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -91,13 +98,13 @@ __device__ __forceinline__ void stream_body(const StepArgs<float> &a, const int 
     const uint32_t seg_bytes = (uint32_t)(ce - cs) * 4u;
     const float *fields[kFields] = {a.h, a.z, a.n, a.qx, a.qy};
 
-    if (active && lane == 0) {
+    if (fresh && lane == 0) {                 // every warp: it may be idle here and busy on a later item
         for (int s = 0; s < kDepth; s++) mbar_init(&ring.bar[s], 1);
         fence_mbar_init();
     }
     __syncwarp();
     auto issue = [&](int idx) {
-        const int s = idx % kDepth;
+        const uint32_t s = (ring_base + (uint32_t)idx) % kDepth;
         const size_t row = (size_t)(jstart + idx) * P + cs;
         mbar_arrive_expect_tx(&ring.bar[s], seg_bytes * kFields);
 #pragma unroll
@@ -106,6 +113,7 @@ __device__ __forceinline__ void stream_body(const StepArgs<float> &a, const int 
     int issued = 0, consumed = 0;
     bool abort = false;
     if (active && lane == 0) {
+        fence_proxy_async();              // this warp's reads of an earlier item come first
         for (; issued < min(kDepth, nload); issued++) issue(issued);
     }
 
@@ -118,8 +126,9 @@ __device__ __forceinline__ void stream_body(const StepArgs<float> &a, const int 
             float4 ch = make_float4(0, 0, 0, 0), cz = ch, cn = ch, cqx = ch, cqy = ch;
             float hW = 0.f, zW = 0.f, nW = 0.f, hE = 0.f, zE = 0.f, nE = 0.f, qxE = 0.f;
             if (j < ny) {
-                const int s = idx % kDepth;
-                bool ok = mbar_wait_bounded(&ring.bar[s], (uint32_t)((idx / kDepth) & 1), kBudgetNs);
+                const uint32_t g = ring_base + (uint32_t)idx;
+                const uint32_t s = g % kDepth;
+                bool ok = mbar_wait_bounded(&ring.bar[s], (g / kDepth) & 1u, kBudgetNs);
                 if (__any_sync(0xffffffffu, !ok)) {
                     abort = true;
                     break;
@@ -288,12 +297,15 @@ __device__ __forceinline__ void stream_body(const StepArgs<float> &a, const int 
         if (abort) {
             // leave no bulk copy writing into shared memory after exit
             if (lane == 0) {
-                for (int k = consumed; k < issued; k++)
-                    mbar_wait_bounded(&ring.bar[k % kDepth], (uint32_t)((k / kDepth) & 1), kBudgetNs);
+                for (int k = consumed; k < issued; k++) {
+                    const uint32_t g = ring_base + (uint32_t)k;
+                    mbar_wait_bounded(&ring.bar[g % kDepth], (g / kDepth) & 1u, kBudgetNs);
+                }
                 atomicOr(&a.ctrl->status, kStatusTimeout);
             }
             __syncwarp();
         }
+        if (!abort) ring_base += (uint32_t)nload;
     }
     double bo = block_reduce<false>(vout, red);
     if (threadIdx.x == 0 && bo != 0.0) atomicAdd(&a.ctrl->V_out, dtd * bo);
@@ -312,13 +324,15 @@ __device__ __forceinline__ void stream_body(const StepArgs<float> &a, const int 
         a.ctrl->V_in = vin;
         a.ctrl->t = a.t_list[step + 1];
     }
+    return abort;
 }
 
 __global__ void __launch_bounds__(kMaxWarps * 32, 5) step_stream_kernel(const StepArgs<float> a, const int rows)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
-    stream_body(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, smem_raw, red);
+    uint32_t ring_base = 0;
+    stream_body(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, smem_raw, red, ring_base, true);
 }
 
 // Many grids in one launch: block b belongs to the scenario whose block range
@@ -341,7 +355,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 5)
     const int strips = (a.geo.nx + 127) / 128;
     const int nbx = (strips + nwarps - 1) / nwarps;
     const int local = b - base[lo];
-    stream_body(a, step, want_hmax, local % nbx, local / nbx, rows, smem_raw, red);
+    uint32_t ring_base = 0;
+    stream_body(a, step, want_hmax, local % nbx, local / nbx, rows, smem_raw, red, ring_base, true);
 }
 
 cudaError_t configure(int warps)
