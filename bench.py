@@ -338,7 +338,7 @@ def ensemble_throughput(F, torch, single_value: float, n: int = 96, steps: int =
         probs.append(p)
     ens = F.Ensemble(probs)
     tune = autotune.tune_ensemble(ens, use_cache=False)
-    spg = tune["shape"][2]
+    spg = tune["shape"][3]                 # (K, warps, rows, steps per graph)
     steps = max(spg, steps // spg * spg)
     ens.step(spg)
     stream = torch.cuda.current_stream()

@@ -236,8 +236,10 @@ const char *flood_last_error(const flood_handle *h);
  * release policies and climate scenarios are the use): n independent FP32
  * scenarios, each with its own grid, DEM, Manning field and boundary
  * sections (arguments as for flood_create, element k of each array), advanced
- * together.  Every step is one launch of the stream kernel over the blocks of
- * all scenarios, largest grid first; each scenario keeps its own CFL time
+ * together.  Every launch covers all scenarios, largest grid first: one step
+ * of the stream kernel over their blocks (default), or, after
+ * flood_ensemble_set_kernel(TILED, K), K steps of the temporal-blocking kernel
+ * over their (chunk, strip) items.  Each scenario keeps its own CFL time
  * step, Eq. 6 inflow and ledger.  Whole epochs are captured once into a CUDA
  * graph (steps_per_graph steps, a multiple of epoch_steps) and replayed.
  * opts applies to every scenario (kernel and use_graph are set by the
@@ -249,9 +251,17 @@ typedef struct flood_ensemble flood_ensemble;
 flood_status flood_ensemble_create(int32_t n, const flood_grid *grids, const void *const *dems,
                                    const void *const *mannings, const flood_bc_section *const *sections,
                                    const int32_t *n_sections, const flood_opts *opts, flood_ensemble **out);
-/* Launch shape: warps per block (1..4), rows per chunk, steps per graph replay, graph on/off. */
+/* Launch shape: warps per block (1..4, stream kernel), rows per chunk (stream
+ * blocks, or rows per (chunk, strip) item of the tiled kernel), steps per
+ * graph replay, graph on/off.  FLOOD_ERR_ARG on values out of range. */
 flood_status flood_ensemble_set_launch(flood_ensemble *e, int32_t warps, int32_t rows, int32_t steps_per_graph,
                                        int32_t use_graph);
+/* Kernel for the steps: FLOOD_KERNEL_STREAM (one step per launch) or
+ * FLOOD_KERNEL_TILED with steps_per_launch K (1..4, dividing epoch_steps;
+ * 0 = 4), the temporal blocking of Eq. 3-4 over K steps per launch; a launch
+ * never crosses an epoch end.  FLOOD_ERR_ARG otherwise.  Drops the captured
+ * graphs.  No counterpart in the paper: a launch-configuration choice. */
+flood_status flood_ensemble_set_kernel(flood_ensemble *e, int32_t kernel, int32_t steps_per_launch);
 flood_status flood_ensemble_step(flood_ensemble *e, int64_t n_steps);
 flood_handle *flood_ensemble_member(flood_ensemble *e, int32_t k);
 flood_status flood_ensemble_destroy(flood_ensemble *e);

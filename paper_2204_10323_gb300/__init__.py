@@ -97,14 +97,15 @@ def _load():
                                         C.POINTER(C.POINTER(flood_bc_section)), C.POINTER(i32),
                                         C.POINTER(flood_opts), C.POINTER(vp)]
     L.flood_ensemble_set_launch.argtypes = [vp, i32, i32, i32, i32]
+    L.flood_ensemble_set_kernel.argtypes = [vp, i32, i32]
     L.flood_ensemble_step.argtypes = [vp, i64]
     L.flood_ensemble_member.argtypes = [vp, i32]
     L.flood_ensemble_member.restype = vp
     L.flood_ensemble_destroy.argtypes = [vp]
     L.flood_ensemble_last_error.argtypes = [vp]
     L.flood_ensemble_last_error.restype = C.c_char_p
-    for name in ("flood_ensemble_create", "flood_ensemble_set_launch", "flood_ensemble_step",
-                 "flood_ensemble_destroy"):
+    for name in ("flood_ensemble_create", "flood_ensemble_set_launch", "flood_ensemble_set_kernel",
+                 "flood_ensemble_step", "flood_ensemble_destroy"):
         getattr(L, name).restype = C.c_int
     for name in ("flood_create", "flood_step", "flood_sync", "flood_read", "flood_write_state",
                  "flood_set_clock", "flood_set_manning", "flood_run_gauges", "flood_adjoint", "flood_destroy"):
@@ -347,6 +348,10 @@ def flood_ensemble_set_launch(e, warps, rows, steps_per_graph, use_graph):
     _ens_check(lib().flood_ensemble_set_launch(e, int(warps), int(rows), int(steps_per_graph), int(use_graph)), e)
 
 
+def flood_ensemble_set_kernel(e, kernel, steps_per_launch):
+    _ens_check(lib().flood_ensemble_set_kernel(e, int(kernel), int(steps_per_launch)), e)
+
+
 def flood_ensemble_step(e, n_steps):
     _ens_check(lib().flood_ensemble_step(e, int(n_steps)), e)
 
@@ -419,6 +424,10 @@ class Ensemble:
     def set_launch(self, warps=4, rows=64, steps_per_graph=None, use_graph=True):
         E = self.problems[0].opts.epoch_steps
         flood_ensemble_set_launch(self.e, warps, rows, steps_per_graph or E, int(use_graph))
+
+    def set_kernel(self, kernel=KERNEL_STREAM, steps_per_launch=0):
+        """KERNEL_STREAM (one step per launch) or KERNEL_TILED with K steps per launch."""
+        flood_ensemble_set_kernel(self.e, kernel, steps_per_launch)
 
     def step(self, n_steps: int):
         flood_ensemble_step(self.e, n_steps)

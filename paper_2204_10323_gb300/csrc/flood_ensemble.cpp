@@ -1,9 +1,11 @@
 // flood_ensemble.cpp -- many independent scenarios (own grid size, terrain,
-// roughness, hydrograph) advanced together: per step one launch of the
-// stream kernel covers the blocks of every scenario (largest first), and
-// whole CFL epochs (per-scenario time step and Eq. 6 inflow, then the steps)
-// are captured once into a CUDA graph and replayed.  Each scenario is an
-// ordinary FP32 handle, so flood_read / flood_write_state work on it.
+// roughness, hydrograph) advanced together: one launch covers every scenario
+// (largest first), either one step of the stream kernel over the blocks of
+// all scenarios, or K steps of the temporal-blocking kernel over their
+// (chunk, strip) items; whole CFL epochs (per-scenario time step and Eq. 6
+// inflow, then the steps) are captured once into a CUDA graph and replayed.
+// Each scenario is an ordinary FP32 handle, so flood_read / flood_write_state
+// work on it.
 #include "flood.h"
 
 #include <cuda_runtime.h>
@@ -25,13 +27,17 @@ struct flood_ensemble {
     int64_t step = 0;
     cudaStream_t stream = nullptr;
     int warps = 4, rows = 64, steps_per_graph = 16;
+    int kernel = FLOOD_KERNEL_STREAM, k_steps = 4;   // TILED: k_steps per launch, rows per item
     StepArgs<float> *table[2] = {nullptr, nullptr};   // per parity of the ping-pong buffers
     int *base = nullptr;                   // block prefix, n + 1
     int total_blocks = 0;
+    int *tbase = nullptr;                  // tiled item prefix, n + 1
+    int total_items = 0;
     EpochArgs<float> *etab = nullptr;      // per member: epoch bookkeeping arguments
     int2 *tasks = nullptr;                 // (member, inflow section) pairs
     int n_tasks = 0;
     std::vector<cudaGraphExec_t> graphs;   // [parity]
+    int graph_launches = 0;                // step launches in one graph (each flips the buffers)
     int use_graph = 1;
     std::string err;
     flood_handle *owner = nullptr;         // member 0: allocations for the tables
@@ -58,10 +64,13 @@ void drop_graphs(flood_ensemble *e)
 flood_status build_tables(flood_ensemble *e)
 {
     const int n = (int)e->members.size();
-    std::vector<int> base(n + 1, 0);
-    for (int k = 0; k < n; k++)
+    std::vector<int> base(n + 1, 0), tbase(n + 1, 0);
+    for (int k = 0; k < n; k++) {
         base[k + 1] = base[k] + stream_blocks(e->members[e->order[k]]->geo, e->warps, e->rows);
+        tbase[k + 1] = tbase[k] + tiled_items(e->members[e->order[k]]->geo, e->rows);
+    }
     e->total_blocks = base[n];
+    e->total_items = tbase[n];
     for (int p = 0; p < 2; p++) {
         std::vector<StepArgs<float>> t(n);
         for (int k = 0; k < n; k++) {
@@ -77,14 +86,18 @@ flood_status build_tables(flood_ensemble *e)
     }
     cudaError_t c = cudaMemcpyAsync(e->base, base.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, e->stream);
     if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+    c = cudaMemcpyAsync(e->tbase, tbase.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, e->stream);
+    if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
     c = cudaStreamSynchronize(e->stream);
     if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
     drop_graphs(e);
     return FLOOD_OK;
 }
 
-// One step of every member (epoch bookkeeping per member when due).
-flood_status ensemble_step(flood_ensemble *e, cudaStream_t st)
+// One launch for every member: one step (stream kernel) or up to k_steps steps
+// (temporal blocking), never past the end of the epoch or beyond `limit`
+// steps; epoch bookkeeping per member when due.  Returns the steps taken in *k.
+flood_status ensemble_step(flood_ensemble *e, int64_t limit, cudaStream_t st, int *k)
 {
     const int E = e->E;
     const int s = (int)(e->step % E);
@@ -93,14 +106,24 @@ flood_status ensemble_step(flood_ensemble *e, cudaStream_t st)
         if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
     }
     const int parity = e->members[0]->cur;
-    cudaError_t c = launch_step_stream_ensemble(e->table[parity], e->base, (int)e->members.size(), e->total_blocks,
-                                                e->warps, e->rows, s, s == E - 1 ? 1 : 0, st);
+    const int n = (int)e->members.size();
+    int steps = 1;
+    cudaError_t c;
+    if (e->kernel == FLOOD_KERNEL_TILED) {
+        steps = (int)std::min<int64_t>(e->k_steps, std::min<int64_t>(E - s, limit));
+        c = launch_step_tiled_ensemble(e->table[parity], e->tbase, n, e->total_items, e->rows, steps, s,
+                                       s + steps == E ? 1 : 0, st);
+    } else {
+        c = launch_step_stream_ensemble(e->table[parity], e->base, n, e->total_blocks, e->warps, e->rows, s,
+                                        s == E - 1 ? 1 : 0, st);
+    }
     if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
     for (flood_handle *h : e->members) {
         h->cur = 1 - h->cur;
-        h->step += 1;
+        h->step += steps;
     }
-    e->step += 1;
+    e->step += steps;
+    *k = steps;
     return FLOOD_OK;
 }
 
@@ -118,8 +141,10 @@ flood_status capture(flood_ensemble *e, int parity)
     }
     c = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     flood_status fs = FLOOD_OK;
+    int launches = 0;
     if (c == cudaSuccess)
-        for (int k = 0; k < e->steps_per_graph && !fs; k++) fs = ensemble_step(e, cap);
+        for (int k = 0, taken = 0; k < e->steps_per_graph && !fs; k += taken, launches++)
+            fs = ensemble_step(e, e->steps_per_graph - k, cap, &taken);
     cudaGraph_t graph = nullptr;
     cudaError_t c2 = cudaStreamEndCapture(cap, &graph);
     cudaStreamDestroy(cap);
@@ -140,6 +165,7 @@ flood_status capture(flood_ensemble *e, int parity)
         e->graphs[parity] = nullptr;
         return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
     }
+    e->graph_launches = launches;
     return FLOOD_OK;
 }
 
@@ -197,6 +223,7 @@ extern "C" flood_status flood_ensemble_create(int32_t n, const flood_grid *grids
         }
     }
     e->base = (int *)dev_alloc(e->owner, (n + 1) * sizeof(int));
+    e->tbase = (int *)dev_alloc(e->owner, (n + 1) * sizeof(int));
     e->etab = (EpochArgs<float> *)dev_alloc(e->owner, n * sizeof(EpochArgs<float>));
     std::vector<EpochArgs<float>> et(n);
     std::vector<int2> tk;
@@ -221,7 +248,7 @@ extern "C" flood_status flood_ensemble_create(int32_t n, const flood_grid *grids
     }
     e->n_tasks = (int)tk.size();
     e->tasks = (int2 *)dev_alloc(e->owner, std::max<size_t>(tk.size(), 1) * sizeof(int2));
-    if (!e->base || !e->etab || !e->tasks ||
+    if (!e->base || !e->tbase || !e->etab || !e->tasks ||
         cudaMemcpyAsync(e->etab, et.data(), n * sizeof(EpochArgs<float>), cudaMemcpyHostToDevice, e->stream) ||
         (tk.size() &&
          cudaMemcpyAsync(e->tasks, tk.data(), tk.size() * sizeof(int2), cudaMemcpyHostToDevice, e->stream))) {
@@ -251,6 +278,20 @@ extern "C" flood_status flood_ensemble_set_launch(flood_ensemble *e, int32_t war
     return build_tables(e);
 }
 
+extern "C" flood_status flood_ensemble_set_kernel(flood_ensemble *e, int32_t kernel, int32_t steps_per_launch)
+{
+    if (!e) return efail(nullptr, FLOOD_ERR_ARG, "ensemble is NULL");
+    if (kernel != FLOOD_KERNEL_STREAM && kernel != FLOOD_KERNEL_TILED)
+        return efail(e, FLOOD_ERR_ARG, "ensemble kernel must be FLOOD_KERNEL_STREAM or FLOOD_KERNEL_TILED");
+    const int K = steps_per_launch > 0 ? steps_per_launch : 4;
+    if (kernel == FLOOD_KERNEL_TILED && (K > 4 || e->E % K != 0))
+        return efail(e, FLOOD_ERR_ARG, "steps_per_launch must divide epoch_steps and be <= 4");
+    e->kernel = kernel;
+    e->k_steps = kernel == FLOOD_KERNEL_TILED ? K : 1;
+    drop_graphs(e);
+    return FLOOD_OK;
+}
+
 extern "C" flood_status flood_ensemble_step(flood_ensemble *e, int64_t n_steps)
 {
     if (!e) return efail(nullptr, FLOOD_ERR_ARG, "ensemble is NULL");
@@ -267,7 +308,7 @@ extern "C" flood_status flood_ensemble_step(flood_ensemble *e, int64_t n_steps)
             }
             cudaError_t c = cudaGraphLaunch(e->graphs[parity], e->stream);
             if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
-            const int flips = e->steps_per_graph & 1;
+            const int flips = e->graph_launches & 1;
             for (flood_handle *h : e->members) {
                 h->cur ^= flips;
                 h->step += e->steps_per_graph;
@@ -276,9 +317,10 @@ extern "C" flood_status flood_ensemble_step(flood_ensemble *e, int64_t n_steps)
             n_steps -= e->steps_per_graph;
             continue;
         }
-        flood_status st = ensemble_step(e, e->stream);
+        int taken = 0;
+        flood_status st = ensemble_step(e, n_steps, e->stream, &taken);
         if (st) return st;
-        n_steps -= 1;
+        n_steps -= taken;
     }
     return FLOOD_OK;
 }
@@ -298,6 +340,7 @@ extern "C" flood_status flood_ensemble_destroy(flood_ensemble *e)
         for (int p = 0; p < 2; p++)
             if (e->table[p]) dev_free(e->owner, e->table[p]);
         if (e->base) dev_free(e->owner, e->base);
+        if (e->tbase) dev_free(e->owner, e->tbase);
         if (e->etab) dev_free(e->owner, e->etab);
         if (e->tasks) dev_free(e->owner, e->tasks);
     }

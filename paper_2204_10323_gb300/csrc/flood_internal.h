@@ -89,6 +89,11 @@ cudaError_t launch_step_stream_ensemble(const StepArgs<float> *table, const int 
                                         int warps, int rows, int step, int want_hmax, cudaStream_t st);
 // Blocks of one grid for the stream kernel, and the (warps, rows) a tile pair selects.
 int stream_blocks(const Geom &g, int warps, int rows);
+// Temporal blocking over many grids: the (chunk, strip) items of grid k are
+// base[k] .. base[k+1] - 1 (tiled_items per grid), k_steps steps from s0.
+int tiled_items(const Geom &g, int chunk_rows);
+cudaError_t launch_step_tiled_ensemble(const StepArgs<float> *table, const int *base, int n, int total_items,
+                                       int chunk_rows, int k_steps, int s0, int want_hmax, cudaStream_t st);
 void stream_launch_shape(const Geom &g, int tile_x, int tile_y, int *warps, int *rows);
 cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st);
 size_t tiled_smem_bytes(int tile_x, int tile_y, int k);

@@ -60,292 +60,283 @@ __device__ __forceinline__ void set(float4 &v, int k, float x)
     else v.w = x;
 }
 
-template <int K>
-__global__ void __launch_bounds__(K * 32, K == 4 ? 5 : 1) step_tiled_kernel(const StepArgs<float> a)
+// This thread's share of one grid's ledger terms over a launch.
+struct TiledLedger {
+    double vout = 0.0, vclip = 0.0;      // folded from the float runs below
+    float hmax = 0.0f;
+    bool nan_seen = false;
+};
+
+__device__ __forceinline__ FastConst tiled_const(const StepArgs<float> &a)
 {
-    using Smem = PipeSmem<K>;
-    constexpr int kDZ = Smem::kDZ;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
-    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    const Geom &G = a.geo;
+    const float dt = (float)a.ctrl->dt, dx = (float)G.dx, g = (float)G.g;
+    FastConst Kc;
+    Kc.gdt = g * dt;
+    Kc.a1 = Kc.gdt / dx;
+    Kc.h_dry = (float)G.h_dry;
+    Kc.dtdx = dt / dx;
+    return Kc;
+}
+
+// One work item: the pipeline over strip `strip`, rows [y0, y1) of grid a, for
+// steps s0 .. s0 + K - 1 of the epoch.  base counts the rows staged by earlier
+// items (ring slot and phase of staged row idx are those of base + idx).
+// Returns true (uniformly over the block) if a wait on a copy timed out; the
+// copies in flight are then drained and the status word has the timeout bit.
+template <int K>
+__device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s0, const FastConst &Kc,
+                                           const int strip, const int y0, const int y1, PipeSmem<K> &sm,
+                                           uint32_t &base, TiledLedger &L)
+{
+    constexpr int kDZ = PipeSmem<K>::kDZ;
     const Geom &G = a.geo;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lvl = warp + 1;                         // this warp's time level
     const int nx = G.nx, ny = G.ny, P = G.pitch;
-    // work items (chunk, strip) in chunk-major order, block b takes items b, b + grid, ...
-    const int n_strips = a.tile_x, chunk_rows = a.tile_y;
-    const int n_items = n_strips * ((ny + chunk_rows - 1) / chunk_rows);
-    const int step = a.s + (lvl - 1);                 // this level's step in the epoch
-
-    const double dtd = a.ctrl->dt;
-    FastConst Kc;
-    {
-        const float dt = (float)dtd, dx = (float)G.dx, g = (float)G.g;
-        Kc.gdt = g * dt;
-        Kc.a1 = Kc.gdt / dx;
-        Kc.h_dry = (float)G.h_dry;
-        Kc.dtdx = dt / dx;
-    }
-    double vout = 0.0, vclip = 0.0;                   // folded from the float runs below
-    float hmax = 0.0f;
-    bool nan_seen = false;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kPF; s++) mbar_init(&sm.bar[s], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    // rows staged by earlier segments: ring slot and phase of staged row idx of
-    // this segment are those of the running count base + idx
-    uint32_t base = 0;
+    const int step = s0 + (lvl - 1);                  // this level's step in the epoch
     int issued = 0, consumed = 0;
     bool abort = false;
-    for (int item = blockIdx.x; item < n_items && !abort; item += gridDim.x) {
-        const int strip = item % n_strips;
-        const int y0 = (item / n_strips) * chunk_rows;
-        const int y1 = min(y0 + chunk_rows, ny);
-        const int x0 = strip * kOut - kHalo;
-        const int c0 = x0 + 4 * lane;
-        const int own_lo = strip * kOut, own_hi = min(strip * kOut + kOut, nx);
-        const int jb = max(y0 - K, 0);
-        const int jload_hi = min(y1 + K - 1, ny - 1);     // last staged row
-        const int nload = jload_hi - jb + 1;
-        const int jlast = min(y1, ny) + 2 * (K - 1);      // last tick: level K reaches row min(y1, ny)
-        const int rstart = jb == 0 ? 0 : jb + (lvl - 1);  // first row this level sees (halo row if jb > 0)
-        const int cs = max(x0, 0);
-        const int ce = min(x0 + 128, P);
-        const int so = cs - x0;
-        const uint32_t seg_bytes = (uint32_t)(ce - cs) * 4u;
-        auto issue = [&](int idx) {
-            const int j = jb + idx;
-            const uint32_t slot = (base + (uint32_t)idx) % kPF;
-            const size_t row = (size_t)j * P + cs;
-            uint64_t *bar = &sm.bar[slot];
-            mbar_arrive_expect_tx(bar, seg_bytes * 5u);
-            float *hq = &sm.hq[slot][0][0];
-            float *zn = &sm.zn[j % kDZ][0][0];
-            bulk_copy_g2s(hq + 0 * 128 + so, a.h + row, seg_bytes, bar);
-            bulk_copy_g2s(hq + 1 * 128 + so, a.qx + row, seg_bytes, bar);
-            bulk_copy_g2s(hq + 2 * 128 + so, a.qy + row, seg_bytes, bar);
-            bulk_copy_g2s(zn + 0 * 128 + so, a.z + row, seg_bytes, bar);
-            bulk_copy_g2s(zn + 1 * 128 + so, a.n + row, seg_bytes, bar);
-        };
-        issued = 0;
-        consumed = 0;
-        if (threadIdx.x == 0) {
-            fence_proxy_async();                          // earlier segments' reads of the rings come first
-            for (; issued < min(kPF, nload); issued++) issue(issued);
-        }
+    const int x0 = strip * kOut - kHalo;
+    const int c0 = x0 + 4 * lane;
+    const int own_lo = strip * kOut, own_hi = min(strip * kOut + kOut, nx);
+    const int jb = max(y0 - K, 0);
+    const int jload_hi = min(y1 + K - 1, ny - 1);     // last staged row
+    const int nload = jload_hi - jb + 1;
+    const int jlast = min(y1, ny) + 2 * (K - 1);      // last tick: level K reaches row min(y1, ny)
+    const int rstart = jb == 0 ? 0 : jb + (lvl - 1);  // first row this level sees (halo row if jb > 0)
+    const int cs = max(x0, 0);
+    const int ce = min(x0 + 128, P);
+    const int so = cs - x0;
+    const uint32_t seg_bytes = (uint32_t)(ce - cs) * 4u;
+    auto issue = [&](int idx) {
+        const int j = jb + idx;
+        const uint32_t slot = (base + (uint32_t)idx) % kPF;
+        const size_t row = (size_t)j * P + cs;
+        uint64_t *bar = &sm.bar[slot];
+        mbar_arrive_expect_tx(bar, seg_bytes * 5u);
+        float *hq = &sm.hq[slot][0][0];
+        float *zn = &sm.zn[j % kDZ][0][0];
+        bulk_copy_g2s(hq + 0 * 128 + so, a.h + row, seg_bytes, bar);
+        bulk_copy_g2s(hq + 1 * 128 + so, a.qx + row, seg_bytes, bar);
+        bulk_copy_g2s(hq + 2 * 128 + so, a.qy + row, seg_bytes, bar);
+        bulk_copy_g2s(zn + 0 * 128 + so, a.z + row, seg_bytes, bar);
+        bulk_copy_g2s(zn + 1 * 128 + so, a.n + row, seg_bytes, bar);
+    };
+    if (threadIdx.x == 0) {
+        fence_proxy_async();                          // earlier items' reads of the rings come first
+        for (; issued < min(kPF, nload); issued++) issue(issued);
+    }
 
-        bool own_cell[4], own_wface[4], in_col[4], in_wface[4], all_cell = true, all_wface = true;
-        const bool edge_lane = c0 <= 0 || c0 + 3 >= nx;   // holds a column outside (0, nx)
+    bool own_cell[4], own_wface[4], in_col[4], in_wface[4], all_cell = true, all_wface = true;
+    const bool edge_lane = c0 <= 0 || c0 + 3 >= nx;   // holds a column outside (0, nx)
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const int c = c0 + k;
-            in_col[k] = c >= 0 && c < nx;                 // a cell of the grid (its south face exists)
-            in_wface[k] = c > 0 && c < nx;                // an interior west face
-            own_cell[k] = c >= own_lo && c < own_hi;
-            own_wface[k] = c >= own_lo && (c < own_hi || (c == nx && own_hi == nx));
-            all_cell &= own_cell[k];
-            all_wface &= own_wface[k];
-        }
+    for (int k = 0; k < 4; k++) {
+        const int c = c0 + k;
+        in_col[k] = c >= 0 && c < nx;                 // a cell of the grid (its south face exists)
+        in_wface[k] = c > 0 && c < nx;                // an interior west face
+        own_cell[k] = c >= own_lo && c < own_hi;
+        own_wface[k] = c >= own_lo && (c < own_hi || (c == nx && own_hi == nx));
+        all_cell &= own_cell[k];
+        all_wface &= own_wface[k];
+    }
 
-        // this level's previous row: input depth and the new faces computed for it
-        float4 hp = make_float4(0, 0, 0, 0), qxw_p = hp, qys_p = hp;
-        float qxe_p = 0.0f;
-        // runs of up to 32 ticks; the float partial sums of the boundary outflow (fq)
-        // and the clipped depth (fc) are folded into the double ledger after each run
-        for (int j0 = jb; j0 <= jlast && !abort; j0 += 32) {
-            float fq = 0.0f, fc = 0.0f;
-            const int jend = min(j0 + 31, jlast);
-            for (int j = j0; j <= jend; j++) {
-                const int r = j - 2 * (lvl - 1);
-                // ---- level 1 waits for its staged row; the other levels only read rows that
-                // level 1 waited for at earlier ticks (ordered by the end-of-tick barrier)
-                bool stop = false;
-                if (lvl == 1 && r >= jb && r <= jload_hi) {
-                    const uint32_t g = base + (uint32_t)(r - jb);
-                    const int ok = mbar_wait_bounded(&sm.bar[g % kPF], (g / kPF) & 1u, kBudgetNs) ? 1 : 0;
-                    stop = !__all_sync(0xffffffffu, ok);
-                }
-                if (!stop && r >= rstart && r <= ny && r <= y1 + K - lvl) {
-                    // current row inputs
-                    float4 ch = make_float4(0, 0, 0, 0), cqx = ch, cqy = ch, cz = ch, cn = ch, pz = ch, pn = ch;
-                    if (r < ny) {
-                        if (lvl == 1) {
-                            const float *hq = &sm.hq[(base + (uint32_t)(r - jb)) % kPF][0][0];
-                            ch = lds4(hq + 0 * 128 + 4 * lane);
-                            cqx = lds4(hq + 1 * 128 + 4 * lane);
-                            cqy = lds4(hq + 2 * 128 + 4 * lane);
-                        } else {
-                            const float *ho = &sm.ho[lvl - 2][(j - 1) & 1][0][0];
-                            ch = lds4(ho + 0 * 128 + 4 * lane);
-                            cqx = lds4(ho + 1 * 128 + 4 * lane);
-                            cqy = lds4(ho + 2 * 128 + 4 * lane);
-                        }
-                        cz = lds4(&sm.zn[r % kDZ][0][4 * lane]);
-                        cn = lds4(&sm.zn[r % kDZ][1][4 * lane]);
-                    }
-                    if (r > 0) {
-                        pz = lds4(&sm.zn[(r - 1) % kDZ][0][4 * lane]);
-                        pn = lds4(&sm.zn[(r - 1) % kDZ][1][4 * lane]);
-                    }
-                    if (r == rstart && jb > 0) {
-                        hp = ch;                          // halo row: only becomes the previous row
+    // this level's previous row: input depth and the new faces computed for it
+    float4 hp = make_float4(0, 0, 0, 0), qxw_p = hp, qys_p = hp;
+    float qxe_p = 0.0f;
+    // runs of up to 32 ticks; the float partial sums of the boundary outflow (fq)
+    // and the clipped depth (fc) are folded into the double ledger after each run
+    for (int j0 = jb; j0 <= jlast && !abort; j0 += 32) {
+        float fq = 0.0f, fc = 0.0f;
+        const int jend = min(j0 + 31, jlast);
+        for (int j = j0; j <= jend; j++) {
+            const int r = j - 2 * (lvl - 1);
+            // ---- level 1 waits for its staged row; the other levels only read rows that
+            // level 1 waited for at earlier ticks (ordered by the end-of-tick barrier)
+            bool stop = false;
+            if (lvl == 1 && r >= jb && r <= jload_hi) {
+                const uint32_t g = base + (uint32_t)(r - jb);
+                const int ok = mbar_wait_bounded(&sm.bar[g % kPF], (g / kPF) & 1u, kBudgetNs) ? 1 : 0;
+                stop = !__all_sync(0xffffffffu, ok);
+            }
+            if (!stop && r >= rstart && r <= ny && r <= y1 + K - lvl) {
+                // current row inputs
+                float4 ch = make_float4(0, 0, 0, 0), cqx = ch, cqy = ch, cz = ch, cn = ch, pz = ch, pn = ch;
+                if (r < ny) {
+                    if (lvl == 1) {
+                        const float *hq = &sm.hq[(base + (uint32_t)(r - jb)) % kPF][0][0];
+                        ch = lds4(hq + 0 * 128 + 4 * lane);
+                        cqx = lds4(hq + 1 * 128 + 4 * lane);
+                        cqy = lds4(hq + 2 * 128 + 4 * lane);
                     } else {
-                        // ---- new south faces of row r (interior rows branch-free; the boundary
-                        // rows, uniform over the warp, take the Eq. 5-6 path)
-                        float4 qys;
-                        if (r > 0 && r < ny) {
+                        const float *ho = &sm.ho[lvl - 2][(j - 1) & 1][0][0];
+                        ch = lds4(ho + 0 * 128 + 4 * lane);
+                        cqx = lds4(ho + 1 * 128 + 4 * lane);
+                        cqy = lds4(ho + 2 * 128 + 4 * lane);
+                    }
+                    cz = lds4(&sm.zn[r % kDZ][0][4 * lane]);
+                    cn = lds4(&sm.zn[r % kDZ][1][4 * lane]);
+                }
+                if (r > 0) {
+                    pz = lds4(&sm.zn[(r - 1) % kDZ][0][4 * lane]);
+                    pn = lds4(&sm.zn[(r - 1) % kDZ][1][4 * lane]);
+                }
+                if (r == rstart && jb > 0) {
+                    hp = ch;                          // halo row: only becomes the previous row
+                } else {
+                    // ---- new south faces of row r (interior rows branch-free; the boundary
+                    // rows, uniform over the warp, take the Eq. 5-6 path)
+                    float4 qys;
+                    if (r > 0 && r < ny) {
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            const float zl = get(pz, k), zr = get(cz, k);
+                            const float v = face_fast_sel(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr,
+                                                          fmaxf(zl, zr), get(pn, k) + get(cn, k), Kc);
+                            set(qys, k, v);
+                        }
+                        if (edge_lane) {
+#pragma unroll
+                            for (int k = 0; k < 4; k++)
+                                if (!in_col[k]) set(qys, k, 0.0f);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            const int c = c0 + k;
+                            float v = 0.0f;
+                            if (in_col[k]) {
+                                float qo = 0.0f;
+                                v = r == 0 ? boundary_fast_flux(a, step, 2, c, get(ch, k), get(cn, k), qo)
+                                           : boundary_fast_flux(a, step, 3, c, get(hp, k), get(pn, k), qo);
+                                if (own_cell[k] && ((r == 0 && y0 == 0) || (r == ny && y1 == ny))) fq += qo;
+                            }
+                            set(qys, k, v);
+                        }
+                    }
+                    // ---- finish row r-1: Eq. 4 and the clip; hand it on (or store it at level K)
+                    const bool has_prev = jb == 0 ? r > 0 : r > rstart + 1;
+                    if (has_prev) {
+                        const int rr = r - 1;
+                        const bool own_row = rr >= y0 && rr < y1;
+                        float4 fin;
+                        bool neg = false;
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            const float qe = k < 3 ? get(qxw_p, k + 1) : qxe_p;
+                            const float dv = __fadd_rn(__fsub_rn(get(qxw_p, k), qe), __fsub_rn(get(qys_p, k), get(qys, k)));
+                            const float v = __fmaf_rn(Kc.dtdx, dv, get(hp, k));
+                            neg |= v < 0.0f;
+                            set(fin, k, v);
+                        }
+                        if (neg) {                    // rare: clip to zero, book the removed volume
 #pragma unroll
                             for (int k = 0; k < 4; k++) {
-                                const float zl = get(pz, k), zr = get(cz, k);
-                                const float v = face_fast_sel(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr,
-                                                              fmaxf(zl, zr), get(pn, k) + get(cn, k), Kc);
-                                set(qys, k, v);
+                                const float v = get(fin, k);
+                                if (v < 0.0f) {
+                                    if (own_row && own_cell[k]) fc -= v;
+                                    set(fin, k, 0.0f);
+                                }
                             }
-                            if (edge_lane) {
+                        }
+                        if (lvl == K && own_row) {
+#pragma unroll
+                            for (int k = 0; k < 4; k++) {
+                                const float v = get(fin, k);
+                                if (own_cell[k]) {
+                                    L.hmax = fmaxf(L.hmax, v);
+                                    L.nan_seen |= (v != v);
+                                }
+                            }
+                        }
+                        if (lvl < K) {
+                            float *ho = &sm.ho[lvl - 1][j & 1][0][0];
+                            sts4(ho + 0 * 128 + 4 * lane, fin);
+                            sts4(ho + 1 * 128 + 4 * lane, qxw_p);
+                            sts4(ho + 2 * 128 + 4 * lane, qys_p);
+                        } else if (own_row) {
+                            const size_t ro = (size_t)rr * P + c0;
+                            if (all_cell) {
+                                *reinterpret_cast<float4 *>(a.h_out + ro) = fin;
+                                *reinterpret_cast<float4 *>(a.qy_out + ro) = qys_p;
+                                if (rr == ny - 1) *reinterpret_cast<float4 *>(a.qy_out + ro + P) = qys;
+                            } else {
 #pragma unroll
                                 for (int k = 0; k < 4; k++)
-                                    if (!in_col[k]) set(qys, k, 0.0f);
+                                    if (own_cell[k]) {
+                                        a.h_out[ro + k] = get(fin, k);
+                                        a.qy_out[ro + k] = get(qys_p, k);
+                                        if (rr == ny - 1) a.qy_out[ro + P + k] = get(qys, k);
+                                    }
                             }
-                        } else {
+                            if (all_wface) *reinterpret_cast<float4 *>(a.qx_out + ro) = qxw_p;
+                            else {
+#pragma unroll
+                                for (int k = 0; k < 4; k++)
+                                    if (own_wface[k]) a.qx_out[ro + k] = get(qxw_p, k);
+                            }
+                        }
+                    }
+                    // ---- new west faces of row r; row r becomes this level's previous row
+                    if (r < ny) {
+                        const bool own_row_r = r >= y0 && r < y1;
+                        const float hl0 = __shfl_up_sync(0xffffffffu, ch.w, 1);
+                        const float zl0 = __shfl_up_sync(0xffffffffu, cz.w, 1);
+                        const float nl0 = __shfl_up_sync(0xffffffffu, cn.w, 1);
+                        float4 qxw;
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            const float hl = k == 0 ? hl0 : get(ch, k - 1);
+                            const float zl = k == 0 ? zl0 : get(cz, k - 1);
+                            const float nl = k == 0 ? nl0 : get(cn, k - 1);
+                            const float zr = get(cz, k);
+                            const float v = face_fast_sel(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr),
+                                                          nl + get(cn, k), Kc);
+                            set(qxw, k, v);
+                        }
+                        if (edge_lane) {              // lanes at or beyond x = 0 or x = nx: Eq. 5-6, or no face
 #pragma unroll
                             for (int k = 0; k < 4; k++) {
                                 const int c = c0 + k;
-                                float v = 0.0f;
-                                if (in_col[k]) {
+                                if (!in_wface[k]) set(qxw, k, 0.0f);
+                                if (c == 0 || c == nx) {
                                     float qo = 0.0f;
-                                    v = r == 0 ? boundary_fast_flux(a, step, 2, c, get(ch, k), get(cn, k), qo)
-                                               : boundary_fast_flux(a, step, 3, c, get(hp, k), get(pn, k), qo);
-                                    if (own_cell[k] && ((r == 0 && y0 == 0) || (r == ny && y1 == ny))) fq += qo;
-                                }
-                                set(qys, k, v);
-                            }
-                        }
-                        // ---- finish row r-1: Eq. 4 and the clip; hand it on (or store it at level K)
-                        const bool has_prev = jb == 0 ? r > 0 : r > rstart + 1;
-                        if (has_prev) {
-                            const int rr = r - 1;
-                            const bool own_row = rr >= y0 && rr < y1;
-                            float4 fin;
-                            bool neg = false;
-#pragma unroll
-                            for (int k = 0; k < 4; k++) {
-                                const float qe = k < 3 ? get(qxw_p, k + 1) : qxe_p;
-                                const float dv = __fadd_rn(__fsub_rn(get(qxw_p, k), qe), __fsub_rn(get(qys_p, k), get(qys, k)));
-                                const float v = __fmaf_rn(Kc.dtdx, dv, get(hp, k));
-                                neg |= v < 0.0f;
-                                set(fin, k, v);
-                            }
-                            if (neg) {                    // rare: clip to zero, book the removed volume
-#pragma unroll
-                                for (int k = 0; k < 4; k++) {
-                                    const float v = get(fin, k);
-                                    if (v < 0.0f) {
-                                        if (own_row && own_cell[k]) fc -= v;
-                                        set(fin, k, 0.0f);
-                                    }
-                                }
-                            }
-                            if (lvl == K && own_row) {
-#pragma unroll
-                                for (int k = 0; k < 4; k++) {
-                                    const float v = get(fin, k);
-                                    if (own_cell[k]) {
-                                        hmax = fmaxf(hmax, v);
-                                        nan_seen |= (v != v);
-                                    }
-                                }
-                            }
-                            if (lvl < K) {
-                                float *ho = &sm.ho[lvl - 1][j & 1][0][0];
-                                sts4(ho + 0 * 128 + 4 * lane, fin);
-                                sts4(ho + 1 * 128 + 4 * lane, qxw_p);
-                                sts4(ho + 2 * 128 + 4 * lane, qys_p);
-                            } else if (own_row) {
-                                const size_t ro = (size_t)rr * P + c0;
-                                if (all_cell) {
-                                    *reinterpret_cast<float4 *>(a.h_out + ro) = fin;
-                                    *reinterpret_cast<float4 *>(a.qy_out + ro) = qys_p;
-                                    if (rr == ny - 1) *reinterpret_cast<float4 *>(a.qy_out + ro + P) = qys;
-                                } else {
-#pragma unroll
-                                    for (int k = 0; k < 4; k++)
-                                        if (own_cell[k]) {
-                                            a.h_out[ro + k] = get(fin, k);
-                                            a.qy_out[ro + k] = get(qys_p, k);
-                                            if (rr == ny - 1) a.qy_out[ro + P + k] = get(qys, k);
-                                        }
-                                }
-                                if (all_wface) *reinterpret_cast<float4 *>(a.qx_out + ro) = qxw_p;
-                                else {
-#pragma unroll
-                                    for (int k = 0; k < 4; k++)
-                                        if (own_wface[k]) a.qx_out[ro + k] = get(qxw_p, k);
+                                    const float hl = k == 0 ? hl0 : get(ch, k - 1);
+                                    const float nl = k == 0 ? nl0 : get(cn, k - 1);
+                                    const float v = c == 0 ? boundary_fast_flux(a, step, 0, r, get(ch, 0), get(cn, 0), qo)
+                                                           : boundary_fast_flux(a, step, 1, r, hl, nl, qo);
+                                    if (own_row_r && own_wface[k]) fq += qo;
+                                    set(qxw, k, v);
                                 }
                             }
                         }
-                        // ---- new west faces of row r; row r becomes this level's previous row
-                        if (r < ny) {
-                            const bool own_row_r = r >= y0 && r < y1;
-                            const float hl0 = __shfl_up_sync(0xffffffffu, ch.w, 1);
-                            const float zl0 = __shfl_up_sync(0xffffffffu, cz.w, 1);
-                            const float nl0 = __shfl_up_sync(0xffffffffu, cn.w, 1);
-                            float4 qxw;
-#pragma unroll
-                            for (int k = 0; k < 4; k++) {
-                                const float hl = k == 0 ? hl0 : get(ch, k - 1);
-                                const float zl = k == 0 ? zl0 : get(cz, k - 1);
-                                const float nl = k == 0 ? nl0 : get(cn, k - 1);
-                                const float zr = get(cz, k);
-                                const float v = face_fast_sel(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr),
-                                                              nl + get(cn, k), Kc);
-                                set(qxw, k, v);
-                            }
-                            if (edge_lane) {              // lanes at or beyond x = 0 or x = nx: Eq. 5-6, or no face
-#pragma unroll
-                                for (int k = 0; k < 4; k++) {
-                                    const int c = c0 + k;
-                                    if (!in_wface[k]) set(qxw, k, 0.0f);
-                                    if (c == 0 || c == nx) {
-                                        float qo = 0.0f;
-                                        const float hl = k == 0 ? hl0 : get(ch, k - 1);
-                                        const float nl = k == 0 ? nl0 : get(cn, k - 1);
-                                        const float v = c == 0 ? boundary_fast_flux(a, step, 0, r, get(ch, 0), get(cn, 0), qo)
-                                                               : boundary_fast_flux(a, step, 1, r, hl, nl, qo);
-                                        if (own_row_r && own_wface[k]) fq += qo;
-                                        set(qxw, k, v);
-                                    }
-                                }
-                            }
-                            qxe_p = __shfl_down_sync(0xffffffffu, qxw.x, 1);
-                            hp = ch;
-                            qxw_p = qxw;
-                            qys_p = qys;
-                        }
-                    }
-                }
-                // ---- end of tick (shares a timeout); then level 1 refills the ring
-                if (__syncthreads_or(stop ? 1 : 0)) {
-                    abort = true;
-                    break;
-                }
-                if (lvl == 1 && lane == 0 && r >= jb && r <= jload_hi) {
-                    consumed = r - jb + 1;
-                    if (issued < nload) {
-                        fence_proxy_async();
-                        issue(issued);
-                        issued++;
+                        qxe_p = __shfl_down_sync(0xffffffffu, qxw.x, 1);
+                        hp = ch;
+                        qxw_p = qxw;
+                        qys_p = qys;
                     }
                 }
             }
-            vout += (double)fq * G.dx;
-            vclip += (double)fc * G.dx * G.dx;
+            // ---- end of tick (shares a timeout); then level 1 refills the ring
+            if (__syncthreads_or(stop ? 1 : 0)) {
+                abort = true;
+                break;
+            }
+            if (lvl == 1 && lane == 0 && r >= jb && r <= jload_hi) {
+                consumed = r - jb + 1;
+                if (issued < nload) {
+                    fence_proxy_async();
+                    issue(issued);
+                    issued++;
+                }
+            }
         }
-        if (!abort) base += (uint32_t)nload;
-    }   // segments
-    if (abort && threadIdx.x == 0) {
+        L.vout += (double)fq * G.dx;
+        L.vclip += (double)fc * G.dx * G.dx;
+    }
+    if (!abort) {
+        base += (uint32_t)nload;
+    } else if (threadIdx.x == 0) {
         // leave no bulk copy writing into shared memory after exit
         for (int k = consumed; k < issued; k++) {
             const uint32_t g = base + (uint32_t)k;
@@ -353,24 +344,114 @@ __global__ void __launch_bounds__(K * 32, K == 4 ? 5 : 1) step_tiled_kernel(cons
         }
         atomicOr(&a.ctrl->status, kStatusTimeout);
     }
-    double bo = block_reduce<false>(vout, red);
+    return abort;
+}
+
+// Block-wide sums of the ledger terms into grid a's control block.
+__device__ __forceinline__ void tiled_flush(const StepArgs<float> &a, const TiledLedger &L, const int want_hmax,
+                                            double *red)
+{
+    const double dtd = a.ctrl->dt;
+    const double bo = block_reduce<false>(L.vout, red);
     if (threadIdx.x == 0 && bo != 0.0) atomicAdd(&a.ctrl->V_out, dtd * bo);
-    double bc = block_reduce<false>(vclip, red);
+    const double bc = block_reduce<false>(L.vclip, red);
     if (threadIdx.x == 0 && bc != 0.0) atomicAdd(&a.ctrl->V_clip, bc);
-    if (a.want_hmax) {
-        double bm = block_reduce<true>(nan_seen ? (double)NAN : (double)hmax, red);
+    if (want_hmax) {
+        const double bm = block_reduce<true>(L.nan_seen ? (double)NAN : (double)L.hmax, red);
         if (threadIdx.x == 0) atomic_max_nonneg(&a.ctrl->hmax_bits, bm);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double vin = a.ctrl->V_in;
-        for (int s = 0; s < K; s++)
-            for (int k = 0; k < a.n_inflow_sec; k++) {
-                const double Q = a.inflow_Q[(size_t)(a.s + s) * a.n_inflow_sec + k];
-                if (Q > 0.0) vin += dtd * Q;
-            }
-        a.ctrl->V_in = vin;
-        a.ctrl->t = a.t_list[a.s + K];
+}
+
+// Inflow volume of the K steps and the clock after them (one thread per grid).
+template <int K>
+__device__ __forceinline__ void tiled_finish(const StepArgs<float> &a, const int s0)
+{
+    const double dtd = a.ctrl->dt;
+    double vin = a.ctrl->V_in;
+    for (int s = 0; s < K; s++)
+        for (int k = 0; k < a.n_inflow_sec; k++) {
+            const double Q = a.inflow_Q[(size_t)(s0 + s) * a.n_inflow_sec + k];
+            if (Q > 0.0) vin += dtd * Q;
+        }
+    a.ctrl->V_in = vin;
+    a.ctrl->t = a.t_list[s0 + K];
+}
+
+template <int K>
+__device__ __forceinline__ void init_ring(PipeSmem<K> &sm)
+{
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kPF; s++) mbar_init(&sm.bar[s], 1);
+        fence_mbar_init();
     }
+    __syncthreads();
+}
+
+// One grid: work items (chunk, strip) in chunk-major order, block b takes
+// items b, b + grid, ... (a.tile_x strips, a.tile_y rows per chunk).
+template <int K>
+__global__ void __launch_bounds__(K * 32, K == 4 ? 5 : 1) step_tiled_kernel(const StepArgs<float> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    PipeSmem<K> &sm = *reinterpret_cast<PipeSmem<K> *>(smem_raw);
+    init_ring<K>(sm);
+    const int n_strips = a.tile_x, chunk_rows = a.tile_y;
+    const int n_items = n_strips * ((a.geo.ny + chunk_rows - 1) / chunk_rows);
+    const FastConst Kc = tiled_const(a);
+    TiledLedger L;
+    uint32_t base = 0;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int strip = item % n_strips;
+        const int y0 = (item / n_strips) * chunk_rows;
+        const int y1 = min(y0 + chunk_rows, a.geo.ny);
+        if (tiled_item<K>(a, a.s, Kc, strip, y0, y1, sm, base, L)) break;
+    }
+    tiled_flush(a, L, a.want_hmax, red);
+    if (blockIdx.x == 0 && threadIdx.x == 0) tiled_finish<K>(a, a.s);
+}
+
+// Many grids: the items of grid k (its (chunk, strip) items, chunk_rows rows
+// per chunk) are numbered base[k] .. base[k+1] - 1, grids ordered largest
+// first, and block b takes items b, b + grid, ...  A block sums a grid's
+// ledger terms while its items belong to that grid and hands them to the
+// grid's control block when it moves on; the grid's first item books its
+// inflow volume and clock.
+template <int K>
+__global__ void __launch_bounds__(K * 32, K == 4 ? 5 : 1)
+    step_tiled_ensemble_kernel(const StepArgs<float> *table, const int *base, const int n, const int chunk_rows,
+                               const int s0, const int want_hmax)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    PipeSmem<K> &sm = *reinterpret_cast<PipeSmem<K> *>(smem_raw);
+    init_ring<K>(sm);
+    const int total = base[n];
+    TiledLedger L;
+    uint32_t ring = 0;
+    int cur = -1;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (base[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        if (lo != cur) {
+            if (cur >= 0) tiled_flush(table[cur], L, want_hmax, red);
+            L = TiledLedger();
+            cur = lo;
+        }
+        const StepArgs<float> &a = table[lo];
+        const int local = item - base[lo];
+        const int n_strips = (a.geo.nx + kOut - 1) / kOut;
+        const int strip = local % n_strips;
+        const int y0 = (local / n_strips) * chunk_rows;
+        const int y1 = min(y0 + chunk_rows, a.geo.ny);
+        if (local == 0 && threadIdx.x == 0) tiled_finish<K>(a, s0);
+        if (tiled_item<K>(a, s0, tiled_const(a), strip, y0, y1, sm, ring, L)) break;
+    }
+    if (cur >= 0) tiled_flush(table[cur], L, want_hmax, red);
 }
 
 }  // namespace
@@ -416,25 +497,37 @@ void tiled_split(int n_strips, int ny, int resident, int K, int *chunk_rows, int
 namespace {
 
 template <int K>
-cudaError_t launch_k(const StepArgs<float> &a0, cudaStream_t st)
+cudaError_t resident_pipelines(int *out)
 {
-    static int blocks_per_sm = 0, num_sms = 0;
-    const size_t smem = sizeof(PipeSmem<K>);
-    if (!blocks_per_sm) {
+    static int resident = 0;
+    if (!resident) {
+        const size_t smem = sizeof(PipeSmem<K>);
         cudaError_t e = cudaFuncSetAttribute(step_tiled_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, step_tiled_kernel<K>, K * 32, smem);
+        e = cudaFuncSetAttribute(step_tiled_ensemble_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
         if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tiled_kernel<K>, K * 32, smem);
+        if (e != cudaSuccess) return e;
+        resident = (per_sm < 1 ? 1 : per_sm) * sms;
     }
+    *out = resident;
+    return cudaSuccess;
+}
+
+template <int K>
+cudaError_t launch_k(const StepArgs<float> &a0, cudaStream_t st)
+{
+    int resident = 0;
+    cudaError_t e = resident_pipelines<K>(&resident);
+    if (e != cudaSuccess) return e;
     StepArgs<float> a = a0;
     const int nx = a.geo.nx, ny = a.geo.ny;
     const int n_strips = (nx + kOut - 1) / kOut;
-    int resident = num_sms * blocks_per_sm;
     if (a0.tile_x > 0 && a0.tile_x < resident) resident = a0.tile_x;   // caller's cap on pipelines
     int chunk_rows = 0, blocks = 0;
     if (a0.tile_y > 0) {                                                // caller's rows per work item
@@ -446,11 +539,43 @@ cudaError_t launch_k(const StepArgs<float> &a0, cudaStream_t st)
     }
     a.tile_x = n_strips;
     a.tile_y = chunk_rows;
-    step_tiled_kernel<K><<<blocks, K * 32, smem, st>>>(a);
+    step_tiled_kernel<K><<<blocks, K * 32, sizeof(PipeSmem<K>), st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_ens_k(const StepArgs<float> *table, const int *base, int n, int total_items, int chunk_rows,
+                         int s0, int want_hmax, cudaStream_t st)
+{
+    int resident = 0;
+    cudaError_t e = resident_pipelines<K>(&resident);
+    if (e != cudaSuccess) return e;
+    const int blocks = total_items < resident ? total_items : resident;
+    if (blocks < 1) return cudaSuccess;
+    step_tiled_ensemble_kernel<K><<<blocks, K * 32, sizeof(PipeSmem<K>), st>>>(table, base, n, chunk_rows, s0,
+                                                                               want_hmax);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+int tiled_items(const Geom &g, int chunk_rows)
+{
+    const int n_strips = (g.nx + kOut - 1) / kOut;
+    return n_strips * ((g.ny + chunk_rows - 1) / chunk_rows);
+}
+
+cudaError_t launch_step_tiled_ensemble(const StepArgs<float> *table, const int *base, int n, int total_items,
+                                       int chunk_rows, int k_steps, int s0, int want_hmax, cudaStream_t st)
+{
+    switch (k_steps) {
+    case 1: return launch_ens_k<1>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
+    case 2: return launch_ens_k<2>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
+    case 3: return launch_ens_k<3>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
+    case 4: return launch_ens_k<4>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 size_t tiled_smem_bytes(int, int, int k) { return k >= 4 ? sizeof(PipeSmem<4>) : sizeof(PipeSmem<2>); }
 

@@ -50,6 +50,53 @@ def test_ensemble_equals_members_alone(warps, rows, spg, graph):
     ens.close()
 
 
+@pytest.mark.parametrize("K,rows,spg,graph", [(4, 16, 4, True), (2, 7, 8, True), (4, 64, 4, False),
+                                              (1, 33, 4, True), (2, 300, 4, False)])
+def test_tiled_ensemble_equals_members_alone(K, rows, spg, graph):
+    """K steps per launch over every scenario's (chunk, strip) items give the
+    bits of each scenario stepped alone by the single-step kernel."""
+    Fm = F()
+    probs = scenarios()
+    for p in probs:
+        p.opts.epoch_steps = 4
+    ens = Fm.Ensemble(probs)
+    ens.set_launch(2, rows, spg, use_graph=graph)
+    ens.set_kernel(Fm.KERNEL_TILED, K)
+    for n in (3, 2 * spg, 5, 1):           # partial launches, graph replays, epoch ends
+        ens.step(n)
+    n = 3 + 2 * spg + 5 + 1
+    for mb, p in zip(ens.members, probs):
+        s = Fm.Sim(p, kernel=Fm.KERNEL_STREAM)
+        s.step(n)
+        for f in (Fm.FIELD_H, Fm.FIELD_QX, Fm.FIELD_QY):
+            assert np.array_equal(mb.read(f), s.read(f)), (p.name, f)
+        La, Lb = mb.ledger(), s.ledger()
+        for k in ("t", "dt", "V_in", "volume", "step", "h_max"):
+            assert La[k] == pytest.approx(Lb[k], rel=1e-12, abs=1e-12), (p.name, k)
+        # boundary outflow and clipped depth are summed per lane in float over
+        # runs of at most 32 rows by the temporal-blocking kernel
+        for k in ("V_out", "V_clip"):
+            assert La[k] == pytest.approx(Lb[k], rel=1e-6, abs=1e-9), (p.name, k)
+    ens.close()
+
+
+def test_ensemble_set_kernel_rejects_bad_values():
+    Fm = F()
+    probs = scenarios()[:2]
+    ens = Fm.Ensemble(probs)
+    E = probs[0].opts.epoch_steps
+    with pytest.raises(Fm.FloodError):
+        ens.set_kernel(Fm.KERNEL_ROWS, 0)
+    with pytest.raises(Fm.FloodError):
+        ens.set_kernel(Fm.KERNEL_TILED, 5)
+    if E % 3:
+        with pytest.raises(Fm.FloodError):
+            ens.set_kernel(Fm.KERNEL_TILED, 3)
+    ens.set_kernel(Fm.KERNEL_TILED, 0)
+    ens.step(E)
+    ens.close()
+
+
 def test_ensemble_member_matches_oracle():
     Fm = F()
     probs = scenarios()
@@ -68,8 +115,9 @@ def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
     Fm = F()
     monkeypatch.setenv("FLOOD_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     ens = Fm.Ensemble(scenarios())
-    r = autotune.tune_ensemble(ens, candidates=[(4, 64, 4), (2, 32, 8)], trial_steps=8)
-    assert not r["cached"] and len(r["trials"]) == 2 and tuple(r["shape"]) in [(4, 64, 4), (2, 32, 8)]
+    cands = [(0, 4, 64, 4), (4, 2, 32, 8), (2, 2, 16, 4)]     # (K, warps, rows, steps per graph)
+    r = autotune.tune_ensemble(ens, candidates=cands, trial_steps=8)
+    assert not r["cached"] and len(r["trials"]) == 3 and tuple(r["shape"]) in cands
     r2 = autotune.tune_ensemble(ens)
     assert r2["cached"] and r2["shape"] == r["shape"]
     ens.close()
