@@ -88,7 +88,7 @@ __device__ __forceinline__ float boundary_fast_at(const StepArgs<float> &a, int 
     if (type == kBcWall) return 0.0f;
     float inward = (side == 0 || side == 2) ? 1.0f : -1.0f;
     if (type == kBcInflow) return inward * a.inflow_q[(size_t)step * a.n_slots + a.bc.slot[off + k]];
-    float q = outflow_fast(h, (float)a.bc.sqrtS[off + k], n, (float)G.dx, (float)G.h_dry, G.bc_form);
+    float q = outflow_fast(h, a.bc.sqrtS_f[off + k], n, G.dx_f, G.h_dry_f, G.bc_form);
     vout += (double)q * G.dx;
     return -inward * q;
 }
@@ -105,7 +105,7 @@ __device__ __forceinline__ float boundary_fast_flux(const StepArgs<float> &a, in
     if (type == kBcWall) return 0.0f;
     float inward = (side == 0 || side == 2) ? 1.0f : -1.0f;
     if (type == kBcInflow) return inward * a.inflow_q[(size_t)step * a.n_slots + a.bc.slot[off + k]];
-    float q = outflow_fast(h, (float)a.bc.sqrtS[off + k], n, (float)G.dx, (float)G.h_dry, G.bc_form);
+    float q = outflow_fast(h, a.bc.sqrtS_f[off + k], n, G.dx_f, G.h_dry_f, G.bc_form);
     qout += q;
     return -inward * q;
 }
@@ -120,7 +120,7 @@ __device__ __forceinline__ float boundary_fast(const StepArgs<float> &a, int sid
     if (type == kBcWall) return 0.0f;
     float inward = (side == 0 || side == 2) ? 1.0f : -1.0f;
     if (type == kBcInflow) return inward * a.inflow_q[(size_t)a.s * a.n_slots + a.bc.slot[off + k]];
-    float q = outflow_fast(h, (float)a.bc.sqrtS[off + k], n, (float)G.dx, (float)G.h_dry, G.bc_form);
+    float q = outflow_fast(h, a.bc.sqrtS_f[off + k], n, G.dx_f, G.h_dry_f, G.bc_form);
     vout += (double)q * G.dx;
     return -inward * q;
 }

@@ -222,6 +222,7 @@ flood_status reverse_step_t(Sweep &S)
     a.bc.type = h->bc_type;
     a.bc.slot = h->bc_slot;
     a.bc.sqrtS = h->bc_sqrtS;
+    a.bc.sqrtS_f = h->bc_sqrtS_f;
     a.inflow_q = (const T *)h->inflow_q;
     a.n_slots = h->n_slots;
     a.inflow_Q = h->inflow_Q;

@@ -200,6 +200,7 @@ StepArgs<T> make_args(flood_handle *h, int s, int k_steps, int want_hmax, const 
     a.bc.type = h->bc_type;
     a.bc.slot = h->bc_slot;
     a.bc.sqrtS = h->bc_sqrtS;
+    a.bc.sqrtS_f = h->bc_sqrtS_f;
     a.inflow_q = (const T *)h->inflow_q;
     a.n_slots = h->n_slots;
     a.inflow_Q = h->inflow_Q;
@@ -392,8 +393,10 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
     G.pitch = (grid->nx + 1 + 31) / 32 * 32;
     G.bc_form = o.bc_form;
     G.dx = grid->dx;
+    G.dx_f = (float)grid->dx;
     G.g = o.g;
     G.h_dry = o.h_dry;
+    G.h_dry_f = (float)o.h_dry;
     G.cfl_alpha = o.cfl_alpha;
     G.dt_cap = o.dt_cap;
     G.dt_const = o.dt_const;
@@ -498,6 +501,8 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
     ALLOC(h->bc_type, int8_t *, nb);
     ALLOC(h->bc_slot, int32_t *, nb * sizeof(int32_t));
     ALLOC(h->bc_sqrtS, double *, nb * sizeof(double));
+    ALLOC(h->bc_sqrtS_f, float *, nb * sizeof(float));
+    std::vector<float> bsqrt_f(bsqrt.begin(), bsqrt.end());
     ALLOC(h->secs_dev, InflowSec *, std::max<size_t>(isecs.size(), 1) * sizeof(InflowSec));
     ALLOC(h->sec_cells, int64_t *, std::max<size_t>(icells.size(), 1) * sizeof(int64_t));
     ALLOC(h->tab_t, double *, std::max<size_t>(tt.size(), 1) * sizeof(double));
@@ -514,7 +519,7 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
         return bytes == 0 ? cudaSuccess : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream);
     };
     if (up(h->bc_type, btype.data(), nb) || up(h->bc_slot, bslot.data(), nb * sizeof(int32_t)) ||
-        up(h->bc_sqrtS, bsqrt.data(), nb * sizeof(double)) ||
+        up(h->bc_sqrtS, bsqrt.data(), nb * sizeof(double)) || up(h->bc_sqrtS_f, bsqrt_f.data(), nb * sizeof(float)) ||
         up(h->secs_dev, isecs.data(), isecs.size() * sizeof(InflowSec)) ||
         up(h->sec_cells, icells.data(), icells.size() * sizeof(int64_t)) ||
         up(h->tab_t, tt.data(), tt.size() * sizeof(double)) || up(h->tab_q, tq.data(), tq.size() * sizeof(double)))

@@ -44,6 +44,7 @@ struct Geom {
     int pitch;                    // elements per row of every grid array
     int bc_form;
     double dx, g, h_dry;
+    float dx_f, h_dry_f;          // dx and h_dry rounded to FP32 once (the fast kernels' boundary faces)
     double cfl_alpha, dt_cap, dt_const;
     int dt_mode, epoch_steps;
 };
@@ -54,6 +55,7 @@ struct Boundary {
     const int8_t *type;           // kBcWall / kBcInflow / kBcOutflow
     const int32_t *slot;          // inflow: column in the per-step inflow flux row
     const double *sqrtS;          // outflow: sqrt(S_out)
+    const float *sqrtS_f;         // the same rounded to FP32 (fast kernels)
 };
 
 template <typename T>
@@ -96,7 +98,6 @@ cudaError_t launch_step_tiled_ensemble(const StepArgs<float> *table, const int *
                                        int chunk_rows, int k_steps, int s0, int want_hmax, cudaStream_t st);
 void stream_launch_shape(const Geom &g, int tile_x, int tile_y, int *warps, int *rows);
 cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st);
-size_t tiled_smem_bytes(int tile_x, int tile_y, int k);
 
 // Epoch start: choose dt from h_max (or constant), fill t_list, reset the
 // running maximum, count CFL exceedances, flag NaN/Inf.

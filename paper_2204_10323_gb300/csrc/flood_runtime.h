@@ -32,6 +32,7 @@ struct flood_handle {
     int8_t *bc_type = nullptr;
     int32_t *bc_slot = nullptr;
     double *bc_sqrtS = nullptr;
+    float *bc_sqrtS_f = nullptr;
     flood::InflowSec *secs_dev = nullptr;
     int n_in = 0, n_slots = 1;
     int64_t *sec_cells = nullptr;

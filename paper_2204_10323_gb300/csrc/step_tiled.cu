@@ -32,10 +32,13 @@ namespace {
 
 constexpr int kHalo = 4;                    // halo columns per side (= largest K)
 constexpr int kOut = 128 - 2 * kHalo;       // output columns per strip
-constexpr int kPF = 8;                      // level-1 rows in flight
+// level-1 rows in flight and pipelines per SM: one grid uses 6 and 6 (six
+// pipelines of 4 warps fit the registers and shared memory of an SM); the
+// ensemble kernel, which keeps more per-scenario state in registers, 8 and 5
+constexpr int kPF1 = 6, kPFE = 8;
 constexpr uint64_t kBudgetNs = 2000000000ull;
 
-template <int K>
+template <int K, int kPF>
 struct alignas(16) PipeSmem {
     static constexpr int kDZ = kPF + 2 * K; // z,n rows kept: the lagging levels read 2(K-1)+1 rows back
     float hq[kPF][3][128];                  // level-1 input rows: h, qx, qy
@@ -84,12 +87,12 @@ __device__ __forceinline__ FastConst tiled_const(const StepArgs<float> &a)
 // items (ring slot and phase of staged row idx are those of base + idx).
 // Returns true (uniformly over the block) if a wait on a copy timed out; the
 // copies in flight are then drained and the status word has the timeout bit.
-template <int K>
+template <int K, int kPF>
 __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s0, const FastConst &Kc,
-                                           const int strip, const int y0, const int y1, PipeSmem<K> &sm,
+                                           const int strip, const int y0, const int y1, PipeSmem<K, kPF> &sm,
                                            uint32_t &base, TiledLedger &L)
 {
-    constexpr int kDZ = PipeSmem<K>::kDZ;
+    constexpr int kDZ = PipeSmem<K, kPF>::kDZ;
     const Geom &G = a.geo;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lvl = warp + 1;                         // this warp's time level
@@ -377,8 +380,8 @@ __device__ __forceinline__ void tiled_finish(const StepArgs<float> &a, const int
     a.ctrl->t = a.t_list[s0 + K];
 }
 
-template <int K>
-__device__ __forceinline__ void init_ring(PipeSmem<K> &sm)
+template <int K, int kPF>
+__device__ __forceinline__ void init_ring(PipeSmem<K, kPF> &sm)
 {
     if (threadIdx.x == 0) {
         for (int s = 0; s < kPF; s++) mbar_init(&sm.bar[s], 1);
@@ -390,12 +393,12 @@ __device__ __forceinline__ void init_ring(PipeSmem<K> &sm)
 // One grid: work items (chunk, strip) in chunk-major order, block b takes
 // items b, b + grid, ... (a.tile_x strips, a.tile_y rows per chunk).
 template <int K>
-__global__ void __launch_bounds__(K * 32, K == 4 ? 5 : 1) step_tiled_kernel(const StepArgs<float> a)
+__global__ void __launch_bounds__(K * 32, K == 4 ? 6 : 1) step_tiled_kernel(const StepArgs<float> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
-    PipeSmem<K> &sm = *reinterpret_cast<PipeSmem<K> *>(smem_raw);
-    init_ring<K>(sm);
+    PipeSmem<K, kPF1> &sm = *reinterpret_cast<PipeSmem<K, kPF1> *>(smem_raw);
+    init_ring<K, kPF1>(sm);
     const int n_strips = a.tile_x, chunk_rows = a.tile_y;
     const int n_items = n_strips * ((a.geo.ny + chunk_rows - 1) / chunk_rows);
     const FastConst Kc = tiled_const(a);
@@ -405,7 +408,7 @@ __global__ void __launch_bounds__(K * 32, K == 4 ? 5 : 1) step_tiled_kernel(cons
         const int strip = item % n_strips;
         const int y0 = (item / n_strips) * chunk_rows;
         const int y1 = min(y0 + chunk_rows, a.geo.ny);
-        if (tiled_item<K>(a, a.s, Kc, strip, y0, y1, sm, base, L)) break;
+        if (tiled_item<K, kPF1>(a, a.s, Kc, strip, y0, y1, sm, base, L)) break;
     }
     tiled_flush(a, L, a.want_hmax, red);
     if (blockIdx.x == 0 && threadIdx.x == 0) tiled_finish<K>(a, a.s);
@@ -424,8 +427,8 @@ __global__ void __launch_bounds__(K * 32, K == 4 ? 5 : 1)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
-    PipeSmem<K> &sm = *reinterpret_cast<PipeSmem<K> *>(smem_raw);
-    init_ring<K>(sm);
+    PipeSmem<K, kPFE> &sm = *reinterpret_cast<PipeSmem<K, kPFE> *>(smem_raw);
+    init_ring<K, kPFE>(sm);
     const int total = base[n];
     TiledLedger L;
     uint32_t ring = 0;
@@ -449,7 +452,7 @@ __global__ void __launch_bounds__(K * 32, K == 4 ? 5 : 1)
         const int y0 = (local / n_strips) * chunk_rows;
         const int y1 = min(y0 + chunk_rows, a.geo.ny);
         if (local == 0 && threadIdx.x == 0) tiled_finish<K>(a, s0);
-        if (tiled_item<K>(a, s0, tiled_const(a), strip, y0, y1, sm, ring, L)) break;
+        if (tiled_item<K, kPFE>(a, s0, tiled_const(a), strip, y0, y1, sm, ring, L)) break;
     }
     if (cur >= 0) tiled_flush(table[cur], L, want_hmax, red);
 }
@@ -496,34 +499,30 @@ void tiled_split(int n_strips, int ny, int resident, int K, int *chunk_rows, int
 
 namespace {
 
-template <int K>
-cudaError_t resident_pipelines(int *out)
+// Blocks of `kernel` (K warps, `smem` bytes) resident on the GPU at once.
+template <typename Kern>
+cudaError_t resident_blocks(Kern kernel, int threads, size_t smem, int *cache, int *out)
 {
-    static int resident = 0;
-    if (!resident) {
-        const size_t smem = sizeof(PipeSmem<K>);
-        cudaError_t e = cudaFuncSetAttribute(step_tiled_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(step_tiled_ensemble_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+    if (!*cache) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tiled_kernel<K>, K * 32, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
         if (e != cudaSuccess) return e;
-        resident = (per_sm < 1 ? 1 : per_sm) * sms;
+        *cache = (per_sm < 1 ? 1 : per_sm) * sms;
     }
-    *out = resident;
+    *out = *cache;
     return cudaSuccess;
 }
 
 template <int K>
 cudaError_t launch_k(const StepArgs<float> &a0, cudaStream_t st)
 {
+    static int cache = 0;
     int resident = 0;
-    cudaError_t e = resident_pipelines<K>(&resident);
+    cudaError_t e = resident_blocks(step_tiled_kernel<K>, K * 32, sizeof(PipeSmem<K, kPF1>), &cache, &resident);
     if (e != cudaSuccess) return e;
     StepArgs<float> a = a0;
     const int nx = a.geo.nx, ny = a.geo.ny;
@@ -539,7 +538,7 @@ cudaError_t launch_k(const StepArgs<float> &a0, cudaStream_t st)
     }
     a.tile_x = n_strips;
     a.tile_y = chunk_rows;
-    step_tiled_kernel<K><<<blocks, K * 32, sizeof(PipeSmem<K>), st>>>(a);
+    step_tiled_kernel<K><<<blocks, K * 32, sizeof(PipeSmem<K, kPF1>), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -547,12 +546,14 @@ template <int K>
 cudaError_t launch_ens_k(const StepArgs<float> *table, const int *base, int n, int total_items, int chunk_rows,
                          int s0, int want_hmax, cudaStream_t st)
 {
+    static int cache = 0;
     int resident = 0;
-    cudaError_t e = resident_pipelines<K>(&resident);
+    cudaError_t e = resident_blocks(step_tiled_ensemble_kernel<K>, K * 32, sizeof(PipeSmem<K, kPFE>), &cache,
+                                    &resident);
     if (e != cudaSuccess) return e;
     const int blocks = total_items < resident ? total_items : resident;
     if (blocks < 1) return cudaSuccess;
-    step_tiled_ensemble_kernel<K><<<blocks, K * 32, sizeof(PipeSmem<K>), st>>>(table, base, n, chunk_rows, s0,
+    step_tiled_ensemble_kernel<K><<<blocks, K * 32, sizeof(PipeSmem<K, kPFE>), st>>>(table, base, n, chunk_rows, s0,
                                                                                want_hmax);
     return cudaGetLastError();
 }
@@ -576,8 +577,6 @@ cudaError_t launch_step_tiled_ensemble(const StepArgs<float> *table, const int *
     default: return cudaErrorInvalidValue;
     }
 }
-
-size_t tiled_smem_bytes(int, int, int k) { return k >= 4 ? sizeof(PipeSmem<4>) : sizeof(PipeSmem<2>); }
 
 cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st)
 {
