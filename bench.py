@@ -30,6 +30,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_CELL = 32          # read h, qx, qy, z, n (20 B) + write h, qx, qy (12 B), FP32
+# DRAM bytes read + written per cell by one launch of a kernel on the 16384^2
+# workload: one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the 4096^2 case of the same workload (state > L2), scaled by the cell count;
+# key (kernel, steps per launch).  The summaries are under profiles/.
+# (profiles/step_stream_4096_full.md, step_tiled4_4096_full.md, step_rows_4096_full.md)
+TRAFFIC_B_PER_CELL = {("stream", 1): 32.24, ("tiled", 4): 31.62, ("rows", 1): 30.92}
 METRIC = "Gcell-updates/s and % of HBM roofline (FP32, 1 GB300); adjoint/forward time ratio"
 UNIT = "Gcell-updates/s"
 
@@ -158,6 +164,57 @@ def run_reference(args):
     return 0
 
 
+def timed_run(F, torch, prob, kernel_name, k, tile, graph, steps_req, warmup, local, dist):
+    """Warm up and time whole epochs of one kernel on `prob`: CUDA events around
+    every launch on the library's stream, nvidia-smi clocks sampled meanwhile."""
+    kernel = {"rows": F.KERNEL_ROWS, "tiled": F.KERNEL_TILED, "reference": F.KERNEL_REFERENCE,
+              "stream": F.KERNEL_STREAM}[kernel_name]
+    sim = F.Sim(prob, precision=F.F32, kernel=kernel, steps_per_launch=k, tile=tile, use_graph=graph)
+    E = prob.opts.epoch_steps
+    stream = torch.cuda.current_stream()
+    # steps per launch: K for the temporal-blocked kernel, else 1; time whole epochs
+    per_launch = (k or 4) if kernel_name == "tiled" else 1
+    n_launch_total = max(E // per_launch, (steps_req + per_launch - 1) // per_launch)
+    n_launch_total = (n_launch_total + (E // per_launch) - 1) // (E // per_launch) * (E // per_launch)
+    steps = n_launch_total * per_launch
+    # warm-up: whole epochs so the timed region starts at an epoch start
+    warm = max(warmup, E)
+    warm = (warm + E - 1) // E * E
+    for _ in range(warm // per_launch):
+        sim.step(per_launch)
+    sim.sync()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch_total + 1)]
+    step0 = int(sim.ledger()["step"])
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for j in range(n_launch_total):
+        sim.step(per_launch)
+        ev[j + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    per = [ev[j].elapsed_time(ev[j + 1]) for j in range(n_launch_total)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    sim.sync()
+    # launches that did not start an epoch run the step kernel alone
+    starts = [(step0 + j * per_launch) % E == 0 for j in range(n_launch_total)]
+    kern = [per[j] for j in range(n_launch_total) if not starts[j]]
+    kern_ms = statistics.mean(kern) if kern else statistics.mean(per)
+    n_epochs = sum(starts)
+    launches = n_launch_total + n_epochs * (1 + (1 if sim_inflows(prob) else 0))
+    return {"sim": sim, "total_ms": total_ms, "kern_ms": kern_ms, "per_launch": per_launch, "steps": steps,
+            "clocks": clk, "launches": launches, "ledger": sim.ledger()}
+
+
 def run_gpu(args):
     import torch
     import paper_2204_10323_gb300 as F
@@ -173,57 +230,14 @@ def run_gpu(args):
 
     prob, wname = workload(args.workload)
     ncell = prob.nx * prob.ny
-    kernel = {"rows": F.KERNEL_ROWS, "tiled": F.KERNEL_TILED, "reference": F.KERNEL_REFERENCE,
-              "stream": F.KERNEL_STREAM}[args.kernel]
-    tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else (0, 0)
-    sim = F.Sim(prob, precision=F.F32, kernel=kernel, steps_per_launch=args.k, tile=tile, use_graph=args.graph)
     E = prob.opts.epoch_steps
     h0, qx0, qy0 = prob.initial_state(np.float32)
     stream = torch.cuda.current_stream()
-
-    # steps per launch: K for the temporal-blocked kernel, else 1; time whole epochs
-    per_launch = (args.k or 4) if args.kernel == "tiled" else 1
-    n_launch_total = max(E // per_launch, (args.steps + per_launch - 1) // per_launch)
-    n_launch_total = (n_launch_total + (E // per_launch) - 1) // (E // per_launch) * (E // per_launch)
-    steps = n_launch_total * per_launch
-
-    # warm-up: whole epochs so the timed region starts at an epoch start
-    warm = max(args.warmup, E)
-    warm = (warm + E - 1) // E * E
-    for _ in range(warm // per_launch):
-        sim.step(per_launch)
-    sim.sync()
-
-    # timed region: one event per launch on the library's stream
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch_total + 1)]
-    step0 = int(sim.ledger()["step"])
-    torch.cuda.synchronize()
-    ev[0].record(stream)
-    for k in range(n_launch_total):
-        sim.step(per_launch)
-        ev[k + 1].record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(n_launch_total)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    sim.sync()
-    L = sim.ledger()
-    # launches that did not start an epoch run the step kernel alone
-    starts = [(step0 + k * per_launch) % E == 0 for k in range(n_launch_total)]
-    kern = [per[k] for k in range(n_launch_total) if not starts[k]]
-    kern_ms = statistics.mean(kern) if kern else statistics.mean(per)
-    n_epochs = sum(starts)
-    launches = n_launch_total + n_epochs * (1 + (1 if sim_inflows(prob) else 0))
+    tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else (0, 0)
+    run = timed_run(F, torch, prob, args.kernel, args.k, tile, args.graph, args.steps, args.warmup, local, dist)
+    sim, total_ms, kern_ms, per_launch, steps = run["sim"], run["total_ms"], run["kern_ms"], run["per_launch"], \
+        run["steps"]
+    clk, launches, L = run["clocks"], run["launches"], run["ledger"]
     args.steps = steps
 
     value = world * ncell * steps / (total_ms * 1e-3) / 1e9
@@ -232,6 +246,8 @@ def run_gpu(args):
     traffic = None
     if args.traffic_bytes:
         traffic = float(args.traffic_bytes)
+    elif args.workload == "c3" and (args.kernel, per_launch) in TRAFFIC_B_PER_CELL:
+        traffic = TRAFFIC_B_PER_CELL[(args.kernel, per_launch)] * ncell
 
     # end to end through the C ABI with host buffers: upload state, K steps, read depth + ledger
     pin_h = torch.from_numpy(h0).pin_memory()
@@ -266,10 +282,13 @@ def run_gpu(args):
             "ledger": {k: L[k] for k in ("t", "dt", "V_in", "V_out", "V_clip", "volume")}}
     sim.close()
     del sim
+    if args.kernel != "tiled" and not args.no_temporal:
+        line["temporal_blocking"] = temporal_leg(F, torch, prob, args, local, dist, ncell, peak)
     if not args.no_adjoint:
         line["adjoint"] = adjoint_ratio(F, torch)
     if not args.no_ensemble:
-        line["ensemble"] = ensemble_throughput(F, torch, value)
+        shape = [int(v) for v in args.ensemble_shape.split(",")] if args.ensemble_shape else None
+        line["ensemble"] = ensemble_throughput(F, torch, value, shape=shape)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, seconds_target=args.cpu_seconds)
     if rank == 0:
@@ -277,6 +296,22 @@ def run_gpu(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def temporal_leg(F, torch, prob, args, local, dist, ncell, peak, K: int = 4):
+    """The same workload on the temporal-blocking kernel (K steps per launch):
+    whole-job Gcell-updates/s, and its kernel time as an equivalent fraction of
+    the one-step HBM roofline (32 B per cell-update), beside the DRAM bytes it
+    actually moves per launch."""
+    run = timed_run(F, torch, prob, "tiled", K, (0, 0), args.graph, args.steps, args.warmup, local, dist)
+    run["sim"].close()
+    value = ncell * run["steps"] / (run["total_ms"] * 1e-3) / 1e9
+    eq = BYTES_PER_CELL * ncell * K / (run["kern_ms"] * 1e-3) / 1e9
+    tr = TRAFFIC_B_PER_CELL.get(("tiled", K)) if args.workload == "c3" else None
+    return {"kernel": "tiled", "steps_per_launch": K, "value": value, "unit": UNIT,
+            "ms_per_step": run["total_ms"] / run["steps"], "kernel_ms_per_launch": run["kern_ms"],
+            "equivalent_gbs": eq, "frac_of_one_step_roofline": eq / peak,
+            "traffic_per_launch": tr * ncell if tr else None, "clocks": run["clocks"]}
 
 
 def adjoint_ratio(F, torch, steps: int = 2000, checkpoints: int = 40):
@@ -325,7 +360,7 @@ def adjoint_ratio(F, torch, steps: int = 2000, checkpoints: int = 40):
             "gradient_ms": t_grad, "forward_run_ms": t_fwd}
 
 
-def ensemble_throughput(F, torch, single_value: float, n: int = 96, steps: int = 1024):
+def ensemble_throughput(F, torch, single_value: float, n: int = 96, steps: int = 1024, shape=None):
     """96 uneven scenarios (256^2 .. 2048^2, own terrain seed, n ~ U(0.02, 0.08),
     hydrograph peak ~ U(100, 1000) m^3/s), primed ~30 % wet, stepped together
     with the autotuned launch shape; Gcell-updates/s over all scenarios."""
@@ -337,7 +372,11 @@ def ensemble_throughput(F, torch, single_value: float, n: int = 96, steps: int =
         p.h0 = inputs.wet_start(p.z, p.dx, 0.3)
         probs.append(p)
     ens = F.Ensemble(probs)
-    tune = autotune.tune_ensemble(ens, use_cache=False)
+    if shape:                              # a fixed launch shape instead of tuning
+        autotune.apply(ens, tuple(shape))
+        tune = {"shape": list(shape), "trials": []}
+    else:
+        tune = autotune.tune_ensemble(ens, use_cache=False)
     spg = tune["shape"][3]                 # (K, warps, rows, steps per graph)
     steps = max(spg, steps // spg * spg)
     ens.step(spg)
@@ -379,6 +418,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-temporal", action="store_true", help="skip the temporal-blocking leg")
+    ap.add_argument("--ensemble-shape", default="", help="K,warps,rows,steps_per_graph instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
