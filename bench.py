@@ -34,8 +34,9 @@ BYTES_PER_CELL = 32          # read h, qx, qy, z, n (20 B) + write h, qx, qy (12
 # workload: one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
 # the 4096^2 case of the same workload (state > L2), scaled by the cell count;
 # key (kernel, steps per launch).  The summaries are under profiles/.
-# (profiles/step_stream_4096_full.md, step_tiled4_4096_full.md, step_rows_4096_full.md)
-TRAFFIC_B_PER_CELL = {("stream", 1): 32.24, ("tiled", 4): 31.62, ("rows", 1): 30.92}
+# (profiles/step_stream_4096_full.md, step_tiled4_4096_full.md, step_rows_4096_full.md,
+# step_tma_4096_full.md)
+TRAFFIC_B_PER_CELL = {("stream", 1): 32.24, ("tiled", 4): 31.62, ("rows", 1): 30.92, ("tma", 1): 32.17}
 METRIC = "Gcell-updates/s and % of HBM roofline (FP32, 1 GB300); adjoint/forward time ratio"
 UNIT = "Gcell-updates/s"
 
@@ -168,7 +169,7 @@ def timed_run(F, torch, prob, kernel_name, k, tile, graph, steps_req, warmup, lo
     """Warm up and time whole epochs of one kernel on `prob`: CUDA events around
     every launch on the library's stream, nvidia-smi clocks sampled meanwhile."""
     kernel = {"rows": F.KERNEL_ROWS, "tiled": F.KERNEL_TILED, "reference": F.KERNEL_REFERENCE,
-              "stream": F.KERNEL_STREAM}[kernel_name]
+              "stream": F.KERNEL_STREAM, "tma": F.KERNEL_TMA}[kernel_name]
     sim = F.Sim(prob, precision=F.F32, kernel=kernel, steps_per_launch=k, tile=tile, use_graph=graph)
     E = prob.opts.epoch_steps
     stream = torch.cuda.current_stream()
@@ -409,7 +410,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c3")
-    ap.add_argument("--kernel", default="stream", choices=["stream", "rows", "tiled", "reference"])
+    ap.add_argument("--kernel", default="stream", choices=["stream", "rows", "tiled", "tma", "reference"])
     ap.add_argument("--k", type=int, default=0, help="steps per launch (tiled kernel)")
     ap.add_argument("--graph", action="store_true")
     ap.add_argument("--tile", default="", help="stream kernel launch shape: warps,rows")

@@ -95,8 +95,9 @@ typedef enum {
     FLOOD_KERNEL_AUTO = 0,
     FLOOD_KERNEL_REFERENCE = 1,  /* one thread per cell, IEEE ops in the oracle's order */
     FLOOD_KERNEL_ROWS = 2,       /* one warp per 128-column strip, float4 row streaming */
-    FLOOD_KERNEL_TILED = 3,      /* shared-memory tiles, K steps per launch (temporal blocking) */
-    FLOOD_KERNEL_STREAM = 4      /* one warp per 128-column strip, rows staged by bulk copies (default) */
+    FLOOD_KERNEL_TILED = 3,      /* pipeline of K warps per strip, K steps per launch (temporal blocking) */
+    FLOOD_KERNEL_STREAM = 4,     /* one warp per 128-column strip, rows staged by bulk copies (default) */
+    FLOOD_KERNEL_TMA = 5         /* as STREAM, rows staged as 2D tiles by tensor-map (TMA) copies */
 } flood_kernel;
 
 typedef struct {

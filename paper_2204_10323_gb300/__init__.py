@@ -25,7 +25,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_CFL, ERR_TIMEOUT, ERR_STATE, 
 F32, F64 = 0, 1
 XMIN, XMAX, YMIN, YMAX = 0, 1, 2, 3
 INFLOW, OUTFLOW = 0, 1
-KERNEL_AUTO, KERNEL_REFERENCE, KERNEL_ROWS, KERNEL_TILED, KERNEL_STREAM = 0, 1, 2, 3, 4
+KERNEL_AUTO, KERNEL_REFERENCE, KERNEL_ROWS, KERNEL_TILED, KERNEL_STREAM, KERNEL_TMA = 0, 1, 2, 3, 4, 5
 FIELD_H, FIELD_QX, FIELD_QY, FIELD_Z, FIELD_N, FIELD_LEDGER = 0, 1, 2, 3, 4, 5
 LEDGER_KEYS = ("t", "dt", "V_in", "V_out", "V_clip", "volume", "h_max", "step", "cfl_exceed")
 

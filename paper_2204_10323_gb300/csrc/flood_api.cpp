@@ -242,6 +242,7 @@ flood_status launch_steps(flood_handle *h, int s, int k, int want_hmax, const in
             }
             break;
         case FLOOD_KERNEL_STREAM: e = launch_step_stream(a, h->stream); break;
+        case FLOOD_KERNEL_TMA: e = launch_step_tma(a, h->stream); break;
         default: e = launch_step_rows(a, h->stream); break;
         }
     }
@@ -305,7 +306,7 @@ static flood_status validate(const flood_grid *grid, const flood_bc_section *sec
         return fail(nullptr, FLOOD_ERR_ARG, "g, h_dry, cfl_alpha, dt_cap, dt_const must be > 0");
     if (o.dt_mode != 0 && o.dt_mode != 1) return fail(nullptr, FLOOD_ERR_ARG, "dt_mode must be 0 or 1");
     if (o.bc_form != 0 && o.bc_form != 1) return fail(nullptr, FLOOD_ERR_ARG, "bc_form must be 0 or 1");
-    if (o.kernel < 0 || o.kernel > 4) return fail(nullptr, FLOOD_ERR_ARG, "unknown kernel");
+    if (o.kernel < 0 || o.kernel > 5) return fail(nullptr, FLOOD_ERR_ARG, "unknown kernel");
     if (o.tile_x < 0 || o.tile_y < 0) return fail(nullptr, FLOOD_ERR_ARG, "tile_x and tile_y must be >= 0");
     if (o.kernel == FLOOD_KERNEL_TILED) {
         int K = o.steps_per_launch > 0 ? o.steps_per_launch : 4;

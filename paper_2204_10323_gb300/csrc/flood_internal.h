@@ -91,6 +91,7 @@ cudaError_t launch_step_stream_ensemble(const StepArgs<float> *table, const int 
                                         int warps, int rows, int step, int want_hmax, cudaStream_t st);
 // Blocks of one grid for the stream kernel, and the (warps, rows) a tile pair selects.
 int stream_blocks(const Geom &g, int warps, int rows);
+cudaError_t launch_step_tma(const StepArgs<float> &a, cudaStream_t st);
 // Temporal blocking over many grids: the (chunk, strip) items of grid k are
 // base[k] .. base[k+1] - 1 (tiled_items per grid), k_steps steps from s0.
 int tiled_items(const Geom &g, int chunk_rows);

@@ -13,6 +13,10 @@
 // Waits are bounded: a stage that does not complete within ~2 s sets the
 // timeout status bit, the warp waits (bounded) for its copies in flight and
 // leaves without storing.
+#include <cuda.h>
+
+#include <type_traits>
+
 #include "fast_face.cuh"
 #include "tma_util.cuh"
 
@@ -37,6 +41,26 @@ struct alignas(16) WarpRing {
 
 static_assert(sizeof(WarpRing) % 16 == 0, "per-warp ring must keep 16-byte alignment");
 
+// The TMA-tile variant stages 2D tiles: per stage and field one tensor copy of
+// kRowsT rows x kSeg columns (box origin x0-4, 16-byte aligned; elements
+// outside the grid arrive as zeros).  A tensor copy's shared-memory
+// destination must be 128-byte aligned, so each field's tile takes a slot of
+// kSlotT floats (a multiple of 32) and the ring a multiple of 128 bytes.
+constexpr int kRowsT = 2;        // rows per staged tile
+constexpr int kStagesT = 2;      // tiles in flight per warp
+constexpr int kSlotT = 288;      // >= kRowsT * kSeg, multiple of 32 floats
+struct alignas(128) WarpRingT {
+    float buf[kStagesT][kFields][kSlotT];
+    uint64_t bar[kStagesT];
+};
+static_assert(kSlotT >= kRowsT * kSeg && kSlotT % 32 == 0, "tile slot must hold the box and keep 128 B alignment");
+static_assert(sizeof(WarpRingT) % 128 == 0, "per-warp tile ring must keep 128-byte alignment");
+
+// Tensor maps of h, z, n, qx, qy (the current buffers) for the TMA-tile kernel.
+struct TmaMaps {
+    CUtensorMap m[kFields];
+};
+
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
 __device__ __forceinline__ float get(const float4 &v, int k)
@@ -60,10 +84,16 @@ __device__ __forceinline__ void set(float4 &v, int k, float x)
 // those of ring_base + idx.  fresh: the ring's barriers still need their
 // initialisation.  Returns true if a wait on a copy timed out (the status word
 // then has the timeout bit).
+//
+// kTensor: stage 2D tiles of kRowsT rows with tensor copies (maps: the grid's
+// tensor maps; the ring counts tiles) instead of one 1D copy per row.
+template <bool kTensor>
 __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int step, const int want_hmax, const int bx,
                                             const int by, const int rows, unsigned char *smem_raw, double *red,
-                                            uint32_t &ring_base, const bool fresh)
+                                            uint32_t &ring_base, const bool fresh, const TmaMaps *maps = nullptr)
 {
+    constexpr int R = kTensor ? kRowsT : 1;            // rows per stage
+    constexpr int NS = kTensor ? kStagesT : kDepth;    // stages in flight
     const Geom &G = a.geo;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nx = G.nx, ny = G.ny;
@@ -77,7 +107,14 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
     const int jstart = y0 > 0 ? y0 - 1 : 0;
     const int jlast = min(y1, ny - 1);             // last row that is staged
     const int nload = jlast - jstart + 1;
-    WarpRing &ring = reinterpret_cast<WarpRing *>(smem_raw)[warp];
+    const int nstage = (nload + R - 1) / R;        // stages (tiles) to stage
+    using Ring = typename std::conditional<kTensor, WarpRingT, WarpRing>::type;
+    Ring &ring = reinterpret_cast<Ring *>(smem_raw)[warp];
+    // field f of staged row `sub` of stage slot s: columns x0-4 .. x0+131 at offsets 0 .. 135
+    auto row_at = [&](uint32_t s, int f, int sub) -> const float * {
+        if constexpr (kTensor) return &ring.buf[s][f][sub * kSeg];
+        else return &ring.buf[s][f][0];
+    };
 
     const double dtd = a.ctrl->dt;
     FastConst K;
@@ -99,22 +136,28 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
     const float *fields[kFields] = {a.h, a.z, a.n, a.qx, a.qy};
 
     if (fresh && lane == 0) {                 // every warp: it may be idle here and busy on a later item
-        for (int s = 0; s < kDepth; s++) mbar_init(&ring.bar[s], 1);
+        for (int s = 0; s < NS; s++) mbar_init(&ring.bar[s], 1);
         fence_mbar_init();
     }
     __syncwarp();
-    auto issue = [&](int idx) {
-        const uint32_t s = (ring_base + (uint32_t)idx) % kDepth;
-        const size_t row = (size_t)(jstart + idx) * P + cs;
-        mbar_arrive_expect_tx(&ring.bar[s], seg_bytes * kFields);
+    auto issue = [&](int st) {                // stage st covers staged rows st*R .. st*R + R - 1
+        const uint32_t s = (ring_base + (uint32_t)st) % NS;
+        if constexpr (kTensor) {
+            mbar_arrive_expect_tx(&ring.bar[s], (uint32_t)(kFields * kRowsT * kSeg * 4));
 #pragma unroll
-        for (int f = 0; f < kFields; f++) bulk_copy_g2s(&ring.buf[s][f][so], fields[f] + row, seg_bytes, &ring.bar[s]);
+            for (int f = 0; f < kFields; f++) tma_load_2d(&ring.buf[s][f][0], &maps->m[f], x0 - 4, jstart + st * R, &ring.bar[s]);
+        } else {
+            const size_t row = (size_t)(jstart + st) * P + cs;
+            mbar_arrive_expect_tx(&ring.bar[s], seg_bytes * kFields);
+#pragma unroll
+            for (int f = 0; f < kFields; f++) bulk_copy_g2s(&ring.buf[s][f][so], fields[f] + row, seg_bytes, &ring.bar[s]);
+        }
     };
-    int issued = 0, consumed = 0;
+    int issued = 0, consumed = 0;             // stages
     bool abort = false;
     if (active && lane == 0) {
         fence_proxy_async();              // this warp's reads of an earlier item come first
-        for (; issued < min(kDepth, nload); issued++) issue(issued);
+        for (; issued < min(NS, nstage); issued++) issue(issued);
     }
 
     float4 hp = make_float4(0, 0, 0, 0), zp = hp, np_ = hp;
@@ -126,36 +169,41 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
             float4 ch = make_float4(0, 0, 0, 0), cz = ch, cn = ch, cqx = ch, cqy = ch;
             float hW = 0.f, zW = 0.f, nW = 0.f, hE = 0.f, zE = 0.f, nE = 0.f, qxE = 0.f;
             if (j < ny) {
-                const uint32_t g = ring_base + (uint32_t)idx;
-                const uint32_t s = g % kDepth;
-                bool ok = mbar_wait_bounded(&ring.bar[s], (g / kDepth) & 1u, kBudgetNs);
-                if (__any_sync(0xffffffffu, !ok)) {
-                    abort = true;
-                    break;
+                const int st = idx / R, sub = idx - st * R;
+                const uint32_t g = ring_base + (uint32_t)st;
+                const uint32_t s = g % NS;
+                if (sub == 0) {               // first row of a stage: wait for its copies
+                    bool ok = mbar_wait_bounded(&ring.bar[s], (g / NS) & 1u, kBudgetNs);
+                    if (__any_sync(0xffffffffu, !ok)) {
+                        abort = true;
+                        break;
+                    }
+                    consumed = st + 1;
                 }
-                consumed = idx + 1;
                 const int o = 4 + 4 * lane;
-                ch = lds4(&ring.buf[s][0][o]);
-                cz = lds4(&ring.buf[s][1][o]);
-                cn = lds4(&ring.buf[s][2][o]);
-                cqx = lds4(&ring.buf[s][3][o]);
-                cqy = lds4(&ring.buf[s][4][o]);
+                ch = lds4(row_at(s, 0, sub) + o);
+                cz = lds4(row_at(s, 1, sub) + o);
+                cn = lds4(row_at(s, 2, sub) + o);
+                cqx = lds4(row_at(s, 3, sub) + o);
+                cqy = lds4(row_at(s, 4, sub) + o);
                 if (lane == 0) {
-                    hW = ring.buf[s][0][3];
-                    zW = ring.buf[s][1][3];
-                    nW = ring.buf[s][2][3];
+                    hW = row_at(s, 0, sub)[3];
+                    zW = row_at(s, 1, sub)[3];
+                    nW = row_at(s, 2, sub)[3];
                 }
                 if (lane == 31) {
-                    hE = ring.buf[s][0][132];
-                    zE = ring.buf[s][1][132];
-                    nE = ring.buf[s][2][132];
-                    qxE = ring.buf[s][3][132];
+                    hE = row_at(s, 0, sub)[132];
+                    zE = row_at(s, 1, sub)[132];
+                    nE = row_at(s, 2, sub)[132];
+                    qxE = row_at(s, 3, sub)[132];
                 }
-                __syncwarp();
-                if (lane == 0 && issued < nload) {
-                    fence_proxy_async();
-                    issue(issued);
-                    issued++;
+                if (sub == R - 1) {           // stage read completely: refill it
+                    __syncwarp();
+                    if (lane == 0 && issued < nstage) {
+                        fence_proxy_async();
+                        issue(issued);
+                        issued++;
+                    }
                 }
             }
             if (j < y0) {                 // halo row south of the chunk
@@ -299,13 +347,13 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
             if (lane == 0) {
                 for (int k = consumed; k < issued; k++) {
                     const uint32_t g = ring_base + (uint32_t)k;
-                    mbar_wait_bounded(&ring.bar[g % kDepth], (g / kDepth) & 1u, kBudgetNs);
+                    mbar_wait_bounded(&ring.bar[g % NS], (g / NS) & 1u, kBudgetNs);
                 }
                 atomicOr(&a.ctrl->status, kStatusTimeout);
             }
             __syncwarp();
         }
-        if (!abort) ring_base += (uint32_t)nload;
+        if (!abort) ring_base += (uint32_t)nstage;
     }
     double bo = block_reduce<false>(vout, red);
     if (threadIdx.x == 0 && bo != 0.0) atomicAdd(&a.ctrl->V_out, dtd * bo);
@@ -332,7 +380,18 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 5) step_stream_kernel(const St
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     uint32_t ring_base = 0;
-    stream_body(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, smem_raw, red, ring_base, true);
+    stream_body<false>(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, smem_raw, red, ring_base, true);
+}
+
+// The same step with every warp's rows staged as 2D tiles by tensor copies.
+__global__ void __launch_bounds__(kMaxWarps * 32, 4)
+    step_tma_kernel(const StepArgs<float> a, const int rows, const __grid_constant__ TmaMaps maps)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    unsigned char *base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);   // 128-byte aligned rings
+    uint32_t ring_base = 0;
+    stream_body<true>(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, base, red, ring_base, true, &maps);
 }
 
 // Many grids in one launch: block b belongs to the scenario whose block range
@@ -356,7 +415,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 5)
     const int nbx = (strips + nwarps - 1) / nwarps;
     const int local = b - base[lo];
     uint32_t ring_base = 0;
-    stream_body(a, step, want_hmax, local % nbx, local / nbx, rows, smem_raw, red, ring_base, true);
+    stream_body<false>(a, step, want_hmax, local % nbx, local / nbx, rows, smem_raw, red, ring_base, true);
 }
 
 cudaError_t configure(int warps)
@@ -414,6 +473,70 @@ cudaError_t launch_step_stream(const StepArgs<float> &a, cudaStream_t st)
     dim3 grid((strips + warps - 1) / warps, (a.geo.ny + rows - 1) / rows);
     step_stream_kernel<<<grid, warps * 32, sizeof(WarpRing) * warps, st>>>(a, rows);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.gauge_out) return launch_gauges<float>(a.geo, a.h_out, a.gauge_cells, a.n_gauges, a.gauge_out, st);
+    return cudaSuccess;
+}
+
+// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point
+// query, so the library needs no link against the driver library).
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encode_tiled()
+{
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// Map of a pitched FP32 field of `height` rows: boxes of kRowsT rows x kSeg
+// columns, zero fill outside [0, pitch) x [0, height).
+static cudaError_t encode_field(EncodeTiled fn, CUtensorMap *m, const float *base, int pitch, int height)
+{
+    const cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)height};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kSeg, (cuuint32_t)kRowsT};
+    const cuuint32_t elem[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, elem,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step_tma(const StepArgs<float> &a, cudaStream_t st)
+{
+    EncodeTiled fn = encode_tiled();
+    if (!fn) return cudaErrorNotSupported;
+    int warps, rows;
+    stream_launch_shape(a.geo, a.tile_x, a.tile_y, &warps, &rows);
+    const size_t smem = sizeof(WarpRingT) * warps + 128;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(step_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(WarpRingT) * kMaxWarps + 128));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int P = a.geo.pitch, ny = a.geo.ny;
+    TmaMaps maps;
+    const float *f[kFields] = {a.h, a.z, a.n, a.qx, a.qy};
+    for (int k = 0; k < kFields; k++) {
+        cudaError_t e = encode_field(fn, &maps.m[k], f[k], P, k == 4 ? ny + 1 : ny);
+        if (e != cudaSuccess) return e;
+    }
+    const int strips = (a.geo.nx + 127) / 128;
+    dim3 grid((strips + warps - 1) / warps, (ny + rows - 1) / rows);
+    step_tma_kernel<<<grid, warps * 32, smem, st>>>(a, rows, maps);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.gauge_out) return launch_gauges<float>(a.geo, a.h_out, a.gauge_cells, a.n_gauges, a.gauge_out, st);
     return cudaSuccess;

@@ -115,6 +115,10 @@ def test_create_rejects_bad_options():
     st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
     assert st == F.ERR_ARG
     o = F.default_opts()
+    o.kernel = 6                  # no such kernel family
+    st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
+    assert st == F.ERR_ARG and "kernel" in F.flood_last_error(None)
+    o = F.default_opts()
     o.tile_y = -1
     st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
     assert st == F.ERR_ARG and "tile" in F.flood_last_error(None)

@@ -90,7 +90,7 @@ def test_options_fp64_match_oracle(bc_form, dt_mode):
 
 
 # ---------------------------------------------------------------- FP32 parity
-@pytest.mark.parametrize("kernel", [1, 2, 4])
+@pytest.mark.parametrize("kernel", [1, 2, 4, 5])
 def test_c1_fp32_matches_oracle_1000_steps(kernel):
     p = inputs.c1_tilted_channel()
     o, V0, h, qx, qy, L = run_pair(p, 1000, F().F32, kernel=kernel)
@@ -102,7 +102,7 @@ def test_c1_fp32_matches_oracle_1000_steps(kernel):
     assert abs(bal) / L["V_in"] < TOL32_MASS
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 4])
+@pytest.mark.parametrize("kernel", [1, 2, 4, 5])
 @pytest.mark.parametrize("shape,seed", [((33, 17), 0), ((7, 5), 1), ((130, 70), 2), ((257, 129), 6),
                                         ((1, 1), 7), ((1, 40), 3), ((40, 1), 4), ((128, 32), 8), ((129, 33), 9)])
 def test_random_fp32_matches_oracle(kernel, shape, seed):
@@ -123,7 +123,7 @@ def test_c2_fp32_parity_1000_steps():
 
 
 # ---------------------------------------------------------------- invariants on the GPU
-@pytest.mark.parametrize("precision,kernel", [(0, 1), (0, 2), (0, 4), (1, 1)])
+@pytest.mark.parametrize("precision,kernel", [(0, 1), (0, 2), (0, 4), (0, 5), (1, 1)])
 def test_lake_at_rest_is_exact_on_gpu(precision, kernel):
     p = inputs.lake_at_rest(67, 45)
     s = F().Sim(p, precision=precision, kernel=kernel)
@@ -294,6 +294,26 @@ def test_tiled_many_items_per_pipeline_bitwise(K, shape, seed, tile):
         assert Lb[k] == pytest.approx(La[k], rel=1e-12, abs=1e-12), k
     for k in ("V_out", "V_clip"):
         assert Lb[k] == pytest.approx(La[k], rel=1e-6, abs=1e-9), k
+
+
+@pytest.mark.parametrize("shape,seed,tile", [((130, 70), 2, (0, 0)), ((257, 129), 6, (2, 9)), ((7, 5), 1, (0, 0)),
+                                             ((1, 40), 3, (1, 3)), ((40, 1), 4, (0, 0)), ((361, 97), 16, (4, 64)),
+                                             ((129, 33), 9, (3, 1))])
+def test_tma_tiles_equal_row_staging_bitwise(shape, seed, tile):
+    """Rows staged as 2D tensor-map tiles (zero-filled outside the grid) give the
+    bits and the ledger of rows staged by 1D bulk copies, for every launch shape."""
+    Fm = F()
+    p = as_f32_problem(inputs.random_small(shape[0], shape[1], seed))
+    a = Fm.Sim(p, kernel=Fm.KERNEL_STREAM, tile=tile)
+    b = Fm.Sim(p, kernel=Fm.KERNEL_TMA, tile=tile)
+    for n in (5, 12, 1, 30):
+        a.step(n)
+        b.step(n)
+    for f in (Fm.FIELD_H, Fm.FIELD_QX, Fm.FIELD_QY):
+        assert np.array_equal(a.read(f), b.read(f)), f
+    La, Lb = a.ledger(), b.ledger()
+    for k in ("V_in", "V_out", "V_clip", "volume", "t", "h_max"):
+        assert Lb[k] == pytest.approx(La[k], rel=1e-12, abs=1e-12), k
 
 
 def test_tiled_c1_matches_oracle_and_lake_at_rest():
