@@ -34,9 +34,9 @@ BYTES_PER_CELL = 32          # read h, qx, qy, z, n (20 B) + write h, qx, qy (12
 # workload: one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
 # the 4096^2 case of the same workload (state > L2), scaled by the cell count;
 # key (kernel, steps per launch).  The summaries are under profiles/.
-# (profiles/step_stream_4096_full.md, step_tiled4_4096_full.md, step_rows_4096_full.md,
-# step_tma_4096_full.md)
-TRAFFIC_B_PER_CELL = {("stream", 1): 32.24, ("tiled", 4): 31.62, ("rows", 1): 30.92, ("tma", 1): 32.17}
+# (profiles/step_*_4096_full.md, profiles/roofline_study_16384.md)
+TRAFFIC_B_PER_CELL = {("stream", 1): 32.24, ("tma", 1): 32.18, ("rows", 1): 30.94, ("tiled", 1): 30.40,
+                      ("tiled", 2): 30.68, ("tiled", 4): 31.59, ("tiled", 8): 30.81}
 METRIC = "Gcell-updates/s and % of HBM roofline (FP32, 1 GB300); adjoint/forward time ratio"
 UNIT = "Gcell-updates/s"
 

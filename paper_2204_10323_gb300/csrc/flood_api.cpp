@@ -268,6 +268,7 @@ flood_status advance(flood_handle *h, int64_t n, const int64_t *gcells, int ng, 
         int k = 1;
         if (h->prec == FLOOD_F32 && h->kernel == FLOOD_KERNEL_TILED && !gcells) {
             k = std::min<int64_t>(h->k_per_launch, std::min<int64_t>(E - s, n - done));
+            if (k > 4 && k < 8) k = 4;   // the kernel exists for 1..4 and 8 steps per launch
         }
         int want = (s + k == E) ? 1 : 0;
         flood_status st = launch_steps(h, s, k, want, gcells, ng, gcells ? gbuf + done * ng : nullptr);
@@ -310,8 +311,8 @@ static flood_status validate(const flood_grid *grid, const flood_bc_section *sec
     if (o.tile_x < 0 || o.tile_y < 0) return fail(nullptr, FLOOD_ERR_ARG, "tile_x and tile_y must be >= 0");
     if (o.kernel == FLOOD_KERNEL_TILED) {
         int K = o.steps_per_launch > 0 ? o.steps_per_launch : 4;
-        if (K > 4 || o.epoch_steps % K != 0)
-            return fail(nullptr, FLOOD_ERR_ARG, "steps_per_launch must divide epoch_steps and be <= 4");
+        if (!(K <= 4 || K == 8) || o.epoch_steps % K != 0)
+            return fail(nullptr, FLOOD_ERR_ARG, "steps_per_launch must be 1..4 or 8 and divide epoch_steps");
     }
     std::vector<int> used(2 * (size_t)grid->nx + 2 * (size_t)grid->ny, 0);
     for (int k = 0; k < nsec; k++) {

@@ -67,7 +67,7 @@ flood_status build_tables(flood_ensemble *e)
     std::vector<int> base(n + 1, 0), tbase(n + 1, 0);
     for (int k = 0; k < n; k++) {
         base[k + 1] = base[k] + stream_blocks(e->members[e->order[k]]->geo, e->warps, e->rows);
-        tbase[k + 1] = tbase[k] + tiled_items(e->members[e->order[k]]->geo, e->rows);
+        tbase[k + 1] = tbase[k] + tiled_items(e->members[e->order[k]]->geo, e->rows, e->k_steps);
     }
     e->total_blocks = base[n];
     e->total_items = tbase[n];
@@ -111,9 +111,14 @@ flood_status ensemble_step(flood_ensemble *e, int64_t limit, cudaStream_t st, in
     cudaError_t c;
     if (e->kernel == FLOOD_KERNEL_TILED) {
         steps = (int)std::min<int64_t>(e->k_steps, std::min<int64_t>(E - s, limit));
+    }
+    // the item table is laid out for k_steps: 8-step tables (wider halos) take
+    // only whole 8-step launches, anything shorter runs single stream steps
+    if (e->kernel == FLOOD_KERNEL_TILED && !(e->k_steps == 8 && steps < 8)) {
         c = launch_step_tiled_ensemble(e->table[parity], e->tbase, n, e->total_items, e->rows, steps, s,
                                        s + steps == E ? 1 : 0, st);
     } else {
+        steps = 1;
         c = launch_step_stream_ensemble(e->table[parity], e->base, n, e->total_blocks, e->warps, e->rows, s,
                                         s == E - 1 ? 1 : 0, st);
     }
@@ -284,12 +289,11 @@ extern "C" flood_status flood_ensemble_set_kernel(flood_ensemble *e, int32_t ker
     if (kernel != FLOOD_KERNEL_STREAM && kernel != FLOOD_KERNEL_TILED)
         return efail(e, FLOOD_ERR_ARG, "ensemble kernel must be FLOOD_KERNEL_STREAM or FLOOD_KERNEL_TILED");
     const int K = steps_per_launch > 0 ? steps_per_launch : 4;
-    if (kernel == FLOOD_KERNEL_TILED && (K > 4 || e->E % K != 0))
-        return efail(e, FLOOD_ERR_ARG, "steps_per_launch must divide epoch_steps and be <= 4");
+    if (kernel == FLOOD_KERNEL_TILED && (!(K <= 4 || K == 8) || e->E % K != 0))
+        return efail(e, FLOOD_ERR_ARG, "steps_per_launch must be 1..4 or 8 and divide epoch_steps");
     e->kernel = kernel;
     e->k_steps = kernel == FLOOD_KERNEL_TILED ? K : 1;
-    drop_graphs(e);
-    return FLOOD_OK;
+    return build_tables(e);                  // item counts depend on K; drops the graphs
 }
 
 extern "C" flood_status flood_ensemble_step(flood_ensemble *e, int64_t n_steps)

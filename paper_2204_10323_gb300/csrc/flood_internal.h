@@ -94,7 +94,7 @@ int stream_blocks(const Geom &g, int warps, int rows);
 cudaError_t launch_step_tma(const StepArgs<float> &a, cudaStream_t st);
 // Temporal blocking over many grids: the (chunk, strip) items of grid k are
 // base[k] .. base[k+1] - 1 (tiled_items per grid), k_steps steps from s0.
-int tiled_items(const Geom &g, int chunk_rows);
+int tiled_items(const Geom &g, int chunk_rows, int k_steps);
 cudaError_t launch_step_tiled_ensemble(const StepArgs<float> *table, const int *base, int n, int total_items,
                                        int chunk_rows, int k_steps, int s0, int want_hmax, cudaStream_t st);
 void stream_launch_shape(const Geom &g, int tile_x, int tile_y, int *warps, int *rows);

@@ -30,8 +30,10 @@ namespace flood {
 
 namespace {
 
-constexpr int kHalo = 4;                    // halo columns per side (= largest K)
-constexpr int kOut = 128 - 2 * kHalo;       // output columns per strip
+// halo columns per side (at least K: the dependency cone of K steps) and
+// output columns of a 128-column strip, per steps per launch K
+__host__ __device__ constexpr int halo_cols(int K) { return K <= 4 ? 4 : 8; }
+__host__ __device__ constexpr int out_cols(int K) { return 128 - 2 * halo_cols(K); }
 // level-1 rows in flight and pipelines per SM: one grid uses 6 and 6 (six
 // pipelines of 4 warps fit the registers and shared memory of an SM); the
 // ensemble kernel, which keeps more per-scenario state in registers, 8 and 5
@@ -100,7 +102,8 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
     const int step = s0 + (lvl - 1);                  // this level's step in the epoch
     int issued = 0, consumed = 0;
     bool abort = false;
-    const int x0 = strip * kOut - kHalo;
+    constexpr int kOut = out_cols(K);
+    const int x0 = strip * kOut - halo_cols(K);
     const int c0 = x0 + 4 * lane;
     const int own_lo = strip * kOut, own_hi = min(strip * kOut + kOut, nx);
     const int jb = max(y0 - K, 0);
@@ -393,7 +396,7 @@ __device__ __forceinline__ void init_ring(PipeSmem<K, kPF> &sm)
 // One grid: work items (chunk, strip) in chunk-major order, block b takes
 // items b, b + grid, ... (a.tile_x strips, a.tile_y rows per chunk).
 template <int K>
-__global__ void __launch_bounds__(K * 32, K == 4 ? 6 : 1) step_tiled_kernel(const StepArgs<float> a)
+__global__ void __launch_bounds__(K * 32, K == 4 ? 6 : K == 8 ? 2 : 1) step_tiled_kernel(const StepArgs<float> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
@@ -421,7 +424,7 @@ __global__ void __launch_bounds__(K * 32, K == 4 ? 6 : 1) step_tiled_kernel(cons
 // grid's control block when it moves on; the grid's first item books its
 // inflow volume and clock.
 template <int K>
-__global__ void __launch_bounds__(K * 32, K == 4 ? 5 : 1)
+__global__ void __launch_bounds__(K * 32, K == 4 ? 5 : K == 8 ? 2 : 1)
     step_tiled_ensemble_kernel(const StepArgs<float> *table, const int *base, const int n, const int chunk_rows,
                                const int s0, const int want_hmax)
 {
@@ -447,7 +450,7 @@ __global__ void __launch_bounds__(K * 32, K == 4 ? 5 : 1)
         }
         const StepArgs<float> &a = table[lo];
         const int local = item - base[lo];
-        const int n_strips = (a.geo.nx + kOut - 1) / kOut;
+        const int n_strips = (a.geo.nx + out_cols(K) - 1) / out_cols(K);
         const int strip = local % n_strips;
         const int y0 = (local / n_strips) * chunk_rows;
         const int y1 = min(y0 + chunk_rows, a.geo.ny);
@@ -526,7 +529,7 @@ cudaError_t launch_k(const StepArgs<float> &a0, cudaStream_t st)
     if (e != cudaSuccess) return e;
     StepArgs<float> a = a0;
     const int nx = a.geo.nx, ny = a.geo.ny;
-    const int n_strips = (nx + kOut - 1) / kOut;
+    const int n_strips = (nx + out_cols(K) - 1) / out_cols(K);
     if (a0.tile_x > 0 && a0.tile_x < resident) resident = a0.tile_x;   // caller's cap on pipelines
     int chunk_rows = 0, blocks = 0;
     if (a0.tile_y > 0) {                                                // caller's rows per work item
@@ -560,9 +563,9 @@ cudaError_t launch_ens_k(const StepArgs<float> *table, const int *base, int n, i
 
 }  // namespace
 
-int tiled_items(const Geom &g, int chunk_rows)
+int tiled_items(const Geom &g, int chunk_rows, int k_steps)
 {
-    const int n_strips = (g.nx + kOut - 1) / kOut;
+    const int n_strips = (g.nx + out_cols(k_steps) - 1) / out_cols(k_steps);
     return n_strips * ((g.ny + chunk_rows - 1) / chunk_rows);
 }
 
@@ -574,6 +577,7 @@ cudaError_t launch_step_tiled_ensemble(const StepArgs<float> *table, const int *
     case 2: return launch_ens_k<2>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
     case 3: return launch_ens_k<3>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
     case 4: return launch_ens_k<4>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
+    case 8: return launch_ens_k<8>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -585,6 +589,7 @@ cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st)
     case 2: return launch_k<2>(a, st);
     case 3: return launch_k<3>(a, st);
     case 4: return launch_k<4>(a, st);
+    case 8: return launch_k<8>(a, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -114,6 +114,10 @@ def test_create_rejects_bad_options():
     o.steps_per_launch = 3        # must divide E
     st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
     assert st == F.ERR_ARG
+    o.steps_per_launch = 5        # 1..4 or 8
+    o.epoch_steps = 20
+    st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
+    assert st == F.ERR_ARG and "steps_per_launch" in F.flood_last_error(None)
     o = F.default_opts()
     o.kernel = 6                  # no such kernel family
     st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)

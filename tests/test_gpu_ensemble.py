@@ -51,14 +51,15 @@ def test_ensemble_equals_members_alone(warps, rows, spg, graph):
 
 
 @pytest.mark.parametrize("K,rows,spg,graph", [(4, 16, 4, True), (2, 7, 8, True), (4, 64, 4, False),
-                                              (1, 33, 4, True), (2, 300, 4, False)])
+                                              (1, 33, 4, True), (2, 300, 4, False), (8, 16, 8, True),
+                                              (8, 40, 16, False)])
 def test_tiled_ensemble_equals_members_alone(K, rows, spg, graph):
     """K steps per launch over every scenario's (chunk, strip) items give the
     bits of each scenario stepped alone by the single-step kernel."""
     Fm = F()
     probs = scenarios()
     for p in probs:
-        p.opts.epoch_steps = 4
+        p.opts.epoch_steps = max(4, K)
     ens = Fm.Ensemble(probs)
     ens.set_launch(2, rows, spg, use_graph=graph)
     ens.set_kernel(Fm.KERNEL_TILED, K)

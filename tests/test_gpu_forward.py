@@ -249,14 +249,14 @@ def test_empty_section_and_zero_inflow():
 
 
 # ---------------------------------------------------------------- temporal blocking
-@pytest.mark.parametrize("K", [1, 2, 3, 4])
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 8])
 @pytest.mark.parametrize("shape,seed", [((130, 70), 2), ((257, 129), 6), ((241, 50), 14), ((120, 33), 15),
                                         ((7, 5), 1), ((1, 40), 3), ((40, 1), 4), ((361, 97), 16)])
 def test_tiled_equals_single_steps_bitwise(K, shape, seed):
     """K time levels per launch give the same bits and ledger as K single steps."""
     Fm = F()
     p = as_f32_problem(inputs.random_small(shape[0], shape[1], seed))
-    p.opts.epoch_steps = 4 if K in (1, 2, 4) else 3
+    p.opts.epoch_steps = {1: 4, 2: 4, 3: 3, 4: 4, 8: 8}[K]
     a = Fm.Sim(p, kernel=Fm.KERNEL_STREAM)
     b = Fm.Sim(p, kernel=Fm.KERNEL_TILED, steps_per_launch=K)
     for n in (5, 12, 1, 30):              # stops inside and at the ends of epochs
@@ -273,7 +273,7 @@ def test_tiled_equals_single_steps_bitwise(K, shape, seed):
         assert Lb[k] == pytest.approx(La[k], rel=1e-6, abs=1e-9), k
 
 
-@pytest.mark.parametrize("K", [2, 4])
+@pytest.mark.parametrize("K", [2, 4, 8])
 @pytest.mark.parametrize("shape,seed,tile", [((361, 97), 16, (3, 16)), ((257, 129), 6, (5, 7)),
                                              ((130, 70), 2, (1, 9)), ((40, 33), 4, (2, 1))])
 def test_tiled_many_items_per_pipeline_bitwise(K, shape, seed, tile):
@@ -281,7 +281,7 @@ def test_tiled_many_items_per_pipeline_bitwise(K, shape, seed, tile):
     carries its slots and phases from item to item."""
     Fm = F()
     p = as_f32_problem(inputs.random_small(shape[0], shape[1], seed))
-    p.opts.epoch_steps = 4
+    p.opts.epoch_steps = max(4, K)
     a = Fm.Sim(p, kernel=Fm.KERNEL_STREAM)
     b = Fm.Sim(p, kernel=Fm.KERNEL_TILED, steps_per_launch=K, tile=tile)
     for n in (5, 12, 1, 30):
