@@ -175,8 +175,11 @@ flood_status flood_read(flood_handle *h, int32_t field, void *dst, size_t bytes,
 /*
  * Install a state (initial condition or resume from a checkpoint): depth
  * (ny*nx), qx (ny*(nx+1)) and qy ((ny+1)*nx), host or device (src_on_device).
- * qx or qy may be NULL for zero fluxes.  Clears an error state.  The time,
- * step count and volumes are not changed (see flood_set_clock).
+ * qx or qy may be NULL for zero fluxes.  Host input holding NaN or Inf is
+ * rejected (FLOOD_ERR_ARG) and the state stays as it was (the check runs on
+ * the GPU on a staged copy); device input is taken as it is (a non-finite
+ * depth is then reported at the next epoch start).  Clears an error state.
+ * The time, step count and volumes are not changed (see flood_set_clock).
  */
 flood_status flood_write_state(flood_handle *h, const void *depth, const void *qx, const void *qy,
                                int32_t src_on_device);

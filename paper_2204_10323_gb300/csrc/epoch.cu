@@ -273,6 +273,27 @@ cudaError_t launch_volume(const Geom &g, const T *h, double *partials, int n_par
     return cudaGetLastError();
 }
 
+// Non-finite values among rows x cols elements of a pitched array: OR of the
+// test into *flag (rows grid-strided over blocks, columns over threads).
+template <typename T>
+__global__ void nonfinite_kernel(const T *a, int rows, int cols, int pitch, int *flag)
+{
+    int bad = 0;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const T *row = a + (size_t)r * pitch;
+        for (int c = threadIdx.x; c < cols; c += blockDim.x) bad |= !isfinite(row[c]);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+template <typename T>
+cudaError_t launch_nonfinite(const T *a, int rows, int cols, int pitch, int *flag, cudaStream_t st)
+{
+    const int blocks = rows < 152 * 8 ? rows : 152 * 8;
+    nonfinite_kernel<T><<<blocks, 256, 0, st>>>(a, rows, cols, pitch, flag);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_gauges(const Geom &g, const T *h, const int64_t *cells, int G, double *out,
                           cudaStream_t st)
@@ -289,7 +310,8 @@ cudaError_t launch_gauges(const Geom &g, const T *h, const int64_t *cells, int G
                                           cudaStream_t);                                                    \
     template cudaError_t launch_hmax<T>(const Geom &, const T *, Ctrl *, cudaStream_t);                     \
     template cudaError_t launch_volume<T>(const Geom &, const T *, double *, int, double *, cudaStream_t);   \
-    template cudaError_t launch_gauges<T>(const Geom &, const T *, const int64_t *, int, double *, cudaStream_t);
+    template cudaError_t launch_gauges<T>(const Geom &, const T *, const int64_t *, int, double *, cudaStream_t); \
+    template cudaError_t launch_nonfinite<T>(const T *, int, int, int, int *, cudaStream_t);
 FLOOD_INST(float)
 FLOOD_INST(double)
 #undef FLOOD_INST

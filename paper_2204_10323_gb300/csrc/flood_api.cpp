@@ -517,6 +517,7 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
     h->n_partials = 1024;
     ALLOC(h->vol_partials, double *, h->n_partials * sizeof(double));
     ALLOC(h->vol_out, double *, sizeof(double));
+    ALLOC(h->flag, int *, sizeof(int));
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes == 0 ? cudaSuccess : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream);
     };
@@ -624,16 +625,41 @@ extern "C" flood_status flood_write_state(flood_handle *h, const void *depth, co
 {
     if (!h || !depth) return fail(h, FLOOD_ERR_ARG, "NULL argument");
     CK(cudaStreamSynchronize(h->stream));
-    if (!src_on_device && !check_finite_host(depth, (size_t)h->geo.nx * h->geo.ny, h->prec))
-        return fail(h, FLOOD_ERR_ARG, "depth has NaN/Inf");
-    flood_status st = copy_in(h, h->h[h->cur], depth, h->geo.ny, h->geo.nx, src_on_device);
+    // host input: stage the new state in the idle half of the ping-pong buffers
+    // (the next step's output, free now), check it on the device, and only then
+    // copy it over the current state, so a rejected state leaves the handle as
+    // it was.  Device input is taken as it is.
+    const bool staged = !src_on_device;
+    const int cur = h->cur, dst = staged ? 1 - h->cur : h->cur;
+    const int nx = h->geo.nx, ny = h->geo.ny, P = h->geo.pitch;
+    flood_status st = copy_in(h, h->h[dst], depth, ny, nx, src_on_device);
     if (st) return st;
-    if (qx) st = copy_in(h, h->qx[h->cur], qx, h->geo.ny, h->geo.nx + 1, src_on_device);
-    else CK(cudaMemsetAsync(h->qx[h->cur], 0, plane_elems(h, FLOOD_FIELD_QX) * h->esz, h->stream));
+    if (qx) st = copy_in(h, h->qx[dst], qx, ny, nx + 1, src_on_device);
     if (st) return st;
-    if (qy) st = copy_in(h, h->qy[h->cur], qy, h->geo.ny + 1, h->geo.nx, src_on_device);
-    else CK(cudaMemsetAsync(h->qy[h->cur], 0, plane_elems(h, FLOOD_FIELD_QY) * h->esz, h->stream));
+    if (qy) st = copy_in(h, h->qy[dst], qy, ny + 1, nx, src_on_device);
     if (st) return st;
+    if (staged) {
+        CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+        if (h->prec == FLOOD_F32) {
+            CK(launch_nonfinite<float>((const float *)h->h[dst], ny, nx, P, h->flag, h->stream));
+            if (qx) CK(launch_nonfinite<float>((const float *)h->qx[dst], ny, nx + 1, P, h->flag, h->stream));
+            if (qy) CK(launch_nonfinite<float>((const float *)h->qy[dst], ny + 1, nx, P, h->flag, h->stream));
+        } else {
+            CK(launch_nonfinite<double>((const double *)h->h[dst], ny, nx, P, h->flag, h->stream));
+            if (qx) CK(launch_nonfinite<double>((const double *)h->qx[dst], ny, nx + 1, P, h->flag, h->stream));
+            if (qy) CK(launch_nonfinite<double>((const double *)h->qy[dst], ny + 1, nx, P, h->flag, h->stream));
+        }
+        int bad = 0;
+        CK(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (bad) return fail(h, FLOOD_ERR_ARG, "depth or discharge has NaN/Inf");
+        const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+        CK(cudaMemcpyAsync(h->h[cur], h->h[dst], plane_elems(h, FLOOD_FIELD_H) * h->esz, d2d, h->stream));
+        if (qx) CK(cudaMemcpyAsync(h->qx[cur], h->qx[dst], plane_elems(h, FLOOD_FIELD_QX) * h->esz, d2d, h->stream));
+        if (qy) CK(cudaMemcpyAsync(h->qy[cur], h->qy[dst], plane_elems(h, FLOOD_FIELD_QY) * h->esz, d2d, h->stream));
+    }
+    if (!qx) CK(cudaMemsetAsync(h->qx[cur], 0, plane_elems(h, FLOOD_FIELD_QX) * h->esz, h->stream));
+    if (!qy) CK(cudaMemsetAsync(h->qy[cur], 0, plane_elems(h, FLOOD_FIELD_QY) * h->esz, h->stream));
     // clear the device status word (keep the rest of the control block)
     CK(cudaMemsetAsync(&h->ctrl->status, 0, sizeof(int), h->stream));
     st = refresh_hmax(h);

@@ -133,6 +133,9 @@ cudaError_t launch_epoch_batched(const EpochArgs<T> *tab, int n, const int2 *tas
 // h_max of a state into ctrl->hmax_bits (max with what is there).
 template <typename T>
 cudaError_t launch_hmax(const Geom &g, const T *h, Ctrl *ctrl, cudaStream_t st);
+// OR of "some element is NaN or Inf" over rows x cols of a pitched array into *flag (device).
+template <typename T>
+cudaError_t launch_nonfinite(const T *a, int rows, int cols, int pitch, int *flag, cudaStream_t st);
 // Deterministic two-pass sum of h * dx^2 into *out (double, device).
 template <typename T>
 cudaError_t launch_volume(const Geom &g, const T *h, double *partials, int n_partials, double *out,

@@ -45,6 +45,7 @@ struct flood_handle {
 
     // reductions and gauges
     double *vol_partials = nullptr, *vol_out = nullptr;
+    int *flag = nullptr;                  // device word for the non-finite check of flood_write_state
     int n_partials = 1024;
     int64_t *gauge_dev = nullptr;
     int gauge_cap = 0;
