@@ -307,7 +307,7 @@ def run_gpu(args):
     if not args.no_ensemble:
         shape = [int(v) for v in args.ensemble_shape.split(",")] if args.ensemble_shape else None
         line["ensemble"] = ensemble_throughput(F, torch, value, shape=shape)
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, seconds_target=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line))
