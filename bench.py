@@ -182,6 +182,22 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(ms: float, dist) -> float:
+    """The slowest rank's time (all ranks get it); ms itself without a process group."""
+    if not dist:
+        return ms
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, cells: int, steps: int, ms: float) -> float:
+    """Whole-job Gcell-updates/s of `world` replicas of `cells` cells over `steps` steps in ms."""
+    return world * cells * steps / (ms * 1e-3) / 1e9
+
+
 def timed_run(F, torch, prob, kernel_name, k, tile, graph, steps_req, warmup, local, dist):
     """Warm up and time whole epochs of one kernel on `prob`: CUDA events around
     every launch on the library's stream, nvidia-smi clocks sampled meanwhile."""
@@ -217,11 +233,7 @@ def timed_run(F, torch, prob, kernel_name, k, tile, graph, steps_req, warmup, lo
     torch.cuda.synchronize()
     clk = clocks.stop()
     per = [ev[j].elapsed_time(ev[j + 1]) for j in range(n_launch_total)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), dist)
     sim.sync()
     # launches that did not start an epoch run the step kernel alone
     starts = [(step0 + j * per_launch) % E == 0 for j in range(n_launch_total)]
@@ -258,7 +270,7 @@ def run_gpu(args):
     clk, launches, L = run["clocks"], run["launches"], run["ledger"]
     args.steps = steps
 
-    value = world * ncell * steps / (total_ms * 1e-3) / 1e9
+    value = job_throughput(world, ncell, steps, total_ms)
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_CELL * ncell * per_launch / (kern_ms * 1e-3) / 1e9
     traffic = None

@@ -32,8 +32,8 @@ constexpr int BX = 32, BY = 8;
 template <typename T> struct Fwd;
 
 template <> struct Fwd<double> {
-    double g, dt, dx, hd, dtdx_unused;
-    __device__ Fwd(const Geom &G, double dt_) : g(G.g), dt(dt_), dx(G.dx), hd(G.h_dry), dtdx_unused(0) {}
+    double g, dt, dx, hd;
+    __device__ Fwd(const Geom &G, double dt_) : g(G.g), dt(dt_), dx(G.dx), hd(G.h_dry) {}
     __device__ double face(double q, double hL, double zL, double nL, double hR, double zR, double nR) const
     {
         return face_update_ieee<double>(q, hL, zL, nL, hR, zR, nR, g, dt, dx, hd);

@@ -220,8 +220,8 @@ __global__ void gauges_kernel(Geom G, const T *h, const int64_t *cells, int ng, 
 
 }  // namespace
 
-cudaError_t launch_epoch_begin(const Geom &g, Ctrl *ctrl, double *t_list, int E, int /*unused*/,
-                               const double *fixed_dt, cudaStream_t st)
+cudaError_t launch_epoch_begin(const Geom &g, Ctrl *ctrl, double *t_list, int E, const double *fixed_dt,
+                               cudaStream_t st)
 {
     epoch_begin_kernel<<<1, 32, 0, st>>>(g, ctrl, t_list, E, fixed_dt);
     return cudaGetLastError();

@@ -110,19 +110,4 @@ __device__ __forceinline__ float boundary_fast_flux(const StepArgs<float> &a, in
     return -inward * q;
 }
 
-// Boundary face value on `side` at index k along it, for the adjacent cell (h, n).
-__device__ __forceinline__ float boundary_fast(const StepArgs<float> &a, int side, int k, float h, float n,
-                                               double &vout)
-{
-    const Geom &G = a.geo;
-    int off = side == 0 ? 0 : side == 1 ? G.ny : side == 2 ? 2 * G.ny : 2 * G.ny + G.nx;
-    int type = a.bc.type[off + k];
-    if (type == kBcWall) return 0.0f;
-    float inward = (side == 0 || side == 2) ? 1.0f : -1.0f;
-    if (type == kBcInflow) return inward * a.inflow_q[(size_t)a.s * a.n_slots + a.bc.slot[off + k]];
-    float q = outflow_fast(h, a.bc.sqrtS_f[off + k], n, G.dx_f, G.h_dry_f, G.bc_form);
-    vout += (double)q * G.dx;
-    return -inward * q;
-}
-
 }  // namespace flood

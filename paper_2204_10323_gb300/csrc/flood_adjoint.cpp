@@ -149,7 +149,7 @@ flood_status ensure_epoch(Sweep &S, int64_t e)
         // first visit: the working state is the epoch's first state; choose dt by the rule
         flood_status st = refresh_hmax(h);
         if (st) return st;
-        CKA(launch_epoch_begin(h->geo, h->ctrl, h->t_list, E, 0, nullptr, h->stream));
+        CKA(launch_epoch_begin(h->geo, h->ctrl, h->t_list, E, nullptr, h->stream));
         CKA(cudaMemcpyAsync(dtl, &h->ctrl->dt, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         CKA(cudaMemcpyAsync(tll, h->t_list, (E + 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         S.logged[ie] = 1;

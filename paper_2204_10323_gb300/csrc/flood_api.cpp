@@ -261,7 +261,7 @@ flood_status advance(flood_handle *h, int64_t n, const int64_t *gcells, int ng, 
         int s = (int)(h->step % E);
         if (s == 0) {
             const double *fdt = fixed_dt_log ? fixed_dt_log + done : nullptr;
-            CK(launch_epoch_begin(h->geo, h->ctrl, h->t_list, E, 0, fdt, h->stream));
+            CK(launch_epoch_begin(h->geo, h->ctrl, h->t_list, E, fdt, h->stream));
             flood_status st = launch_inflow_epoch(h);
             if (st) return st;
         }

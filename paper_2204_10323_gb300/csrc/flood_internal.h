@@ -76,7 +76,7 @@ struct StepArgs {
     const int64_t *gauge_cells;   // flat j*nx+i; h after each step -> gauge_out
     int n_gauges;
     double *gauge_out;            // (k_steps) x n_gauges rows for this launch, or null
-    int tile_x, tile_y;           // tiled kernel only
+    int tile_x, tile_y;           // launch shape (stream/TMA: warps, rows; tiled: strips, rows per item)
 };
 
 // ---------------------------------------------------------------- launchers
@@ -100,10 +100,11 @@ cudaError_t launch_step_tiled_ensemble(const StepArgs<float> *table, const int *
 void stream_launch_shape(const Geom &g, int tile_x, int tile_y, int *warps, int *rows);
 cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st);
 
-// Epoch start: choose dt from h_max (or constant), fill t_list, reset the
-// running maximum, count CFL exceedances, flag NaN/Inf.
-cudaError_t launch_epoch_begin(const Geom &g, Ctrl *ctrl, double *t_list, int E, int fixed_dt_mode,
-                               const double *fixed_dt, cudaStream_t st);
+// Epoch start: choose dt from h_max (or constant, or fixed_dt[0] when given:
+// the adjoint's replay of a logged epoch), fill t_list, reset the running
+// maximum, count CFL exceedances, flag NaN/Inf.
+cudaError_t launch_epoch_begin(const Geom &g, Ctrl *ctrl, double *t_list, int E, const double *fixed_dt,
+                               cudaStream_t st);
 // Eq. 6 for every (step of the epoch, inflow section) pair.
 template <typename T>
 cudaError_t launch_inflow(const Geom &g, const InflowSec *secs, int nsec, const int64_t *sec_cells,

@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(kWarps * 32) step_rows_kernel(const StepArgs<f
                     int c = c0 + k;
                     float v = 0.0f;
                     if (c < nx)
-                        v = j == 0 ? boundary_fast(a, 2, c, get(cur.h, k), get(cur.n, k), vout)
-                                   : boundary_fast(a, 3, c, get(hp, k), get(np_, k), vout);
+                        v = j == 0 ? boundary_fast_at(a, a.s, 2, c, get(cur.h, k), get(cur.n, k), vout)
+                                   : boundary_fast_at(a, a.s, 3, c, get(hp, k), get(np_, k), vout);
                     set(qys, k, v);
                 }
             }
@@ -220,8 +220,8 @@ __global__ void __launch_bounds__(kWarps * 32) step_rows_kernel(const StepArgs<f
                     const int c = c0 + k;
                     const float hl = k == 0 ? hW : get(cur.h, k - 1);
                     const float nl = k == 0 ? nW : get(cur.n, k - 1);
-                    if (c == 0) set(qxw, k, boundary_fast(a, 0, j, get(cur.h, 0), get(cur.n, 0), vout));
-                    else if (c == nx) set(qxw, k, boundary_fast(a, 1, j, hl, nl, vout));
+                    if (c == 0) set(qxw, k, boundary_fast_at(a, a.s, 0, j, get(cur.h, 0), get(cur.n, 0), vout));
+                    else if (c == nx) set(qxw, k, boundary_fast_at(a, a.s, 1, j, hl, nl, vout));
                     else if (c > nx) set(qxw, k, 0.0f);
                 }
             }
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kWarps * 32) step_rows_kernel(const StepArgs<f
             if (lane == 31) {
                 const int c = x0 + 128;
                 qe = 0.0f;
-                if (c == nx) qe = boundary_fast(a, 1, j, cur.h.w, cur.n.w, vout);
+                if (c == nx) qe = boundary_fast_at(a, a.s, 1, j, cur.h.w, cur.n.w, vout);
                 else if (c < nx) {
                     size_t r = (size_t)j * P + c;
                     float hr = __ldg(H + r), zr = __ldg(Z + r), nr = __ldg(N + r);
