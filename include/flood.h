@@ -184,6 +184,17 @@ flood_status flood_read(flood_handle *h, int32_t field, void *dst, size_t bytes,
 flood_status flood_write_state(flood_handle *h, const void *depth, const void *qx, const void *qy,
                                int32_t src_on_device);
 
+/*
+ * Advance to the simulated time t_end (seconds, >= the current time): whole
+ * steps while they end at or before t_end, then one step shortened to end
+ * exactly at t_end (the run loop's final-step truncation, Results "Running
+ * the Simulation"); the current CFL epoch keeps its time step for the steps
+ * after it.  *steps_taken (may be NULL) gets the number of steps.
+ * FLOOD_ERR_ARG if t_end is not finite or lies before the current time.
+ * Synchronous on the handle's stream.
+ */
+flood_status flood_advance(flood_handle *h, double t_end, int64_t *steps_taken);
+
 /* Set time, step count and cumulative volumes (a checkpoint's ledger).  The
  * next step starts a new CFL epoch when step % E == 0. */
 flood_status flood_set_clock(flood_handle *h, double t, int64_t step, double dt, double v_in,

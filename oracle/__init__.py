@@ -70,6 +70,9 @@ def lib():
         L.orc_run.argtypes = [C.POINTER(Params), C.POINTER(SectionC), C.c_int32, dp, dp, dp, dp, dp,
                               C.c_int64, C.POINTER(Ledger), C.POINTER(C.c_int64), C.c_int32, dp, dp]
         L.orc_run.restype = C.c_int
+        L.orc_advance.argtypes = [C.POINTER(Params), C.POINTER(SectionC), C.c_int32, dp, dp, dp, dp, dp,
+                                  C.c_double, C.POINTER(Ledger), C.POINTER(C.c_int64)]
+        L.orc_advance.restype = C.c_int
         L.orc_dt.argtypes = [C.POINTER(Params), dp]
         L.orc_dt.restype = C.c_double
         L.orc_volume.argtypes = [C.POINTER(Params), dp]
@@ -145,6 +148,19 @@ class Oracle:
         if rc != 0:
             raise MemoryError("oracle work arrays")
         return out, dts
+
+    def advance(self, t_end: float) -> int:
+        """Advance to time t_end, the last step shortened to land on it (the run
+        loop's final-step truncation); returns the number of steps."""
+        k = C.c_int64(0)
+        rc = lib().orc_advance(C.byref(self.params), self.secs, self.nsec, _dp(self.z), _dp(self.n),
+                               _dp(self.h), _dp(self.qx), _dp(self.qy), float(t_end), C.byref(self.ledger),
+                               C.byref(k))
+        if rc == -2:
+            raise ValueError("t_end is before the current time")
+        if rc != 0:
+            raise MemoryError("oracle work arrays")
+        return int(k.value)
 
     def step_dt(self, dt: float) -> None:
         """One step with a given dt at the current time (does not touch the epoch counter)."""

@@ -360,6 +360,36 @@ int orc_run(const orc_params *p, const orc_section *secs, int32_t nsec, const do
     return 0;
 }
 
+/*
+ * Advance to the time t_end >= led->t: steps as in orc_run, except that the
+ * step that would pass t_end is shortened to end exactly at t_end (the
+ * run loop's final-step truncation); the epoch keeps its time step for any
+ * steps after it.  *steps_taken gets the number of steps.  Returns 0, -1 if
+ * the work arrays cannot be allocated, -2 if t_end < led->t.
+ */
+int orc_advance(const orc_params *p, const orc_section *secs, int32_t nsec, const double *z,
+                const double *n, double *h, double *qx, double *qy, double t_end, orc_ledger *led,
+                int64_t *steps_taken)
+{
+    if (!(t_end >= led->t)) return -2;
+    int32_t E = p->epoch_steps > 0 ? p->epoch_steps : 1;
+    orc_scratch w;
+    if (scratch_alloc(p, &w)) { scratch_free(&w); return -1; }
+    int64_t k = 0;
+    while (led->t < t_end) {
+        if (led->step % E == 0) led->dt = orc_dt(p, h);
+        const int last = led->t + led->dt > t_end;     /* this step would pass t_end */
+        const double dt = last ? t_end - led->t : led->dt;
+        step_with(p, secs, nsec, z, n, h, qx, qy, dt, led->t, led, &w);
+        led->t = last ? t_end : led->t + led->dt;
+        led->step += 1;
+        k += 1;
+    }
+    scratch_free(&w);
+    *steps_taken = k;
+    return 0;
+}
+
 /* Stored volume sum(h) dx^2 with compensated (Kahan) summation. */
 double orc_volume(const orc_params *p, const double *h)
 {

@@ -74,6 +74,7 @@ def _load():
     L.flood_create.argtypes = [C.POINTER(flood_grid), vp, vp, C.POINTER(flood_bc_section), i32,
                                C.POINTER(flood_opts), C.POINTER(H)]
     L.flood_step.argtypes = [H, i64]
+    L.flood_advance.argtypes = [vp, C.c_double, C.POINTER(i64)]
     L.flood_sync.argtypes = [H]
     L.flood_read.argtypes = [H, i32, vp, C.c_size_t, i32]
     L.flood_write_state.argtypes = [H, vp, vp, vp, i32]
@@ -107,7 +108,7 @@ def _load():
     for name in ("flood_ensemble_create", "flood_ensemble_set_launch", "flood_ensemble_set_kernel",
                  "flood_ensemble_step", "flood_ensemble_destroy"):
         getattr(L, name).restype = C.c_int
-    for name in ("flood_create", "flood_step", "flood_sync", "flood_read", "flood_write_state",
+    for name in ("flood_create", "flood_step", "flood_advance", "flood_sync", "flood_read", "flood_write_state",
                  "flood_set_clock", "flood_set_manning", "flood_run_gauges", "flood_adjoint", "flood_destroy"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -142,6 +143,12 @@ def flood_create(grid: flood_grid, dem, manning, sections, n_sections: int, opts
 
 def flood_step(h, n_steps: int):
     _check(lib().flood_step(h, int(n_steps)), h)
+
+
+def flood_advance(h, t_end: float) -> int:
+    k = C.c_int64(0)
+    _check(lib().flood_advance(h, float(t_end), C.byref(k)), h)
+    return int(k.value)
 
 
 def flood_sync(h):
@@ -281,6 +288,11 @@ class Sim:
         flood_step(self.h, n_steps)
         if check:
             self.sync()
+
+    def advance(self, t_end: float) -> int:
+        """Advance to simulated time t_end, the last step shortened to land on it;
+        returns the number of steps."""
+        return flood_advance(self.h, t_end)
 
     def sync(self):
         st = flood_sync(self.h)

@@ -252,14 +252,16 @@ flood_status launch_steps(flood_handle *h, int s, int k, int want_hmax, const in
 }
 
 // Advance n steps; if gcells, record gauges after each step into gbuf (device, n x ng).
+// epoch_open: the current epoch was begun already (its dt, times and inflow rows
+// are in place), so a first step at an epoch start does not begin it again.
 flood_status advance(flood_handle *h, int64_t n, const int64_t *gcells, int ng, double *gbuf,
-                     const double *fixed_dt_log)
+                     const double *fixed_dt_log, bool epoch_open)
 {
     const int E = h->geo.epoch_steps;
     int64_t done = 0;
     while (done < n) {
         int s = (int)(h->step % E);
-        if (s == 0) {
+        if (s == 0 && !(epoch_open && done == 0)) {
             const double *fdt = fixed_dt_log ? fixed_dt_log + done : nullptr;
             CK(launch_epoch_begin(h->geo, h->ctrl, h->t_list, E, fdt, h->stream));
             flood_status st = launch_inflow_epoch(h);
@@ -570,6 +572,69 @@ extern "C" flood_status flood_step(flood_handle *h, int64_t n_steps)
     if (h->sticky) return fail(h, FLOOD_ERR_STATE, "handle is in an error state; write a new state first");
     if (h->opts.use_graph) return advance_graph(h, n_steps);
     return advance(h, n_steps, nullptr, 0, nullptr, nullptr);
+}
+
+// Advance to the time t_end: whole steps while they end at or before t_end,
+// then one step shortened to end exactly at t_end; the epoch keeps its time
+// step for the steps after it (their start times are rebuilt from t_end and
+// the epoch's inflow rows recomputed).
+extern "C" flood_status flood_advance(flood_handle *h, double t_end, int64_t *steps_taken)
+{
+    if (!h) return fail(nullptr, FLOOD_ERR_ARG, "handle is NULL");
+    if (h->sticky) return fail(h, FLOOD_ERR_STATE, "handle is in an error state; write a new state first");
+    if (!std::isfinite(t_end)) return fail(h, FLOOD_ERR_ARG, "t_end must be finite");
+    const int E = h->geo.epoch_steps;
+    std::vector<double> tl(E + 1);
+    int64_t taken = 0;
+    Ctrl c;
+    CK(cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (!(t_end >= c.t)) return fail(h, FLOOD_ERR_ARG, "t_end is before the current time");
+    while (c.t < t_end) {
+        const int s = (int)(h->step % E);
+        const bool begun = s == 0;
+        if (begun) {                                   // begin the epoch here: its dt decides the steps
+            CK(launch_epoch_begin(h->geo, h->ctrl, h->t_list, E, nullptr, h->stream));
+            flood_status st = launch_inflow_epoch(h);
+            if (st) return st;
+        }
+        CK(cudaMemcpyAsync(tl.data(), h->t_list, (E + 1) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        int m = s;                                     // steps s .. m-1 end at or before t_end
+        while (m < E && tl[m + 1] <= t_end) m++;
+        if (m > s) {
+            flood_status st = advance(h, m - s, nullptr, 0, nullptr, nullptr, begun);
+            if (st) return st;
+            taken += m - s;
+        }
+        if (tl[m] == t_end) break;
+        if (m == E) {                                  // the epoch ended before t_end
+            c.t = tl[E];
+            continue;
+        }
+        // step m from tl[m] to t_end exactly
+        const double dt = c.dt, dt_last = t_end - tl[m];
+        CK(cudaMemcpyAsync(&h->ctrl->dt, &dt_last, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->t_list + m + 1, &t_end, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        flood_status st = advance(h, 1, nullptr, 0, nullptr, nullptr, begun && m == s);
+        if (st) return st;
+        taken += 1;
+        // the rest of the epoch continues from t_end with the epoch's dt
+        tl[m + 1] = t_end;
+        for (int k = m + 1; k < E; k++) tl[k + 1] = tl[k] + dt;
+        CK(cudaMemcpyAsync(&h->ctrl->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->t_list, tl.data(), (E + 1) * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        if (m + 1 < E) {
+            st = launch_inflow_epoch(h);
+            if (st) return st;
+        }
+        CK(cudaStreamSynchronize(h->stream));          // host values above are in flight until here
+        break;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    if (steps_taken) *steps_taken = taken;
+    return FLOOD_OK;
 }
 
 extern "C" flood_status flood_sync(flood_handle *h)

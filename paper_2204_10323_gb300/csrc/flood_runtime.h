@@ -84,7 +84,7 @@ flood_status launch_inflow_epoch(flood_handle *h);
 flood_status launch_steps(flood_handle *h, int s, int k, int want_hmax, const int64_t *gcells, int ng,
                           double *gout);
 flood_status advance(flood_handle *h, int64_t n, const int64_t *gcells, int ng, double *gbuf,
-                     const double *fixed_dt_log);
+                     const double *fixed_dt_log, bool epoch_open = false);
 flood_status check_device_status(flood_handle *h);
 StepArgs<float> step_args_f32(flood_handle *h, int s);
 flood_status ensure_gauge_buffers(flood_handle *h, int ng, size_t n_values);

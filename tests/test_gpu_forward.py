@@ -248,6 +248,63 @@ def test_empty_section_and_zero_inflow():
     assert s.ledger()["V_in"] == 0.0
 
 
+# ---------------------------------------------------------------- final-step truncation
+def _advance_pair(p, precision, targets, kernel=0, k=0):
+    """Oracle and GPU through the same sequence of advances and whole steps."""
+    Fm = F()
+    q = as_f32_problem(p) if precision == Fm.F32 else p
+    o = oracle.Oracle(q)
+    s = Fm.Sim(q, precision=precision, kernel=kernel, steps_per_launch=k)
+    for T in targets:
+        if isinstance(T, int):               # whole steps
+            o.run(T)
+            s.step(T)
+        else:
+            na, nb = s.advance(T), o.advance(T)
+            # FP32 picks its CFL dt from an FP32 depth maximum: a target within
+            # rounding of a step end may split differently, so only FP64 counts
+            if precision == Fm.F64:
+                assert na == nb
+            assert s.ledger()["t"] == T == o.ledger.t
+    return o, s
+
+
+def test_advance_fp64_matches_oracle():
+    p = inputs.random_small(70, 45, 21)
+    o, s = _advance_pair(p, F().F64, [0.37, 3, 1.234, 1.2341, 5, 9.9, 9.9])
+    h, qx, qy = s.state()
+    assert np.abs(h - o.h).max() < TOL64
+    assert np.abs(qx - o.qx).max() < TOL64
+    check_ledger(o, s.ledger(), 1e-12)
+    assert s.ledger()["dt"] == o.ledger.dt
+
+
+@pytest.mark.parametrize("kernel,k", [(4, 0), (5, 0), (3, 4)])
+def test_advance_fp32_matches_oracle(kernel, k):
+    p = inputs.random_small(130, 70, 22)
+    o, s = _advance_pair(p, F().F32, [0.91, 7, 2.5, 2.500001, 13, 6.75], kernel=kernel, k=k)
+    assert np.abs(s.read(F().FIELD_H).astype(np.float64) - o.h).max() < TOL32_H
+    assert s.ledger()["V_in"] == pytest.approx(o.ledger.V_in, rel=1e-6)
+
+
+def test_advance_books_the_truncated_inflow_exactly():
+    """Constant Q into a closed basin: after advancing to T, V_in = Q T and the
+    stored volume grew by V_in + V_clip (FP64 path)."""
+    Fm = F()
+    sec = Section.cells(XMIN, 1, 3, INFLOW, 1e-3, 6, 4, [0.0, 100.0], [2.0, 2.0])
+    p = Problem("basin", 6, 4, 1.0, np.zeros((4, 6)), np.full((4, 6), 0.03), [sec],
+                Options(dt_mode=1, dt_const=0.1), h0=np.full((4, 6), 0.5))
+    s = Fm.Sim(p, precision=Fm.F64)
+    V0 = s.ledger()["volume"]
+    assert s.advance(0.55) == 6
+    L = s.ledger()
+    assert L["t"] == 0.55 and L["dt"] == 0.1
+    assert L["V_in"] == pytest.approx(2.0 * 0.55, rel=1e-14)
+    assert L["volume"] - V0 == pytest.approx(L["V_in"] + L["V_clip"], rel=1e-12)
+    with pytest.raises(Fm.FloodError):
+        s.advance(0.5)
+
+
 # ---------------------------------------------------------------- temporal blocking
 @pytest.mark.parametrize("K", [1, 2, 3, 4, 8])
 @pytest.mark.parametrize("shape,seed", [((130, 70), 2), ((257, 129), 6), ((241, 50), 14), ((120, 33), 15),

@@ -274,6 +274,53 @@ def test_cfl_rule_and_epochs():
     assert dry.dt() == 1.5
 
 
+# ---------------------------------------------------------------- final-step truncation
+def _basin_with_inflow(t_s, q, **opt):
+    """Closed flat 6 x 4 basin, 0.5 m of water, one inflow section on xmin (rows 1-2)."""
+    sec = Section.cells(XMIN, 1, 3, INFLOW, 1e-3, 6, 4, t_s, q)
+    return closed_box(np.zeros((4, 6)), np.full((4, 6), 0.5), sections=[sec], **opt)
+
+
+def test_advance_lands_on_the_end_time_with_exact_inflow_volume():
+    """Constant Q = 2 m^3/s, dt = 0.1 s: advancing 0.55 s takes ceil(5.5) = 6 steps,
+    the last one 0.05 s long; the clock reads 0.55 exactly, V_in = Q x 0.55 and the
+    stored volume grows by exactly V_in (closed basin, nothing leaves)."""
+    o = oracle.Oracle(_basin_with_inflow([0.0, 100.0], [2.0, 2.0], dt_const=0.1))
+    V0 = o.volume()
+    assert o.advance(0.55) == 6
+    assert o.ledger.t == 0.55
+    assert o.ledger.V_in == pytest.approx(2.0 * 0.55, rel=1e-14)
+    assert o.volume() - V0 == pytest.approx(o.ledger.V_in, rel=1e-12)
+    assert o.ledger.V_out == 0.0 and o.ledger.V_clip == 0.0
+    assert o.ledger.dt == 0.1                        # the epoch keeps its time step
+    assert o.advance(0.55) == 0                      # already there
+    with pytest.raises(ValueError):
+        o.advance(0.5)
+
+
+def test_advance_truncated_step_uses_its_start_time_and_length():
+    """Q(t) = 10 t, dt = 1 s, advance to 2.5 s: steps start at 0, 1, 2 with lengths
+    1, 1, 0.5, so V_in = Q(0)*1 + Q(1)*1 + Q(2)*0.5 = 20 m^3 (a full last step would
+    give 30, a last step sampled at its end 22.5)."""
+    o = oracle.Oracle(_basin_with_inflow([0.0, 100.0], [0.0, 1000.0], dt_const=1.0))
+    assert o.advance(2.5) == 3
+    assert o.ledger.V_in == pytest.approx(20.0, rel=1e-14)
+
+
+def test_advance_in_cfl_epochs_keeps_the_books():
+    """CFL epochs of 4 steps: several advances to arbitrary times land on them
+    exactly, with constant inflow into the closed basin V_in = Q (t - t0), and the
+    ledger closes (V - V0 = V_in + V_clip, nothing leaves)."""
+    o = oracle.Oracle(_basin_with_inflow([0.0, 1e4], [3.0, 3.0], dt_mode=0, dt_cap=0.7, epoch_steps=4))
+    V0 = o.volume()
+    for T in (0.3, 1.9, 2.0, 7.777):
+        o.advance(T)
+        assert o.ledger.t == T
+    assert o.ledger.V_in == pytest.approx(3.0 * 7.777, rel=1e-13)
+    assert o.ledger.V_out == 0.0
+    assert o.volume() - V0 == pytest.approx(o.ledger.V_in + o.ledger.V_clip, rel=1e-12)
+
+
 # ---------------------------------------------------------------- boundary conditions
 def test_section_fraction_rule():
     p = inputs.random_small(20, 12, 0)
