@@ -314,6 +314,8 @@ def run_gpu(args):
     del sim
     if args.kernel != "tiled" and not args.no_temporal:
         line["temporal_blocking"] = temporal_leg(F, torch, prob, args, local, dist, ncell, peak)
+    if not args.no_sweep:
+        line["resolution_sweep"] = resolution_sweep(F, torch, prob, args, local, dist, total_ms / steps)
     if not args.no_adjoint:
         line["adjoint"] = adjoint_ratio(F, torch)
     if not args.no_ensemble:
@@ -342,6 +344,30 @@ def temporal_leg(F, torch, prob, args, local, dist, ncell, peak, K: int = 4):
             "ms_per_step": run["total_ms"] / run["steps"], "kernel_ms_per_launch": run["kern_ms"],
             "equivalent_gbs": eq, "frac_of_one_step_roofline": eq / peak,
             "traffic_per_launch": tr * ncell if tr else None, "clocks": run["clocks"]}
+
+
+def resolution_sweep(F, torch, prob, args, local, dist, ms_per_step_1m: float):
+    """Steps/s of the step at 1, 2, 4 and 8 m: the workload's DEM, Manning field and
+    initial depth coarsened by block averaging on the GPU (flood_coarsen), the way
+    the paper derives its coarser grids from the 1 m DEM, each timed like the main
+    leg; the paper's steps/s per TPU v3 core (Table 1) beside them as context."""
+    from inputs import Problem
+    rows = [{"dx_m": prob.dx, "nx": prob.nx, "ny": prob.ny, "steps_per_s": 1e3 / ms_per_step_1m,
+             "gcell_s": prob.nx * prob.ny / ms_per_step_1m / 1e6}]
+    for f in (2, 4, 8):
+        z, n = F.coarsen(prob.z, f), F.coarsen(prob.n, f)
+        h0 = None if prob.h0 is None else F.coarsen(prob.h0, f)
+        sub = Problem(f"{prob.name}_coarse{f}", z.shape[1], z.shape[0], prob.dx * f, z, n, prob.sections,
+                      prob.opts, h0=h0)
+        run = timed_run(F, torch, sub, args.kernel if args.kernel != "reference" else "stream", args.k, (0, 0),
+                        args.graph, args.steps, args.warmup, local, dist)
+        run["sim"].close()
+        ms = run["total_ms"] / run["steps"]
+        rows.append({"dx_m": sub.dx, "nx": sub.nx, "ny": sub.ny, "steps_per_s": 1e3 / ms,
+                     "gcell_s": sub.nx * sub.ny / ms / 1e6})
+    return {"kernel": args.kernel, "rows": rows,
+            "paper_steps_per_s_one_tpu_v3_core": {"2 m, 248 M cells": 7.57, "4 m, 62 M cells": 30.2,
+                                                  "8 m, 15.5 M cells": 118.0}}
 
 
 def adjoint_ratio(F, torch, steps: int = 2000, checkpoints: int = 40):
@@ -449,6 +475,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-temporal", action="store_true", help="skip the temporal-blocking leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 1/2/4/8 m resolution sweep")
     ap.add_argument("--ensemble-shape", default="", help="K,warps,rows,steps_per_graph instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:

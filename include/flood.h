@@ -282,6 +282,20 @@ flood_handle *flood_ensemble_member(flood_ensemble *e, int32_t k);
 flood_status flood_ensemble_destroy(flood_ensemble *e);
 const char *flood_ensemble_last_error(const flood_ensemble *e);
 
+/*
+ * Coarsen a cell field (DEM, Manning n or depth; ny*nx, row-major, x fastest,
+ * FLOOD_F32 or FLOOD_F64) by block averaging, the way the paper derives its
+ * coarser grids from the 1 m DEM (Methods, "Data"): dst is ceil(ny/factor) x
+ * ceil(nx/factor), cell (J, I) the mean of the input cells of block
+ * [J*factor, (J+1)*factor) x [I*factor, (I+1)*factor) that lie in the grid.
+ * src and dst are both host (on_device = 0) or both device memory on the
+ * current device; stream NULL = PyTorch's current stream.  Synchronous.
+ * FLOOD_ERR_ARG for NULL pointers or sizes below 1 (message:
+ * flood_last_error(NULL)).
+ */
+flood_status flood_coarsen(int32_t precision, const void *src, int32_t nx, int32_t ny, int32_t factor, void *dst,
+                           int32_t on_device, void *stream);
+
 /* Library version string. */
 const char *flood_version(void);
 

@@ -93,6 +93,8 @@ def _load():
     L.flood_adjoint_times.argtypes = [H, C.POINTER(dbl), C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64)]
     L.flood_adjoint_times.restype = C.c_int
     L.flood_volume_noalloc.argtypes = [vp, i32, i32, i64, i32, dbl, vp, vp]
+    L.flood_coarsen.argtypes = [i32, vp, i32, i32, i32, vp, i32, vp]
+    L.flood_coarsen.restype = C.c_int
     L.flood_volume_noalloc.restype = C.c_int
     L.flood_ensemble_create.argtypes = [i32, C.POINTER(flood_grid), C.POINTER(vp), C.POINTER(vp),
                                         C.POINTER(C.POINTER(flood_bc_section)), C.POINTER(i32),
@@ -200,6 +202,27 @@ def flood_volume_noalloc(depth_ptr, nx: int, ny: int, row_pitch: int, precision:
 
 
 # ------------------------------------------------------------------ convenience wrapper
+def coarsen(field, factor: int):
+    """Block mean of a (ny, nx) float32/float64 field (NumPy array or CUDA tensor)
+    over factor x factor cells, the coarsening of the paper's 1 m DEM; returns the
+    (ceil(ny/f), ceil(nx/f)) field of the same kind and device."""
+    ny, nx = field.shape
+    my, mx = -(-ny // factor), -(-nx // factor)
+    if isinstance(field, np.ndarray):
+        src = np.ascontiguousarray(field)
+        out = np.empty((my, mx), src.dtype)
+        prec = F32 if src.dtype == np.float32 else F64
+    else:
+        import torch
+        src = field.contiguous()
+        out = src.new_empty((my, mx))
+        prec = F32 if src.dtype == torch.float32 else F64
+    ps, dev = _ptr(src)
+    pd, _ = _ptr(out)
+    _check(lib().flood_coarsen(prec, ps, nx, ny, int(factor), pd, dev, None), None)
+    return out
+
+
 def _ptr(a):
     """(pointer, on_device) of a contiguous NumPy array or torch tensor (None -> NULL)."""
     if a is None:

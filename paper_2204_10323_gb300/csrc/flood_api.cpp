@@ -574,6 +574,45 @@ extern "C" flood_status flood_step(flood_handle *h, int64_t n_steps)
     return advance(h, n_steps, nullptr, 0, nullptr, nullptr);
 }
 
+extern "C" flood_status flood_coarsen(int32_t precision, const void *src, int32_t nx, int32_t ny, int32_t factor,
+                                      void *dst, int32_t on_device, void *stream)
+{
+    if (!src || !dst) return fail(nullptr, FLOOD_ERR_ARG, "NULL argument");
+    if (precision != FLOOD_F32 && precision != FLOOD_F64) return fail(nullptr, FLOOD_ERR_ARG, "bad precision");
+    if (nx < 1 || ny < 1 || factor < 1) return fail(nullptr, FLOOD_ERR_ARG, "nx, ny and factor must be >= 1");
+    if ((int64_t)nx * ny > (int64_t)1 << 34) return fail(nullptr, FLOOD_ERR_ARG, "grid too large");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, FLOOD_ERR_CUDA, cudaGetErrorString(e));
+    cudaStream_t st = stream ? (cudaStream_t)stream : c10::cuda::getCurrentCUDAStream(dev).stream();
+    const size_t esz = precision == FLOOD_F32 ? 4 : 8;
+    const int mx = (nx + factor - 1) / factor, my = (ny + factor - 1) / factor;
+    const size_t in_bytes = (size_t)nx * ny * esz, out_bytes = (size_t)mx * my * esz;
+    void *d_src = const_cast<void *>(src), *d_dst = dst;
+    if (!on_device) {
+        try {
+            d_src = c10::cuda::CUDACachingAllocator::raw_alloc_with_stream(in_bytes, st);
+            d_dst = c10::cuda::CUDACachingAllocator::raw_alloc_with_stream(out_bytes, st);
+        } catch (...) {
+            if (d_src != src) c10::cuda::CUDACachingAllocator::raw_delete(d_src);
+            return fail(nullptr, FLOOD_ERR_OOM, "coarsen buffers");
+        }
+        e = cudaMemcpyAsync(d_src, src, in_bytes, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess)
+        e = precision == FLOOD_F32
+                ? launch_coarsen<float>((const float *)d_src, nx, ny, factor, (float *)d_dst, st)
+                : launch_coarsen<double>((const double *)d_src, nx, ny, factor, (double *)d_dst, st);
+    if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(dst, d_dst, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (!on_device) {
+        c10::cuda::CUDACachingAllocator::raw_delete(d_src);
+        c10::cuda::CUDACachingAllocator::raw_delete(d_dst);
+    }
+    if (e != cudaSuccess) return fail(nullptr, FLOOD_ERR_CUDA, cudaGetErrorString(e));
+    return FLOOD_OK;
+}
+
 // Advance to the time t_end: whole steps while they end at or before t_end,
 // then one step shortened to end exactly at t_end; the epoch keeps its time
 // step for the steps after it (their start times are rebuilt from t_end and

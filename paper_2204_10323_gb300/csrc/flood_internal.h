@@ -134,6 +134,9 @@ cudaError_t launch_epoch_batched(const EpochArgs<T> *tab, int n, const int2 *tas
 // h_max of a state into ctrl->hmax_bits (max with what is there).
 template <typename T>
 cudaError_t launch_hmax(const Geom &g, const T *h, Ctrl *ctrl, cudaStream_t st);
+// Block mean (f x f, partial blocks at the far edges) of a ny x nx field into ceil(ny/f) x ceil(nx/f).
+template <typename T>
+cudaError_t launch_coarsen(const T *src, int nx, int ny, int f, T *dst, cudaStream_t st);
 // OR of "some element is NaN or Inf" over rows x cols of a pitched array into *flag (device).
 template <typename T>
 cudaError_t launch_nonfinite(const T *a, int rows, int cols, int pitch, int *flag, cudaStream_t st);

@@ -149,3 +149,16 @@ def test_create_without_gpu_reports_cuda_error():
     import paper_2204_10323_gb300 as F
     st, h = _create(_grid(8, 8), np.zeros(64, np.float32))
     assert st == F.ERR_CUDA and not h.value
+
+
+def test_coarsen_rejects_bad_arguments():
+    import paper_2204_10323_gb300 as F
+    L = F.lib()
+    a = np.zeros((4, 4), np.float32)
+    b = np.zeros((2, 2), np.float32)
+    pa, pb = C.c_void_p(a.ctypes.data), C.c_void_p(b.ctypes.data)
+    assert L.flood_coarsen(F.F32, pa, 4, 4, 0, pb, 0, None) == F.ERR_ARG      # factor 0
+    assert L.flood_coarsen(F.F32, pa, 0, 4, 2, pb, 0, None) == F.ERR_ARG      # empty grid
+    assert L.flood_coarsen(7, pa, 4, 4, 2, pb, 0, None) == F.ERR_ARG          # precision
+    assert L.flood_coarsen(F.F32, None, 4, 4, 2, pb, 0, None) == F.ERR_ARG    # NULL source
+    assert "NULL" in F.flood_last_error(None)

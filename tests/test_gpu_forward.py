@@ -248,6 +248,30 @@ def test_empty_section_and_zero_inflow():
     assert s.ledger()["V_in"] == 0.0
 
 
+# ---------------------------------------------------------------- coarsening
+def block_mean(a, f):
+    """Mean over f x f blocks (partial blocks at the far edges over their cells), in float64."""
+    ny, nx = a.shape
+    out = np.empty((-(-ny // f), -(-nx // f)))
+    for J in range(out.shape[0]):
+        for I in range(out.shape[1]):
+            out[J, I] = a[J * f:(J + 1) * f, I * f:(I + 1) * f].astype(np.float64).mean()
+    return out
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("shape,f", [((64, 48), 2), ((37, 29), 4), ((5, 3), 8), ((16, 16), 1), ((1, 9), 2)])
+def test_coarsen_matches_block_mean(dtype, shape, f):
+    import torch
+    Fm = F()
+    z = np.random.default_rng(5).normal(10.0, 3.0, size=shape).astype(dtype)
+    ref = block_mean(z, f).astype(dtype)
+    rtol = 1e-15 if dtype == np.float64 else 1.2e-7
+    np.testing.assert_allclose(Fm.coarsen(z, f), ref, rtol=rtol)
+    zd = torch.from_numpy(z).cuda()
+    np.testing.assert_allclose(Fm.coarsen(zd, f).cpu().numpy(), ref, rtol=rtol)
+
+
 # ---------------------------------------------------------------- final-step truncation
 def _advance_pair(p, precision, targets, kernel=0, k=0):
     """Oracle and GPU through the same sequence of advances and whole steps."""
