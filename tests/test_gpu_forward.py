@@ -113,6 +113,15 @@ def test_random_fp32_matches_oracle(kernel, shape, seed):
     assert np.abs(qy - o.qy).max() < 10 * TOL32_H
 
 
+@pytest.mark.parametrize("kernel,k", [(1, 0), (2, 0), (4, 0), (5, 0), (3, 4)])
+def test_literal_bc_form_fp32_matches_oracle(kernel, k):
+    """Eq. 5 taken literally (A = dx^2, dx^2 h^(2/3) sqrt(S)/n) on every FP32 kernel family."""
+    p = inputs.random_small(97, 61, 23, bc_form=1)
+    o, V0, h, qx, qy, L = run_pair(p, 200, F().F32, kernel=kernel, steps_per_launch=k)
+    assert np.abs(h - o.h).max() < TOL32_H
+    assert abs(L["V_out"] - o.ledger.V_out) <= 1e-5 * max(o.ledger.V_out, 1.0)
+
+
 def test_c2_fp32_parity_1000_steps():
     """The 2048^2 fractal workload at reduced size (256^2 crop of the same generator)."""
     p = inputs.c2_fractal(nx=256, ny=256, steps=1000)

@@ -1,0 +1,131 @@
+"""Parity at the full sizes of the workloads, in the launch configurations the
+benchmark times.
+
+* 2048^2 fractal workload: element by element against the FP64 oracle (the
+  oracle finishes the full grid in seconds).
+* 16384^2 workload: too large for the oracle, so sampled cells.  After N steps
+  a cell depends only on the cells within N of it (one face per step), so the
+  oracle run on a window of radius N + 2 around a cell, with the GPU's time
+  step and closed window edges, gives that cell's exact FP64 value: the edge
+  faces reach only N + 1 cells inward in N steps.
+* 96-scenario ensemble (256^2 .. 2048^2) with the launch shape the benchmark's
+  autotuner picks (temporal blocking, 4 steps per launch, 128-row items):
+  sampled members element by element against the oracle run on each alone.
+
+FP32 tolerance: the FP32 path rounds about 6e-8 relative per operation on water
+levels of 10-100 m; over these 16-100 steps that stays below 1e-4 m (the
+1000-step bound is 1e-3 m).
+"""
+import numpy as np
+import pytest
+
+import inputs
+from inputs import Options, Problem
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL_SHORT = 1e-4
+
+
+def F():
+    import paper_2204_10323_gb300 as F
+    return F
+
+
+def f32(a):
+    return None if a is None else a.astype(np.float32).astype(np.float64)
+
+
+def as_f32(p):
+    return Problem(p.name, p.nx, p.ny, p.dx, f32(p.z), f32(p.n), p.sections, p.opts, h0=f32(p.h0), qx0=f32(p.qx0),
+                   qy0=f32(p.qy0), steps=p.steps, gauges=p.gauges)
+
+
+# ---------------------------------------------------------------- 2048^2, element by element
+@pytest.mark.parametrize("wet,steps", [(False, 200), (True, 100)])
+def test_c2_full_grid_matches_oracle(wet, steps):
+    Fm = F()
+    p = inputs.c2_fractal()
+    if wet:
+        p.h0 = inputs.wet_start(p.z, p.dx, 0.3)
+    q = as_f32(p)
+    o = oracle.Oracle(q)
+    o.run(steps)
+    s = Fm.Sim(q, precision=Fm.F32)                 # the default stream kernel and launch shape
+    s.step(steps)
+    h, qx, qy = s.state()
+    assert np.abs(h.astype(np.float64) - o.h).max() < TOL_SHORT
+    assert np.abs(qx.astype(np.float64) - o.qx).max() < 10 * TOL_SHORT
+    assert np.abs(qy.astype(np.float64) - o.qy).max() < 10 * TOL_SHORT
+    L = s.ledger()
+    # the CFL time step of later epochs comes from an FP32 depth maximum
+    assert L["t"] == pytest.approx(o.ledger.t, rel=1e-6)
+    assert abs(L["volume"] - o.volume()) <= 1e-5 * o.volume()
+    s.close()
+
+
+# ---------------------------------------------------------------- 16384^2, sampled cells
+@pytest.fixture(scope="module")
+def c3():
+    p = as_f32(inputs.c3_large())
+    rng = np.random.default_rng(20405)
+    N = 16
+    r = N + 2
+    wet = np.argwhere(p.h0[r:-r, r:-r] > 0) + r        # cells of the wet region (away from the borders)
+    dry = np.argwhere(p.h0[r:-r, r:-r] == 0) + r
+    pick = np.concatenate([wet[rng.choice(len(wet), 16, replace=False)],
+                           dry[rng.choice(len(dry), 4, replace=False)]])
+    return p, N, r, pick
+
+
+def window_oracle(p, jc, ic, r, dt, steps):
+    sl = (slice(jc - r, jc + r + 1), slice(ic - r, ic + r + 1))
+    w = Problem("window", 2 * r + 1, 2 * r + 1, p.dx, p.z[sl].copy(), p.n[sl].copy(), [],
+                Options(dt_mode=1, dt_const=dt, g=p.opts.g, h_dry=p.opts.h_dry), h0=p.h0[sl].copy())
+    o = oracle.Oracle(w)
+    o.run(steps)
+    return o
+
+
+@pytest.mark.parametrize("kernel,k", [(4, 0), (5, 0), (3, 4)])
+def test_c3_full_grid_sampled_cells_match_oracle(c3, kernel, k):
+    Fm = F()
+    p, N, r, pick = c3
+    s = Fm.Sim(p, precision=Fm.F32, kernel=kernel, steps_per_launch=k)
+    s.step(N)                                         # one CFL epoch of 16 steps
+    dt = s.ledger()["dt"]
+    h = s.read(Fm.FIELD_H)
+    qx = s.read(Fm.FIELD_QX)
+    s.close()
+    moved = 0
+    for jc, ic in pick:
+        o = window_oracle(p, int(jc), int(ic), r, dt, N)
+        assert abs(float(h[jc, ic]) - o.h[r, r]) < TOL_SHORT, (jc, ic)
+        assert abs(float(qx[jc, ic]) - o.qx[r, r]) < 10 * TOL_SHORT, (jc, ic)
+        moved += abs(o.h[r, r] - p.h0[jc, ic]) > 1e-6
+    assert moved >= 4                                 # the samples see water move
+
+
+# ---------------------------------------------------------------- 96-scenario ensemble
+def test_ensemble_96_sampled_members_match_oracle():
+    Fm = F()
+    probs = []
+    for s in range(96):
+        p = inputs.c4_scenario(s, steps=5000)
+        p.h0 = inputs.wet_start(p.z, p.dx, 0.3)
+        probs.append(as_f32(p))
+    ens = Fm.Ensemble(probs)
+    E = probs[0].opts.epoch_steps
+    ens.set_launch(2, 128, 4 * E)
+    ens.set_kernel(Fm.KERNEL_TILED, 4)
+    steps = 2 * E
+    ens.step(steps)
+    sizes = [q.nx * q.ny for q in probs]
+    order = np.argsort(sizes, kind="stable")
+    for m in list(order[:3]) + [int(order[len(order) // 2])]:
+        o = oracle.Oracle(probs[m])
+        o.run(steps)
+        h = ens.members[m].read(Fm.FIELD_H).astype(np.float64)
+        assert np.abs(h - o.h).max() < TOL_SHORT, m
+    ens.close()
