@@ -116,6 +116,12 @@ typedef struct {
                                     per work item (a chunk of one 120-column strip).  Negative: invalid. */
     int32_t use_graph;           /* 1: replay whole epochs from a captured CUDA graph */
     void *stream;                /* cudaStream_t, NULL = current PyTorch stream */
+    double theta;                /* face-flux weighting (default 1 = Eq. 3 as printed).  theta in (0, 1):
+                                    the numerator discharge of a face is theta q + (1 - theta)/2 times the
+                                    sum of its two neighbours along the same axis (the theta scheme of
+                                    de Almeida et al. 2012, cited in Methods); friction keeps |q| of the
+                                    face.  theta != 1: kernels REFERENCE, STREAM, TMA (AUTO) and FP64 only,
+                                    no ensembles, no adjoint (FLOOD_ERR_UNSUPPORTED) */
 } flood_opts;
 
 typedef struct flood_handle flood_handle;

@@ -71,6 +71,7 @@ class Options:
     dt_mode: int = 0          # 0: CFL epochs, 1: constant dt
     epoch_steps: int = 16
     bc_form: int = 0          # 0: cross-section Manning, 1: literal A = dx^2
+    theta: float = 1.0        # flux weighting: 1 = Eq. 3 as printed, < 1 de Almeida's theta scheme
 
 
 @dataclasses.dataclass

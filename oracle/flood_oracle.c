@@ -47,6 +47,7 @@ typedef struct {
     int32_t dt_mode;      /* 0: CFL epochs, 1: constant dt */
     int32_t epoch_steps;  /* E */
     int32_t bc_form;      /* 0: dx h^(5/3) sqrt(S)/n, 1: dx^2 h^(2/3) sqrt(S)/n */
+    double theta;         /* flux weighting: 1 = Eq. 3 as printed, < 1 de Almeida's theta scheme */
 } orc_params;
 
 typedef struct {
@@ -186,7 +187,11 @@ static double outflow_flux(const orc_params *p, double h, double slope, double n
  * Eq. 3 at one interior face between cells L (lower index) and R, with the
  * time step restored in the numerator and |q| the face's own component.
  */
-static double face_update(const orc_params *p, double dt, double q, double hL, double zL,
+/* Eq. 3 at one face.  q: the face's discharge (friction); qn: the discharge in
+ * the numerator, q itself, or with theta < 1 the weighted
+ * theta q + (1 - theta)/2 (q_prev + q_next) of the two neighbouring faces along
+ * the same axis (de Almeida et al. 2012, cited in Methods). */
+static double face_update(const orc_params *p, double dt, double q, double qn, double hL, double zL,
                           double nL, double hR, double zR, double nR)
 {
     double etaL = hL + zL, etaR = hR + zR;
@@ -196,7 +201,15 @@ static double face_update(const orc_params *p, double dt, double q, double hL, d
     double slope_term = p->g * dt * hf * (etaR - etaL) / p->dx;
     double hf_m73 = 1.0 / (hf * hf * cbrt(hf));
     double friction = p->g * dt * nf * nf * fabs(q) * hf_m73;
-    return (q - slope_term) / (1.0 + friction);
+    return (qn - slope_term) / (1.0 + friction);
+}
+
+/* Numerator discharge of a face from its own and its two neighbours' along the axis. */
+static double theta_q(const orc_params *p, double q, double q_prev, double q_next)
+{
+    if (p->theta == 1.0) return q;
+    const double w = 0.5 * (1.0 - p->theta);
+    return p->theta * q + w * (q_prev + q_next);
 }
 
 /* Set every boundary face from the sections (walls elsewhere); books V_in, V_out. */
@@ -275,13 +288,17 @@ static void step_with(const orc_params *p, const orc_section *secs, int32_t nsec
 #pragma omp parallel for num_threads(n_threads) schedule(static)
     for (int32_t j = 0; j < ny; j++)
         for (int32_t i = 1; i < nx; i++)
-            QX(qxn, j, i) = face_update(p, dt, QX(qx, j, i), H(h, j, i - 1), H(z, j, i - 1),
-                                        H(n, j, i - 1), H(h, j, i), H(z, j, i), H(n, j, i));
+            QX(qxn, j, i) = face_update(p, dt, QX(qx, j, i),
+                                        theta_q(p, QX(qx, j, i), QX(qx, j, i - 1), QX(qx, j, i + 1)),
+                                        H(h, j, i - 1), H(z, j, i - 1), H(n, j, i - 1), H(h, j, i),
+                                        H(z, j, i), H(n, j, i));
 #pragma omp parallel for num_threads(n_threads) schedule(static)
     for (int32_t j = 1; j < ny; j++)
         for (int32_t i = 0; i < nx; i++)
-            QY(qyn, j, i) = face_update(p, dt, QY(qy, j, i), H(h, j - 1, i), H(z, j - 1, i),
-                                        H(n, j - 1, i), H(h, j, i), H(z, j, i), H(n, j, i));
+            QY(qyn, j, i) = face_update(p, dt, QY(qy, j, i),
+                                        theta_q(p, QY(qy, j, i), QY(qy, j - 1, i), QY(qy, j + 1, i)),
+                                        H(h, j - 1, i), H(z, j - 1, i), H(n, j - 1, i), H(h, j, i),
+                                        H(z, j, i), H(n, j, i));
 
 #pragma omp parallel for num_threads(n_threads) schedule(static)
     for (int32_t j = 0; j < ny; j++) {
@@ -490,11 +507,11 @@ static void orc_step_reverse(const orc_params *p, const orc_section *secs, int32
     boundary_faces(p, secs, nsec, z, n, h, dt, t, qxn, qyn, &dummy);
     for (int32_t j = 0; j < ny; j++)
         for (int32_t i = 1; i < nx; i++)
-            QX(qxn, j, i) = face_update(p, dt, QX(qx, j, i), H(h, j, i - 1), H(z, j, i - 1),
+            QX(qxn, j, i) = face_update(p, dt, QX(qx, j, i), QX(qx, j, i), H(h, j, i - 1), H(z, j, i - 1),
                                         H(n, j, i - 1), H(h, j, i), H(z, j, i), H(n, j, i));
     for (int32_t j = 1; j < ny; j++)
         for (int32_t i = 0; i < nx; i++)
-            QY(qyn, j, i) = face_update(p, dt, QY(qy, j, i), H(h, j - 1, i), H(z, j - 1, i),
+            QY(qyn, j, i) = face_update(p, dt, QY(qy, j, i), QY(qy, j, i), H(h, j - 1, i), H(z, j - 1, i),
                                         H(n, j - 1, i), H(h, j, i), H(z, j, i), H(n, j, i));
 
     /* Eq. 4 and the clip: h' = max(h + dt div / dx, 0) (kept when h + ... >= 0) */
@@ -624,7 +641,8 @@ static void orc_step_reverse(const orc_params *p, const orc_section *secs, int32
  * dLdh[k*n_gauges + g] is dL/d(depth at gauge g after step k).  Starts from
  * (h0, qx0, qy0) at led0 (time, step count, dt), runs n_steps forward storing
  * every state, then sweeps back.  Writes dL/dn to gn (zeroed here) and, if the
- * pointers are given, dL/d(h0, qx0, qy0).  Returns 0, or -1 on allocation failure.
+ * pointers are given, dL/d(h0, qx0, qy0).  Returns 0, -1 on allocation failure,
+ * -3 for theta != 1 (the reverse sweep covers Eq. 3 as printed).
  */
 int orc_adjoint(const orc_params *p, const orc_section *secs, int32_t nsec, const double *z,
                 const double *n, const double *h0, const double *qx0, const double *qy0,
@@ -632,6 +650,7 @@ int orc_adjoint(const orc_params *p, const orc_section *secs, int32_t nsec, cons
                 int32_t n_gauges, const double *dLdh, double *gn, double *lh0, double *lqx0,
                 double *lqy0)
 {
+    if (p->theta != 1.0) return -3;          /* the reverse sweep covers Eq. 3 as printed */
     int32_t nx = p->nx, ny = p->ny;
     size_t NC = (size_t)nx * ny, NX = (size_t)ny * (nx + 1), NY = (size_t)(ny + 1) * nx;
     size_t per = NC + NX + NY;

@@ -41,10 +41,11 @@ template <> struct R<double> {
 
 // Eq. 3 at one interior face between cell L (lower index) and R, with the
 // time step in the numerator, |q| the face's own component, and
-// h_f = max(eta_L, eta_R) - max(z_L, z_R); 0 when h_f <= h_dry.  Operations
+// h_f = max(eta_L, eta_R) - max(z_L, z_R); 0 when h_f <= h_dry.  qn is the
+// discharge in the numerator (q itself unless theta-weighted).  Operations
 // in the order of the plain definition, each rounded once (no contraction).
 template <typename T>
-__device__ __forceinline__ T face_update_ieee(T q, T hL, T zL, T nL, T hR, T zR, T nR, T g, T dt,
+__device__ __forceinline__ T face_update_ieee(T q, T qn, T hL, T zL, T nL, T hR, T zR, T nR, T g, T dt,
                                               T dx, T h_dry)
 {
     using O = R<T>;
@@ -56,7 +57,17 @@ __device__ __forceinline__ T face_update_ieee(T q, T hL, T zL, T nL, T hR, T zR,
     T slope_term = O::div(O::mul(O::mul(gdt, hf), O::sub(etaR, etaL)), dx);
     T hf_m73 = O::div(T(1), O::mul(O::mul(hf, hf), O::cbrt(hf)));
     T friction = O::mul(O::mul(O::mul(O::mul(gdt, nf), nf), O::abs(q)), hf_m73);
-    return O::div(O::sub(q, slope_term), O::add(T(1), friction));
+    return O::div(O::sub(qn, slope_term), O::add(T(1), friction));
+}
+
+// Numerator discharge of a face (qn of face_update_ieee): q itself, or with
+// theta < 1 the weighted theta q + w (q_prev + q_next), w = (1 - theta)/2, of
+// the face and its two neighbours along the same axis.
+template <typename T>
+__device__ __forceinline__ T theta_q_ieee(T q, T q_prev, T q_next, T theta, T w, bool weighted)
+{
+    using O = R<T>;
+    return weighted ? O::add(O::mul(theta, q), O::mul(w, O::add(q_prev, q_next))) : q;
 }
 
 // Eq. 5 per boundary cell as a unit-width flux (m^2/s): bc_form 0 uses the

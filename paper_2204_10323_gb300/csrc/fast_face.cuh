@@ -14,7 +14,15 @@ struct FastConst {
     float gdt;      // g dt        (friction factor)
     float h_dry;
     float dtdx;     // dt / dx
+    float theta, w; // face-flux weighting theta and (1 - theta)/2
 };
+
+// Numerator discharge of a theta-weighted face from its own and its two
+// neighbours' discharge along the same axis.
+__device__ __forceinline__ float theta_q(float q, float q_prev, float q_next, const FastConst &k)
+{
+    return __fadd_rn(__fmul_rn(k.theta, q), __fmul_rn(k.w, __fadd_rn(q_prev, q_next)));
+}
 
 // x^(-7/3) for x > 0 as 2^(-7/3 log2 x) with the hardware base-2 logarithm
 // and exponential (relative error below 1e-6 for the depths of a flood).
@@ -36,14 +44,16 @@ __device__ __forceinline__ float rcp_fast(float x)
     return r;
 }
 
-// Eq. 3 for a wet face of flow depth hf.  Called with hf <= 0 the result is
-// NaN or garbage, never a trap; face_fast_sel discards it.
-__device__ __forceinline__ float face_wet(float q, float etaL, float etaR, float hf, float nsum, const FastConst &k)
+// Eq. 3 for a wet face of flow depth hf: friction from the face's own q, qn in
+// the numerator (q itself unless theta-weighted).  Called with hf <= 0 the
+// result is NaN or garbage, never a trap; face_fast_sel discards it.
+__device__ __forceinline__ float face_wet(float q, float qn, float etaL, float etaR, float hf, float nsum,
+                                          const FastConst &k)
 {
     float r7 = pow_m73(hf);
     float nf = __fmul_rn(0.5f, nsum);
     float fric = __fmul_rn(__fmul_rn(__fmul_rn(k.gdt, __fmul_rn(nf, nf)), fabsf(q)), r7);
-    float num = __fsub_rn(q, __fmul_rn(__fmul_rn(k.a1, hf), __fsub_rn(etaR, etaL)));
+    float num = __fsub_rn(qn, __fmul_rn(__fmul_rn(k.a1, hf), __fsub_rn(etaR, etaL)));
     return __fmul_rn(num, rcp_fast(__fadd_rn(1.0f, fric)));
 }
 
@@ -54,7 +64,16 @@ __device__ __forceinline__ float face_fast(float q, float etaL, float etaR, floa
 {
     float hf = __fsub_rn(fmaxf(etaL, etaR), zmax);
     if (!(hf > k.h_dry)) return 0.0f;
-    return face_wet(q, etaL, etaR, hf, nsum, k);
+    return face_wet(q, q, etaL, etaR, hf, nsum, k);
+}
+
+// face_fast with the numerator discharge qn given (theta-weighted faces).
+__device__ __forceinline__ float face_fast_qn(float q, float qn, float etaL, float etaR, float zmax, float nsum,
+                                              const FastConst &k)
+{
+    float hf = __fsub_rn(fmaxf(etaL, etaR), zmax);
+    if (!(hf > k.h_dry)) return 0.0f;
+    return face_wet(q, qn, etaL, etaR, hf, nsum, k);
 }
 
 // The same value as face_fast without a branch: a dry face is evaluated too
@@ -64,7 +83,16 @@ __device__ __forceinline__ float face_fast_sel(float q, float etaL, float etaR, 
                                                const FastConst &k)
 {
     float hf = __fsub_rn(fmaxf(etaL, etaR), zmax);
-    float v = face_wet(q, etaL, etaR, hf, nsum, k);
+    float v = face_wet(q, q, etaL, etaR, hf, nsum, k);
+    return hf > k.h_dry ? v : 0.0f;
+}
+
+// face_fast_sel with the numerator discharge qn given (theta-weighted faces).
+__device__ __forceinline__ float face_fast_sel_qn(float q, float qn, float etaL, float etaR, float zmax, float nsum,
+                                                  const FastConst &k)
+{
+    float hf = __fsub_rn(fmaxf(etaL, etaR), zmax);
+    float v = face_wet(q, qn, etaL, etaR, hf, nsum, k);
     return hf > k.h_dry ? v : 0.0f;
 }
 

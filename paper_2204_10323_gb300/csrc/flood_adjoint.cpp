@@ -336,6 +336,7 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     if (n_steps < 1 || n_gauges < 0 || n_checkpoints < 1 || !dLdn_out || (n_gauges > 0 && (!gauge_cells || !dLdh)))
         return fail(h, FLOOD_ERR_ARG, "bad adjoint arguments");
     if (h->sticky) return fail(h, FLOOD_ERR_STATE, "handle is in an error state; write a new state first");
+    if (h->geo.theta != 1.0) return fail(h, FLOOD_ERR_UNSUPPORTED, "the adjoint covers theta = 1 (Eq. 3 as printed)");
     const int64_t nc = (int64_t)h->geo.nx * h->geo.ny;
     for (int g = 0; g < n_gauges; g++)
         if (gauge_cells[g] < 0 || gauge_cells[g] >= nc) return fail(h, FLOOD_ERR_ARG, "gauge cell out of range");

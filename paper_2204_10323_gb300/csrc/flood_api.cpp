@@ -92,6 +92,7 @@ extern "C" void flood_default_opts(flood_opts *o)
     o->tile_y = 0;
     o->use_graph = 0;
     o->stream = nullptr;
+    o->theta = 1.0;
 }
 
 extern "C" const char *flood_version(void) { return "flood-gb300 0.1 (sm_103a)"; }
@@ -311,6 +312,11 @@ static flood_status validate(const flood_grid *grid, const flood_bc_section *sec
     if (o.bc_form != 0 && o.bc_form != 1) return fail(nullptr, FLOOD_ERR_ARG, "bc_form must be 0 or 1");
     if (o.kernel < 0 || o.kernel > 5) return fail(nullptr, FLOOD_ERR_ARG, "unknown kernel");
     if (o.tile_x < 0 || o.tile_y < 0) return fail(nullptr, FLOOD_ERR_ARG, "tile_x and tile_y must be >= 0");
+    if (!(o.theta > 0.0 && o.theta <= 1.0)) return fail(nullptr, FLOOD_ERR_ARG, "theta must lie in (0, 1]");
+    if (o.theta != 1.0 && grid->precision == FLOOD_F32 &&
+        !(o.kernel == FLOOD_KERNEL_AUTO || o.kernel == FLOOD_KERNEL_REFERENCE || o.kernel == FLOOD_KERNEL_STREAM ||
+          o.kernel == FLOOD_KERNEL_TMA))
+        return fail(nullptr, FLOOD_ERR_UNSUPPORTED, "theta != 1 needs the REFERENCE, STREAM or TMA kernel");
     if (o.kernel == FLOOD_KERNEL_TILED) {
         int K = o.steps_per_launch > 0 ? o.steps_per_launch : 4;
         if (!(K <= 4 || K == 8) || o.epoch_steps % K != 0)
@@ -396,6 +402,7 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
     G.ny = grid->ny;
     G.pitch = (grid->nx + 1 + 31) / 32 * 32;
     G.bc_form = o.bc_form;
+    G.theta = o.theta;
     G.dx = grid->dx;
     G.dx_f = (float)grid->dx;
     G.g = o.g;

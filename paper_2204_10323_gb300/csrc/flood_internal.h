@@ -45,6 +45,7 @@ struct Geom {
     int bc_form;
     double dx, g, h_dry;
     float dx_f, h_dry_f;          // dx and h_dry rounded to FP32 once (the fast kernels' boundary faces)
+    double theta;                 // face-flux weighting (1 = Eq. 3 as printed)
     double cfl_alpha, dt_cap, dt_const;
     int dt_mode, epoch_steps;
 };

@@ -38,6 +38,8 @@ __global__ void __launch_bounds__(BX *BY) step_reference_kernel(const StepArgs<T
     const int j = blockIdx.y * BY + threadIdx.y;
     const bool in = i < G.nx && j < G.ny;
     const T dt = T(a.ctrl->dt), dx = T(G.dx), g = T(G.g), hd = T(G.h_dry);
+    const bool wt = G.theta != 1.0;                   // theta-weighted numerator discharges
+    const T th = T(G.theta), w = T(0.5 * (1.0 - G.theta));
     double vout = 0.0, vclip = 0.0, hmax = 0.0;
     T hn = T(0);
     if (in) {
@@ -45,14 +47,20 @@ __global__ void __launch_bounds__(BX *BY) step_reference_kernel(const StepArgs<T
         const size_t c = (size_t)j * P + i;
         const T hC = a.h[c], zC = a.z[c], nC = a.n[c];
         T qW, qE, qS, qN;
+        // (interior x-faces i in 1..nx-1 have neighbours i-1 >= 0 and i+1 <= nx in the row,
+        // interior y-faces j in 1..ny-1 neighbours j-1 >= 0 and j+1 <= ny)
         if (i == 0) qW = boundary_face(a, 0, j, hC, nC, vout);
-        else qW = face_update_ieee<T>(a.qx[c], a.h[c - 1], a.z[c - 1], a.n[c - 1], hC, zC, nC, g, dt, dx, hd);
+        else qW = face_update_ieee<T>(a.qx[c], wt ? theta_q_ieee<T>(a.qx[c], a.qx[c - 1], a.qx[c + 1], th, w, true) : a.qx[c],
+                                      a.h[c - 1], a.z[c - 1], a.n[c - 1], hC, zC, nC, g, dt, dx, hd);
         if (i == G.nx - 1) qE = boundary_face(a, 1, j, hC, nC, vout);
-        else qE = face_update_ieee<T>(a.qx[c + 1], hC, zC, nC, a.h[c + 1], a.z[c + 1], a.n[c + 1], g, dt, dx, hd);
+        else qE = face_update_ieee<T>(a.qx[c + 1], wt ? theta_q_ieee<T>(a.qx[c + 1], a.qx[c], a.qx[c + 2], th, w, true) : a.qx[c + 1],
+                                      hC, zC, nC, a.h[c + 1], a.z[c + 1], a.n[c + 1], g, dt, dx, hd);
         if (j == 0) qS = boundary_face(a, 2, i, hC, nC, vout);
-        else qS = face_update_ieee<T>(a.qy[c], a.h[c - P], a.z[c - P], a.n[c - P], hC, zC, nC, g, dt, dx, hd);
+        else qS = face_update_ieee<T>(a.qy[c], wt ? theta_q_ieee<T>(a.qy[c], a.qy[c - P], a.qy[c + P], th, w, true) : a.qy[c],
+                                      a.h[c - P], a.z[c - P], a.n[c - P], hC, zC, nC, g, dt, dx, hd);
         if (j == G.ny - 1) qN = boundary_face(a, 3, i, hC, nC, vout);
-        else qN = face_update_ieee<T>(a.qy[c + P], hC, zC, nC, a.h[c + P], a.z[c + P], a.n[c + P], g, dt, dx, hd);
+        else qN = face_update_ieee<T>(a.qy[c + P], wt ? theta_q_ieee<T>(a.qy[c + P], a.qy[c], a.qy[c + 2 * P], th, w, true) : a.qy[c + P],
+                                      hC, zC, nC, a.h[c + P], a.z[c + P], a.n[c + P], g, dt, dx, hd);
         // Eq. 4 with the new fluxes, then the depth clip
         T dv = O::add(O::sub(qW, qE), O::sub(qS, qN));
         hn = O::add(hC, O::div(O::mul(dt, dv), dx));

@@ -87,7 +87,11 @@ __device__ __forceinline__ void set(float4 &v, int k, float x)
 //
 // kTensor: stage 2D tiles of kRowsT rows with tensor copies (maps: the grid's
 // tensor maps; the ring counts tiles) instead of one 1D copy per row.
-template <bool kTensor>
+// kTheta: theta-weighted numerator discharges (FastConst theta, w): an x-face
+// takes its row neighbours from the lane, the neighbouring lanes and the
+// staged halo columns, a y-face the previous row's old qy (kept in registers)
+// and the next row's (one global load per row).
+template <bool kTensor, bool kTheta = false>
 __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int step, const int want_hmax, const int bx,
                                             const int by, const int rows, unsigned char *smem_raw, double *red,
                                             uint32_t &ring_base, const bool fresh, const TmaMaps *maps = nullptr)
@@ -123,6 +127,8 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
     K.a1 = K.gdt / dx;
     K.h_dry = (float)G.h_dry;
     K.dtdx = dt / dx;
+    K.theta = (float)G.theta;
+    K.w = (float)(0.5 * (1.0 - G.theta));
 
     double vout = 0.0, vclip = 0.0;
     float hmax = 0.0f;
@@ -162,12 +168,14 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
 
     float4 hp = make_float4(0, 0, 0, 0), zp = hp, np_ = hp;
     float4 qxw_p = hp, qys_p = hp;
+    float4 qyo_p = hp;                            // old qy of the previous row (theta weighting)
     float qxe_p3 = 0.0f;
     if (active) {
         for (int j = jstart; j <= y1; j++) {
             const int idx = j - jstart;
             float4 ch = make_float4(0, 0, 0, 0), cz = ch, cn = ch, cqx = ch, cqy = ch;
             float hW = 0.f, zW = 0.f, nW = 0.f, hE = 0.f, zE = 0.f, nE = 0.f, qxE = 0.f;
+            float qxW = 0.f, qxEE = 0.f;              // old qx at x0-1 and x0+129 (theta weighting)
             if (j < ny) {
                 const int st = idx / R, sub = idx - st * R;
                 const uint32_t g = ring_base + (uint32_t)st;
@@ -190,12 +198,14 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
                     hW = row_at(s, 0, sub)[3];
                     zW = row_at(s, 1, sub)[3];
                     nW = row_at(s, 2, sub)[3];
+                    if constexpr (kTheta) qxW = row_at(s, 3, sub)[3];
                 }
                 if (lane == 31) {
                     hE = row_at(s, 0, sub)[132];
                     zE = row_at(s, 1, sub)[132];
                     nE = row_at(s, 2, sub)[132];
                     qxE = row_at(s, 3, sub)[132];
+                    if constexpr (kTheta) qxEE = row_at(s, 3, sub)[133];
                 }
                 if (sub == R - 1) {           // stage read completely: refill it
                     __syncwarp();
@@ -210,17 +220,30 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
                 hp = ch;
                 zp = cz;
                 np_ = cn;
+                qyo_p = cqy;
                 continue;
             }
             // ---- new south faces of row j
             // (interior rows branch-free; the boundary rows, uniform over the warp, take Eq. 5-6)
             float4 qys;
             if (j > 0 && j < ny) {
+                if constexpr (kTheta) {
+                    // old qy of the next row's south faces (row j + 1 <= ny of the qy array)
+                    float4 qyn = make_float4(0, 0, 0, 0);
+                    if (c0 < P) qyn = __ldg(reinterpret_cast<const float4 *>(a.qy + (size_t)(j + 1) * P + c0));
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const float zl = get(zp, k), zr = get(cz, k);
-                    set(qys, k, face_fast_sel(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr, fmaxf(zl, zr),
-                                              get(np_, k) + get(cn, k), K));
+                    for (int k = 0; k < 4; k++) {
+                        const float zl = get(zp, k), zr = get(cz, k), q = get(cqy, k);
+                        set(qys, k, face_fast_sel_qn(q, theta_q(q, get(qyo_p, k), get(qyn, k), K), get(hp, k) + zl,
+                                                     get(ch, k) + zr, fmaxf(zl, zr), get(np_, k) + get(cn, k), K));
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const float zl = get(zp, k), zr = get(cz, k);
+                        set(qys, k, face_fast_sel(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr, fmaxf(zl, zr),
+                                                  get(np_, k) + get(cn, k), K));
+                    }
                 }
                 if (!full) {
 #pragma unroll
@@ -309,13 +332,30 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
                 nl0 = nW;
             }
             float4 qxw;
+            if constexpr (kTheta) {
+                // old qx of the faces left of the lane's first and right of its last column
+                float ql0 = __shfl_up_sync(0xffffffffu, cqx.w, 1);
+                float qr3 = __shfl_down_sync(0xffffffffu, cqx.x, 1);
+                if (lane == 0) ql0 = qxW;
+                if (lane == 31) qr3 = qxE;
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const float hl = k == 0 ? hl0 : get(ch, k - 1);
-                const float zl = k == 0 ? zl0 : get(cz, k - 1);
-                const float nl = k == 0 ? nl0 : get(cn, k - 1);
-                const float zr = get(cz, k);
-                set(qxw, k, face_fast_sel(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), K));
+                for (int k = 0; k < 4; k++) {
+                    const float hl = k == 0 ? hl0 : get(ch, k - 1);
+                    const float zl = k == 0 ? zl0 : get(cz, k - 1);
+                    const float nl = k == 0 ? nl0 : get(cn, k - 1);
+                    const float zr = get(cz, k), q = get(cqx, k);
+                    const float qn = theta_q(q, k == 0 ? ql0 : get(cqx, k - 1), k == 3 ? qr3 : get(cqx, k + 1), K);
+                    set(qxw, k, face_fast_sel_qn(q, qn, hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), K));
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float hl = k == 0 ? hl0 : get(ch, k - 1);
+                    const float zl = k == 0 ? zl0 : get(cz, k - 1);
+                    const float nl = k == 0 ? nl0 : get(cn, k - 1);
+                    const float zr = get(cz, k);
+                    set(qxw, k, face_fast_sel(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), K));
+                }
             }
             if (c0 == 0 || !full) {               // lanes holding x = 0 or x >= nx: Eq. 5-6, or no face
 #pragma unroll
@@ -333,11 +373,18 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
                 const int c = x0 + 128;
                 qe = 0.0f;
                 if (c == nx) qe = boundary_fast_at(a, step, 1, j, ch.w, cn.w, vout);
-                else if (c < nx) qe = face_fast(qxE, ch.w + cz.w, hE + zE, fmaxf(cz.w, zE), cn.w + nE, K);
+                else if (c < nx) {
+                    if constexpr (kTheta)
+                        qe = face_fast_qn(qxE, theta_q(qxE, cqx.w, qxEE, K), ch.w + cz.w, hE + zE, fmaxf(cz.w, zE),
+                                          cn.w + nE, K);
+                    else
+                        qe = face_fast(qxE, ch.w + cz.w, hE + zE, fmaxf(cz.w, zE), cn.w + nE, K);
+                }
             }
             hp = ch;
             zp = cz;
             np_ = cn;
+            qyo_p = cqy;
             qxw_p = qxw;
             qxe_p3 = qe;
             qys_p = qys;
@@ -375,15 +422,17 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
     return abort;
 }
 
+template <bool kTheta>
 __global__ void __launch_bounds__(kMaxWarps * 32, 5) step_stream_kernel(const StepArgs<float> a, const int rows)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     uint32_t ring_base = 0;
-    stream_body<false>(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, smem_raw, red, ring_base, true);
+    stream_body<false, kTheta>(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, smem_raw, red, ring_base, true);
 }
 
 // The same step with every warp's rows staged as 2D tiles by tensor copies.
+template <bool kTheta>
 __global__ void __launch_bounds__(kMaxWarps * 32, 4)
     step_tma_kernel(const StepArgs<float> a, const int rows, const __grid_constant__ TmaMaps maps)
 {
@@ -391,7 +440,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
     __shared__ double red[32];
     unsigned char *base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);   // 128-byte aligned rings
     uint32_t ring_base = 0;
-    stream_body<true>(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, base, red, ring_base, true, &maps);
+    stream_body<true, kTheta>(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, base, red, ring_base, true,
+                              &maps);
 }
 
 // Many grids in one launch: block b belongs to the scenario whose block range
@@ -422,8 +472,11 @@ cudaError_t configure(int warps)
 {
     static bool configured = false;
     if (configured) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(step_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(step_stream_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(sizeof(WarpRing) * kMaxWarps));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(step_stream_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(WarpRing) * kMaxWarps));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(step_stream_ensemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(WarpRing) * kMaxWarps));
@@ -471,7 +524,8 @@ cudaError_t launch_step_stream(const StepArgs<float> &a, cudaStream_t st)
     if (e != cudaSuccess) return e;
     const int strips = (a.geo.nx + 127) / 128;
     dim3 grid((strips + warps - 1) / warps, (a.geo.ny + rows - 1) / rows);
-    step_stream_kernel<<<grid, warps * 32, sizeof(WarpRing) * warps, st>>>(a, rows);
+    if (a.geo.theta != 1.0) step_stream_kernel<true><<<grid, warps * 32, sizeof(WarpRing) * warps, st>>>(a, rows);
+    else step_stream_kernel<false><<<grid, warps * 32, sizeof(WarpRing) * warps, st>>>(a, rows);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.gauge_out) return launch_gauges<float>(a.geo, a.h_out, a.gauge_cells, a.n_gauges, a.gauge_out, st);
@@ -521,9 +575,11 @@ cudaError_t launch_step_tma(const StepArgs<float> &a, cudaStream_t st)
     const size_t smem = sizeof(WarpRingT) * warps + 128;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(step_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(WarpRingT) * kMaxWarps + 128));
-        if (e != cudaSuccess) return e;
+        for (auto k : {step_tma_kernel<false>, step_tma_kernel<true>}) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(sizeof(WarpRingT) * kMaxWarps + 128));
+            if (e != cudaSuccess) return e;
+        }
         configured = true;
     }
     const int P = a.geo.pitch, ny = a.geo.ny;
@@ -535,7 +591,8 @@ cudaError_t launch_step_tma(const StepArgs<float> &a, cudaStream_t st)
     }
     const int strips = (a.geo.nx + 127) / 128;
     dim3 grid((strips + warps - 1) / warps, (ny + rows - 1) / rows);
-    step_tma_kernel<<<grid, warps * 32, smem, st>>>(a, rows, maps);
+    if (a.geo.theta != 1.0) step_tma_kernel<true><<<grid, warps * 32, smem, st>>>(a, rows, maps);
+    else step_tma_kernel<false><<<grid, warps * 32, smem, st>>>(a, rows, maps);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.gauge_out) return launch_gauges<float>(a.geo, a.h_out, a.gauge_cells, a.n_gauges, a.gauge_out, st);

@@ -162,3 +162,18 @@ def test_coarsen_rejects_bad_arguments():
     assert L.flood_coarsen(7, pa, 4, 4, 2, pb, 0, None) == F.ERR_ARG          # precision
     assert L.flood_coarsen(F.F32, None, 4, 4, 2, pb, 0, None) == F.ERR_ARG    # NULL source
     assert "NULL" in F.flood_last_error(None)
+
+
+def test_create_rejects_theta_out_of_range_and_unsupported_kernels():
+    import paper_2204_10323_gb300 as F
+    for bad in (0.0, -0.5, 1.5, float("nan")):
+        o = F.default_opts()
+        o.theta = bad
+        st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
+        assert st == F.ERR_ARG and "theta" in F.flood_last_error(None)
+    for kernel in (F.KERNEL_ROWS, F.KERNEL_TILED):
+        o = F.default_opts()
+        o.theta = 0.8
+        o.kernel = kernel
+        st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
+        assert st == F.ERR_UNSUPPORTED and "theta" in F.flood_last_error(None)

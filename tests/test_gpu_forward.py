@@ -257,6 +257,66 @@ def test_empty_section_and_zero_inflow():
     assert s.ledger()["V_in"] == 0.0
 
 
+# ---------------------------------------------------------------- theta-weighted faces
+def with_theta(p, theta):
+    p.opts.theta = theta
+    return p
+
+
+@pytest.mark.parametrize("theta", [0.9, 0.7])
+@pytest.mark.parametrize("shape,seed", [((33, 17), 0), ((130, 70), 2), ((1, 9), 3), ((9, 1), 4)])
+def test_theta_fp64_matches_oracle(theta, shape, seed):
+    p = with_theta(inputs.random_small(shape[0], shape[1], seed), theta)
+    o, V0, h, qx, qy, L = run_pair(p, 120, F().F64)
+    assert np.abs(h - o.h).max() < TOL64
+    assert np.abs(qx - o.qx).max() < TOL64
+    assert np.abs(qy - o.qy).max() < TOL64
+    check_ledger(o, L, 1e-12)
+
+
+def test_theta_fp64_channel_1000_steps():
+    # theta = 0.8: at theta = 0.7 the channel at the CFL limit (alpha 0.7, 2 s steps)
+    # diverges after ~750 steps in the oracle as on the GPU (a property of the scheme)
+    p = with_theta(inputs.c1_tilted_channel(), 0.8)
+    o, V0, h, qx, qy, L = run_pair(p, 1000, F().F64)
+    assert np.abs(h - o.h).max() < TOL64
+    check_ledger(o, L, 1e-12)
+
+
+@pytest.mark.parametrize("kernel", [1, 4, 5])
+@pytest.mark.parametrize("shape,seed", [((130, 70), 2), ((257, 129), 6), ((129, 33), 9)])
+def test_theta_fp32_matches_oracle(kernel, shape, seed):
+    p = with_theta(inputs.random_small(shape[0], shape[1], seed), 0.8)
+    o, V0, h, qx, qy, L = run_pair(p, 100, F().F32, kernel=kernel)
+    assert np.abs(h - o.h).max() < TOL32_H
+    assert np.abs(qx - o.qx).max() < 10 * TOL32_H
+    assert np.abs(qy - o.qy).max() < 10 * TOL32_H
+
+
+@pytest.mark.parametrize("tile", [(0, 0), (2, 9), (1, 3)])
+def test_theta_tma_tiles_equal_row_staging_bitwise(tile):
+    Fm = F()
+    p = as_f32_problem(with_theta(inputs.random_small(257, 129, 6), 0.75))
+    a = Fm.Sim(p, kernel=Fm.KERNEL_STREAM, tile=tile)
+    b = Fm.Sim(p, kernel=Fm.KERNEL_TMA, tile=tile)
+    a.step(37)
+    b.step(37)
+    for f in (Fm.FIELD_H, Fm.FIELD_QX, Fm.FIELD_QY):
+        assert np.array_equal(a.read(f), b.read(f)), f
+
+
+def test_theta_adjoint_and_ensemble_are_refused():
+    Fm = F()
+    p = with_theta(inputs.random_small(20, 12, 2), 0.8)
+    s = Fm.Sim(p, precision=Fm.F64)
+    with pytest.raises(Fm.FloodError) as e:
+        s.adjoint(4, np.array([[3, 3]]), np.ones((4, 1)))
+    assert e.value.status == Fm.ERR_UNSUPPORTED
+    with pytest.raises(Fm.FloodError) as e:
+        Fm.Ensemble([p])
+    assert e.value.status == Fm.ERR_UNSUPPORTED
+
+
 # ---------------------------------------------------------------- coarsening
 def block_mean(a, f):
     """Mean over f x f blocks (partial blocks at the far edges over their cells), in float64."""

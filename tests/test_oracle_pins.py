@@ -321,6 +321,53 @@ def test_advance_in_cfl_epochs_keeps_the_books():
     assert o.volume() - V0 == pytest.approx(o.ledger.V_in + o.ledger.V_clip, rel=1e-12)
 
 
+# ---------------------------------------------------------------- theta-weighted faces
+def test_theta_scheme_hand_values_one_row():
+    """de Almeida's theta weighting, theta = 0.7, one step on a row of 4 cells:
+    flat bed, h = (1.0, 0.9, 0.8, 0.7), faces (0, 0.2, 0.1, 0.05, 0) with closed
+    ends, n = 0.03, dt = 0.1 s, dx = 1 m.  Numerator discharge of face i:
+    0.7 q_i + 0.15 (q_{i-1} + q_{i+1}); friction with |q_i| itself.  Literals:
+    40-digit decimal evaluation of those formulas, done by hand."""
+    p = closed_box(np.zeros((1, 4)), [[1.0, 0.9, 0.8, 0.7]], theta=0.7, n=0.03)
+    p.qx0 = np.array([[0.0, 0.2, 0.1, 0.05, 0.0]])
+    o = oracle.Oracle(p)
+    o.run(1)
+    np.testing.assert_allclose(o.qx[0, 1:4], [0.2530553154923903537113417, 0.1957678985649310959148924,
+                                              0.1284704542920134320134527], rtol=1e-14)
+    np.testing.assert_allclose(o.h[0], [0.9746944684507609646288658, 0.9057287416927459257796449,
+                                        0.8067297444272917663901440, 0.7128470454292013432013453], rtol=1e-14)
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.9, 0.7, 0.55])
+def test_theta_scheme_uniform_and_checkerboard_fluxes(theta):
+    """Flat water surface, no friction: the slope term vanishes and a face keeps
+    theta q + (1 - theta)/2 (q_prev + q_next).  A uniform flux field (faces away
+    from the walls) is kept exactly; a field alternating +a, -a from face to face
+    is scaled by 2 theta - 1 per step (the damping of the theta scheme)."""
+    nx = 12
+    z = np.zeros((1, nx))
+    h0 = np.full((1, nx), 2.0)
+    uni = closed_box(z, h0, theta=theta, n=0.0)
+    uni.qx0 = np.concatenate([[0.0], np.full(nx - 1, 0.3), [0.0]])[None, :]
+    o = oracle.Oracle(uni)
+    o.step_dt(1e-9)                     # a step too short to change the depths measurably
+    np.testing.assert_allclose(o.qx[0, 2:nx - 1], 0.3, rtol=1e-14)
+    chk = closed_box(z, h0, theta=theta, n=0.0)
+    a = 0.2 * (-1.0) ** np.arange(nx + 1)
+    a[0] = a[-1] = 0.0
+    chk.qx0 = a[None, :]
+    o = oracle.Oracle(chk)
+    o.step_dt(1e-9)
+    np.testing.assert_allclose(o.qx[0, 2:nx - 1], (2 * theta - 1) * a[2:nx - 1], rtol=1e-12, atol=1e-15)
+
+
+def test_theta_scheme_oracle_adjoint_is_refused():
+    p = closed_box(np.zeros((2, 3)), np.ones((2, 3)), theta=0.8)
+    o = oracle.Oracle(p)
+    with pytest.raises(NotImplementedError):
+        o.adjoint(2, np.array([[1, 1]]), np.ones((2, 1)))
+
+
 # ---------------------------------------------------------------- boundary conditions
 def test_section_fraction_rule():
     p = inputs.random_small(20, 12, 0)
