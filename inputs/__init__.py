@@ -72,6 +72,7 @@ class Options:
     epoch_steps: int = 16
     bc_form: int = 0          # 0: cross-section Manning, 1: literal A = dx^2
     theta: float = 1.0        # flux weighting: 1 = Eq. 3 as printed, < 1 de Almeida's theta scheme
+    friction: int = 0         # |q| in friction: 0 the face's component, 1 vector norm with the orthogonal mean
 
 
 @dataclasses.dataclass

@@ -27,7 +27,7 @@ class Params(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("dx", C.c_double), ("g", C.c_double),
                 ("h_dry", C.c_double), ("cfl_alpha", C.c_double), ("dt_cap", C.c_double),
                 ("dt_const", C.c_double), ("dt_mode", C.c_int32), ("epoch_steps", C.c_int32),
-                ("bc_form", C.c_int32), ("theta", C.c_double)]
+                ("bc_form", C.c_int32), ("theta", C.c_double), ("friction", C.c_int32)]
 
 
 class SectionC(C.Structure):
@@ -111,7 +111,8 @@ class Oracle:
         self.prob = prob
         o = prob.opts
         self.params = Params(prob.nx, prob.ny, prob.dx, o.g, o.h_dry, o.cfl_alpha, o.dt_cap,
-                             o.dt_const, o.dt_mode, o.epoch_steps, o.bc_form, getattr(o, "theta", 1.0))
+                             o.dt_const, o.dt_mode, o.epoch_steps, o.bc_form, getattr(o, "theta", 1.0),
+                             getattr(o, "friction", 0))
         self.z = np.ascontiguousarray(prob.z, np.float64)
         self.n = np.ascontiguousarray(prob.n, np.float64)
         h0, qx0, qy0 = prob.initial_state(np.float64)
@@ -215,7 +216,7 @@ class Oracle:
                                cells.ctypes.data_as(C.POINTER(C.c_int64)), cells.size, _dp(seed), _dp(gn),
                                _dp(lh), _dp(lqx), _dp(lqy))
         if rc == -3:
-            raise NotImplementedError("the oracle adjoint covers theta = 1 (Eq. 3 as printed)")
+            raise NotImplementedError("the oracle adjoint covers Eq. 3 as printed (theta = 1, own-component friction)")
         if rc != 0:
             raise MemoryError("oracle adjoint store")
         return (gn, lh, lqx, lqy) if want_state else gn

@@ -48,6 +48,7 @@ typedef struct {
     int32_t epoch_steps;  /* E */
     int32_t bc_form;      /* 0: dx h^(5/3) sqrt(S)/n, 1: dx^2 h^(2/3) sqrt(S)/n */
     double theta;         /* flux weighting: 1 = Eq. 3 as printed, < 1 de Almeida's theta scheme */
+    int32_t friction;     /* 0: |q| of the face's own component, 1: vector norm with the orthogonal mean */
 } orc_params;
 
 typedef struct {
@@ -191,8 +192,8 @@ static double outflow_flux(const orc_params *p, double h, double slope, double n
  * the numerator, q itself, or with theta < 1 the weighted
  * theta q + (1 - theta)/2 (q_prev + q_next) of the two neighbouring faces along
  * the same axis (de Almeida et al. 2012, cited in Methods). */
-static double face_update(const orc_params *p, double dt, double q, double qn, double hL, double zL,
-                          double nL, double hR, double zR, double nR)
+static double face_update(const orc_params *p, double dt, double q, double qn, double qmag, double hL,
+                          double zL, double nL, double hR, double zR, double nR)
 {
     double etaL = hL + zL, etaR = hR + zR;
     double hf = fmax(etaL, etaR) - fmax(zL, zR);
@@ -200,8 +201,19 @@ static double face_update(const orc_params *p, double dt, double q, double qn, d
     double nf = 0.5 * (nL + nR);
     double slope_term = p->g * dt * hf * (etaR - etaL) / p->dx;
     double hf_m73 = 1.0 / (hf * hf * cbrt(hf));
-    double friction = p->g * dt * nf * nf * fabs(q) * hf_m73;
+    double friction = p->g * dt * nf * nf * qmag * hf_m73;
     return (qn - slope_term) / (1.0 + friction);
+}
+
+/* |q| in the friction term: the face's own component (reading of Methods'
+ * axis-by-axis integration), or the vector norm with the orthogonal component
+ * taken as the mean of the four faces of the other axis around this face
+ * (a, b: the two on the lower-index side, c, d: on the other). */
+static double q_mag(const orc_params *p, double q, double a, double b, double c, double d)
+{
+    if (p->friction == 0) return fabs(q);
+    const double qo = 0.25 * ((a + b) + (c + d));
+    return sqrt(q * q + qo * qo);
 }
 
 /* Numerator discharge of a face from its own and its two neighbours' along the axis. */
@@ -290,6 +302,8 @@ static void step_with(const orc_params *p, const orc_section *secs, int32_t nsec
         for (int32_t i = 1; i < nx; i++)
             QX(qxn, j, i) = face_update(p, dt, QX(qx, j, i),
                                         theta_q(p, QX(qx, j, i), QX(qx, j, i - 1), QX(qx, j, i + 1)),
+                                        q_mag(p, QX(qx, j, i), QY(qy, j, i - 1), QY(qy, j, i),
+                                              QY(qy, j + 1, i - 1), QY(qy, j + 1, i)),
                                         H(h, j, i - 1), H(z, j, i - 1), H(n, j, i - 1), H(h, j, i),
                                         H(z, j, i), H(n, j, i));
 #pragma omp parallel for num_threads(n_threads) schedule(static)
@@ -297,6 +311,8 @@ static void step_with(const orc_params *p, const orc_section *secs, int32_t nsec
         for (int32_t i = 0; i < nx; i++)
             QY(qyn, j, i) = face_update(p, dt, QY(qy, j, i),
                                         theta_q(p, QY(qy, j, i), QY(qy, j - 1, i), QY(qy, j + 1, i)),
+                                        q_mag(p, QY(qy, j, i), QX(qx, j - 1, i), QX(qx, j - 1, i + 1),
+                                              QX(qx, j, i), QX(qx, j, i + 1)),
                                         H(h, j - 1, i), H(z, j - 1, i), H(n, j - 1, i), H(h, j, i),
                                         H(z, j, i), H(n, j, i));
 
@@ -507,11 +523,11 @@ static void orc_step_reverse(const orc_params *p, const orc_section *secs, int32
     boundary_faces(p, secs, nsec, z, n, h, dt, t, qxn, qyn, &dummy);
     for (int32_t j = 0; j < ny; j++)
         for (int32_t i = 1; i < nx; i++)
-            QX(qxn, j, i) = face_update(p, dt, QX(qx, j, i), QX(qx, j, i), H(h, j, i - 1), H(z, j, i - 1),
+            QX(qxn, j, i) = face_update(p, dt, QX(qx, j, i), QX(qx, j, i), fabs(QX(qx, j, i)), H(h, j, i - 1), H(z, j, i - 1),
                                         H(n, j, i - 1), H(h, j, i), H(z, j, i), H(n, j, i));
     for (int32_t j = 1; j < ny; j++)
         for (int32_t i = 0; i < nx; i++)
-            QY(qyn, j, i) = face_update(p, dt, QY(qy, j, i), QY(qy, j, i), H(h, j - 1, i), H(z, j - 1, i),
+            QY(qyn, j, i) = face_update(p, dt, QY(qy, j, i), QY(qy, j, i), fabs(QY(qy, j, i)), H(h, j - 1, i), H(z, j - 1, i),
                                         H(n, j - 1, i), H(h, j, i), H(z, j, i), H(n, j, i));
 
     /* Eq. 4 and the clip: h' = max(h + dt div / dx, 0) (kept when h + ... >= 0) */
@@ -642,7 +658,8 @@ static void orc_step_reverse(const orc_params *p, const orc_section *secs, int32
  * (h0, qx0, qy0) at led0 (time, step count, dt), runs n_steps forward storing
  * every state, then sweeps back.  Writes dL/dn to gn (zeroed here) and, if the
  * pointers are given, dL/d(h0, qx0, qy0).  Returns 0, -1 on allocation failure,
- * -3 for theta != 1 (the reverse sweep covers Eq. 3 as printed).
+ * -3 for theta != 1 or vector-norm friction (the reverse sweep covers Eq. 3 as
+ * printed with the face's own |q|).
  */
 int orc_adjoint(const orc_params *p, const orc_section *secs, int32_t nsec, const double *z,
                 const double *n, const double *h0, const double *qx0, const double *qy0,
@@ -650,7 +667,7 @@ int orc_adjoint(const orc_params *p, const orc_section *secs, int32_t nsec, cons
                 int32_t n_gauges, const double *dLdh, double *gn, double *lh0, double *lqx0,
                 double *lqy0)
 {
-    if (p->theta != 1.0) return -3;          /* the reverse sweep covers Eq. 3 as printed */
+    if (p->theta != 1.0 || p->friction != 0) return -3;   /* the reverse sweep covers Eq. 3 as printed */
     int32_t nx = p->nx, ny = p->ny;
     size_t NC = (size_t)nx * ny, NX = (size_t)ny * (nx + 1), NY = (size_t)(ny + 1) * nx;
     size_t per = NC + NX + NY;

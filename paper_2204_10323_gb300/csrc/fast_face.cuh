@@ -44,15 +44,25 @@ __device__ __forceinline__ float rcp_fast(float x)
     return r;
 }
 
-// Eq. 3 for a wet face of flow depth hf: friction from the face's own q, qn in
-// the numerator (q itself unless theta-weighted).  Called with hf <= 0 the
-// result is NaN or garbage, never a trap; face_fast_sel discards it.
-__device__ __forceinline__ float face_wet(float q, float qn, float etaL, float etaR, float hf, float nsum,
+// |q| of a face in the friction term as the vector norm: the face's discharge q
+// and the mean of the four faces of the other axis around it (a, b on the
+// lower-index side, c, d on the other).
+__device__ __forceinline__ float q_norm(float q, float a, float b, float c, float d)
+{
+    const float qo = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(a, b), __fadd_rn(c, d)));
+    return __fsqrt_rn(__fadd_rn(__fmul_rn(q, q), __fmul_rn(qo, qo)));
+}
+
+// Eq. 3 for a wet face of flow depth hf: qmag the |q| of the friction term
+// (the face's own |q| unless the vector norm is asked for), qn the numerator
+// discharge (q itself unless theta-weighted).  Called with hf <= 0 the result
+// is NaN or garbage, never a trap; face_fast_sel discards it.
+__device__ __forceinline__ float face_wet(float qmag, float qn, float etaL, float etaR, float hf, float nsum,
                                           const FastConst &k)
 {
     float r7 = pow_m73(hf);
     float nf = __fmul_rn(0.5f, nsum);
-    float fric = __fmul_rn(__fmul_rn(__fmul_rn(k.gdt, __fmul_rn(nf, nf)), fabsf(q)), r7);
+    float fric = __fmul_rn(__fmul_rn(__fmul_rn(k.gdt, __fmul_rn(nf, nf)), qmag), r7);
     float num = __fsub_rn(qn, __fmul_rn(__fmul_rn(k.a1, hf), __fsub_rn(etaR, etaL)));
     return __fmul_rn(num, rcp_fast(__fadd_rn(1.0f, fric)));
 }
@@ -64,16 +74,17 @@ __device__ __forceinline__ float face_fast(float q, float etaL, float etaR, floa
 {
     float hf = __fsub_rn(fmaxf(etaL, etaR), zmax);
     if (!(hf > k.h_dry)) return 0.0f;
-    return face_wet(q, q, etaL, etaR, hf, nsum, k);
+    return face_wet(fabsf(q), q, etaL, etaR, hf, nsum, k);
 }
 
-// face_fast with the numerator discharge qn given (theta-weighted faces).
-__device__ __forceinline__ float face_fast_qn(float q, float qn, float etaL, float etaR, float zmax, float nsum,
-                                              const FastConst &k)
+// face_fast with the friction magnitude qmag and the numerator discharge qn
+// given (vector-norm friction, theta-weighted faces).
+__device__ __forceinline__ float face_fast_gen(float qmag, float qn, float etaL, float etaR, float zmax, float nsum,
+                                               const FastConst &k)
 {
     float hf = __fsub_rn(fmaxf(etaL, etaR), zmax);
     if (!(hf > k.h_dry)) return 0.0f;
-    return face_wet(q, qn, etaL, etaR, hf, nsum, k);
+    return face_wet(qmag, qn, etaL, etaR, hf, nsum, k);
 }
 
 // The same value as face_fast without a branch: a dry face is evaluated too
@@ -83,16 +94,16 @@ __device__ __forceinline__ float face_fast_sel(float q, float etaL, float etaR, 
                                                const FastConst &k)
 {
     float hf = __fsub_rn(fmaxf(etaL, etaR), zmax);
-    float v = face_wet(q, q, etaL, etaR, hf, nsum, k);
+    float v = face_wet(fabsf(q), q, etaL, etaR, hf, nsum, k);
     return hf > k.h_dry ? v : 0.0f;
 }
 
-// face_fast_sel with the numerator discharge qn given (theta-weighted faces).
-__device__ __forceinline__ float face_fast_sel_qn(float q, float qn, float etaL, float etaR, float zmax, float nsum,
-                                                  const FastConst &k)
+// face_fast_sel with qmag and qn given (vector-norm friction, theta-weighted faces).
+__device__ __forceinline__ float face_fast_sel_gen(float qmag, float qn, float etaL, float etaR, float zmax,
+                                                   float nsum, const FastConst &k)
 {
     float hf = __fsub_rn(fmaxf(etaL, etaR), zmax);
-    float v = face_wet(q, qn, etaL, etaR, hf, nsum, k);
+    float v = face_wet(qmag, qn, etaL, etaR, hf, nsum, k);
     return hf > k.h_dry ? v : 0.0f;
 }
 

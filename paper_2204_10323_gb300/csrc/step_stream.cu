@@ -234,7 +234,7 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
                         const float zl = get(zp, k), zr = get(cz, k), q = get(cqy, k);
-                        set(qys, k, face_fast_sel_qn(q, theta_q(q, get(qyo_p, k), get(qyn, k), K), get(hp, k) + zl,
+                        set(qys, k, face_fast_sel_gen(fabsf(q), theta_q(q, get(qyo_p, k), get(qyn, k), K), get(hp, k) + zl,
                                                      get(ch, k) + zr, fmaxf(zl, zr), get(np_, k) + get(cn, k), K));
                     }
                 } else {
@@ -345,7 +345,7 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
                     const float nl = k == 0 ? nl0 : get(cn, k - 1);
                     const float zr = get(cz, k), q = get(cqx, k);
                     const float qn = theta_q(q, k == 0 ? ql0 : get(cqx, k - 1), k == 3 ? qr3 : get(cqx, k + 1), K);
-                    set(qxw, k, face_fast_sel_qn(q, qn, hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), K));
+                    set(qxw, k, face_fast_sel_gen(fabsf(q), qn, hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), K));
                 }
             } else {
 #pragma unroll
@@ -375,7 +375,7 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
                 if (c == nx) qe = boundary_fast_at(a, step, 1, j, ch.w, cn.w, vout);
                 else if (c < nx) {
                     if constexpr (kTheta)
-                        qe = face_fast_qn(qxE, theta_q(qxE, cqx.w, qxEE, K), ch.w + cz.w, hE + zE, fmaxf(cz.w, zE),
+                        qe = face_fast_gen(fabsf(qxE), theta_q(qxE, cqx.w, qxEE, K), ch.w + cz.w, hE + zE, fmaxf(cz.w, zE),
                                           cn.w + nE, K);
                     else
                         qe = face_fast(qxE, ch.w + cz.w, hE + zE, fmaxf(cz.w, zE), cn.w + nE, K);

@@ -361,6 +361,24 @@ def test_theta_scheme_uniform_and_checkerboard_fluxes(theta):
     np.testing.assert_allclose(o.qx[0, 2:nx - 1], (2 * theta - 1) * a[2:nx - 1], rtol=1e-12, atol=1e-15)
 
 
+@pytest.mark.parametrize("friction", [0, 1])
+def test_friction_norm_closed_form(friction):
+    """Flat water 1 m deep, n = 0.05, dt = 0.1 s, every old x-face carries 0.3 and
+    every y-face 0.4 m^2/s.  No slope term, so a face keeps q / (1 + g dt n^2 |q|):
+    |q| is the face's own component (0.3 or 0.4) by default, and the vector norm
+    sqrt(0.3^2 + 0.4^2) = 0.5 with the orthogonal mean of the four faces around it."""
+    nx, ny = 5, 4
+    p = closed_box(np.zeros((ny, nx)), np.ones((ny, nx)), n=0.05, friction=friction)
+    p.qx0 = np.full((ny, nx + 1), 0.3)
+    p.qy0 = np.full((ny + 1, nx), 0.4)
+    o = oracle.Oracle(p)
+    o.step_dt(0.1)
+    c = 9.81 * 0.1 * 0.05 ** 2
+    mx, my = (0.5, 0.5) if friction else (0.3, 0.4)
+    np.testing.assert_allclose(o.qx[:, 1:nx], 0.3 / (1 + c * mx), rtol=1e-14)
+    np.testing.assert_allclose(o.qy[1:ny, :], 0.4 / (1 + c * my), rtol=1e-14)
+
+
 def test_theta_scheme_oracle_adjoint_is_refused():
     p = closed_box(np.zeros((2, 3)), np.ones((2, 3)), theta=0.8)
     o = oracle.Oracle(p)
