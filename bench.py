@@ -259,6 +259,9 @@ def run_gpu(args):
         dist.init_process_group("nccl")
 
     prob, wname = workload(args.workload)
+    prob.opts.theta = args.theta
+    prob.opts.friction = args.friction
+    variant = args.theta != 1.0 or args.friction != 0
     ncell = prob.nx * prob.ny
     E = prob.opts.epoch_steps
     h0, qx0, qy0 = prob.initial_state(np.float32)
@@ -276,7 +279,7 @@ def run_gpu(args):
     traffic = None
     if args.traffic_bytes:
         traffic = float(args.traffic_bytes)
-    elif args.workload == "c3" and (args.kernel, per_launch) in TRAFFIC_B_PER_CELL:
+    elif args.workload == "c3" and not variant and (args.kernel, per_launch) in TRAFFIC_B_PER_CELL:
         traffic = TRAFFIC_B_PER_CELL[(args.kernel, per_launch)] * ncell
 
     # end to end through the C ABI with host buffers: upload state, K steps, read depth + ledger
@@ -304,6 +307,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wname, "nx": prob.nx, "ny": prob.ny, "kernel": args.kernel,
                        "steps_per_launch": args.k, "epoch_steps": E, "l2": "inputs larger than L2 (5.4 GB state)",
+                       "theta": args.theta, "friction": "vector norm" if args.friction else "own component",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
@@ -312,7 +316,7 @@ def run_gpu(args):
             "ledger": {k: L[k] for k in ("t", "dt", "V_in", "V_out", "V_clip", "volume")}}
     sim.close()
     del sim
-    if args.kernel != "tiled" and not args.no_temporal:
+    if args.kernel != "tiled" and not args.no_temporal and not variant:     # the tiled kernel runs Eq. 3 as printed
         line["temporal_blocking"] = temporal_leg(F, torch, prob, args, local, dist, ncell, peak)
     if not args.no_sweep:
         line["resolution_sweep"] = resolution_sweep(F, torch, prob, args, local, dist, total_ms / steps)
@@ -476,6 +480,8 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-temporal", action="store_true", help="skip the temporal-blocking leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 1/2/4/8 m resolution sweep")
+    ap.add_argument("--theta", type=float, default=1.0, help="face-flux weighting (1 = Eq. 3 as printed)")
+    ap.add_argument("--friction", type=int, default=0, help="1: vector-norm |q| in the friction term")
     ap.add_argument("--ensemble-shape", default="", help="K,warps,rows,steps_per_graph instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -92,7 +92,7 @@ typedef struct {
 
 /* Kernel families for the forward step (FLOOD_F32; FLOOD_F64 always uses REFERENCE). */
 typedef enum {
-    FLOOD_KERNEL_AUTO = 0,
+    FLOOD_KERNEL_AUTO = 0,       /* STREAM; TMA with vector-norm friction (flood_opts.friction = 1) */
     FLOOD_KERNEL_REFERENCE = 1,  /* one thread per cell, IEEE ops in the oracle's order */
     FLOOD_KERNEL_ROWS = 2,       /* one warp per 128-column strip, float4 row streaming */
     FLOOD_KERNEL_TILED = 3,      /* pipeline of K warps per strip, K steps per launch (temporal blocking) */
@@ -122,6 +122,11 @@ typedef struct {
                                     de Almeida et al. 2012, cited in Methods); friction keeps |q| of the
                                     face.  theta != 1: kernels REFERENCE, STREAM, TMA (AUTO) and FP64 only,
                                     no ensembles, no adjoint (FLOOD_ERR_UNSUPPORTED) */
+    int32_t friction;            /* |q| in the friction term of Eq. 3.  0 (default): the face's own discharge
+                                    component (the axis-by-axis integration of Methods).  1: the vector norm
+                                    sqrt(q^2 + qo^2), qo the mean of the four faces of the other axis around
+                                    the face.  1: kernels REFERENCE, STREAM, TMA (AUTO) and FP64 only, no
+                                    ensembles, no adjoint (FLOOD_ERR_UNSUPPORTED); other values FLOOD_ERR_ARG */
 } flood_opts;
 
 typedef struct flood_handle flood_handle;

@@ -51,7 +51,8 @@ class flood_opts(C.Structure):
                 ("dt_const", C.c_double), ("dt_mode", C.c_int32), ("epoch_steps", C.c_int32),
                 ("bc_form", C.c_int32), ("kernel", C.c_int32), ("steps_per_launch", C.c_int32),
                 ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("use_graph", C.c_int32),
-                ("stream", C.c_void_p), ("theta", C.c_double)]
+                ("stream", C.c_void_p), ("theta", C.c_double),
+                ("friction", C.c_int32)]
 
 
 _lib = None
@@ -252,6 +253,7 @@ class Sim:
         o.g, o.h_dry, o.cfl_alpha, o.dt_cap, o.dt_const = po.g, po.h_dry, po.cfl_alpha, po.dt_cap, po.dt_const
         o.dt_mode, o.epoch_steps, o.bc_form = po.dt_mode, po.epoch_steps, po.bc_form
         o.theta = getattr(po, "theta", 1.0)
+        o.friction = getattr(po, "friction", 0)
         o.kernel, o.steps_per_launch = kernel, steps_per_launch
         o.tile_x, o.tile_y = tile
         o.use_graph = int(use_graph)
@@ -425,6 +427,7 @@ class Ensemble:
         o.g, o.h_dry, o.cfl_alpha, o.dt_cap, o.dt_const = po.g, po.h_dry, po.cfl_alpha, po.dt_cap, po.dt_const
         o.dt_mode, o.epoch_steps, o.bc_form = po.dt_mode, po.epoch_steps, po.bc_form
         o.theta = getattr(po, "theta", 1.0)
+        o.friction = getattr(po, "friction", 0)
         o.stream = None if stream is None else C.c_void_p(stream.cuda_stream)
         self._keep = []
         grids = (flood_grid * n)()

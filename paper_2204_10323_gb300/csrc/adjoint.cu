@@ -36,7 +36,7 @@ template <> struct Fwd<double> {
     __device__ Fwd(const Geom &G, double dt_) : g(G.g), dt(dt_), dx(G.dx), hd(G.h_dry) {}
     __device__ double face(double q, double hL, double zL, double nL, double hR, double zR, double nR) const
     {
-        return face_update_ieee<double>(q, q, hL, zL, nL, hR, zR, nR, g, dt, dx, hd);
+        return face_update_ieee<double>(q, fabs(q), hL, zL, nL, hR, zR, nR, g, dt, dx, hd);
     }
     __device__ double hf(double hL, double zL, double hR, double zR) const
     {

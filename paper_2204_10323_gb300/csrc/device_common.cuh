@@ -40,12 +40,13 @@ template <> struct R<double> {
 };
 
 // Eq. 3 at one interior face between cell L (lower index) and R, with the
-// time step in the numerator, |q| the face's own component, and
-// h_f = max(eta_L, eta_R) - max(z_L, z_R); 0 when h_f <= h_dry.  qn is the
-// discharge in the numerator (q itself unless theta-weighted).  Operations
-// in the order of the plain definition, each rounded once (no contraction).
+// time step in the numerator and h_f = max(eta_L, eta_R) - max(z_L, z_R);
+// 0 when h_f <= h_dry.  qn is the discharge in the numerator (q itself unless
+// theta-weighted), qmag the |q| of the friction term (q_norm_ieee).
+// Operations in the order of the plain definition, each rounded once (no
+// contraction).
 template <typename T>
-__device__ __forceinline__ T face_update_ieee(T q, T qn, T hL, T zL, T nL, T hR, T zR, T nR, T g, T dt,
+__device__ __forceinline__ T face_update_ieee(T qn, T qmag, T hL, T zL, T nL, T hR, T zR, T nR, T g, T dt,
                                               T dx, T h_dry)
 {
     using O = R<T>;
@@ -56,8 +57,20 @@ __device__ __forceinline__ T face_update_ieee(T q, T qn, T hL, T zL, T nL, T hR,
     T gdt = O::mul(g, dt);
     T slope_term = O::div(O::mul(O::mul(gdt, hf), O::sub(etaR, etaL)), dx);
     T hf_m73 = O::div(T(1), O::mul(O::mul(hf, hf), O::cbrt(hf)));
-    T friction = O::mul(O::mul(O::mul(O::mul(gdt, nf), nf), O::abs(q)), hf_m73);
+    T friction = O::mul(O::mul(O::mul(O::mul(gdt, nf), nf), qmag), hf_m73);
     return O::div(O::sub(qn, slope_term), O::add(T(1), friction));
+}
+
+// |q| of the friction term of a face: its own |q|, or with vec the vector
+// norm sqrt(q^2 + qo^2), qo = ((a + b) + (c + d)) / 4 the mean of the four
+// faces of the other axis around it (a, b on the lower-index side).
+template <typename T>
+__device__ __forceinline__ T q_norm_ieee(T q, T a, T b, T c, T d, bool vec)
+{
+    using O = R<T>;
+    if (!vec) return O::abs(q);
+    const T qo = O::mul(T(0.25), O::add(O::add(a, b), O::add(c, d)));
+    return O::sqrt(O::add(O::mul(q, q), O::mul(qo, qo)));
 }
 
 // Numerator discharge of a face (qn of face_update_ieee): q itself, or with

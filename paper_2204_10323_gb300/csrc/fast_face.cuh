@@ -44,13 +44,22 @@ __device__ __forceinline__ float rcp_fast(float x)
     return r;
 }
 
+// Square root by the hardware approximation (a few ulp; sqrt(0) = 0 without
+// the special-case path of the IEEE-rounded square root).
+__device__ __forceinline__ float sqrt_fast(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // |q| of a face in the friction term as the vector norm: the face's discharge q
 // and the mean of the four faces of the other axis around it (a, b on the
 // lower-index side, c, d on the other).
 __device__ __forceinline__ float q_norm(float q, float a, float b, float c, float d)
 {
     const float qo = __fmul_rn(0.25f, __fadd_rn(__fadd_rn(a, b), __fadd_rn(c, d)));
-    return __fsqrt_rn(__fadd_rn(__fmul_rn(q, q), __fmul_rn(qo, qo)));
+    return sqrt_fast(__fmaf_rn(q, q, __fmul_rn(qo, qo)));
 }
 
 // Eq. 3 for a wet face of flow depth hf: qmag the |q| of the friction term

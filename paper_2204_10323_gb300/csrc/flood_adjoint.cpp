@@ -337,6 +337,8 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
         return fail(h, FLOOD_ERR_ARG, "bad adjoint arguments");
     if (h->sticky) return fail(h, FLOOD_ERR_STATE, "handle is in an error state; write a new state first");
     if (h->geo.theta != 1.0) return fail(h, FLOOD_ERR_UNSUPPORTED, "the adjoint covers theta = 1 (Eq. 3 as printed)");
+    if (h->geo.friction != 0)
+        return fail(h, FLOOD_ERR_UNSUPPORTED, "the adjoint covers the face's own |q| in the friction term");
     const int64_t nc = (int64_t)h->geo.nx * h->geo.ny;
     for (int g = 0; g < n_gauges; g++)
         if (gauge_cells[g] < 0 || gauge_cells[g] >= nc) return fail(h, FLOOD_ERR_ARG, "gauge cell out of range");

@@ -189,6 +189,8 @@ extern "C" flood_status flood_ensemble_create(int32_t n, const flood_grid *grids
     else flood_default_opts(&o);
     o.kernel = FLOOD_KERNEL_STREAM;
     if (o.theta != 1.0) return efail(nullptr, FLOOD_ERR_UNSUPPORTED, "ensembles run theta = 1 (Eq. 3 as printed)");
+    if (o.friction != 0)
+        return efail(nullptr, FLOOD_ERR_UNSUPPORTED, "ensembles run the face's own |q| in the friction term");
     o.use_graph = 0;
     flood_ensemble *e = new flood_ensemble();
     e->E = o.epoch_steps;

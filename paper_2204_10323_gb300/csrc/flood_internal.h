@@ -46,6 +46,7 @@ struct Geom {
     double dx, g, h_dry;
     float dx_f, h_dry_f;          // dx and h_dry rounded to FP32 once (the fast kernels' boundary faces)
     double theta;                 // face-flux weighting (1 = Eq. 3 as printed)
+    int friction;                 // |q| of the friction term: 0 the face's own, 1 the vector norm
     double cfl_alpha, dt_cap, dt_const;
     int dt_mode, epoch_steps;
 };

@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(BX *BY) step_reference_kernel(const StepArgs<T
     const bool in = i < G.nx && j < G.ny;
     const T dt = T(a.ctrl->dt), dx = T(G.dx), g = T(G.g), hd = T(G.h_dry);
     const bool wt = G.theta != 1.0;                   // theta-weighted numerator discharges
+    const bool vec = G.friction != 0;                 // vector-norm |q| in the friction term
     const T th = T(G.theta), w = T(0.5 * (1.0 - G.theta));
     double vout = 0.0, vclip = 0.0, hmax = 0.0;
     T hn = T(0);
@@ -47,19 +48,29 @@ __global__ void __launch_bounds__(BX *BY) step_reference_kernel(const StepArgs<T
         const size_t c = (size_t)j * P + i;
         const T hC = a.h[c], zC = a.z[c], nC = a.n[c];
         T qW, qE, qS, qN;
-        // (interior x-faces i in 1..nx-1 have neighbours i-1 >= 0 and i+1 <= nx in the row,
-        // interior y-faces j in 1..ny-1 neighbours j-1 >= 0 and j+1 <= ny)
+        // (interior x-faces i in 1..nx-1 have neighbours i-1 >= 0 and i+1 <= nx in the row and
+        // y-faces of columns i-1, i in rows j, j+1 <= ny; interior y-faces j in 1..ny-1 neighbours
+        // j-1 >= 0 and j+1 <= ny and x-faces of columns i, i+1 <= nx in rows j-1, j)
+        const T *qx = a.qx, *qy = a.qy;
         if (i == 0) qW = boundary_face(a, 0, j, hC, nC, vout);
-        else qW = face_update_ieee<T>(a.qx[c], wt ? theta_q_ieee<T>(a.qx[c], a.qx[c - 1], a.qx[c + 1], th, w, true) : a.qx[c],
+        else qW = face_update_ieee<T>(wt ? theta_q_ieee<T>(qx[c], qx[c - 1], qx[c + 1], th, w, true) : qx[c],
+                                      vec ? q_norm_ieee<T>(qx[c], qy[c - 1], qy[c], qy[c + P - 1], qy[c + P], true)
+                                          : R<T>::abs(qx[c]),
                                       a.h[c - 1], a.z[c - 1], a.n[c - 1], hC, zC, nC, g, dt, dx, hd);
         if (i == G.nx - 1) qE = boundary_face(a, 1, j, hC, nC, vout);
-        else qE = face_update_ieee<T>(a.qx[c + 1], wt ? theta_q_ieee<T>(a.qx[c + 1], a.qx[c], a.qx[c + 2], th, w, true) : a.qx[c + 1],
+        else qE = face_update_ieee<T>(wt ? theta_q_ieee<T>(qx[c + 1], qx[c], qx[c + 2], th, w, true) : qx[c + 1],
+                                      vec ? q_norm_ieee<T>(qx[c + 1], qy[c], qy[c + 1], qy[c + P], qy[c + P + 1], true)
+                                          : R<T>::abs(qx[c + 1]),
                                       hC, zC, nC, a.h[c + 1], a.z[c + 1], a.n[c + 1], g, dt, dx, hd);
         if (j == 0) qS = boundary_face(a, 2, i, hC, nC, vout);
-        else qS = face_update_ieee<T>(a.qy[c], wt ? theta_q_ieee<T>(a.qy[c], a.qy[c - P], a.qy[c + P], th, w, true) : a.qy[c],
+        else qS = face_update_ieee<T>(wt ? theta_q_ieee<T>(qy[c], qy[c - P], qy[c + P], th, w, true) : qy[c],
+                                      vec ? q_norm_ieee<T>(qy[c], qx[c - P], qx[c - P + 1], qx[c], qx[c + 1], true)
+                                          : R<T>::abs(qy[c]),
                                       a.h[c - P], a.z[c - P], a.n[c - P], hC, zC, nC, g, dt, dx, hd);
         if (j == G.ny - 1) qN = boundary_face(a, 3, i, hC, nC, vout);
-        else qN = face_update_ieee<T>(a.qy[c + P], wt ? theta_q_ieee<T>(a.qy[c + P], a.qy[c], a.qy[c + 2 * P], th, w, true) : a.qy[c + P],
+        else qN = face_update_ieee<T>(wt ? theta_q_ieee<T>(qy[c + P], qy[c], qy[c + 2 * P], th, w, true) : qy[c + P],
+                                      vec ? q_norm_ieee<T>(qy[c + P], qx[c], qx[c + 1], qx[c + P], qx[c + P + 1], true)
+                                          : R<T>::abs(qy[c + P]),
                                       hC, zC, nC, a.h[c + P], a.z[c + P], a.n[c + P], g, dt, dx, hd);
         // Eq. 4 with the new fluxes, then the depth clip
         T dv = O::add(O::sub(qW, qE), O::sub(qS, qN));

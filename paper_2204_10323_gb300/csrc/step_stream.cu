@@ -90,12 +90,18 @@ __device__ __forceinline__ void set(float4 &v, int k, float x)
 // kTheta: theta-weighted numerator discharges (FastConst theta, w): an x-face
 // takes its row neighbours from the lane, the neighbouring lanes and the
 // staged halo columns, a y-face the previous row's old qy (kept in registers)
-// and the next row's (one global load per row).
-template <bool kTensor, bool kTheta = false>
+// and the next row's (read from the ring one row ahead).
+// kMode bit 0: kTheta.  Bit 1: vector-norm |q| in the friction term: an x-face
+// takes the old qy of its two cells' south faces (this row, staged) and north
+// faces (the next row's, read one row ahead as for kTheta), a y-face the old qx
+// of its two cells' west and east faces (this row and the previous row's, kept
+// in registers).
+template <bool kTensor, int kMode = 0>
 __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int step, const int want_hmax, const int bx,
                                             const int by, const int rows, unsigned char *smem_raw, double *red,
                                             uint32_t &ring_base, const bool fresh, const TmaMaps *maps = nullptr)
 {
+    constexpr bool kTheta = (kMode & 1) != 0, kVec = (kMode & 2) != 0;
     constexpr int R = kTensor ? kRowsT : 1;            // rows per stage
     constexpr int NS = kTensor ? kStagesT : kDepth;    // stages in flight
     const Geom &G = a.geo;
@@ -169,6 +175,8 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
     float4 hp = make_float4(0, 0, 0, 0), zp = hp, np_ = hp;
     float4 qxw_p = hp, qys_p = hp;
     float4 qyo_p = hp;                            // old qy of the previous row (theta weighting)
+    float4 qxo_p = hp;                            // old qx of the previous row (vector-norm friction)
+    float qxEo_p = 0.0f;                          // lane 31: the previous row's old qx at x0 + 128
     float qxe_p3 = 0.0f;
     if (active) {
         for (int j = jstart; j <= y1; j++) {
@@ -176,6 +184,7 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
             float4 ch = make_float4(0, 0, 0, 0), cz = ch, cn = ch, cqx = ch, cqy = ch;
             float hW = 0.f, zW = 0.f, nW = 0.f, hE = 0.f, zE = 0.f, nE = 0.f, qxE = 0.f;
             float qxW = 0.f, qxEE = 0.f;              // old qx at x0-1 and x0+129 (theta weighting)
+            float qyW = 0.f, qyE = 0.f;               // old qy at x0-1 and x0+128 (vector-norm friction)
             if (j < ny) {
                 const int st = idx / R, sub = idx - st * R;
                 const uint32_t g = ring_base + (uint32_t)st;
@@ -199,6 +208,7 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
                     zW = row_at(s, 1, sub)[3];
                     nW = row_at(s, 2, sub)[3];
                     if constexpr (kTheta) qxW = row_at(s, 3, sub)[3];
+                    if constexpr (kVec) qyW = row_at(s, 4, sub)[3];
                 }
                 if (lane == 31) {
                     hE = row_at(s, 0, sub)[132];
@@ -206,6 +216,7 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
                     nE = row_at(s, 2, sub)[132];
                     qxE = row_at(s, 3, sub)[132];
                     if constexpr (kTheta) qxEE = row_at(s, 3, sub)[133];
+                    if constexpr (kVec) qyE = row_at(s, 4, sub)[132];
                 }
                 if (sub == R - 1) {           // stage read completely: refill it
                     __syncwarp();
@@ -221,21 +232,70 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
                 zp = cz;
                 np_ = cn;
                 qyo_p = cqy;
+                qxo_p = cqx;
+                qxEo_p = qxE;
                 continue;
+            }
+            // old qy of row j + 1 <= ny (the north faces of row j), with lane 0's column
+            // x0 - 1 and lane 31's x0 + 128 for the vector norm: a staged row is read from
+            // the ring one row ahead (waiting for its copies if they have not landed), the
+            // rows beyond the staged ones (the chunk's last, the grid's north edge) from
+            // global memory
+            float4 qyn = make_float4(0, 0, 0, 0);
+            float qynW = 0.0f, qynE = 0.0f;
+            if constexpr (kTheta || kVec) {
+                const int jn = j + 1;
+                if (jn <= jlast) {
+                    const int idn = jn - jstart;
+                    const int st = idn / R, sub = idn - st * R;
+                    const uint32_t g = ring_base + (uint32_t)st;
+                    const uint32_t s = g % NS;
+                    if (sub == 0) {
+                        bool ok = mbar_wait_bounded(&ring.bar[s], (g / NS) & 1u, kBudgetNs);
+                        if (__any_sync(0xffffffffu, !ok)) {
+                            abort = true;
+                            break;
+                        }
+                        consumed = st + 1;
+                    }
+                    qyn = lds4(row_at(s, 4, sub) + 4 + 4 * lane);
+                    if constexpr (kVec) {
+                        if (lane == 0) qynW = row_at(s, 4, sub)[3];
+                        if (lane == 31) qynE = row_at(s, 4, sub)[132];
+                    }
+                } else if (jn <= ny && (kTheta || j < y1)) {
+                    const float *row = a.qy + (size_t)jn * P;
+                    if (c0 < P) qyn = __ldg(reinterpret_cast<const float4 *>(row + c0));
+                    if constexpr (kVec) {
+                        if (lane == 0 && x0 > 0) qynW = __ldg(row + x0 - 1);
+                        if (lane == 31 && x0 + 128 < nx) qynE = __ldg(row + x0 + 128);
+                    }
+                }
             }
             // ---- new south faces of row j
             // (interior rows branch-free; the boundary rows, uniform over the warp, take Eq. 5-6)
             float4 qys;
             if (j > 0 && j < ny) {
-                if constexpr (kTheta) {
-                    // old qy of the next row's south faces (row j + 1 <= ny of the qy array)
-                    float4 qyn = make_float4(0, 0, 0, 0);
-                    if (c0 < P) qyn = __ldg(reinterpret_cast<const float4 *>(a.qy + (size_t)(j + 1) * P + c0));
+                if constexpr (kTheta || kVec) {
+                    // old qx of rows j - 1 and j right of the lane's last column
+                    float xs4 = 0.0f, xn4 = 0.0f;
+                    if constexpr (kVec) {
+                        xs4 = __shfl_down_sync(0xffffffffu, qxo_p.x, 1);
+                        xn4 = __shfl_down_sync(0xffffffffu, cqx.x, 1);
+                        if (lane == 31) {
+                            xs4 = qxEo_p;
+                            xn4 = qxE;
+                        }
+                    }
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
                         const float zl = get(zp, k), zr = get(cz, k), q = get(cqy, k);
-                        set(qys, k, face_fast_sel_gen(fabsf(q), theta_q(q, get(qyo_p, k), get(qyn, k), K), get(hp, k) + zl,
-                                                     get(ch, k) + zr, fmaxf(zl, zr), get(np_, k) + get(cn, k), K));
+                        const float qn = kTheta ? theta_q(q, get(qyo_p, k), get(qyn, k), K) : q;
+                        const float qm = kVec ? q_norm(q, get(qxo_p, k), k < 3 ? get(qxo_p, k + 1) : xs4, get(cqx, k),
+                                                       k < 3 ? get(cqx, k + 1) : xn4)
+                                              : fabsf(q);
+                        set(qys, k, face_fast_sel_gen(qm, qn, get(hp, k) + zl, get(ch, k) + zr, fmaxf(zl, zr),
+                                                      get(np_, k) + get(cn, k), K));
                     }
                 } else {
 #pragma unroll
@@ -332,20 +392,37 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
                 nl0 = nW;
             }
             float4 qxw;
-            if constexpr (kTheta) {
+            if constexpr (kTheta || kVec) {
                 // old qx of the faces left of the lane's first and right of its last column
-                float ql0 = __shfl_up_sync(0xffffffffu, cqx.w, 1);
-                float qr3 = __shfl_down_sync(0xffffffffu, cqx.x, 1);
-                if (lane == 0) ql0 = qxW;
-                if (lane == 31) qr3 = qxE;
+                float ql0 = 0.0f, qr3 = 0.0f;
+                if constexpr (kTheta) {
+                    ql0 = __shfl_up_sync(0xffffffffu, cqx.w, 1);
+                    qr3 = __shfl_down_sync(0xffffffffu, cqx.x, 1);
+                    if (lane == 0) ql0 = qxW;
+                    if (lane == 31) qr3 = qxE;
+                }
+                // old qy of rows j and j + 1 left of the lane's first column
+                float ys0 = 0.0f, yn0 = 0.0f;
+                if constexpr (kVec) {
+                    ys0 = __shfl_up_sync(0xffffffffu, cqy.w, 1);
+                    yn0 = __shfl_up_sync(0xffffffffu, qyn.w, 1);
+                    if (lane == 0) {
+                        ys0 = qyW;
+                        yn0 = qynW;
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     const float hl = k == 0 ? hl0 : get(ch, k - 1);
                     const float zl = k == 0 ? zl0 : get(cz, k - 1);
                     const float nl = k == 0 ? nl0 : get(cn, k - 1);
                     const float zr = get(cz, k), q = get(cqx, k);
-                    const float qn = theta_q(q, k == 0 ? ql0 : get(cqx, k - 1), k == 3 ? qr3 : get(cqx, k + 1), K);
-                    set(qxw, k, face_fast_sel_gen(fabsf(q), qn, hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), K));
+                    const float qn = kTheta ? theta_q(q, k == 0 ? ql0 : get(cqx, k - 1), k == 3 ? qr3 : get(cqx, k + 1), K)
+                                            : q;
+                    const float qm = kVec ? q_norm(q, k == 0 ? ys0 : get(cqy, k - 1), get(cqy, k),
+                                                   k == 0 ? yn0 : get(qyn, k - 1), get(qyn, k))
+                                          : fabsf(q);
+                    set(qxw, k, face_fast_sel_gen(qm, qn, hl + zl, get(ch, k) + zr, fmaxf(zl, zr), nl + get(cn, k), K));
                 }
             } else {
 #pragma unroll
@@ -374,10 +451,11 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
                 qe = 0.0f;
                 if (c == nx) qe = boundary_fast_at(a, step, 1, j, ch.w, cn.w, vout);
                 else if (c < nx) {
-                    if constexpr (kTheta)
-                        qe = face_fast_gen(fabsf(qxE), theta_q(qxE, cqx.w, qxEE, K), ch.w + cz.w, hE + zE, fmaxf(cz.w, zE),
-                                          cn.w + nE, K);
-                    else
+                    if constexpr (kTheta || kVec) {
+                        const float qn = kTheta ? theta_q(qxE, cqx.w, qxEE, K) : qxE;
+                        const float qm = kVec ? q_norm(qxE, cqy.w, qyE, qyn.w, qynE) : fabsf(qxE);
+                        qe = face_fast_gen(qm, qn, ch.w + cz.w, hE + zE, fmaxf(cz.w, zE), cn.w + nE, K);
+                    } else
                         qe = face_fast(qxE, ch.w + cz.w, hE + zE, fmaxf(cz.w, zE), cn.w + nE, K);
                 }
             }
@@ -385,6 +463,8 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
             zp = cz;
             np_ = cn;
             qyo_p = cqy;
+            qxo_p = cqx;
+            qxEo_p = qxE;
             qxw_p = qxw;
             qxe_p3 = qe;
             qys_p = qys;
@@ -422,17 +502,17 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
     return abort;
 }
 
-template <bool kTheta>
+template <int kMode>
 __global__ void __launch_bounds__(kMaxWarps * 32, 5) step_stream_kernel(const StepArgs<float> a, const int rows)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     uint32_t ring_base = 0;
-    stream_body<false, kTheta>(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, smem_raw, red, ring_base, true);
+    stream_body<false, kMode>(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, smem_raw, red, ring_base, true);
 }
 
 // The same step with every warp's rows staged as 2D tiles by tensor copies.
-template <bool kTheta>
+template <int kMode>
 __global__ void __launch_bounds__(kMaxWarps * 32, 4)
     step_tma_kernel(const StepArgs<float> a, const int rows, const __grid_constant__ TmaMaps maps)
 {
@@ -440,7 +520,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
     __shared__ double red[32];
     unsigned char *base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);   // 128-byte aligned rings
     uint32_t ring_base = 0;
-    stream_body<true, kTheta>(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, base, red, ring_base, true,
+    stream_body<true, kMode>(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, base, red, ring_base, true,
                               &maps);
 }
 
@@ -468,17 +548,20 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 5)
     stream_body<false>(a, step, want_hmax, local % nbx, local / nbx, rows, smem_raw, red, ring_base, true);
 }
 
+// Variant of the stream/TMA kernels for a grid's options: bit 0 theta
+// weighting, bit 1 vector-norm friction.
+int kernel_mode(const Geom &g) { return (g.theta != 1.0 ? 1 : 0) | (g.friction != 0 ? 2 : 0); }
+
 cudaError_t configure(int warps)
 {
     static bool configured = false;
     if (configured) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(step_stream_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(WarpRing) * kMaxWarps));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(step_stream_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(WarpRing) * kMaxWarps));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(step_stream_ensemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    for (auto k : {step_stream_kernel<0>, step_stream_kernel<1>, step_stream_kernel<2>, step_stream_kernel<3>}) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(WarpRing) * kMaxWarps));
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaFuncSetAttribute(step_stream_ensemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(WarpRing) * kMaxWarps));
     if (e != cudaSuccess) return e;
     configured = true;
@@ -524,8 +607,13 @@ cudaError_t launch_step_stream(const StepArgs<float> &a, cudaStream_t st)
     if (e != cudaSuccess) return e;
     const int strips = (a.geo.nx + 127) / 128;
     dim3 grid((strips + warps - 1) / warps, (a.geo.ny + rows - 1) / rows);
-    if (a.geo.theta != 1.0) step_stream_kernel<true><<<grid, warps * 32, sizeof(WarpRing) * warps, st>>>(a, rows);
-    else step_stream_kernel<false><<<grid, warps * 32, sizeof(WarpRing) * warps, st>>>(a, rows);
+    const size_t smem = sizeof(WarpRing) * warps;
+    switch (kernel_mode(a.geo)) {
+    case 0: step_stream_kernel<0><<<grid, warps * 32, smem, st>>>(a, rows); break;
+    case 1: step_stream_kernel<1><<<grid, warps * 32, smem, st>>>(a, rows); break;
+    case 2: step_stream_kernel<2><<<grid, warps * 32, smem, st>>>(a, rows); break;
+    default: step_stream_kernel<3><<<grid, warps * 32, smem, st>>>(a, rows); break;
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.gauge_out) return launch_gauges<float>(a.geo, a.h_out, a.gauge_cells, a.n_gauges, a.gauge_out, st);
@@ -575,7 +663,7 @@ cudaError_t launch_step_tma(const StepArgs<float> &a, cudaStream_t st)
     const size_t smem = sizeof(WarpRingT) * warps + 128;
     static bool configured = false;
     if (!configured) {
-        for (auto k : {step_tma_kernel<false>, step_tma_kernel<true>}) {
+        for (auto k : {step_tma_kernel<0>, step_tma_kernel<1>, step_tma_kernel<2>, step_tma_kernel<3>}) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)(sizeof(WarpRingT) * kMaxWarps + 128));
             if (e != cudaSuccess) return e;
@@ -591,8 +679,12 @@ cudaError_t launch_step_tma(const StepArgs<float> &a, cudaStream_t st)
     }
     const int strips = (a.geo.nx + 127) / 128;
     dim3 grid((strips + warps - 1) / warps, (ny + rows - 1) / rows);
-    if (a.geo.theta != 1.0) step_tma_kernel<true><<<grid, warps * 32, smem, st>>>(a, rows, maps);
-    else step_tma_kernel<false><<<grid, warps * 32, smem, st>>>(a, rows, maps);
+    switch (kernel_mode(a.geo)) {
+    case 0: step_tma_kernel<0><<<grid, warps * 32, smem, st>>>(a, rows, maps); break;
+    case 1: step_tma_kernel<1><<<grid, warps * 32, smem, st>>>(a, rows, maps); break;
+    case 2: step_tma_kernel<2><<<grid, warps * 32, smem, st>>>(a, rows, maps); break;
+    default: step_tma_kernel<3><<<grid, warps * 32, smem, st>>>(a, rows, maps); break;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.gauge_out) return launch_gauges<float>(a.geo, a.h_out, a.gauge_cells, a.n_gauges, a.gauge_out, st);

@@ -164,6 +164,21 @@ def test_coarsen_rejects_bad_arguments():
     assert "NULL" in F.flood_last_error(None)
 
 
+def test_create_rejects_bad_friction_and_unsupported_kernels():
+    import paper_2204_10323_gb300 as F
+    for bad in (-1, 2, 7):
+        o = F.default_opts()
+        o.friction = bad
+        st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
+        assert st == F.ERR_ARG and "friction" in F.flood_last_error(None)
+    for kernel in (F.KERNEL_ROWS, F.KERNEL_TILED):
+        o = F.default_opts()
+        o.friction = 1
+        o.kernel = kernel
+        st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
+        assert st == F.ERR_UNSUPPORTED and "friction" in F.flood_last_error(None)
+
+
 def test_create_rejects_theta_out_of_range_and_unsupported_kernels():
     import paper_2204_10323_gb300 as F
     for bad in (0.0, -0.5, 1.5, float("nan")):

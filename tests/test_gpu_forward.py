@@ -317,6 +317,97 @@ def test_theta_adjoint_and_ensemble_are_refused():
     assert e.value.status == Fm.ERR_UNSUPPORTED
 
 
+# ---------------------------------------------------------------- vector-norm friction
+def with_friction(p, friction, theta=1.0):
+    p.opts.friction = friction
+    p.opts.theta = theta
+    return p
+
+
+def test_vector_friction_changes_the_solution():
+    # the parity cases below see the term: on these inputs the two readings of
+    # |q| differ by far more than the FP32 tolerance
+    a = oracle.Oracle(inputs.random_small(257, 129, 6))
+    b = oracle.Oracle(with_friction(inputs.random_small(257, 129, 6), 1))
+    a.run(100)
+    b.run(100)
+    assert np.abs(a.h - b.h).max() > 30 * TOL32_H
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.8])
+@pytest.mark.parametrize("shape,seed", [((33, 17), 0), ((130, 70), 2), ((1, 9), 3), ((9, 1), 4)])
+def test_vector_friction_fp64_matches_oracle(theta, shape, seed):
+    p = with_friction(inputs.random_small(shape[0], shape[1], seed), 1, theta)
+    o, V0, h, qx, qy, L = run_pair(p, 120, F().F64)
+    assert np.abs(h - o.h).max() < TOL64
+    assert np.abs(qx - o.qx).max() < TOL64
+    assert np.abs(qy - o.qy).max() < TOL64
+    check_ledger(o, L, 1e-12)
+
+
+def test_vector_friction_fp64_channel_1000_steps():
+    p = with_friction(inputs.c1_tilted_channel(), 1)
+    o, V0, h, qx, qy, L = run_pair(p, 1000, F().F64)
+    assert np.abs(h - o.h).max() < TOL64
+    check_ledger(o, L, 1e-12)
+
+
+@pytest.mark.parametrize("kernel", [1, 4, 5])
+@pytest.mark.parametrize("theta", [1.0, 0.8])
+@pytest.mark.parametrize("shape,seed", [((130, 70), 2), ((257, 129), 6), ((129, 33), 9)])
+def test_vector_friction_fp32_matches_oracle(kernel, theta, shape, seed):
+    p = with_friction(inputs.random_small(shape[0], shape[1], seed), 1, theta)
+    o, V0, h, qx, qy, L = run_pair(p, 100, F().F32, kernel=kernel)
+    assert np.abs(h - o.h).max() < TOL32_H
+    assert np.abs(qx - o.qx).max() < 10 * TOL32_H
+    assert np.abs(qy - o.qy).max() < 10 * TOL32_H
+    check_ledger(o, L, TOL32_MASS)
+
+
+@pytest.mark.parametrize("kernel", [4, 5])
+def test_vector_friction_fp32_channel_1000_steps(kernel):
+    p = with_friction(inputs.c1_tilted_channel(), 1)
+    o, V0, h, qx, qy, L = run_pair(p, 1000, F().F32, kernel=kernel)
+    assert np.abs(h - o.h).max() < TOL32_H
+    assert abs(L["volume"] - o.volume()) <= TOL32_MASS * o.volume()
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.75])
+@pytest.mark.parametrize("tile", [(0, 0), (2, 9), (1, 3)])
+def test_vector_friction_tma_tiles_equal_row_staging_bitwise(theta, tile):
+    Fm = F()
+    p = as_f32_problem(with_friction(inputs.random_small(257, 129, 6), 1, theta))
+    a = Fm.Sim(p, kernel=Fm.KERNEL_STREAM, tile=tile)
+    b = Fm.Sim(p, kernel=Fm.KERNEL_TMA, tile=tile)
+    a.step(37)
+    b.step(37)
+    for f in (Fm.FIELD_H, Fm.FIELD_QX, Fm.FIELD_QY):
+        assert np.array_equal(a.read(f), b.read(f)), f
+
+
+def test_vector_friction_auto_runs_the_tensor_tile_kernel():
+    Fm = F()
+    p = as_f32_problem(with_friction(inputs.random_small(257, 129, 6), 1))
+    a = Fm.Sim(p, kernel=Fm.KERNEL_AUTO)
+    b = Fm.Sim(p, kernel=Fm.KERNEL_TMA)
+    a.step(21)
+    b.step(21)
+    for f in (Fm.FIELD_H, Fm.FIELD_QX, Fm.FIELD_QY):
+        assert np.array_equal(a.read(f), b.read(f)), f
+
+
+def test_vector_friction_adjoint_and_ensemble_are_refused():
+    Fm = F()
+    p = with_friction(inputs.random_small(20, 12, 2), 1)
+    s = Fm.Sim(p, precision=Fm.F64)
+    with pytest.raises(Fm.FloodError) as e:
+        s.adjoint(4, np.array([[3, 3]]), np.ones((4, 1)))
+    assert e.value.status == Fm.ERR_UNSUPPORTED
+    with pytest.raises(Fm.FloodError) as e:
+        Fm.Ensemble([p])
+    assert e.value.status == Fm.ERR_UNSUPPORTED
+
+
 # ---------------------------------------------------------------- coarsening
 def block_mean(a, f):
     """Mean over f x f blocks (partial blocks at the far edges over their cells), in float64."""

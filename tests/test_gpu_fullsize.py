@@ -65,6 +65,25 @@ def test_c2_full_grid_matches_oracle(wet, steps):
     s.close()
 
 
+@pytest.mark.parametrize("kernel", [4, 5])
+def test_c2_full_grid_vector_friction_matches_oracle(kernel):
+    Fm = F()
+    p = inputs.c2_fractal()
+    p.h0 = inputs.wet_start(p.z, p.dx, 0.3)
+    p.opts.friction = 1
+    q = as_f32(p)
+    o = oracle.Oracle(q)
+    o.run(100)
+    s = Fm.Sim(q, precision=Fm.F32, kernel=kernel)
+    s.step(100)
+    h, qx, qy = s.state()
+    assert np.abs(h.astype(np.float64) - o.h).max() < TOL_SHORT
+    assert np.abs(qx.astype(np.float64) - o.qx).max() < 10 * TOL_SHORT
+    assert np.abs(qy.astype(np.float64) - o.qy).max() < 10 * TOL_SHORT
+    assert abs(s.ledger()["volume"] - o.volume()) <= 1e-5 * o.volume()
+    s.close()
+
+
 # ---------------------------------------------------------------- 16384^2, sampled cells
 @pytest.fixture(scope="module")
 def c3():
