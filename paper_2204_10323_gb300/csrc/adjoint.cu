@@ -20,6 +20,8 @@
 // The clip mask is recomputed with the forward kernels' own arithmetic (IEEE
 // order for FP64, the fast FP32 face for FP32), so the clip and wet/dry
 // decisions are exactly the forward's.
+#include <algorithm>
+
 #include "fast_face.cuh"
 
 namespace flood {
@@ -172,7 +174,7 @@ constexpr int kTileGauges = 32;
 template <> struct TileRows<double> { static constexpr int v = 8; };
 
 template <typename T>
-__global__ void __launch_bounds__(BX * TileRows<T>::v) adj_step_kernel(const AdjArgs<T> A)
+__global__ void __launch_bounds__(BX * TileRows<T>::v) adj_step_kernel(const AdjArgs<T> A, const int nbx)
 {
     constexpr int BYT = TileRows<T>::v;
     constexpr int NT = BX * BYT;
@@ -191,7 +193,8 @@ __global__ void __launch_bounds__(BX * TileRows<T>::v) adj_step_kernel(const Adj
     const Fwd<T> F(G, dtd);
     const T dt = T(dtd), dx = T(G.dx), g = T(G.g), hd = T(G.h_dry), dtdx = dt / dx;
     const int tid = threadIdx.y * BX + threadIdx.x;
-    const int I0 = blockIdx.x * BX, J0 = blockIdx.y * BYT;
+    // one-dimensional grid (grids taller than 65535 tiles): tile (bx, by) of nbx columns of tiles
+    const int I0 = (int)(blockIdx.x % (unsigned)nbx) * BX, J0 = (int)(blockIdx.x / (unsigned)nbx) * BYT;
 
     // 0. stage cells and old face fluxes (zeros outside the domain)
     for (int t = tid; t < (BYT + 4) * (BX + 4); t += NT) {
@@ -457,10 +460,11 @@ __global__ void adj_inflow_kernel(const AdjArgs<T> A)
 template <typename T>
 __global__ void gn_out_kernel(Geom G, const double *gn, T *dst)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-    if (i >= G.nx || j >= G.ny) return;
-    const size_t c = (size_t)j * G.pitch + i;
-    dst[c] = T(gn[c]);
+    const size_t N = (size_t)G.nx * G.ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
+        const size_t c = (k / G.nx) * G.pitch + k % G.nx;
+        dst[c] = T(gn[c]);
+    }
 }
 
 }  // namespace
@@ -468,8 +472,9 @@ __global__ void gn_out_kernel(Geom G, const double *gn, T *dst)
 template <typename T>
 cudaError_t launch_gn_out(const Geom &g, const double *gn, T *dst, cudaStream_t st)
 {
-    dim3 grid((g.nx + 255) / 256, g.ny);
-    gn_out_kernel<T><<<grid, 256, 0, st>>>(g, gn, dst);
+    const size_t N = (size_t)g.nx * g.ny;
+    const int blocks = (int)std::min<size_t>((N + 255) / 256, 152 * 16);
+    gn_out_kernel<T><<<blocks, 256, 0, st>>>(g, gn, dst);
     return cudaGetLastError();
 }
 
@@ -481,8 +486,8 @@ cudaError_t launch_adjoint_step(const AdjArgs<T> &A, cudaStream_t st)
 {
     constexpr int BYT = TileRows<T>::v;
     dim3 block(BX, BYT);
-    dim3 grid((A.fwd.geo.nx + BX - 1) / BX, (A.fwd.geo.ny + BYT - 1) / BYT);
-    adj_step_kernel<T><<<grid, block, 0, st>>>(A);
+    const int nbx = (A.fwd.geo.nx + BX - 1) / BX, nby = (A.fwd.geo.ny + BYT - 1) / BYT;
+    adj_step_kernel<T><<<(unsigned)((int64_t)nbx * nby), block, 0, st>>>(A, nbx);
     if (A.fwd.n_inflow_sec > 0) adj_inflow_kernel<T><<<A.fwd.n_inflow_sec, 256, 0, st>>>(A);
     return cudaGetLastError();
 }

@@ -173,30 +173,64 @@ __global__ void inflow_batched_kernel(const EpochArgs<T> *tab, const int2 *tasks
                    A.inflow_Q, A.inflow_W, blockIdx.x, t.y, red);
 }
 
+// Rows over blocks, columns over threads; the maximum is exact in the state's
+// own precision, and a NaN, once seen, is kept.
 template <typename T>
 __global__ void hmax_kernel(Geom G, const T *h, Ctrl *ctrl)
 {
     __shared__ double red[32];
-    double m = 0.0;
-    const size_t N = (size_t)G.nx * G.ny;
-    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
-        size_t j = c / G.nx, i = c % G.nx;
-        double v = (double)h[j * G.pitch + i];
-        m = (v > m || v != v) ? v : m;
+    T m = T(0);
+    for (int j = blockIdx.x; j < G.ny; j += gridDim.x) {
+        const T *row = h + (size_t)j * G.pitch;
+        for (int i = threadIdx.x; i < G.nx; i += blockDim.x) {
+            const T v = row[i];
+            m = (v > m || v != v) ? v : m;
+        }
     }
-    m = block_reduce<true>(m, red);
-    if (threadIdx.x == 0) atomic_max_nonneg(&ctrl->hmax_bits, m);
+    const double bm = block_reduce<true>((double)m, red);
+    if (threadIdx.x == 0) atomic_max_nonneg(&ctrl->hmax_bits, bm);
 }
+
+// Sum of a thread's share of the depths: FP64 state in double; FP32 state as
+// an unevaluated float pair (s, c) by Knuth's branch-free two-sum, each
+// addition's rounding error carried in c, so the pair holds the exact sum to
+// about n u^2 of the summands (n per thread, u = 2^-24) and the FP64 pipe is
+// left out of the per-element work.
+template <typename T>
+struct ThreadSum;
+
+template <>
+struct ThreadSum<double> {
+    double s = 0.0;
+    __device__ void add(double x) { s += x; }
+    __device__ double value() const { return s; }
+};
+
+template <>
+struct ThreadSum<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ void add(float x)
+    {
+        const float t = __fadd_rn(s, x);
+        const float bp = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+        c = __fadd_rn(c, e);
+        s = t;
+    }
+    __device__ double value() const { return (double)s + (double)c; }
+};
 
 // Pass 1: block b sums rows b, b + nb, ... (fixed order for a fixed launch shape).
 template <typename T>
 __global__ void volume_partial_kernel(Geom G, const T *h, double *partials)
 {
     __shared__ double red[32];
-    double s = 0.0;
-    for (int j = blockIdx.x; j < G.ny; j += gridDim.x)
-        for (int i = threadIdx.x; i < G.nx; i += blockDim.x) s += (double)h[(size_t)j * G.pitch + i];
-    s = block_reduce<false>(s, red);
+    ThreadSum<T> acc;
+    for (int j = blockIdx.x; j < G.ny; j += gridDim.x) {
+        const T *row = h + (size_t)j * G.pitch;
+        for (int i = threadIdx.x; i < G.nx; i += blockDim.x) acc.add(row[i]);
+    }
+    const double s = block_reduce<false>(acc.value(), red);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
@@ -256,10 +290,7 @@ cudaError_t launch_inflow(const Geom &g, const InflowSec *secs, int nsec, const 
 template <typename T>
 cudaError_t launch_hmax(const Geom &g, const T *h, Ctrl *ctrl, cudaStream_t st)
 {
-    size_t N = (size_t)g.nx * g.ny;
-    int blocks = (int)((N + 255) / 256);
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    if (blocks < 1) blocks = 1;
+    const int blocks = g.ny < 152 * 8 ? g.ny : 152 * 8;
     hmax_kernel<T><<<blocks, 256, 0, st>>>(g, h, ctrl);
     return cudaGetLastError();
 }

@@ -748,11 +748,13 @@ extern "C" flood_status flood_write_state(flood_handle *h, const void *depth, co
     if (!h || !depth) return fail(h, FLOOD_ERR_ARG, "NULL argument");
     CK(cudaStreamSynchronize(h->stream));
     // host input: stage the new state in the idle half of the ping-pong buffers
-    // (the next step's output, free now), check it on the device, and only then
-    // copy it over the current state, so a rejected state leaves the handle as
-    // it was.  Device input is taken as it is.
+    // (the next step's output, free now) and check it on the device; only a
+    // finite state becomes current, so a rejected one leaves the handle as it
+    // was.  The staged half is made current by swapping the halves; an
+    // ensemble member (whose launch tables fix its half) copies it over
+    // instead.  Device input is taken as it is.
     const bool staged = !src_on_device;
-    const int cur = h->cur, dst = staged ? 1 - h->cur : h->cur;
+    const int dst = staged ? 1 - h->cur : h->cur;
     const int nx = h->geo.nx, ny = h->geo.ny, P = h->geo.pitch;
     flood_status st = copy_in(h, h->h[dst], depth, ny, nx, src_on_device);
     if (st) return st;
@@ -775,13 +777,18 @@ extern "C" flood_status flood_write_state(flood_handle *h, const void *depth, co
         CK(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         if (bad) return fail(h, FLOOD_ERR_ARG, "depth or discharge has NaN/Inf");
-        const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
-        CK(cudaMemcpyAsync(h->h[cur], h->h[dst], plane_elems(h, FLOOD_FIELD_H) * h->esz, d2d, h->stream));
-        if (qx) CK(cudaMemcpyAsync(h->qx[cur], h->qx[dst], plane_elems(h, FLOOD_FIELD_QX) * h->esz, d2d, h->stream));
-        if (qy) CK(cudaMemcpyAsync(h->qy[cur], h->qy[dst], plane_elems(h, FLOOD_FIELD_QY) * h->esz, d2d, h->stream));
+        if (!h->in_ensemble) {
+            h->cur = dst;
+        } else {
+            const int cur = h->cur;
+            const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+            CK(cudaMemcpyAsync(h->h[cur], h->h[dst], plane_elems(h, FLOOD_FIELD_H) * h->esz, d2d, h->stream));
+            if (qx) CK(cudaMemcpyAsync(h->qx[cur], h->qx[dst], plane_elems(h, FLOOD_FIELD_QX) * h->esz, d2d, h->stream));
+            if (qy) CK(cudaMemcpyAsync(h->qy[cur], h->qy[dst], plane_elems(h, FLOOD_FIELD_QY) * h->esz, d2d, h->stream));
+        }
     }
-    if (!qx) CK(cudaMemsetAsync(h->qx[cur], 0, plane_elems(h, FLOOD_FIELD_QX) * h->esz, h->stream));
-    if (!qy) CK(cudaMemsetAsync(h->qy[cur], 0, plane_elems(h, FLOOD_FIELD_QY) * h->esz, h->stream));
+    if (!qx) CK(cudaMemsetAsync(h->qx[h->cur], 0, plane_elems(h, FLOOD_FIELD_QX) * h->esz, h->stream));
+    if (!qy) CK(cudaMemsetAsync(h->qy[h->cur], 0, plane_elems(h, FLOOD_FIELD_QY) * h->esz, h->stream));
     // clear the device status word (keep the rest of the control block)
     CK(cudaMemsetAsync(&h->ctrl->status, 0, sizeof(int), h->stream));
     st = refresh_hmax(h);

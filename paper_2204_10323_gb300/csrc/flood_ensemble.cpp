@@ -208,6 +208,7 @@ extern "C" flood_status flood_ensemble_create(int32_t n, const flood_grid *grids
             flood_ensemble_destroy(e);
             return efail(nullptr, st, m);
         }
+        h->in_ensemble = true;
         e->members.push_back(h);
     }
     e->stream = e->members[0]->stream;

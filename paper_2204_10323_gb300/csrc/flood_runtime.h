@@ -26,6 +26,7 @@ struct flood_handle {
     // state (ping-pong) and static fields, pitched rows of geo.pitch elements
     void *h[2] = {nullptr, nullptr}, *qx[2] = {nullptr, nullptr}, *qy[2] = {nullptr, nullptr};
     int cur = 0;
+    bool in_ensemble = false;     // a member of an ensemble (whose launch tables fix each member's cur)
     void *z = nullptr, *n = nullptr;
 
     // boundary description and the per-epoch inflow solution

@@ -28,14 +28,16 @@ __device__ __forceinline__ T boundary_face(const StepArgs<T> &a, int side, int k
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX *BY) step_reference_kernel(const StepArgs<T> a)
+__global__ void __launch_bounds__(BX *BY) step_reference_kernel(const StepArgs<T> a, const int nbx)
 {
+    // one-dimensional grid (grids taller than 65535 blocks): block (bx, by) of nbx columns of blocks
+    const int bx = (int)(blockIdx.x % (unsigned)nbx), by = (int)(blockIdx.x / (unsigned)nbx);
     using O = R<T>;
     __shared__ double red[32];
     __shared__ T tile[BY][BX];
     const Geom &G = a.geo;
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
+    const int i = bx * BX + threadIdx.x;
+    const int j = by * BY + threadIdx.y;
     const bool in = i < G.nx && j < G.ny;
     const T dt = T(a.ctrl->dt), dx = T(G.dx), g = T(G.g), hd = T(G.h_dry);
     const bool wt = G.theta != 1.0;                   // theta-weighted numerator discharges
@@ -102,11 +104,11 @@ __global__ void __launch_bounds__(BX *BY) step_reference_kernel(const StepArgs<T
         for (int k = tid; k < a.n_gauges; k += BX * BY) {
             int64_t cell = a.gauge_cells[k];
             int gi = (int)(cell % G.nx), gj = (int)(cell / G.nx);
-            int li = gi - blockIdx.x * BX, lj = gj - blockIdx.y * BY;
+            int li = gi - bx * BX, lj = gj - by * BY;
             if (li >= 0 && li < BX && lj >= 0 && lj < BY) a.gauge_out[k] = (double)tile[lj][li];
         }
     }
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
         double vin = a.ctrl->V_in;
         for (int k = 0; k < a.n_inflow_sec; k++) {
             double Q = a.inflow_Q[(size_t)a.s * a.n_inflow_sec + k];
@@ -123,8 +125,8 @@ template <typename T>
 cudaError_t launch_step_reference(const StepArgs<T> &a, cudaStream_t st)
 {
     dim3 block(BX, BY);
-    dim3 grid((a.geo.nx + BX - 1) / BX, (a.geo.ny + BY - 1) / BY);
-    step_reference_kernel<T><<<grid, block, 0, st>>>(a);
+    const int nbx = (a.geo.nx + BX - 1) / BX, nby = (a.geo.ny + BY - 1) / BY;
+    step_reference_kernel<T><<<(unsigned)((int64_t)nbx * nby), block, 0, st>>>(a, nbx);
     return cudaGetLastError();
 }
 

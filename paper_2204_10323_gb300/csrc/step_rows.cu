@@ -42,19 +42,21 @@ __device__ __forceinline__ void set(float4 &v, int k, float x)
     else v.w = x;
 }
 
-__global__ void __launch_bounds__(kWarps * 32) step_rows_kernel(const StepArgs<float> a)
+__global__ void __launch_bounds__(kWarps * 32) step_rows_kernel(const StepArgs<float> a, const int nbx)
 {
+    // one-dimensional grid (grids taller than 65535 blocks): block (bx, by) of nbx columns of blocks
+    const int bx = (int)(blockIdx.x % (unsigned)nbx), by = (int)(blockIdx.x / (unsigned)nbx);
     __shared__ double red[32];
     const Geom &G = a.geo;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nx = G.nx, ny = G.ny;
     const size_t P = (size_t)G.pitch;
-    const int x0 = (blockIdx.x * kWarps + warp) * 128;
+    const int x0 = (bx * kWarps + warp) * 128;
     const int c0 = x0 + 4 * lane;
     const bool full = c0 + 3 < nx;                       // all four columns of the lane inside the grid
     const bool active = x0 < nx;
     const bool lane_in = active && c0 < (int)P;        // float4 lies inside the row pitch
-    const int y0 = blockIdx.y * kRows;
+    const int y0 = by * kRows;
     const int y1 = min(y0 + kRows, ny);
     const double dtd = a.ctrl->dt;
     FastConst K;
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(kWarps * 32) step_rows_kernel(const StepArgs<f
         double bm = block_reduce<true>(nan_seen ? (double)NAN : (double)hmax, red);
         if (threadIdx.x == 0) atomic_max_nonneg(&a.ctrl->hmax_bits, bm);
     }
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         double vin = a.ctrl->V_in;
         for (int k = 0; k < a.n_inflow_sec; k++) {
             double Q = a.inflow_Q[(size_t)a.s * a.n_inflow_sec + k];
@@ -272,8 +274,8 @@ __global__ void __launch_bounds__(kWarps * 32) step_rows_kernel(const StepArgs<f
 cudaError_t launch_step_rows(const StepArgs<float> &a, cudaStream_t st)
 {
     const int strips = (a.geo.nx + 127) / 128;
-    dim3 grid((strips + kWarps - 1) / kWarps, (a.geo.ny + kRows - 1) / kRows);
-    step_rows_kernel<<<grid, kWarps * 32, 0, st>>>(a);
+    const int nbx = (strips + kWarps - 1) / kWarps, nby = (a.geo.ny + kRows - 1) / kRows;
+    step_rows_kernel<<<(unsigned)((int64_t)nbx * nby), kWarps * 32, 0, st>>>(a, nbx);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.gauge_out) return launch_gauges<float>(a.geo, a.h_out, a.gauge_cells, a.n_gauges, a.gauge_out, st);

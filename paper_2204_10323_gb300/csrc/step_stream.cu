@@ -503,24 +503,27 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
 }
 
 template <int kMode>
-__global__ void __launch_bounds__(kMaxWarps * 32, 5) step_stream_kernel(const StepArgs<float> a, const int rows)
+__global__ void __launch_bounds__(kMaxWarps * 32, 5) step_stream_kernel(const StepArgs<float> a, const int rows,
+                                                                         const int nbx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     uint32_t ring_base = 0;
-    stream_body<false, kMode>(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, smem_raw, red, ring_base, true);
+    stream_body<false, kMode>(a, a.s, a.want_hmax, (int)(blockIdx.x % (unsigned)nbx), (int)(blockIdx.x / (unsigned)nbx),
+                              rows, smem_raw, red, ring_base, true);
 }
 
 // The same step with every warp's rows staged as 2D tiles by tensor copies.
 template <int kMode>
 __global__ void __launch_bounds__(kMaxWarps * 32, 4)
-    step_tma_kernel(const StepArgs<float> a, const int rows, const __grid_constant__ TmaMaps maps)
+    step_tma_kernel(const StepArgs<float> a, const int rows, const int nbx, const __grid_constant__ TmaMaps maps)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     unsigned char *base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);   // 128-byte aligned rings
     uint32_t ring_base = 0;
-    stream_body<true, kMode>(a, a.s, a.want_hmax, blockIdx.x, blockIdx.y, rows, base, red, ring_base, true,
+    stream_body<true, kMode>(a, a.s, a.want_hmax, (int)(blockIdx.x % (unsigned)nbx), (int)(blockIdx.x / (unsigned)nbx),
+                             rows, base, red, ring_base, true,
                               &maps);
 }
 
@@ -606,13 +609,14 @@ cudaError_t launch_step_stream(const StepArgs<float> &a, cudaStream_t st)
     cudaError_t e = configure(warps);
     if (e != cudaSuccess) return e;
     const int strips = (a.geo.nx + 127) / 128;
-    dim3 grid((strips + warps - 1) / warps, (a.geo.ny + rows - 1) / rows);
+    const int nbx = (strips + warps - 1) / warps, nby = (a.geo.ny + rows - 1) / rows;
+    const unsigned grid = (unsigned)((int64_t)nbx * nby);     // one-dimensional: (bx, by) from the block index
     const size_t smem = sizeof(WarpRing) * warps;
     switch (kernel_mode(a.geo)) {
-    case 0: step_stream_kernel<0><<<grid, warps * 32, smem, st>>>(a, rows); break;
-    case 1: step_stream_kernel<1><<<grid, warps * 32, smem, st>>>(a, rows); break;
-    case 2: step_stream_kernel<2><<<grid, warps * 32, smem, st>>>(a, rows); break;
-    default: step_stream_kernel<3><<<grid, warps * 32, smem, st>>>(a, rows); break;
+    case 0: step_stream_kernel<0><<<grid, warps * 32, smem, st>>>(a, rows, nbx); break;
+    case 1: step_stream_kernel<1><<<grid, warps * 32, smem, st>>>(a, rows, nbx); break;
+    case 2: step_stream_kernel<2><<<grid, warps * 32, smem, st>>>(a, rows, nbx); break;
+    default: step_stream_kernel<3><<<grid, warps * 32, smem, st>>>(a, rows, nbx); break;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -678,12 +682,13 @@ cudaError_t launch_step_tma(const StepArgs<float> &a, cudaStream_t st)
         if (e != cudaSuccess) return e;
     }
     const int strips = (a.geo.nx + 127) / 128;
-    dim3 grid((strips + warps - 1) / warps, (ny + rows - 1) / rows);
+    const int nbx = (strips + warps - 1) / warps, nby = (ny + rows - 1) / rows;
+    const unsigned grid = (unsigned)((int64_t)nbx * nby);     // one-dimensional: (bx, by) from the block index
     switch (kernel_mode(a.geo)) {
-    case 0: step_tma_kernel<0><<<grid, warps * 32, smem, st>>>(a, rows, maps); break;
-    case 1: step_tma_kernel<1><<<grid, warps * 32, smem, st>>>(a, rows, maps); break;
-    case 2: step_tma_kernel<2><<<grid, warps * 32, smem, st>>>(a, rows, maps); break;
-    default: step_tma_kernel<3><<<grid, warps * 32, smem, st>>>(a, rows, maps); break;
+    case 0: step_tma_kernel<0><<<grid, warps * 32, smem, st>>>(a, rows, nbx, maps); break;
+    case 1: step_tma_kernel<1><<<grid, warps * 32, smem, st>>>(a, rows, nbx, maps); break;
+    case 2: step_tma_kernel<2><<<grid, warps * 32, smem, st>>>(a, rows, nbx, maps); break;
+    default: step_tma_kernel<3><<<grid, warps * 32, smem, st>>>(a, rows, nbx, maps); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

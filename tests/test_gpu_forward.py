@@ -164,6 +164,54 @@ def test_fp32_run_is_deterministic_and_resumable():
     assert np.array_equal(ha, hc) and np.array_equal(qxa, qxc) and np.array_equal(qya, qyc)
 
 
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_write_state_mid_run_swaps_halves_under_graph_replay(use_graph):
+    # write_state makes the staged half current (the halves swap); captured
+    # epochs are kept per half, so replay continues from the written state
+    Fm = F()
+    p = as_f32_problem(inputs.random_small(150, 90, 12))
+    p.opts.epoch_steps = 4
+    a = Fm.Sim(p, use_graph=use_graph)
+    a.step(12)
+    h1, qx1, qy1 = a.state()
+    L1 = a.ledger()
+    a.step(5)                            # move on, then rewind to the saved state
+    for k in range(3):                   # both halves current in turn
+        a.write_state(h1, qx1, qy1)
+        a.set_clock(L1["t"], int(L1["step"]), L1["dt"], L1["V_in"], L1["V_out"], L1["V_clip"])
+        a.step(k + 1)
+    a.write_state(h1, qx1, qy1)
+    a.set_clock(L1["t"], int(L1["step"]), L1["dt"], L1["V_in"], L1["V_out"], L1["V_clip"])
+    a.step(20)
+    b = Fm.Sim(p)
+    b.step(32)
+    for f in (Fm.FIELD_H, Fm.FIELD_QX, Fm.FIELD_QY):
+        assert np.array_equal(a.read(f), b.read(f)), f
+    a.close()
+    b.close()
+
+
+def test_write_state_of_an_ensemble_member():
+    Fm = F()
+    probs = [as_f32_problem(inputs.random_small(nx, ny, 20 + k)) for k, (nx, ny) in enumerate([(150, 90), (64, 40)])]
+    for q in probs:
+        q.opts.epoch_steps = 4
+    ref = Fm.Sim(probs[1])
+    ref.step(8)
+    h8, qx8, qy8 = ref.state()
+    L8 = ref.ledger()
+    ref.step(8)
+    e = Fm.Ensemble(probs)
+    e.step(4)
+    m = e.members[1]
+    m.write_state(h8, qx8, qy8)
+    m.set_clock(L8["t"], 4, L8["dt"], L8["V_in"], L8["V_out"], L8["V_clip"])
+    e.step(8)
+    assert np.array_equal(m.read(Fm.FIELD_H), ref.read(Fm.FIELD_H))
+    e.close()
+    ref.close()
+
+
 def test_inflow_distribution_matches_oracle_eq6():
     """First-step boundary faces equal the oracle's Eq. 6 split (FP64)."""
     Fm = F()
