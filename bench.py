@@ -35,8 +35,10 @@ BYTES_PER_CELL = 32          # read h, qx, qy, z, n (20 B) + write h, qx, qy (12
 # the 4096^2 case of the same workload (state > L2), scaled by the cell count;
 # key (kernel, steps per launch).  The summaries are under profiles/.
 # (profiles/step_*_4096_full.md, profiles/roofline_study_16384.md)
-TRAFFIC_B_PER_CELL = {("stream", 1): 32.24, ("tma", 1): 32.18, ("rows", 1): 30.94, ("tiled", 1): 30.40,
-                      ("tiled", 2): 30.68, ("tiled", 4): 31.59, ("tiled", 8): 30.81}
+TRAFFIC_B_PER_CELL = {("stream", 1): 32.22, ("tma", 1): 32.12, ("rows", 1): 30.93, ("tiled", 1): 30.42,
+                      ("tiled", 2): 30.65, ("tiled", 4): 31.54, ("tiled", 8): 30.83}
+# the same for the vector-norm friction option (theta = 1)
+TRAFFIC_VEC_B_PER_CELL = {("stream", 1): 32.20, ("tma", 1): 32.18}
 METRIC = "Gcell-updates/s and % of HBM roofline (FP32, 1 GB300); adjoint/forward time ratio"
 UNIT = "Gcell-updates/s"
 
@@ -281,6 +283,9 @@ def run_gpu(args):
         traffic = float(args.traffic_bytes)
     elif args.workload == "c3" and not variant and (args.kernel, per_launch) in TRAFFIC_B_PER_CELL:
         traffic = TRAFFIC_B_PER_CELL[(args.kernel, per_launch)] * ncell
+    elif args.workload == "c3" and args.theta == 1.0 and args.friction == 1 and \
+            (args.kernel, per_launch) in TRAFFIC_VEC_B_PER_CELL:
+        traffic = TRAFFIC_VEC_B_PER_CELL[(args.kernel, per_launch)] * ncell
 
     # end to end through the C ABI with host buffers: upload state, K steps, read depth + ledger
     pin_h = torch.from_numpy(h0).pin_memory()
