@@ -75,12 +75,19 @@ struct Sweep {
     size_t plane = 0, plane_y = 0;
     std::vector<Planes> slots;
     std::vector<int> free_slots;
-    int64_t work_step = -1;          // local index of the state in the handle's buffers
-    // epoch logs (device): dt and the E+1 start times of each epoch touched
+    Planes work[2];                  // the handle's two state buffers (replay outputs)
+    Planes src;                      // where the state of work_step lives: a work buffer or a slot
+    int64_t work_step = -1;          // local index of that state
+    // epoch logs (device), one slice per epoch touched: dt, the E+1 start times
+    // and the Eq. 6 rows (inflow_q, inflow_Q, inflow_W); the handle's epoch
+    // pointers are aimed at the slice of the epoch in use
     double *dt_log = nullptr, *tl_log = nullptr;
+    void *iq_log = nullptr;
+    double *iQ_log = nullptr, *iW_log = nullptr;
+    size_t iq_bytes = 0, nQ = 0;     // per epoch: bytes of inflow_q, doubles of inflow_Q / inflow_W
     std::vector<char> logged;
     int64_t e0 = 0;
-    int64_t loaded = -1;             // epoch whose inflow buffers are loaded
+    int64_t loaded = -1;             // epoch whose slice the handle's epoch pointers hold
     // adjoint buffers
     void *lh[2] = {nullptr, nullptr}, *lqx[2] = {nullptr, nullptr}, *lqy[2] = {nullptr, nullptr};
     void *lhu = nullptr;
@@ -136,34 +143,41 @@ double sum_pairs(std::vector<cudaEvent_t> &evs)
     return total;
 }
 
-// Make the inflow buffers and dt of epoch e current (logging it the first time).
+// Aim the handle's epoch pointers at epoch e's slice; the first visit (the
+// state of work_step is then the epoch's first state) chooses dt by the rule
+// and solves Eq. 6 into the slice, later visits only set dt.
 flood_status ensure_epoch(Sweep &S, int64_t e)
 {
     flood_handle *h = S.h;
     if (S.loaded == e) return FLOOD_OK;
     const int64_t ie = e - S.e0;
     const int E = S.E;
+    h->t_list = S.tl_log + ie * (E + 1);
+    h->inflow_q = (char *)S.iq_log + ie * S.iq_bytes;
+    h->inflow_Q = S.iQ_log + ie * S.nQ;
+    h->inflow_W = S.iW_log + ie * S.nQ;
     double *dtl = S.dt_log + ie;
-    double *tll = S.tl_log + ie * (E + 1);
     if (!S.logged[ie]) {
-        // first visit: the working state is the epoch's first state; choose dt by the rule
-        flood_status st = refresh_hmax(h);
-        if (st) return st;
+        CKA(cudaMemsetAsync(&h->ctrl->hmax_bits, 0, sizeof(unsigned long long), h->stream));
+        if (h->prec == FLOOD_F32) CKA(launch_hmax<float>(h->geo, (const float *)S.src.h, h->ctrl, h->stream));
+        else CKA(launch_hmax<double>(h->geo, (const double *)S.src.h, h->ctrl, h->stream));
         CKA(launch_epoch_begin(h->geo, h->ctrl, h->t_list, E, nullptr, h->stream));
         CKA(cudaMemcpyAsync(dtl, &h->ctrl->dt, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-        CKA(cudaMemcpyAsync(tll, h->t_list, (E + 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        flood_status st = launch_inflow_epoch(h);
+        if (st) return st;
         S.logged[ie] = 1;
     } else {
-        CKA(cudaMemcpyAsync(h->t_list, tll, (E + 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         CKA(cudaMemcpyAsync(&h->ctrl->dt, dtl, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     }
-    flood_status st = launch_inflow_epoch(h);
-    if (st) return st;
     S.loaded = e;
     return FLOOD_OK;
 }
 
-flood_status forward_step(Sweep &S)
+bool same(const Planes &a, const Planes &b) { return a.h == b.h; }
+
+// One forward replay step from S.src into `dst` (a free slot: a checkpoint
+// being taken) or else into the work buffer that S.src is not.
+flood_status forward_step(Sweep &S, const Planes *dst = nullptr)
 {
     flood_handle *h = S.h;
     const int64_t g = S.g0 + S.work_step;
@@ -172,27 +186,32 @@ flood_status forward_step(Sweep &S)
     if (s == 0 && !S.logged[e - S.e0]) S.loaded = -1;
     flood_status st = ensure_epoch(S, e);
     if (st) return st;
-    if (S.profile) st = timed(S, S.ev_fwd, [&] { return launch_steps(h, s, 1, s == S.E - 1 ? 1 : 0, nullptr, 0, nullptr); });
-    else st = launch_steps(h, s, 1, s == S.E - 1 ? 1 : 0, nullptr, 0, nullptr);
+    const Planes out = dst ? *dst : same(S.src, S.work[0]) ? S.work[1] : S.work[0];
+    const void *in[3] = {S.src.h, S.src.qx, S.src.qy};
+    void *o[3] = {out.h, out.qx, out.qy};
+    if (S.profile) st = timed(S, S.ev_fwd, [&] { return launch_step_planes(h, s, in, o); });
+    else st = launch_step_planes(h, s, in, o);
     if (st) return st;
+    S.src = out;
     S.work_step += 1;
     S.fwd_steps += 1;
     return FLOOD_OK;
 }
 
+// The state of `step` is the checkpoint in `slot`: read it in place.
 flood_status restore(Sweep &S, int slot, int64_t step)
 {
     if (S.work_step == step) return FLOOD_OK;
-    flood_status st = copy_planes(S.h, working(S.h), S.slots[slot], S.plane, S.plane_y);
-    if (st) return st;
+    S.src = S.slots[slot];
     S.work_step = step;
     return FLOOD_OK;
 }
 
-flood_status advance_to(Sweep &S, int64_t step)
+// Replay to `step`; the last step writes into `last_dst` when given.
+flood_status advance_to(Sweep &S, int64_t step, const Planes *last_dst = nullptr)
 {
     while (S.work_step < step) {
-        flood_status st = forward_step(S);
+        flood_status st = forward_step(S, S.work_step + 1 == step ? last_dst : nullptr);
         if (st) return st;
     }
     return FLOOD_OK;
@@ -214,9 +233,9 @@ flood_status reverse_step_t(Sweep &S)
     std::memset(&A, 0, sizeof(A));
     StepArgs<T> &a = A.fwd;
     a.geo = h->geo;
-    a.h = (const T *)h->h[h->cur];
-    a.qx = (const T *)h->qx[h->cur];
-    a.qy = (const T *)h->qy[h->cur];
+    a.h = (const T *)S.src.h;
+    a.qx = (const T *)S.src.qx;
+    a.qy = (const T *)S.src.qy;
     a.z = (const T *)h->z;
     a.n = (const T *)h->n;
     a.bc.type = h->bc_type;
@@ -294,10 +313,15 @@ flood_status reverse_range(Sweep &S, int64_t a, int64_t b, int sa)
     if (S.work_step > m || S.work_step < a) {
         if ((st = restore(S, sa, a))) return st;
     }
-    if ((st = advance_to(S, m))) return st;
+    // checkpoint m in a free slot: the replay's last step writes it there
     const int sm = S.free_slots.back();
     S.free_slots.pop_back();
-    if ((st = copy_planes(S.h, S.slots[sm], working(S.h), S.plane, S.plane_y))) return st;
+    if (S.work_step == m) {
+        if ((st = copy_planes(S.h, S.slots[sm], S.src, S.plane, S.plane_y))) return st;
+        S.src = S.slots[sm];
+    } else if ((st = advance_to(S, m, &S.slots[sm]))) {
+        return st;
+    }
     if ((st = reverse_range(S, m, b, sm))) return st;
     S.free_slots.push_back(sm);
     return reverse_range(S, a, m, sa);
@@ -377,8 +401,14 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     S.e0 = S.g0 / S.E;
     const int64_t n_ep = (S.g0 + n_steps - 1) / S.E - S.e0 + 1;
     S.logged.assign(n_ep, 0);
+    const int E = S.E;
+    S.iq_bytes = (size_t)E * h->n_slots * esz;
+    S.nQ = (size_t)E * std::max(h->n_in, 1);
     S.dt_log = (double *)alloc(n_ep * sizeof(double));
-    S.tl_log = (double *)alloc(n_ep * (S.E + 1) * sizeof(double));
+    S.tl_log = (double *)alloc(n_ep * (E + 1) * sizeof(double));
+    S.iq_log = alloc(n_ep * S.iq_bytes);
+    S.iQ_log = (double *)alloc(n_ep * S.nQ * sizeof(double));
+    S.iW_log = (double *)alloc(n_ep * S.nQ * sizeof(double));
     for (int b = 0; b < 2; b++) {
         S.lh[b] = alloc(S.plane);
         S.lqx[b] = alloc(S.plane);
@@ -388,25 +418,28 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     S.gn = (double *)alloc(P * h->geo.ny * sizeof(double));
     double *seed_dev = (double *)alloc(std::max<size_t>((size_t)n_steps * n_gauges, 1) * sizeof(double));
     int64_t *cells_dev = (int64_t *)alloc(std::max(n_gauges, 1) * sizeof(int64_t));
-    // saved handle state: control block, epoch buffers
-    Ctrl saved_ctrl;
-    const int E = S.E;
-    void *saved_inflow_q = alloc((size_t)E * h->n_slots * esz);
-    double *saved_inflow_Q = (double *)alloc((size_t)E * std::max(h->n_in, 1) * sizeof(double));
-    double *saved_inflow_W = (double *)alloc((size_t)E * std::max(h->n_in, 1) * sizeof(double));
-    double *saved_tlist = (double *)alloc((E + 1) * sizeof(double));
-    for (void *p : {(void *)S.dt_log, (void *)S.tl_log, S.lh[0], S.lh[1], S.lqx[0], S.lqx[1], S.lqy[0], S.lqy[1],
-                    S.lhu, (void *)S.gn, (void *)seed_dev, (void *)cells_dev, saved_inflow_q,
-                    (void *)saved_inflow_Q, (void *)saved_inflow_W, (void *)saved_tlist})
+    for (void *p : {(void *)S.dt_log, (void *)S.tl_log, S.iq_log, (void *)S.iQ_log, (void *)S.iW_log, S.lh[0],
+                    S.lh[1], S.lqx[0], S.lqx[1], S.lqy[0], S.lqy[1], S.lhu, (void *)S.gn, (void *)seed_dev,
+                    (void *)cells_dev})
         if (!p) {
             release();
             return fail(h, FLOOD_ERR_OOM, "adjoint buffer allocation");
         }
+    // saved handle state: control block, kernel, state index and epoch pointers (the
+    // sweep aims the epoch pointers at its own slices and writes nothing through the
+    // handle's own epoch buffers)
+    Ctrl saved_ctrl;
     const int saved_kernel = h->kernel;
     const int saved_cur = h->cur;
     const int64_t saved_step = h->step;
+    void *const saved_iq = h->inflow_q;
+    double *const saved_iQ = h->inflow_Q, *const saved_iW = h->inflow_W, *const saved_tl = h->t_list;
     auto finish = [&](flood_status st) {
         h->kernel = saved_kernel;
+        h->inflow_q = saved_iq;
+        h->inflow_Q = saved_iQ;
+        h->inflow_W = saved_iW;
+        h->t_list = saved_tl;
         release();
         return st;
     };
@@ -416,18 +449,15 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
         if (e_ != cudaSuccess) return finish(cuda_fail(h, e_, #expr));              \
     } while (0)
     CKF(cudaMemcpyAsync(&saved_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
-    CKF(cudaMemcpyAsync(saved_inflow_q, h->inflow_q, (size_t)E * h->n_slots * esz, cudaMemcpyDeviceToDevice, h->stream));
-    CKF(cudaMemcpyAsync(saved_inflow_Q, h->inflow_Q, (size_t)E * std::max(h->n_in, 1) * sizeof(double),
-                        cudaMemcpyDeviceToDevice, h->stream));
-    CKF(cudaMemcpyAsync(saved_inflow_W, h->inflow_W, (size_t)E * std::max(h->n_in, 1) * sizeof(double),
-                        cudaMemcpyDeviceToDevice, h->stream));
-    CKF(cudaMemcpyAsync(saved_tlist, h->t_list, (E + 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     // the epoch in progress at the start is logged from the handle
     if (S.g0 % E != 0) {
-        CKF(cudaMemcpyAsync(S.dt_log, &h->ctrl->dt, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-        CKF(cudaMemcpyAsync(S.tl_log, h->t_list, (E + 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+        CKF(cudaMemcpyAsync(S.dt_log, &h->ctrl->dt, sizeof(double), d2d, h->stream));
+        CKF(cudaMemcpyAsync(S.tl_log, h->t_list, (E + 1) * sizeof(double), d2d, h->stream));
+        CKF(cudaMemcpyAsync(S.iq_log, h->inflow_q, S.iq_bytes, d2d, h->stream));
+        CKF(cudaMemcpyAsync(S.iQ_log, h->inflow_Q, S.nQ * sizeof(double), d2d, h->stream));
+        CKF(cudaMemcpyAsync(S.iW_log, h->inflow_W, S.nQ * sizeof(double), d2d, h->stream));
         S.logged[0] = 1;
-        S.loaded = S.e0;
     }
     if (n_gauges > 0) {
         CKF(cudaMemcpyAsync(seed_dev, dLdh, (size_t)n_steps * n_gauges * sizeof(double), cudaMemcpyHostToDevice,
@@ -446,10 +476,16 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     S.seed = seed_dev;
     // FP32 forward replays use the row-streaming arithmetic the adjoint linearises
     if (h->prec == FLOOD_F32) h->kernel = FLOOD_KERNEL_STREAM;
+    for (int b = 0; b < 2; b++) {
+        S.work[b].h = h->h[b];
+        S.work[b].qx = h->qx[b];
+        S.work[b].qy = h->qy[b];
+    }
     {
         flood_status st = copy_planes(h, S.slots[0], working(h), S.plane, S.plane_y);
         if (st) return finish(st);
     }
+    S.src = S.slots[0];
     S.work_step = 0;
     {
         flood_status st = reverse_range(S, 0, n_steps, 0);
@@ -484,12 +520,6 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     }
     h->step = saved_step;
     CKF(cudaMemcpyAsync(h->ctrl, &saved_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
-    CKF(cudaMemcpyAsync(h->inflow_q, saved_inflow_q, (size_t)E * h->n_slots * esz, cudaMemcpyDeviceToDevice, h->stream));
-    CKF(cudaMemcpyAsync(h->inflow_Q, saved_inflow_Q, (size_t)E * std::max(h->n_in, 1) * sizeof(double),
-                        cudaMemcpyDeviceToDevice, h->stream));
-    CKF(cudaMemcpyAsync(h->inflow_W, saved_inflow_W, (size_t)E * std::max(h->n_in, 1) * sizeof(double),
-                        cudaMemcpyDeviceToDevice, h->stream));
-    CKF(cudaMemcpyAsync(h->t_list, saved_tlist, (E + 1) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CKF(cudaStreamSynchronize(h->stream));
 #undef CKF
     return finish(FLOOD_OK);

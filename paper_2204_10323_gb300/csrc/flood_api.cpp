@@ -222,34 +222,63 @@ StepArgs<T> make_args(flood_handle *h, int s, int k_steps, int want_hmax, const 
 
 StepArgs<float> step_args_f32(flood_handle *h, int s) { return make_args<float>(h, s, 1, 0, nullptr, 0, nullptr); }
 
+// The FP32 step of the handle's kernel family for prepared arguments.
+static cudaError_t launch_f32(flood_handle *h, const StepArgs<float> &a)
+{
+    switch (h->kernel) {
+    case FLOOD_KERNEL_REFERENCE: return launch_step_reference<float>(a, h->stream);
+    case FLOOD_KERNEL_TILED:
+        // gauge recording needs the depth after every step: single steps there
+        if (a.gauge_out) {
+            StepArgs<float> b = a;
+            b.tile_x = b.tile_y = 0;
+            return launch_step_stream(b, h->stream);
+        }
+        return launch_step_tiled(a, h->stream);
+    case FLOOD_KERNEL_STREAM: return launch_step_stream(a, h->stream);
+    case FLOOD_KERNEL_TMA: return launch_step_tma(a, h->stream);
+    default: return launch_step_rows(a, h->stream);
+    }
+}
+
 // One launch of k steps starting at step-in-epoch s.
 flood_status launch_steps(flood_handle *h, int s, int k, int want_hmax, const int64_t *gcells, int ng,
                           double *gout)
 {
     cudaError_t e;
-    if (h->prec == FLOOD_F64) {
+    if (h->prec == FLOOD_F64)
         e = launch_step_reference<double>(make_args<double>(h, s, 1, want_hmax, gcells, ng, gout), h->stream);
-    } else {
-        StepArgs<float> a = make_args<float>(h, s, k, want_hmax, gcells, ng, gout);
-        switch (h->kernel) {
-        case FLOOD_KERNEL_REFERENCE: e = launch_step_reference<float>(a, h->stream); break;
-        case FLOOD_KERNEL_TILED:
-            // gauge recording needs the depth after every step: single steps there
-            if (gout) {
-                StepArgs<float> b = a;
-                b.tile_x = b.tile_y = 0;
-                e = launch_step_stream(b, h->stream);
-            } else {
-                e = launch_step_tiled(a, h->stream);
-            }
-            break;
-        case FLOOD_KERNEL_STREAM: e = launch_step_stream(a, h->stream); break;
-        case FLOOD_KERNEL_TMA: e = launch_step_tma(a, h->stream); break;
-        default: e = launch_step_rows(a, h->stream); break;
-        }
-    }
+    else
+        e = launch_f32(h, make_args<float>(h, s, k, want_hmax, gcells, ng, gout));
     if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
     h->cur = 1 - h->cur;
+    return FLOOD_OK;
+}
+
+template <typename T>
+static void set_planes(StepArgs<T> &a, const void *const in[3], void *const out[3])
+{
+    a.h = (const T *)in[0];
+    a.qx = (const T *)in[1];
+    a.qy = (const T *)in[2];
+    a.h_out = (T *)out[0];
+    a.qx_out = (T *)out[1];
+    a.qy_out = (T *)out[2];
+}
+
+flood_status launch_step_planes(flood_handle *h, int s, const void *const in[3], void *const out[3])
+{
+    cudaError_t e;
+    if (h->prec == FLOOD_F64) {
+        StepArgs<double> a = make_args<double>(h, s, 1, 0, nullptr, 0, nullptr);
+        set_planes(a, in, out);
+        e = launch_step_reference<double>(a, h->stream);
+    } else {
+        StepArgs<float> a = make_args<float>(h, s, 1, 0, nullptr, 0, nullptr);
+        set_planes(a, in, out);
+        e = launch_f32(h, a);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
     return FLOOD_OK;
 }
 

@@ -16,6 +16,8 @@ FP32 tolerance: the FP32 path rounds about 6e-8 relative per operation on water
 levels of 10-100 m; over these 16-100 steps that stays below 1e-4 m (the
 1000-step bound is 1e-3 m).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -101,16 +103,19 @@ def c3():
 def window_oracle(p, jc, ic, r, dt, steps):
     sl = (slice(jc - r, jc + r + 1), slice(ic - r, ic + r + 1))
     w = Problem("window", 2 * r + 1, 2 * r + 1, p.dx, p.z[sl].copy(), p.n[sl].copy(), [],
-                Options(dt_mode=1, dt_const=dt, g=p.opts.g, h_dry=p.opts.h_dry), h0=p.h0[sl].copy())
+                Options(dt_mode=1, dt_const=dt, g=p.opts.g, h_dry=p.opts.h_dry, friction=p.opts.friction),
+                h0=p.h0[sl].copy())
     o = oracle.Oracle(w)
     o.run(steps)
     return o
 
 
-@pytest.mark.parametrize("kernel,k", [(4, 0), (5, 0), (3, 4)])
-def test_c3_full_grid_sampled_cells_match_oracle(c3, kernel, k):
+@pytest.mark.parametrize("kernel,k,friction", [(4, 0, 0), (5, 0, 0), (3, 4, 0), (5, 0, 1)])
+def test_c3_full_grid_sampled_cells_match_oracle(c3, kernel, k, friction):
     Fm = F()
     p, N, r, pick = c3
+    if friction:                                      # the vector-norm friction option (TMA tiles)
+        p = dataclasses.replace(p, opts=dataclasses.replace(p.opts, friction=friction))
     s = Fm.Sim(p, precision=Fm.F32, kernel=kernel, steps_per_launch=k)
     s.step(N)                                         # one CFL epoch of 16 steps
     dt = s.ledger()["dt"]
