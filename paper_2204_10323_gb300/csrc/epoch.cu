@@ -84,6 +84,76 @@ __device__ __forceinline__ double manning_cell_t(double hh, double sqrtS, double
 
 constexpr int kInflowThreads = 128;
 
+// Sections of at most this many cells are solved by warp 0 alone: a bisection
+// step then costs one warp reduction instead of two block barriers, and the
+// solve is latency-bound (the sections of the workloads hold 12-512 cells).
+// FP64 handles evaluate Eq. 5 with the slow double pow, so only the smallest
+// sections go to one warp there.  The choice depends on the section alone, so
+// a single grid and an ensemble member solve a section in the same order.
+constexpr int kWarpCells = 1024;     // shared-memory copy of a one-warp section's z and n
+
+template <typename T>
+__device__ __forceinline__ bool one_warp(const InflowSec &S)
+{
+    return S.ncell <= (sizeof(T) == 4 ? kWarpCells : 32);
+}
+
+// Sum of a one-warp section's Eq. 5 discharges at level W from its cells' z
+// and n staged in shared memory (every lane of warp 0 gets the sum).
+template <typename T>
+__device__ double section_total_warp(const InflowSec &S, const T *sz, const T *sn, double W, double dx,
+                                     int form)
+{
+    double s = 0.0;
+    for (int c = threadIdx.x; c < S.ncell; c += 32) {
+        double hh = W - (double)sz[c];
+        if (hh > 0.0) s += manning_cell_t(hh, S.sqrtS, sn[c], dx, form);
+    }
+    return warp_sum(s);
+}
+
+// FP32 handles, one-warp sections: Eq. 6 in single precision throughout the
+// search (the level W, Eq. 5 per cell, the warp's butterfly sum), bisecting
+// until the midpoint rounds to an end of the bracket (the double-precision
+// search to 1e-12 m spends about twenty more halvings below the resolution of
+// single-precision Eq. 5, each on the slow FP64 pipe); then each cell's
+// discharge rescaled to Q_in in double.
+__device__ void inflow_solve_warp_f32(const InflowSec &S, const float *sz, const float *sn, float zmin, double Q,
+                                      double dx, int form, float *out, double *W_slot)
+{
+    const int lane = threadIdx.x;
+    const float p = form == 0 ? 5.0f / 3.0f : 2.0f / 3.0f;
+    const float a = form == 0 ? (float)dx : (float)(dx * dx);
+    const float sq = (float)S.sqrtS;
+    auto total = [&](float W) {
+        float s = 0.0f;
+        for (int c = lane; c < S.ncell; c += 32) {
+            const float hh = W - sz[c];
+            if (hh > 0.0f) s += a * powf(hh, p) * sq / sn[c];
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        return s;
+    };
+    const float Qf = (float)Q;
+    float Hb = 1.0f;
+    while (total(zmin + Hb) < Qf && Hb < 1e12f) Hb *= 2.0f;
+    float lo = zmin, hi = zmin + Hb;
+    for (int it = 0; it < 200; it++) {
+        const float mid = 0.5f * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        if (total(mid) < Qf) lo = mid;
+        else hi = mid;
+    }
+    const float W = hi;
+    if (lane == 0 && W_slot) *W_slot = (double)W;
+    const double tot = (double)total(W);
+    for (int c = lane; c < S.ncell; c += 32) {
+        const float hh = W - sz[c];
+        const float w = hh > 0.0f ? a * powf(hh, p) * sq / sn[c] : 0.0f;
+        out[c] = (float)(((double)w * (Q / tot)) / dx);
+    }
+}
+
 // Block-wide sum of the section's Eq. 5 discharges at level W (all threads get it).
 template <typename T>
 __device__ double section_total(const InflowSec &S, const int64_t *cells, const T *z, const T *n,
@@ -104,7 +174,8 @@ __device__ double section_total(const InflowSec &S, const int64_t *cells, const 
     return t;
 }
 
-// Eq. 6 for (step s of the epoch, inflow section k), one warp: bisection for
+// Eq. 6 for (step s of the epoch, inflow section k), by warp 0 or the whole
+// block (one_warp): bisection for
 // the level W with sum_c Q_c(W) = Q_in(t_s) on [min z, min z + H] (H doubled
 // from 1 m), 200 halvings at most or a bracket below 1e-12 m, W = upper end;
 // then each cell's discharge scaled by Q_in / sum, stored as unit-width flux.
@@ -112,7 +183,7 @@ template <typename T>
 __device__ void inflow_body(const Geom &G, const InflowSec *secs, int nsec, const int64_t *cells,
                             const double *tab_t, const double *tab_q, const T *z, const T *n,
                             const double *t_list, T *inflow_q, int n_slots, double *inflow_Q, double *W_out,
-                            const int s, const int k, double *red)
+                            const int s, const int k, double *red, T *sz, T *sn)
 {
     const int tid = threadIdx.x;
     const InflowSec S = secs[k];
@@ -131,20 +202,39 @@ __device__ void inflow_body(const Geom &G, const InflowSec *secs, int nsec, cons
         for (int c = tid; c < S.ncell; c += kInflowThreads) out[c] = T(0);
         return;
     }
+    const bool warp_only = one_warp<T>(S);
+    if (warp_only && tid >= 32) return;           // warp 0 solves and distributes
+    const int nthreads = warp_only ? 32 : kInflowThreads;
     const double dx = G.dx;
     const int form = G.bc_form;
+    if (warp_only) {                              // the section's z and n, read once
+        for (int c = tid; c < S.ncell; c += 32) {
+            const int64_t idx = cells[S.cell0 + c];
+            sz[c] = z[idx];
+            sn[c] = n[idx];
+        }
+        __syncwarp();
+        if constexpr (sizeof(T) == 4) {
+            inflow_solve_warp_f32(S, sz, sn, (float)zmin, Q, dx, form, out,
+                                  W_out ? W_out + (size_t)s * nsec + k : nullptr);
+            return;
+        }
+    }
+    auto total_at = [&](double W) {
+        return warp_only ? section_total_warp(S, sz, sn, W, dx, form) : section_total(S, cells, z, n, W, dx, form, red);
+    };
     double Hb = 1.0;
-    while (section_total(S, cells, z, n, zmin + Hb, dx, form, red) < Q && Hb < 1e12) Hb *= 2.0;
+    while (total_at(zmin + Hb) < Q && Hb < 1e12) Hb *= 2.0;
     double lo = zmin, hi = zmin + Hb;
     for (int it = 0; it < 200 && hi - lo >= 1e-12; it++) {
         double mid = 0.5 * (lo + hi);
-        if (section_total(S, cells, z, n, mid, dx, form, red) < Q) lo = mid;
+        if (total_at(mid) < Q) lo = mid;
         else hi = mid;
     }
     const double W = hi;
     if (tid == 0 && W_out) W_out[(size_t)s * nsec + k] = W;
-    const double total = section_total(S, cells, z, n, W, dx, form, red);
-    for (int c = tid; c < S.ncell; c += kInflowThreads) {
+    const double total = total_at(W);
+    for (int c = tid; c < S.ncell; c += nthreads) {
         int64_t idx = cells[S.cell0 + c];
         double hh = W - (double)z[idx];
         double w = hh > 0.0 ? manning_cell_t(hh, S.sqrtS, n[idx], dx, form) : 0.0;
@@ -158,8 +248,9 @@ __global__ void inflow_kernel(Geom G, const InflowSec *secs, int nsec, const int
                               const double *t_list, T *inflow_q, int n_slots, double *inflow_Q, double *W_out)
 {
     __shared__ double red[kInflowThreads / 32];
+    __shared__ T sz[kWarpCells], sn[kWarpCells];
     inflow_body<T>(G, secs, nsec, cells, tab_t, tab_q, z, n, t_list, inflow_q, n_slots, inflow_Q, W_out, blockIdx.x,
-                   blockIdx.y, red);
+                   blockIdx.y, red, sz, sn);
 }
 
 // Eq. 6 for every (step, section) of a batch of simulations: block (s, task).
@@ -167,10 +258,11 @@ template <typename T>
 __global__ void inflow_batched_kernel(const EpochArgs<T> *tab, const int2 *tasks)
 {
     __shared__ double red[kInflowThreads / 32];
+    __shared__ T sz[kWarpCells], sn[kWarpCells];
     const int2 t = tasks[blockIdx.y];
     const EpochArgs<T> &A = tab[t.x];
     inflow_body<T>(A.geo, A.secs, A.nsec, A.cells, A.tab_t, A.tab_q, A.z, A.n, A.t_list, A.inflow_q, A.n_slots,
-                   A.inflow_Q, A.inflow_W, blockIdx.x, t.y, red);
+                   A.inflow_Q, A.inflow_W, blockIdx.x, t.y, red, sz, sn);
 }
 
 // Rows over blocks, columns over threads; the maximum is exact in the state's
