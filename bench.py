@@ -35,10 +35,11 @@ BYTES_PER_CELL = 32          # read h, qx, qy, z, n (20 B) + write h, qx, qy (12
 # the 4096^2 case of the same workload (state > L2), scaled by the cell count;
 # key (kernel, steps per launch).  The summaries are under profiles/.
 # (profiles/step_*_4096_full.md, profiles/roofline_study_16384.md)
-TRAFFIC_B_PER_CELL = {("stream", 1): 32.22, ("tma", 1): 32.12, ("rows", 1): 30.93, ("tiled", 1): 30.42,
+# (stream and TMA captured in the 16384^2 launch shape, 4 warps x 32-row chunks)
+TRAFFIC_B_PER_CELL = {("stream", 1): 31.30, ("tma", 1): 31.24, ("rows", 1): 30.93, ("tiled", 1): 30.42,
                       ("tiled", 2): 30.65, ("tiled", 4): 31.54, ("tiled", 8): 30.83}
 # the same for the vector-norm friction option (theta = 1)
-TRAFFIC_VEC_B_PER_CELL = {("stream", 1): 32.20, ("tma", 1): 32.18}
+TRAFFIC_VEC_B_PER_CELL = {("stream", 1): 31.28, ("tma", 1): 31.24}
 METRIC = "Gcell-updates/s and % of HBM roofline (FP32, 1 GB300); adjoint/forward time ratio"
 UNIT = "Gcell-updates/s"
 
@@ -204,7 +205,7 @@ def timed_run(F, torch, prob, kernel_name, k, tile, graph, steps_req, warmup, lo
     """Warm up and time whole epochs of one kernel on `prob`: CUDA events around
     every launch on the library's stream, nvidia-smi clocks sampled meanwhile."""
     kernel = {"rows": F.KERNEL_ROWS, "tiled": F.KERNEL_TILED, "reference": F.KERNEL_REFERENCE,
-              "stream": F.KERNEL_STREAM, "tma": F.KERNEL_TMA}[kernel_name]
+              "stream": F.KERNEL_STREAM, "tma": F.KERNEL_TMA, "auto": F.KERNEL_AUTO}[kernel_name]
     sim = F.Sim(prob, precision=F.F32, kernel=kernel, steps_per_launch=k, tile=tile, use_graph=graph)
     E = prob.opts.epoch_steps
     stream = torch.cuda.current_stream()
@@ -363,6 +364,8 @@ def resolution_sweep(F, torch, prob, args, local, dist, ms_per_step_1m: float):
     the paper derives its coarser grids from the 1 m DEM, each timed like the main
     leg; the paper's steps/s per TPU v3 core (Table 1) beside them as context."""
     from inputs import Problem
+    # the library's own choice per grid (AUTO) unless a kernel family was asked for
+    sweep_kernel = "auto" if args.kernel in ("stream", "reference") else args.kernel
     rows = [{"dx_m": prob.dx, "nx": prob.nx, "ny": prob.ny, "steps_per_s": 1e3 / ms_per_step_1m,
              "gcell_s": prob.nx * prob.ny / ms_per_step_1m / 1e6}]
     for f in (2, 4, 8):
@@ -370,13 +373,13 @@ def resolution_sweep(F, torch, prob, args, local, dist, ms_per_step_1m: float):
         h0 = None if prob.h0 is None else F.coarsen(prob.h0, f)
         sub = Problem(f"{prob.name}_coarse{f}", z.shape[1], z.shape[0], prob.dx * f, z, n, prob.sections,
                       prob.opts, h0=h0)
-        run = timed_run(F, torch, sub, args.kernel if args.kernel != "reference" else "stream", args.k, (0, 0),
-                        args.graph, args.steps, args.warmup, local, dist)
+        run = timed_run(F, torch, sub, sweep_kernel, args.k, (0, 0), args.graph, args.steps, args.warmup, local,
+                        dist)
         run["sim"].close()
         ms = run["total_ms"] / run["steps"]
         rows.append({"dx_m": sub.dx, "nx": sub.nx, "ny": sub.ny, "steps_per_s": 1e3 / ms,
                      "gcell_s": sub.nx * sub.ny / ms / 1e6})
-    return {"kernel": args.kernel, "rows": rows,
+    return {"kernel": sweep_kernel + " at 2, 4, 8 m (" + args.kernel + " at 1 m)", "rows": rows,
             "paper_steps_per_s_one_tpu_v3_core": {"2 m, 248 M cells": 7.57, "4 m, 62 M cells": 30.2,
                                                   "8 m, 15.5 M cells": 118.0}}
 

@@ -475,7 +475,8 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     S.G = n_gauges;
     S.seed = seed_dev;
     // FP32 forward replays use the row-streaming arithmetic the adjoint linearises
-    if (h->prec == FLOOD_F32) h->kernel = FLOOD_KERNEL_STREAM;
+    // (the stream kernel, or its bitwise-equal tensor-tile form)
+    if (h->prec == FLOOD_F32 && h->kernel != FLOOD_KERNEL_TMA) h->kernel = FLOOD_KERNEL_STREAM;
     for (int b = 0; b < 2; b++) {
         S.work[b].h = h->h[b];
         S.work[b].qx = h->qx[b];

@@ -452,10 +452,15 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
     const int E = o.epoch_steps;
 
     // kernel family and temporal-blocking depth
-    // AUTO: the row-staged stream kernel; with vector-norm friction the tensor-tile
-    // variant, whose two-row tiles hold the next row's qy half of the time
-    // (measured on the 16384^2 workload: 184 against 165 Gcell-updates/s)
-    if (o.kernel == FLOOD_KERNEL_AUTO) h->kernel = o.friction != 0 ? FLOOD_KERNEL_TMA : FLOOD_KERNEL_STREAM;
+    // AUTO: the tensor-tile kernel below 2^27 cells and with vector-norm friction
+    // (whose next-row look-ahead two-row tiles serve half of the time), else the
+    // row-staged stream kernel.  Measured on the fractal workload (us per step,
+    // stream / TMA): 16.7 / 14.7 at 1024^2, 37.5 / 32.6 at 2048^2, 105.5 / 100.8
+    // at 4096^2, 349.5 / 345.9 at 8192^2, 1291 / 1301 at 16384^2; with vector
+    // friction 1629 / 1455 at 16384^2.  The two are bitwise equal.
+    if (o.kernel == FLOOD_KERNEL_AUTO)
+        h->kernel = (o.friction != 0 || (int64_t)grid->nx * grid->ny < ((int64_t)1 << 27)) ? FLOOD_KERNEL_TMA
+                                                                                          : FLOOD_KERNEL_STREAM;
     else h->kernel = o.kernel;
     if (h->prec == FLOOD_F64) h->kernel = FLOOD_KERNEL_REFERENCE;
     h->k_per_launch = 1;
