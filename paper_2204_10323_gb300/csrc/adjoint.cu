@@ -158,8 +158,10 @@ __device__ __forceinline__ void outflow_adj(const StepArgs<T> &a, const Fwd<T> &
     gn += -nu * q / n;
 }
 
-// One launch per reverse step, face-centric within a BX x by tile (by = 16
-// rows in FP32, 8 in FP64 to stay inside static shared memory):
+// One launch per reverse step, face-centric within a BX x 8 tile (256
+// threads: 32 registers and 19 KB of shared memory in FP32 let eight blocks
+// share an SM, so one block's barriers and loads overlap the others' work;
+// 32 x 16 and 32 x 4 tiles measured 12 % and 15 % slower at 1024^2):
 //  0. the tile's cells with a two-cell halo (h, z, n) and the faces around it
 //     (old q) are staged in shared memory;
 //  A. every face around the tile and its one-cell halo gets its new value q'
@@ -169,9 +171,8 @@ __device__ __forceinline__ void outflow_adj(const StepArgs<T> &a, const Fwd<T> &
 //  C. every face touching a tile cell gets mu and its derivatives once,
 //     leaving its contributions to the two cells and the adjoint of its old q;
 //  D. every tile cell gathers the contributions of its four faces.
-template <typename T> struct TileRows { static constexpr int v = 16; };
+template <typename T> struct TileRows { static constexpr int v = 8; };
 constexpr int kTileGauges = 32;
-template <> struct TileRows<double> { static constexpr int v = 8; };
 
 template <typename T>
 __global__ void __launch_bounds__(BX * TileRows<T>::v) adj_step_kernel(const AdjArgs<T> A, const int nbx)
