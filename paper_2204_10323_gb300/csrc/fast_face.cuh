@@ -64,16 +64,99 @@ __device__ __forceinline__ float q_norm(float q, float a, float b, float c, floa
 
 // Eq. 3 for a wet face of flow depth hf: qmag the |q| of the friction term
 // (the face's own |q| unless the vector norm is asked for), qn the numerator
-// discharge (q itself unless theta-weighted).  Called with hf <= 0 the result
-// is NaN or garbage, never a trap; face_fast_sel discards it.
+// discharge (q itself unless theta-weighted).  The numerator
+// qn - (a1 hf)(eta_R - eta_L) and the denominator 1 + friction are each one
+// fused multiply-add (one rounding), as the paired form below computes them.
+// Called with hf <= 0 the result is NaN or garbage, never a trap;
+// face_fast_sel discards it.
 __device__ __forceinline__ float face_wet(float qmag, float qn, float etaL, float etaR, float hf, float nsum,
                                           const FastConst &k)
 {
     float r7 = pow_m73(hf);
     float nf = __fmul_rn(0.5f, nsum);
-    float fric = __fmul_rn(__fmul_rn(__fmul_rn(k.gdt, __fmul_rn(nf, nf)), qmag), r7);
-    float num = __fsub_rn(qn, __fmul_rn(__fmul_rn(k.a1, hf), __fsub_rn(etaR, etaL)));
-    return __fmul_rn(num, rcp_fast(__fadd_rn(1.0f, fric)));
+    float aq = __fmul_rn(__fmul_rn(k.gdt, __fmul_rn(nf, nf)), qmag);
+    float num = __fmaf_rn(__fmul_rn(-k.a1, hf), __fsub_rn(etaR, etaL), qn);
+    return __fmul_rn(num, rcp_fast(__fmaf_rn(aq, r7, 1.0f)));
+}
+
+// ---- two faces at once on the paired single-precision instructions
+// (add/sub/mul .f32x2: one instruction for two lanes of a 64-bit register
+// pair, each rounded as the scalar instruction), for the issue-bound
+// temporal-blocking kernel.  face_fast_sel_x2 returns exactly the two values
+// face_fast_sel returns for (x, y): the same operations in the same order.
+__device__ __forceinline__ unsigned long long f2pack(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ float2 f2unpack(unsigned long long r)
+{
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+__device__ __forceinline__ float lg2_fast(float x)
+{
+    float l;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+    return l;
+}
+
+__device__ __forceinline__ float ex2_fast(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// etaL, etaR, zmax, nsum, q: the two faces' arguments of face_fast_sel.
+__device__ __forceinline__ float2 face_fast_sel_x2(float2 q, unsigned long long etaL, unsigned long long etaR,
+                                                   float2 zmax, unsigned long long nsum, const FastConst &k)
+{
+    const float2 eL = f2unpack(etaL), eR = f2unpack(etaR);
+    const unsigned long long hf = f2sub(f2pack(fmaxf(eL.x, eR.x), fmaxf(eL.y, eR.y)), f2pack(zmax.x, zmax.y));
+    const float2 h = f2unpack(hf);
+    const unsigned long long l = f2mul(f2pack(lg2_fast(h.x), lg2_fast(h.y)), f2pack(-7.0f / 3.0f, -7.0f / 3.0f));
+    const float2 lv = f2unpack(l);
+    const unsigned long long r7 = f2pack(ex2_fast(lv.x), ex2_fast(lv.y));
+    const unsigned long long nf = f2mul(f2pack(0.5f, 0.5f), nsum);
+    const unsigned long long aq = f2mul(f2mul(f2pack(k.gdt, k.gdt), f2mul(nf, nf)), f2pack(fabsf(q.x), fabsf(q.y)));
+    const unsigned long long num =
+        f2fma(f2mul(f2pack(-k.a1, -k.a1), hf), f2sub(etaR, etaL), f2pack(q.x, q.y));
+    const float2 den = f2unpack(f2fma(aq, r7, f2pack(1.0f, 1.0f)));
+    const float2 v = f2unpack(f2mul(num, f2pack(rcp_fast(den.x), rcp_fast(den.y))));
+    return make_float2(h.x > k.h_dry ? v.x : 0.0f, h.y > k.h_dry ? v.y : 0.0f);
 }
 
 // Eq. 3 at one face: eta_L, eta_R water levels, zmax = max(z_L, z_R),

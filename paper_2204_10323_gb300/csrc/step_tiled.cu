@@ -37,12 +37,21 @@ __host__ __device__ constexpr int out_cols(int K) { return 128 - 2 * halo_cols(K
 // level-1 rows in flight and pipelines per SM: one grid uses 6 and 6 (six
 // pipelines of 4 warps fit the registers and shared memory of an SM); the
 // ensemble kernel, which keeps more per-scenario state in registers, 8 and 5
-constexpr int kPF1 = 6, kPFE = 8;
+constexpr int kPF1 = 4, kPFE = 8;
 constexpr uint64_t kBudgetNs = 2000000000ull;
+
+constexpr int pow2_ceil(int v)
+{
+    int p = 1;
+    while (p < v) p *= 2;
+    return p;
+}
 
 template <int K, int kPF>
 struct alignas(16) PipeSmem {
-    static constexpr int kDZ = kPF + 2 * K; // z,n rows kept: the lagging levels read 2(K-1)+1 rows back
+    // z,n rows kept: the lagging levels read 2(K-1)+1 rows back; a power of two,
+    // so that the row's slot is a mask of its index
+    static constexpr int kDZ = pow2_ceil(kPF + 2 * K);
     float hq[kPF][3][128];                  // level-1 input rows: h, qx, qy
     float zn[kDZ][2][128];                  // z, n of recent rows
     float ho[K > 1 ? K - 1 : 1][2][3][128]; // hand-off: level s -> s+1, double buffered by tick parity
@@ -122,7 +131,7 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
         uint64_t *bar = &sm.bar[slot];
         mbar_arrive_expect_tx(bar, seg_bytes * 5u);
         float *hq = &sm.hq[slot][0][0];
-        float *zn = &sm.zn[j % kDZ][0][0];
+        float *zn = &sm.zn[(unsigned)j % kDZ][0][0];
         bulk_copy_g2s(hq + 0 * 128 + so, a.h + row, seg_bytes, bar);
         bulk_copy_g2s(hq + 1 * 128 + so, a.qx + row, seg_bytes, bar);
         bulk_copy_g2s(hq + 2 * 128 + so, a.qy + row, seg_bytes, bar);
@@ -180,12 +189,12 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
                         cqx = lds4(ho + 1 * 128 + 4 * lane);
                         cqy = lds4(ho + 2 * 128 + 4 * lane);
                     }
-                    cz = lds4(&sm.zn[r % kDZ][0][4 * lane]);
-                    cn = lds4(&sm.zn[r % kDZ][1][4 * lane]);
+                    cz = lds4(&sm.zn[(unsigned)r % kDZ][0][4 * lane]);
+                    cn = lds4(&sm.zn[(unsigned)r % kDZ][1][4 * lane]);
                 }
                 if (r > 0) {
-                    pz = lds4(&sm.zn[(r - 1) % kDZ][0][4 * lane]);
-                    pn = lds4(&sm.zn[(r - 1) % kDZ][1][4 * lane]);
+                    pz = lds4(&sm.zn[(unsigned)(r - 1) % kDZ][0][4 * lane]);
+                    pn = lds4(&sm.zn[(unsigned)(r - 1) % kDZ][1][4 * lane]);
                 }
                 if (r == rstart && jb > 0) {
                     hp = ch;                          // halo row: only becomes the previous row
@@ -194,12 +203,19 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
                     // rows, uniform over the warp, take the Eq. 5-6 path)
                     float4 qys;
                     if (r > 0 && r < ny) {
+                        // two faces per paired instruction (bitwise the scalar face_fast_sel)
 #pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            const float zl = get(pz, k), zr = get(cz, k);
-                            const float v = face_fast_sel(get(cqy, k), get(hp, k) + zl, get(ch, k) + zr,
-                                                          fmaxf(zl, zr), get(pn, k) + get(cn, k), Kc);
-                            set(qys, k, v);
+                        for (int k = 0; k < 4; k += 2) {
+                            const unsigned long long eL = f2add(f2pack(get(hp, k), get(hp, k + 1)),
+                                                                f2pack(get(pz, k), get(pz, k + 1)));
+                            const unsigned long long eR = f2add(f2pack(get(ch, k), get(ch, k + 1)),
+                                                                f2pack(get(cz, k), get(cz, k + 1)));
+                            const unsigned long long ns = f2add(f2pack(get(pn, k), get(pn, k + 1)),
+                                                                f2pack(get(cn, k), get(cn, k + 1)));
+                            const float2 zm = make_float2(fmaxf(get(pz, k), get(cz, k)), fmaxf(get(pz, k + 1), get(cz, k + 1)));
+                            const float2 v = face_fast_sel_x2(make_float2(get(cqy, k), get(cqy, k + 1)), eL, eR, zm, ns, Kc);
+                            set(qys, k, v.x);
+                            set(qys, k + 1, v.y);
                         }
                         if (edge_lane) {
 #pragma unroll
@@ -291,14 +307,18 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
                         const float nl0 = __shfl_up_sync(0xffffffffu, cn.w, 1);
                         float4 qxw;
 #pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            const float hl = k == 0 ? hl0 : get(ch, k - 1);
-                            const float zl = k == 0 ? zl0 : get(cz, k - 1);
-                            const float nl = k == 0 ? nl0 : get(cn, k - 1);
-                            const float zr = get(cz, k);
-                            const float v = face_fast_sel(get(cqx, k), hl + zl, get(ch, k) + zr, fmaxf(zl, zr),
-                                                          nl + get(cn, k), Kc);
-                            set(qxw, k, v);
+                        for (int k = 0; k < 4; k += 2) {
+                            const float hla = k == 0 ? hl0 : get(ch, k - 1), hlb = get(ch, k);
+                            const float zla = k == 0 ? zl0 : get(cz, k - 1), zlb = get(cz, k);
+                            const float nla = k == 0 ? nl0 : get(cn, k - 1), nlb = get(cn, k);
+                            const unsigned long long eL = f2add(f2pack(hla, hlb), f2pack(zla, zlb));
+                            const unsigned long long eR = f2add(f2pack(get(ch, k), get(ch, k + 1)),
+                                                                f2pack(get(cz, k), get(cz, k + 1)));
+                            const unsigned long long ns = f2add(f2pack(nla, nlb), f2pack(get(cn, k), get(cn, k + 1)));
+                            const float2 zm = make_float2(fmaxf(zla, get(cz, k)), fmaxf(zlb, get(cz, k + 1)));
+                            const float2 v = face_fast_sel_x2(make_float2(get(cqx, k), get(cqx, k + 1)), eL, eR, zm, ns, Kc);
+                            set(qxw, k, v.x);
+                            set(qxw, k + 1, v.y);
                         }
                         if (edge_lane) {              // lanes at or beyond x = 0 or x = nx: Eq. 5-6, or no face
 #pragma unroll
