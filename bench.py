@@ -5,7 +5,10 @@ state h, qx, qy with DEM z and Manning n, ~5.4 GB resident, far larger than
 the 129 MB L2), fractal terrain with a carved channel, two inflow sections and
 an outflow edge, primed to ~30 % wet.  One benchmark "step" is one time step
 of the whole grid: epoch bookkeeping (CFL dt, Eq. 6 inflow) when due, the
-face update (Eq. 3), depth update (Eq. 4), boundary faces and ledgers.
+face update (Eq. 3), depth update (Eq. 4), boundary faces and ledgers.  The
+default kernel is the temporal-blocking one (4 steps per launch, the
+library's AUTO choice for this grid); the one-step stream kernel is timed
+beside it (`one_step`).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -319,13 +322,21 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "bytes_per_cell": BYTES_PER_CELL, "kernel_ms": kern_ms, "steps_per_launch": per_launch},
+                         "bytes_per_cell": BYTES_PER_CELL, "kernel_ms": kern_ms, "steps_per_launch": per_launch,
+                         "dram_gbs": traffic / (kern_ms * 1e-3) / 1e9 if traffic else None,
+                         "note": ("one-step algorithmic bytes (32 B per cell-update) over the launch time; with "
+                                  f"{per_launch} steps per launch the kernel moves {traffic / ncell / per_launch:.1f} "
+                                  "B of DRAM traffic per cell-update and is bound by instruction issue, so the "
+                                  "fraction can pass 1") if per_launch > 1 and traffic else None},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "ledger": {k: L[k] for k in ("t", "dt", "V_in", "V_out", "V_clip", "volume")}}
     sim.close()
     del sim
-    if args.kernel != "tiled" and not args.no_temporal and not variant:     # the tiled kernel runs Eq. 3 as printed
-        line["temporal_blocking"] = temporal_leg(F, torch, prob, args, local, dist, ncell, peak)
+    if not args.no_temporal and not variant:     # the tiled kernel runs Eq. 3 as printed
+        if args.kernel != "tiled":
+            line["temporal_blocking"] = temporal_leg(F, torch, prob, args, local, dist, ncell, peak)
+        else:
+            line["one_step"] = temporal_leg(F, torch, prob, args, local, dist, ncell, peak, K=1, kernel="stream")
     if not args.no_sweep:
         line["resolution_sweep"] = resolution_sweep(F, torch, prob, args, local, dist, total_ms / steps)
     if not args.no_adjoint:
@@ -342,17 +353,19 @@ def run_gpu(args):
     return 0
 
 
-def temporal_leg(F, torch, prob, args, local, dist, ncell, peak, K: int = 4):
-    """The same workload on the temporal-blocking kernel (K steps per launch):
-    whole-job Gcell-updates/s, and its kernel time as an equivalent fraction of
-    the one-step HBM roofline (32 B per cell-update), beside the DRAM bytes it
-    actually moves per launch."""
-    run = timed_run(F, torch, prob, "tiled", K, (0, 0), args.graph, args.steps, args.warmup, local, dist)
+def temporal_leg(F, torch, prob, args, local, dist, ncell, peak, K: int = 4, kernel: str = "tiled"):
+    """The same workload on another kernel: the temporal-blocking kernel (K
+    steps per launch) beside a one-step headline, or the one-step stream kernel
+    beside a temporal-blocking headline.  Whole-job Gcell-updates/s, and the
+    kernel time as a fraction of the one-step HBM roofline (32 B per
+    cell-update), beside the DRAM bytes it actually moves per launch."""
+    run = timed_run(F, torch, prob, kernel, K if kernel == "tiled" else 0, (0, 0), args.graph, args.steps,
+                    args.warmup, local, dist)
     run["sim"].close()
     value = ncell * run["steps"] / (run["total_ms"] * 1e-3) / 1e9
     eq = BYTES_PER_CELL * ncell * K / (run["kern_ms"] * 1e-3) / 1e9
-    tr = TRAFFIC_B_PER_CELL.get(("tiled", K)) if args.workload == "c3" else None
-    return {"kernel": "tiled", "steps_per_launch": K, "value": value, "unit": UNIT,
+    tr = TRAFFIC_B_PER_CELL.get((kernel, K)) if args.workload == "c3" else None
+    return {"kernel": kernel, "steps_per_launch": K, "value": value, "unit": UNIT,
             "ms_per_step": run["total_ms"] / run["steps"], "kernel_ms_per_launch": run["kern_ms"],
             "equivalent_gbs": eq, "frac_of_one_step_roofline": eq / peak,
             "traffic_per_launch": tr * ncell if tr else None, "clocks": run["clocks"]}
@@ -479,8 +492,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c3")
-    ap.add_argument("--kernel", default="stream", choices=["stream", "rows", "tiled", "tma", "reference"])
-    ap.add_argument("--k", type=int, default=0, help="steps per launch (tiled kernel)")
+    ap.add_argument("--kernel", default="tiled", choices=["stream", "rows", "tiled", "tma", "reference"])
+    ap.add_argument("--k", type=int, default=4, help="steps per launch (tiled kernel)")
     ap.add_argument("--graph", action="store_true")
     ap.add_argument("--tile", default="", help="stream kernel launch shape: warps,rows")
     ap.add_argument("--traffic-bytes", type=float, default=None)

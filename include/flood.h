@@ -92,7 +92,9 @@ typedef struct {
 
 /* Kernel families for the forward step (FLOOD_F32; FLOOD_F64 always uses REFERENCE). */
 typedef enum {
-    FLOOD_KERNEL_AUTO = 0,       /* TMA below 2^27 cells or with vector-norm friction, else STREAM */
+    FLOOD_KERNEL_AUTO = 0,       /* TILED (K = 4) for Eq. 3 as printed with E a multiple of 4 and no launch
+                                    shape given; else TMA below 2^27 cells or with vector-norm friction,
+                                    else STREAM */
     FLOOD_KERNEL_REFERENCE = 1,  /* one thread per cell, IEEE ops in the oracle's order */
     FLOOD_KERNEL_ROWS = 2,       /* one warp per 128-column strip, float4 row streaming */
     FLOOD_KERNEL_TILED = 3,      /* pipeline of K warps per strip, K steps per launch (temporal blocking) */

@@ -474,9 +474,11 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     S.cells = cells_dev;
     S.G = n_gauges;
     S.seed = seed_dev;
-    // FP32 forward replays use the row-streaming arithmetic the adjoint linearises
-    // (the stream kernel, or its bitwise-equal tensor-tile form)
-    if (h->prec == FLOOD_F32 && h->kernel != FLOOD_KERNEL_TMA) h->kernel = FLOOD_KERNEL_STREAM;
+    // FP32 forward replays run one step at a time with the arithmetic the adjoint
+    // linearises: the tensor-tile kernel below 2^27 cells, the stream kernel above
+    // (bitwise equal to each other and to the temporal-blocking kernel)
+    if (h->prec == FLOOD_F32)
+        h->kernel = (int64_t)h->geo.nx * h->geo.ny < ((int64_t)1 << 27) ? FLOOD_KERNEL_TMA : FLOOD_KERNEL_STREAM;
     for (int b = 0; b < 2; b++) {
         S.work[b].h = h->h[b];
         S.work[b].qx = h->qx[b];

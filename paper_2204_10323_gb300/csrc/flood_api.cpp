@@ -451,24 +451,29 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
     G.epoch_steps = o.epoch_steps;
     const int E = o.epoch_steps;
 
-    // kernel family and temporal-blocking depth
-    // AUTO: the tensor-tile kernel below 2^27 cells and with vector-norm friction
-    // (whose next-row look-ahead two-row tiles serve half of the time), else the
-    // row-staged stream kernel.  Measured on the fractal workload (us per step,
-    // stream / TMA): 16.7 / 14.7 at 1024^2, 37.5 / 32.6 at 2048^2, 105.5 / 100.8
-    // at 4096^2, 349.5 / 345.9 at 8192^2, 1291 / 1301 at 16384^2; with vector
-    // friction 1629 / 1455 at 16384^2.  The two are bitwise equal.
-    if (o.kernel == FLOOD_KERNEL_AUTO)
-        h->kernel = (o.friction != 0 || (int64_t)grid->nx * grid->ny < ((int64_t)1 << 27)) ? FLOOD_KERNEL_TMA
-                                                                                          : FLOOD_KERNEL_STREAM;
-    else h->kernel = o.kernel;
+    // kernel family and temporal-blocking depth.  AUTO: the temporal-blocking
+    // kernel with K = 4 where it applies (Eq. 3 as printed, E a multiple of 4, no
+    // explicit launch shape), else the tensor-tile kernel below 2^27 cells or with
+    // vector-norm friction (whose next-row look-ahead two-row tiles serve half of
+    // the time), else the row-staged stream kernel.  Measured on the fractal
+    // workload (us per step): tiled K = 4 / TMA / stream 15.2 / 16.5 / 16.7 at
+    // 1024^2, 31.1 / 33.9 / 37.5 at 2048^2, 92.6 / 102.3 / 105.5 at 4096^2,
+    // 339 / 348 / 350 at 8192^2, 1181 / 1301 / 1288 at 16384^2; with vector
+    // friction TMA / stream 1455 / 1629 at 16384^2.  All three are bitwise equal.
+    if (o.kernel == FLOOD_KERNEL_AUTO) {
+        const bool tiled = o.theta == 1.0 && o.friction == 0 && E % 4 == 0 && o.tile_x == 0 && o.tile_y == 0;
+        if (tiled) h->kernel = FLOOD_KERNEL_TILED;
+        else h->kernel = (o.friction != 0 || (int64_t)grid->nx * grid->ny < ((int64_t)1 << 27)) ? FLOOD_KERNEL_TMA
+                                                                                                 : FLOOD_KERNEL_STREAM;
+    } else {
+        h->kernel = o.kernel;
+    }
     if (h->prec == FLOOD_F64) h->kernel = FLOOD_KERNEL_REFERENCE;
     h->k_per_launch = 1;
     h->tile_x = o.tile_x;
     h->tile_y = o.tile_y;
-    if (h->kernel == FLOOD_KERNEL_TILED) {
-        h->k_per_launch = o.steps_per_launch > 0 ? o.steps_per_launch : 4;
-    }
+    if (h->kernel == FLOOD_KERNEL_TILED)
+        h->k_per_launch = (o.kernel == FLOOD_KERNEL_TILED && o.steps_per_launch > 0) ? o.steps_per_launch : 4;
 
     auto bail = [&](flood_status st, const char *msg) {
         std::string m = msg;
