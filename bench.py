@@ -39,8 +39,8 @@ BYTES_PER_CELL = 32          # read h, qx, qy, z, n (20 B) + write h, qx, qy (12
 # key (kernel, steps per launch).  The summaries are under profiles/.
 # (profiles/step_*_4096_full.md, profiles/roofline_study_16384.md)
 # (stream and TMA captured in the 16384^2 launch shape, 4 warps x 32-row chunks)
-TRAFFIC_B_PER_CELL = {("stream", 1): 31.30, ("tma", 1): 31.24, ("rows", 1): 30.93, ("tiled", 1): 30.42,
-                      ("tiled", 2): 30.65, ("tiled", 4): 31.54, ("tiled", 8): 30.83}
+TRAFFIC_B_PER_CELL = {("stream", 1): 31.30, ("tma", 1): 31.24, ("rows", 1): 30.93, ("tiled", 1): 30.55,
+                      ("tiled", 2): 30.79, ("tiled", 4): 31.65, ("tiled", 8): 30.91}
 # the same for the vector-norm friction option (theta = 1)
 TRAFFIC_VEC_B_PER_CELL = {("stream", 1): 31.28, ("tma", 1): 31.24}
 METRIC = "Gcell-updates/s and % of HBM roofline (FP32, 1 GB300); adjoint/forward time ratio"
