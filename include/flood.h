@@ -112,7 +112,7 @@ typedef struct {
     int32_t epoch_steps;         /* E: steps per CFL epoch (1..1024) */
     int32_t bc_form;             /* 0 cell discharge dx h^(5/3) sqrt(S)/n, 1 literal dx^2 h^(2/3) sqrt(S)/n */
     int32_t kernel;              /* flood_kernel */
-    int32_t steps_per_launch;    /* K for FLOOD_KERNEL_TILED: 1..4, must divide E (0 = 4) */
+    int32_t steps_per_launch;    /* K for FLOOD_KERNEL_TILED: 1..4 or 8, must divide E (0 = 4) */
     int32_t tile_x, tile_y;      /* launch shape, 0 = chosen by the library.  STREAM: warps per block (1..4),
                                     rows per chunk.  TILED: at most tile_x pipelines (blocks), tile_y rows
                                     per work item (a chunk of one 120-column strip).  Negative: invalid. */
@@ -285,7 +285,7 @@ flood_status flood_ensemble_create(int32_t n, const flood_grid *grids, const voi
 flood_status flood_ensemble_set_launch(flood_ensemble *e, int32_t warps, int32_t rows, int32_t steps_per_graph,
                                        int32_t use_graph);
 /* Kernel for the steps: FLOOD_KERNEL_STREAM (one step per launch) or
- * FLOOD_KERNEL_TILED with steps_per_launch K (1..4, dividing epoch_steps;
+ * FLOOD_KERNEL_TILED with steps_per_launch K (1..4 or 8, dividing epoch_steps;
  * 0 = 4), the temporal blocking of Eq. 3-4 over K steps per launch; a launch
  * never crosses an epoch end.  FLOOD_ERR_ARG otherwise.  Drops the captured
  * graphs.  No counterpart in the paper: a launch-configuration choice. */
