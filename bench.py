@@ -41,6 +41,11 @@ BYTES_PER_CELL = 32          # read h, qx, qy, z, n (20 B) + write h, qx, qy (12
 # (stream and TMA captured in the 16384^2 launch shape, 4 warps x 32-row chunks)
 TRAFFIC_B_PER_CELL = {("stream", 1): 31.30, ("tma", 1): 31.24, ("rows", 1): 30.93, ("tiled", 1): 30.55,
                       ("tiled", 2): 30.79, ("tiled", 4): 31.65, ("tiled", 8): 30.91}
+# Warp instructions per cell-update of the temporal-blocking kernel (issue-bound), from the same 4096^2
+# capture (smsp__inst_executed.sum; profiles/step_tiled4_4096_full.md): the "alu" roofline beside the
+# one-step HBM one.  The issue peak is 152 SMs x 4 warp-instructions per cycle x the sampled SM clock.
+INST_PER_CELL_UPDATE = {("tiled", 4): 243920737 / (4096 * 4096 * 4)}
+SMS, ISSUE_PER_SM_CYCLE = 152, 4
 # the same for the vector-norm friction option (theta = 1)
 TRAFFIC_VEC_B_PER_CELL = {("stream", 1): 31.28, ("tma", 1): 31.24}
 METRIC = "Gcell-updates/s and % of HBM roofline (FP32, 1 GB300); adjoint/forward time ratio"
@@ -324,6 +329,7 @@ def run_gpu(args):
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "bytes_per_cell": BYTES_PER_CELL, "kernel_ms": kern_ms, "steps_per_launch": per_launch,
                          "dram_gbs": traffic / (kern_ms * 1e-3) / 1e9 if traffic else None,
+                         "issue": issue_roofline(args.kernel, per_launch, ncell, kern_ms, clk),
                          "note": ("one-step algorithmic bytes (32 B per cell-update) over the launch time; with "
                                   f"{per_launch} steps per launch the kernel moves {traffic / ncell / per_launch:.1f} "
                                   "B of DRAM traffic per cell-update and is bound by instruction issue, so the "
@@ -351,6 +357,20 @@ def run_gpu(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def issue_roofline(kernel: str, per_launch: int, ncell: int, kern_ms: float, clk):
+    """Instruction-issue roofline of an issue-bound kernel: warp instructions per
+    launch (ncu count per cell-update x the launch's cell-updates) over the launch
+    time, against 152 SMs x 4 issue slots x the SM clock sampled meanwhile."""
+    ipc = INST_PER_CELL_UPDATE.get((kernel, per_launch))
+    if ipc is None:
+        return None
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    achieved = ipc * ncell * per_launch / (kern_ms * 1e-3)
+    peak = SMS * ISSUE_PER_SM_CYCLE * mhz * 1e6
+    return {"bound": "alu", "unit": "warp-instructions/s", "achieved": achieved, "peak": peak,
+            "frac": achieved / peak, "inst_per_cell_update": ipc}
 
 
 def temporal_leg(F, torch, prob, args, local, dist, ncell, peak, K: int = 4, kernel: str = "tiled"):
