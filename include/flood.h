@@ -331,6 +331,18 @@ const char *flood_version(void);
 flood_status flood_volume_noalloc(const void *depth, int32_t nx, int32_t ny, int64_t row_pitch,
                                   int32_t precision, double dx, double *out_device, void *stream);
 
+/*
+ * Failure-detection check of the bounded device waits that every kernel's
+ * copy waits use: one thread waits on a shared-memory mbarrier that nothing
+ * arrives at, for budget_s seconds of device time (0 < budget_s <= 10), then
+ * gives up the way the step kernels do on a copy that never lands.  Returns
+ * FLOOD_ERR_TIMEOUT when the wait gave up (the expected outcome; the CUDA
+ * context stays usable), FLOOD_OK if it did not, FLOOD_ERR_ARG for a budget
+ * out of range, FLOOD_ERR_CUDA on a CUDA error.  Synchronous, on the current
+ * device's default stream; allocates and frees 4 bytes of device memory.
+ */
+flood_status flood_check_bounded_wait(double budget_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,8 @@ def _load():
     L = C.CDLL(path, mode=C.RTLD_GLOBAL)
     vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
     H = C.c_void_p
+    L.flood_check_bounded_wait.argtypes = [C.c_double]
+    L.flood_check_bounded_wait.restype = C.c_int
     L.flood_default_opts.argtypes = [C.POINTER(flood_opts)]
     L.flood_default_opts.restype = None
     L.flood_create.argtypes = [C.POINTER(flood_grid), vp, vp, C.POINTER(flood_bc_section), i32,

@@ -96,6 +96,21 @@ extern "C" void flood_default_opts(flood_opts *o)
     o->friction = 0;
 }
 
+extern "C" flood_status flood_check_bounded_wait(double budget_s)
+{
+    if (!(budget_s > 0.0 && budget_s <= 10.0)) return fail(nullptr, FLOOD_ERR_ARG, "budget_s must lie in (0, 10]");
+    int *d = nullptr;
+    int gave_up = -1;
+    cudaError_t e = cudaMalloc(&d, sizeof(int));
+    if (e != cudaSuccess) return fail(nullptr, FLOOD_ERR_CUDA, cudaGetErrorString(e));
+    e = launch_wait_probe((uint64_t)(budget_s * 1e9), d, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(&gave_up, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(nullptr, FLOOD_ERR_CUDA, cudaGetErrorString(e));
+    if (gave_up == 1) return fail(nullptr, FLOOD_ERR_TIMEOUT, "the bounded wait gave up");
+    return FLOOD_OK;
+}
+
 extern "C" const char *flood_version(void) { return "flood-gb300 0.1 (sm_103a)"; }
 
 namespace flood {

@@ -168,6 +168,10 @@ cudaError_t launch_adjoint_step(const AdjArgs<T> &a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_gn_out(const Geom &g, const double *gn, T *dst, cudaStream_t st);
 
+// One thread waits budget_ns of device time on an mbarrier nothing arrives at;
+// *gave_up (device) = 1 when the bounded wait gave up (the expected outcome).
+cudaError_t launch_wait_probe(uint64_t budget_ns, int *gave_up, cudaStream_t st);
+
 // Gather h at gauge cells into out[0..G).
 template <typename T>
 cudaError_t launch_gauges(const Geom &g, const T *h, const int64_t *cells, int G, double *out,

@@ -164,6 +164,13 @@ def test_coarsen_rejects_bad_arguments():
     assert "NULL" in F.flood_last_error(None)
 
 
+def test_bounded_wait_check_rejects_budgets_out_of_range():
+    import paper_2204_10323_gb300 as F
+    for bad in (0.0, -1.0, 11.0, float("nan")):
+        assert F.lib().flood_check_bounded_wait(bad) == F.ERR_ARG
+        assert "budget" in F.flood_last_error(None)
+
+
 def test_create_rejects_bad_friction_and_unsupported_kernels():
     import paper_2204_10323_gb300 as F
     for bad in (-1, 2, 7):

@@ -250,6 +250,21 @@ def test_gauge_series_matches_state_reads():
         np.testing.assert_array_equal(series[k], h[g[:, 1], g[:, 0]].astype(np.float64))
 
 
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """A device wait on an mbarrier nothing arrives at gives up after its budget
+    (the path a lost copy takes in every step kernel) and reports a timeout;
+    the context then runs a simulation as before."""
+    import time
+    Fm = F()
+    t0 = time.perf_counter()
+    assert Fm.lib().flood_check_bounded_wait(0.002) == Fm.ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert "gave up" in Fm.flood_last_error(None)
+    p = as_f32_problem(inputs.random_small(33, 17, 0))
+    o, V0, h, qx, qy, L = run_pair(p, 20, Fm.F32)
+    assert np.abs(h - o.h).max() < TOL32_H
+
+
 def test_nonfinite_depth_is_reported_and_sticky():
     Fm = F()
     p = inputs.random_small(20, 12, 2)
