@@ -303,11 +303,13 @@ flood_status launch_step_planes(flood_handle *h, int s, const void *const in[3],
 flood_status advance(flood_handle *h, int64_t n, const int64_t *gcells, int ng, double *gbuf,
                      const double *fixed_dt_log, bool epoch_open)
 {
+    NvtxRange range("flood: steps");
     const int E = h->geo.epoch_steps;
     int64_t done = 0;
     while (done < n) {
         int s = (int)(h->step % E);
         if (s == 0 && !(epoch_open && done == 0)) {
+            NvtxRange epoch("flood: epoch start (dt, Eq. 6 inflow)");
             const double *fdt = fixed_dt_log ? fixed_dt_log + done : nullptr;
             CK(launch_epoch_begin(h->geo, h->ctrl, h->t_list, E, fdt, h->stream));
             flood_status st = launch_inflow_epoch(h);

@@ -303,6 +303,7 @@ extern "C" flood_status flood_ensemble_set_kernel(flood_ensemble *e, int32_t ker
 extern "C" flood_status flood_ensemble_step(flood_ensemble *e, int64_t n_steps)
 {
     if (!e) return efail(nullptr, FLOOD_ERR_ARG, "ensemble is NULL");
+    NvtxRange range("flood: ensemble steps");
     if (n_steps < 0) return efail(e, FLOOD_ERR_ARG, "n_steps must be >= 0");
     for (flood_handle *h : e->members)
         if (h->sticky) return efail(e, FLOOD_ERR_STATE, "a member is in an error state");

@@ -10,6 +10,8 @@
 #include "flood.h"
 #include "flood_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 struct flood_adjoint_state;   // adjoint work buffers (flood_adjoint.cpp)
 
 struct flood_handle {
@@ -69,6 +71,16 @@ struct flood_handle {
 };
 
 namespace flood {
+
+// An NVTX range for the lifetime of the object: the runtime marks each stepping
+// call, each epoch's bookkeeping, each adjoint sweep and each ensemble step, so
+// a profiler's timeline shows them (no cost without a profiler attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 void *dev_alloc(flood_handle *h, size_t bytes);
 void dev_free(flood_handle *h, void *p);
