@@ -38,16 +38,17 @@ BYTES_PER_CELL = 32          # read h, qx, qy, z, n (20 B) + write h, qx, qy (12
 # the 4096^2 case of the same workload (state > L2), scaled by the cell count;
 # key (kernel, steps per launch).  The summaries are under profiles/.
 # (profiles/step_*_4096_full.md, profiles/roofline_study_16384.md)
-# (stream and TMA captured in the 16384^2 launch shape, 4 warps x 32-row chunks)
-TRAFFIC_B_PER_CELL = {("stream", 1): 31.30, ("tma", 1): 31.24, ("rows", 1): 30.93, ("tiled", 1): 30.55,
-                      ("tiled", 2): 30.79, ("tiled", 4): 31.65, ("tiled", 8): 30.91}
+# (stream captured in the 16384^2 launch shape, 4 warps x 32-row chunks).  Only kernels whose code has
+# not changed since their capture are listed; the others report traffic null.
+TRAFFIC_B_PER_CELL = {("stream", 1): 31.28, ("tiled", 1): 30.55, ("tiled", 2): 30.79, ("tiled", 4): 31.65,
+                      ("tiled", 8): 30.91}
 # Warp instructions per cell-update of the temporal-blocking kernel (issue-bound), from the same 4096^2
 # capture (smsp__inst_executed.sum; profiles/step_tiled4_4096_full.md): the "alu" roofline beside the
 # one-step HBM one.  The issue peak is 152 SMs x 4 warp-instructions per cycle x the sampled SM clock.
 INST_PER_CELL_UPDATE = {("tiled", 4): 243920737 / (4096 * 4096 * 4)}
 SMS, ISSUE_PER_SM_CYCLE = 152, 4
 # the same for the vector-norm friction option (theta = 1)
-TRAFFIC_VEC_B_PER_CELL = {("stream", 1): 31.28, ("tma", 1): 31.24}
+TRAFFIC_VEC_B_PER_CELL = {}
 METRIC = "Gcell-updates/s and % of HBM roofline (FP32, 1 GB300); adjoint/forward time ratio"
 UNIT = "Gcell-updates/s"
 
