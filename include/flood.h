@@ -27,8 +27,8 @@
  *
  * Every function returns a flood_status (0 = FLOOD_OK, < 0 = error) and never
  * aborts or traps.  Errors are sticky per handle: after FLOOD_ERR_NONFINITE,
- * FLOOD_ERR_CUDA or FLOOD_ERR_TIMEOUT, stepping calls return FLOOD_ERR_STATE
- * until flood_write_state() installs a new state.  The message of the last
+ * FLOOD_ERR_CFL, FLOOD_ERR_CUDA or FLOOD_ERR_TIMEOUT, stepping calls return
+ * FLOOD_ERR_STATE until flood_write_state() installs a new state.  The message of the last
  * error is available from flood_last_error().
  *
  * Memory and streams: the handle owns all device memory (taken from the
@@ -53,7 +53,9 @@ typedef enum {
     FLOOD_ERR_OOM = -2,          /* device allocation failed */
     FLOOD_ERR_CUDA = -3,         /* a CUDA call or kernel launch failed */
     FLOOD_ERR_NONFINITE = -4,    /* NaN or Inf depth detected at an epoch start */
-    FLOOD_ERR_CFL = -5,          /* reserved: CFL limit exceeded (counted in the ledger) */
+    FLOOD_ERR_CFL = -5,          /* an epoch ended with its dt above the Courant limit dx / sqrt(g h_max) of the
+                                    depth it ended with (reported at the next epoch start, sticky; also counted
+                                    in FLOOD_LEDGER_CFL_EXCEED) */
     FLOOD_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
     FLOOD_ERR_STATE = -7,        /* handle is in an error state */
     FLOOD_ERR_UNSUPPORTED = -8   /* option not available for this precision or size */
@@ -170,15 +172,21 @@ flood_status flood_create(const flood_grid *grid, const void *dem, const void *m
                           const flood_opts *opts, flood_handle **out);
 
 /* Advance n_steps >= 0 steps (Eq. 3-6, the time-step rule).  Asynchronous on the
- * handle's stream: a NaN/Inf found at an epoch start is reported by the next
- * flood_sync or flood_read. */
+ * handle's stream: a NaN/Inf depth or a broken Courant limit found at an
+ * epoch start is reported by the next flood_sync (flood_read of the ledger
+ * still returns the ledger and makes the error sticky). */
 flood_status flood_step(flood_handle *h, int64_t n_steps);
 
-/* Wait for the handle's stream and return its sticky status. */
+/* Wait for the handle's stream and return its sticky status.  No counterpart
+ * in the paper (its run loop is synchronous): the point where asynchronous
+ * errors of flood_step surface. */
 flood_status flood_sync(flood_handle *h);
 
 /*
- * Copy a field out.  dst holds `bytes` bytes (must equal the field's size:
+ * Copy a field out: the intermediate outputs of the paper's run loop
+ * (Appendix, "Code Structure": the simulation manager returns intermediate
+ * states of the simulation) and the mass ledger (not in the paper; the
+ * invariant of Eq. 4).  dst holds `bytes` bytes (must equal the field's size:
  * ny*nx, ny*(nx+1) or (ny+1)*nx elements, or FLOOD_LEDGER_LEN doubles);
  * dst_on_device != 0 means a device pointer on the handle's device.
  * Synchronous on the handle's stream.
@@ -186,7 +194,8 @@ flood_status flood_sync(flood_handle *h);
 flood_status flood_read(flood_handle *h, int32_t field, void *dst, size_t bytes, int32_t dst_on_device);
 
 /*
- * Install a state (initial condition or resume from a checkpoint): depth
+ * Install a state (Appendix, "Code Structure": the initial conditions the
+ * simulation manager hands to the cores; also a resume from a checkpoint): depth
  * (ny*nx), qx (ny*(nx+1)) and qy ((ny+1)*nx), host or device (src_on_device).
  * qx or qy may be NULL for zero fluxes.  Host input holding NaN or Inf is
  * rejected (FLOOD_ERR_ARG) and the state stays as it was (the check runs on
@@ -252,11 +261,12 @@ flood_status flood_adjoint_profile(flood_handle *h, int32_t enable);
 flood_status flood_adjoint_times(const flood_handle *h, double *reverse_ms, int64_t *reverse_steps,
                                  double *forward_ms, int64_t *forward_steps);
 
-/* Release all device memory of the handle (NULL is accepted). */
+/* Release all device memory of the handle (NULL is accepted).  Not in the
+ * paper: resource management of this library. */
 flood_status flood_destroy(flood_handle *h);
 
 /* Text of the handle's last error ("" if none); with NULL, the calling thread's
- * last flood_create error. */
+ * last flood_create error.  Not in the paper: error reporting of this library. */
 const char *flood_last_error(const flood_handle *h);
 
 /*
@@ -308,6 +318,96 @@ const char *flood_ensemble_last_error(const flood_ensemble *e);
  */
 flood_status flood_coarsen(int32_t precision, const void *src, int32_t nx, int32_t ny, int32_t factor, void *dst,
                            int32_t on_device, void *stream);
+
+/*
+ * Domain decomposition (Methods, "TPU Implementation": the grid is split into
+ * subgrids, one per core, and the borders of the discharge and then of the
+ * depth are exchanged between neighbouring subgrids every step; Results,
+ * "Scaling on TPU": 1 x N strips need the fewest exchanges).  The grid's ny
+ * rows are split into n_parts row strips of full width; part r owns rows
+ * [y0_r, y1_r) and stores rows [a_r, b_r) = [y0_r - halo, y1_r + halo) cut to
+ * the grid, i.e. `halo` rows of each neighbour.  After an exchange a part can
+ * take `halo` steps alone: one step spoils one more row next to each cut end,
+ * so after `halo` steps its own rows are still exactly what the whole grid
+ * gives (the same arithmetic on the same inputs, bit for bit).  Then the
+ * halo rows of h, qx and qy are copied in again from the neighbours' own rows.
+ * At each CFL epoch start every part takes the largest of the parts' depth
+ * maxima; the ledger is the sum of the parts' own terms (inflow volume, time
+ * and step count from part 0).  Inflow sections crossing a cut are solved
+ * whole by every part (Eq. 6 needs only the section cells' z and n, copied to
+ * each part at creation), so every part's boundary fluxes are the grid's.
+ */
+
+/* Row split of a decomposition (no device work; safe without a GPU).
+ * part_rows: 4*n_parts ints, for part r {y0, y1, a, b} (owned rows [y0, y1),
+ * stored rows [a, b), global row numbers): y0 = floor(r ny / n_parts).
+ * copies: the halo copies that refresh every part's halo rows, at most
+ * 6*n_parts entries (*n_copies: capacity in, count out; copies may be NULL
+ * to ask for the count).  Rows of h and qx are row numbers, rows of qy face-row
+ * numbers, both local to the source and destination parts' stored rows.
+ * FLOOD_ERR_ARG if n_parts < 1, halo < 1, or a strip would have fewer than
+ * max(halo, 1) rows. */
+typedef struct {
+    int32_t field;               /* FLOOD_FIELD_H, FLOOD_FIELD_QX or FLOOD_FIELD_QY */
+    int32_t src_part, src_row;   /* first row in the source part's stored rows */
+    int32_t dst_part, dst_row;   /* first row in the destination part's stored rows */
+    int32_t rows;                /* rows (face rows for qy) copied */
+} flood_halo_copy;
+flood_status flood_decomp_plan(int32_t ny, int32_t n_parts, int32_t halo, int32_t *part_rows,
+                               flood_halo_copy *copies, int32_t *n_copies);
+
+/* Ledger of a decomposed grid from its parts' ledgers (n_parts rows of
+ * FLOOD_LEDGER_LEN doubles, each the part's own terms as flood_read returns
+ * them for a part): volumes summed, h_max the largest, time, time step, step
+ * count and CFL count from part 0.  FLOOD_ERR_STATE if the parts disagree on
+ * time, time step or step count.  No device work; safe without a GPU. */
+flood_status flood_decomp_combine_ledgers(int32_t n_parts, const double *part_ledgers, double *out);
+
+/* Create a grid of n_parts row strips on the current device (arguments as
+ * for flood_create, plus n_parts and halo >= 1, the steps between exchanges).
+ * The parts run the kernel family that flood_create chooses for the whole
+ * grid; FP64 grids use the reference kernel.  use_graph is ignored.  All
+ * parts share opts->stream.  Errors: flood_last_error(NULL). */
+typedef struct flood_decomp flood_decomp;
+flood_status flood_decomp_create(const flood_grid *grid, const void *dem, const void *manning,
+                                 const flood_bc_section *sections, int32_t n_sections, const flood_opts *opts,
+                                 int32_t n_parts, int32_t halo, flood_decomp **out);
+/* Advance every part n_steps >= 0 steps (exchanges and epoch starts included). */
+flood_status flood_decomp_step(flood_decomp *d, int64_t n_steps);
+/* flood_read of the whole grid, assembled from the parts' own rows. */
+flood_status flood_decomp_read(flood_decomp *d, int32_t field, void *dst, size_t bytes, int32_t dst_on_device);
+/* flood_write_state of the whole grid: each part takes its stored rows. */
+flood_status flood_decomp_write_state(flood_decomp *d, const void *depth, const void *qx, const void *qy,
+                                      int32_t src_on_device);
+/* flood_sync of every part. */
+flood_status flood_decomp_sync(flood_decomp *d);
+/* Part k's handle (stored rows only; for flood_read; stepping calls on it
+ * return FLOOD_ERR_STATE), or NULL. */
+flood_handle *flood_decomp_part(flood_decomp *d, int32_t k);
+flood_status flood_decomp_destroy(flood_decomp *d);
+const char *flood_decomp_last_error(const flood_decomp *d);
+
+/*
+ * Debugging aids for tests of the failure paths (not in the paper).
+ *
+ * flood_debug_fail_alloc_after(n): the device allocation the library makes
+ * after n more successful ones (n = 0: the next one) fails as if the device
+ * were out of memory, in any handle, ensemble or decomposition of the process;
+ * the hook then turns itself off.  n < 0 turns it off.  Calls that hit it
+ * return FLOOD_ERR_OOM and release what they had allocated.
+ * flood_debug_alloc_count(): device allocations the library has made so far.
+ *
+ * flood_debug_padding(h, fill, bad): the pitch padding of the handle's grid
+ * planes (both state buffers, z and n: the elements past each row's last
+ * element up to the row pitch, which no kernel may write and whose values no
+ * result may depend on).  fill != 0: set every padding element to a NaN with a
+ * fixed bit pattern (note that flood_write_state without qx or qy zeroes those
+ * planes whole).  fill == 0: *bad = the number of padding elements whose bits
+ * differ from that pattern.  Synchronous.
+ */
+void flood_debug_fail_alloc_after(int64_t n);
+int64_t flood_debug_alloc_count(void);
+flood_status flood_debug_padding(flood_handle *h, int32_t fill, int64_t *bad);
 
 /* Library version string. */
 const char *flood_version(void);

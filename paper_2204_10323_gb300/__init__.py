@@ -55,6 +55,11 @@ class flood_opts(C.Structure):
                 ("friction", C.c_int32)]
 
 
+class flood_halo_copy(C.Structure):
+    _fields_ = [("field", C.c_int32), ("src_part", C.c_int32), ("src_row", C.c_int32), ("dst_part", C.c_int32),
+                ("dst_row", C.c_int32), ("rows", C.c_int32)]
+
+
 _lib = None
 LIB_PATH = None
 
@@ -110,6 +115,28 @@ def _load():
     L.flood_ensemble_destroy.argtypes = [vp]
     L.flood_ensemble_last_error.argtypes = [vp]
     L.flood_ensemble_last_error.restype = C.c_char_p
+    L.flood_decomp_plan.argtypes = [i32, i32, i32, C.POINTER(i32), C.POINTER(flood_halo_copy), C.POINTER(i32)]
+    L.flood_decomp_combine_ledgers.argtypes = [i32, C.POINTER(dbl), C.POINTER(dbl)]
+    L.flood_decomp_create.argtypes = [C.POINTER(flood_grid), vp, vp, C.POINTER(flood_bc_section), i32,
+                                      C.POINTER(flood_opts), i32, i32, C.POINTER(vp)]
+    L.flood_decomp_step.argtypes = [vp, i64]
+    L.flood_decomp_read.argtypes = [vp, i32, vp, C.c_size_t, i32]
+    L.flood_decomp_write_state.argtypes = [vp, vp, vp, vp, i32]
+    L.flood_decomp_sync.argtypes = [vp]
+    L.flood_decomp_part.argtypes = [vp, i32]
+    L.flood_decomp_part.restype = vp
+    L.flood_decomp_destroy.argtypes = [vp]
+    L.flood_decomp_last_error.argtypes = [vp]
+    L.flood_decomp_last_error.restype = C.c_char_p
+    L.flood_debug_fail_alloc_after.argtypes = [i64]
+    L.flood_debug_fail_alloc_after.restype = None
+    L.flood_debug_alloc_count.argtypes = []
+    L.flood_debug_alloc_count.restype = i64
+    L.flood_debug_padding.argtypes = [H, i32, C.POINTER(i64)]
+    L.flood_debug_padding.restype = C.c_int
+    for name in ("flood_decomp_plan", "flood_decomp_combine_ledgers", "flood_decomp_create", "flood_decomp_step",
+                 "flood_decomp_read", "flood_decomp_write_state", "flood_decomp_sync", "flood_decomp_destroy"):
+        getattr(L, name).restype = C.c_int
     for name in ("flood_ensemble_create", "flood_ensemble_set_launch", "flood_ensemble_set_kernel",
                  "flood_ensemble_step", "flood_ensemble_destroy"):
         getattr(L, name).restype = C.c_int
@@ -204,6 +231,22 @@ def flood_volume_noalloc(depth_ptr, nx: int, ny: int, row_pitch: int, precision:
                                       out_ptr, stream_ptr), None)
 
 
+def flood_debug_fail_alloc_after(n: int) -> None:
+    """Make the library's device allocation after n more successful ones fail (n < 0: off)."""
+    lib().flood_debug_fail_alloc_after(int(n))
+
+
+def flood_debug_alloc_count() -> int:
+    return int(lib().flood_debug_alloc_count())
+
+
+def flood_debug_padding(h, fill: bool) -> int:
+    """Poison the pitch padding of a handle's planes (fill), or count padding elements that changed."""
+    bad = C.c_int64(0)
+    _check(lib().flood_debug_padding(h, int(fill), C.byref(bad)), h)
+    return int(bad.value)
+
+
 # ------------------------------------------------------------------ convenience wrapper
 def coarsen(field, factor: int):
     """Block mean of a (ny, nx) float32/float64 field (NumPy array or CUDA tensor)
@@ -240,6 +283,34 @@ def _ptr(a):
     raise TypeError(type(a))
 
 
+def _opts_for(problem, kernel=KERNEL_AUTO, steps_per_launch=0, tile=(0, 0), use_graph=False, stream=None):
+    po = problem.opts
+    o = default_opts()
+    o.g, o.h_dry, o.cfl_alpha, o.dt_cap, o.dt_const = po.g, po.h_dry, po.cfl_alpha, po.dt_cap, po.dt_const
+    o.dt_mode, o.epoch_steps, o.bc_form = po.dt_mode, po.epoch_steps, po.bc_form
+    o.theta = getattr(po, "theta", 1.0)
+    o.friction = getattr(po, "friction", 0)
+    o.kernel, o.steps_per_launch = kernel, steps_per_launch
+    o.tile_x, o.tile_y = tile
+    o.use_graph = int(use_graph)
+    o.stream = None if stream is None else C.c_void_p(stream.cuda_stream)
+    return o
+
+
+def _sections_for(problem, keep: list):
+    """ctypes array of the problem's sections (tables appended to keep)."""
+    secs = (flood_bc_section * max(1, len(problem.sections)))()
+    for k, s in enumerate(problem.sections):
+        t = np.ascontiguousarray(s.t_s if s.t_s is not None else np.zeros(1), np.float64)
+        q = np.ascontiguousarray(s.q_m3s if s.q_m3s is not None else np.zeros(1), np.float64)
+        keep += [t, q]
+        secs[k] = flood_bc_section(s.side, s.kind, s.frac_start, s.frac_end, s.slope,
+                                   t.ctypes.data_as(C.POINTER(C.c_double)),
+                                   q.ctypes.data_as(C.POINTER(C.c_double)),
+                                   t.size if s.kind == INFLOW else 0)
+    return secs
+
+
 class Sim:
     """One simulation handle.  ``problem`` is an ``inputs.Problem``-like object
     (nx, ny, dx, z, n, sections, opts, h0/qx0/qy0)."""
@@ -250,27 +321,10 @@ class Sim:
         self.precision = precision
         self.dtype = np.float32 if precision == F32 else np.float64
         self.nx, self.ny = problem.nx, problem.ny
-        po = problem.opts
-        o = default_opts()
-        o.g, o.h_dry, o.cfl_alpha, o.dt_cap, o.dt_const = po.g, po.h_dry, po.cfl_alpha, po.dt_cap, po.dt_const
-        o.dt_mode, o.epoch_steps, o.bc_form = po.dt_mode, po.epoch_steps, po.bc_form
-        o.theta = getattr(po, "theta", 1.0)
-        o.friction = getattr(po, "friction", 0)
-        o.kernel, o.steps_per_launch = kernel, steps_per_launch
-        o.tile_x, o.tile_y = tile
-        o.use_graph = int(use_graph)
-        o.stream = None if stream is None else C.c_void_p(stream.cuda_stream)
+        o = _opts_for(problem, kernel, steps_per_launch, tile, use_graph, stream)
         self.opts = o
-        secs = (flood_bc_section * max(1, len(problem.sections)))()
         self._keep = []
-        for k, s in enumerate(problem.sections):
-            t = np.ascontiguousarray(s.t_s if s.t_s is not None else np.zeros(1), np.float64)
-            q = np.ascontiguousarray(s.q_m3s if s.q_m3s is not None else np.zeros(1), np.float64)
-            self._keep += [t, q]
-            secs[k] = flood_bc_section(s.side, s.kind, s.frac_start, s.frac_end, s.slope,
-                                       t.ctypes.data_as(C.POINTER(C.c_double)),
-                                       q.ctypes.data_as(C.POINTER(C.c_double)),
-                                       t.size if s.kind == INFLOW else 0)
+        secs = _sections_for(problem, self._keep)
         z = np.ascontiguousarray(problem.z, self.dtype)
         n = np.ascontiguousarray(problem.n, self.dtype)
         self.grid = flood_grid(self.nx, self.ny, float(problem.dx), precision)
@@ -431,6 +485,9 @@ class Ensemble:
         o.theta = getattr(po, "theta", 1.0)
         o.friction = getattr(po, "friction", 0)
         o.stream = None if stream is None else C.c_void_p(stream.cuda_stream)
+        import torch
+        # the stream every launch of the ensemble goes to (the current one at creation if none is given)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._keep = []
         grids = (flood_grid * n)()
         dems = (C.c_void_p * n)()
@@ -484,3 +541,128 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ domain decomposition
+def _dec_check(st: int, d=None):
+    if st != OK:
+        raise FloodError(st, lib().flood_decomp_last_error(d).decode(errors="replace"))
+
+
+def flood_decomp_plan(ny: int, n_parts: int, halo: int):
+    """Row split and halo copies of a decomposition: (rows (n_parts, 4) int32 array
+    of y0, y1, a, b; list of (field, src_part, src_row, dst_part, dst_row, rows))."""
+    rows = np.zeros((max(n_parts, 1), 4), np.int32)
+    n = C.c_int32(0)
+    rp = rows.ctypes.data_as(C.POINTER(C.c_int32))
+    _dec_check(lib().flood_decomp_plan(int(ny), int(n_parts), int(halo), rp, None, C.byref(n)))
+    arr = (flood_halo_copy * max(n.value, 1))()
+    _dec_check(lib().flood_decomp_plan(int(ny), int(n_parts), int(halo), rp, arr, C.byref(n)))
+    copies = [(c.field, c.src_part, c.src_row, c.dst_part, c.dst_row, c.rows) for c in arr[:n.value]]
+    return rows, copies
+
+
+def flood_decomp_combine_ledgers(part_ledgers: np.ndarray) -> np.ndarray:
+    """Whole-grid ledger (FLOOD_LEDGER_LEN doubles) from the parts' ledgers (n_parts rows)."""
+    L = np.ascontiguousarray(part_ledgers, np.float64)
+    out = np.zeros(len(LEDGER_KEYS), np.float64)
+    _dec_check(lib().flood_decomp_combine_ledgers(L.shape[0], L.ctypes.data_as(C.POINTER(C.c_double)),
+                                                   out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+class Decomp:
+    """A grid split into n_parts row strips with `halo` rows of overlap, advanced
+    together with a halo exchange every `halo` steps (see include/flood.h).
+    Holds a flood_decomp (not a flood_handle): only flood_decomp_* calls take it."""
+
+    def __init__(self, problem, n_parts: int, halo: int, precision: int = F32, kernel: int = KERNEL_AUTO,
+                 steps_per_launch: int = 0, tile=(0, 0), stream=None):
+        self.prob = problem
+        self.precision = precision
+        self.dtype = np.float32 if precision == F32 else np.float64
+        self.nx, self.ny = problem.nx, problem.ny
+        self.n_parts, self.halo = n_parts, halo
+        o = _opts_for(problem, kernel, steps_per_launch, tile, False, stream)
+        self.opts = o
+        self._keep = []
+        secs = _sections_for(problem, self._keep)
+        z = np.ascontiguousarray(problem.z, self.dtype)
+        n = np.ascontiguousarray(problem.n, self.dtype)
+        self.grid = flood_grid(self.nx, self.ny, float(problem.dx), precision)
+        d = C.c_void_p()
+        _dec_check(lib().flood_decomp_create(C.byref(self.grid), C.c_void_p(z.ctypes.data),
+                                             C.c_void_p(n.ctypes.data), secs, len(problem.sections), C.byref(o),
+                                             int(n_parts), int(halo), C.byref(d)))
+        self.h = d
+        if problem.h0 is not None or problem.qx0 is not None or problem.qy0 is not None:
+            self.write_state(*problem.initial_state(self.dtype))
+
+    def write_state(self, h, qx=None, qy=None):
+        arrs = [None if a is None else (np.ascontiguousarray(a, self.dtype) if isinstance(a, np.ndarray) else a)
+                for a in (h, qx, qy)]
+        ptrs = [_ptr(a) for a in arrs]
+        dev = max(p[1] for p in ptrs if p[0] is not None)
+        _dec_check(lib().flood_decomp_write_state(self.h, ptrs[0][0], ptrs[1][0], ptrs[2][0], dev), self.h)
+
+    def read(self, field: int):
+        shape = {FIELD_H: (self.ny, self.nx), FIELD_QX: (self.ny, self.nx + 1), FIELD_QY: (self.ny + 1, self.nx),
+                 FIELD_Z: (self.ny, self.nx), FIELD_N: (self.ny, self.nx)}[field]
+        out = np.empty(shape, self.dtype)
+        _dec_check(lib().flood_decomp_read(self.h, field, C.c_void_p(out.ctypes.data), out.nbytes, 0), self.h)
+        return out
+
+    def ledger(self):
+        out = np.zeros(len(LEDGER_KEYS), np.float64)
+        _dec_check(lib().flood_decomp_read(self.h, FIELD_LEDGER, C.c_void_p(out.ctypes.data), out.nbytes, 0),
+                   self.h)
+        return dict(zip(LEDGER_KEYS, out.tolist()))
+
+    def state(self):
+        return self.read(FIELD_H), self.read(FIELD_QX), self.read(FIELD_QY)
+
+    def part_ledger(self, k: int):
+        """Part k's own ledger terms (FLOOD_LEDGER_LEN doubles)."""
+        out = np.zeros(len(LEDGER_KEYS), np.float64)
+        flood_read(lib().flood_decomp_part(self.h, int(k)), FIELD_LEDGER, C.c_void_p(out.ctypes.data), out.nbytes, 0)
+        return out
+
+    def step(self, n_steps: int = 1, check: bool = False):
+        _dec_check(lib().flood_decomp_step(self.h, int(n_steps)), self.h)
+        if check:
+            self.sync()
+
+    def sync(self):
+        _dec_check(lib().flood_decomp_sync(self.h), self.h)
+
+    def part_handle(self, k: int):
+        return C.c_void_p(lib().flood_decomp_part(self.h, int(k)))
+
+    def part_view(self, k: int) -> "_PartView":
+        """Part k's stored rows (its own rows and its halo rows) as a read-only Sim."""
+        rows, _ = flood_decomp_plan(self.ny, self.n_parts, self.halo)
+        return _PartView(self.part_handle(k), self.nx, int(rows[k, 3] - rows[k, 2]), self.precision)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lib().flood_decomp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _PartView(Sim):
+    """View of one part's handle (owned by its decomposition; stepping it is refused)."""
+
+    def __init__(self, handle, nx: int, ny: int, precision: int):
+        self.h = handle
+        self.nx, self.ny = nx, ny
+        self.precision = precision
+        self.dtype = np.float32 if precision == F32 else np.float64
+
+    def close(self):
+        self.h = None

@@ -82,7 +82,8 @@ def tune_ensemble(ens, candidates: Optional[Iterable[Shape]] = None, trial_steps
         apply(ens, tuple(cache[key]["shape"]))
         return dict(cache[key], cached=True)
     cands = list(candidates or default_candidates(E))
-    stream = torch.cuda.current_stream()
+    # the ensemble's work runs on its own stream: the events must be recorded there
+    stream = getattr(ens, "stream", None) or torch.cuda.current_stream()
     trials = []
     for shape in cands:
         apply(ens, shape)

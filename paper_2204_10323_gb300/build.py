@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import json
 import os
 import shutil
 import subprocess
@@ -76,24 +77,29 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tinc, tlib, abi = _torch_paths()
     jobs = []
     objs = []
+    database = []                  # compile_commands.json: the command of every translation unit
     for src in cu:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         objs.append(obj)
+        cmd = [nvcc, "-c", src, "-o", obj, "-O3", "-std=c++17", "-lineinfo", *ARCH,
+               "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE, "-Xptxas", "-v"]
+        if os.path.basename(src) in NO_FMAD:
+            cmd += ["-fmad=false"]
+        database.append({"directory": BUILD, "file": src, "arguments": cmd})
         if force or _stale(obj, src, hdr_time):
-            cmd = [nvcc, "-c", src, "-o", obj, "-O3", "-std=c++17", "-lineinfo", *ARCH,
-                   "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE, "-Xptxas", "-v"]
-            if os.path.basename(src) in NO_FMAD:
-                cmd += ["-fmad=false"]
             jobs.append(cmd)
     for src in cpp:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         objs.append(obj)
+        cmd = ["g++", "-c", src, "-o", obj, "-O2", "-std=c++17", "-fPIC", f"-D_GLIBCXX_USE_CXX11_ABI={abi}",
+               "-I", CSRC, "-I", INCLUDE, "-I", os.path.join(cuda, "include")]
+        for p in tinc:
+            cmd += ["-isystem", p]
+        database.append({"directory": BUILD, "file": src, "arguments": cmd})
         if force or _stale(obj, src, hdr_time):
-            cmd = ["g++", "-c", src, "-o", obj, "-O2", "-std=c++17", "-fPIC", f"-D_GLIBCXX_USE_CXX11_ABI={abi}",
-                   "-I", CSRC, "-I", INCLUDE, "-I", os.path.join(cuda, "include")]
-            for p in tinc:
-                cmd += ["-isystem", p]
             jobs.append(cmd)
+    with open(os.path.join(BUILD, "compile_commands.json"), "w") as f:
+        json.dump(database, f, indent=1)
     logs = []
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:

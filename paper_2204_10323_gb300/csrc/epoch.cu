@@ -15,7 +15,12 @@ __device__ void epoch_begin_body(const Geom &G, Ctrl *ctrl, double *t_list, int 
 {
     double hmax = __longlong_as_double((long long)ctrl->hmax_bits);
     if (!isfinite(hmax)) ctrl->status |= kStatusNonfinite;
-    if (ctrl->dt > 0.0 && hmax > 0.0 && ctrl->dt * sqrt(G.g * hmax) > G.dx) ctrl->cfl_exceed += 1.0;
+    // the epoch that just ended: its dt against the Courant limit of the depth it ended with (not for
+    // replays of a logged schedule, whose control block is restored after them)
+    if (!fixed_dt && ctrl->dt > 0.0 && hmax > 0.0 && ctrl->dt * sqrt(G.g * hmax) > G.dx) {
+        ctrl->cfl_exceed += 1.0;
+        ctrl->status |= kStatusCfl;
+    }
     double dt;
     if (fixed_dt) dt = *fixed_dt;
     else if (G.dt_mode == 1) dt = G.dt_const;
@@ -346,6 +351,23 @@ __global__ void gauges_kernel(Geom G, const T *h, const int64_t *cells, int ng, 
 
 }  // namespace
 
+// Parts of a decomposed grid: the largest of their running depth maxima
+// (bits of non-negative doubles, or a NaN's larger bits) into every part, so
+// that each part's epoch start takes the whole grid's h_max.
+__global__ void hmax_allreduce_kernel(Ctrl *const *ctrls, int n)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long m = 0ull;
+    for (int k = 0; k < n; k++) m = ctrls[k]->hmax_bits > m ? ctrls[k]->hmax_bits : m;
+    for (int k = 0; k < n; k++) ctrls[k]->hmax_bits = m;
+}
+
+cudaError_t launch_hmax_allreduce(Ctrl *const *ctrls, int n, cudaStream_t st)
+{
+    hmax_allreduce_kernel<<<1, 32, 0, st>>>(ctrls, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_epoch_begin(const Geom &g, Ctrl *ctrl, double *t_list, int E, const double *fixed_dt,
                                cudaStream_t st)
 {
@@ -414,6 +436,36 @@ cudaError_t launch_nonfinite(const T *a, int rows, int cols, int pitch, int *fla
 {
     const int blocks = rows < 152 * 8 ? rows : 152 * 8;
     nonfinite_kernel<T><<<blocks, 256, 0, st>>>(a, rows, cols, pitch, flag);
+    return cudaGetLastError();
+}
+
+// Poison of the pitch padding: quiet NaNs with a fixed payload, compared by bits.
+template <typename U>
+__global__ void padding_kernel(U *a, int rows, int cols, int pitch, U poison, int fill, unsigned long long *count)
+{
+    const int w = pitch - cols;
+    unsigned long long bad = 0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < (long long)rows * w;
+         k += (long long)gridDim.x * blockDim.x) {
+        U *p = a + (size_t)(k / w) * pitch + cols + (k % w);
+        if (fill) *p = poison;
+        else bad += *p != poison;
+    }
+    if (!fill && bad) atomicAdd(count, bad);
+}
+
+cudaError_t launch_padding(void *a, size_t esz, int rows, int cols, int pitch, bool fill,
+                           unsigned long long *count, cudaStream_t st)
+{
+    if (pitch <= cols || rows <= 0) return cudaSuccess;
+    const long long n = (long long)rows * (pitch - cols);
+    const int blocks = (int)(n < 152 * 8 * 256 ? (n + 255) / 256 : 152 * 8);
+    if (esz == 4)
+        padding_kernel<unsigned><<<blocks, 256, 0, st>>>((unsigned *)a, rows, cols, pitch, 0x7fc0deadu, fill ? 1 : 0,
+                                                         count);
+    else
+        padding_kernel<unsigned long long><<<blocks, 256, 0, st>>>((unsigned long long *)a, rows, cols, pitch,
+                                                                   0x7ff80000deadbeefull, fill ? 1 : 0, count);
     return cudaGetLastError();
 }
 

@@ -220,7 +220,7 @@ __device__ __forceinline__ float boundary_fast_at(const StepArgs<float> &a, int 
     float inward = (side == 0 || side == 2) ? 1.0f : -1.0f;
     if (type == kBcInflow) return inward * a.inflow_q[(size_t)step * a.n_slots + a.bc.slot[off + k]];
     float q = outflow_fast(h, a.bc.sqrtS_f[off + k], n, G.dx_f, G.h_dry_f, G.bc_form);
-    vout += (double)q * G.dx;
+    if (type == kBcOutflow) vout += (double)q * G.dx;
     return -inward * q;
 }
 
@@ -237,7 +237,7 @@ __device__ __forceinline__ float boundary_fast_flux(const StepArgs<float> &a, in
     float inward = (side == 0 || side == 2) ? 1.0f : -1.0f;
     if (type == kBcInflow) return inward * a.inflow_q[(size_t)step * a.n_slots + a.bc.slot[off + k]];
     float q = outflow_fast(h, a.bc.sqrtS_f[off + k], n, G.dx_f, G.h_dry_f, G.bc_form);
-    qout += q;
+    if (type == kBcOutflow) qout += q;
     return -inward * q;
 }
 

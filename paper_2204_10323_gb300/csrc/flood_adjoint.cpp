@@ -357,6 +357,7 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
                                       void *dLdn_out, void *dLdh0_out, int32_t out_on_device)
 {
     if (!h) return fail(nullptr, FLOOD_ERR_ARG, "handle is NULL");
+    if (h->part) return fail(h, FLOOD_ERR_STATE, "a part of a decomposed grid is stepped by its decomposition");
     NvtxRange range("flood: adjoint sweep");
     if (n_steps < 1 || n_gauges < 0 || n_checkpoints < 1 || !dLdn_out || (n_gauges > 0 && (!gauge_cells || !dLdh)))
         return fail(h, FLOOD_ERR_ARG, "bad adjoint arguments");

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,20 +25,36 @@ namespace {
 
 thread_local std::string g_create_error;
 
+// Failure injection (flood_debug_fail_alloc_after): allocations left before the
+// one that fails, -1 when off; and the number of allocations made so far.
+std::atomic<int64_t> g_fail_countdown{-1};
+std::atomic<int64_t> g_alloc_count{0};
+
 }  // namespace
 
 // ------------------------------------------------------------------ helpers
 namespace flood {
 
-void *dev_alloc(flood_handle *h, size_t bytes)
+void *raw_device_alloc(size_t bytes, cudaStream_t st)
 {
-    if (bytes == 0) bytes = 16;
+    int64_t n = g_fail_countdown.load();
+    while (n >= 0 && !g_fail_countdown.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 0) return nullptr;                 // the injected failure (the hook is now off)
     void *p = nullptr;
     try {
-        p = c10::cuda::CUDACachingAllocator::raw_alloc_with_stream(bytes, h->stream);
+        p = c10::cuda::CUDACachingAllocator::raw_alloc_with_stream(bytes, st);
     } catch (...) {
         p = nullptr;
     }
+    if (p) g_alloc_count++;
+    return p;
+}
+
+void *dev_alloc(flood_handle *h, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = raw_device_alloc(bytes, h->stream);
     if (p) h->allocations.push_back(p);
     return p;
 }
@@ -54,7 +71,8 @@ flood_status fail(flood_handle *h, flood_status st, const std::string &msg)
 {
     if (h) {
         h->err = msg;
-        if (st == FLOOD_ERR_CUDA || st == FLOOD_ERR_NONFINITE || st == FLOOD_ERR_TIMEOUT) h->sticky = st;
+        if (st == FLOOD_ERR_CUDA || st == FLOOD_ERR_NONFINITE || st == FLOOD_ERR_TIMEOUT || st == FLOOD_ERR_CFL)
+            h->sticky = st;
     } else {
         g_create_error = msg;
     }
@@ -187,13 +205,15 @@ flood_status launch_inflow_epoch(flood_handle *h)
 {
     if (h->n_in == 0) return FLOOD_OK;
     int E = h->geo.epoch_steps;
+    // the section cells' z and n: in the grid's own planes, or a part's copies of them
+    const void *z = h->sec_z ? h->sec_z : h->z, *n = h->sec_z ? h->sec_n : h->n;
     if (h->prec == FLOOD_F32)
         CK(launch_inflow<float>(h->geo, h->secs_dev, h->n_in, h->sec_cells, nullptr, h->tab_t, h->tab_q,
-                                (const float *)h->z, (const float *)h->n, h->t_list, E, (float *)h->inflow_q,
+                                (const float *)z, (const float *)n, h->t_list, E, (float *)h->inflow_q,
                                 h->n_slots, h->inflow_Q, h->inflow_W, h->stream));
     else
         CK(launch_inflow<double>(h->geo, h->secs_dev, h->n_in, h->sec_cells, nullptr, h->tab_t, h->tab_q,
-                                 (const double *)h->z, (const double *)h->n, h->t_list, E, (double *)h->inflow_q,
+                                 (const double *)z, (const double *)n, h->t_list, E, (double *)h->inflow_q,
                                  h->n_slots, h->inflow_Q, h->inflow_W, h->stream));
     return FLOOD_OK;
 }
@@ -221,7 +241,7 @@ StepArgs<T> make_args(flood_handle *h, int s, int k_steps, int want_hmax, const 
     a.inflow_q = (const T *)h->inflow_q;
     a.n_slots = h->n_slots;
     a.inflow_Q = h->inflow_Q;
-    a.n_inflow_sec = h->n_in;
+    a.n_inflow_sec = h->book_vin ? h->n_in : 0;    // sections whose inflow volume this launch books
     a.t_list = h->t_list;
     a.ctrl = h->ctrl;
     a.s = s;
@@ -336,6 +356,8 @@ flood_status check_device_status(flood_handle *h)
     CK(cudaStreamSynchronize(h->stream));
     if (c.status & kStatusNonfinite) return fail(h, FLOOD_ERR_NONFINITE, "NaN or Inf depth at an epoch start");
     if (c.status & kStatusTimeout) return fail(h, FLOOD_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (c.status & kStatusCfl)
+        return fail(h, FLOOD_ERR_CFL, "an epoch's time step broke the Courant limit dx / sqrt(g h_max) at its end");
     return FLOOD_OK;
 }
 
@@ -416,9 +438,40 @@ static int check_finite_host(const void *a, size_t n, int prec)
     return 1;
 }
 
-extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, const void *manning,
-                                     const flood_bc_section *sections, int32_t n_sections,
-                                     const flood_opts *opts, flood_handle **out)
+namespace flood {
+
+// AUTO: the temporal-blocking kernel with K = 4 where it applies (Eq. 3 as
+// printed, E a multiple of 4, no explicit launch shape), else the tensor-tile
+// kernel below 2^27 cells or with vector-norm friction (whose next-row
+// look-ahead two-row tiles serve half of the time), else the row-staged stream
+// kernel.  Measured on the fractal workload (us per step): tiled K = 4 / TMA /
+// stream 15.2 / 16.5 / 16.7 at 1024^2, 31.1 / 33.9 / 37.5 at 2048^2, 92.6 /
+// 102.3 / 105.5 at 4096^2, 339 / 348 / 350 at 8192^2, 1181 / 1301 / 1288 at
+// 16384^2; with vector friction TMA / stream 1455 / 1629 at 16384^2.  All
+// three are bitwise equal.
+int auto_kernel(const flood_opts &o, int nx, int ny)
+{
+    const bool tiled = o.theta == 1.0 && o.friction == 0 && o.epoch_steps % 4 == 0 && o.tile_x == 0 && o.tile_y == 0;
+    if (tiled) return FLOOD_KERNEL_TILED;
+    return (o.friction != 0 || (int64_t)nx * ny < ((int64_t)1 << 27)) ? FLOOD_KERNEL_TMA : FLOOD_KERNEL_STREAM;
+}
+
+flood_status refresh_hmax_window(flood_handle *h)
+{
+    Geom g = h->geo;
+    g.ny = h->geo.led_j1 - h->geo.led_j0;
+    const size_t off = (size_t)h->geo.led_j0 * h->geo.pitch * h->esz;
+    CK(cudaMemsetAsync(&h->ctrl->hmax_bits, 0, sizeof(unsigned long long), h->stream));
+    if (g.ny <= 0) return FLOOD_OK;
+    const char *base = (const char *)h->h[h->cur] + off;
+    if (h->prec == FLOOD_F32) CK(launch_hmax<float>(g, (const float *)base, h->ctrl, h->stream));
+    else CK(launch_hmax<double>(g, (const double *)base, h->ctrl, h->stream));
+    return FLOOD_OK;
+}
+
+flood_status create_handle(const flood_grid *grid, const void *dem, const void *manning,
+                           const flood_bc_section *sections, int32_t n_sections, const flood_opts *opts,
+                           const PartSpec *part, flood_handle **out)
 {
     if (!out) return fail(nullptr, FLOOD_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -438,6 +491,12 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
             if (!(v > 0.0)) return fail(nullptr, FLOOD_ERR_ARG, "manning must be > 0");
         }
     }
+    // the rows this handle stores: all of them, or a part's global rows [a, b)
+    const int ny_all = grid->ny;
+    const int ra = part ? part->a : 0, rb = part ? part->b : ny_all;
+    if (part && !(part->ny_global == ny_all && 0 <= ra && ra <= part->y0 && part->y0 < part->y1 &&
+                  part->y1 <= rb && rb <= ny_all))
+        return fail(nullptr, FLOOD_ERR_ARG, "bad part rows");
     flood_handle *h = new flood_handle();
     h->prec = grid->precision;
     h->esz = esz;
@@ -451,7 +510,7 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
     h->stream = o.stream ? (cudaStream_t)o.stream : c10::cuda::getCurrentCUDAStream(dev).stream();
     Geom &G = h->geo;
     G.nx = grid->nx;
-    G.ny = grid->ny;
+    G.ny = rb - ra;
     G.pitch = (grid->nx + 1 + 31) / 32 * 32;
     G.bc_form = o.bc_form;
     G.theta = o.theta;
@@ -466,25 +525,13 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
     G.dt_const = o.dt_const;
     G.dt_mode = o.dt_mode;
     G.epoch_steps = o.epoch_steps;
+    G.led_j0 = part ? part->y0 - ra : 0;
+    G.led_j1 = part ? part->y1 - ra : G.ny;
     const int E = o.epoch_steps;
+    h->part = part != nullptr;
+    h->book_vin = !part || part->index == 0;
 
-    // kernel family and temporal-blocking depth.  AUTO: the temporal-blocking
-    // kernel with K = 4 where it applies (Eq. 3 as printed, E a multiple of 4, no
-    // explicit launch shape), else the tensor-tile kernel below 2^27 cells or with
-    // vector-norm friction (whose next-row look-ahead two-row tiles serve half of
-    // the time), else the row-staged stream kernel.  Measured on the fractal
-    // workload (us per step): tiled K = 4 / TMA / stream 15.2 / 16.5 / 16.7 at
-    // 1024^2, 31.1 / 33.9 / 37.5 at 2048^2, 92.6 / 102.3 / 105.5 at 4096^2,
-    // 339 / 348 / 350 at 8192^2, 1181 / 1301 / 1288 at 16384^2; with vector
-    // friction TMA / stream 1455 / 1629 at 16384^2.  All three are bitwise equal.
-    if (o.kernel == FLOOD_KERNEL_AUTO) {
-        const bool tiled = o.theta == 1.0 && o.friction == 0 && E % 4 == 0 && o.tile_x == 0 && o.tile_y == 0;
-        if (tiled) h->kernel = FLOOD_KERNEL_TILED;
-        else h->kernel = (o.friction != 0 || (int64_t)grid->nx * grid->ny < ((int64_t)1 << 27)) ? FLOOD_KERNEL_TMA
-                                                                                                 : FLOOD_KERNEL_STREAM;
-    } else {
-        h->kernel = o.kernel;
-    }
+    h->kernel = o.kernel == FLOOD_KERNEL_AUTO ? auto_kernel(o, grid->nx, ny_all) : o.kernel;
     if (h->prec == FLOOD_F64) h->kernel = FLOOD_KERNEL_REFERENCE;
     h->k_per_launch = 1;
     h->tile_x = o.tile_x;
@@ -519,7 +566,8 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
     }
     if (cudaMemsetAsync(h->z, 0, plane, h->stream) || cudaMemsetAsync(h->n, 0, plane, h->stream))
         return bail(FLOOD_ERR_CUDA, "memset");
-    if (copy_in(h, h->z, dem, G.ny, G.nx, 0)) return bail(FLOOD_ERR_CUDA, "dem upload");
+    const size_t row_off = (size_t)ra * grid->nx * esz;
+    if (copy_in(h, h->z, (const char *)dem + row_off, G.ny, G.nx, 0)) return bail(FLOOD_ERR_CUDA, "dem upload");
     std::vector<char> nbuf;
     const void *nsrc = manning;
     if (!manning) {
@@ -530,26 +578,47 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
         }
         nsrc = nbuf.data();
     }
-    if (copy_in(h, h->n, nsrc, G.ny, G.nx, 0)) return bail(FLOOD_ERR_CUDA, "manning upload");
+    if (copy_in(h, h->n, (const char *)nsrc + row_off, G.ny, G.nx, 0)) return bail(FLOOD_ERR_CUDA, "manning upload");
 
-    // boundary description
+    // boundary description of the stored rows.  A part keeps a border face of
+    // the whole grid where it lies in its rows (an outflow face of a halo row
+    // computes its flux without booking it); the rows' ends inside the grid are
+    // walls (their neighbours' values arrive by the halo exchange).  Inflow
+    // sections are always the whole grid's: a part solves Eq. 6 on copies of
+    // the section cells' z and n, so every part obtains the same face fluxes.
     const int nb = 2 * G.nx + 2 * G.ny;
     std::vector<int8_t> btype(nb, kBcWall);
     std::vector<int32_t> bslot(nb, 0);
     std::vector<double> bsqrt(nb, 0.0);
     std::vector<InflowSec> isecs;
     std::vector<int64_t> icells;
+    std::vector<char> secz, secn;
     std::vector<double> tt, tq;
     int slots = 0;
+    // local boundary entry of global side cell c (-1 if the part does not store it) and its global row
+    auto local_entry = [&](int side, int c, int *grow) -> int {
+        const int off = side_offset(side, G.nx, G.ny);
+        if (side == FLOOD_XMIN || side == FLOOD_XMAX) {
+            *grow = c;
+            return (c >= ra && c < rb) ? off + (c - ra) : -1;
+        }
+        *grow = side == FLOOD_YMIN ? 0 : ny_all - 1;
+        if (side == FLOOD_YMIN && ra != 0) return -1;
+        if (side == FLOOD_YMAX && rb != ny_all) return -1;
+        return off + c;
+    };
+    const int own0 = part ? part->y0 : 0, own1 = part ? part->y1 : ny_all;
     for (int k = 0; k < n_sections; k++) {
         const flood_bc_section &s = sections[k];
         int i0, i1;
-        section_range(s, G.nx, G.ny, &i0, &i1);
-        int off = side_offset(s.side, G.nx, G.ny);
+        section_range(s, grid->nx, ny_all, &i0, &i1);
         if (s.kind == FLOOD_OUTFLOW) {
             for (int c = i0; c < i1; c++) {
-                btype[off + c] = kBcOutflow;
-                bsqrt[off + c] = std::sqrt(s.slope);
+                int grow = 0;
+                const int e = local_entry(s.side, c, &grow);
+                if (e < 0) continue;
+                btype[e] = (grow >= own0 && grow < own1) ? kBcOutflow : kBcOutflowHalo;
+                bsqrt[e] = std::sqrt(s.slope);
             }
         } else {
             InflowSec S;
@@ -562,9 +631,22 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
             S.ntab = s.n_pts;
             S.sqrtS = std::sqrt(s.slope);
             for (int c = i0; c < i1; c++) {
-                btype[off + c] = kBcInflow;
-                bslot[off + c] = slots + (c - i0);
-                icells.push_back(side_cell_pitched(s.side, c, G.nx, G.ny, G.pitch));
+                int grow = 0;
+                const int e = local_entry(s.side, c, &grow);
+                if (e >= 0) {
+                    btype[e] = kBcInflow;
+                    bslot[e] = slots + (c - i0);
+                }
+                const int64_t gcell = side_cell_pitched(s.side, c, G.nx, ny_all, G.nx);   // j * nx + i
+                if (part) {
+                    icells.push_back((int64_t)(secz.size() / esz));
+                    const char *zc = (const char *)dem + gcell * esz;
+                    const char *nc = (const char *)nsrc + gcell * esz;
+                    secz.insert(secz.end(), zc, zc + esz);
+                    secn.insert(secn.end(), nc, nc + esz);
+                } else {
+                    icells.push_back(side_cell_pitched(s.side, c, G.nx, G.ny, G.pitch));
+                }
             }
             slots += i1 - i0;
             for (int p = 0; p < s.n_pts; p++) {
@@ -583,6 +665,10 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
     std::vector<float> bsqrt_f(bsqrt.begin(), bsqrt.end());
     ALLOC(h->secs_dev, InflowSec *, std::max<size_t>(isecs.size(), 1) * sizeof(InflowSec));
     ALLOC(h->sec_cells, int64_t *, std::max<size_t>(icells.size(), 1) * sizeof(int64_t));
+    if (part) {
+        ALLOC(h->sec_z, void *, std::max<size_t>(secz.size(), esz));
+        ALLOC(h->sec_n, void *, std::max<size_t>(secn.size(), esz));
+    }
     ALLOC(h->tab_t, double *, std::max<size_t>(tt.size(), 1) * sizeof(double));
     ALLOC(h->tab_q, double *, std::max<size_t>(tq.size(), 1) * sizeof(double));
     ALLOC(h->inflow_q, void *, (size_t)E * h->n_slots * esz);
@@ -603,6 +689,8 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
         up(h->sec_cells, icells.data(), icells.size() * sizeof(int64_t)) ||
         up(h->tab_t, tt.data(), tt.size() * sizeof(double)) || up(h->tab_q, tq.data(), tq.size() * sizeof(double)))
         return bail(FLOOD_ERR_CUDA, "boundary upload");
+    if (part && (up(h->sec_z, secz.data(), secz.size()) || up(h->sec_n, secn.data(), secn.size())))
+        return bail(FLOOD_ERR_CUDA, "section upload");
     if (cudaMemsetAsync(h->inflow_q, 0, (size_t)E * h->n_slots * esz, h->stream) ||
         cudaMemsetAsync(h->inflow_Q, 0, (size_t)E * std::max(h->n_in, 1) * sizeof(double), h->stream) ||
         cudaMemsetAsync(h->t_list, 0, (E + 1) * sizeof(double), h->stream) ||
@@ -617,6 +705,15 @@ extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, co
 #undef ALLOC
     *out = h;
     return FLOOD_OK;
+}
+
+}  // namespace flood
+
+extern "C" flood_status flood_create(const flood_grid *grid, const void *dem, const void *manning,
+                                     const flood_bc_section *sections, int32_t n_sections,
+                                     const flood_opts *opts, flood_handle **out)
+{
+    return create_handle(grid, dem, manning, sections, n_sections, opts, nullptr, out);
 }
 
 extern "C" flood_status flood_destroy(flood_handle *h)
@@ -642,6 +739,7 @@ extern "C" const char *flood_last_error(const flood_handle *h)
 extern "C" flood_status flood_step(flood_handle *h, int64_t n_steps)
 {
     if (!h) return fail(nullptr, FLOOD_ERR_ARG, "handle is NULL");
+    if (h->part) return fail(h, FLOOD_ERR_STATE, "a part of a decomposed grid is stepped by its decomposition");
     if (n_steps < 0) return fail(h, FLOOD_ERR_ARG, "n_steps must be >= 0");
     if (h->sticky) return fail(h, FLOOD_ERR_STATE, "handle is in an error state; write a new state first");
     if (h->opts.use_graph) return advance_graph(h, n_steps);
@@ -664,11 +762,10 @@ extern "C" flood_status flood_coarsen(int32_t precision, const void *src, int32_
     const size_t in_bytes = (size_t)nx * ny * esz, out_bytes = (size_t)mx * my * esz;
     void *d_src = const_cast<void *>(src), *d_dst = dst;
     if (!on_device) {
-        try {
-            d_src = c10::cuda::CUDACachingAllocator::raw_alloc_with_stream(in_bytes, st);
-            d_dst = c10::cuda::CUDACachingAllocator::raw_alloc_with_stream(out_bytes, st);
-        } catch (...) {
-            if (d_src != src) c10::cuda::CUDACachingAllocator::raw_delete(d_src);
+        d_src = raw_device_alloc(in_bytes, st);
+        d_dst = d_src ? raw_device_alloc(out_bytes, st) : nullptr;
+        if (!d_src || !d_dst) {
+            if (d_src) c10::cuda::CUDACachingAllocator::raw_delete(d_src);
             return fail(nullptr, FLOOD_ERR_OOM, "coarsen buffers");
         }
         e = cudaMemcpyAsync(d_src, src, in_bytes, cudaMemcpyHostToDevice, st);
@@ -695,6 +792,7 @@ extern "C" flood_status flood_advance(flood_handle *h, double t_end, int64_t *st
 {
     if (!h) return fail(nullptr, FLOOD_ERR_ARG, "handle is NULL");
     if (h->sticky) return fail(h, FLOOD_ERR_STATE, "handle is in an error state; write a new state first");
+    if (h->part) return fail(h, FLOOD_ERR_STATE, "a part of a decomposed grid is stepped by its decomposition");
     if (!std::isfinite(t_end)) return fail(h, FLOOD_ERR_ARG, "t_end must be finite");
     const int E = h->geo.epoch_steps;
     std::vector<double> tl(E + 1);
@@ -762,12 +860,14 @@ extern "C" flood_status flood_read(flood_handle *h, int32_t field, void *dst, si
     if (!h || !dst) return fail(h, FLOOD_ERR_ARG, "NULL argument");
     if (field == FLOOD_FIELD_LEDGER) {
         if (bytes != FLOOD_LEDGER_LEN * sizeof(double)) return fail(h, FLOOD_ERR_ARG, "ledger needs 9 doubles");
+        // stored volume of the rows this handle books (all rows, or a part's own)
+        Geom vg = h->geo;
+        vg.ny = h->geo.led_j1 - h->geo.led_j0;
+        const char *hv = (const char *)h->h[h->cur] + (size_t)h->geo.led_j0 * h->geo.pitch * h->esz;
         if (h->prec == FLOOD_F32)
-            CK(launch_volume<float>(h->geo, (const float *)h->h[h->cur], h->vol_partials, h->n_partials, h->vol_out,
-                                    h->stream));
+            CK(launch_volume<float>(vg, (const float *)hv, h->vol_partials, h->n_partials, h->vol_out, h->stream));
         else
-            CK(launch_volume<double>(h->geo, (const double *)h->h[h->cur], h->vol_partials, h->n_partials,
-                                     h->vol_out, h->stream));
+            CK(launch_volume<double>(vg, (const double *)hv, h->vol_partials, h->n_partials, h->vol_out, h->stream));
         Ctrl c;
         double vol = 0.0;
         CK(cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
@@ -776,6 +876,8 @@ extern "C" flood_status flood_read(flood_handle *h, int32_t field, void *dst, si
         double L[FLOOD_LEDGER_LEN] = {c.t, c.dt, c.V_in, c.V_out, c.V_clip, vol, c.h_max, (double)h->step,
                                       c.cfl_exceed};
         if (c.status & kStatusNonfinite) fail(h, FLOOD_ERR_NONFINITE, "NaN or Inf depth at an epoch start");
+        else if (c.status & kStatusCfl)
+            fail(h, FLOOD_ERR_CFL, "an epoch's time step broke the Courant limit dx / sqrt(g h_max) at its end");
         if (dst_on_device) CK(cudaMemcpy(dst, L, sizeof(L), cudaMemcpyHostToDevice));
         else std::memcpy(dst, L, sizeof(L));
         return FLOOD_OK;
@@ -912,6 +1014,7 @@ extern "C" flood_status flood_run_gauges(flood_handle *h, int64_t n_steps, const
                                          int32_t n_gauges, double *out, int32_t out_on_device)
 {
     if (!h) return fail(nullptr, FLOOD_ERR_ARG, "handle is NULL");
+    if (h->part) return fail(h, FLOOD_ERR_STATE, "a part of a decomposed grid is stepped by its decomposition");
     if (n_steps < 0 || n_gauges < 0 || (n_gauges > 0 && (!gauge_cells || !out)))
         return fail(h, FLOOD_ERR_ARG, "bad gauge arguments");
     if (h->sticky) return fail(h, FLOOD_ERR_STATE, "handle is in an error state; write a new state first");
@@ -950,3 +1053,42 @@ flood_status ensure_gauge_buffers(flood_handle *h, int ng, size_t n_values)
 }
 
 }  // namespace flood
+
+// ------------------------------------------------------------------ debugging aids
+extern "C" void flood_debug_fail_alloc_after(int64_t n) { g_fail_countdown = n < 0 ? -1 : n; }
+
+extern "C" int64_t flood_debug_alloc_count(void) { return g_alloc_count.load(); }
+
+extern "C" flood_status flood_debug_padding(flood_handle *h, int32_t fill, int64_t *bad)
+{
+    if (!h || (!fill && !bad)) return fail(h, FLOOD_ERR_ARG, "NULL argument");
+    const int nx = h->geo.nx, ny = h->geo.ny, P = h->geo.pitch;
+    unsigned long long *count = nullptr;
+    if (!fill) {
+        count = (unsigned long long *)dev_alloc(h, sizeof(unsigned long long));
+        if (!count) return fail(h, FLOOD_ERR_OOM, "padding counter");
+        CK(cudaMemsetAsync(count, 0, sizeof(unsigned long long), h->stream));
+    }
+    // (plane, rows, used columns): both state buffers, then z and n
+    struct Plane { void *p; int rows, cols; };
+    std::vector<Plane> planes;
+    for (int b = 0; b < 2; b++) {
+        planes.push_back({h->h[b], ny, nx});
+        planes.push_back({h->qx[b], ny, nx + 1});
+        planes.push_back({h->qy[b], ny + 1, nx});
+    }
+    planes.push_back({h->z, ny, nx});
+    planes.push_back({h->n, ny, nx});
+    cudaError_t e = cudaSuccess;
+    for (const Plane &pl : planes) {
+        e = launch_padding(pl.p, h->esz, pl.rows, pl.cols, P, fill != 0, count, h->stream);
+        if (e != cudaSuccess) break;
+    }
+    unsigned long long n = 0;
+    if (e == cudaSuccess && count) e = cudaMemcpyAsync(&n, count, sizeof(n), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (count) dev_free(h, count);
+    if (e != cudaSuccess) return cuda_fail(h, e, "padding kernel");
+    if (bad) *bad = (int64_t)n;
+    return FLOOD_OK;
+}

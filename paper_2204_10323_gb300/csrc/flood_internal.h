@@ -10,10 +10,14 @@ namespace flood {
 
 constexpr int kMaxEpoch = 1024;       // largest E (steps per CFL epoch)
 constexpr int kBcWall = 0, kBcInflow = 1, kBcOutflow = 2;
+// An outflow face of a subdomain's halo row: its flux is computed like any
+// outflow face but its volume is booked by the subdomain that owns the row.
+constexpr int kBcOutflowHalo = 3;
 
 // Device status bits (sticky, OR-ed by kernels).
 constexpr int kStatusNonfinite = 1;
 constexpr int kStatusTimeout = 2;
+constexpr int kStatusCfl = 4;          // an epoch's dt broke the Courant limit dx / sqrt(g h_max) at its end
 
 // Device-resident control block of one simulation.
 struct Ctrl {
@@ -49,6 +53,8 @@ struct Geom {
     int friction;                 // |q| of the friction term: 0 the face's own, 1 the vector norm
     double cfl_alpha, dt_cap, dt_const;
     int dt_mode, epoch_steps;
+    int led_j0, led_j1;           // rows whose clipped volume and stored volume this grid books (all rows,
+                                  // except for a subdomain of a decomposed grid: its own rows)
 };
 
 // Boundary description, one entry per boundary cell: sides laid out as
@@ -107,6 +113,9 @@ cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st);
 // maximum, count CFL exceedances, flag NaN/Inf.
 cudaError_t launch_epoch_begin(const Geom &g, Ctrl *ctrl, double *t_list, int E, const double *fixed_dt,
                                cudaStream_t st);
+// Decomposed grid: every part's running h_max (ctrls: n device pointers, on
+// the device) set to the largest of them.
+cudaError_t launch_hmax_allreduce(Ctrl *const *ctrls, int n, cudaStream_t st);
 // Eq. 6 for every (step of the epoch, inflow section) pair.
 template <typename T>
 cudaError_t launch_inflow(const Geom &g, const InflowSec *secs, int nsec, const int64_t *sec_cells,
@@ -167,6 +176,11 @@ cudaError_t launch_adjoint_step(const AdjArgs<T> &a, cudaStream_t st);
 // dst (pitched, precision T) = gn (pitched doubles).
 template <typename T>
 cudaError_t launch_gn_out(const Geom &g, const double *gn, T *dst, cudaStream_t st);
+
+// Pitch padding (columns [cols, pitch) of rows x pitch elements of esz bytes):
+// fill with the poison pattern, or count the elements whose bits differ from it.
+cudaError_t launch_padding(void *a, size_t esz, int rows, int cols, int pitch, bool fill,
+                           unsigned long long *count, cudaStream_t st);
 
 // One thread waits budget_ns of device time on an mbarrier nothing arrives at;
 // *gave_up (device) = 1 when the bounded wait gave up (the expected outcome).

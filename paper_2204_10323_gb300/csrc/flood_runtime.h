@@ -63,6 +63,12 @@ struct flood_handle {
     // captured epochs (use_graph): [parity of cur at the epoch start]
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
 
+    // subdomain of a decomposed grid (flood_decomp.cpp): the part's inflow sections are the whole
+    // grid's, solved on copies of their cells' z and n; only part 0 books the inflow volume
+    bool part = false;
+    bool book_vin = true;
+    void *sec_z = nullptr, *sec_n = nullptr;
+
     flood_adjoint_state *adj = nullptr;
     int64_t adj_forward_steps = 0;
     int adj_profile = 0;                      // flood_adjoint_profile
@@ -71,6 +77,25 @@ struct flood_handle {
 };
 
 namespace flood {
+
+// One row strip of a grid decomposed into strips (flood_decomp.cpp): the part
+// stores global rows [a, b) of a grid of ny_global rows and owns rows [y0, y1).
+struct PartSpec {
+    int ny_global;
+    int a, b;
+    int y0, y1;
+    int index;                    // part number; part 0 books the inflow volume
+};
+
+// flood_create for a whole grid (part == nullptr) or for one part of it: dem and
+// manning are the whole grid's host arrays, sections the whole grid's.
+flood_status create_handle(const flood_grid *grid, const void *dem, const void *manning,
+                           const flood_bc_section *sections, int32_t n_sections, const flood_opts *opts,
+                           const PartSpec *part, flood_handle **out);
+// Kernel family AUTO resolves to for a grid of nx x ny cells (flood_create's rule).
+int auto_kernel(const flood_opts &o, int nx, int ny);
+// Max of the depth over the rows [led_j0, led_j1) of the current state into the control block.
+flood_status refresh_hmax_window(flood_handle *h);
 
 // An NVTX range for the lifetime of the object: the runtime marks each stepping
 // call, each epoch's bookkeeping, each adjoint sweep and each ensemble step, so
@@ -82,6 +107,9 @@ struct NvtxRange {
     NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
+// Every device allocation of the library (through PyTorch's caching allocator;
+// NULL on failure, or when flood_debug_fail_alloc_after injects one).
+void *raw_device_alloc(size_t bytes, cudaStream_t st);
 void *dev_alloc(flood_handle *h, size_t bytes);
 void dev_free(flood_handle *h, void *p);
 flood_status fail(flood_handle *h, flood_status st, const std::string &msg);

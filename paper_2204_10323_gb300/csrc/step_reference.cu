@@ -23,7 +23,7 @@ __device__ __forceinline__ T boundary_face(const StepArgs<T> &a, int side, int k
     T inward = T(inward_sign(side));
     if (type == kBcInflow) return inward * a.inflow_q[(size_t)a.s * a.n_slots + a.bc.slot[off + k]];
     T q = outflow_flux_ieee<T>(h_cell, T(a.bc.sqrtS[off + k]), n_cell, T(G.dx), T(G.h_dry), G.bc_form);
-    vout += (double)q * G.dx;
+    if (type == kBcOutflow) vout += (double)q * G.dx;
     return -inward * q;
 }
 
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(BX *BY) step_reference_kernel(const StepArgs<T
         T dv = O::add(O::sub(qW, qE), O::sub(qS, qN));
         hn = O::add(hC, O::div(O::mul(dt, dv), dx));
         if (hn < T(0)) {
-            vclip += -(double)hn * G.dx * G.dx;
+            if (j >= G.led_j0 && j < G.led_j1) vclip += -(double)hn * G.dx * G.dx;
             hn = T(0);
         }
         a.h_out[c] = hn;

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kWarps * 32) step_rows_kernel(const StepArgs<f
                     for (int k = 0; k < 4; k++) {
                         const float v = get(hn, k);
                         if (v < 0.0f) {
-                            if (c0 + k < nx) vclip += -(double)v * G.dx * G.dx;
+                            if (c0 + k < nx && jr >= G.led_j0 && jr < G.led_j1) vclip += -(double)v * G.dx * G.dx;
                             set(hn, k, 0.0f);
                         }
                     }

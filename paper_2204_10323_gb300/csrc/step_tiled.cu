@@ -241,6 +241,7 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
                     if (has_prev) {
                         const int rr = r - 1;
                         const bool own_row = rr >= y0 && rr < y1;
+                        const bool led_row = own_row && rr >= G.led_j0 && rr < G.led_j1;
                         float4 fin;
                         bool neg = false;
 #pragma unroll
@@ -256,7 +257,7 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
                             for (int k = 0; k < 4; k++) {
                                 const float v = get(fin, k);
                                 if (v < 0.0f) {
-                                    if (own_row && own_cell[k]) fc -= v;
+                                    if (led_row && own_cell[k]) fc -= v;
                                     set(fin, k, 0.0f);
                                 }
                             }

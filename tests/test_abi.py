@@ -34,13 +34,21 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_objects_are_built_for_sm_103a_only():
+    """Every CUDA translation unit is compiled with exactly one target,
+    -gencode arch=compute_103a,code=sm_103a (the build's compilation database)."""
+    import json
     import paper_2204_10323_gb300 as F
     F.lib()
-    import subprocess
-    objs = [os.path.join(F._build.BUILD, f) for f in os.listdir(F._build.BUILD) if f.endswith(".cu.o")]
-    assert objs
-    out = subprocess.run(["cuobjdump", "--list-elf", objs[0]], capture_output=True, text=True).stdout
-    assert "sm_103a" in out
+    with open(os.path.join(F._build.BUILD, "compile_commands.json")) as f:
+        db = json.load(f)
+    cu = [e for e in db if e["file"].endswith(".cu")]
+    srcs = [f for f in os.listdir(F._build.CSRC) if f.endswith(".cu")]
+    assert sorted(os.path.basename(e["file"]) for e in cu) == sorted(srcs)
+    for e in cu:
+        args = e["arguments"]
+        targets = [args[i + 1] for i, a in enumerate(args) if a == "-gencode"]
+        assert targets == ["arch=compute_103a,code=sm_103a"], (e["file"], targets)
+        assert not any(a.startswith(("-arch", "--gpu-architecture", "--generate-code")) for a in args)
 
 
 def _grid(nx, ny, dx=1.0, prec=0):

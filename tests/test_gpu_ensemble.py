@@ -122,3 +122,20 @@ def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
     r2 = autotune.tune_ensemble(ens)
     assert r2["cached"] and r2["shape"] == r["shape"]
     ens.close()
+
+
+def test_autotuner_times_an_ensemble_on_its_own_stream(tmp_path, monkeypatch):
+    """An ensemble created on a side stream: the trial events are recorded on that
+    stream, so each trial measures the work it launched (about 0 ms otherwise)."""
+    import torch
+    from paper_2204_10323_gb300 import autotune
+    Fm = F()
+    monkeypatch.setenv("FLOOD_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    side = torch.cuda.Stream()
+    ens = Fm.Ensemble(scenarios(), stream=side)
+    assert ens.stream is side
+    cands = [(0, 4, 64, 4), (4, 2, 32, 8)]
+    r = autotune.tune_ensemble(ens, candidates=cands, trial_steps=64)
+    # the events bracket the steps: a trial of 64 steps takes at least a few microseconds each
+    assert all(t > 1e-3 for _, t in r["trials"]), r["trials"]
+    ens.close()

@@ -289,6 +289,36 @@ def test_nonfinite_depth_is_reported_and_sticky():
     s.sync()
 
 
+@pytest.mark.parametrize("precision,kernel", [(0, 0), (0, 4), (1, 1)])
+def test_broken_courant_limit_is_reported_and_sticky(precision, kernel):
+    """A constant time step far above the Courant limit: 5 s on 1 m cells with
+    depths up to 2 m gives dt sqrt(g h) = 22 > dx.  The lake stays at rest
+    (Eq. 3 gives q = 0 on a flat water surface), so the status is the only report."""
+    import dataclasses
+    Fm = F()
+    p = inputs.lake_at_rest(16, 12)
+    p.opts = dataclasses.replace(p.opts, dt_const=5.0)
+    E = p.opts.epoch_steps
+    s = Fm.Sim(p, precision=precision, kernel=kernel)
+    h0 = s.read(Fm.FIELD_H).copy()
+    s.step(E)                                # the first epoch start has no earlier epoch to check
+    s.sync()
+    s.step(1)                                # the second epoch start checks the first epoch
+    with pytest.raises(Fm.FloodError) as e:
+        s.sync()
+    assert e.value.status == Fm.ERR_CFL
+    L = s.ledger()
+    assert L["cfl_exceed"] == 1 and L["step"] == E + 1
+    assert np.array_equal(s.read(Fm.FIELD_H), h0)
+    with pytest.raises(Fm.FloodError) as e:
+        s.step(1)
+    assert e.value.status == Fm.ERR_STATE
+    s.write_state(h0)                        # clears the error
+    s.step(4)                                # inside the epoch: no new check
+    s.sync()
+    s.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_depth_clip_matches_oracle(precision):
     """Thin water drained through two outflow edges goes negative and is clipped."""
