@@ -36,15 +36,13 @@ BYTES_PER_CELL = 32          # read h, qx, qy, z, n (20 B) + write h, qx, qy (12
 # DRAM bytes read + written per cell by one launch of a kernel on the 16384^2
 # workload: one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
 # the 4096^2 case of the same workload (state > L2), scaled by the cell count;
-# key (kernel, steps per launch).  The summaries are under profiles/.
-# (profiles/step_*_4096_full.md, profiles/roofline_study_16384.md)
-# (stream captured in the 16384^2 launch shape, 4 warps x 32-row chunks).  Only kernels whose code has
-# not changed since their capture are listed; the others report traffic null.
+# key (kernel, steps per launch); the stream kernel captured in the 16384^2
+# launch shape (4 warps x 32-row chunks).  Only kernels whose code has not
+# changed since their capture are listed; the others report traffic null.
 TRAFFIC_B_PER_CELL = {("stream", 1): 31.28, ("tiled", 1): 30.55, ("tiled", 2): 30.79, ("tiled", 4): 31.65,
                       ("tiled", 8): 30.91}
 # Warp instructions per cell-update of the temporal-blocking kernel (issue-bound), from the same 4096^2
-# capture (smsp__inst_executed.sum; profiles/step_tiled4_4096_full.md): the "alu" roofline beside the
-# one-step HBM one.  The issue peak is 152 SMs x 4 warp-instructions per cycle x the sampled SM clock.
+# capture (smsp__inst_executed.sum): the "alu" roofline beside the one-step HBM one.  The issue peak is 152 SMs x 4 warp-instructions per cycle x the sampled SM clock.
 INST_PER_CELL_UPDATE = {("tiled", 4): 243920737 / (4096 * 4096 * 4)}
 SMS, ISSUE_PER_SM_CYCLE = 152, 4
 # the same for the vector-norm friction option (theta = 1)
@@ -149,20 +147,46 @@ def oracle_strip(prob, rows: int = 1024):
     return oracle.Oracle(sub), sub, threads
 
 
-def cpu_baseline(prob, seconds_target: float = 15.0):
-    """Time the FP64 oracle on a bounded sample (a full-width strip of the grid)."""
-    o, sub, threads = oracle_strip(prob)
+def _oracle_rate(o, sub, seconds: float, min_steps: int = 1, max_steps: int = 10 ** 9):
+    """Gcell-updates/s of the oracle on `sub`: steps until `seconds` have passed."""
     o.run(1)                      # warm (page-in)
     steps, elapsed = 0, 0.0
-    while elapsed < seconds_target:
+    while (elapsed < seconds or steps < min_steps) and steps < max_steps:
         t0 = time.perf_counter()
         o.run(1)
         elapsed += time.perf_counter() - t0
         steps += 1
-    v = sub.nx * sub.ny * steps / elapsed / 1e9
-    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"FP64 C oracle, {sub.nx}x{sub.ny} full-width strip of the workload, {steps} steps, "
-                      f"{elapsed:.1f} s, OpenMP {threads} threads"}
+    return sub.nx * sub.ny * steps / elapsed / 1e9, steps, elapsed
+
+
+def cpu_baseline(prob, seconds_target: float = 10.0):
+    """The FP64 oracle on the host cores: all cores on a bounded sample of the
+    workload (a full-width strip of the grid), beside it one core on the same
+    strip, and the 2048^2 workload over 100 steps on all cores and on one core
+    (the per-core figure the paper's CPU column reports, Table 1)."""
+    import inputs
+    import oracle
+    o, sub, threads = oracle_strip(prob)
+    v, steps, el = _oracle_rate(o, sub, seconds_target)
+    out = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"FP64 C oracle, {sub.nx}x{sub.ny} full-width strip of the workload, {steps} steps, "
+                     f"{el:.1f} s, OpenMP {threads} threads", "more": []}
+    oracle.set_threads(1)
+    o1, sub1, _ = oracle_strip(prob)
+    oracle.set_threads(1)
+    v1, steps1, el1 = _oracle_rate(o1, sub1, seconds_target / 3)
+    out["more"].append({"workload": f"{sub1.nx}x{sub1.ny} strip", "threads": 1, "steps": steps1,
+                        "seconds": round(el1, 2), "value": v1})
+    c2 = inputs.c2_fractal()
+    c2.h0 = inputs.wet_start(c2.z, c2.dx, 0.3)
+    for t, cap in ((threads, 100), (1, 100)):
+        oracle.set_threads(t)
+        oc = oracle.Oracle(c2)
+        vc, sc, ec = _oracle_rate(oc, c2, 0.0, min_steps=cap, max_steps=cap)
+        out["more"].append({"workload": "fractal_2048x2048_5m (30 % wet)", "threads": t, "steps": sc,
+                            "seconds": round(ec, 2), "value": vc})
+    oracle.set_threads(threads)
+    return out
 
 
 def run_reference(args):
@@ -210,51 +234,57 @@ def job_throughput(world: int, cells: int, steps: int, ms: float) -> float:
     return world * cells * steps / (ms * 1e-3) / 1e9
 
 
-def timed_run(F, torch, prob, kernel_name, k, tile, graph, steps_req, warmup, local, dist):
-    """Warm up and time whole epochs of one kernel on `prob`: CUDA events around
-    every launch on the library's stream, nvidia-smi clocks sampled meanwhile."""
+def timed_run(F, torch, prob, kernel_name, k, tile, graph, steps_req, warmup, local, dist, repeats=5):
+    """Warm up, then time `repeats` runs of exactly steps_req steps of one kernel
+    on `prob`, each bracketed by a barrier and a synchronize: CUDA events around
+    every launch on the library's stream, nvidia-smi clocks sampled meanwhile.
+    The runs continue one simulation (a run may start and end inside a CFL
+    epoch; its epoch starts are timed with it).  total_ms is the median run."""
     kernel = {"rows": F.KERNEL_ROWS, "tiled": F.KERNEL_TILED, "reference": F.KERNEL_REFERENCE,
               "stream": F.KERNEL_STREAM, "tma": F.KERNEL_TMA, "auto": F.KERNEL_AUTO}[kernel_name]
     sim = F.Sim(prob, precision=F.F32, kernel=kernel, steps_per_launch=k, tile=tile, use_graph=graph)
     E = prob.opts.epoch_steps
     stream = torch.cuda.current_stream()
-    # steps per launch: K for the temporal-blocked kernel, else 1; time whole epochs
-    per_launch = (k or 4) if kernel_name == "tiled" else 1
-    n_launch_total = max(E // per_launch, (steps_req + per_launch - 1) // per_launch)
-    n_launch_total = (n_launch_total + (E // per_launch) - 1) // (E // per_launch) * (E // per_launch)
-    steps = n_launch_total * per_launch
-    # warm-up: whole epochs so the timed region starts at an epoch start
+    # steps per launch: K for the temporal-blocked kernel, else 1 (a launch never crosses an epoch end)
+    per_launch = (k or 4) if kernel_name in ("tiled", "auto") else 1
+    # warm-up: at least one whole epoch
     warm = max(warmup, E)
-    warm = (warm + E - 1) // E * E
-    for _ in range(warm // per_launch):
-        sim.step(per_launch)
+    sim.step(warm)
     sim.sync()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_launch_total + 1)]
-    step0 = int(sim.ledger()["step"])
-    torch.cuda.synchronize()
-    ev[0].record(stream)
-    for j in range(n_launch_total):
-        sim.step(per_launch)
-        ev[j + 1].record(stream)
-    torch.cuda.synchronize()
+    runs_ms, kern, launches = [], [], 0
+    for _ in range(repeats):
+        step0 = int(sim.ledger()["step"])
+        # the launches of this run: up to per_launch steps each, cut at epoch ends
+        plan, st = [], step0
+        while st < step0 + steps_req:
+            kk = min(per_launch, E - st % E, step0 + steps_req - st)
+            plan.append((st % E == 0, kk))
+            st += kk
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(plan) + 1)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for j, (_, kk) in enumerate(plan):
+            sim.step(kk)
+            ev[j + 1].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        runs_ms.append(ev[0].elapsed_time(ev[-1]))
+        # launches that neither start an epoch nor are cut short run the step kernel alone
+        kern += [ev[j].elapsed_time(ev[j + 1]) for j, (begin, kk) in enumerate(plan) if not begin and kk == per_launch]
+        n_epochs = sum(1 for begin, _ in plan if begin)
+        launches += len(plan) + n_epochs * (1 + (1 if sim_inflows(prob) else 0))
     clk = clocks.stop()
-    per = [ev[j].elapsed_time(ev[j + 1]) for j in range(n_launch_total)]
-    total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), dist)
     sim.sync()
-    # launches that did not start an epoch run the step kernel alone
-    starts = [(step0 + j * per_launch) % E == 0 for j in range(n_launch_total)]
-    kern = [per[j] for j in range(n_launch_total) if not starts[j]]
-    kern_ms = statistics.mean(kern) if kern else statistics.mean(per)
-    n_epochs = sum(starts)
-    launches = n_launch_total + n_epochs * (1 + (1 if sim_inflows(prob) else 0))
-    return {"sim": sim, "total_ms": total_ms, "kern_ms": kern_ms, "per_launch": per_launch, "steps": steps,
-            "clocks": clk, "launches": launches, "ledger": sim.ledger()}
+    total_ms = max_over_ranks(statistics.median(runs_ms), dist)
+    kern_ms = statistics.mean(kern) if kern else total_ms / max(1, steps_req // per_launch)
+    return {"sim": sim, "total_ms": total_ms, "kern_ms": kern_ms, "per_launch": per_launch, "steps": steps_req,
+            "runs_ms": runs_ms, "clocks": clk, "launches": launches, "ledger": sim.ledger(), "warmup": warm}
 
 
 def run_gpu(args):
@@ -279,11 +309,11 @@ def run_gpu(args):
     h0, qx0, qy0 = prob.initial_state(np.float32)
     stream = torch.cuda.current_stream()
     tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else (0, 0)
-    run = timed_run(F, torch, prob, args.kernel, args.k, tile, args.graph, args.steps, args.warmup, local, dist)
+    run = timed_run(F, torch, prob, args.kernel, args.k, tile, args.graph, args.steps, args.warmup, local, dist,
+                    repeats=args.repeats)
     sim, total_ms, kern_ms, per_launch, steps = run["sim"], run["total_ms"], run["kern_ms"], run["per_launch"], \
         run["steps"]
     clk, launches, L = run["clocks"], run["launches"], run["ledger"]
-    args.steps = steps
 
     value = job_throughput(world, ncell, steps, total_ms)
     peak, peak_kind = measured_peaks()
@@ -303,24 +333,42 @@ def run_gpu(args):
     pin_qy = torch.from_numpy(qy0).pin_memory()
     out_h = torch.empty_like(pin_h).pin_memory()
     e2e_steps = args.steps
+    # untimed first pass: the first copies out of freshly pinned host buffers cost
+    # about 40 ms more than later ones (first use of the new pinned pages)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.write_state(pin_h.numpy(), pin_qx.numpy(), pin_qy.numpy())
+    first_write_ms = (time.perf_counter() - t0) * 1e3
+    F.flood_read(sim.h, F.FIELD_H, __import__("ctypes").c_void_p(out_h.data_ptr()), out_h.numel() * 4, 0)
     runs = []
-    for _ in range(5):                    # median of five end-to-end runs
+    phases = {"write_state": [], "steps": [], "read_depth": [], "ledger": []}
+    for _ in range(max(5, args.repeats)):   # median of the end-to-end runs, each phase timed on the host
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim.write_state(pin_h.numpy(), pin_qx.numpy(), pin_qy.numpy())
+        t1 = time.perf_counter()
         sim.step(e2e_steps)
+        F.flood_sync(sim.h)
+        t2 = time.perf_counter()
         F.flood_read(sim.h, F.FIELD_H, __import__("ctypes").c_void_p(out_h.data_ptr()), out_h.numel() * 4, 0)
+        t3 = time.perf_counter()
         led = sim.ledger()
-        runs.append(ncell * e2e_steps / (time.perf_counter() - t0) / 1e9)
+        t4 = time.perf_counter()
+        runs.append(ncell * e2e_steps / (t4 - t0) / 1e9)
+        for key, dt_s in zip(phases, (t1 - t0, t2 - t1, t3 - t2, t4 - t3)):
+            phases[key].append(round(dt_s * 1e3, 3))
     h2d = (pin_h.numel() + pin_qx.numel() + pin_qy.numel()) * 4
     d2h = out_h.numel() * 4 + 9 * 8
-    e2e = {"value": statistics.median(runs), "unit": UNIT, "runs": runs,
+    e2e = {"value": statistics.median(runs), "unit": UNIT, "runs": runs, "phases_ms": phases,
+           "first_write_state_ms": round(first_write_ms, 3),
            "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
            "what": f"flood_write_state from pinned host (h, qx, qy), flood_step({e2e_steps}), "
-                   f"flood_read(depth) + ledger to host; median of five runs"}
+                   f"flood_read(depth) + ledger to host; median of {len(runs)} runs"}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "steps_requested": args.steps, "repeats": len(run["runs_ms"]),
+            "repeat_ms": [round(x, 4) for x in run["runs_ms"]],
+            "warmup": run["warmup"], "ms_per_step": total_ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wname, "nx": prob.nx, "ny": prob.ny, "kernel": args.kernel,
                        "steps_per_launch": args.k, "epoch_steps": E, "l2": "inputs larger than L2 (5.4 GB state)",
@@ -330,6 +378,7 @@ def run_gpu(args):
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "bytes_per_cell": BYTES_PER_CELL, "kernel_ms": kern_ms, "steps_per_launch": per_launch,
                          "dram_gbs": traffic / (kern_ms * 1e-3) / 1e9 if traffic else None,
+                         "dram_frac": traffic / (kern_ms * 1e-3) / 1e9 / peak if traffic else None,
                          "issue": issue_roofline(args.kernel, per_launch, ncell, kern_ms, clk),
                          "note": ("one-step algorithmic bytes (32 B per cell-update) over the launch time; with "
                                   f"{per_launch} steps per launch the kernel moves {traffic / ncell / per_launch:.1f} "
@@ -511,6 +560,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--repeats", type=int, default=5, help="timed runs of --steps steps; the median is reported")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c3")
     ap.add_argument("--kernel", default="tiled", choices=["stream", "rows", "tiled", "tma", "reference"])
@@ -518,7 +568,7 @@ def main():
     ap.add_argument("--graph", action="store_true")
     ap.add_argument("--tile", default="", help="stream kernel launch shape: warps,rows")
     ap.add_argument("--traffic-bytes", type=float, default=None)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
