@@ -124,13 +124,14 @@ typedef struct {
                                     the numerator discharge of a face is theta q + (1 - theta)/2 times the
                                     sum of its two neighbours along the same axis (the theta scheme of
                                     de Almeida et al. 2012, cited in Methods); friction keeps |q| of the
-                                    face.  theta != 1: kernels REFERENCE, STREAM, TMA (AUTO) and FP64 only,
-                                    no ensembles, no adjoint (FLOOD_ERR_UNSUPPORTED) */
+                                    face.  theta != 1: kernels REFERENCE, STREAM, TMA (AUTO), TILED and
+                                    FP64, ensembles; not ROWS, no adjoint (FLOOD_ERR_UNSUPPORTED) */
     int32_t friction;            /* |q| in the friction term of Eq. 3.  0 (default): the face's own discharge
                                     component (the axis-by-axis integration of Methods).  1: the vector norm
                                     sqrt(q^2 + qo^2), qo the mean of the four faces of the other axis around
-                                    the face.  1: kernels REFERENCE, STREAM, TMA (AUTO) and FP64 only, no
-                                    ensembles, no adjoint (FLOOD_ERR_UNSUPPORTED); other values FLOOD_ERR_ARG */
+                                    the face.  1: kernels REFERENCE, STREAM, TMA (AUTO), TILED and FP64,
+                                    ensembles; not ROWS, no adjoint (FLOOD_ERR_UNSUPPORTED); other values
+                                    FLOOD_ERR_ARG */
 } flood_opts;
 
 typedef struct flood_handle flood_handle;
@@ -281,7 +282,8 @@ const char *flood_last_error(const flood_handle *h);
  * step, Eq. 6 inflow and ledger.  Whole epochs are captured once into a CUDA
  * graph (steps_per_graph steps, a multiple of epoch_steps) and replayed.
  * opts applies to every scenario (kernel and use_graph are set by the
- * ensemble); all scenarios share its stream.  flood_ensemble_member returns
+ * ensemble; theta and friction apply to every scenario); all scenarios share
+ * its stream.  flood_ensemble_member returns
  * scenario k's handle for flood_read / flood_write_state / flood_set_clock
  * (do not destroy it or step it alone).  Errors: flood_ensemble_last_error.
  */

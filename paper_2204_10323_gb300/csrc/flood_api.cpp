@@ -382,15 +382,12 @@ static flood_status validate(const flood_grid *grid, const flood_bc_section *sec
     if (o.kernel < 0 || o.kernel > 5) return fail(nullptr, FLOOD_ERR_ARG, "unknown kernel");
     if (o.tile_x < 0 || o.tile_y < 0) return fail(nullptr, FLOOD_ERR_ARG, "tile_x and tile_y must be >= 0");
     if (!(o.theta > 0.0 && o.theta <= 1.0)) return fail(nullptr, FLOOD_ERR_ARG, "theta must lie in (0, 1]");
-    if (o.theta != 1.0 && grid->precision == FLOOD_F32 &&
-        !(o.kernel == FLOOD_KERNEL_AUTO || o.kernel == FLOOD_KERNEL_REFERENCE || o.kernel == FLOOD_KERNEL_STREAM ||
-          o.kernel == FLOOD_KERNEL_TMA))
-        return fail(nullptr, FLOOD_ERR_UNSUPPORTED, "theta != 1 needs the REFERENCE, STREAM or TMA kernel");
+    if (o.theta != 1.0 && grid->precision == FLOOD_F32 && o.kernel == FLOOD_KERNEL_ROWS)
+        return fail(nullptr, FLOOD_ERR_UNSUPPORTED, "theta != 1 needs the REFERENCE, STREAM, TMA or TILED kernel");
     if (o.friction != 0 && o.friction != 1) return fail(nullptr, FLOOD_ERR_ARG, "friction must be 0 or 1");
-    if (o.friction != 0 && grid->precision == FLOOD_F32 &&
-        !(o.kernel == FLOOD_KERNEL_AUTO || o.kernel == FLOOD_KERNEL_REFERENCE || o.kernel == FLOOD_KERNEL_STREAM ||
-          o.kernel == FLOOD_KERNEL_TMA))
-        return fail(nullptr, FLOOD_ERR_UNSUPPORTED, "vector-norm friction needs the REFERENCE, STREAM or TMA kernel");
+    if (o.friction != 0 && grid->precision == FLOOD_F32 && o.kernel == FLOOD_KERNEL_ROWS)
+        return fail(nullptr, FLOOD_ERR_UNSUPPORTED,
+                    "vector-norm friction needs the REFERENCE, STREAM, TMA or TILED kernel");
     if (o.kernel == FLOOD_KERNEL_TILED) {
         int K = o.steps_per_launch > 0 ? o.steps_per_launch : 4;
         if (!(K <= 4 || K == 8) || o.epoch_steps % K != 0)

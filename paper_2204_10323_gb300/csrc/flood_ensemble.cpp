@@ -28,6 +28,7 @@ struct flood_ensemble {
     cudaStream_t stream = nullptr;
     int warps = 4, rows = 64, steps_per_graph = 16;
     int kernel = FLOOD_KERNEL_STREAM, k_steps = 4;   // TILED: k_steps per launch, rows per item
+    int mode = 0;                          // scheme options: bit 0 theta weighting, bit 1 vector-norm friction
     StepArgs<float> *table[2] = {nullptr, nullptr};   // per parity of the ping-pong buffers
     int *base = nullptr;                   // block prefix, n + 1
     int total_blocks = 0;
@@ -116,11 +117,11 @@ flood_status ensemble_step(flood_ensemble *e, int64_t limit, cudaStream_t st, in
     // only whole 8-step launches, anything shorter runs single stream steps
     if (e->kernel == FLOOD_KERNEL_TILED && !(e->k_steps == 8 && steps < 8)) {
         c = launch_step_tiled_ensemble(e->table[parity], e->tbase, n, e->total_items, e->rows, steps, s,
-                                       s + steps == E ? 1 : 0, st);
+                                       s + steps == E ? 1 : 0, e->mode, st);
     } else {
         steps = 1;
         c = launch_step_stream_ensemble(e->table[parity], e->base, n, e->total_blocks, e->warps, e->rows, s,
-                                        s == E - 1 ? 1 : 0, st);
+                                        s == E - 1 ? 1 : 0, e->mode, st);
     }
     if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
     for (flood_handle *h : e->members) {
@@ -188,12 +189,10 @@ extern "C" flood_status flood_ensemble_create(int32_t n, const flood_grid *grids
     if (opts) o = *opts;
     else flood_default_opts(&o);
     o.kernel = FLOOD_KERNEL_STREAM;
-    if (o.theta != 1.0) return efail(nullptr, FLOOD_ERR_UNSUPPORTED, "ensembles run theta = 1 (Eq. 3 as printed)");
-    if (o.friction != 0)
-        return efail(nullptr, FLOOD_ERR_UNSUPPORTED, "ensembles run the face's own |q| in the friction term");
     o.use_graph = 0;
     flood_ensemble *e = new flood_ensemble();
     e->E = o.epoch_steps;
+    e->mode = (o.theta != 1.0 ? 1 : 0) | (o.friction != 0 ? 2 : 0);
     e->graphs.assign(2, nullptr);
     for (int k = 0; k < n; k++) {
         if (grids[k].precision != FLOOD_F32) {

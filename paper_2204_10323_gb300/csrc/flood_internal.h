@@ -95,8 +95,9 @@ cudaError_t launch_step_rows(const StepArgs<float> &a, cudaStream_t st);
 cudaError_t launch_step_stream(const StepArgs<float> &a, cudaStream_t st);
 // Stream kernel over many grids: table of per-grid arguments (device), block
 // prefix base[n+1] (device), one launch of total_blocks blocks.
+// mode: the scheme options shared by every grid (bit 0 theta weighting, bit 1 vector-norm friction).
 cudaError_t launch_step_stream_ensemble(const StepArgs<float> *table, const int *base, int n, int total_blocks,
-                                        int warps, int rows, int step, int want_hmax, cudaStream_t st);
+                                        int warps, int rows, int step, int want_hmax, int mode, cudaStream_t st);
 // Blocks of one grid for the stream kernel, and the (warps, rows) a tile pair selects.
 int stream_blocks(const Geom &g, int warps, int rows);
 cudaError_t launch_step_tma(const StepArgs<float> &a, cudaStream_t st);
@@ -104,7 +105,7 @@ cudaError_t launch_step_tma(const StepArgs<float> &a, cudaStream_t st);
 // base[k] .. base[k+1] - 1 (tiled_items per grid), k_steps steps from s0.
 int tiled_items(const Geom &g, int chunk_rows, int k_steps);
 cudaError_t launch_step_tiled_ensemble(const StepArgs<float> *table, const int *base, int n, int total_items,
-                                       int chunk_rows, int k_steps, int s0, int want_hmax, cudaStream_t st);
+                                       int chunk_rows, int k_steps, int s0, int want_hmax, int mode, cudaStream_t st);
 void stream_launch_shape(const Geom &g, int tile_x, int tile_y, int *warps, int *rows);
 cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st);
 

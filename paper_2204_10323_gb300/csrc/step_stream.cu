@@ -526,7 +526,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
 }
 
 // Many grids in one launch: block b belongs to the scenario whose block range
-// [base[k], base[k+1]) holds it (scenarios ordered largest first).
+// [base[k], base[k+1]) holds it (scenarios ordered largest first); kMode as
+// for one grid (the scenarios share their scheme options).
+template <int kMode>
 __global__ void __launch_bounds__(kMaxWarps * 32, 5)
     step_stream_ensemble_kernel(const StepArgs<float> *table, const int *base, const int n, const int rows,
                                 const int step, const int want_hmax)
@@ -546,7 +548,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 5)
     const int nbx = (strips + nwarps - 1) / nwarps;
     const int local = b - base[lo];
     uint32_t ring_base = 0;
-    stream_body<false>(a, step, want_hmax, local % nbx, local / nbx, rows, smem_raw, red, ring_base, true);
+    stream_body<false, kMode>(a, step, want_hmax, local % nbx, local / nbx, rows, smem_raw, red, ring_base, true);
 }
 
 // Variant of the stream/TMA kernels for a grid's options: bit 0 theta
@@ -562,9 +564,12 @@ cudaError_t configure(int warps)
                                              (int)(sizeof(WarpRing) * kMaxWarps));
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaFuncSetAttribute(step_stream_ensemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(WarpRing) * kMaxWarps));
-    if (e != cudaSuccess) return e;
+    for (auto k : {step_stream_ensemble_kernel<0>, step_stream_ensemble_kernel<1>, step_stream_ensemble_kernel<2>,
+                   step_stream_ensemble_kernel<3>}) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(WarpRing) * kMaxWarps));
+        if (e != cudaSuccess) return e;
+    }
     configured = true;
     (void)warps;
     return cudaSuccess;
@@ -700,12 +705,17 @@ cudaError_t launch_step_tma(const StepArgs<float> &a, cudaStream_t st)
 }
 
 cudaError_t launch_step_stream_ensemble(const StepArgs<float> *table, const int *base, int n, int total_blocks,
-                                        int warps, int rows, int step, int want_hmax, cudaStream_t st)
+                                        int warps, int rows, int step, int want_hmax, int mode, cudaStream_t st)
 {
     cudaError_t e = configure(warps);
     if (e != cudaSuccess) return e;
-    step_stream_ensemble_kernel<<<total_blocks, warps * 32, sizeof(WarpRing) * warps, st>>>(table, base, n, rows,
-                                                                                          step, want_hmax);
+    const size_t smem = sizeof(WarpRing) * warps;
+    switch (mode) {
+    case 0: step_stream_ensemble_kernel<0><<<total_blocks, warps * 32, smem, st>>>(table, base, n, rows, step, want_hmax); break;
+    case 1: step_stream_ensemble_kernel<1><<<total_blocks, warps * 32, smem, st>>>(table, base, n, rows, step, want_hmax); break;
+    case 2: step_stream_ensemble_kernel<2><<<total_blocks, warps * 32, smem, st>>>(table, base, n, rows, step, want_hmax); break;
+    default: step_stream_ensemble_kernel<3><<<total_blocks, warps * 32, smem, st>>>(table, base, n, rows, step, want_hmax); break;
+    }
     return cudaGetLastError();
 }
 

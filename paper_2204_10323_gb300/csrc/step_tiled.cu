@@ -1,487 +1,9 @@
-// step_tiled.cu -- FP32 temporal blocking: K <= 4 time steps per launch.
-//
-// One block is a pipeline of K warps over output strips of 120 columns (128
-// staged, 4 halo columns on each side held by lanes 0 and 31); warp s-1
-// advances the strip by time level s.  The grid is persistent, one block per
-// resident pipeline, and each block takes an equal contiguous share of the
-// strip-major sequence of (strip, row) units, running the pipeline once per
-// strip segment of its share, so that every SM gets the same work.  The warps move
-// in lockstep ticks: at tick j, level s works on row r = j - 2(s-1), i.e. it
-// computes the new south faces of row r, finishes row r-1 (Eq. 4) and
-// computes the new west faces of row r, exactly like the single-step row
-// kernels.  Level 1 reads its rows from a shared-memory ring filled by bulk
-// copies (cp.async.bulk + mbarrier, a few rows ahead); level s > 1 reads the
-// row that level s-1 finished at the previous tick from a double-buffered
-// hand-off slot; only level K stores.  The dependency cone of K steps is K
-// columns wide on each side, so the 120 inner columns are exact; in y the
-// chunk needs K extra rows at each end.  HBM traffic per cell and step is
-// about (20 B read + 12 B written) / K plus the 8/120 column overlap.
-//
-// Per cell and level the arithmetic is the single-step kernels' (the same
-// explicitly rounded face function and depth update), so K levels give the
-// same bits as K single steps.  Boundary faces (Eq. 5-6) use that level's
-// inflow row; ledger volumes are booked only by the pipeline that owns the
-// cell or boundary face.  Waits on the copies are bounded (about 2 s), after
-// which the status word gets the timeout bit and the pipeline stops storing.
-#include "fast_face.cuh"
-#include "tma_util.cuh"
+// step_tiled.cu -- the temporal-blocking kernels (step_tiled.cuh) for Eq. 3 as
+// printed, the host-side split of a grid into (chunk, strip) work items, and
+// the launchers, which send the scheme options to step_tiled_opts.cu.
+#include "step_tiled.cuh"
 
 namespace flood {
-
-namespace {
-
-// halo columns per side (at least K: the dependency cone of K steps) and
-// output columns of a 128-column strip, per steps per launch K
-__host__ __device__ constexpr int halo_cols(int K) { return K <= 4 ? 4 : 8; }
-__host__ __device__ constexpr int out_cols(int K) { return 128 - 2 * halo_cols(K); }
-// level-1 rows in flight and pipelines per SM: one grid uses 6 and 6 (six
-// pipelines of 4 warps fit the registers and shared memory of an SM); the
-// ensemble kernel, which keeps more per-scenario state in registers, 8 and 5
-constexpr int kPF1 = 4, kPFE = 8;
-constexpr uint64_t kBudgetNs = 2000000000ull;
-
-constexpr int pow2_ceil(int v)
-{
-    int p = 1;
-    while (p < v) p *= 2;
-    return p;
-}
-
-template <int K, int kPF>
-struct alignas(16) PipeSmem {
-    // z,n rows kept: the lagging levels read 2(K-1)+1 rows back; a power of two,
-    // so that the row's slot is a mask of its index
-    static constexpr int kDZ = pow2_ceil(kPF + 2 * K);
-    float hq[kPF][3][128];                  // level-1 input rows: h, qx, qy
-    float zn[kDZ][2][128];                  // z, n of recent rows
-    float ho[K > 1 ? K - 1 : 1][2][3][128]; // hand-off: level s -> s+1, double buffered by tick parity
-    uint64_t bar[kPF];
-};
-
-__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-__device__ __forceinline__ void sts4(float *p, const float4 &v) { *reinterpret_cast<float4 *>(p) = v; }
-
-__device__ __forceinline__ float get(const float4 &v, int k)
-{
-    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
-}
-
-__device__ __forceinline__ void set(float4 &v, int k, float x)
-{
-    if (k == 0) v.x = x;
-    else if (k == 1) v.y = x;
-    else if (k == 2) v.z = x;
-    else v.w = x;
-}
-
-// This thread's share of one grid's ledger terms over a launch.
-struct TiledLedger {
-    double vout = 0.0, vclip = 0.0;      // folded from the float runs below
-    float hmax = 0.0f;
-    bool nan_seen = false;
-};
-
-__device__ __forceinline__ FastConst tiled_const(const StepArgs<float> &a)
-{
-    const Geom &G = a.geo;
-    const float dt = (float)a.ctrl->dt, dx = (float)G.dx, g = (float)G.g;
-    FastConst Kc;
-    Kc.gdt = g * dt;
-    Kc.a1 = Kc.gdt / dx;
-    Kc.h_dry = (float)G.h_dry;
-    Kc.dtdx = dt / dx;
-    return Kc;
-}
-
-// One work item: the pipeline over strip `strip`, rows [y0, y1) of grid a, for
-// steps s0 .. s0 + K - 1 of the epoch.  base counts the rows staged by earlier
-// items (ring slot and phase of staged row idx are those of base + idx).
-// Returns true (uniformly over the block) if a wait on a copy timed out; the
-// copies in flight are then drained and the status word has the timeout bit.
-template <int K, int kPF>
-__device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s0, const FastConst &Kc,
-                                           const int strip, const int y0, const int y1, PipeSmem<K, kPF> &sm,
-                                           uint32_t &base, TiledLedger &L)
-{
-    constexpr int kDZ = PipeSmem<K, kPF>::kDZ;
-    const Geom &G = a.geo;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int lvl = warp + 1;                         // this warp's time level
-    const int nx = G.nx, ny = G.ny, P = G.pitch;
-    const int step = s0 + (lvl - 1);                  // this level's step in the epoch
-    int issued = 0, consumed = 0;
-    bool abort = false;
-    constexpr int kOut = out_cols(K);
-    const int x0 = strip * kOut - halo_cols(K);
-    const int c0 = x0 + 4 * lane;
-    const int own_lo = strip * kOut, own_hi = min(strip * kOut + kOut, nx);
-    const int jb = max(y0 - K, 0);
-    const int jload_hi = min(y1 + K - 1, ny - 1);     // last staged row
-    const int nload = jload_hi - jb + 1;
-    const int jlast = min(y1, ny) + 2 * (K - 1);      // last tick: level K reaches row min(y1, ny)
-    const int rstart = jb == 0 ? 0 : jb + (lvl - 1);  // first row this level sees (halo row if jb > 0)
-    const int cs = max(x0, 0);
-    const int ce = min(x0 + 128, P);
-    const int so = cs - x0;
-    const uint32_t seg_bytes = (uint32_t)(ce - cs) * 4u;
-    auto issue = [&](int idx) {
-        const int j = jb + idx;
-        const uint32_t slot = (base + (uint32_t)idx) % kPF;
-        const size_t row = (size_t)j * P + cs;
-        uint64_t *bar = &sm.bar[slot];
-        mbar_arrive_expect_tx(bar, seg_bytes * 5u);
-        float *hq = &sm.hq[slot][0][0];
-        float *zn = &sm.zn[(unsigned)j % kDZ][0][0];
-        bulk_copy_g2s(hq + 0 * 128 + so, a.h + row, seg_bytes, bar);
-        bulk_copy_g2s(hq + 1 * 128 + so, a.qx + row, seg_bytes, bar);
-        bulk_copy_g2s(hq + 2 * 128 + so, a.qy + row, seg_bytes, bar);
-        bulk_copy_g2s(zn + 0 * 128 + so, a.z + row, seg_bytes, bar);
-        bulk_copy_g2s(zn + 1 * 128 + so, a.n + row, seg_bytes, bar);
-    };
-    if (threadIdx.x == 0) {
-        fence_proxy_async();                          // earlier items' reads of the rings come first
-        for (; issued < min(kPF, nload); issued++) issue(issued);
-    }
-
-    bool own_cell[4], own_wface[4], in_col[4], in_wface[4], all_cell = true, all_wface = true;
-    const bool edge_lane = c0 <= 0 || c0 + 3 >= nx;   // holds a column outside (0, nx)
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const int c = c0 + k;
-        in_col[k] = c >= 0 && c < nx;                 // a cell of the grid (its south face exists)
-        in_wface[k] = c > 0 && c < nx;                // an interior west face
-        own_cell[k] = c >= own_lo && c < own_hi;
-        own_wface[k] = c >= own_lo && (c < own_hi || (c == nx && own_hi == nx));
-        all_cell &= own_cell[k];
-        all_wface &= own_wface[k];
-    }
-
-    // this level's previous row: input depth and the new faces computed for it
-    float4 hp = make_float4(0, 0, 0, 0), qxw_p = hp, qys_p = hp;
-    float qxe_p = 0.0f;
-    // runs of up to 32 ticks; the float partial sums of the boundary outflow (fq)
-    // and the clipped depth (fc) are folded into the double ledger after each run
-    for (int j0 = jb; j0 <= jlast && !abort; j0 += 32) {
-        float fq = 0.0f, fc = 0.0f;
-        const int jend = min(j0 + 31, jlast);
-        for (int j = j0; j <= jend; j++) {
-            const int r = j - 2 * (lvl - 1);
-            // ---- level 1 waits for its staged row; the other levels only read rows that
-            // level 1 waited for at earlier ticks (ordered by the end-of-tick barrier)
-            bool stop = false;
-            if (lvl == 1 && r >= jb && r <= jload_hi) {
-                const uint32_t g = base + (uint32_t)(r - jb);
-                const int ok = mbar_wait_bounded(&sm.bar[g % kPF], (g / kPF) & 1u, kBudgetNs) ? 1 : 0;
-                stop = !__all_sync(0xffffffffu, ok);
-            }
-            if (!stop && r >= rstart && r <= ny && r <= y1 + K - lvl) {
-                // current row inputs
-                float4 ch = make_float4(0, 0, 0, 0), cqx = ch, cqy = ch, cz = ch, cn = ch, pz = ch, pn = ch;
-                if (r < ny) {
-                    if (lvl == 1) {
-                        const float *hq = &sm.hq[(base + (uint32_t)(r - jb)) % kPF][0][0];
-                        ch = lds4(hq + 0 * 128 + 4 * lane);
-                        cqx = lds4(hq + 1 * 128 + 4 * lane);
-                        cqy = lds4(hq + 2 * 128 + 4 * lane);
-                    } else {
-                        const float *ho = &sm.ho[lvl - 2][(j - 1) & 1][0][0];
-                        ch = lds4(ho + 0 * 128 + 4 * lane);
-                        cqx = lds4(ho + 1 * 128 + 4 * lane);
-                        cqy = lds4(ho + 2 * 128 + 4 * lane);
-                    }
-                    cz = lds4(&sm.zn[(unsigned)r % kDZ][0][4 * lane]);
-                    cn = lds4(&sm.zn[(unsigned)r % kDZ][1][4 * lane]);
-                }
-                if (r > 0) {
-                    pz = lds4(&sm.zn[(unsigned)(r - 1) % kDZ][0][4 * lane]);
-                    pn = lds4(&sm.zn[(unsigned)(r - 1) % kDZ][1][4 * lane]);
-                }
-                if (r == rstart && jb > 0) {
-                    hp = ch;                          // halo row: only becomes the previous row
-                } else {
-                    // ---- new south faces of row r (interior rows branch-free; the boundary
-                    // rows, uniform over the warp, take the Eq. 5-6 path)
-                    float4 qys;
-                    if (r > 0 && r < ny) {
-                        // two faces per paired instruction (bitwise the scalar face_fast_sel)
-#pragma unroll
-                        for (int k = 0; k < 4; k += 2) {
-                            const unsigned long long eL = f2add(f2pack(get(hp, k), get(hp, k + 1)),
-                                                                f2pack(get(pz, k), get(pz, k + 1)));
-                            const unsigned long long eR = f2add(f2pack(get(ch, k), get(ch, k + 1)),
-                                                                f2pack(get(cz, k), get(cz, k + 1)));
-                            const unsigned long long ns = f2add(f2pack(get(pn, k), get(pn, k + 1)),
-                                                                f2pack(get(cn, k), get(cn, k + 1)));
-                            const float2 zm = make_float2(fmaxf(get(pz, k), get(cz, k)), fmaxf(get(pz, k + 1), get(cz, k + 1)));
-                            const float2 v = face_fast_sel_x2(make_float2(get(cqy, k), get(cqy, k + 1)), eL, eR, zm, ns, Kc);
-                            set(qys, k, v.x);
-                            set(qys, k + 1, v.y);
-                        }
-                        if (edge_lane) {
-#pragma unroll
-                            for (int k = 0; k < 4; k++)
-                                if (!in_col[k]) set(qys, k, 0.0f);
-                        }
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            const int c = c0 + k;
-                            float v = 0.0f;
-                            if (in_col[k]) {
-                                float qo = 0.0f;
-                                v = r == 0 ? boundary_fast_flux(a, step, 2, c, get(ch, k), get(cn, k), qo)
-                                           : boundary_fast_flux(a, step, 3, c, get(hp, k), get(pn, k), qo);
-                                if (own_cell[k] && ((r == 0 && y0 == 0) || (r == ny && y1 == ny))) fq += qo;
-                            }
-                            set(qys, k, v);
-                        }
-                    }
-                    // ---- finish row r-1: Eq. 4 and the clip; hand it on (or store it at level K)
-                    const bool has_prev = jb == 0 ? r > 0 : r > rstart + 1;
-                    if (has_prev) {
-                        const int rr = r - 1;
-                        const bool own_row = rr >= y0 && rr < y1;
-                        const bool led_row = own_row && rr >= G.led_j0 && rr < G.led_j1;
-                        float4 fin;
-                        bool neg = false;
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            const float qe = k < 3 ? get(qxw_p, k + 1) : qxe_p;
-                            const float dv = __fadd_rn(__fsub_rn(get(qxw_p, k), qe), __fsub_rn(get(qys_p, k), get(qys, k)));
-                            const float v = __fmaf_rn(Kc.dtdx, dv, get(hp, k));
-                            neg |= v < 0.0f;
-                            set(fin, k, v);
-                        }
-                        if (neg) {                    // rare: clip to zero, book the removed volume
-#pragma unroll
-                            for (int k = 0; k < 4; k++) {
-                                const float v = get(fin, k);
-                                if (v < 0.0f) {
-                                    if (led_row && own_cell[k]) fc -= v;
-                                    set(fin, k, 0.0f);
-                                }
-                            }
-                        }
-                        if (lvl == K && own_row) {
-#pragma unroll
-                            for (int k = 0; k < 4; k++) {
-                                const float v = get(fin, k);
-                                if (own_cell[k]) {
-                                    L.hmax = fmaxf(L.hmax, v);
-                                    L.nan_seen |= (v != v);
-                                }
-                            }
-                        }
-                        if (lvl < K) {
-                            float *ho = &sm.ho[lvl - 1][j & 1][0][0];
-                            sts4(ho + 0 * 128 + 4 * lane, fin);
-                            sts4(ho + 1 * 128 + 4 * lane, qxw_p);
-                            sts4(ho + 2 * 128 + 4 * lane, qys_p);
-                        } else if (own_row) {
-                            const size_t ro = (size_t)rr * P + c0;
-                            if (all_cell) {
-                                *reinterpret_cast<float4 *>(a.h_out + ro) = fin;
-                                *reinterpret_cast<float4 *>(a.qy_out + ro) = qys_p;
-                                if (rr == ny - 1) *reinterpret_cast<float4 *>(a.qy_out + ro + P) = qys;
-                            } else {
-#pragma unroll
-                                for (int k = 0; k < 4; k++)
-                                    if (own_cell[k]) {
-                                        a.h_out[ro + k] = get(fin, k);
-                                        a.qy_out[ro + k] = get(qys_p, k);
-                                        if (rr == ny - 1) a.qy_out[ro + P + k] = get(qys, k);
-                                    }
-                            }
-                            if (all_wface) *reinterpret_cast<float4 *>(a.qx_out + ro) = qxw_p;
-                            else {
-#pragma unroll
-                                for (int k = 0; k < 4; k++)
-                                    if (own_wface[k]) a.qx_out[ro + k] = get(qxw_p, k);
-                            }
-                        }
-                    }
-                    // ---- new west faces of row r; row r becomes this level's previous row
-                    if (r < ny) {
-                        const bool own_row_r = r >= y0 && r < y1;
-                        const float hl0 = __shfl_up_sync(0xffffffffu, ch.w, 1);
-                        const float zl0 = __shfl_up_sync(0xffffffffu, cz.w, 1);
-                        const float nl0 = __shfl_up_sync(0xffffffffu, cn.w, 1);
-                        float4 qxw;
-#pragma unroll
-                        for (int k = 0; k < 4; k += 2) {
-                            const float hla = k == 0 ? hl0 : get(ch, k - 1), hlb = get(ch, k);
-                            const float zla = k == 0 ? zl0 : get(cz, k - 1), zlb = get(cz, k);
-                            const float nla = k == 0 ? nl0 : get(cn, k - 1), nlb = get(cn, k);
-                            const unsigned long long eL = f2add(f2pack(hla, hlb), f2pack(zla, zlb));
-                            const unsigned long long eR = f2add(f2pack(get(ch, k), get(ch, k + 1)),
-                                                                f2pack(get(cz, k), get(cz, k + 1)));
-                            const unsigned long long ns = f2add(f2pack(nla, nlb), f2pack(get(cn, k), get(cn, k + 1)));
-                            const float2 zm = make_float2(fmaxf(zla, get(cz, k)), fmaxf(zlb, get(cz, k + 1)));
-                            const float2 v = face_fast_sel_x2(make_float2(get(cqx, k), get(cqx, k + 1)), eL, eR, zm, ns, Kc);
-                            set(qxw, k, v.x);
-                            set(qxw, k + 1, v.y);
-                        }
-                        if (edge_lane) {              // lanes at or beyond x = 0 or x = nx: Eq. 5-6, or no face
-#pragma unroll
-                            for (int k = 0; k < 4; k++) {
-                                const int c = c0 + k;
-                                if (!in_wface[k]) set(qxw, k, 0.0f);
-                                if (c == 0 || c == nx) {
-                                    float qo = 0.0f;
-                                    const float hl = k == 0 ? hl0 : get(ch, k - 1);
-                                    const float nl = k == 0 ? nl0 : get(cn, k - 1);
-                                    const float v = c == 0 ? boundary_fast_flux(a, step, 0, r, get(ch, 0), get(cn, 0), qo)
-                                                           : boundary_fast_flux(a, step, 1, r, hl, nl, qo);
-                                    if (own_row_r && own_wface[k]) fq += qo;
-                                    set(qxw, k, v);
-                                }
-                            }
-                        }
-                        qxe_p = __shfl_down_sync(0xffffffffu, qxw.x, 1);
-                        hp = ch;
-                        qxw_p = qxw;
-                        qys_p = qys;
-                    }
-                }
-            }
-            // ---- end of tick (shares a timeout); then level 1 refills the ring
-            if (__syncthreads_or(stop ? 1 : 0)) {
-                abort = true;
-                break;
-            }
-            if (lvl == 1 && lane == 0 && r >= jb && r <= jload_hi) {
-                consumed = r - jb + 1;
-                if (issued < nload) {
-                    fence_proxy_async();
-                    issue(issued);
-                    issued++;
-                }
-            }
-        }
-        L.vout += (double)fq * G.dx;
-        L.vclip += (double)fc * G.dx * G.dx;
-    }
-    if (!abort) {
-        base += (uint32_t)nload;
-    } else if (threadIdx.x == 0) {
-        // leave no bulk copy writing into shared memory after exit
-        for (int k = consumed; k < issued; k++) {
-            const uint32_t g = base + (uint32_t)k;
-            mbar_wait_bounded(&sm.bar[g % kPF], (g / kPF) & 1u, kBudgetNs);
-        }
-        atomicOr(&a.ctrl->status, kStatusTimeout);
-    }
-    return abort;
-}
-
-// Block-wide sums of the ledger terms into grid a's control block.
-__device__ __forceinline__ void tiled_flush(const StepArgs<float> &a, const TiledLedger &L, const int want_hmax,
-                                            double *red)
-{
-    const double dtd = a.ctrl->dt;
-    const double bo = block_reduce<false>(L.vout, red);
-    if (threadIdx.x == 0 && bo != 0.0) atomicAdd(&a.ctrl->V_out, dtd * bo);
-    const double bc = block_reduce<false>(L.vclip, red);
-    if (threadIdx.x == 0 && bc != 0.0) atomicAdd(&a.ctrl->V_clip, bc);
-    if (want_hmax) {
-        const double bm = block_reduce<true>(L.nan_seen ? (double)NAN : (double)L.hmax, red);
-        if (threadIdx.x == 0) atomic_max_nonneg(&a.ctrl->hmax_bits, bm);
-    }
-}
-
-// Inflow volume of the K steps and the clock after them (one thread per grid).
-template <int K>
-__device__ __forceinline__ void tiled_finish(const StepArgs<float> &a, const int s0)
-{
-    const double dtd = a.ctrl->dt;
-    double vin = a.ctrl->V_in;
-    for (int s = 0; s < K; s++)
-        for (int k = 0; k < a.n_inflow_sec; k++) {
-            const double Q = a.inflow_Q[(size_t)(s0 + s) * a.n_inflow_sec + k];
-            if (Q > 0.0) vin += dtd * Q;
-        }
-    a.ctrl->V_in = vin;
-    a.ctrl->t = a.t_list[s0 + K];
-}
-
-template <int K, int kPF>
-__device__ __forceinline__ void init_ring(PipeSmem<K, kPF> &sm)
-{
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kPF; s++) mbar_init(&sm.bar[s], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-}
-
-// One grid: work items (chunk, strip) in chunk-major order, block b takes
-// items b, b + grid, ... (a.tile_x strips, a.tile_y rows per chunk).
-template <int K>
-__global__ void __launch_bounds__(K * 32, K == 4 ? 6 : K == 8 ? 2 : 1) step_tiled_kernel(const StepArgs<float> a)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
-    PipeSmem<K, kPF1> &sm = *reinterpret_cast<PipeSmem<K, kPF1> *>(smem_raw);
-    init_ring<K, kPF1>(sm);
-    const int n_strips = a.tile_x, chunk_rows = a.tile_y;
-    const int n_items = n_strips * ((a.geo.ny + chunk_rows - 1) / chunk_rows);
-    const FastConst Kc = tiled_const(a);
-    TiledLedger L;
-    uint32_t base = 0;
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int strip = item % n_strips;
-        const int y0 = (item / n_strips) * chunk_rows;
-        const int y1 = min(y0 + chunk_rows, a.geo.ny);
-        if (tiled_item<K, kPF1>(a, a.s, Kc, strip, y0, y1, sm, base, L)) break;
-    }
-    tiled_flush(a, L, a.want_hmax, red);
-    if (blockIdx.x == 0 && threadIdx.x == 0) tiled_finish<K>(a, a.s);
-}
-
-// Many grids: the items of grid k (its (chunk, strip) items, chunk_rows rows
-// per chunk) are numbered base[k] .. base[k+1] - 1, grids ordered largest
-// first, and block b takes items b, b + grid, ...  A block sums a grid's
-// ledger terms while its items belong to that grid and hands them to the
-// grid's control block when it moves on; the grid's first item books its
-// inflow volume and clock.
-template <int K>
-__global__ void __launch_bounds__(K * 32, K == 4 ? 5 : K == 8 ? 2 : 1)
-    step_tiled_ensemble_kernel(const StepArgs<float> *table, const int *base, const int n, const int chunk_rows,
-                               const int s0, const int want_hmax)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
-    PipeSmem<K, kPFE> &sm = *reinterpret_cast<PipeSmem<K, kPFE> *>(smem_raw);
-    init_ring<K, kPFE>(sm);
-    const int total = base[n];
-    TiledLedger L;
-    uint32_t ring = 0;
-    int cur = -1;
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (base[mid] <= item) lo = mid;
-            else hi = mid - 1;
-        }
-        if (lo != cur) {
-            if (cur >= 0) tiled_flush(table[cur], L, want_hmax, red);
-            L = TiledLedger();
-            cur = lo;
-        }
-        const StepArgs<float> &a = table[lo];
-        const int local = item - base[lo];
-        const int n_strips = (a.geo.nx + out_cols(K) - 1) / out_cols(K);
-        const int strip = local % n_strips;
-        const int y0 = (local / n_strips) * chunk_rows;
-        const int y1 = min(y0 + chunk_rows, a.geo.ny);
-        if (local == 0 && threadIdx.x == 0) tiled_finish<K>(a, s0);
-        if (tiled_item<K, kPFE>(a, s0, tiled_const(a), strip, y0, y1, sm, ring, L)) break;
-    }
-    if (cur >= 0) tiled_flush(table[cur], L, want_hmax, red);
-}
-
-}  // namespace
 
 // Row chunks for the (chunk, strip) work items of a grid of n_strips strips and
 // ny rows on `resident` pipelines: the chunk count minimises the ticks of the
@@ -521,98 +43,37 @@ void tiled_split(int n_strips, int ny, int resident, int K, int *chunk_rows, int
     *blocks = (int)(items < resident ? items : resident);
 }
 
-namespace {
-
-// Blocks of `kernel` (K warps, `smem` bytes) resident on the GPU at once.
-template <typename Kern>
-cudaError_t resident_blocks(Kern kernel, int threads, size_t smem, int *cache, int *out)
-{
-    if (!*cache) {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-        if (e != cudaSuccess) return e;
-        *cache = (per_sm < 1 ? 1 : per_sm) * sms;
-    }
-    *out = *cache;
-    return cudaSuccess;
-}
-
-template <int K>
-cudaError_t launch_k(const StepArgs<float> &a0, cudaStream_t st)
-{
-    static int cache = 0;
-    int resident = 0;
-    cudaError_t e = resident_blocks(step_tiled_kernel<K>, K * 32, sizeof(PipeSmem<K, kPF1>), &cache, &resident);
-    if (e != cudaSuccess) return e;
-    StepArgs<float> a = a0;
-    const int nx = a.geo.nx, ny = a.geo.ny;
-    const int n_strips = (nx + out_cols(K) - 1) / out_cols(K);
-    if (a0.tile_x > 0 && a0.tile_x < resident) resident = a0.tile_x;   // caller's cap on pipelines
-    int chunk_rows = 0, blocks = 0;
-    if (a0.tile_y > 0) {                                                // caller's rows per work item
-        chunk_rows = a0.tile_y < ny ? a0.tile_y : ny;
-        const long long items = (long long)n_strips * ((ny + chunk_rows - 1) / chunk_rows);
-        blocks = (int)(items < resident ? items : resident);
-    } else {
-        tiled_split(n_strips, ny, resident, K, &chunk_rows, &blocks);
-    }
-    a.tile_x = n_strips;
-    a.tile_y = chunk_rows;
-    step_tiled_kernel<K><<<blocks, K * 32, sizeof(PipeSmem<K, kPF1>), st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int K>
-cudaError_t launch_ens_k(const StepArgs<float> *table, const int *base, int n, int total_items, int chunk_rows,
-                         int s0, int want_hmax, cudaStream_t st)
-{
-    static int cache = 0;
-    int resident = 0;
-    cudaError_t e = resident_blocks(step_tiled_ensemble_kernel<K>, K * 32, sizeof(PipeSmem<K, kPFE>), &cache,
-                                    &resident);
-    if (e != cudaSuccess) return e;
-    const int blocks = total_items < resident ? total_items : resident;
-    if (blocks < 1) return cudaSuccess;
-    step_tiled_ensemble_kernel<K><<<blocks, K * 32, sizeof(PipeSmem<K, kPFE>), st>>>(table, base, n, chunk_rows, s0,
-                                                                               want_hmax);
-    return cudaGetLastError();
-}
-
-}  // namespace
-
 int tiled_items(const Geom &g, int chunk_rows, int k_steps)
 {
-    const int n_strips = (g.nx + out_cols(k_steps) - 1) / out_cols(k_steps);
+    const int mode = (g.theta != 1.0 ? 1 : 0) | (g.friction != 0 ? 2 : 0);
+    const int out = out_cols(k_steps, mode);
+    const int n_strips = (g.nx + out - 1) / out;
     return n_strips * ((g.ny + chunk_rows - 1) / chunk_rows);
 }
 
+// Scheme mode of a grid: bit 0 theta weighting, bit 1 vector-norm friction.
+static int tiled_mode(const Geom &g) { return (g.theta != 1.0 ? 1 : 0) | (g.friction != 0 ? 2 : 0); }
+
+// step_tiled_opts.cu: the same launchers for modes 1..3.
+cudaError_t launch_step_tiled_opts(const StepArgs<float> &a, int mode, cudaStream_t st);
+cudaError_t launch_step_tiled_ensemble_opts(const StepArgs<float> *table, const int *base, int n, int total_items,
+                                            int chunk_rows, int k_steps, int s0, int want_hmax, int mode,
+                                            cudaStream_t st);
+
 cudaError_t launch_step_tiled_ensemble(const StepArgs<float> *table, const int *base, int n, int total_items,
-                                       int chunk_rows, int k_steps, int s0, int want_hmax, cudaStream_t st)
+                                       int chunk_rows, int k_steps, int s0, int want_hmax, int mode, cudaStream_t st)
 {
-    switch (k_steps) {
-    case 1: return launch_ens_k<1>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
-    case 2: return launch_ens_k<2>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
-    case 3: return launch_ens_k<3>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
-    case 4: return launch_ens_k<4>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
-    case 8: return launch_ens_k<8>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
-    default: return cudaErrorInvalidValue;
-    }
+    if (mode != 0)
+        return launch_step_tiled_ensemble_opts(table, base, n, total_items, chunk_rows, k_steps, s0, want_hmax, mode,
+                                               st);
+    return launch_tiled_ensemble_mode<0>(table, base, n, total_items, chunk_rows, k_steps, s0, want_hmax, st);
 }
 
 cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st)
 {
-    switch (a.k_steps) {
-    case 1: return launch_k<1>(a, st);
-    case 2: return launch_k<2>(a, st);
-    case 3: return launch_k<3>(a, st);
-    case 4: return launch_k<4>(a, st);
-    case 8: return launch_k<8>(a, st);
-    default: return cudaErrorInvalidValue;
-    }
+    const int mode = tiled_mode(a.geo);
+    if (mode != 0) return launch_step_tiled_opts(a, mode, st);
+    return launch_tiled_mode<0>(a, st);
 }
 
 }  // namespace flood

@@ -186,7 +186,7 @@ def test_create_rejects_bad_friction_and_unsupported_kernels():
         o.friction = bad
         st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
         assert st == F.ERR_ARG and "friction" in F.flood_last_error(None)
-    for kernel in (F.KERNEL_ROWS, F.KERNEL_TILED):
+    for kernel in (F.KERNEL_ROWS,):
         o = F.default_opts()
         o.friction = 1
         o.kernel = kernel
@@ -201,7 +201,7 @@ def test_create_rejects_theta_out_of_range_and_unsupported_kernels():
         o.theta = bad
         st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
         assert st == F.ERR_ARG and "theta" in F.flood_last_error(None)
-    for kernel in (F.KERNEL_ROWS, F.KERNEL_TILED):
+    for kernel in (F.KERNEL_ROWS,):
         o = F.default_opts()
         o.theta = 0.8
         o.kernel = kernel

@@ -376,7 +376,7 @@ def test_theta_fp64_channel_1000_steps():
     check_ledger(o, L, 1e-12)
 
 
-@pytest.mark.parametrize("kernel", [1, 4, 5])
+@pytest.mark.parametrize("kernel", [1, 4, 5, 3])
 @pytest.mark.parametrize("shape,seed", [((130, 70), 2), ((257, 129), 6), ((129, 33), 9)])
 def test_theta_fp32_matches_oracle(kernel, shape, seed):
     p = with_theta(inputs.random_small(shape[0], shape[1], seed), 0.8)
@@ -398,16 +398,63 @@ def test_theta_tma_tiles_equal_row_staging_bitwise(tile):
         assert np.array_equal(a.read(f), b.read(f)), f
 
 
-def test_theta_adjoint_and_ensemble_are_refused():
+def test_theta_adjoint_is_refused():
     Fm = F()
     p = with_theta(inputs.random_small(20, 12, 2), 0.8)
     s = Fm.Sim(p, precision=Fm.F64)
     with pytest.raises(Fm.FloodError) as e:
         s.adjoint(4, np.array([[3, 3]]), np.ones((4, 1)))
     assert e.value.status == Fm.ERR_UNSUPPORTED
-    with pytest.raises(Fm.FloodError) as e:
-        Fm.Ensemble([p])
-    assert e.value.status == Fm.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("theta,friction", [(0.75, 0), (1.0, 1), (0.75, 1)])
+@pytest.mark.parametrize("K,E,tile", [(4, 4, (0, 0)), (4, 8, (2, 9)), (2, 4, (1, 3)), (3, 6, (3, 40)),
+                                      (1, 4, (0, 0)), (8, 8, (0, 0)), (8, 16, (2, 17))])
+def test_options_temporal_blocking_equals_single_steps_bitwise(theta, friction, K, E, tile):
+    """K steps per launch with the theta weighting and/or the vector norm give the
+    bits of K single steps of the stream kernel (the same face arithmetic), on
+    ragged grids with several strips, chunk seams and pipelines walking many items."""
+    Fm = F()
+    for shape, seed in (((257, 129), 6), ((130, 70), 2), ((33, 17), 0)):
+        p = as_f32_problem(with_friction(inputs.random_small(shape[0], shape[1], seed), friction, theta))
+        p.opts.epoch_steps = E
+        a = Fm.Sim(p, kernel=Fm.KERNEL_STREAM)
+        b = Fm.Sim(p, kernel=Fm.KERNEL_TILED, steps_per_launch=K, tile=tile)
+        for n in (3 * E, 5, 2 * E + 1):
+            a.step(n)
+            b.step(n)
+        for f in (Fm.FIELD_H, Fm.FIELD_QX, Fm.FIELD_QY):
+            assert np.array_equal(a.read(f), b.read(f)), (shape, f)
+        La, Lb = a.ledger(), b.ledger()
+        for k in ("t", "dt", "V_in", "volume", "h_max", "step"):
+            assert La[k] == pytest.approx(Lb[k], rel=1e-12, abs=1e-12), k
+        for k in ("V_out", "V_clip"):
+            assert La[k] == pytest.approx(Lb[k], rel=1e-6, abs=1e-9), k
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("kernel,K", [(4, 0), (3, 4), (3, 2)])
+@pytest.mark.parametrize("theta,friction", [(0.8, 0), (1.0, 1), (0.8, 1)])
+def test_options_ensemble_members_equal_solo_runs(kernel, K, theta, friction):
+    Fm = F()
+    probs = []
+    for nx, ny, seed in ((130, 70, 2), (257, 129, 6), (64, 300, 17), (33, 17, 0)):
+        probs.append(as_f32_problem(with_friction(inputs.random_small(nx, ny, seed), friction, theta)))
+    ens = Fm.Ensemble(probs)
+    E = probs[0].opts.epoch_steps
+    ens.set_launch(2, 16, 2 * E)
+    ens.set_kernel(kernel, K)
+    ens.step(3)
+    ens.step(4 * E)
+    n = 3 + 4 * E
+    for mb, p in zip(ens.members, probs):
+        s = Fm.Sim(p, kernel=Fm.KERNEL_STREAM)
+        s.step(n)
+        for f in (Fm.FIELD_H, Fm.FIELD_QX, Fm.FIELD_QY):
+            assert np.array_equal(mb.read(f), s.read(f)), (p.name, f)
+        s.close()
+    ens.close()
 
 
 # ---------------------------------------------------------------- vector-norm friction
@@ -445,7 +492,7 @@ def test_vector_friction_fp64_channel_1000_steps():
     check_ledger(o, L, 1e-12)
 
 
-@pytest.mark.parametrize("kernel", [1, 4, 5])
+@pytest.mark.parametrize("kernel", [1, 4, 5, 3])
 @pytest.mark.parametrize("theta", [1.0, 0.8])
 @pytest.mark.parametrize("shape,seed", [((130, 70), 2), ((257, 129), 6), ((129, 33), 9)])
 def test_vector_friction_fp32_matches_oracle(kernel, theta, shape, seed):
@@ -457,7 +504,7 @@ def test_vector_friction_fp32_matches_oracle(kernel, theta, shape, seed):
     check_ledger(o, L, TOL32_MASS)
 
 
-@pytest.mark.parametrize("kernel", [4, 5])
+@pytest.mark.parametrize("kernel", [4, 5, 3])
 def test_vector_friction_fp32_channel_1000_steps(kernel):
     p = with_friction(inputs.c1_tilted_channel(), 1)
     o, V0, h, qx, qy, L = run_pair(p, 1000, F().F32, kernel=kernel)
@@ -489,15 +536,12 @@ def test_vector_friction_auto_runs_the_tensor_tile_kernel():
         assert np.array_equal(a.read(f), b.read(f)), f
 
 
-def test_vector_friction_adjoint_and_ensemble_are_refused():
+def test_vector_friction_adjoint_is_refused():
     Fm = F()
     p = with_friction(inputs.random_small(20, 12, 2), 1)
     s = Fm.Sim(p, precision=Fm.F64)
     with pytest.raises(Fm.FloodError) as e:
         s.adjoint(4, np.array([[3, 3]]), np.ones((4, 1)))
-    assert e.value.status == Fm.ERR_UNSUPPORTED
-    with pytest.raises(Fm.FloodError) as e:
-        Fm.Ensemble([p])
     assert e.value.status == Fm.ERR_UNSUPPORTED
 
 

@@ -93,7 +93,7 @@ def test_c2_full_grid_1000_steps_matches_oracle(wet):
     assert (o.h > 0).sum() > (0.25 * o.h.size if wet else 500)
 
 
-@pytest.mark.parametrize("kernel", [4, 5])
+@pytest.mark.parametrize("kernel", [4, 5, 3])
 def test_c2_full_grid_vector_friction_matches_oracle(kernel):
     Fm = F()
     p = inputs.c2_fractal()
@@ -141,7 +141,7 @@ def window_oracle(p, jc, ic, r, dt, steps):
     return o
 
 
-@pytest.mark.parametrize("kernel,k,friction", [(4, 0, 0), (5, 0, 0), (3, 4, 0), (5, 0, 1)])
+@pytest.mark.parametrize("kernel,k,friction", [(4, 0, 0), (5, 0, 0), (3, 4, 0), (5, 0, 1), (3, 4, 1)])
 def test_c3_full_grid_sampled_cells_match_oracle(c3, kernel, k, friction):
     Fm = F()
     p, N, r, pick = c3
