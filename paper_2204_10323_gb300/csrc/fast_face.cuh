@@ -18,10 +18,13 @@ struct FastConst {
 };
 
 // Numerator discharge of a theta-weighted face from its own and its two
-// neighbours' discharge along the same axis.
+// neighbours' discharge along the same axis: theta q + w (q_prev + q_next) as
+// one fused multiply-add (the paired form below is the same operation; a paired
+// multiply followed by a paired add is fused by the hardware, so both forms
+// write the fusion out).
 __device__ __forceinline__ float theta_q(float q, float q_prev, float q_next, const FastConst &k)
 {
-    return __fadd_rn(__fmul_rn(k.theta, q), __fmul_rn(k.w, __fadd_rn(q_prev, q_next)));
+    return __fmaf_rn(k.theta, q, __fmul_rn(k.w, __fadd_rn(q_prev, q_next)));
 }
 
 // x^(-7/3) for x > 0 as 2^(-7/3 log2 x) with the hardware base-2 logarithm
@@ -140,9 +143,11 @@ __device__ __forceinline__ float ex2_fast(float x)
     return r;
 }
 
-// etaL, etaR, zmax, nsum, q: the two faces' arguments of face_fast_sel.
-__device__ __forceinline__ float2 face_fast_sel_x2(float2 q, unsigned long long etaL, unsigned long long etaR,
-                                                   float2 zmax, unsigned long long nsum, const FastConst &k)
+// face_fast_sel_gen for two faces: qmag and qn packed (|q| of the friction term,
+// numerator discharge), etaL, etaR, nsum packed, zmax the two faces' max(z_L, z_R).
+__device__ __forceinline__ float2 face_fast_sel_x2_gen(unsigned long long qmag, unsigned long long qn,
+                                                       unsigned long long etaL, unsigned long long etaR, float2 zmax,
+                                                       unsigned long long nsum, const FastConst &k)
 {
     const float2 eL = f2unpack(etaL), eR = f2unpack(etaR);
     const unsigned long long hf = f2sub(f2pack(fmaxf(eL.x, eR.x), fmaxf(eL.y, eR.y)), f2pack(zmax.x, zmax.y));
@@ -151,12 +156,35 @@ __device__ __forceinline__ float2 face_fast_sel_x2(float2 q, unsigned long long 
     const float2 lv = f2unpack(l);
     const unsigned long long r7 = f2pack(ex2_fast(lv.x), ex2_fast(lv.y));
     const unsigned long long nf = f2mul(f2pack(0.5f, 0.5f), nsum);
-    const unsigned long long aq = f2mul(f2mul(f2pack(k.gdt, k.gdt), f2mul(nf, nf)), f2pack(fabsf(q.x), fabsf(q.y)));
-    const unsigned long long num =
-        f2fma(f2mul(f2pack(-k.a1, -k.a1), hf), f2sub(etaR, etaL), f2pack(q.x, q.y));
+    const unsigned long long aq = f2mul(f2mul(f2pack(k.gdt, k.gdt), f2mul(nf, nf)), qmag);
+    const unsigned long long num = f2fma(f2mul(f2pack(-k.a1, -k.a1), hf), f2sub(etaR, etaL), qn);
     const float2 den = f2unpack(f2fma(aq, r7, f2pack(1.0f, 1.0f)));
     const float2 v = f2unpack(f2mul(num, f2pack(rcp_fast(den.x), rcp_fast(den.y))));
     return make_float2(h.x > k.h_dry ? v.x : 0.0f, h.y > k.h_dry ? v.y : 0.0f);
+}
+
+// etaL, etaR, zmax, nsum, q: the two faces' arguments of face_fast_sel.
+__device__ __forceinline__ float2 face_fast_sel_x2(float2 q, unsigned long long etaL, unsigned long long etaR,
+                                                   float2 zmax, unsigned long long nsum, const FastConst &k)
+{
+    return face_fast_sel_x2_gen(f2pack(fabsf(q.x), fabsf(q.y)), f2pack(q.x, q.y), etaL, etaR, zmax, nsum, k);
+}
+
+// theta_q for two faces (packed q, previous and next neighbours).
+__device__ __forceinline__ unsigned long long theta_q_x2(unsigned long long q, unsigned long long q_prev,
+                                                         unsigned long long q_next, const FastConst &k)
+{
+    return f2fma(f2pack(k.theta, k.theta), q, f2mul(f2pack(k.w, k.w), f2add(q_prev, q_next)));
+}
+
+// q_norm for two faces (packed q and the four orthogonal neighbours a, b, c, d).
+__device__ __forceinline__ unsigned long long q_norm_x2(unsigned long long q, unsigned long long a,
+                                                        unsigned long long b, unsigned long long c,
+                                                        unsigned long long d)
+{
+    const unsigned long long qo = f2mul(f2pack(0.25f, 0.25f), f2add(f2add(a, b), f2add(c, d)));
+    const float2 s = f2unpack(f2fma(q, q, f2mul(qo, qo)));
+    return f2pack(sqrt_fast(s.x), sqrt_fast(s.y));
 }
 
 // Eq. 3 at one face: eta_L, eta_R water levels, zmax = max(z_L, z_R),

@@ -279,15 +279,31 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
                             xs4 = __shfl_down_sync(0xffffffffu, qxo_p.x, 1);
                             xn4 = __shfl_down_sync(0xffffffffu, cqx.x, 1);
                         }
+                        // two faces per paired instruction (bitwise the scalar face_fast_sel_gen)
 #pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            const float zl = get(pz, k), zr = get(cz, k), q = get(cqy, k);
-                            const float qn = kTheta ? theta_q(q, get(qyo_p, k), get(qyn, k), Kc) : q;
-                            const float qm = kVec ? q_norm(q, get(qxo_p, k), k < 3 ? get(qxo_p, k + 1) : xs4,
-                                                           get(cqx, k), k < 3 ? get(cqx, k + 1) : xn4)
-                                                  : fabsf(q);
-                            set(qys, k, face_fast_sel_gen(qm, qn, get(hp, k) + zl, get(ch, k) + zr, fmaxf(zl, zr),
-                                                          get(pn, k) + get(cn, k), Kc));
+                        for (int k = 0; k < 4; k += 2) {
+                            const unsigned long long q = f2pack(get(cqy, k), get(cqy, k + 1));
+                            unsigned long long qn = q, qm;
+                            if constexpr (kTheta)
+                                qn = theta_q_x2(q, f2pack(get(qyo_p, k), get(qyo_p, k + 1)),
+                                                f2pack(get(qyn, k), get(qyn, k + 1)), Kc);
+                            if constexpr (kVec)
+                                qm = q_norm_x2(q, f2pack(get(qxo_p, k), get(qxo_p, k + 1)),
+                                               f2pack(get(qxo_p, k + 1), k + 1 < 3 ? get(qxo_p, k + 2) : xs4),
+                                               f2pack(get(cqx, k), get(cqx, k + 1)),
+                                               f2pack(get(cqx, k + 1), k + 1 < 3 ? get(cqx, k + 2) : xn4));
+                            else
+                                qm = f2pack(fabsf(get(cqy, k)), fabsf(get(cqy, k + 1)));
+                            const unsigned long long eL = f2add(f2pack(get(hp, k), get(hp, k + 1)),
+                                                                f2pack(get(pz, k), get(pz, k + 1)));
+                            const unsigned long long eR = f2add(f2pack(get(ch, k), get(ch, k + 1)),
+                                                                f2pack(get(cz, k), get(cz, k + 1)));
+                            const unsigned long long ns = f2add(f2pack(get(pn, k), get(pn, k + 1)),
+                                                                f2pack(get(cn, k), get(cn, k + 1)));
+                            const float2 zm = make_float2(fmaxf(get(pz, k), get(cz, k)), fmaxf(get(pz, k + 1), get(cz, k + 1)));
+                            const float2 v = face_fast_sel_x2_gen(qm, qn, eL, eR, zm, ns, Kc);
+                            set(qys, k, v.x);
+                            set(qys, k + 1, v.y);
                         }
                         if (edge_lane) {
 #pragma unroll
@@ -412,20 +428,32 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
                                 ys0 = __shfl_up_sync(0xffffffffu, cqy.w, 1);
                                 yn0 = __shfl_up_sync(0xffffffffu, qyn.w, 1);
                             }
+                            // two faces per paired instruction (bitwise the scalar face_fast_sel_gen)
 #pragma unroll
-                            for (int k = 0; k < 4; k++) {
-                                const float hl = k == 0 ? hl0 : get(ch, k - 1);
-                                const float zl = k == 0 ? zl0 : get(cz, k - 1);
-                                const float nl = k == 0 ? nl0 : get(cn, k - 1);
-                                const float zr = get(cz, k), q = get(cqx, k);
-                                const float qn = kTheta ? theta_q(q, k == 0 ? ql0 : get(cqx, k - 1),
-                                                                  k == 3 ? qr3 : get(cqx, k + 1), Kc)
-                                                        : q;
-                                const float qm = kVec ? q_norm(q, k == 0 ? ys0 : get(cqy, k - 1), get(cqy, k),
-                                                               k == 0 ? yn0 : get(qyn, k - 1), get(qyn, k))
-                                                      : fabsf(q);
-                                set(qxw, k, face_fast_sel_gen(qm, qn, hl + zl, get(ch, k) + zr, fmaxf(zl, zr),
-                                                              nl + get(cn, k), Kc));
+                            for (int k = 0; k < 4; k += 2) {
+                                const float hla = k == 0 ? hl0 : get(ch, k - 1), hlb = get(ch, k);
+                                const float zla = k == 0 ? zl0 : get(cz, k - 1), zlb = get(cz, k);
+                                const float nla = k == 0 ? nl0 : get(cn, k - 1), nlb = get(cn, k);
+                                const unsigned long long q = f2pack(get(cqx, k), get(cqx, k + 1));
+                                unsigned long long qn = q, qm;
+                                if constexpr (kTheta)
+                                    qn = theta_q_x2(q, f2pack(k == 0 ? ql0 : get(cqx, k - 1), get(cqx, k)),
+                                                    f2pack(get(cqx, k + 1), k + 1 == 3 ? qr3 : get(cqx, k + 2)), Kc);
+                                if constexpr (kVec)
+                                    qm = q_norm_x2(q, f2pack(k == 0 ? ys0 : get(cqy, k - 1), get(cqy, k)),
+                                                   f2pack(get(cqy, k), get(cqy, k + 1)),
+                                                   f2pack(k == 0 ? yn0 : get(qyn, k - 1), get(qyn, k)),
+                                                   f2pack(get(qyn, k), get(qyn, k + 1)));
+                                else
+                                    qm = f2pack(fabsf(get(cqx, k)), fabsf(get(cqx, k + 1)));
+                                const unsigned long long eL = f2add(f2pack(hla, hlb), f2pack(zla, zlb));
+                                const unsigned long long eR = f2add(f2pack(get(ch, k), get(ch, k + 1)),
+                                                                    f2pack(get(cz, k), get(cz, k + 1)));
+                                const unsigned long long ns = f2add(f2pack(nla, nlb), f2pack(get(cn, k), get(cn, k + 1)));
+                                const float2 zm = make_float2(fmaxf(zla, get(cz, k)), fmaxf(zlb, get(cz, k + 1)));
+                                const float2 v = face_fast_sel_x2_gen(qm, qn, eL, eR, zm, ns, Kc);
+                                set(qxw, k, v.x);
+                                set(qxw, k + 1, v.y);
                             }
                         } else {
 #pragma unroll
