@@ -426,7 +426,9 @@ const char *flood_version(void);
  * fixed device array of 65536 row sums (512 KiB) that every GPU loading the
  * library keeps until exit, so ny > 65536 returns FLOOD_ERR_ARG.  The first
  * call on each device (with that device current) looks up the scratch's
- * address; make that call outside any stream capture.  All calls on a device
+ * address; make that call outside any stream capture.  The address is kept
+ * for the life of the process and does not survive cudaDeviceReset on that
+ * device: do not call this entry point on a device after resetting it.  All calls on a device
  * share the scratch, which keeps the last call's row sums: calls whose kernels
  * overlap on the GPU race.  Errors: flood_last_error(NULL).
  */
