@@ -215,8 +215,6 @@ class Oracle:
                                _dp(self.h), _dp(self.qx), _dp(self.qy), C.byref(self.ledger), int(n_steps),
                                cells.ctypes.data_as(C.POINTER(C.c_int64)), cells.size, _dp(seed), _dp(gn),
                                _dp(lh), _dp(lqx), _dp(lqy))
-        if rc == -3:
-            raise NotImplementedError("the oracle adjoint covers Eq. 3 as printed (theta = 1, own-component friction)")
         if rc != 0:
             raise MemoryError("oracle adjoint store")
         return (gn, lh, lqx, lqy) if want_state else gn

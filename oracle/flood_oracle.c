@@ -440,60 +440,85 @@ double orc_volume(const orc_params *p, const double *h)
 /* ------------------------------------------------------------------ adjoint
  * Reverse-mode derivative of the run above with the time-step schedule held
  * fixed (dt does not depend on n).  Non-smooth points take these branches:
- * max(eta_L, eta_R) sends its derivative to L on a tie; d|q|/dq = 0 at q = 0;
- * the dry-face test, the outflow dry test and the depth clip are constant
- * masks.  The inflow W solve (Eq. 6) is differentiated exactly through the
- * implicit function theorem.  All forward states are stored (no checkpoints).
+ * max(eta_L, eta_R) sends its derivative to L on a tie; d|q|/dq = 0 at q = 0,
+ * and for the vector norm d|q|/d(q, qo) = 0 where |q| = 0; the dry-face test,
+ * the outflow dry test and the depth clip are constant masks.  The inflow W
+ * solve (Eq. 6) is differentiated exactly through the implicit function
+ * theorem.  All forward states are stored (no checkpoints).
  */
 
+/* Forward values of one face of Eq. 3 in the general form
+ * F = (qn - a hf (eta_r - eta_l)) / (1 + cc qmag), cc = g dt nf^2 hf^(-7/3):
+ * qn the numerator discharge (theta_q), qmag the friction magnitude (q_mag),
+ * qo the mean orthogonal discharge of the vector norm (0 otherwise). */
 typedef struct {
-    double q, eta_l, eta_r, hf, nf, den, F, fric;   /* forward values of one wet face */
+    double q, qmag, qo, eta_l, eta_r, hf, nf, den, F, cc;
     int wet;
 } face_fwd;
 
-static face_fwd face_forward(const orc_params *p, double dt, double q, double hL, double zL,
-                             double nL, double hR, double zR, double nR)
+static face_fwd face_forward(const orc_params *p, double dt, double q, double qn, double qmag, double qo,
+                             double hL, double zL, double nL, double hR, double zR, double nR)
 {
     face_fwd f;
     f.q = q;
+    f.qmag = qmag;
+    f.qo = qo;
     f.eta_l = hL + zL;
     f.eta_r = hR + zR;
     f.hf = fmax(f.eta_l, f.eta_r) - fmax(zL, zR);
     f.wet = f.hf > p->h_dry;
     f.nf = 0.5 * (nL + nR);
-    if (!f.wet) { f.F = 0.0; f.den = 1.0; f.fric = 0.0; return f; }
+    if (!f.wet) { f.F = 0.0; f.den = 1.0; f.cc = 0.0; return f; }
     double slope_term = p->g * dt * f.hf * (f.eta_r - f.eta_l) / p->dx;
     double hf_m73 = 1.0 / (f.hf * f.hf * cbrt(f.hf));
-    f.fric = p->g * dt * f.nf * f.nf * fabs(q) * hf_m73;
-    f.den = 1.0 + f.fric;
-    f.F = (q - slope_term) / f.den;
+    f.cc = p->g * dt * f.nf * f.nf * hf_m73;
+    f.den = 1.0 + f.cc * qmag;
+    f.F = (qn - slope_term) / f.den;
     return f;
 }
 
-/* Pull mu (adjoint of the new face flux) back to q, h_L, h_R, n_L, n_R. */
-static void face_reverse(const orc_params *p, double dt, const face_fwd *f, double mu,
-                         double *lq, double *lhL, double *lhR, double *lnL, double *lnR)
+/* Pull mu (adjoint of the new face flux) back to the face's own old discharge
+ * (lq), its two neighbours along the axis (lqp, lqn; theta weighting), each of
+ * the four orthogonal faces of the vector norm (lo), h_L, h_R, n_L, n_R. */
+static void face_reverse(const orc_params *p, double dt, const face_fwd *f, double mu, double *lq,
+                         double *lqp, double *lqn, double *lo, double *lhL, double *lhR, double *lnL,
+                         double *lnR)
 {
-    *lq = *lhL = *lhR = *lnL = *lnR = 0.0;
+    *lq = *lqp = *lqn = *lo = *lhL = *lhR = *lnL = *lnR = 0.0;
     if (!f->wet || mu == 0.0) return;
-    double sgn = f->q > 0.0 ? 1.0 : (f->q < 0.0 ? -1.0 : 0.0);
     double a = p->g * dt / p->dx;
-    /* F = (q - a hf (eta_r - eta_l)) / (1 + c),  c = g dt nf^2 |q| hf^(-7/3) */
-    double dF_dq = (1.0 - f->F * (f->fric == 0.0 ? 0.0 : f->fric / fabs(f->q)) * sgn) / f->den;
-    if (f->q == 0.0) {
-        /* c = 0 at q = 0 and dc/dq = g dt nf^2 sgn(q) hf^(-7/3) = 0 there */
-        dF_dq = 1.0 / f->den;
+    double th = p->theta, w = 0.5 * (1.0 - p->theta);
+    /* dF/dqn = 1/den, dF/dqmag = -F cc / den */
+    double dF_dqmag = -f->F * f->cc / f->den;
+    double dqmag_dq, dqmag_dqo;
+    if (p->friction == 0) {
+        dqmag_dq = f->q > 0.0 ? 1.0 : (f->q < 0.0 ? -1.0 : 0.0);
+        dqmag_dqo = 0.0;
+    } else if (f->qmag > 0.0) {
+        dqmag_dq = f->q / f->qmag;
+        dqmag_dqo = f->qo / f->qmag;
+    } else {
+        dqmag_dq = dqmag_dqo = 0.0;
     }
-    double dF_dhf = (-a * (f->eta_r - f->eta_l) + f->F * (7.0 / 3.0) * f->fric / f->hf) / f->den;
+    double fric = f->cc * f->qmag;
+    double dF_dhf = (-a * (f->eta_r - f->eta_l) + f->F * (7.0 / 3.0) * fric / f->hf) / f->den;
     double dF_detal = a * f->hf / f->den;
     double dF_detar = -a * f->hf / f->den;
-    double dF_dnf = -f->F * (2.0 * f->fric / f->nf) / f->den;
+    double dF_dnf = -f->F * (2.0 * fric / f->nf) / f->den;
     int left_max = f->eta_l >= f->eta_r;
-    *lq = mu * dF_dq;
+    *lq = mu * (th / f->den + dF_dqmag * dqmag_dq);
+    if (p->theta != 1.0) *lqp = *lqn = mu * w / f->den;
+    *lo = mu * dF_dqmag * dqmag_dqo * 0.25;
     *lhL = mu * (dF_detal + (left_max ? dF_dhf : 0.0));
     *lhR = mu * (dF_detar + (left_max ? 0.0 : dF_dhf));
     *lnL = mu * 0.5 * dF_dnf;
     *lnR = mu * 0.5 * dF_dnf;
+}
+
+/* The mean orthogonal discharge of the vector norm (0 for the face's own |q|). */
+static double q_ortho(const orc_params *p, double a, double b, double c, double d)
+{
+    return p->friction == 0 ? 0.0 : 0.25 * ((a + b) + (c + d));
 }
 
 /* d(cell discharge)/d(depth) divided by the discharge: p_exp / h. */
@@ -519,16 +544,24 @@ static void orc_step_reverse(const orc_params *p, const orc_section *secs, int32
     double *lqy_out = (double *)calloc(NY, sizeof(double));
     orc_ledger dummy = {0};
 
-    /* forward recompute of the new face fluxes */
+    /* forward recompute of the new face fluxes (as in the step) */
     boundary_faces(p, secs, nsec, z, n, h, dt, t, qxn, qyn, &dummy);
     for (int32_t j = 0; j < ny; j++)
         for (int32_t i = 1; i < nx; i++)
-            QX(qxn, j, i) = face_update(p, dt, QX(qx, j, i), QX(qx, j, i), fabs(QX(qx, j, i)), H(h, j, i - 1), H(z, j, i - 1),
-                                        H(n, j, i - 1), H(h, j, i), H(z, j, i), H(n, j, i));
+            QX(qxn, j, i) = face_update(p, dt, QX(qx, j, i),
+                                        theta_q(p, QX(qx, j, i), QX(qx, j, i - 1), QX(qx, j, i + 1)),
+                                        q_mag(p, QX(qx, j, i), QY(qy, j, i - 1), QY(qy, j, i),
+                                              QY(qy, j + 1, i - 1), QY(qy, j + 1, i)),
+                                        H(h, j, i - 1), H(z, j, i - 1), H(n, j, i - 1), H(h, j, i),
+                                        H(z, j, i), H(n, j, i));
     for (int32_t j = 1; j < ny; j++)
         for (int32_t i = 0; i < nx; i++)
-            QY(qyn, j, i) = face_update(p, dt, QY(qy, j, i), QY(qy, j, i), fabs(QY(qy, j, i)), H(h, j - 1, i), H(z, j - 1, i),
-                                        H(n, j - 1, i), H(h, j, i), H(z, j, i), H(n, j, i));
+            QY(qyn, j, i) = face_update(p, dt, QY(qy, j, i),
+                                        theta_q(p, QY(qy, j, i), QY(qy, j - 1, i), QY(qy, j + 1, i)),
+                                        q_mag(p, QY(qy, j, i), QX(qx, j - 1, i), QX(qx, j - 1, i + 1),
+                                              QX(qx, j, i), QX(qx, j, i + 1)),
+                                        H(h, j - 1, i), H(z, j - 1, i), H(n, j - 1, i), H(h, j, i),
+                                        H(z, j, i), H(n, j, i));
 
     /* Eq. 4 and the clip: h' = max(h + dt div / dx, 0) (kept when h + ... >= 0) */
     for (int32_t j = 0; j < ny; j++)
@@ -556,14 +589,24 @@ static void orc_step_reverse(const orc_params *p, const orc_section *secs, int32
             QY(lqy, j, i) = mu;
         }
 
-    /* interior faces through Eq. 3 */
+    /* interior faces through Eq. 3 (numerator discharge and friction magnitude
+       taken with the same neighbours as the forward step) */
     for (int32_t j = 0; j < ny; j++)
         for (int32_t i = 1; i < nx; i++) {
-            face_fwd f = face_forward(p, dt, QX(qx, j, i), H(h, j, i - 1), H(z, j, i - 1),
-                                      H(n, j, i - 1), H(h, j, i), H(z, j, i), H(n, j, i));
-            double lq, lhL, lhR, lnL, lnR;
-            face_reverse(p, dt, &f, QX(lqx, j, i), &lq, &lhL, &lhR, &lnL, &lnR);
+            double q = QX(qx, j, i);
+            double a = QY(qy, j, i - 1), b = QY(qy, j, i), c = QY(qy, j + 1, i - 1), d = QY(qy, j + 1, i);
+            face_fwd f = face_forward(p, dt, q, theta_q(p, q, QX(qx, j, i - 1), QX(qx, j, i + 1)),
+                                      q_mag(p, q, a, b, c, d), q_ortho(p, a, b, c, d), H(h, j, i - 1),
+                                      H(z, j, i - 1), H(n, j, i - 1), H(h, j, i), H(z, j, i), H(n, j, i));
+            double lq, lqp, lqn, lo, lhL, lhR, lnL, lnR;
+            face_reverse(p, dt, &f, QX(lqx, j, i), &lq, &lqp, &lqn, &lo, &lhL, &lhR, &lnL, &lnR);
             QX(lqx_out, j, i) += lq;
+            QX(lqx_out, j, i - 1) += lqp;
+            QX(lqx_out, j, i + 1) += lqn;
+            QY(lqy_out, j, i - 1) += lo;
+            QY(lqy_out, j, i) += lo;
+            QY(lqy_out, j + 1, i - 1) += lo;
+            QY(lqy_out, j + 1, i) += lo;
             H(lh_out, j, i - 1) += lhL;
             H(lh_out, j, i) += lhR;
             H(gn, j, i - 1) += lnL;
@@ -571,11 +614,20 @@ static void orc_step_reverse(const orc_params *p, const orc_section *secs, int32
         }
     for (int32_t j = 1; j < ny; j++)
         for (int32_t i = 0; i < nx; i++) {
-            face_fwd f = face_forward(p, dt, QY(qy, j, i), H(h, j - 1, i), H(z, j - 1, i),
-                                      H(n, j - 1, i), H(h, j, i), H(z, j, i), H(n, j, i));
-            double lq, lhL, lhR, lnL, lnR;
-            face_reverse(p, dt, &f, QY(lqy, j, i), &lq, &lhL, &lhR, &lnL, &lnR);
+            double q = QY(qy, j, i);
+            double a = QX(qx, j - 1, i), b = QX(qx, j - 1, i + 1), c = QX(qx, j, i), d = QX(qx, j, i + 1);
+            face_fwd f = face_forward(p, dt, q, theta_q(p, q, QY(qy, j - 1, i), QY(qy, j + 1, i)),
+                                      q_mag(p, q, a, b, c, d), q_ortho(p, a, b, c, d), H(h, j - 1, i),
+                                      H(z, j - 1, i), H(n, j - 1, i), H(h, j, i), H(z, j, i), H(n, j, i));
+            double lq, lqp, lqn, lo, lhL, lhR, lnL, lnR;
+            face_reverse(p, dt, &f, QY(lqy, j, i), &lq, &lqp, &lqn, &lo, &lhL, &lhR, &lnL, &lnR);
             QY(lqy_out, j, i) += lq;
+            QY(lqy_out, j - 1, i) += lqp;
+            QY(lqy_out, j + 1, i) += lqn;
+            QX(lqx_out, j - 1, i) += lo;
+            QX(lqx_out, j - 1, i + 1) += lo;
+            QX(lqx_out, j, i) += lo;
+            QX(lqx_out, j, i + 1) += lo;
             H(lh_out, j - 1, i) += lhL;
             H(lh_out, j, i) += lhR;
             H(gn, j - 1, i) += lnL;
@@ -657,9 +709,9 @@ static void orc_step_reverse(const orc_params *p, const orc_section *secs, int32
  * dLdh[k*n_gauges + g] is dL/d(depth at gauge g after step k).  Starts from
  * (h0, qx0, qy0) at led0 (time, step count, dt), runs n_steps forward storing
  * every state, then sweeps back.  Writes dL/dn to gn (zeroed here) and, if the
- * pointers are given, dL/d(h0, qx0, qy0).  Returns 0, -1 on allocation failure,
- * -3 for theta != 1 or vector-norm friction (the reverse sweep covers Eq. 3 as
- * printed with the face's own |q|).
+ * pointers are given, dL/d(h0, qx0, qy0).  Returns 0, or -1 on allocation
+ * failure.  Covers Eq. 3 as printed and its theta-weighted and vector-norm
+ * forms.
  */
 int orc_adjoint(const orc_params *p, const orc_section *secs, int32_t nsec, const double *z,
                 const double *n, const double *h0, const double *qx0, const double *qy0,
@@ -667,7 +719,6 @@ int orc_adjoint(const orc_params *p, const orc_section *secs, int32_t nsec, cons
                 int32_t n_gauges, const double *dLdh, double *gn, double *lh0, double *lqx0,
                 double *lqy0)
 {
-    if (p->theta != 1.0 || p->friction != 0) return -3;   /* the reverse sweep covers Eq. 3 as printed */
     int32_t nx = p->nx, ny = p->ny;
     size_t NC = (size_t)nx * ny, NX = (size_t)ny * (nx + 1), NY = (size_t)(ny + 1) * nx;
     size_t per = NC + NX + NY;

@@ -379,13 +379,6 @@ def test_friction_norm_closed_form(friction):
     np.testing.assert_allclose(o.qy[1:ny, :], 0.4 / (1 + c * my), rtol=1e-14)
 
 
-def test_theta_scheme_oracle_adjoint_is_refused():
-    p = closed_box(np.zeros((2, 3)), np.ones((2, 3)), theta=0.8)
-    o = oracle.Oracle(p)
-    with pytest.raises(NotImplementedError):
-        o.adjoint(2, np.array([[1, 1]]), np.ones((2, 1)))
-
-
 # ---------------------------------------------------------------- boundary conditions
 def test_section_fraction_rule():
     p = inputs.random_small(20, 12, 0)
@@ -454,7 +447,7 @@ def test_outflow_literal_form_hand_value():
 
 
 # ---------------------------------------------------------------- adjoint
-def wet_case(nx=12, ny=9, seed=0, bc_form=0):
+def wet_case(nx=12, ny=9, seed=0, bc_form=0, theta=1.0, friction=0):
     rng = np.random.default_rng(500 + seed)
     dx = 4.0
     xm = (np.arange(nx) + 0.5) * dx
@@ -465,7 +458,8 @@ def wet_case(nx=12, ny=9, seed=0, bc_form=0):
     secs = [Section.cells(XMIN, 2, 7, INFLOW, 2e-3, nx, ny, [0.0, 30.0], [1.0, 3.0]),
             Section.cells(XMAX, 0, ny, OUTFLOW, so, nx, ny),
             Section.cells(YMAX, 3, 8, OUTFLOW, so / 2, nx, ny)]
-    p = Problem("wet", nx, ny, dx, z, n, secs, Options(dt_mode=1, dt_const=0.4, bc_form=bc_form), h0=h0,
+    p = Problem("wet", nx, ny, dx, z, n, secs,
+                Options(dt_mode=1, dt_const=0.4, bc_form=bc_form, theta=theta, friction=friction), h0=h0,
                 qx0=np.zeros((ny, nx + 1)), qy0=np.zeros((ny + 1, nx)))
     return p
 
@@ -478,10 +472,12 @@ def _loss(p, n, steps, gauges, w):
     return float(np.sum(series * w))
 
 
-@pytest.mark.parametrize("bc_form", [0, 1])
-def test_adjoint_dn_matches_central_differences(bc_form):
-    """dL/dn by the reverse sweep equals central finite differences of the forward run."""
-    p = wet_case(bc_form=bc_form)
+@pytest.mark.parametrize("bc_form,theta,friction", [(0, 1.0, 0), (1, 1.0, 0), (0, 0.8, 0), (0, 1.0, 1),
+                                                     (0, 0.8, 1), (1, 0.85, 1)])
+def test_adjoint_dn_matches_central_differences(bc_form, theta, friction):
+    """dL/dn by the reverse sweep equals central finite differences of the forward run,
+    for Eq. 3 as printed and its theta-weighted and vector-norm forms."""
+    p = wet_case(bc_form=bc_form, theta=theta, friction=friction)
     steps = 40
     rng = np.random.default_rng(3)
     gauges = np.array([[3, 4], [8, 2], [10, 7], [0, 4], [11, 0]])
@@ -498,35 +494,39 @@ def test_adjoint_dn_matches_central_differences(bc_form):
         assert gn[j, i] == pytest.approx(fd, rel=1e-5, abs=1e-9 * np.abs(gn).max())
 
 
-def test_adjoint_dh0_matches_central_differences():
-    p = wet_case(seed=1)
+@pytest.mark.parametrize("theta,friction", [(1.0, 0), (0.8, 0), (1.0, 1), (0.8, 1)])
+def test_adjoint_dh0_matches_central_differences(theta, friction):
+    """dL/d(h0, qx0, qy0) against central differences; with the vector norm the
+    faces of one axis also reach the other axis's faces, and with the theta
+    weighting a face's neighbours along its axis (the boundary faces included)."""
+    p = wet_case(seed=1, theta=theta, friction=friction)
+    rng = np.random.default_rng(11)
+    p.qx0 = rng.uniform(-0.05, 0.05, (p.ny, p.nx + 1))     # moving water: |q| and the vector norm are smooth
+    p.qy0 = rng.uniform(-0.05, 0.05, (p.ny + 1, p.nx))
+    p.qx0[:, 0] = 0.0
+    p.qy0[-1, :] = 0.0
     steps = 30
     gauges = np.array([[5, 5], [9, 3]])
     w = np.ones((steps, 2))
     o = oracle.Oracle(p)
     gn, lh, lqx, lqy = o.adjoint(steps, gauges, w, want_state=True)
-    for (i, j) in [(5, 5), (2, 2), (10, 6), (0, 0)]:
-        eps = 1e-6
-        lo = []
+
+    def fd(field, j, i, eps=1e-6):
+        vals = []
         for sgn in (1, -1):
-            p2 = wet_case(seed=1)
-            p2.h0 = p.h0.copy()
-            p2.h0[j, i] += sgn * eps
-            o2 = oracle.Oracle(p2)
-            s, _ = o2.run(steps, gauges=gauges)
-            lo.append(np.sum(s * w))
-        fd = (lo[0] - lo[1]) / (2 * eps)
-        assert lh[j, i] == pytest.approx(fd, rel=2e-5, abs=1e-8)
-    # and one interior x-face discharge
-    eps = 1e-6
-    vals = []
-    for sgn in (1, -1):
-        p2 = wet_case(seed=1)
-        p2.qx0 = p.qx0.copy()
-        p2.qx0[4, 6] += sgn * eps
-        s, _ = oracle.Oracle(p2).run(steps, gauges=gauges)
-        vals.append(np.sum(s * w))
-    assert lqx[4, 6] == pytest.approx((vals[0] - vals[1]) / (2 * eps), rel=2e-5, abs=1e-8)
+            p2 = wet_case(seed=1, theta=theta, friction=friction)
+            p2.h0, p2.qx0, p2.qy0 = p.h0.copy(), p.qx0.copy(), p.qy0.copy()
+            getattr(p2, field)[j, i] += sgn * eps
+            s, _ = oracle.Oracle(p2).run(steps, gauges=gauges)
+            vals.append(np.sum(s * w))
+        return (vals[0] - vals[1]) / (2 * eps)
+
+    for (i, j) in [(5, 5), (2, 2), (10, 6), (0, 0)]:
+        assert lh[j, i] == pytest.approx(fd("h0", j, i), rel=2e-5, abs=1e-8)
+    for (j, i) in [(4, 6), (5, 1), (3, 0)]:           # interior x-faces, and a boundary face's old value
+        assert lqx[j, i] == pytest.approx(fd("qx0", j, i), rel=2e-5, abs=1e-8)
+    for (j, i) in [(4, 6), (2, 9)]:                    # interior y-faces
+        assert lqy[j, i] == pytest.approx(fd("qy0", j, i), rel=2e-5, abs=1e-8)
 
 
 def test_adjoint_zero_seed_gives_zero():
