@@ -125,12 +125,12 @@ typedef struct {
                                     sum of its two neighbours along the same axis (the theta scheme of
                                     de Almeida et al. 2012, cited in Methods); friction keeps |q| of the
                                     face.  theta != 1: kernels REFERENCE, STREAM, TMA (AUTO), TILED and
-                                    FP64, ensembles; not ROWS, no adjoint (FLOOD_ERR_UNSUPPORTED) */
+                                    FP64, ensembles, the adjoint; not ROWS (FLOOD_ERR_UNSUPPORTED) */
     int32_t friction;            /* |q| in the friction term of Eq. 3.  0 (default): the face's own discharge
                                     component (the axis-by-axis integration of Methods).  1: the vector norm
                                     sqrt(q^2 + qo^2), qo the mean of the four faces of the other axis around
                                     the face.  1: kernels REFERENCE, STREAM, TMA (AUTO), TILED and FP64,
-                                    ensembles; not ROWS, no adjoint (FLOOD_ERR_UNSUPPORTED); other values
+                                    ensembles, the adjoint; not ROWS (FLOOD_ERR_UNSUPPORTED); other values
                                     FLOOD_ERR_ARG */
 } flood_opts;
 
@@ -244,9 +244,12 @@ flood_status flood_run_gauges(flood_handle *h, int64_t n_steps, const int64_t *g
  * or device.  dLdh0_out: optional (NULL) gradient with respect to the
  * starting depth.  The handle's state, clock and ledger are unchanged.
  * Branch conventions at non-smooth points: max() sends its derivative to the
- * lower-index cell on ties, d|q|/dq = 0 at q = 0, and the dry-face test, the
- * outflow dry test and the depth clip are held as constant masks; the Eq. 6
- * inflow level is differentiated exactly (implicit function theorem).
+ * lower-index cell on ties, d|q|/dq = 0 at q = 0 (for the vector norm the
+ * derivative of |q| is 0 where |q| = 0), and the dry-face test, the outflow
+ * dry test and the depth clip are held as constant masks; the Eq. 6 inflow
+ * level is differentiated exactly (implicit function theorem).  With theta
+ * weighting or vector-norm friction the reverse step runs as three passes
+ * over global memory (11 scratch planes of the grid's size).
  */
 flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const int64_t *gauge_cells,
                            int32_t n_gauges, const double *dLdh, int32_t n_checkpoints,

@@ -458,6 +458,311 @@ __global__ void adj_inflow_kernel(const AdjArgs<T> A)
     }
 }
 
+// ---------------------------------------------------------------- the scheme options
+// With the theta weighting or the vector norm a face's new value also depends
+// on its two neighbours along the axis and on the four faces of the other axis
+// around it, so their adjoints receive contributions too.  The reverse step
+// then runs in three passes over global memory (each face's derivatives once):
+//  R1 per cell: the new faces (the forward kernels' own arithmetic, so the clip
+//     and wet/dry decisions are the forward's), the clip mask, and the adjoint
+//     of the unclipped depth (gauge seeds added by a one-thread pass after it);
+//  R2 per face: mu and the face's derivatives, stored as its contributions to
+//     the two cells (depth, Manning n), to its own old discharge, to its axis
+//     neighbours (theta) and to the orthogonal faces (vector norm);
+//  R3 per cell: the gathers, for the cell and for the faces it owns (its west
+//     and south faces; the last column and row also the east and north ones).
+// Scratch planes (pitch x (ny + 1) each): 0..4 x-faces (to L, to R, dL/dn,
+// to the axis neighbours, to the orthogonal faces), 5..9 the same for y-faces,
+// 10 the clip mask.
+template <typename T> struct OptFace;
+
+template <> struct OptFace<float> {
+    FastConst K;
+    __device__ OptFace(const Geom &G, double dt_)
+    {
+        const float dt = (float)dt_, dx = (float)G.dx;
+        K.gdt = (float)G.g * dt;
+        K.a1 = K.gdt / dx;
+        K.h_dry = (float)G.h_dry;
+        K.dtdx = dt / dx;
+        K.theta = (float)G.theta;
+        K.w = (float)(0.5 * (1.0 - G.theta));
+    }
+    __device__ float qn(float q, float qp, float qx, bool th) const { return th ? theta_q(q, qp, qx, K) : q; }
+    __device__ float qm(float q, float a, float b, float c, float d, bool vec) const
+    {
+        return vec ? q_norm(q, a, b, c, d) : fabsf(q);
+    }
+    __device__ float qo(float a, float b, float c, float d) const
+    {
+        return __fmul_rn(0.25f, __fadd_rn(__fadd_rn(a, b), __fadd_rn(c, d)));
+    }
+    __device__ float face(float qmag, float qnum, float hL, float zL, float nL, float hR, float zR, float nR) const
+    {
+        return face_fast_gen(qmag, qnum, hL + zL, hR + zR, fmaxf(zL, zR), nL + nR, K);
+    }
+};
+
+template <> struct OptFace<double> {
+    double g, dt, dx, hd, th, w;
+    __device__ OptFace(const Geom &G, double dt_)
+        : g(G.g), dt(dt_), dx(G.dx), hd(G.h_dry), th(G.theta), w(0.5 * (1.0 - G.theta)) {}
+    __device__ double qn(double q, double qp, double qx, bool t) const { return theta_q_ieee<double>(q, qp, qx, th, w, t); }
+    __device__ double qm(double q, double a, double b, double c, double d, bool vec) const
+    {
+        return q_norm_ieee<double>(q, a, b, c, d, vec);
+    }
+    __device__ double qo(double a, double b, double c, double d) const
+    {
+        using O = R<double>;
+        return O::mul(0.25, O::add(O::add(a, b), O::add(c, d)));
+    }
+    __device__ double face(double qmag, double qnum, double hL, double zL, double nL, double hR, double zR,
+                           double nR) const
+    {
+        return face_update_ieee<double>(qnum, qmag, hL, zL, nL, hR, zR, nR, g, dt, dx, hd);
+    }
+};
+
+// Inputs of an interior face: its old q, the numerator discharge, the friction
+// magnitude and the mean orthogonal discharge, with the forward step's neighbours.
+template <typename T>
+struct OptIn {
+    T q, qn, qm, qo;
+};
+
+template <typename T>
+__device__ __forceinline__ OptIn<T> opt_x_in(const StepArgs<T> &a, const OptFace<T> &O, int j, int fi, bool th,
+                                             bool vec)
+{
+    const size_t P = (size_t)a.geo.pitch, r = (size_t)j * P;
+    OptIn<T> v;
+    v.q = a.qx[r + fi];
+    v.qn = O.qn(v.q, a.qx[r + fi - 1], a.qx[r + fi + 1], th);
+    const T qa = a.qy[r + fi - 1], qb = a.qy[r + fi], qc = a.qy[r + P + fi - 1], qd = a.qy[r + P + fi];
+    v.qm = O.qm(v.q, qa, qb, qc, qd, vec);
+    v.qo = vec ? O.qo(qa, qb, qc, qd) : T(0);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ OptIn<T> opt_y_in(const StepArgs<T> &a, const OptFace<T> &O, int fj, int i, bool th,
+                                             bool vec)
+{
+    const size_t P = (size_t)a.geo.pitch, r = (size_t)fj * P;
+    OptIn<T> v;
+    v.q = a.qy[r + i];
+    v.qn = O.qn(v.q, a.qy[r - P + i], a.qy[r + P + i], th);
+    const T qa = a.qx[r - P + i], qb = a.qx[r - P + i + 1], qc = a.qx[r + i], qd = a.qx[r + i + 1];
+    v.qm = O.qm(v.q, qa, qb, qc, qd, vec);
+    v.qo = vec ? O.qo(qa, qb, qc, qd) : T(0);
+    return v;
+}
+
+// New value of x-face (j, fi), fi in [0, nx], and of y-face (fj, i), fj in [0, ny].
+template <typename T>
+__device__ __forceinline__ T opt_new_x(const StepArgs<T> &a, const Fwd<T> &F, const OptFace<T> &O, int j, int fi,
+                                       bool th, bool vec)
+{
+    const Geom &G = a.geo;
+    const size_t r = (size_t)j * G.pitch;
+    if (fi == 0) return bface(a, F, 0, j, a.h[r], a.n[r]);
+    if (fi == G.nx) return bface(a, F, 1, j, a.h[r + G.nx - 1], a.n[r + G.nx - 1]);
+    const OptIn<T> v = opt_x_in(a, O, j, fi, th, vec);
+    return O.face(v.qm, v.qn, a.h[r + fi - 1], a.z[r + fi - 1], a.n[r + fi - 1], a.h[r + fi], a.z[r + fi], a.n[r + fi]);
+}
+
+template <typename T>
+__device__ __forceinline__ T opt_new_y(const StepArgs<T> &a, const Fwd<T> &F, const OptFace<T> &O, int fj, int i,
+                                       bool th, bool vec)
+{
+    const Geom &G = a.geo;
+    const size_t P = (size_t)G.pitch, r = (size_t)fj * P;
+    if (fj == 0) return bface(a, F, 2, i, a.h[i], a.n[i]);
+    if (fj == G.ny) return bface(a, F, 3, i, a.h[r - P + i], a.n[r - P + i]);
+    const OptIn<T> v = opt_y_in(a, O, fj, i, th, vec);
+    return O.face(v.qm, v.qn, a.h[r - P + i], a.z[r - P + i], a.n[r - P + i], a.h[r + i], a.z[r + i], a.n[r + i]);
+}
+
+// Derivatives of one wet face F = (qn - a1 hf (eta_R - eta_L)) / (1 + cc qmag),
+// cc = g dt nf^2 hf^(-7/3): own old q, each axis neighbour (theta), each of
+// the four orthogonal faces (vector norm), h_L, h_R and n (per cell).
+template <typename T> struct OptLin {
+    T dq, dnb, dorth, dhL, dhR, dn;
+};
+
+template <typename T>
+__device__ __forceinline__ OptLin<T> opt_lin(const OptIn<T> &v, T hL, T zL, T nL, T hR, T zR, T nR, T hf, T g, T dt,
+                                             T dx, T th, T w, bool vec)
+{
+    OptLin<T> r;
+    const T etaL = hL + zL, etaR = hR + zR;
+    const T nf = T(0.5) * (nL + nR);
+    const T gdt = g * dt, a1 = gdt / dx;
+    const T cc = gdt * nf * nf * Fwd<T>::pow_m73_(hf);
+    const T fric = cc * v.qm;
+    const T inv_den = Fwd<T>::rcp_(T(1) + fric);
+    const T F = (v.qn - a1 * hf * (etaR - etaL)) * inv_den;
+    const T dF_dqm = -F * cc * inv_den;
+    T dqm_dq, dqm_dqo;
+    if (!vec) {
+        dqm_dq = v.q > T(0) ? T(1) : (v.q < T(0) ? T(-1) : T(0));
+        dqm_dqo = T(0);
+    } else if (v.qm > T(0)) {
+        const T inv = Fwd<T>::rcp_(v.qm);
+        dqm_dq = v.q * inv;
+        dqm_dqo = v.qo * inv;
+    } else {
+        dqm_dq = dqm_dqo = T(0);
+    }
+    r.dq = th * inv_den + dF_dqm * dqm_dq;
+    r.dnb = w * inv_den;
+    r.dorth = T(0.25) * dF_dqm * dqm_dqo;
+    const T dF_dhf = (-a1 * (etaR - etaL) + F * (T(7) / T(3)) * fric * Fwd<T>::rcp_(hf)) * inv_den;
+    const T d_expl = a1 * hf * inv_den;
+    const bool left = etaL >= etaR;
+    r.dhL = d_expl + (left ? dF_dhf : T(0));
+    r.dhR = -d_expl + (left ? T(0) : dF_dhf);
+    r.dn = -F * fric * inv_den * Fwd<T>::rcp_(nf);
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T *opt_plane(const AdjArgs<T> &A, int k)
+{
+    return A.scratch + (size_t)k * A.fwd.geo.pitch * (A.fwd.geo.ny + 1);
+}
+
+// R1: clip mask and the adjoint of the unclipped depth of every cell.
+template <typename T>
+__global__ void __launch_bounds__(256) adj_opt_cells_kernel(const AdjArgs<T> A, const int nbx)
+{
+    const StepArgs<T> &a = A.fwd;
+    const Geom &G = a.geo;
+    const int i = (int)(blockIdx.x % (unsigned)nbx) * BX + threadIdx.x;
+    const int j = (int)(blockIdx.x / (unsigned)nbx) * 8 + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    const bool th = G.theta != 1.0, vec = G.friction != 0;
+    const Fwd<T> F(G, a.ctrl->dt);
+    const OptFace<T> O(G, a.ctrl->dt);
+    const size_t c = (size_t)j * G.pitch + i;
+    const T qW = opt_new_x(a, F, O, j, i, th, vec), qE = opt_new_x(a, F, O, j, i + 1, th, vec);
+    const T qS = opt_new_y(a, F, O, j, i, th, vec), qN = opt_new_y(a, F, O, j + 1, i, th, vec);
+    const T hu = F.update(a.h[c], qW, qE, qS, qN);
+    const bool keep = !(hu < T(0));
+    A.lhu[c] = keep ? A.lh[c] : T(0);
+    opt_plane(A, 10)[c] = keep ? T(1) : T(0);
+}
+
+// Gauge seeds into the unclipped depth's adjoint, in gauge order (repeated gauges add up in order).
+template <typename T>
+__global__ void adj_opt_seeds_kernel(const AdjArgs<T> A)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const Geom &G = A.fwd.geo;
+    for (int k = 0; k < A.n_gauges; k++) {
+        const int64_t flat = A.gauge_cells[k];
+        const size_t c = (size_t)(flat / G.nx) * G.pitch + (size_t)(flat % G.nx);
+        if (opt_plane(A, 10)[c] != T(0)) A.lhu[c] = A.lhu[c] + T(A.seed[k]);
+    }
+}
+
+// R2: every face's contributions (axis 0: x-faces, rows ny, faces nx + 1; axis 1: y-faces).
+template <typename T>
+__global__ void __launch_bounds__(256) adj_opt_faces_kernel(const AdjArgs<T> A, const int axis, const int nbx)
+{
+    const StepArgs<T> &a = A.fwd;
+    const Geom &G = a.geo;
+    const int nx = G.nx, ny = G.ny;
+    const int fi = (int)(blockIdx.x % (unsigned)nbx) * BX + threadIdx.x;
+    const int fj = (int)(blockIdx.x / (unsigned)nbx) * 8 + threadIdx.y;
+    const int ncol = axis == 0 ? nx + 1 : nx, nrow = axis == 0 ? ny : ny + 1;
+    if (fi >= ncol || fj >= nrow) return;
+    const bool th = G.theta != 1.0, vec = G.friction != 0;
+    const Fwd<T> F(G, a.ctrl->dt);
+    const OptFace<T> O(G, a.ctrl->dt);
+    const T dt = T(a.ctrl->dt), dx = T(G.dx), g = T(G.g), hd = T(G.h_dry), dtdx = dt / dx;
+    const T tw = T(G.theta), ww = T(0.5 * (1.0 - G.theta));
+    const size_t P = (size_t)G.pitch, f = (size_t)fj * P + fi;
+    // the face's two cells (L lower index, R) as flat pitched indices, and whether they exist
+    const bool hasL = axis == 0 ? fi > 0 : fj > 0, hasR = axis == 0 ? fi < nx : fj < ny;
+    const size_t cL = axis == 0 ? f - 1 : f - P, cR = f;
+    const T lL = hasL ? A.lhu[cL] : T(0), lR = hasR ? A.lhu[cR] : T(0);
+    const T mu = (axis == 0 ? A.lqx[f] : A.lqy[f]) + dtdx * (lR - lL);
+    T cl = T(0), cr = T(0), cn = T(0), lq = T(0), lt = T(0), lo = T(0);
+    if (!hasL || !hasR) {                                    // a border face: Eq. 5-6 or a wall
+        const int side = axis == 0 ? (hasL ? 1 : 0) : (hasL ? 3 : 2);
+        const int k = axis == 0 ? fj : fi;
+        const size_t cell = hasL ? cL : cR;
+        outflow_adj(a, F, side, k, a.h[cell], a.n[cell], mu, hasL ? cl : cr, cn);
+    } else {
+        const OptIn<T> v = axis == 0 ? opt_x_in(a, O, fj, fi, th, vec) : opt_y_in(a, O, fj, fi, th, vec);
+        const T hL = a.h[cL], zL = a.z[cL], nL = a.n[cL], hR = a.h[cR], zR = a.z[cR], nR = a.n[cR];
+        const T hf = F.hf(hL, zL, hR, zR);
+        if (hf > hd && mu != T(0)) {
+            const OptLin<T> d = opt_lin<T>(v, hL, zL, nL, hR, zR, nR, hf, g, dt, dx, tw, ww, vec);
+            cl = mu * d.dhL;
+            cr = mu * d.dhR;
+            cn = mu * d.dn;
+            lq = mu * d.dq;
+            lt = th ? mu * d.dnb : T(0);
+            lo = vec ? mu * d.dorth : T(0);
+        }
+    }
+    const int b = axis == 0 ? 0 : 5;
+    opt_plane(A, b + 0)[f] = cl;
+    opt_plane(A, b + 1)[f] = cr;
+    opt_plane(A, b + 2)[f] = cn;
+    opt_plane(A, b + 3)[f] = lt;
+    opt_plane(A, b + 4)[f] = lo;
+    (axis == 0 ? A.lqx_out : A.lqy_out)[f] = lq;
+}
+
+// R3: per cell, its own adjoint and dL/dn, and the gathers of the faces it owns.
+template <typename T>
+__global__ void __launch_bounds__(256) adj_opt_gather_kernel(const AdjArgs<T> A, const int nbx)
+{
+    const Geom &G = A.fwd.geo;
+    const int nx = G.nx, ny = G.ny;
+    const int i = (int)(blockIdx.x % (unsigned)nbx) * BX + threadIdx.x;
+    const int j = (int)(blockIdx.x / (unsigned)nbx) * 8 + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const size_t P = (size_t)G.pitch, c = (size_t)j * P + i;
+    const T *XL = opt_plane(A, 0), *XR = opt_plane(A, 1), *XN = opt_plane(A, 2), *XT = opt_plane(A, 3),
+            *XO = opt_plane(A, 4);
+    const T *YL = opt_plane(A, 5), *YR = opt_plane(A, 6), *YN = opt_plane(A, 7), *YT = opt_plane(A, 8),
+            *YO = opt_plane(A, 9);
+    A.lh_out[c] = A.lhu[c] + XR[c] + XL[c + 1] + YR[c] + YL[c + P];
+    const T gs = (XN[c] + XN[c + 1]) + (YN[c] + YN[c + P]);
+    A.gn[c] += (double)gs;
+    // x-face (j, fi): theta from x-faces fi - 1 and fi + 1; vector norm from the y-faces
+    // (j, fi - 1), (j, fi), (j + 1, fi - 1), (j + 1, fi) that read its old value
+    auto gather_x = [&](int fi) {
+        const size_t f = (size_t)j * P + fi;
+        T s = T(0);
+        if (fi > 0) s += XT[f - 1];
+        if (fi < nx) s += XT[f + 1];
+        if (fi > 0) s += YO[f - 1] + YO[f + P - 1];
+        if (fi < nx) s += YO[f] + YO[f + P];
+        A.lqx_out[f] += s;
+    };
+    // y-face (fj, i): theta from y-faces fj - 1 and fj + 1; vector norm from the x-faces
+    // (fj - 1, i), (fj - 1, i + 1), (fj, i), (fj, i + 1) that read its old value
+    auto gather_y = [&](int fj) {
+        const size_t f = (size_t)fj * P + i;
+        T s = T(0);
+        if (fj > 0) s += YT[f - P];
+        if (fj < ny) s += YT[f + P];
+        if (fj > 0) s += XO[f - P] + XO[f - P + 1];
+        if (fj < ny) s += XO[f] + XO[f + 1];
+        A.lqy_out[f] += s;
+    };
+    gather_x(i);
+    if (i == nx - 1) gather_x(nx);
+    gather_y(j);
+    if (j == ny - 1) gather_y(ny);
+}
+
 template <typename T>
 __global__ void gn_out_kernel(Geom G, const double *gn, T *dst)
 {
@@ -485,10 +790,24 @@ template cudaError_t launch_gn_out<double>(const Geom &, const double *, double 
 template <typename T>
 cudaError_t launch_adjoint_step(const AdjArgs<T> &A, cudaStream_t st)
 {
-    constexpr int BYT = TileRows<T>::v;
-    dim3 block(BX, BYT);
-    const int nbx = (A.fwd.geo.nx + BX - 1) / BX, nby = (A.fwd.geo.ny + BYT - 1) / BYT;
-    adj_step_kernel<T><<<(unsigned)((int64_t)nbx * nby), block, 0, st>>>(A, nbx);
+    const Geom &G = A.fwd.geo;
+    if (G.theta != 1.0 || G.friction != 0) {
+        if (!A.scratch) return cudaErrorInvalidValue;
+        const dim3 block(BX, 8);
+        const int nbx = (G.nx + BX - 1) / BX, nby = (G.ny + 7) / 8;
+        adj_opt_cells_kernel<T><<<(unsigned)((int64_t)nbx * nby), block, 0, st>>>(A, nbx);
+        if (A.n_gauges > 0) adj_opt_seeds_kernel<T><<<1, 32, 0, st>>>(A);
+        const int nbx0 = (G.nx + 1 + BX - 1) / BX;
+        adj_opt_faces_kernel<T><<<(unsigned)((int64_t)nbx0 * nby), block, 0, st>>>(A, 0, nbx0);
+        const int nby1 = (G.ny + 1 + 7) / 8;
+        adj_opt_faces_kernel<T><<<(unsigned)((int64_t)nbx * nby1), block, 0, st>>>(A, 1, nbx);
+        adj_opt_gather_kernel<T><<<(unsigned)((int64_t)nbx * nby), block, 0, st>>>(A, nbx);
+    } else {
+        constexpr int BYT = TileRows<T>::v;
+        dim3 block(BX, BYT);
+        const int nbx = (G.nx + BX - 1) / BX, nby = (G.ny + BYT - 1) / BYT;
+        adj_step_kernel<T><<<(unsigned)((int64_t)nbx * nby), block, 0, st>>>(A, nbx);
+    }
     if (A.fwd.n_inflow_sec > 0) adj_inflow_kernel<T><<<A.fwd.n_inflow_sec, 256, 0, st>>>(A);
     return cudaGetLastError();
 }

@@ -91,6 +91,7 @@ struct Sweep {
     // adjoint buffers
     void *lh[2] = {nullptr, nullptr}, *lqx[2] = {nullptr, nullptr}, *lqy[2] = {nullptr, nullptr};
     void *lhu = nullptr;
+    void *scratch = nullptr;      // the scheme options' reverse step: 11 planes of pitch x (ny + 1)
     double *gn = nullptr;
     int cur_l = 0;
     const int64_t *cells = nullptr;
@@ -264,6 +265,7 @@ flood_status reverse_step_t(Sweep &S)
     A.gauge_cells = S.cells;
     A.n_gauges = S.G;
     A.seed = S.seed + (size_t)k * S.G;      // dL/dh after step k, added to lambda_{k+1}
+    A.scratch = (T *)S.scratch;
     if (S.profile) {
         flood_status ts = timed(S, S.ev_rev, [&] {
             cudaError_t e = launch_adjoint_step<T>(A, h->stream);
@@ -362,9 +364,6 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     if (n_steps < 1 || n_gauges < 0 || n_checkpoints < 1 || !dLdn_out || (n_gauges > 0 && (!gauge_cells || !dLdh)))
         return fail(h, FLOOD_ERR_ARG, "bad adjoint arguments");
     if (h->sticky) return fail(h, FLOOD_ERR_STATE, "handle is in an error state; write a new state first");
-    if (h->geo.theta != 1.0) return fail(h, FLOOD_ERR_UNSUPPORTED, "the adjoint covers theta = 1 (Eq. 3 as printed)");
-    if (h->geo.friction != 0)
-        return fail(h, FLOOD_ERR_UNSUPPORTED, "the adjoint covers the face's own |q| in the friction term");
     const int64_t nc = (int64_t)h->geo.nx * h->geo.ny;
     for (int g = 0; g < n_gauges; g++)
         if (gauge_cells[g] < 0 || gauge_cells[g] >= nc) return fail(h, FLOOD_ERR_ARG, "gauge cell out of range");
@@ -417,6 +416,8 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
         S.lqy[b] = alloc(S.plane_y);
     }
     S.lhu = alloc(S.plane);
+    const bool opts = h->geo.theta != 1.0 || h->geo.friction != 0;
+    if (opts) S.scratch = alloc(11 * S.plane_y);
     S.gn = (double *)alloc(P * h->geo.ny * sizeof(double));
     double *seed_dev = (double *)alloc(std::max<size_t>((size_t)n_steps * n_gauges, 1) * sizeof(double));
     int64_t *cells_dev = (int64_t *)alloc(std::max(n_gauges, 1) * sizeof(int64_t));
@@ -427,6 +428,10 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
             release();
             return fail(h, FLOOD_ERR_OOM, "adjoint buffer allocation");
         }
+    if (opts && !S.scratch) {
+        release();
+        return fail(h, FLOOD_ERR_OOM, "adjoint buffer allocation");
+    }
     // saved handle state: control block, kernel, state index and epoch pointers (the
     // sweep aims the epoch pointers at its own slices and writes nothing through the
     // handle's own epoch buffers)

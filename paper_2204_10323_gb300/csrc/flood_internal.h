@@ -171,6 +171,8 @@ struct AdjArgs {
     const int64_t *gauge_cells;   // flat j*nx+i of the loss's gauges
     int n_gauges;
     const double *seed;           // dL/d(depth at gauge g after this step), n_gauges values (device)
+    T *scratch;                   // scheme options only: 11 planes of pitch x (ny + 1) elements (face
+                                  // contributions of both axes and the clip mask); null otherwise
 };
 template <typename T>
 cudaError_t launch_adjoint_step(const AdjArgs<T> &a, cudaStream_t st);

@@ -24,7 +24,7 @@ def F():
     return F
 
 
-def wet_case(nx=24, ny=17, seed=0, bc_form=0, dt_mode=1, E=4):
+def wet_case(nx=24, ny=17, seed=0, bc_form=0, dt_mode=1, E=4, theta=1.0, friction=0, moving=False):
     rng = np.random.default_rng(700 + seed)
     dx = 4.0
     xm = (np.arange(nx) + 0.5) * dx
@@ -35,9 +35,15 @@ def wet_case(nx=24, ny=17, seed=0, bc_form=0, dt_mode=1, E=4):
     secs = [Section.cells(XMIN, 2, ny - 3, INFLOW, 2e-3, nx, ny, [0.0, 30.0], [1.0, 3.0]),
             Section.cells(XMAX, 0, ny, OUTFLOW, so, nx, ny),
             Section.cells(YMAX, 3, nx - 4, OUTFLOW, so / 2, nx, ny)]
+    qx0, qy0 = np.zeros((ny, nx + 1)), np.zeros((ny + 1, nx))
+    if moving:                                   # moving water: |q| and the vector norm away from 0
+        qx0 = rng.uniform(-0.05, 0.05, (ny, nx + 1))
+        qy0 = rng.uniform(-0.05, 0.05, (ny + 1, nx))
+        qx0[:, 0] = qy0[-1, :] = 0.0
     return Problem("wet", nx, ny, dx, z, n, secs,
-                   Options(dt_mode=dt_mode, dt_const=0.4, dt_cap=0.4, epoch_steps=E, bc_form=bc_form),
-                   h0=h0, qx0=np.zeros((ny, nx + 1)), qy0=np.zeros((ny + 1, nx)))
+                   Options(dt_mode=dt_mode, dt_const=0.4, dt_cap=0.4, epoch_steps=E, bc_form=bc_form,
+                           theta=theta, friction=friction),
+                   h0=h0, qx0=qx0, qy0=qy0)
 
 
 def closed_cost(l, c):
@@ -66,6 +72,43 @@ def test_fp64_adjoint_matches_oracle(bc_form, dt_mode):
     assert scale > 0
     assert np.abs(gn - gn_o).max() <= 1e-9 * scale
     assert np.abs(lh - lh_o).max() <= 1e-9 * np.abs(lh_o).max()
+
+
+@pytest.mark.parametrize("theta,friction,bc_form,dt_mode", [(0.8, 0, 0, 1), (1.0, 1, 0, 1), (0.8, 1, 0, 0),
+                                                             (0.9, 1, 1, 1)])
+def test_fp64_option_adjoint_matches_oracle(theta, friction, bc_form, dt_mode):
+    """The theta-weighted and vector-norm forms: dL/dn and dL/d(h0, qx0, qy0) of the
+    three-pass reverse step against the oracle's reverse sweep."""
+    Fm = F()
+    p = wet_case(bc_form=bc_form, dt_mode=dt_mode, theta=theta, friction=friction, moving=True, seed=8)
+    steps = 33
+    w = np.random.default_rng(9).standard_normal((steps, len(GAUGES)))
+    o = oracle.Oracle(p)
+    gn_o, lh_o, _, _ = o.adjoint(steps, GAUGES, w, want_state=True)
+    s = Fm.Sim(p, precision=Fm.F64)
+    gn, lh = s.adjoint(steps, GAUGES, w, n_checkpoints=5, want_dh0=True)
+    assert np.abs(gn - gn_o).max() <= 1e-9 * np.abs(gn_o).max()
+    assert np.abs(lh - lh_o).max() <= 1e-9 * np.abs(lh_o).max()
+    # revolve and store-all give the same bits
+    ref = s.adjoint(steps, GAUGES, w, n_checkpoints=steps)
+    assert np.array_equal(ref, gn)
+
+
+@pytest.mark.parametrize("theta,friction", [(0.8, 0), (1.0, 1), (0.8, 1)])
+def test_fp32_option_adjoint_is_close_to_fp64(theta, friction):
+    Fm = F()
+    p = wet_case(theta=theta, friction=friction, moving=True, seed=10, nx=70, ny=45)
+    steps = 40
+    w = np.random.default_rng(11).standard_normal((steps, len(GAUGES)))
+    g64 = Fm.Sim(p, precision=Fm.F64).adjoint(steps, GAUGES, w, n_checkpoints=6)
+    q = Problem(p.name, p.nx, p.ny, p.dx, p.z.astype(np.float32).astype(np.float64),
+                p.n.astype(np.float32).astype(np.float64), p.sections, p.opts,
+                h0=p.h0.astype(np.float32).astype(np.float64), qx0=p.qx0.astype(np.float32).astype(np.float64),
+                qy0=p.qy0.astype(np.float32).astype(np.float64))
+    g32 = Fm.Sim(q, precision=Fm.F32).adjoint(steps, GAUGES, w, n_checkpoints=6).astype(np.float64)
+    cos = float(np.sum(g32 * g64) / (np.linalg.norm(g32) * np.linalg.norm(g64)))
+    assert cos > 0.999
+    assert np.abs(g32 - g64).max() <= 1e-2 * np.abs(g64).max()
 
 
 def test_fp64_adjoint_from_mid_epoch_state():

@@ -398,15 +398,6 @@ def test_theta_tma_tiles_equal_row_staging_bitwise(tile):
         assert np.array_equal(a.read(f), b.read(f)), f
 
 
-def test_theta_adjoint_is_refused():
-    Fm = F()
-    p = with_theta(inputs.random_small(20, 12, 2), 0.8)
-    s = Fm.Sim(p, precision=Fm.F64)
-    with pytest.raises(Fm.FloodError) as e:
-        s.adjoint(4, np.array([[3, 3]]), np.ones((4, 1)))
-    assert e.value.status == Fm.ERR_UNSUPPORTED
-
-
 @pytest.mark.parametrize("theta,friction", [(0.75, 0), (1.0, 1), (0.75, 1)])
 @pytest.mark.parametrize("K,E,tile", [(4, 4, (0, 0)), (4, 8, (2, 9)), (2, 4, (1, 3)), (3, 6, (3, 40)),
                                       (1, 4, (0, 0)), (8, 8, (0, 0)), (8, 16, (2, 17))])
@@ -534,15 +525,6 @@ def test_vector_friction_auto_runs_the_tensor_tile_kernel():
     b.step(21)
     for f in (Fm.FIELD_H, Fm.FIELD_QX, Fm.FIELD_QY):
         assert np.array_equal(a.read(f), b.read(f)), f
-
-
-def test_vector_friction_adjoint_is_refused():
-    Fm = F()
-    p = with_friction(inputs.random_small(20, 12, 2), 1)
-    s = Fm.Sim(p, precision=Fm.F64)
-    with pytest.raises(Fm.FloodError) as e:
-        s.adjoint(4, np.array([[3, 3]]), np.ones((4, 1)))
-    assert e.value.status == Fm.ERR_UNSUPPORTED
 
 
 # ---------------------------------------------------------------- coarsening
