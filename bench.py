@@ -39,14 +39,15 @@ BYTES_PER_CELL = 32          # read h, qx, qy, z, n (20 B) + write h, qx, qy (12
 # key (kernel, steps per launch); the stream kernel captured in the 16384^2
 # launch shape (4 warps x 32-row chunks).  Only kernels whose code has not
 # changed since their capture are listed; the others report traffic null.
-TRAFFIC_B_PER_CELL = {("stream", 1): 31.28, ("tiled", 1): 30.55, ("tiled", 2): 30.79, ("tiled", 4): 31.65,
-                      ("tiled", 8): 30.91}
+TRAFFIC_B_PER_CELL = {("stream", 1): 31.31, ("tiled", 4): 31.15}
 # Warp instructions per cell-update of the temporal-blocking kernel (issue-bound), from the same 4096^2
-# capture (smsp__inst_executed.sum): the "alu" roofline beside the one-step HBM one.  The issue peak is 152 SMs x 4 warp-instructions per cycle x the sampled SM clock.
-INST_PER_CELL_UPDATE = {("tiled", 4): 243920737 / (4096 * 4096 * 4)}
+# capture (smsp__inst_executed.sum): the "alu" roofline beside the one-step HBM one.  The issue peak is
+# 152 SMs x 4 warp-instructions per cycle x the sampled SM clock.
+INST_PER_CELL_UPDATE = {("tiled", 4): 241634294 / (4096 * 4096 * 4)}
 SMS, ISSUE_PER_SM_CYCLE = 152, 4
-# the same for the vector-norm friction option (theta = 1)
-TRAFFIC_VEC_B_PER_CELL = {}
+# the same two for the vector-norm friction option (theta = 1)
+TRAFFIC_VEC_B_PER_CELL = {("tiled", 4): 30.99}
+INST_VEC_PER_CELL_UPDATE = {("tiled", 4): 289921697 / (4096 * 4096 * 4)}
 METRIC = "Gcell-updates/s and % of HBM roofline (FP32, 1 GB300); adjoint/forward time ratio"
 UNIT = "Gcell-updates/s"
 
@@ -379,7 +380,7 @@ def run_gpu(args):
                          "bytes_per_cell": BYTES_PER_CELL, "kernel_ms": kern_ms, "steps_per_launch": per_launch,
                          "dram_gbs": traffic / (kern_ms * 1e-3) / 1e9 if traffic else None,
                          "dram_frac": traffic / (kern_ms * 1e-3) / 1e9 / peak if traffic else None,
-                         "issue": issue_roofline(args.kernel, per_launch, ncell, kern_ms, clk),
+                         "issue": issue_roofline(args.kernel, per_launch, ncell, kern_ms, clk, args),
                          "note": ("one-step algorithmic bytes (32 B per cell-update) over the launch time; with "
                                   f"{per_launch} steps per launch the kernel moves {traffic / ncell / per_launch:.1f} "
                                   "B of DRAM traffic per cell-update and is bound by instruction issue, so the "
@@ -397,6 +398,8 @@ def run_gpu(args):
         line["resolution_sweep"] = resolution_sweep(F, torch, prob, args, local, dist, total_ms / steps)
     if not args.no_adjoint:
         line["adjoint"] = adjoint_ratio(F, torch)
+    if not args.no_decomp and not variant:
+        line["decomposition"] = decomposition_leg(F, torch, prob, value, steps)
     if not args.no_ensemble:
         shape = [int(v) for v in args.ensemble_shape.split(",")] if args.ensemble_shape else None
         line["ensemble"] = ensemble_throughput(F, torch, value, shape=shape)
@@ -409,11 +412,14 @@ def run_gpu(args):
     return 0
 
 
-def issue_roofline(kernel: str, per_launch: int, ncell: int, kern_ms: float, clk):
+def issue_roofline(kernel: str, per_launch: int, ncell: int, kern_ms: float, clk, args):
     """Instruction-issue roofline of an issue-bound kernel: warp instructions per
     launch (ncu count per cell-update x the launch's cell-updates) over the launch
     time, against 152 SMs x 4 issue slots x the SM clock sampled meanwhile."""
-    ipc = INST_PER_CELL_UPDATE.get((kernel, per_launch))
+    if args.workload != "c3" or args.theta != 1.0:
+        return None
+    table = INST_VEC_PER_CELL_UPDATE if args.friction == 1 else INST_PER_CELL_UPDATE
+    ipc = table.get((kernel, per_launch))
     if ipc is None:
         return None
     mhz = (clk or {}).get("sm_mhz") or 2070.0
@@ -551,6 +557,34 @@ def ensemble_throughput(F, torch, single_value: float, n: int = 96, steps: int =
     return out
 
 
+def decomposition_leg(F, torch, prob, single_value: float, steps: int, parts=(2, 4), halo: int = 4):
+    """The same workload split into 1 x N row strips with `halo`-row halos,
+    exchanged every `halo` steps (all parts on this GPU, one stream): whole-job
+    Gcell-updates/s and the ratio to the single grid, the cost of the halo rows'
+    redundant steps, the exchanges and the per-part launches."""
+    out = []
+    E = prob.opts.epoch_steps
+    n = max(steps, 2 * E)
+    for n_parts in parts:
+        stream = torch.cuda.current_stream()
+        d = F.Decomp(prob, n_parts, halo, precision=F.F32, stream=stream)
+        d.step(E)                                   # warm-up: one epoch
+        d.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        d.step(n)
+        b.record(stream)
+        torch.cuda.synchronize()
+        d.sync()
+        ms = a.elapsed_time(b)
+        value = prob.nx * prob.ny * n / (ms * 1e-3) / 1e9
+        out.append({"parts": n_parts, "halo": halo, "steps": n, "value": value, "unit": UNIT,
+                    "ratio_to_single_grid": value / single_value})
+        d.close()
+    return {"what": "1 x N row strips with halo exchange on one GPU (the paper's subgrids)", "runs": out}
+
+
 def sim_inflows(prob):
     return any(s.kind == 0 for s in prob.sections)
 
@@ -572,6 +606,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-decomp", action="store_true", help="skip the row-strip decomposition leg")
     ap.add_argument("--no-temporal", action="store_true", help="skip the temporal-blocking leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 1/2/4/8 m resolution sweep")
     ap.add_argument("--theta", type=float, default=1.0, help="face-flux weighting (1 = Eq. 3 as printed)")

@@ -55,10 +55,10 @@ static_assert(out_cols(4, 1) == 116 && out_cols(8, 1) == 108 && out_cols(4, 2) =
 static_assert(out_cols(1, 1) % 4 == 0 && out_cols(2, 1) % 4 == 0 && out_cols(3, 1) % 4 == 0 && out_cols(4, 1) % 4 == 0 &&
                   out_cols(8, 1) % 4 == 0 && halo_cols(4) % 4 == 0 && halo_cols(8) % 4 == 0,
               "strip origins must stay multiples of 4 columns");
-// level-1 rows in flight and pipelines per SM: one grid uses 6 and 6 (six
-// pipelines of 4 warps fit the registers and shared memory of an SM); the
-// ensemble kernel, which keeps more per-scenario state in registers, 8 and 5
-constexpr int kPF1 = 4, kPFE = 8;
+// level-1 rows in flight, for one grid and for the ensemble kernel: with 4 rows
+// in flight six pipelines of 4 warps fit the registers and shared memory of an SM
+// (tiled_min_blocks; the ensemble kernel's launch bounds)
+constexpr int kPF1 = 4, kPFE = 4;
 constexpr uint64_t kBudgetNs = 2000000000ull;
 
 constexpr int pow2_ceil(int v)
@@ -79,6 +79,8 @@ struct alignas(16) PipeSmem {
                                                 // the finished row's h, qx, qy (and, for the scheme options,
                                                 // the new qy of the row above it)
     uint64_t bar[kPF];
+    double led[K][2];                       // per level (warp): boundary outflow volume, clipped volume,
+                                            // summed over the runs of rows of the grid's items so far
 };
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
@@ -97,9 +99,10 @@ __device__ __forceinline__ void set(float4 &v, int k, float x)
     else v.w = x;
 }
 
-// This thread's share of one grid's ledger terms over a launch.
+// This thread's running depth maximum over one grid's cells of a launch (level K).
+// The volume terms are kept in shared memory (PipeSmem::led), out of the registers
+// of the pipeline's inner loop.
 struct TiledLedger {
-    double vout = 0.0, vclip = 0.0;      // folded from the float runs below
     float hmax = 0.0f;
     bool nan_seen = false;
 };
@@ -203,7 +206,8 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
     float4 hp = make_float4(0, 0, 0, 0), qxw_p = hp, qys_p = hp, qyo_p = hp, qxo_p = hp;
     float qxe_p = 0.0f;
     // runs of up to 32 ticks; the float partial sums of the boundary outflow (fq)
-    // and the clipped depth (fc) are folded into the double ledger after each run
+    // and the clipped depth (fc) are summed over the warp in double after each run
+    // and added to the warp's shared-memory sums (led)
     for (int j0 = jb; j0 <= jlast && !abort; j0 += 32) {
         float fq = 0.0f, fc = 0.0f;
         const int jend = min(j0 + 31, jlast);
@@ -349,7 +353,6 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
                     if (has_prev) {
                         const int rr = r - 1;
                         const bool own_row = rr >= y0 && rr < y1;
-                        const bool led_row = own_row && rr >= G.led_j0 && rr < G.led_j1;
                         float4 fin;
                         bool neg = false;
 #pragma unroll
@@ -361,6 +364,9 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
                             set(fin, k, v);
                         }
                         if (neg) {                    // rare: clip to zero, book the removed volume
+                            // (the ledger rows' bounds are read only here: the ensemble kernel's
+                            // arguments live in global memory)
+                            const bool led_row = own_row && rr >= G.led_j0 && rr < G.led_j1;
 #pragma unroll
                             for (int k = 0; k < 4; k++) {
                                 const float v = get(fin, k);
@@ -512,8 +518,14 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
                 }
             }
         }
-        L.vout += (double)fq * G.dx;
-        L.vclip += (double)fc * G.dx * G.dx;
+        // fold the run into the warp's double sums (rare: boundary faces, clipped cells)
+        if (__any_sync(0xffffffffu, fq != 0.0f || fc != 0.0f)) {
+            const double wq = warp_sum((double)fq), wc = warp_sum((double)fc);
+            if (lane == 0) {
+                sm.led[warp][0] += wq * G.dx;
+                sm.led[warp][1] += wc * G.dx * G.dx;
+            }
+        }
     }
     if (!abort) {
         base += (uint32_t)nload;
@@ -528,15 +540,23 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
     return abort;
 }
 
-// Block-wide sums of the ledger terms into grid a's control block.
+// Block-wide sums of the ledger terms into grid a's control block; the
+// warps' volume sums (led, K levels) are reset for the next grid.
+template <int K>
 __device__ __forceinline__ void tiled_flush(const StepArgs<float> &a, const TiledLedger &L, const int want_hmax,
-                                            double *red)
+                                            double *red, double (*led)[2])
 {
-    const double dtd = a.ctrl->dt;
-    const double bo = block_reduce<false>(L.vout, red);
-    if (threadIdx.x == 0 && bo != 0.0) atomicAdd(&a.ctrl->V_out, dtd * bo);
-    const double bc = block_reduce<false>(L.vclip, red);
-    if (threadIdx.x == 0 && bc != 0.0) atomicAdd(&a.ctrl->V_clip, bc);
+    __syncthreads();                                  // every warp's last run is in led
+    if (threadIdx.x == 0) {
+        double bo = 0.0, bc = 0.0;
+        for (int w = 0; w < K; w++) {
+            bo += led[w][0];
+            bc += led[w][1];
+            led[w][0] = led[w][1] = 0.0;
+        }
+        if (bo != 0.0) atomicAdd(&a.ctrl->V_out, a.ctrl->dt * bo);
+        if (bc != 0.0) atomicAdd(&a.ctrl->V_clip, bc);
+    }
     if (want_hmax) {
         const double bm = block_reduce<true>(L.nan_seen ? (double)NAN : (double)L.hmax, red);
         if (threadIdx.x == 0) atomic_max_nonneg(&a.ctrl->hmax_bits, bm);
@@ -564,6 +584,7 @@ __device__ __forceinline__ void init_ring(PipeSmem<K, kPF, kHo> &sm)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kPF; s++) mbar_init(&sm.bar[s], 1);
         fence_mbar_init();
+        for (int w = 0; w < K; w++) sm.led[w][0] = sm.led[w][1] = 0.0;
     }
     __syncthreads();
 }
@@ -593,7 +614,7 @@ __global__ void __launch_bounds__(K * 32, tiled_min_blocks(K, kMode)) step_tiled
         const int y1 = min(y0 + chunk_rows, a.geo.ny);
         if (tiled_item<K, kPF1, kMode>(a, a.s, Kc, strip, y0, y1, sm, base, L)) break;
     }
-    tiled_flush(a, L, a.want_hmax, red);
+    tiled_flush<K>(a, L, a.want_hmax, red, sm.led);
     if (blockIdx.x == 0 && threadIdx.x == 0) tiled_finish<K>(a, a.s);
 }
 
@@ -604,7 +625,7 @@ __global__ void __launch_bounds__(K * 32, tiled_min_blocks(K, kMode)) step_tiled
 // grid's control block when it moves on; the grid's first item books its
 // inflow volume and clock.
 template <int K, int kMode>
-__global__ void __launch_bounds__(K * 32, K == 4 ? (kMode ? 4 : 5) : K == 8 ? 2 : 1)
+__global__ void __launch_bounds__(K * 32, K == 4 ? (kMode ? 4 : 6) : K == 8 ? 2 : 1)
     step_tiled_ensemble_kernel(const StepArgs<float> *table, const int *base, const int n, const int chunk_rows,
                                const int s0, const int want_hmax)
 {
@@ -625,7 +646,7 @@ __global__ void __launch_bounds__(K * 32, K == 4 ? (kMode ? 4 : 5) : K == 8 ? 2 
             else hi = mid - 1;
         }
         if (lo != cur) {
-            if (cur >= 0) tiled_flush(table[cur], L, want_hmax, red);
+            if (cur >= 0) tiled_flush<K>(table[cur], L, want_hmax, red, sm.led);
             L = TiledLedger();
             cur = lo;
         }
@@ -638,7 +659,7 @@ __global__ void __launch_bounds__(K * 32, K == 4 ? (kMode ? 4 : 5) : K == 8 ? 2 
         if (local == 0 && threadIdx.x == 0) tiled_finish<K>(a, s0);
         if (tiled_item<K, kPFE, kMode>(a, s0, tiled_const(a), strip, y0, y1, sm, ring, L)) break;
     }
-    if (cur >= 0) tiled_flush(table[cur], L, want_hmax, red);
+    if (cur >= 0) tiled_flush<K>(table[cur], L, want_hmax, red, sm.led);
 }
 
 
