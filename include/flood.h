@@ -295,8 +295,11 @@ flood_status flood_ensemble_create(int32_t n, const flood_grid *grids, const voi
                                    const void *const *mannings, const flood_bc_section *const *sections,
                                    const int32_t *n_sections, const flood_opts *opts, flood_ensemble **out);
 /* Launch shape: warps per block (1..4, stream kernel), rows per chunk (stream
- * blocks, or rows per (chunk, strip) item of the tiled kernel), steps per
- * graph replay, graph on/off.  FLOOD_ERR_ARG on values out of range. */
+ * blocks; for the tiled kernel the rows per (chunk, strip) item of a grid of
+ * 2^20 cells, scaled by sqrt(cells / 2^20) for the others, at least 32 and at
+ * most the grid's rows: the largest grids come first with the longest items
+ * and the small ones fill the end of the launch), steps per graph replay,
+ * graph on/off.  FLOOD_ERR_ARG on values out of range. */
 flood_status flood_ensemble_set_launch(flood_ensemble *e, int32_t warps, int32_t rows, int32_t steps_per_graph,
                                        int32_t use_graph);
 /* Kernel for the steps: FLOOD_KERNEL_STREAM (one step per launch) or

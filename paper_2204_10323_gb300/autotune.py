@@ -6,7 +6,8 @@ fastest, and caches the choice in a JSON file keyed by the device name and the
 scenario shapes (``$FLOOD_AUTOTUNE_CACHE`` or
 ``~/.cache/paper_2204_10323_gb300/autotune.json``).  K = 0 is the single-step
 stream kernel (warps and rows shape its blocks); K >= 1 the temporal-blocking
-kernel with K steps per launch (rows per (chunk, strip) item).  Every
+kernel with K steps per launch (rows per (chunk, strip) item of a 2^20-cell
+grid, scaled by the square root of each grid's cells).  Every
 candidate computes bit-identical depths and discharges, so tuning on the live
 run does not change its trajectory; it only advances it.
 """
@@ -48,12 +49,12 @@ def _save(path: str, data: dict) -> None:
 
 def ensemble_key(ens) -> str:
     shapes = ",".join(f"{p.nx}x{p.ny}" for p in ens.problems)
-    return f"v2|{torch.cuda.get_device_name()}|E{ens.problems[0].opts.epoch_steps}|{shapes}"
+    return f"v3|{torch.cuda.get_device_name()}|E{ens.problems[0].opts.epoch_steps}|{shapes}"
 
 
 def default_candidates(E: int) -> Sequence[Shape]:
     stream = [(0, w, r, g) for w in (2, 4) for r in (32, 64, 128) for g in (E, 4 * E)]
-    tiled = [(k, 2, r, g) for k in (2, 4) if E % k == 0 for r in (32, 64, 128, 256, 512) for g in (E, 4 * E)]
+    tiled = [(k, 2, r, g) for k in (2, 4) if E % k == 0 for r in (64, 96, 128, 192, 256) for g in (E, 4 * E)]
     return stream + tiled
 
 

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -34,6 +35,7 @@ struct flood_ensemble {
     int total_blocks = 0;
     int *tbase = nullptr;                  // tiled item prefix, n + 1
     int total_items = 0;
+    int *next_item = nullptr;              // tiled: the item counter of the launch (zeroed before each)
     EpochArgs<float> *etab = nullptr;      // per member: epoch bookkeeping arguments
     int2 *tasks = nullptr;                 // (member, inflow section) pairs
     int n_tasks = 0;
@@ -62,13 +64,27 @@ void drop_graphs(flood_ensemble *e)
     e->graphs.assign(2, nullptr);
 }
 
+// Rows per work item of the temporal-blocking kernel for a member grid: the
+// launch shape's rows for a grid of 2^20 cells, scaled by the square root of
+// the grid's cells over that, at least 32 and at most the grid's rows.  The
+// grids come largest first, so the items shrink towards the end of a launch,
+// where the pipelines, taking items as they come free, fill the tail with the
+// small ones (the measured best of several rules on uneven scenario mixes).
+int item_rows(const flood_ensemble *e, const Geom &g)
+{
+    const double cells = (double)g.nx * g.ny;
+    const int r = (int)(e->rows * std::sqrt(cells / (double)(1 << 20)) + 0.5);
+    return std::min(std::max(r, 32), g.ny);
+}
+
 flood_status build_tables(flood_ensemble *e)
 {
     const int n = (int)e->members.size();
     std::vector<int> base(n + 1, 0), tbase(n + 1, 0);
     for (int k = 0; k < n; k++) {
-        base[k + 1] = base[k] + stream_blocks(e->members[e->order[k]]->geo, e->warps, e->rows);
-        tbase[k + 1] = tbase[k] + tiled_items(e->members[e->order[k]]->geo, e->rows, e->k_steps);
+        const Geom &g = e->members[e->order[k]]->geo;
+        base[k + 1] = base[k] + stream_blocks(g, e->warps, e->rows);
+        tbase[k + 1] = tbase[k] + tiled_items(g, item_rows(e, g), e->k_steps);
     }
     e->total_blocks = base[n];
     e->total_items = tbase[n];
@@ -79,6 +95,7 @@ flood_status build_tables(flood_ensemble *e)
             const int cur = h->cur;
             h->cur = p;
             t[k] = step_args_f32(h, 0);
+            t[k].tile_y = item_rows(e, h->geo);
             h->cur = cur;
         }
         cudaError_t c = cudaMemcpyAsync(e->table[p], t.data(), n * sizeof(StepArgs<float>), cudaMemcpyHostToDevice,
@@ -116,8 +133,10 @@ flood_status ensemble_step(flood_ensemble *e, int64_t limit, cudaStream_t st, in
     // the item table is laid out for k_steps: 8-step tables (wider halos) take
     // only whole 8-step launches, anything shorter runs single stream steps
     if (e->kernel == FLOOD_KERNEL_TILED && !(e->k_steps == 8 && steps < 8)) {
-        c = launch_step_tiled_ensemble(e->table[parity], e->tbase, n, e->total_items, e->rows, steps, s,
-                                       s + steps == E ? 1 : 0, e->mode, st);
+        c = cudaMemsetAsync(e->next_item, 0, sizeof(int), st);
+        if (c == cudaSuccess)
+            c = launch_step_tiled_ensemble(e->table[parity], e->tbase, n, e->total_items, steps, s,
+                                           s + steps == E ? 1 : 0, e->next_item, e->mode, st);
     } else {
         steps = 1;
         c = launch_step_stream_ensemble(e->table[parity], e->base, n, e->total_blocks, e->warps, e->rows, s,
@@ -232,6 +251,7 @@ extern "C" flood_status flood_ensemble_create(int32_t n, const flood_grid *grids
     }
     e->base = (int *)dev_alloc(e->owner, (n + 1) * sizeof(int));
     e->tbase = (int *)dev_alloc(e->owner, (n + 1) * sizeof(int));
+    e->next_item = (int *)dev_alloc(e->owner, sizeof(int));
     e->etab = (EpochArgs<float> *)dev_alloc(e->owner, n * sizeof(EpochArgs<float>));
     std::vector<EpochArgs<float>> et(n);
     std::vector<int2> tk;
@@ -256,7 +276,7 @@ extern "C" flood_status flood_ensemble_create(int32_t n, const flood_grid *grids
     }
     e->n_tasks = (int)tk.size();
     e->tasks = (int2 *)dev_alloc(e->owner, std::max<size_t>(tk.size(), 1) * sizeof(int2));
-    if (!e->base || !e->tbase || !e->etab || !e->tasks ||
+    if (!e->base || !e->tbase || !e->next_item || !e->etab || !e->tasks ||
         cudaMemcpyAsync(e->etab, et.data(), n * sizeof(EpochArgs<float>), cudaMemcpyHostToDevice, e->stream) ||
         (tk.size() &&
          cudaMemcpyAsync(e->tasks, tk.data(), tk.size() * sizeof(int2), cudaMemcpyHostToDevice, e->stream))) {
@@ -349,6 +369,7 @@ extern "C" flood_status flood_ensemble_destroy(flood_ensemble *e)
             if (e->table[p]) dev_free(e->owner, e->table[p]);
         if (e->base) dev_free(e->owner, e->base);
         if (e->tbase) dev_free(e->owner, e->tbase);
+        if (e->next_item) dev_free(e->owner, e->next_item);
         if (e->etab) dev_free(e->owner, e->etab);
         if (e->tasks) dev_free(e->owner, e->tasks);
     }

@@ -102,10 +102,12 @@ cudaError_t launch_step_stream_ensemble(const StepArgs<float> *table, const int 
 int stream_blocks(const Geom &g, int warps, int rows);
 cudaError_t launch_step_tma(const StepArgs<float> &a, cudaStream_t st);
 // Temporal blocking over many grids: the (chunk, strip) items of grid k are
-// base[k] .. base[k+1] - 1 (tiled_items per grid), k_steps steps from s0.
+// base[k] .. base[k+1] - 1 (tiled_items per grid, table[k].tile_y rows per item), k_steps steps from s0.
 int tiled_items(const Geom &g, int chunk_rows, int k_steps);
+// next_item (device, zero before the launch): the pipelines take their items after
+// the first from this counter (dynamic scheduling); null: block b takes b, b + grid, ...
 cudaError_t launch_step_tiled_ensemble(const StepArgs<float> *table, const int *base, int n, int total_items,
-                                       int chunk_rows, int k_steps, int s0, int want_hmax, int mode, cudaStream_t st);
+                                       int k_steps, int s0, int want_hmax, int *next_item, int mode, cudaStream_t st);
 void stream_launch_shape(const Geom &g, int tile_x, int tile_y, int *warps, int *rows);
 cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st);
 

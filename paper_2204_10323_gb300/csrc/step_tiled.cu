@@ -57,16 +57,16 @@ static int tiled_mode(const Geom &g) { return (g.theta != 1.0 ? 1 : 0) | (g.fric
 // step_tiled_opts.cu: the same launchers for modes 1..3.
 cudaError_t launch_step_tiled_opts(const StepArgs<float> &a, int mode, cudaStream_t st);
 cudaError_t launch_step_tiled_ensemble_opts(const StepArgs<float> *table, const int *base, int n, int total_items,
-                                            int chunk_rows, int k_steps, int s0, int want_hmax, int mode,
+                                            int k_steps, int s0, int want_hmax, int *next_item, int mode,
                                             cudaStream_t st);
 
 cudaError_t launch_step_tiled_ensemble(const StepArgs<float> *table, const int *base, int n, int total_items,
-                                       int chunk_rows, int k_steps, int s0, int want_hmax, int mode, cudaStream_t st)
+                                       int k_steps, int s0, int want_hmax, int *next_item, int mode, cudaStream_t st)
 {
     if (mode != 0)
-        return launch_step_tiled_ensemble_opts(table, base, n, total_items, chunk_rows, k_steps, s0, want_hmax, mode,
+        return launch_step_tiled_ensemble_opts(table, base, n, total_items, k_steps, s0, want_hmax, next_item, mode,
                                                st);
-    return launch_tiled_ensemble_mode<0>(table, base, n, total_items, chunk_rows, k_steps, s0, want_hmax, st);
+    return launch_tiled_ensemble_mode<0>(table, base, n, total_items, k_steps, s0, want_hmax, next_item, st);
 }
 
 cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st)

@@ -618,19 +618,23 @@ __global__ void __launch_bounds__(K * 32, tiled_min_blocks(K, kMode)) step_tiled
     if (blockIdx.x == 0 && threadIdx.x == 0) tiled_finish<K>(a, a.s);
 }
 
-// Many grids: the items of grid k (its (chunk, strip) items, chunk_rows rows
-// per chunk) are numbered base[k] .. base[k+1] - 1, grids ordered largest
-// first, and block b takes items b, b + grid, ...  A block sums a grid's
+// Many grids: the items of grid k (its (chunk, strip) items, table[k].tile_y
+// rows per chunk) are numbered base[k] .. base[k+1] - 1, grids ordered largest
+// first; block b takes item b first and then, with next_item, the next
+// unclaimed item of the counter (items grid, grid + 1, ... in the order the
+// pipelines come free), else b + grid, b + 2 grid, ...  Either way a block's
+// items ascend, so its grids do too.  A block sums a grid's
 // ledger terms while its items belong to that grid and hands them to the
 // grid's control block when it moves on; the grid's first item books its
 // inflow volume and clock.
 template <int K, int kMode>
 __global__ void __launch_bounds__(K * 32, K == 4 ? (kMode ? 4 : 6) : K == 8 ? 2 : 1)
-    step_tiled_ensemble_kernel(const StepArgs<float> *table, const int *base, const int n, const int chunk_rows,
-                               const int s0, const int want_hmax)
+    step_tiled_ensemble_kernel(const StepArgs<float> *table, const int *base, const int n, const int s0,
+                               const int want_hmax, int *next_item)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
+    __shared__ int next;
     using Smem = PipeSmem<K, kPFE, hand_fields(kMode)>;
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     init_ring(sm);
@@ -638,7 +642,7 @@ __global__ void __launch_bounds__(K * 32, K == 4 ? (kMode ? 4 : 6) : K == 8 ? 2 
     TiledLedger L;
     uint32_t ring = 0;
     int cur = -1;
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    for (int item = blockIdx.x; item < total;) {
         int lo = 0, hi = n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -654,10 +658,14 @@ __global__ void __launch_bounds__(K * 32, K == 4 ? (kMode ? 4 : 6) : K == 8 ? 2 
         const int local = item - base[lo];
         const int n_strips = (a.geo.nx + out_cols(K, kMode) - 1) / out_cols(K, kMode);
         const int strip = local % n_strips;
-        const int y0 = (local / n_strips) * chunk_rows;
-        const int y1 = min(y0 + chunk_rows, a.geo.ny);
+        const int y0 = (local / n_strips) * a.tile_y;
+        const int y1 = min(y0 + a.tile_y, a.geo.ny);
         if (local == 0 && threadIdx.x == 0) tiled_finish<K>(a, s0);
         if (tiled_item<K, kPFE, kMode>(a, s0, tiled_const(a), strip, y0, y1, sm, ring, L)) break;
+        if (threadIdx.x == 0) next = next_item ? (int)gridDim.x + atomicAdd(next_item, 1) : item + (int)gridDim.x;
+        __syncthreads();
+        item = next;
+        __syncthreads();                              // read by every thread before thread 0 writes it again
     }
     if (cur >= 0) tiled_flush<K>(table[cur], L, want_hmax, red, sm.led);
 }
@@ -708,8 +716,8 @@ cudaError_t launch_k(const StepArgs<float> &a0, cudaStream_t st)
 }
 
 template <int K, int kMode>
-cudaError_t launch_ens_k(const StepArgs<float> *table, const int *base, int n, int total_items, int chunk_rows,
-                         int s0, int want_hmax, cudaStream_t st)
+cudaError_t launch_ens_k(const StepArgs<float> *table, const int *base, int n, int total_items, int s0,
+                         int want_hmax, int *next_item, cudaStream_t st)
 {
     using Smem = PipeSmem<K, kPFE, hand_fields(kMode)>;
     static int cache = 0;
@@ -718,8 +726,8 @@ cudaError_t launch_ens_k(const StepArgs<float> *table, const int *base, int n, i
     if (e != cudaSuccess) return e;
     const int blocks = total_items < resident ? total_items : resident;
     if (blocks < 1) return cudaSuccess;
-    step_tiled_ensemble_kernel<K, kMode><<<blocks, K * 32, sizeof(Smem), st>>>(table, base, n, chunk_rows, s0,
-                                                                             want_hmax);
+    step_tiled_ensemble_kernel<K, kMode><<<blocks, K * 32, sizeof(Smem), st>>>(table, base, n, s0, want_hmax,
+                                                                             next_item);
     return cudaGetLastError();
 }
 
@@ -740,14 +748,14 @@ cudaError_t launch_tiled_mode(const StepArgs<float> &a, cudaStream_t st)
 
 template <int kMode>
 cudaError_t launch_tiled_ensemble_mode(const StepArgs<float> *table, const int *base, int n, int total_items,
-                                       int chunk_rows, int k_steps, int s0, int want_hmax, cudaStream_t st)
+                                       int k_steps, int s0, int want_hmax, int *next_item, cudaStream_t st)
 {
     switch (k_steps) {
-    case 1: return launch_ens_k<1, kMode>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
-    case 2: return launch_ens_k<2, kMode>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
-    case 3: return launch_ens_k<3, kMode>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
-    case 4: return launch_ens_k<4, kMode>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
-    case 8: return launch_ens_k<8, kMode>(table, base, n, total_items, chunk_rows, s0, want_hmax, st);
+    case 1: return launch_ens_k<1, kMode>(table, base, n, total_items, s0, want_hmax, next_item, st);
+    case 2: return launch_ens_k<2, kMode>(table, base, n, total_items, s0, want_hmax, next_item, st);
+    case 3: return launch_ens_k<3, kMode>(table, base, n, total_items, s0, want_hmax, next_item, st);
+    case 4: return launch_ens_k<4, kMode>(table, base, n, total_items, s0, want_hmax, next_item, st);
+    case 8: return launch_ens_k<8, kMode>(table, base, n, total_items, s0, want_hmax, next_item, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -17,13 +17,13 @@ cudaError_t launch_step_tiled_opts(const StepArgs<float> &a, int mode, cudaStrea
 }
 
 cudaError_t launch_step_tiled_ensemble_opts(const StepArgs<float> *table, const int *base, int n, int total_items,
-                                            int chunk_rows, int k_steps, int s0, int want_hmax, int mode,
+                                            int k_steps, int s0, int want_hmax, int *next_item, int mode,
                                             cudaStream_t st)
 {
     switch (mode) {
-    case 1: return launch_tiled_ensemble_mode<1>(table, base, n, total_items, chunk_rows, k_steps, s0, want_hmax, st);
-    case 2: return launch_tiled_ensemble_mode<2>(table, base, n, total_items, chunk_rows, k_steps, s0, want_hmax, st);
-    case 3: return launch_tiled_ensemble_mode<3>(table, base, n, total_items, chunk_rows, k_steps, s0, want_hmax, st);
+    case 1: return launch_tiled_ensemble_mode<1>(table, base, n, total_items, k_steps, s0, want_hmax, next_item, st);
+    case 2: return launch_tiled_ensemble_mode<2>(table, base, n, total_items, k_steps, s0, want_hmax, next_item, st);
+    case 3: return launch_tiled_ensemble_mode<3>(table, base, n, total_items, k_steps, s0, want_hmax, next_item, st);
     default: return cudaErrorInvalidValue;
     }
 }
