@@ -21,8 +21,13 @@
 // order for FP64, the fast FP32 face for FP32), so the clip and wet/dry
 // decisions are exactly the forward's.
 #include <algorithm>
+#include <cstddef>
+#include <type_traits>
+
+#include <cuda.h>
 
 #include "fast_face.cuh"
+#include "tma_util.cuh"
 
 namespace flood {
 
@@ -394,13 +399,45 @@ __global__ void __launch_bounds__(BX * TileRows<T>::v) adj_step_kernel(const Adj
 //   dw_c/dn_j = -delta_cj w_c/n_c + (pe w_c/hh_c) dW/dn_j,
 //   dW/dn_j   = (w_j/n_j) / sum_c (pe w_c/hh_c),
 // so dL/dn_j += (w_j/n_j) (sum_c nu_c pe w_c/hh_c / sum_c pe w_c/hh_c - nu_j).
+
+// Adjoint of the unclipped depth of cell (i, j) from global memory: its four new
+// faces, the update and the clip test with the arithmetic of the tile kernels'
+// phases A and B, the gauge seeds in gauge order.
 template <typename T>
-__global__ void adj_inflow_kernel(const AdjArgs<T> A)
+__device__ T cell_lhu(const AdjArgs<T> &A, const Fwd<T> &F, const int i, const int j)
 {
-    __shared__ double red[32];
+    const StepArgs<T> &a = A.fwd;
+    const int nx = a.geo.nx, ny = a.geo.ny;
+    const size_t P = (size_t)a.geo.pitch, c = (size_t)j * P + i;
+    const T h = a.h[c], z = a.z[c], n = a.n[c];
+    T qW, qE, qS, qN;
+    if (i == 0) qW = bface(a, F, 0, j, h, n);
+    else qW = F.face(a.qx[c], a.h[c - 1], a.z[c - 1], a.n[c - 1], h, z, n);
+    if (i == nx - 1) qE = bface(a, F, 1, j, h, n);
+    else qE = F.face(a.qx[c + 1], h, z, n, a.h[c + 1], a.z[c + 1], a.n[c + 1]);
+    if (j == 0) qS = bface(a, F, 2, i, h, n);
+    else qS = F.face(a.qy[c], a.h[c - P], a.z[c - P], a.n[c - P], h, z, n);
+    if (j == ny - 1) qN = bface(a, F, 3, i, h, n);
+    else qN = F.face(a.qy[c + P], h, z, n, a.h[c + P], a.z[c + P], a.n[c + P]);
+    const T hu = F.update(h, qW, qE, qS, qN);
+    if (hu < T(0)) return T(0);
+    T v = A.lh[c];
+    const int64_t flat = (int64_t)j * nx + i;
+    for (int gk = 0; gk < A.n_gauges; gk++)
+        if (A.gauge_cells[gk] == flat) v = v + T(A.seed[gk]);
+    return v;
+}
+
+// Section k of pass 3 on the calling block.  kFused: the block runs beside the
+// tiles of the same launch, so it derives each cell's adjoint of the unclipped
+// depth itself (cell_lhu) and adds its dL/dn terms to gn_in (one double per
+// section cell, added to gn after the sweep); otherwise it reads lhu from the
+// finished tiles and adds into gn.
+template <typename T, bool kFused>
+__device__ void inflow_adjoint(const AdjArgs<T> &A, const int k, double *red)
+{
     const StepArgs<T> &a = A.fwd;
     const Geom &G = a.geo;
-    const int k = blockIdx.x;
     const InflowSec S = A.secs[k];
     const double Q = a.inflow_Q[(size_t)a.s * a.n_inflow_sec + k];
     if (!(Q > 0.0) || S.ncell == 0) return;
@@ -409,53 +446,323 @@ __global__ void adj_inflow_kernel(const AdjArgs<T> A)
     const double pe = G.bc_form == 0 ? 5.0 / 3.0 : 2.0 / 3.0;
     const double inward = (double)inward_sign(S.side);
     const size_t P = (size_t)G.pitch;
-    double D = 0.0, Nn = 0.0;
-    for (int c = threadIdx.x; c < S.ncell; c += blockDim.x) {
+    const Fwd<T> F(G, a.ctrl->dt);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
+    auto lhu_of = [&](int64_t idx) -> double {
+        if constexpr (kFused) return (double)cell_lhu<T>(A, F, (int)(idx % (int64_t)P), (int)(idx / (int64_t)P));
+        else return (double)A.lhu[idx];
+    };
+    auto lq_of = [&](int64_t idx) -> double {
+        switch (S.side) {
+        case 0: return (double)A.lqx[idx];
+        case 1: return (double)A.lqx[idx + 1];
+        case 2: return (double)A.lqy[idx];
+        default: return (double)A.lqy[idx + P];
+        }
+    };
+    double D = 0.0, Nn = 0.0, nu0 = 0.0;             // nu0: this thread's first cell (reused below)
+    for (int c = tid; c < S.ncell; c += nt) {
         const int64_t idx = A.sec_cells[S.cell0 + c];
         const double hh = W - (double)a.z[idx];
         if (!(hh > 0.0)) continue;
         const double w = (double)a.inflow_q[(size_t)a.s * a.n_slots + S.slot0 + c] * dx;
-        size_t face;
-        double lq;
-        switch (S.side) {
-        case 0: face = idx; lq = (double)A.lqx[face]; break;
-        case 1: face = idx + 1; lq = (double)A.lqx[face]; break;
-        case 2: face = idx; lq = (double)A.lqy[face]; break;
-        default: face = idx + P; lq = (double)A.lqy[face]; break;
-        }
-        const double mu = lq + inward * dtdx * (double)A.lhu[idx];
+        const double mu = lq_of(idx) + inward * dtdx * lhu_of(idx);
         const double nu = inward * mu / dx;
+        if (c == tid) nu0 = nu;
         D += pe * w / hh;
         Nn += nu * pe * w / hh;
     }
     D = block_reduce<false>(D, red);
     __syncthreads();
-    if (threadIdx.x == 0) red[31] = D;
+    if (tid == 0) red[31] = D;
     __syncthreads();
     D = red[31];
     __syncthreads();
     Nn = block_reduce<false>(Nn, red);
     __syncthreads();
-    if (threadIdx.x == 0) red[30] = Nn;
+    if (tid == 0) red[30] = Nn;
     __syncthreads();
     Nn = red[30];
     if (!(D > 0.0)) return;
-    for (int c = threadIdx.x; c < S.ncell; c += blockDim.x) {
+    for (int c = tid; c < S.ncell; c += nt) {
         const int64_t idx = A.sec_cells[S.cell0 + c];
         const double hh = W - (double)a.z[idx];
         if (!(hh > 0.0)) continue;
         const double w = (double)a.inflow_q[(size_t)a.s * a.n_slots + S.slot0 + c] * dx;
-        double lq;
-        switch (S.side) {
-        case 0: lq = (double)A.lqx[idx]; break;
-        case 1: lq = (double)A.lqx[idx + 1]; break;
-        case 2: lq = (double)A.lqy[idx]; break;
-        default: lq = (double)A.lqy[idx + P]; break;
-        }
-        const double mu = lq + inward * dtdx * (double)A.lhu[idx];
-        const double nu = inward * mu / dx;
-        A.gn[idx] += (w / (double)a.n[idx]) * (Nn / D - nu);
+        const double nu = c == tid ? nu0 : inward * (lq_of(idx) + inward * dtdx * lhu_of(idx)) / dx;
+        const double term = (w / (double)a.n[idx]) * (Nn / D - nu);
+        if constexpr (kFused) A.gn_in[S.cell0 + c] += term;
+        else A.gn[idx] += term;
     }
+}
+
+// The fused form's entry, kept out of line: its double-precision section sums
+// would otherwise raise the register count of the tile kernel that calls it.
+__device__ __noinline__ void inflow_adjoint_fused(const AdjArgs<float> &A, const int k, double *red)
+{
+    inflow_adjoint<float, true>(A, k, red);
+}
+
+template <typename T>
+__global__ void adj_inflow_kernel(const AdjArgs<T> A)
+{
+    __shared__ double red[32];
+    inflow_adjoint<T, false>(A, blockIdx.x, red);
+}
+
+// The FP32 reverse step with its inputs staged by the tensor-memory accelerator:
+// one thread issues eight 2D tensor copies (the forward state h, z, n, qx, qy and
+// the adjoint after the step lh, lqx, lqy, each box with its halo, zeros outside
+// the grid) onto one mbarrier, so the tile's staging costs no per-element index
+// arithmetic or load latency in the threads; phases A-D are those of
+// adj_step_kernel.  Staged rows start at column I0 - 4 (16-byte aligned) and
+// are kAW = 40 wide.
+struct AdjMaps {
+    CUtensorMap m[8];            // h, z, n, qx, qy, lh, lqx, lqy
+};
+enum { kMh = 0, kMz, kMn, kMqx, kMqy, kMlh, kMlqx, kMlqy };
+constexpr int kAW = 40;
+// A tensor copy's shared-memory destination must be 128-byte aligned: every box
+// starts on its own 128-byte boundary.
+struct alignas(128) AdjStage {
+    alignas(128) float h[BY + 4][kAW];      // cells: rows J0-2 .., columns I0-4 ..
+    alignas(128) float z[BY + 4][kAW];
+    alignas(128) float n[BY + 4][kAW];
+    alignas(128) float qx[BY + 2][kAW];     // x-faces: rows J0-1 .., face columns I0-4 ..
+    alignas(128) float qy[BY + 3][kAW];     // y-faces: face rows J0-1 .., columns I0-4 ..
+    alignas(128) float lh[BY + 2][kAW];     // lambda_h': rows J0-1 .., columns I0-4 ..
+    alignas(128) float lqx[BY][kAW];        // lambda_qx': rows J0 .., face columns I0 ..
+    alignas(128) float lqy[BY + 1][BX];     // lambda_qy': face rows J0 .., columns I0 ..
+    uint64_t bar;
+};
+static_assert(offsetof(AdjStage, z) % 128 == 0 && offsetof(AdjStage, n) % 128 == 0 &&
+                  offsetof(AdjStage, qx) % 128 == 0 && offsetof(AdjStage, qy) % 128 == 0 &&
+                  offsetof(AdjStage, lh) % 128 == 0 && offsetof(AdjStage, lqx) % 128 == 0 &&
+                  offsetof(AdjStage, lqy) % 128 == 0 && offsetof(AdjStage, bar) % 8 == 0,
+              "tensor-copy destinations must be 128-byte aligned");
+// bytes the eight boxes deliver (the barrier's transaction count)
+constexpr uint32_t kAdjBytes = (uint32_t)sizeof(float) * (3 * (BY + 4) * kAW + (BY + 2) * kAW + (BY + 3) * kAW +
+                                                          (BY + 2) * kAW + BY * kAW + (BY + 1) * BX);
+constexpr uint64_t kAdjBudgetNs = 2000000000ull;
+
+__global__ void __launch_bounds__(BX * BY, 6) adj_step_tma_kernel(const AdjArgs<float> A, const int nbx,
+                                                                 const int n_tiles,
+                                                                 const __grid_constant__ AdjMaps maps)
+{
+    using T = float;
+    const int n_sec = (int)gridDim.x - n_tiles;
+    if ((int)blockIdx.x < n_sec) {                   // the first blocks: pass 3, one section each, beside the tiles
+        __shared__ double red_in[32];
+        inflow_adjoint_fused(A, (int)blockIdx.x, red_in);
+        return;
+    }
+    const int tile = (int)blockIdx.x - n_sec;
+    __shared__ AdjStage S;
+    __shared__ T sX[BY + 2][BX + 3];   // new x-faces: rows J0-1 .., face columns I0-1 ..
+    __shared__ T sY[BY + 3][BX + 2];   // new y-faces: face rows J0-1 .., columns I0-1 ..
+    __shared__ T sL[BY + 2][BX + 2];   // cells I0-1 .., J0-1 ..
+    __shared__ T cXl[BY][BX + 1], cXr[BY][BX + 1], cXn[BY][BX + 1];
+    __shared__ T cYl[BY + 1][BX], cYr[BY + 1][BX], cYn[BY + 1][BX];
+    __shared__ int s_ng, s_gk[kTileGauges];
+    const StepArgs<T> &a = A.fwd;
+    const Geom &G = a.geo;
+    const int nx = G.nx, ny = G.ny;
+    const size_t P = (size_t)G.pitch;
+    const double dtd = a.ctrl->dt;
+    const Fwd<T> F(G, dtd);
+    const T dt = T(dtd), dx = T(G.dx), g = T(G.g), hd = T(G.h_dry), dtdx = dt / dx;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    const int I0 = (tile % nbx) * BX, J0 = (tile / nbx) * BY;
+
+    // 0. the eight boxes onto one barrier; the gauge list is built meanwhile
+    if (tid == 0) {
+        mbar_init(&S.bar, 1);
+        fence_mbar_init();
+        s_ng = 0;
+        mbar_arrive_expect_tx(&S.bar, kAdjBytes);
+        tma_load_2d(&S.h[0][0], &maps.m[kMh], I0 - 4, J0 - 2, &S.bar);
+        tma_load_2d(&S.z[0][0], &maps.m[kMz], I0 - 4, J0 - 2, &S.bar);
+        tma_load_2d(&S.n[0][0], &maps.m[kMn], I0 - 4, J0 - 2, &S.bar);
+        tma_load_2d(&S.qx[0][0], &maps.m[kMqx], I0 - 4, J0 - 1, &S.bar);
+        tma_load_2d(&S.qy[0][0], &maps.m[kMqy], I0 - 4, J0 - 1, &S.bar);
+        tma_load_2d(&S.lh[0][0], &maps.m[kMlh], I0 - 4, J0 - 1, &S.bar);
+        tma_load_2d(&S.lqx[0][0], &maps.m[kMlqx], I0, J0, &S.bar);
+        tma_load_2d(&S.lqy[0][0], &maps.m[kMlqy], I0, J0, &S.bar);
+    }
+    __syncthreads();
+    // B prelude: the gauges inside the tile and its halo, in gauge order (repeated
+    // gauges add up in order); a tile holding more than kTileGauges scans them all
+    for (int gk = tid; gk < A.n_gauges; gk += BX * BY) {
+        const int64_t flat = A.gauge_cells[gk];
+        const int gj = (int)(flat / nx), gi = (int)(flat - (int64_t)gj * nx);
+        if (gj >= J0 - 1 && gj <= J0 + BY && gi >= I0 - 1 && gi <= I0 + BX) {
+            const int slot = atomicAdd(&s_ng, 1);
+            if (slot < kTileGauges) s_gk[slot] = gk;
+        }
+    }
+    const bool ok = mbar_wait_bounded(&S.bar, 0u, kAdjBudgetNs);
+    if (!__syncthreads_and(ok ? 1 : 0)) {
+        if (tid == 0) {
+            atomicOr(&a.ctrl->status, kStatusTimeout);
+            mbar_wait_bounded(&S.bar, 0u, kAdjBudgetNs);   // no copy may land after the block is gone
+        }
+        return;
+    }
+    if (tid == 0 && s_ng > 1 && s_ng <= kTileGauges) {
+        for (int x = 1; x < s_ng; x++)
+            for (int y = x; y > 0 && s_gk[y - 1] > s_gk[y]; y--) {
+                const int tmp = s_gk[y];
+                s_gk[y] = s_gk[y - 1];
+                s_gk[y - 1] = tmp;
+            }
+    }
+    // A. new face values.  x-face (lj, li): row J0-1+lj, face column fi = I0-1+li, between
+    // cells at staged columns li+2 (L) and li+3 (R) of staged row lj+1.
+    for (int t = tid; t < (BY + 2) * (BX + 3); t += BX * BY) {
+        const int lj = t / (BX + 3), li = t % (BX + 3);
+        const int j = J0 - 1 + lj, fi = I0 - 1 + li;
+        T v = T(0);
+        if (j >= 0 && j < ny && fi >= 0 && fi <= nx) {
+            const int sj = lj + 1, sl = li + 2, sr = li + 3;
+            if (fi == 0) v = bface(a, F, 0, j, S.h[sj][sr], S.n[sj][sr]);
+            else if (fi == nx) v = bface(a, F, 1, j, S.h[sj][sl], S.n[sj][sl]);
+            else
+                v = F.face(S.qx[lj][li + 3], S.h[sj][sl], S.z[sj][sl], S.n[sj][sl], S.h[sj][sr], S.z[sj][sr],
+                           S.n[sj][sr]);
+        }
+        sX[lj][li] = v;
+    }
+    // y-face (lj, li): face row fj = J0-1+lj, column i = I0-1+li, between cells of
+    // staged rows lj (below) and lj+1 (above) at staged column li+3.
+    for (int t = tid; t < (BY + 3) * (BX + 2); t += BX * BY) {
+        const int lj = t / (BX + 2), li = t % (BX + 2);
+        const int fj = J0 - 1 + lj, i = I0 - 1 + li;
+        T v = T(0);
+        if (i >= 0 && i < nx && fj >= 0 && fj <= ny) {
+            const int sc = li + 3, sb = lj, st = lj + 1;
+            if (fj == 0) v = bface(a, F, 2, i, S.h[st][sc], S.n[st][sc]);
+            else if (fj == ny) v = bface(a, F, 3, i, S.h[sb][sc], S.n[sb][sc]);
+            else
+                v = F.face(S.qy[lj][li + 3], S.h[sb][sc], S.z[sb][sc], S.n[sb][sc], S.h[st][sc], S.z[st][sc],
+                           S.n[st][sc]);
+        }
+        sY[lj][li] = v;
+    }
+    __syncthreads();
+    // B. adjoint of the unclipped depth (gauge seeds included)
+    const int ng_tile = s_ng;
+    for (int t = tid; t < (BY + 2) * (BX + 2); t += BX * BY) {
+        const int lj = t / (BX + 2), li = t % (BX + 2);
+        const int j = J0 - 1 + lj, i = I0 - 1 + li;
+        T v = T(0);
+        if (i >= 0 && i < nx && j >= 0 && j < ny) {
+            const T hu = F.update(S.h[lj + 1][li + 3], sX[lj][li], sX[lj][li + 1], sY[lj][li], sY[lj + 1][li]);
+            if (!(hu < T(0))) {
+                v = S.lh[lj][li + 3];
+                if (ng_tile > 0) {
+                    const int64_t flat = (int64_t)j * nx + i;
+                    if (ng_tile <= kTileGauges) {
+                        for (int x = 0; x < ng_tile; x++)
+                            if (A.gauge_cells[s_gk[x]] == flat) v = v + T(A.seed[s_gk[x]]);
+                    } else {
+                        for (int gk = 0; gk < A.n_gauges; gk++)
+                            if (A.gauge_cells[gk] == flat) v = v + T(A.seed[gk]);
+                    }
+                }
+            }
+        }
+        sL[lj][li] = v;
+    }
+    __syncthreads();
+    // C. each face touching the tile once.  x-face (lj, li): row J0+lj, face column
+    // fi = I0+li; cells at staged columns li+3 (L) and li+4 (R) of staged row lj+2.
+    for (int t = tid; t < BY * (BX + 1); t += BX * BY) {
+        const int lj = t / (BX + 1), li = t % (BX + 1);
+        const int j = J0 + lj, fi = I0 + li;
+        T cl = T(0), cr = T(0), cn = T(0);
+        if (j < ny && fi <= nx) {
+            const size_t r = (size_t)j * P;
+            const T lR = sL[lj + 1][li + 1], lL = sL[lj + 1][li];
+            const int sj = lj + 2, sl = li + 3, sr = li + 4;
+            if (fi == 0) {
+                const T mu = S.lqx[lj][li] + dtdx * lR;
+                outflow_adj(a, F, 0, j, S.h[sj][sr], S.n[sj][sr], mu, cr, cn);
+                A.lqx_out[r] = T(0);
+            } else if (fi == nx) {
+                const T mu = S.lqx[lj][li] - dtdx * lL;
+                outflow_adj(a, F, 1, j, S.h[sj][sl], S.n[sj][sl], mu, cl, cn);
+                A.lqx_out[r + nx] = T(0);
+            } else {
+                const T mu = S.lqx[lj][li] + dtdx * (lR - lL);
+                const T hL = S.h[sj][sl], zL = S.z[sj][sl], nL = S.n[sj][sl];
+                const T hR = S.h[sj][sr], zR = S.z[sj][sr], nR = S.n[sj][sr];
+                const T hf = F.hf(hL, zL, hR, zR);
+                T lq = T(0);
+                if (hf > hd && mu != T(0)) {
+                    FaceLin<T> d = face_lin<T>(S.qx[lj + 1][li + 4], hL, zL, nL, hR, zR, nR, hf, g, dt, dx);
+                    cl = mu * d.dhL;
+                    cr = mu * d.dhR;
+                    cn = mu * d.dn;
+                    lq = mu * d.dq;
+                }
+                if (li < BX) A.lqx_out[r + fi] = lq;        // the tile owns the west faces of its cells
+            }
+        }
+        cXl[lj][li] = cl;
+        cXr[lj][li] = cr;
+        cXn[lj][li] = cn;
+    }
+    // y-face (lj, li): face row fj = J0+lj, column i = I0+li; cells of staged rows
+    // lj+1 (below) and lj+2 (above) at staged column li+4.
+    for (int t = tid; t < (BY + 1) * BX; t += BX * BY) {
+        const int lj = t / BX, li = t % BX;
+        const int fj = J0 + lj, i = I0 + li;
+        T cl = T(0), cr = T(0), cn = T(0);
+        if (i < nx && fj <= ny) {
+            const T lR = sL[lj + 1][li + 1], lL = sL[lj][li + 1];
+            const int sc = li + 4, sb = lj + 1, st = lj + 2;
+            if (fj == 0) {
+                const T mu = S.lqy[lj][li] + dtdx * lR;
+                outflow_adj(a, F, 2, i, S.h[st][sc], S.n[st][sc], mu, cr, cn);
+                A.lqy_out[i] = T(0);
+            } else if (fj == ny) {
+                const size_t c = (size_t)(ny - 1) * P + i;
+                const T mu = S.lqy[lj][li] - dtdx * lL;
+                outflow_adj(a, F, 3, i, S.h[sb][sc], S.n[sb][sc], mu, cl, cn);
+                A.lqy_out[c + P] = T(0);
+            } else {
+                const size_t c = (size_t)fj * P + i;
+                const T mu = S.lqy[lj][li] + dtdx * (lR - lL);
+                const T hL = S.h[sb][sc], zL = S.z[sb][sc], nL = S.n[sb][sc];
+                const T hR = S.h[st][sc], zR = S.z[st][sc], nR = S.n[st][sc];
+                const T hf = F.hf(hL, zL, hR, zR);
+                T lq = T(0);
+                if (hf > hd && mu != T(0)) {
+                    FaceLin<T> d = face_lin<T>(S.qy[lj + 1][li + 4], hL, zL, nL, hR, zR, nR, hf, g, dt, dx);
+                    cl = mu * d.dhL;
+                    cr = mu * d.dhR;
+                    cn = mu * d.dn;
+                    lq = mu * d.dq;
+                }
+                if (lj < BY) A.lqy_out[c] = lq;             // the tile owns the south faces of its cells
+            }
+        }
+        cYl[lj][li] = cl;
+        cYr[lj][li] = cr;
+        cYn[lj][li] = cn;
+    }
+    __syncthreads();
+    // D. gather per tile cell
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = I0 + tx, j = J0 + ty;
+    if (i >= nx || j >= ny) return;
+    const size_t c = (size_t)j * P + i;
+    const T lu = sL[ty + 1][tx + 1];
+    const T lh = lu + cXr[ty][tx] + cXl[ty][tx + 1] + cYr[ty][tx] + cYl[ty + 1][tx];
+    const T gs = (cXn[ty][tx] + cXn[ty][tx + 1]) + (cYn[ty][tx] + cYn[ty + 1][tx]);
+    A.lh_out[c] = lh;
+    A.gn[c] += (double)gs;
+    if (i == 0 || j == 0 || i == nx - 1 || j == ny - 1) A.lhu[c] = lu;   // read by the inflow pass
 }
 
 // ---------------------------------------------------------------- the scheme options
@@ -785,12 +1092,29 @@ cudaError_t launch_gn_out(const Geom &g, const double *gn, T *dst, cudaStream_t 
 }
 
 template cudaError_t launch_gn_out<float>(const Geom &, const double *, float *, cudaStream_t);
+
+namespace {
+__global__ void gn_inflow_add_kernel(double *gn, const double *gn_in, const int64_t *cells, int n)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int c = 0; c < n; c++) gn[cells[c]] += gn_in[c];     // in section-cell order (a corner cell may repeat)
+}
+}  // namespace
+
+cudaError_t launch_gn_inflow_add(double *gn, const double *gn_in, const int64_t *sec_cells, int n_cells,
+                                 cudaStream_t st)
+{
+    if (n_cells <= 0) return cudaSuccess;
+    gn_inflow_add_kernel<<<1, 32, 0, st>>>(gn, gn_in, sec_cells, n_cells);
+    return cudaGetLastError();
+}
 template cudaError_t launch_gn_out<double>(const Geom &, const double *, double *, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_adjoint_step(const AdjArgs<T> &A, cudaStream_t st)
 {
     const Geom &G = A.fwd.geo;
+    cudaError_t e0 = cudaSuccess;
     if (G.theta != 1.0 || G.friction != 0) {
         if (!A.scratch) return cudaErrorInvalidValue;
         const dim3 block(BX, 8);
@@ -802,6 +1126,30 @@ cudaError_t launch_adjoint_step(const AdjArgs<T> &A, cudaStream_t st)
         const int nby1 = (G.ny + 1 + 7) / 8;
         adj_opt_faces_kernel<T><<<(unsigned)((int64_t)nbx * nby1), block, 0, st>>>(A, 1, nbx);
         adj_opt_gather_kernel<T><<<(unsigned)((int64_t)nbx * nby), block, 0, st>>>(A, nbx);
+    } else if constexpr (std::is_same<T, float>::value) {
+        // FP32: the tile's inputs staged by tensor copies (maps of this step's buffers)
+        const int P = G.pitch, nx = G.nx, ny = G.ny;
+        const StepArgs<float> &f = A.fwd;
+        AdjMaps maps;
+        const struct {
+            const float *base;
+            int w, h, bw, bh;
+        } fields[8] = {{f.h, nx, ny, kAW, BY + 4},          {f.z, nx, ny, kAW, BY + 4},
+                       {f.n, nx, ny, kAW, BY + 4},          {f.qx, nx + 1, ny, kAW, BY + 2},
+                       {f.qy, nx, ny + 1, kAW, BY + 3},     {A.lh, nx, ny, kAW, BY + 2},
+                       {A.lqx, nx + 1, ny, kAW, BY},        {A.lqy, nx, ny + 1, BX, BY + 1}};
+        for (int k = 0; k < 8; k++) {
+            const cudaError_t e = encode_map_f32(&maps.m[k], fields[k].base, fields[k].w, fields[k].h, P,
+                                                 fields[k].bw, fields[k].bh);
+            if (e != cudaSuccess) return e;
+        }
+        const int nbx = (nx + BX - 1) / BX, nby = (ny + BY - 1) / BY;
+        const int n_tiles = nbx * nby, n_sec = A.gn_in ? A.fwd.n_inflow_sec : 0;
+        adj_step_tma_kernel<<<(unsigned)(n_tiles + n_sec), dim3(BX, BY), 0, st>>>(A, nbx, n_tiles, maps);
+        e0 = cudaGetLastError();
+        if (e0 != cudaSuccess || n_sec > 0) return e0;   // pass 3 ran in the same launch
+        if (A.fwd.n_inflow_sec > 0) adj_inflow_kernel<T><<<A.fwd.n_inflow_sec, 256, 0, st>>>(A);
+        return cudaGetLastError();
     } else {
         constexpr int BYT = TileRows<T>::v;
         dim3 block(BX, BYT);

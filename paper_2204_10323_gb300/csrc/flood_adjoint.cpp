@@ -93,6 +93,8 @@ struct Sweep {
     void *lhu = nullptr;
     void *scratch = nullptr;      // the scheme options' reverse step: 11 planes of pitch x (ny + 1)
     double *gn = nullptr;
+    double *gn_in = nullptr;      // FP32, Eq. 3 as printed, with inflow sections: their dL/dn terms per cell
+    int n_in_cells = 0;
     int cur_l = 0;
     const int64_t *cells = nullptr;
     int G = 0;
@@ -266,6 +268,7 @@ flood_status reverse_step_t(Sweep &S)
     A.n_gauges = S.G;
     A.seed = S.seed + (size_t)k * S.G;      // dL/dh after step k, added to lambda_{k+1}
     A.scratch = (T *)S.scratch;
+    A.gn_in = S.gn_in;
     if (S.profile) {
         flood_status ts = timed(S, S.ev_rev, [&] {
             cudaError_t e = launch_adjoint_step<T>(A, h->stream);
@@ -419,6 +422,14 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     const bool opts = h->geo.theta != 1.0 || h->geo.friction != 0;
     if (opts) S.scratch = alloc(11 * S.plane_y);
     S.gn = (double *)alloc(P * h->geo.ny * sizeof(double));
+    if (h->prec == FLOOD_F32 && !opts && h->n_in > 0) {      // the reverse step computes pass 3 beside its tiles
+        S.n_in_cells = h->n_slots;
+        S.gn_in = (double *)alloc((size_t)S.n_in_cells * sizeof(double));
+        if (!S.gn_in) {
+            release();
+            return fail(h, FLOOD_ERR_OOM, "adjoint buffer allocation");
+        }
+    }
     double *seed_dev = (double *)alloc(std::max<size_t>((size_t)n_steps * n_gauges, 1) * sizeof(double));
     int64_t *cells_dev = (int64_t *)alloc(std::max(n_gauges, 1) * sizeof(int64_t));
     for (void *p : {(void *)S.dt_log, (void *)S.tl_log, S.iq_log, (void *)S.iQ_log, (void *)S.iW_log, S.lh[0],
@@ -478,6 +489,7 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     }
     CKF(cudaMemsetAsync(S.lhu, 0, S.plane, h->stream));
     CKF(cudaMemsetAsync(S.gn, 0, P * h->geo.ny * sizeof(double), h->stream));
+    if (S.gn_in) CKF(cudaMemsetAsync(S.gn_in, 0, (size_t)S.n_in_cells * sizeof(double), h->stream));
     S.cells = cells_dev;
     S.G = n_gauges;
     S.seed = seed_dev;
@@ -510,6 +522,7 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
         h->adj_prof_fwd_ms = sum_pairs(S.ev_fwd);
     }
     // outputs
+    if (S.gn_in) CKF(launch_gn_inflow_add(S.gn, S.gn_in, h->sec_cells, S.n_in_cells, h->stream));
     {
         flood_status st = FLOOD_OK;
         if (h->prec == FLOOD_F32) st = (flood_status)(launch_gn_out<float>(h->geo, S.gn, (float *)S.lhu, h->stream) ? FLOOD_ERR_CUDA : FLOOD_OK);

@@ -175,12 +175,22 @@ struct AdjArgs {
     const double *seed;           // dL/d(depth at gauge g after this step), n_gauges values (device)
     T *scratch;                   // scheme options only: 11 planes of pitch x (ny + 1) elements (face
                                   // contributions of both axes and the clip mask); null otherwise
+    double *gn_in;                // FP32, Eq. 3 as printed: the inflow sections' dL/dn terms per section cell
+                                  // (index cell0 + c), summed over the sweep, added to gn after it
+                                  // (launch_gn_inflow_add); null: added to gn by each step
 };
 template <typename T>
 cudaError_t launch_adjoint_step(const AdjArgs<T> &a, cudaStream_t st);
+// 2D tensor map (a CUtensorMap, 64-byte aligned storage at map) of a pitched FP32
+// field of width x height elements and a row pitch of `pitch` elements, for boxes
+// of box_w x box_h elements; elements outside the field read as zeros.
+cudaError_t encode_map_f32(void *map, const float *base, int width, int height, int pitch, int box_w, int box_h);
 // dst (pitched, precision T) = gn (pitched doubles).
 template <typename T>
 cudaError_t launch_gn_out(const Geom &g, const double *gn, T *dst, cudaStream_t st);
+// gn[sec_cells[c]] += gn_in[c] for c = 0 .. n_cells - 1, in that order.
+cudaError_t launch_gn_inflow_add(double *gn, const double *gn_in, const int64_t *sec_cells, int n_cells,
+                                 cudaStream_t st);
 
 // Pitch padding (columns [cols, pitch) of rows x pitch elements of esz bytes):
 // fill with the poison pattern, or count the elements whose bits differ from it.
