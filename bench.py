@@ -481,7 +481,9 @@ def adjoint_ratio(F, torch, steps: int = 2000, checkpoints: int = 40):
     both measured by the library's event profiling inside the same
     flood_adjoint call; end_to_end: the gradient with 40 snapshots (binomial
     checkpointing, 5097 forward replays) over the plain 2000-step forward run,
-    CUDA events around the library calls on the library's stream."""
+    CUDA events around the library calls on the library's stream;
+    auto_checkpoints: the same gradient with the snapshot count sized by the
+    free device memory (every state kept on a GB300)."""
     import inputs
     p = inputs.c5_calibration(truth=False, steps=steps)
     g = p.gauges
@@ -505,6 +507,9 @@ def adjoint_ratio(F, torch, steps: int = 2000, checkpoints: int = 40):
     s3.adjoint(64, g, seed[:64], n_checkpoints=8)           # warm-up of the adjoint path
     t_grad = timed(lambda: s3.adjoint(steps, g, seed, n_checkpoints=checkpoints))
     replays = s3.adjoint_forward_steps()
+    # the snapshot count sized by the free device memory (n_checkpoints = 0): every state kept
+    t_grad_auto = timed(lambda: s3.adjoint(steps, g, seed, n_checkpoints=0))
+    replays_auto = s3.adjoint_forward_steps()
     s3.adjoint_profile(True)
     s3.adjoint(steps, g, seed, n_checkpoints=checkpoints)
     prof = s3.adjoint_times()
@@ -516,7 +521,11 @@ def adjoint_ratio(F, torch, steps: int = 2000, checkpoints: int = 40):
             "forward_ms_per_step": per_fwd, "adjoint_ms_per_step": per_rev,
             "per_step_ratio": per_rev / per_fwd, "end_to_end_ratio": t_grad / t_fwd,
             "checkpoints": checkpoints, "forward_replays": replays,
-            "gradient_ms": t_grad, "forward_run_ms": t_fwd}
+            "gradient_ms": t_grad, "forward_run_ms": t_fwd,
+            "auto_checkpoints": {"end_to_end_ratio": t_grad_auto / t_fwd, "gradient_ms": t_grad_auto,
+                                 "forward_replays": replays_auto,
+                                 "what": "n_checkpoints = 0: snapshots sized by half the free device memory "
+                                         "(all 2000 states here)"}}
 
 
 def ensemble_throughput(F, torch, single_value: float, n: int = 96, steps: int = 1024, shape=None):

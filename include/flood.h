@@ -239,7 +239,9 @@ flood_status flood_run_gauges(flood_handle *h, int64_t n_steps, const int64_t *g
  * future work) of L = sum_k sum_g dLdh[k*n_gauges+g] * h_g(after step k) over
  * the next n_steps steps from the current state, with the time-step schedule
  * held fixed (chosen by the forward sweep).  Binomial checkpointing keeps at
- * most n_checkpoints states on the device (>= 1).  dLdh: host doubles.
+ * most n_checkpoints states on the device (>= 1; 0: as many as half the free
+ * device memory holds, up to n_steps, where every state is kept and no step is
+ * replayed twice).  dLdh: host doubles.
  * dLdn_out: ny*nx elements of the grid's precision, host (out_on_device = 0)
  * or device.  dLdh0_out: optional (NULL) gradient with respect to the
  * starting depth.  The handle's state, clock and ledger are unchanged.

@@ -364,7 +364,7 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     if (!h) return fail(nullptr, FLOOD_ERR_ARG, "handle is NULL");
     if (h->part) return fail(h, FLOOD_ERR_STATE, "a part of a decomposed grid is stepped by its decomposition");
     NvtxRange range("flood: adjoint sweep");
-    if (n_steps < 1 || n_gauges < 0 || n_checkpoints < 1 || !dLdn_out || (n_gauges > 0 && (!gauge_cells || !dLdh)))
+    if (n_steps < 1 || n_gauges < 0 || n_checkpoints < 0 || !dLdn_out || (n_gauges > 0 && (!gauge_cells || !dLdh)))
         return fail(h, FLOOD_ERR_ARG, "bad adjoint arguments");
     if (h->sticky) return fail(h, FLOOD_ERR_STATE, "handle is in an error state; write a new state first");
     const int64_t nc = (int64_t)h->geo.nx * h->geo.ny;
@@ -380,7 +380,15 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     S.E = h->geo.epoch_steps;
     S.plane = P * h->geo.ny * esz;
     S.plane_y = P * (h->geo.ny + 1) * esz;
-    const int C = (int)std::min<int64_t>(n_checkpoints, n_steps);
+    // n_checkpoints = 0: as many snapshots as half the free device memory holds, at most
+    // one per step (every state kept: no step is replayed twice)
+    int64_t want = n_checkpoints;
+    if (want == 0) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(h, FLOOD_ERR_CUDA, "cudaMemGetInfo");
+        want = std::max<int64_t>(1, (int64_t)(free_b / 2 / (2 * S.plane + S.plane_y)));
+    }
+    const int C = (int)std::min<int64_t>(want, n_steps);
     std::vector<void *> mine;
     auto alloc = [&](size_t bytes) {
         void *p = dev_alloc(h, bytes);
@@ -391,14 +399,19 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
         for (void *p : mine) dev_free(h, p);
         mine.clear();
     };
+    // the snapshots in one allocation (planes are multiples of 128 bytes)
     S.slots.resize(C);
-    for (int c = 0; c < C; c++) {
-        S.slots[c].h = alloc(S.plane);
-        S.slots[c].qx = alloc(S.plane);
-        S.slots[c].qy = alloc(S.plane_y);
-        if (!S.slots[c].h || !S.slots[c].qx || !S.slots[c].qy) {
+    {
+        const size_t slot = 2 * S.plane + S.plane_y;
+        char *block = (char *)alloc((size_t)C * slot);
+        if (!block) {
             release();
             return fail(h, FLOOD_ERR_OOM, "checkpoint allocation");
+        }
+        for (int c = 0; c < C; c++) {
+            S.slots[c].h = block + (size_t)c * slot;
+            S.slots[c].qx = block + (size_t)c * slot + S.plane;
+            S.slots[c].qy = block + (size_t)c * slot + 2 * S.plane;
         }
     }
     for (int c = C - 1; c >= 1; c--) S.free_slots.push_back(c);

@@ -140,6 +140,22 @@ def test_revolve_equals_store_all_and_costs_the_binomial_minimum(checkpoints):
     assert s.adjoint_forward_steps() == closed_cost(steps, checkpoints)
 
 
+@pytest.mark.parametrize("prec", ["F32", "F64"])
+def test_automatic_checkpoints_keep_every_state(prec):
+    # n_checkpoints = 0 sizes the snapshots by the free device memory: this small
+    # grid keeps all of them, so it replays like store-all and gives its bits
+    Fm = F()
+    p = wet_case(seed=3)
+    steps = 45
+    w = np.random.default_rng(9).standard_normal((steps, len(GAUGES)))
+    s = Fm.Sim(p, precision=getattr(Fm, prec))
+    ref = s.adjoint(steps, GAUGES, w, n_checkpoints=steps)
+    gn = s.adjoint(steps, GAUGES, w, n_checkpoints=0)
+    assert s.adjoint_forward_steps() == steps - 1
+    assert np.array_equal(gn, ref)
+    assert np.array_equal(s.adjoint(steps, GAUGES, w, n_checkpoints=3), ref)
+
+
 def test_adjoint_leaves_the_handle_unchanged():
     Fm = F()
     p = wet_case(seed=4, dt_mode=0)
