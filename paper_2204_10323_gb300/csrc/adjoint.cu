@@ -73,6 +73,7 @@ template <> struct Fwd<float> {
         dx = (float)G.dx;
         K.gdt = (float)G.g * dt;
         K.a1 = K.gdt / dx;
+        K.gdt4 = 0.25f * K.gdt;
         K.h_dry = (float)G.h_dry;
         K.dtdx = dt / dx;
         hd = K.h_dry;
@@ -790,6 +791,7 @@ template <> struct OptFace<float> {
         const float dt = (float)dt_, dx = (float)G.dx;
         K.gdt = (float)G.g * dt;
         K.a1 = K.gdt / dx;
+        K.gdt4 = 0.25f * K.gdt;
         K.h_dry = (float)G.h_dry;
         K.dtdx = dt / dx;
         K.theta = (float)G.theta;

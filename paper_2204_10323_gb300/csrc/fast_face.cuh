@@ -12,6 +12,7 @@ namespace flood {
 struct FastConst {
     float a1;       // g dt / dx   (slope term factor)
     float gdt;      // g dt        (friction factor)
+    float gdt4;     // g dt / 4    (friction factor of the Manning sum n_L + n_R: n_f^2 = (n_L + n_R)^2 / 4)
     float h_dry;
     float dtdx;     // dt / dx
     float theta, w; // face-flux weighting theta and (1 - theta)/2
@@ -76,8 +77,9 @@ __device__ __forceinline__ float face_wet(float qmag, float qn, float etaL, floa
                                           const FastConst &k)
 {
     float r7 = pow_m73(hf);
-    float nf = __fmul_rn(0.5f, nsum);
-    float aq = __fmul_rn(__fmul_rn(k.gdt, __fmul_rn(nf, nf)), qmag);
+    // g dt n_f^2 |q| with n_f = nsum / 2 as (g dt / 4)(nsum^2)|q|: the scalings by
+    // powers of two are exact, so this is the same number with one product fewer
+    float aq = __fmul_rn(__fmul_rn(k.gdt4, __fmul_rn(nsum, nsum)), qmag);
     float num = __fmaf_rn(__fmul_rn(-k.a1, hf), __fsub_rn(etaR, etaL), qn);
     return __fmul_rn(num, rcp_fast(__fmaf_rn(aq, r7, 1.0f)));
 }
@@ -155,8 +157,7 @@ __device__ __forceinline__ float2 face_fast_sel_x2_gen(unsigned long long qmag, 
     const unsigned long long l = f2mul(f2pack(lg2_fast(h.x), lg2_fast(h.y)), f2pack(-7.0f / 3.0f, -7.0f / 3.0f));
     const float2 lv = f2unpack(l);
     const unsigned long long r7 = f2pack(ex2_fast(lv.x), ex2_fast(lv.y));
-    const unsigned long long nf = f2mul(f2pack(0.5f, 0.5f), nsum);
-    const unsigned long long aq = f2mul(f2mul(f2pack(k.gdt, k.gdt), f2mul(nf, nf)), qmag);
+    const unsigned long long aq = f2mul(f2mul(f2pack(k.gdt4, k.gdt4), f2mul(nsum, nsum)), qmag);
     const unsigned long long num = f2fma(f2mul(f2pack(-k.a1, -k.a1), hf), f2sub(etaR, etaL), qn);
     const float2 den = f2unpack(f2fma(aq, r7, f2pack(1.0f, 1.0f)));
     const float2 v = f2unpack(f2mul(num, f2pack(rcp_fast(den.x), rcp_fast(den.y))));

@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(kWarps * 32) step_rows_kernel(const StepArgs<f
     const float dt = (float)dtd, dx = (float)G.dx, g = (float)G.g;
     K.gdt = g * dt;
     K.a1 = K.gdt / dx;
+    K.gdt4 = 0.25f * K.gdt;
     K.h_dry = (float)G.h_dry;
     K.dtdx = dt / dx;
     const float *__restrict__ H = a.h;

@@ -129,6 +129,7 @@ __device__ __forceinline__ bool stream_body(const StepArgs<float> &a, const int 
     const float dt = (float)dtd, dx = (float)G.dx, g = (float)G.g;
     K.gdt = g * dt;
     K.a1 = K.gdt / dx;
+    K.gdt4 = 0.25f * K.gdt;
     K.h_dry = (float)G.h_dry;
     K.dtdx = dt / dx;
     K.theta = (float)G.theta;

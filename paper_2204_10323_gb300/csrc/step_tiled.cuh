@@ -114,6 +114,7 @@ __device__ __forceinline__ FastConst tiled_const(const StepArgs<float> &a)
     FastConst Kc;
     Kc.gdt = g * dt;
     Kc.a1 = Kc.gdt / dx;
+    Kc.gdt4 = 0.25f * Kc.gdt;
     Kc.h_dry = (float)G.h_dry;
     Kc.dtdx = dt / dx;
     Kc.theta = (float)G.theta;
