@@ -528,7 +528,7 @@ def adjoint_ratio(F, torch, steps: int = 2000, checkpoints: int = 40):
                                          "(all 2000 states here)"}}
 
 
-def ensemble_throughput(F, torch, single_value: float, n: int = 96, steps: int = 1024, shape=None):
+def ensemble_throughput(F, torch, single_value: float, n: int = 96, steps: int = 5000, shape=None):
     """96 uneven scenarios (256^2 .. 2048^2, own terrain seed, n ~ U(0.02, 0.08),
     hydrograph peak ~ U(100, 1000) m^3/s), primed ~30 % wet, stepped together
     with the autotuned launch shape; Gcell-updates/s over all scenarios."""

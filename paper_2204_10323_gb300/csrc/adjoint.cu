@@ -524,29 +524,41 @@ struct AdjMaps {
 enum { kMh = 0, kMz, kMn, kMqx, kMqy, kMlh, kMlqx, kMlqy };
 constexpr int kAW = 40;
 // A tensor copy's shared-memory destination must be 128-byte aligned: every box
-// starts on its own 128-byte boundary.
+// starts on its own 128-byte boundary.  TB: rows of the tile.
+template <int TB>
 struct alignas(128) AdjStage {
-    alignas(128) float h[BY + 4][kAW];      // cells: rows J0-2 .., columns I0-4 ..
-    alignas(128) float z[BY + 4][kAW];
-    alignas(128) float n[BY + 4][kAW];
-    alignas(128) float qx[BY + 2][kAW];     // x-faces: rows J0-1 .., face columns I0-4 ..
-    alignas(128) float qy[BY + 3][kAW];     // y-faces: face rows J0-1 .., columns I0-4 ..
-    alignas(128) float lh[BY + 2][kAW];     // lambda_h': rows J0-1 .., columns I0-4 ..
-    alignas(128) float lqx[BY][kAW];        // lambda_qx': rows J0 .., face columns I0 ..
-    alignas(128) float lqy[BY + 1][BX];     // lambda_qy': face rows J0 .., columns I0 ..
+    alignas(128) float h[TB + 4][kAW];      // cells: rows J0-2 .., columns I0-4 ..
+    alignas(128) float z[TB + 4][kAW];
+    alignas(128) float n[TB + 4][kAW];
+    alignas(128) float qx[TB + 2][kAW];     // x-faces: rows J0-1 .., face columns I0-4 ..
+    alignas(128) float qy[TB + 3][kAW];     // y-faces: face rows J0-1 .., columns I0-4 ..
+    alignas(128) float lh[TB + 2][kAW];     // lambda_h': rows J0-1 .., columns I0-4 ..
+    alignas(128) float lqx[TB][kAW];        // lambda_qx': rows J0 .., face columns I0 ..
+    alignas(128) float lqy[TB + 1][BX];     // lambda_qy': face rows J0 .., columns I0 ..
     uint64_t bar;
 };
-static_assert(offsetof(AdjStage, z) % 128 == 0 && offsetof(AdjStage, n) % 128 == 0 &&
-                  offsetof(AdjStage, qx) % 128 == 0 && offsetof(AdjStage, qy) % 128 == 0 &&
-                  offsetof(AdjStage, lh) % 128 == 0 && offsetof(AdjStage, lqx) % 128 == 0 &&
-                  offsetof(AdjStage, lqy) % 128 == 0 && offsetof(AdjStage, bar) % 8 == 0,
-              "tensor-copy destinations must be 128-byte aligned");
+template <int TB>
+__host__ __device__ constexpr bool adj_stage_aligned()
+{
+    using S = AdjStage<TB>;
+    return offsetof(S, z) % 128 == 0 && offsetof(S, n) % 128 == 0 && offsetof(S, qx) % 128 == 0 &&
+           offsetof(S, qy) % 128 == 0 && offsetof(S, lh) % 128 == 0 && offsetof(S, lqx) % 128 == 0 &&
+           offsetof(S, lqy) % 128 == 0 && offsetof(S, bar) % 8 == 0;
+}
+static_assert(adj_stage_aligned<8>() && adj_stage_aligned<16>(), "tensor-copy destinations must be 128-byte aligned");
 // bytes the eight boxes deliver (the barrier's transaction count)
-constexpr uint32_t kAdjBytes = (uint32_t)sizeof(float) * (3 * (BY + 4) * kAW + (BY + 2) * kAW + (BY + 3) * kAW +
-                                                          (BY + 2) * kAW + BY * kAW + (BY + 1) * BX);
+template <int TB>
+__host__ __device__ constexpr uint32_t adj_bytes()
+{
+    return (uint32_t)sizeof(float) *
+           (3 * (TB + 4) * kAW + (TB + 2) * kAW + (TB + 3) * kAW + (TB + 2) * kAW + TB * kAW + (TB + 1) * BX);
+}
+// rows of the FP32 reverse step's tile, and its blocks per SM at 40 registers
+constexpr int kAdjTB = 8;
 constexpr uint64_t kAdjBudgetNs = 2000000000ull;
 
-__global__ void __launch_bounds__(BX * BY, 6) adj_step_tma_kernel(const AdjArgs<float> A, const int nbx,
+template <int TB>
+__global__ void __launch_bounds__(BX * TB, TB == 8 ? 6 : 3) adj_step_tma_kernel(const AdjArgs<float> A, const int nbx,
                                                                  const int n_tiles,
                                                                  const __grid_constant__ AdjMaps maps)
 {
@@ -558,12 +570,12 @@ __global__ void __launch_bounds__(BX * BY, 6) adj_step_tma_kernel(const AdjArgs<
         return;
     }
     const int tile = (int)blockIdx.x - n_sec;
-    __shared__ AdjStage S;
-    __shared__ T sX[BY + 2][BX + 3];   // new x-faces: rows J0-1 .., face columns I0-1 ..
-    __shared__ T sY[BY + 3][BX + 2];   // new y-faces: face rows J0-1 .., columns I0-1 ..
-    __shared__ T sL[BY + 2][BX + 2];   // cells I0-1 .., J0-1 ..
-    __shared__ T cXl[BY][BX + 1], cXr[BY][BX + 1], cXn[BY][BX + 1];
-    __shared__ T cYl[BY + 1][BX], cYr[BY + 1][BX], cYn[BY + 1][BX];
+    __shared__ AdjStage<TB> S;
+    __shared__ T sX[TB + 2][BX + 3];   // new x-faces: rows J0-1 .., face columns I0-1 ..
+    __shared__ T sY[TB + 3][BX + 2];   // new y-faces: face rows J0-1 .., columns I0-1 ..
+    __shared__ T sL[TB + 2][BX + 2];   // cells I0-1 .., J0-1 ..
+    __shared__ T cXl[TB][BX + 1], cXr[TB][BX + 1], cXn[TB][BX + 1];
+    __shared__ T cYl[TB + 1][BX], cYr[TB + 1][BX], cYn[TB + 1][BX];
     __shared__ int s_ng, s_gk[kTileGauges];
     const StepArgs<T> &a = A.fwd;
     const Geom &G = a.geo;
@@ -573,14 +585,14 @@ __global__ void __launch_bounds__(BX * BY, 6) adj_step_tma_kernel(const AdjArgs<
     const Fwd<T> F(G, dtd);
     const T dt = T(dtd), dx = T(G.dx), g = T(G.g), hd = T(G.h_dry), dtdx = dt / dx;
     const int tid = threadIdx.y * BX + threadIdx.x;
-    const int I0 = (tile % nbx) * BX, J0 = (tile / nbx) * BY;
+    const int I0 = (tile % nbx) * BX, J0 = (tile / nbx) * TB;
 
     // 0. the eight boxes onto one barrier; the gauge list is built meanwhile
     if (tid == 0) {
         mbar_init(&S.bar, 1);
         fence_mbar_init();
         s_ng = 0;
-        mbar_arrive_expect_tx(&S.bar, kAdjBytes);
+        mbar_arrive_expect_tx(&S.bar, adj_bytes<TB>());
         tma_load_2d(&S.h[0][0], &maps.m[kMh], I0 - 4, J0 - 2, &S.bar);
         tma_load_2d(&S.z[0][0], &maps.m[kMz], I0 - 4, J0 - 2, &S.bar);
         tma_load_2d(&S.n[0][0], &maps.m[kMn], I0 - 4, J0 - 2, &S.bar);
@@ -593,10 +605,10 @@ __global__ void __launch_bounds__(BX * BY, 6) adj_step_tma_kernel(const AdjArgs<
     __syncthreads();
     // B prelude: the gauges inside the tile and its halo, in gauge order (repeated
     // gauges add up in order); a tile holding more than kTileGauges scans them all
-    for (int gk = tid; gk < A.n_gauges; gk += BX * BY) {
+    for (int gk = tid; gk < A.n_gauges; gk += BX * TB) {
         const int64_t flat = A.gauge_cells[gk];
         const int gj = (int)(flat / nx), gi = (int)(flat - (int64_t)gj * nx);
-        if (gj >= J0 - 1 && gj <= J0 + BY && gi >= I0 - 1 && gi <= I0 + BX) {
+        if (gj >= J0 - 1 && gj <= J0 + TB && gi >= I0 - 1 && gi <= I0 + BX) {
             const int slot = atomicAdd(&s_ng, 1);
             if (slot < kTileGauges) s_gk[slot] = gk;
         }
@@ -619,7 +631,7 @@ __global__ void __launch_bounds__(BX * BY, 6) adj_step_tma_kernel(const AdjArgs<
     }
     // A. new face values.  x-face (lj, li): row J0-1+lj, face column fi = I0-1+li, between
     // cells at staged columns li+2 (L) and li+3 (R) of staged row lj+1.
-    for (int t = tid; t < (BY + 2) * (BX + 3); t += BX * BY) {
+    for (int t = tid; t < (TB + 2) * (BX + 3); t += BX * TB) {
         const int lj = t / (BX + 3), li = t % (BX + 3);
         const int j = J0 - 1 + lj, fi = I0 - 1 + li;
         T v = T(0);
@@ -635,7 +647,7 @@ __global__ void __launch_bounds__(BX * BY, 6) adj_step_tma_kernel(const AdjArgs<
     }
     // y-face (lj, li): face row fj = J0-1+lj, column i = I0-1+li, between cells of
     // staged rows lj (below) and lj+1 (above) at staged column li+3.
-    for (int t = tid; t < (BY + 3) * (BX + 2); t += BX * BY) {
+    for (int t = tid; t < (TB + 3) * (BX + 2); t += BX * TB) {
         const int lj = t / (BX + 2), li = t % (BX + 2);
         const int fj = J0 - 1 + lj, i = I0 - 1 + li;
         T v = T(0);
@@ -652,7 +664,7 @@ __global__ void __launch_bounds__(BX * BY, 6) adj_step_tma_kernel(const AdjArgs<
     __syncthreads();
     // B. adjoint of the unclipped depth (gauge seeds included)
     const int ng_tile = s_ng;
-    for (int t = tid; t < (BY + 2) * (BX + 2); t += BX * BY) {
+    for (int t = tid; t < (TB + 2) * (BX + 2); t += BX * TB) {
         const int lj = t / (BX + 2), li = t % (BX + 2);
         const int j = J0 - 1 + lj, i = I0 - 1 + li;
         T v = T(0);
@@ -677,7 +689,7 @@ __global__ void __launch_bounds__(BX * BY, 6) adj_step_tma_kernel(const AdjArgs<
     __syncthreads();
     // C. each face touching the tile once.  x-face (lj, li): row J0+lj, face column
     // fi = I0+li; cells at staged columns li+3 (L) and li+4 (R) of staged row lj+2.
-    for (int t = tid; t < BY * (BX + 1); t += BX * BY) {
+    for (int t = tid; t < TB * (BX + 1); t += BX * TB) {
         const int lj = t / (BX + 1), li = t % (BX + 1);
         const int j = J0 + lj, fi = I0 + li;
         T cl = T(0), cr = T(0), cn = T(0);
@@ -715,7 +727,7 @@ __global__ void __launch_bounds__(BX * BY, 6) adj_step_tma_kernel(const AdjArgs<
     }
     // y-face (lj, li): face row fj = J0+lj, column i = I0+li; cells of staged rows
     // lj+1 (below) and lj+2 (above) at staged column li+4.
-    for (int t = tid; t < (BY + 1) * BX; t += BX * BY) {
+    for (int t = tid; t < (TB + 1) * BX; t += BX * TB) {
         const int lj = t / BX, li = t % BX;
         const int fj = J0 + lj, i = I0 + li;
         T cl = T(0), cr = T(0), cn = T(0);
@@ -745,7 +757,7 @@ __global__ void __launch_bounds__(BX * BY, 6) adj_step_tma_kernel(const AdjArgs<
                     cn = mu * d.dn;
                     lq = mu * d.dq;
                 }
-                if (lj < BY) A.lqy_out[c] = lq;             // the tile owns the south faces of its cells
+                if (lj < TB) A.lqy_out[c] = lq;             // the tile owns the south faces of its cells
             }
         }
         cYl[lj][li] = cl;
@@ -1133,21 +1145,22 @@ cudaError_t launch_adjoint_step(const AdjArgs<T> &A, cudaStream_t st)
         const int P = G.pitch, nx = G.nx, ny = G.ny;
         const StepArgs<float> &f = A.fwd;
         AdjMaps maps;
+        constexpr int TB = kAdjTB;
         const struct {
             const float *base;
             int w, h, bw, bh;
-        } fields[8] = {{f.h, nx, ny, kAW, BY + 4},          {f.z, nx, ny, kAW, BY + 4},
-                       {f.n, nx, ny, kAW, BY + 4},          {f.qx, nx + 1, ny, kAW, BY + 2},
-                       {f.qy, nx, ny + 1, kAW, BY + 3},     {A.lh, nx, ny, kAW, BY + 2},
-                       {A.lqx, nx + 1, ny, kAW, BY},        {A.lqy, nx, ny + 1, BX, BY + 1}};
+        } fields[8] = {{f.h, nx, ny, kAW, TB + 4},          {f.z, nx, ny, kAW, TB + 4},
+                       {f.n, nx, ny, kAW, TB + 4},          {f.qx, nx + 1, ny, kAW, TB + 2},
+                       {f.qy, nx, ny + 1, kAW, TB + 3},     {A.lh, nx, ny, kAW, TB + 2},
+                       {A.lqx, nx + 1, ny, kAW, TB},        {A.lqy, nx, ny + 1, BX, TB + 1}};
         for (int k = 0; k < 8; k++) {
             const cudaError_t e = encode_map_f32(&maps.m[k], fields[k].base, fields[k].w, fields[k].h, P,
                                                  fields[k].bw, fields[k].bh);
             if (e != cudaSuccess) return e;
         }
-        const int nbx = (nx + BX - 1) / BX, nby = (ny + BY - 1) / BY;
+        const int nbx = (nx + BX - 1) / BX, nby = (ny + TB - 1) / TB;
         const int n_tiles = nbx * nby, n_sec = A.gn_in ? A.fwd.n_inflow_sec : 0;
-        adj_step_tma_kernel<<<(unsigned)(n_tiles + n_sec), dim3(BX, BY), 0, st>>>(A, nbx, n_tiles, maps);
+        adj_step_tma_kernel<TB><<<(unsigned)(n_tiles + n_sec), dim3(BX, TB), 0, st>>>(A, nbx, n_tiles, maps);
         e0 = cudaGetLastError();
         if (e0 != cudaSuccess || n_sec > 0) return e0;   // pass 3 ran in the same launch
         if (A.fwd.n_inflow_sec > 0) adj_inflow_kernel<T><<<A.fwd.n_inflow_sec, 256, 0, st>>>(A);

@@ -100,6 +100,7 @@ struct Sweep {
     int G = 0;
     const double *seed = nullptr;    // device, N x G
     int64_t fwd_steps = 0;
+    int64_t prof_fwd_steps = 0;      // forward steps inside the profiled launches
 };
 
 flood_status copy_planes(flood_handle *h, const Planes &dst, const Planes &src, size_t plane, size_t plane_y)
@@ -178,9 +179,21 @@ flood_status ensure_epoch(Sweep &S, int64_t e)
 
 bool same(const Planes &a, const Planes &b) { return a.h == b.h; }
 
-// One forward replay step from S.src into `dst` (a free slot: a checkpoint
-// being taken) or else into the work buffer that S.src is not.
-flood_status forward_step(Sweep &S, const Planes *dst = nullptr)
+// Steps the next replay launch may take towards `step`: up to 4 for FP32 grids
+// running Eq. 3 as printed (their temporal-blocking kernel gives the single steps'
+// bits), never past the end of the epoch; one otherwise.
+int replay_steps(const Sweep &S, int64_t step)
+{
+    const flood_handle *h = S.h;
+    if (h->prec != FLOOD_F32 || h->geo.theta != 1.0 || h->geo.friction != 0) return 1;
+    const int s = (int)((S.g0 + S.work_step) % S.E);
+    return (int)std::min<int64_t>(std::min<int64_t>(step - S.work_step, 4), S.E - s);
+}
+
+// One forward replay launch of k steps (replay_steps) from S.src into `dst` (a
+// free slot: a checkpoint being taken) or else into the work buffer that S.src
+// is not.
+flood_status forward_step(Sweep &S, const Planes *dst = nullptr, int k = 1)
 {
     flood_handle *h = S.h;
     const int64_t g = S.g0 + S.work_step;
@@ -192,12 +205,13 @@ flood_status forward_step(Sweep &S, const Planes *dst = nullptr)
     const Planes out = dst ? *dst : same(S.src, S.work[0]) ? S.work[1] : S.work[0];
     const void *in[3] = {S.src.h, S.src.qx, S.src.qy};
     void *o[3] = {out.h, out.qx, out.qy};
-    if (S.profile) st = timed(S, S.ev_fwd, [&] { return launch_step_planes(h, s, in, o); });
-    else st = launch_step_planes(h, s, in, o);
+    if (S.profile) st = timed(S, S.ev_fwd, [&] { return launch_step_planes(h, s, k, in, o); });
+    else st = launch_step_planes(h, s, k, in, o);
     if (st) return st;
     S.src = out;
-    S.work_step += 1;
-    S.fwd_steps += 1;
+    S.work_step += k;
+    S.fwd_steps += k;
+    if (S.profile) S.prof_fwd_steps += k;
     return FLOOD_OK;
 }
 
@@ -214,7 +228,9 @@ flood_status restore(Sweep &S, int slot, int64_t step)
 flood_status advance_to(Sweep &S, int64_t step, const Planes *last_dst = nullptr)
 {
     while (S.work_step < step) {
-        flood_status st = forward_step(S, S.work_step + 1 == step ? last_dst : nullptr);
+        // the launch that ends at `step` writes into last_dst
+        const int k = replay_steps(S, step);
+        flood_status st = forward_step(S, S.work_step + k == step ? last_dst : nullptr, k);
         if (st) return st;
     }
     return FLOOD_OK;
@@ -530,7 +546,7 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     if (S.profile) {
         CKF(cudaStreamSynchronize(h->stream));
         h->adj_prof_rev_steps = (int64_t)S.ev_rev.size() / 2;
-        h->adj_prof_fwd_steps = (int64_t)S.ev_fwd.size() / 2;
+        h->adj_prof_fwd_steps = S.prof_fwd_steps;
         h->adj_prof_rev_ms = sum_pairs(S.ev_rev);
         h->adj_prof_fwd_ms = sum_pairs(S.ev_fwd);
     }

@@ -301,17 +301,23 @@ static void set_planes(StepArgs<T> &a, const void *const in[3], void *const out[
     a.qy_out = (T *)out[2];
 }
 
-flood_status launch_step_planes(flood_handle *h, int s, const void *const in[3], void *const out[3])
+flood_status launch_step_planes(flood_handle *h, int s, int k, const void *const in[3], void *const out[3])
 {
     cudaError_t e;
     if (h->prec == FLOOD_F64) {
+        if (k != 1) return fail(h, FLOOD_ERR_ARG, "FP64 planes advance one step per launch");
         StepArgs<double> a = make_args<double>(h, s, 1, 0, nullptr, 0, nullptr);
         set_planes(a, in, out);
         e = launch_step_reference<double>(a, h->stream);
     } else {
-        StepArgs<float> a = make_args<float>(h, s, 1, 0, nullptr, 0, nullptr);
+        StepArgs<float> a = make_args<float>(h, s, k, 0, nullptr, 0, nullptr);
         set_planes(a, in, out);
-        e = launch_f32(h, a);
+        if (k > 1) {                       // several steps: the temporal-blocking kernel (bitwise the single steps)
+            a.tile_x = a.tile_y = 0;
+            e = launch_step_tiled(a, h->stream);
+        } else {
+            e = launch_f32(h, a);
+        }
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
     return FLOOD_OK;

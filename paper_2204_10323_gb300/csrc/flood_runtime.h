@@ -127,7 +127,9 @@ flood_status launch_steps(flood_handle *h, int s, int k, int want_hmax, const in
 // One step at step-in-epoch s reading the state planes in[] = {h, qx, qy} and
 // writing out[] (pitched like the handle's state; the handle's own buffers and
 // its current index are not touched).
-flood_status launch_step_planes(flood_handle *h, int s, const void *const in[3], void *const out[3]);
+// k steps (k > 1: FP32, Eq. 3 as printed, at most 4 and within the epoch) from the planes `in`
+// into the planes `out`, starting at step-in-epoch s.
+flood_status launch_step_planes(flood_handle *h, int s, int k, const void *const in[3], void *const out[3]);
 flood_status advance(flood_handle *h, int64_t n, const int64_t *gcells, int ng, double *gbuf,
                      const double *fixed_dt_log, bool epoch_open = false);
 flood_status check_device_status(flood_handle *h);
