@@ -39,15 +39,15 @@ BYTES_PER_CELL = 32          # read h, qx, qy, z, n (20 B) + write h, qx, qy (12
 # key (kernel, steps per launch); the stream kernel captured in the 16384^2
 # launch shape (4 warps x 32-row chunks).  Only kernels whose code has not
 # changed since their capture are listed; the others report traffic null.
-TRAFFIC_B_PER_CELL = {("stream", 1): 31.31, ("tiled", 4): 31.15}
+TRAFFIC_B_PER_CELL = {("stream", 1): 31.32, ("tiled", 4): 31.18}
 # Warp instructions per cell-update of the temporal-blocking kernel (issue-bound), from the same 4096^2
 # capture (smsp__inst_executed.sum): the "alu" roofline beside the one-step HBM one.  The issue peak is
 # 152 SMs x 4 warp-instructions per cycle x the sampled SM clock.
-INST_PER_CELL_UPDATE = {("tiled", 4): 241634294 / (4096 * 4096 * 4)}
+INST_PER_CELL_UPDATE = {("tiled", 4): 238696226 / (4096 * 4096 * 4)}
 SMS, ISSUE_PER_SM_CYCLE = 152, 4
 # the same two for the vector-norm friction option (theta = 1)
 TRAFFIC_VEC_B_PER_CELL = {("tiled", 4): 30.99}
-INST_VEC_PER_CELL_UPDATE = {("tiled", 4): 289921697 / (4096 * 4096 * 4)}
+INST_VEC_PER_CELL_UPDATE = {("tiled", 4): 287579757 / (4096 * 4096 * 4)}
 METRIC = "Gcell-updates/s and % of HBM roofline (FP32, 1 GB300); adjoint/forward time ratio"
 UNIT = "Gcell-updates/s"
 
