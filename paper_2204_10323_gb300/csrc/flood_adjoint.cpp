@@ -404,7 +404,7 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(h, FLOOD_ERR_CUDA, "cudaMemGetInfo");
         want = std::max<int64_t>(1, (int64_t)(free_b / 2 / (2 * S.plane + S.plane_y)));
     }
-    const int C = (int)std::min<int64_t>(want, n_steps);
+    int C = (int)std::min<int64_t>(want, n_steps);
     std::vector<void *> mine;
     auto alloc = [&](size_t bytes) {
         void *p = dev_alloc(h, bytes);
@@ -415,15 +415,20 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
         for (void *p : mine) dev_free(h, p);
         mine.clear();
     };
-    // the snapshots in one allocation (planes are multiples of 128 bytes)
-    S.slots.resize(C);
+    // the snapshots in one allocation (planes are multiples of 128 bytes); a count
+    // sized by the free memory is halved until the allocation succeeds
     {
         const size_t slot = 2 * S.plane + S.plane_y;
         char *block = (char *)alloc((size_t)C * slot);
+        while (!block && n_checkpoints == 0 && C > 1) {
+            C /= 2;
+            block = (char *)alloc((size_t)C * slot);
+        }
         if (!block) {
             release();
             return fail(h, FLOOD_ERR_OOM, "checkpoint allocation");
         }
+        S.slots.resize(C);
         for (int c = 0; c < C; c++) {
             S.slots[c].h = block + (size_t)c * slot;
             S.slots[c].qx = block + (size_t)c * slot + S.plane;
