@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import inputs
-from inputs import INFLOW, OUTFLOW, XMAX, XMIN, YMAX, Options, Problem, Section
+from inputs import INFLOW, OUTFLOW, XMAX, XMIN, YMAX, YMIN, Options, Problem, Section
 import oracle
 
 pytestmark = pytest.mark.gpu
@@ -193,6 +193,36 @@ def test_fp32_adjoint_close_to_fp64_oracle():
     big = np.abs(gn_o) > 1e-2 * np.abs(gn_o).max()
     rel = np.abs(gn[big] - gn_o[big]) / np.abs(gn_o[big])
     assert np.median(rel) < 1e-3 and rel.max() < 1e-2
+
+
+def test_fp32_adjoint_two_inflow_sections_sharing_a_corner():
+    # two inflow sections meeting at cell (0, 0) (its west and its south face) on a
+    # grid of 3 x 6 reverse-step tiles: the FP32 step's inflow blocks, one per section,
+    # run beside the tiles, and their per-cell terms (the corner cell twice) join dL/dn
+    # after the sweep; against the FP64 oracle's reverse sweep
+    Fm = F()
+    base = wet_case(nx=70, ny=45, seed=11)
+    nx, ny = base.nx, base.ny
+    secs = [Section.cells(XMIN, 0, 9, INFLOW, 2e-3, nx, ny, [0.0, 30.0], [1.0, 3.0]),
+            Section.cells(YMIN, 0, 12, INFLOW, 2e-3, nx, ny, [0.0, 30.0], [2.0, 0.5]),
+            Section.cells(XMAX, 0, ny, OUTFLOW, 2e-3, nx, ny)]
+    r32 = lambda a: a.astype(np.float32).astype(np.float64)
+    p = Problem("two_inflows", nx, ny, base.dx, r32(base.z), r32(base.n), secs, base.opts, h0=r32(base.h0),
+                qx0=base.qx0, qy0=base.qy0)
+    gauges = np.array([[1, 1], [0, 5], [6, 0], [30, 20], [69, 44], [3, 2]])
+    steps = 32
+    w = np.random.default_rng(12).standard_normal((steps, len(gauges)))
+    gn_o = oracle.Oracle(p).adjoint(steps, gauges, w)
+    gn = Fm.Sim(p, precision=Fm.F32).adjoint(steps, gauges, w, n_checkpoints=5).astype(np.float64)
+    cos = float(np.sum(gn * gn_o) / (np.linalg.norm(gn) * np.linalg.norm(gn_o)))
+    assert cos > 0.999
+    sec = np.zeros((ny, nx), bool)
+    sec[:9, 0] = True
+    sec[0, :12] = True
+    big = sec & (np.abs(gn_o) > 1e-3 * np.abs(gn_o).max())
+    assert big.sum() >= 10
+    rel = np.abs(gn[big] - gn_o[big]) / np.abs(gn_o[big])
+    assert np.median(rel) < 1e-3 and rel.max() < 2e-2
 
 
 def test_fp64_directional_derivative_matches_central_difference():
