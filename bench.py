@@ -43,7 +43,7 @@ TRAFFIC_B_PER_CELL = {("stream", 1): 31.32, ("tiled", 4): 31.18}
 # Warp instructions per cell-update of the temporal-blocking kernel (issue-bound), from the same 4096^2
 # capture (smsp__inst_executed.sum): the "alu" roofline beside the one-step HBM one.  The issue peak is
 # 152 SMs x 4 warp-instructions per cycle x the sampled SM clock.
-INST_PER_CELL_UPDATE = {("tiled", 4): 238696226 / (4096 * 4096 * 4)}
+INST_PER_CELL_UPDATE = {("tiled", 4): 235497890 / (4096 * 4096 * 4)}
 SMS, ISSUE_PER_SM_CYCLE = 152, 4
 # the same two for the vector-norm friction option (theta = 1)
 TRAFFIC_VEC_B_PER_CELL = {("tiled", 4): 30.99}

@@ -55,10 +55,11 @@ static_assert(out_cols(4, 1) == 116 && out_cols(8, 1) == 108 && out_cols(4, 2) =
 static_assert(out_cols(1, 1) % 4 == 0 && out_cols(2, 1) % 4 == 0 && out_cols(3, 1) % 4 == 0 && out_cols(4, 1) % 4 == 0 &&
                   out_cols(8, 1) % 4 == 0 && halo_cols(4) % 4 == 0 && halo_cols(8) % 4 == 0,
               "strip origins must stay multiples of 4 columns");
-// level-1 rows in flight, for one grid and for the ensemble kernel: with 4 rows
-// in flight six pipelines of 4 warps fit the registers and shared memory of an SM
-// (tiled_min_blocks; the ensemble kernel's launch bounds)
-constexpr int kPF1 = 4, kPFE = 4;
+// level-1 rows in flight, for one grid and for the ensemble kernel; six pipelines
+// of 4 warps fit the registers and shared memory of an SM with either (tiled_min_blocks;
+// the ensemble kernel's launch bounds).  One grid: 6 rows (3 and 6 measured alike, and
+// 0.8 % faster than 4, which left 4 bytes of spill)
+constexpr int kPF1 = 6, kPFE = 4;
 constexpr uint64_t kBudgetNs = 2000000000ull;
 
 constexpr int pow2_ceil(int v)
