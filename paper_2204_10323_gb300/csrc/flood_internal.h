@@ -28,7 +28,7 @@ struct Ctrl {
     double cfl_exceed;            // epochs whose dt broke dx / sqrt(g h_max) at their end
     unsigned long long hmax_bits; // running max of h (bits of a non-negative double)
     int status;                   // kStatus* bits
-    int pad;
+    int next_item;                // the temporal-blocking kernel's work-item counter (zeroed before each launch)
 };
 
 // One inflow section as seen by the Eq. 6 solver.

@@ -43,6 +43,32 @@ void tiled_split(int n_strips, int ny, int resident, int K, int *chunk_rows, int
     *blocks = (int)(items < resident ? items : resident);
 }
 
+// The same when the pipelines take their items from a counter as they come free:
+// about eight items per pipeline, so that the ones that finish early take more
+// and the launch ends evenly, of at least 24 K rows (an item costs its rows plus
+// the 3K - 1 ticks of filling the pipeline); a grid that would get fewer than four
+// such items per pipeline keeps the round-robin split.  Measured against fixed
+// rows per item of 64 ... 384 on the fractal workload at 16384^2 (304 rows: 8
+// items per pipeline) and 8192^2 (96 rows: 6.5), and against the round-robin
+// split at 4096^2 and 2048^2.
+void tiled_split_dynamic(int n_strips, int ny, int resident, int K, int *chunk_rows, int *blocks)
+{
+    const long long target = 8LL * resident;
+    const long long chunks = (target + n_strips - 1) / n_strips;
+    int rows = (int)((ny + chunks - 1) / chunks);
+    const int min_rows = 24 * K;
+    if (rows < min_rows) {
+        rows = min_rows;
+        if ((long long)n_strips * ((ny + rows - 1) / rows) < 4LL * resident) {
+            tiled_split(n_strips, ny, resident, K, chunk_rows, blocks);
+            return;
+        }
+    }
+    const long long items = (long long)n_strips * ((ny + rows - 1) / rows);
+    *chunk_rows = rows;
+    *blocks = (int)(items < resident ? items : resident);
+}
+
 int tiled_items(const Geom &g, int chunk_rows, int k_steps)
 {
     const int mode = (g.theta != 1.0 ? 1 : 0) | (g.friction != 0 ? 2 : 0);

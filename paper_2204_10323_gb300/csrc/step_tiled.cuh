@@ -32,8 +32,10 @@
 
 namespace flood {
 
-// Rows per (chunk, strip) work item and the number of pipelines for a grid (step_tiled.cu).
+// Rows per (chunk, strip) work item and the number of pipelines for a grid (step_tiled.cu):
+// for items handed out round-robin, and for items taken from a counter.
 void tiled_split(int n_strips, int ny, int resident, int K, int *chunk_rows, int *blocks);
+void tiled_split_dynamic(int n_strips, int ny, int resident, int K, int *chunk_rows, int *blocks);
 
 namespace {
 
@@ -591,8 +593,9 @@ __device__ __forceinline__ void init_ring(PipeSmem<K, kPF, kHo> &sm)
     __syncthreads();
 }
 
-// One grid: work items (chunk, strip) in chunk-major order, block b takes
-// items b, b + grid, ... (a.tile_x strips, a.tile_y rows per chunk).
+// One grid: work items (chunk, strip) in chunk-major order (a.tile_x strips,
+// a.tile_y rows per chunk); block b takes item b first and then the next item
+// of the launch's counter (a.ctrl->next_item) whenever it comes free.
 // Pipelines per SM the launch bounds ask for: six for Eq. 3 as printed with
 // K = 4 (80 registers), five with the scheme options' extra row state.
 __host__ __device__ constexpr int tiled_min_blocks(int K, int mode) { return K == 4 ? (mode ? 5 : 6) : K == 8 ? 2 : 1; }
@@ -610,11 +613,16 @@ __global__ void __launch_bounds__(K * 32, tiled_min_blocks(K, kMode)) step_tiled
     const FastConst Kc = tiled_const(a);
     TiledLedger L;
     uint32_t base = 0;
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    __shared__ int next;
+    for (int item = blockIdx.x; item < n_items;) {
         const int strip = item % n_strips;
         const int y0 = (item / n_strips) * chunk_rows;
         const int y1 = min(y0 + chunk_rows, a.geo.ny);
         if (tiled_item<K, kPF1, kMode>(a, a.s, Kc, strip, y0, y1, sm, base, L)) break;
+        if (threadIdx.x == 0) next = (int)gridDim.x + atomicAdd(&a.ctrl->next_item, 1);
+        __syncthreads();
+        item = next;
+        __syncthreads();                              // read by every thread before thread 0 writes it again
     }
     tiled_flush<K>(a, L, a.want_hmax, red, sm.led);
     if (blockIdx.x == 0 && threadIdx.x == 0) tiled_finish<K>(a, a.s);
@@ -709,10 +717,12 @@ cudaError_t launch_k(const StepArgs<float> &a0, cudaStream_t st)
         const long long items = (long long)n_strips * ((ny + chunk_rows - 1) / chunk_rows);
         blocks = (int)(items < resident ? items : resident);
     } else {
-        tiled_split(n_strips, ny, resident, K, &chunk_rows, &blocks);
+        tiled_split_dynamic(n_strips, ny, resident, K, &chunk_rows, &blocks);
     }
     a.tile_x = n_strips;
     a.tile_y = chunk_rows;
+    e = cudaMemsetAsync(&a.ctrl->next_item, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
     step_tiled_kernel<K, kMode><<<blocks, K * 32, sizeof(Smem), st>>>(a);
     return cudaGetLastError();
 }
