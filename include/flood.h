@@ -94,8 +94,8 @@ typedef struct {
 
 /* Kernel families for the forward step (FLOOD_F32; FLOOD_F64 always uses REFERENCE). */
 typedef enum {
-    FLOOD_KERNEL_AUTO = 0,       /* TILED (K = 4) for Eq. 3 as printed with E a multiple of 4 and no launch
-                                    shape given; else TMA below 2^27 cells or with vector-norm friction,
+    FLOOD_KERNEL_AUTO = 0,       /* TILED (K = 4) with E a multiple of 4 and no launch shape given (Eq. 3
+                                    as printed and the scheme options alike); else TMA below 2^27 cells,
                                     else STREAM */
     FLOOD_KERNEL_REFERENCE = 1,  /* one thread per cell, IEEE ops in the oracle's order */
     FLOOD_KERNEL_ROWS = 2,       /* one warp per 128-column strip, float4 row streaming */
@@ -124,12 +124,12 @@ typedef struct {
                                     the numerator discharge of a face is theta q + (1 - theta)/2 times the
                                     sum of its two neighbours along the same axis (the theta scheme of
                                     de Almeida et al. 2012, cited in Methods); friction keeps |q| of the
-                                    face.  theta != 1: kernels REFERENCE, STREAM, TMA (AUTO), TILED and
+                                    face.  theta != 1: kernels REFERENCE, STREAM, TMA, TILED (AUTO) and
                                     FP64, ensembles, the adjoint; not ROWS (FLOOD_ERR_UNSUPPORTED) */
     int32_t friction;            /* |q| in the friction term of Eq. 3.  0 (default): the face's own discharge
                                     component (the axis-by-axis integration of Methods).  1: the vector norm
                                     sqrt(q^2 + qo^2), qo the mean of the four faces of the other axis around
-                                    the face.  1: kernels REFERENCE, STREAM, TMA (AUTO), TILED and FP64,
+                                    the face.  1: kernels REFERENCE, STREAM, TMA, TILED (AUTO) and FP64,
                                     ensembles, the adjoint; not ROWS (FLOOD_ERR_UNSUPPORTED); other values
                                     FLOOD_ERR_ARG */
 } flood_opts;

@@ -443,20 +443,20 @@ static int check_finite_host(const void *a, size_t n, int prec)
 
 namespace flood {
 
-// AUTO: the temporal-blocking kernel with K = 4 where it applies (Eq. 3 as
-// printed, E a multiple of 4, no explicit launch shape), else the tensor-tile
-// kernel below 2^27 cells or with vector-norm friction (whose next-row
-// look-ahead two-row tiles serve half of the time), else the row-staged stream
-// kernel.  Measured on the fractal workload (us per step): tiled K = 4 / TMA /
-// stream 15.2 / 16.5 / 16.7 at 1024^2, 31.1 / 33.9 / 37.5 at 2048^2, 92.6 /
-// 102.3 / 105.5 at 4096^2, 339 / 348 / 350 at 8192^2, 1181 / 1301 / 1288 at
-// 16384^2; with vector friction TMA / stream 1455 / 1629 at 16384^2.  All
-// three are bitwise equal.
+// AUTO: the temporal-blocking kernel with K = 4 where it applies (E a multiple
+// of 4, no explicit launch shape), for Eq. 3 as printed and for the scheme
+// options alike, else the tensor-tile kernel below 2^27 cells, else the
+// row-staged stream kernel.  Measured on the fractal workload (us per step,
+// epoch starts included): tiled K = 4 / TMA / stream 15.2 / 16.4 / 18.2 at
+// 1024^2, 29.9 / 33.9 / 39.3 at 2048^2, 89.2 / 102.0 / 105.9 at 4096^2,
+// 296 / 349 / 354 at 8192^2, 1059 / 1305 / 1302 at 16384^2; with vector-norm
+// friction tiled / TMA 16.6 / 18.3, 36.1 / 41.0, 116.4 / 119.2, 385 / 381 and
+// 1396 / 1425.  All of them are bitwise equal.
 int auto_kernel(const flood_opts &o, int nx, int ny)
 {
-    const bool tiled = o.theta == 1.0 && o.friction == 0 && o.epoch_steps % 4 == 0 && o.tile_x == 0 && o.tile_y == 0;
+    const bool tiled = o.epoch_steps % 4 == 0 && o.tile_x == 0 && o.tile_y == 0;
     if (tiled) return FLOOD_KERNEL_TILED;
-    return (o.friction != 0 || (int64_t)nx * ny < ((int64_t)1 << 27)) ? FLOOD_KERNEL_TMA : FLOOD_KERNEL_STREAM;
+    return (int64_t)nx * ny < ((int64_t)1 << 27) ? FLOOD_KERNEL_TMA : FLOOD_KERNEL_STREAM;
 }
 
 flood_status refresh_hmax_window(flood_handle *h)
