@@ -34,20 +34,22 @@ sys.path.insert(0, ROOT)
 
 BYTES_PER_CELL = 32          # read h, qx, qy, z, n (20 B) + write h, qx, qy (12 B), FP32
 # DRAM bytes read + written per cell by one launch of a kernel on the 16384^2
-# workload: one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
-# the 4096^2 case of the same workload (state > L2), scaled by the cell count;
-# key (kernel, steps per launch); the stream kernel captured in the 16384^2
-# launch shape (4 warps x 32-row chunks).  Only kernels whose code has not
-# changed since their capture are listed; the others report traffic null.
-TRAFFIC_B_PER_CELL = {("stream", 1): 31.32, ("tiled", 4): 31.18}
-# Warp instructions per cell-update of the temporal-blocking kernel (issue-bound), from the same 4096^2
+# workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# smaller case of the same workload (state > L2) in the same launch shape, scaled by
+# the cell count; key (kernel, steps per launch).  Stream kernel: the 4096^2 case in
+# the 4 warps x 32-row chunks of the 16384^2 launch.  Temporal-blocking kernel: the
+# 8192^2 case with the 304-row (chunk, strip) items the 16384^2 launch takes from its
+# counter (--tile 0,304).  Only kernels whose code has not changed since their capture
+# are listed; the others report traffic null.
+TRAFFIC_B_PER_CELL = {("stream", 1): 31.32, ("tiled", 4): 32.29}
+# Warp instructions per cell-update of the temporal-blocking kernel (issue-bound), from the same
 # capture (smsp__inst_executed.sum): the "alu" roofline beside the one-step HBM one.  The issue peak is
 # 152 SMs x 4 warp-instructions per cycle x the sampled SM clock.
-INST_PER_CELL_UPDATE = {("tiled", 4): 235497890 / (4096 * 4096 * 4)}
+INST_PER_CELL_UPDATE = {("tiled", 4): 907034250 / (8192 * 8192 * 4)}
 SMS, ISSUE_PER_SM_CYCLE = 152, 4
 # the same two for the vector-norm friction option (theta = 1)
-TRAFFIC_VEC_B_PER_CELL = {("tiled", 4): 30.99}
-INST_VEC_PER_CELL_UPDATE = {("tiled", 4): 287579757 / (4096 * 4096 * 4)}
+TRAFFIC_VEC_B_PER_CELL = {("tiled", 4): 32.27}
+INST_VEC_PER_CELL_UPDATE = {("tiled", 4): 1117140607 / (8192 * 8192 * 4)}
 METRIC = "Gcell-updates/s and % of HBM roofline (FP32, 1 GB300); adjoint/forward time ratio"
 UNIT = "Gcell-updates/s"
 
