@@ -570,7 +570,7 @@ def ensemble_throughput(F, torch, single_value: float, n: int = 96, steps: int =
 
 def decomposition_leg(F, torch, prob, single_value: float, steps: int, parts=(2, 4), halo: int = 4):
     """The same workload split into 1 x N row strips with `halo`-row halos,
-    exchanged every `halo` steps (all parts on this GPU, one stream): whole-job
+    exchanged every `halo` steps (all parts on this GPU, each on a stream of its own): whole-job
     Gcell-updates/s and the ratio to the single grid, the cost of the halo rows'
     redundant steps, the exchanges and the per-part launches."""
     out = []

@@ -9,10 +9,12 @@
 // cell), so after `halo` steps the strip's own rows -- and the face row on
 // either side of them -- are still bit for bit what the whole grid computes.
 // Then the halo rows are copied in again from the neighbours' own rows.  Here
-// all strips live on one GPU and the copies are device-to-device copies on
-// the strips' shared stream; the copy list (flood_decomp_plan) names source
-// and destination rows only, so a transport between GPUs would carry the
-// same list (each row into the receiving GPU's own memory).
+// all strips live on one GPU, each stepping on a stream of its own (as each
+// would on its own GPU); the copies are device-to-device copies on the
+// decomposition's stream, between two joins of the strips' streams.  The copy
+// list (flood_decomp_plan) names source and destination rows only, so a
+// transport between GPUs would carry the same list (each row into the
+// receiving GPU's own memory).
 //
 // Ledger: a strip books the clipped volume and outflow of its own rows only
 // (Geom::led_j0/led_j1 and the halo outflow type), part 0 alone books the
@@ -38,7 +40,10 @@ struct flood_decomp {
     int n_parts = 0, halo = 1;
     int nx = 0, ny = 0, prec = 0, E = 16;
     size_t esz = 4;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;           // the caller's: exchanges, h_max reduction, reads
+    std::vector<cudaStream_t> lanes;         // one per part: the part's own work
+    std::vector<cudaEvent_t> lane_ev;        // one per part
+    cudaEvent_t main_ev = nullptr;
     std::vector<flood_handle *> parts;
     std::vector<int32_t> rows;               // 4 per part: y0, y1, a, b
     std::vector<flood_halo_copy> copies;
@@ -87,7 +92,26 @@ void *field_plane(flood_handle *h, int field)
     }
 }
 
-// Refresh every part's halo rows from its neighbours' own rows.
+// The decomposition's stream waits for every part's stream.
+flood_status join_lanes(flood_decomp *d)
+{
+    for (int r = 0; r < d->n_parts; r++) {
+        DCK(cudaEventRecord(d->lane_ev[r], d->lanes[r]));
+        DCK(cudaStreamWaitEvent(d->stream, d->lane_ev[r], 0));
+    }
+    return FLOOD_OK;
+}
+
+// Every part's stream waits for the decomposition's stream.
+flood_status fork_lanes(flood_decomp *d)
+{
+    DCK(cudaEventRecord(d->main_ev, d->stream));
+    for (int r = 0; r < d->n_parts; r++) DCK(cudaStreamWaitEvent(d->lanes[r], d->main_ev, 0));
+    return FLOOD_OK;
+}
+
+// Refresh every part's halo rows from its neighbours' own rows (on the
+// decomposition's stream, the parts' streams joined into it).
 flood_status exchange(flood_decomp *d)
 {
     NvtxRange range("flood: halo exchange");
@@ -200,6 +224,19 @@ extern "C" flood_status flood_decomp_create(const flood_grid *grid, const void *
         d->parts.push_back(h);
     }
     d->stream = d->parts[0]->stream;
+    // a stream per part: the parts step side by side, as on separate GPUs
+    d->lanes.assign(n_parts, nullptr);
+    d->lane_ev.assign(n_parts, nullptr);
+    if (cudaEventCreateWithFlags(&d->main_ev, cudaEventDisableTiming) != cudaSuccess)
+        return bail(FLOOD_ERR_CUDA, "event creation");
+    for (int r = 0; r < n_parts; r++) {
+        if (cudaStreamCreateWithFlags(&d->lanes[r], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&d->lane_ev[r], cudaEventDisableTiming) != cudaSuccess)
+            return bail(FLOOD_ERR_CUDA, "stream creation");
+    }
+    // the parts' set-up on the caller's stream is done before their own streams start
+    if (cudaStreamSynchronize(d->stream) != cudaSuccess) return bail(FLOOD_ERR_CUDA, "part set-up");
+    for (int r = 0; r < n_parts; r++) d->parts[r]->stream = d->lanes[r];
     d->ctrls_dev = (Ctrl **)raw_device_alloc(n_parts * sizeof(Ctrl *), d->stream);
     if (!d->ctrls_dev) return bail(FLOOD_ERR_OOM, "device allocation failed");
     std::vector<Ctrl *> ctrls(n_parts);
@@ -219,21 +256,30 @@ extern "C" flood_status flood_decomp_step(flood_decomp *d, int64_t n_steps)
     NvtxRange range("flood: decomposed steps");
     const int E = d->E;
     int64_t done = 0;
+    {
+        flood_status st = fork_lanes(d);      // whatever the caller queued comes first
+        if (st) return st;
+    }
     while (done < n_steps) {
         const int s = (int)(d->step % E);
+        const bool due = d->since >= d->halo;
+        if (s == 0 || due) {
+            // every part's streams joined: the whole grid's h_max into every part at an
+            // epoch start, the halo rows when due; then the parts go on side by side
+            flood_status st = join_lanes(d);
+            if (st) return st;
+            if (s == 0) DCK(launch_hmax_allreduce(d->ctrls_dev, d->n_parts, d->stream));
+            if (due && (st = exchange(d))) return st;
+            if ((st = fork_lanes(d))) return st;
+        }
         if (s == 0) {
-            // epoch start: every part takes the whole grid's h_max, then chooses dt
-            DCK(launch_hmax_allreduce(d->ctrls_dev, d->n_parts, d->stream));
+            // epoch start: every part chooses dt from the whole grid's h_max, and solves Eq. 6
             for (int r = 0; r < d->n_parts; r++) {
                 flood_handle *h = d->parts[r];
-                DCK(launch_epoch_begin(h->geo, h->ctrl, h->t_list, E, nullptr, d->stream));
+                DCK(launch_epoch_begin(h->geo, h->ctrl, h->t_list, E, nullptr, h->stream));
                 flood_status st = launch_inflow_epoch(h);
                 if (st) return part_fail(d, r, st);
             }
-        }
-        if (d->since >= d->halo) {
-            flood_status st = exchange(d);
-            if (st) return st;
         }
         const int m = (int)std::min<int64_t>(std::min(d->halo - d->since, E - s), n_steps - done);
         for (int r = 0; r < d->n_parts; r++) {
@@ -261,7 +307,7 @@ extern "C" flood_status flood_decomp_step(flood_decomp *d, int64_t n_steps)
         d->since += m;
         done += m;
     }
-    return FLOOD_OK;
+    return join_lanes(d);                       // the caller's stream sees every part's steps
 }
 
 extern "C" flood_status flood_decomp_sync(flood_decomp *d)
@@ -295,6 +341,10 @@ extern "C" flood_status flood_decomp_read(flood_decomp *d, int32_t field, void *
         return FLOOD_OK;
     }
     if (field < FLOOD_FIELD_H || field > FLOOD_FIELD_N) return dfail(d, FLOOD_ERR_ARG, "unknown field");
+    {
+        flood_status st = join_lanes(d);       // the parts' last writes come first
+        if (st) return st;
+    }
     const int rows_all = d->ny + (field == FLOOD_FIELD_QY ? 1 : 0);
     const int cols = d->nx + (field == FLOOD_FIELD_QX ? 1 : 0);
     if (bytes != (size_t)rows_all * cols * d->esz) return dfail(d, FLOOD_ERR_ARG, "dst size does not match the field");
@@ -346,8 +396,20 @@ extern "C" flood_handle *flood_decomp_part(flood_decomp *d, int32_t k)
 extern "C" flood_status flood_decomp_destroy(flood_decomp *d)
 {
     if (!d) return FLOOD_OK;
-    for (flood_handle *h : d->parts) flood_destroy(h);
+    for (cudaStream_t l : d->lanes)
+        if (l) cudaStreamSynchronize(l);
+    // the parts' memory goes back on the caller's stream, where it was taken
+    for (size_t r = 0; r < d->parts.size(); r++) {
+        flood_handle *h = d->parts[r];
+        if (r < d->lanes.size() && d->lanes[r] && h->stream == d->lanes[r]) h->stream = d->stream;
+        flood_destroy(h);
+    }
     if (d->ctrls_dev) c10::cuda::CUDACachingAllocator::raw_delete(d->ctrls_dev);
+    for (cudaEvent_t e : d->lane_ev)
+        if (e) cudaEventDestroy(e);
+    if (d->main_ev) cudaEventDestroy(d->main_ev);
+    for (cudaStream_t l : d->lanes)
+        if (l) cudaStreamDestroy(l);
     delete d;
     return FLOOD_OK;
 }
