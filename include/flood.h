@@ -376,8 +376,11 @@ flood_status flood_decomp_combine_ledgers(int32_t n_parts, const double *part_le
 /* Create a grid of n_parts row strips on the current device (arguments as
  * for flood_create, plus n_parts and halo >= 1, the steps between exchanges).
  * The parts run the kernel family that flood_create chooses for the whole
- * grid; FP64 grids use the reference kernel.  use_graph is ignored.  All
- * parts share opts->stream.  Errors: flood_last_error(NULL). */
+ * grid; FP64 grids use the reference kernel.  use_graph is ignored.  Each part
+ * steps on a stream of its own (created here); flood_decomp_step,
+ * flood_decomp_write_state and flood_decomp_read order the parts' work after
+ * what the caller queued on opts->stream, and flood_decomp_step returns with
+ * opts->stream waiting for every part.  Errors: flood_last_error(NULL). */
 typedef struct flood_decomp flood_decomp;
 flood_status flood_decomp_create(const flood_grid *grid, const void *dem, const void *manning,
                                  const flood_bc_section *sections, int32_t n_sections, const flood_opts *opts,

@@ -369,6 +369,10 @@ extern "C" flood_status flood_decomp_write_state(flood_decomp *d, const void *de
 {
     if (!d || !depth) return dfail(d, FLOOD_ERR_ARG, "NULL argument");
     const size_t e = d->esz;
+    {
+        flood_status st = fork_lanes(d);       // device sources the caller wrote on its stream come first
+        if (st) return st;
+    }
     for (int r = 0; r < d->n_parts; r++) {
         const int a = d->rows[4 * r + 2];
         const char *hp = (const char *)depth + (size_t)a * d->nx * e;
