@@ -36,6 +36,18 @@ struct flood_ensemble {
     int *tbase = nullptr;                  // tiled item prefix, n + 1
     int total_items = 0;
     int *next_item = nullptr;              // tiled: the item counter of the launch (zeroed before each)
+    // tiled: the members in two groups of about equal cells, each launched on a stream of its
+    // own from one epoch start to the next, so that one group's launches fill the other's tails
+    static constexpr int kGroups = 2;
+    std::vector<int> group_of;             // per member
+    StepArgs<float> *gtable[kGroups][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [group][parity]
+    int *gtbase[kGroups] = {nullptr, nullptr};
+    int *gnext[kGroups] = {nullptr, nullptr};
+    int gn[kGroups] = {0, 0}, gtotal[kGroups] = {0, 0};
+    cudaStream_t lane[kGroups] = {nullptr, nullptr};
+    cudaEvent_t lane_ev[kGroups] = {nullptr, nullptr};
+    cudaEvent_t fork_ev = nullptr;
+    bool forked = false;                   // the groups' streams run ahead of `stream`
     EpochArgs<float> *etab = nullptr;      // per member: epoch bookkeeping arguments
     int2 *tasks = nullptr;                 // (member, inflow section) pairs
     int n_tasks = 0;
@@ -106,9 +118,70 @@ flood_status build_tables(flood_ensemble *e)
     if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
     c = cudaMemcpyAsync(e->tbase, tbase.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, e->stream);
     if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+    // the groups: largest member first into the group with fewer cells so far
+    {
+        int64_t cells[flood_ensemble::kGroups] = {0, 0};
+        std::vector<int> members[flood_ensemble::kGroups];
+        for (int k = 0; k < n; k++) {
+            const int m = e->order[k];
+            const int g = cells[1] < cells[0] ? 1 : 0;
+            members[g].push_back(m);
+            cells[g] += (int64_t)e->members[m]->geo.nx * e->members[m]->geo.ny;
+        }
+        for (int g = 0; g < flood_ensemble::kGroups; g++) {
+            const int ng = (int)members[g].size();
+            std::vector<int> gb(ng + 1, 0);
+            for (int i = 0; i < ng; i++) {
+                const Geom &G = e->members[members[g][i]]->geo;
+                gb[i + 1] = gb[i] + tiled_items(G, item_rows(e, G), e->k_steps);
+            }
+            e->gn[g] = ng;
+            e->gtotal[g] = gb[ng];
+            for (int p = 0; p < 2; p++) {
+                std::vector<StepArgs<float>> t(ng);
+                for (int i = 0; i < ng; i++) {
+                    flood_handle *h = e->members[members[g][i]];
+                    const int cur = h->cur;
+                    h->cur = p;
+                    t[i] = step_args_f32(h, 0);
+                    t[i].tile_y = item_rows(e, h->geo);
+                    h->cur = cur;
+                }
+                if (ng && (c = cudaMemcpyAsync(e->gtable[g][p], t.data(), ng * sizeof(StepArgs<float>),
+                                               cudaMemcpyHostToDevice, e->stream)) != cudaSuccess)
+                    return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+            }
+            c = cudaMemcpyAsync(e->gtbase[g], gb.data(), (ng + 1) * sizeof(int), cudaMemcpyHostToDevice, e->stream);
+            if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+        }
+    }
     c = cudaStreamSynchronize(e->stream);
     if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
     drop_graphs(e);
+    return FLOOD_OK;
+}
+
+// `st` waits for the groups' streams (after their launches since the last fork).
+flood_status join_groups(flood_ensemble *e, cudaStream_t st)
+{
+    if (!e->forked) return FLOOD_OK;
+    for (int g = 0; g < flood_ensemble::kGroups; g++) {
+        cudaError_t c = cudaEventRecord(e->lane_ev[g], e->lane[g]);
+        if (c == cudaSuccess) c = cudaStreamWaitEvent(st, e->lane_ev[g], 0);
+        if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+    }
+    e->forked = false;
+    return FLOOD_OK;
+}
+
+// The groups' streams wait for `st`.
+flood_status fork_groups(flood_ensemble *e, cudaStream_t st)
+{
+    if (e->forked) return FLOOD_OK;
+    cudaError_t c = cudaEventRecord(e->fork_ev, st);
+    for (int g = 0; g < flood_ensemble::kGroups && c == cudaSuccess; g++) c = cudaStreamWaitEvent(e->lane[g], e->fork_ev, 0);
+    if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+    e->forked = true;
     return FLOOD_OK;
 }
 
@@ -120,6 +193,8 @@ flood_status ensemble_step(flood_ensemble *e, int64_t limit, cudaStream_t st, in
     const int E = e->E;
     const int s = (int)(e->step % E);
     if (s == 0) {
+        flood_status fs = join_groups(e, st);   // every member's epoch end, then all epoch starts at once
+        if (fs) return fs;
         cudaError_t c = launch_epoch_batched<float>(e->etab, (int)e->members.size(), e->tasks, e->n_tasks, E, st);
         if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
     }
@@ -133,11 +208,19 @@ flood_status ensemble_step(flood_ensemble *e, int64_t limit, cudaStream_t st, in
     // the item table is laid out for k_steps: 8-step tables (wider halos) take
     // only whole 8-step launches, anything shorter runs single stream steps
     if (e->kernel == FLOOD_KERNEL_TILED && !(e->k_steps == 8 && steps < 8)) {
-        c = cudaMemsetAsync(e->next_item, 0, sizeof(int), st);
-        if (c == cudaSuccess)
-            c = launch_step_tiled_ensemble(e->table[parity], e->tbase, n, e->total_items, steps, s,
-                                           s + steps == E ? 1 : 0, e->next_item, e->mode, st);
+        flood_status fs = fork_groups(e, st);
+        if (fs) return fs;
+        c = cudaSuccess;
+        for (int g = 0; g < flood_ensemble::kGroups && c == cudaSuccess; g++) {
+            if (e->gn[g] == 0) continue;
+            c = cudaMemsetAsync(e->gnext[g], 0, sizeof(int), e->lane[g]);
+            if (c == cudaSuccess)
+                c = launch_step_tiled_ensemble(e->gtable[g][parity], e->gtbase[g], e->gn[g], e->gtotal[g], steps, s,
+                                               s + steps == E ? 1 : 0, e->gnext[g], e->mode, e->lane[g]);
+        }
     } else {
+        flood_status fs = join_groups(e, st);
+        if (fs) return fs;
         steps = 1;
         c = launch_step_stream_ensemble(e->table[parity], e->base, n, e->total_blocks, e->warps, e->rows, s,
                                         s == E - 1 ? 1 : 0, e->mode, st);
@@ -167,9 +250,12 @@ flood_status capture(flood_ensemble *e, int parity)
     c = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     flood_status fs = FLOOD_OK;
     int launches = 0;
-    if (c == cudaSuccess)
+    if (c == cudaSuccess) {
         for (int k = 0, taken = 0; k < e->steps_per_graph && !fs; k += taken, launches++)
             fs = ensemble_step(e, e->steps_per_graph - k, cap, &taken);
+        if (!fs) fs = join_groups(e, cap);
+    }
+    e->forked = false;
     cudaGraph_t graph = nullptr;
     cudaError_t c2 = cudaStreamEndCapture(cap, &graph);
     cudaStreamDestroy(cap);
@@ -252,6 +338,21 @@ extern "C" flood_status flood_ensemble_create(int32_t n, const flood_grid *grids
     e->base = (int *)dev_alloc(e->owner, (n + 1) * sizeof(int));
     e->tbase = (int *)dev_alloc(e->owner, (n + 1) * sizeof(int));
     e->next_item = (int *)dev_alloc(e->owner, sizeof(int));
+    for (int g = 0; g < flood_ensemble::kGroups; g++) {
+        for (int p = 0; p < 2; p++) e->gtable[g][p] = (StepArgs<float> *)dev_alloc(e->owner, n * sizeof(StepArgs<float>));
+        e->gtbase[g] = (int *)dev_alloc(e->owner, (n + 1) * sizeof(int));
+        e->gnext[g] = (int *)dev_alloc(e->owner, sizeof(int));
+        if (!e->gtable[g][0] || !e->gtable[g][1] || !e->gtbase[g] || !e->gnext[g] ||
+            cudaStreamCreateWithFlags(&e->lane[g], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e->lane_ev[g], cudaEventDisableTiming) != cudaSuccess) {
+            flood_ensemble_destroy(e);
+            return efail(nullptr, FLOOD_ERR_OOM, "ensemble group tables and streams");
+        }
+    }
+    if (cudaEventCreateWithFlags(&e->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+        flood_ensemble_destroy(e);
+        return efail(nullptr, FLOOD_ERR_CUDA, "event creation");
+    }
     e->etab = (EpochArgs<float> *)dev_alloc(e->owner, n * sizeof(EpochArgs<float>));
     std::vector<EpochArgs<float>> et(n);
     std::vector<int2> tk;
@@ -330,6 +431,8 @@ extern "C" flood_status flood_ensemble_step(flood_ensemble *e, int64_t n_steps)
         const int s = (int)(e->step % e->E);
         if (e->use_graph && s == 0 && n_steps >= e->steps_per_graph) {
             const int parity = e->members[0]->cur;
+            flood_status js = join_groups(e, e->stream);   // the groups' streams join before a capture or replay
+            if (js) return js;
             if (!e->graphs[parity]) {
                 flood_status st = capture(e, parity);
                 if (st) return st;
@@ -350,7 +453,7 @@ extern "C" flood_status flood_ensemble_step(flood_ensemble *e, int64_t n_steps)
         if (st) return st;
         n_steps -= taken;
     }
-    return FLOOD_OK;
+    return join_groups(e, e->stream);           // the members' stream sees every step
 }
 
 extern "C" flood_handle *flood_ensemble_member(flood_ensemble *e, int32_t k)
@@ -363,6 +466,8 @@ extern "C" flood_status flood_ensemble_destroy(flood_ensemble *e)
 {
     if (!e) return FLOOD_OK;
     if (e->stream) cudaStreamSynchronize(e->stream);
+    for (int g = 0; g < flood_ensemble::kGroups; g++)
+        if (e->lane[g]) cudaStreamSynchronize(e->lane[g]);
     drop_graphs(e);
     if (e->owner) {
         for (int p = 0; p < 2; p++)
@@ -370,10 +475,21 @@ extern "C" flood_status flood_ensemble_destroy(flood_ensemble *e)
         if (e->base) dev_free(e->owner, e->base);
         if (e->tbase) dev_free(e->owner, e->tbase);
         if (e->next_item) dev_free(e->owner, e->next_item);
+        for (int g = 0; g < flood_ensemble::kGroups; g++) {
+            for (int p = 0; p < 2; p++)
+                if (e->gtable[g][p]) dev_free(e->owner, e->gtable[g][p]);
+            if (e->gtbase[g]) dev_free(e->owner, e->gtbase[g]);
+            if (e->gnext[g]) dev_free(e->owner, e->gnext[g]);
+        }
         if (e->etab) dev_free(e->owner, e->etab);
         if (e->tasks) dev_free(e->owner, e->tasks);
     }
     for (flood_handle *h : e->members) flood_destroy(h);
+    for (int g = 0; g < flood_ensemble::kGroups; g++) {
+        if (e->lane_ev[g]) cudaEventDestroy(e->lane_ev[g]);
+        if (e->lane[g]) cudaStreamDestroy(e->lane[g]);
+    }
+    if (e->fork_ev) cudaEventDestroy(e->fork_ev);
     delete e;
     return FLOOD_OK;
 }
