@@ -44,6 +44,9 @@ struct flood_ensemble {
     int *gtbase[kGroups] = {nullptr, nullptr};
     int *gnext[kGroups] = {nullptr, nullptr};
     int gn[kGroups] = {0, 0}, gtotal[kGroups] = {0, 0};
+    EpochArgs<float> *getab[kGroups] = {nullptr, nullptr};   // the group's members' epoch arguments
+    int2 *gtasks[kGroups] = {nullptr, nullptr};              // (member in the group, inflow section)
+    int gntasks[kGroups] = {0, 0};
     cudaStream_t lane[kGroups] = {nullptr, nullptr};
     cudaEvent_t lane_ev[kGroups] = {nullptr, nullptr};
     cudaEvent_t fork_ev = nullptr;
@@ -74,6 +77,27 @@ void drop_graphs(flood_ensemble *e)
     for (auto &g : e->graphs)
         if (g) cudaGraphExecDestroy(g);
     e->graphs.assign(2, nullptr);
+}
+
+// Epoch bookkeeping arguments of a member.
+EpochArgs<float> epoch_args(const flood_handle *h)
+{
+    EpochArgs<float> A;
+    A.geo = h->geo;
+    A.ctrl = h->ctrl;
+    A.t_list = h->t_list;
+    A.secs = h->secs_dev;
+    A.nsec = h->n_in;
+    A.cells = h->sec_cells;
+    A.tab_t = h->tab_t;
+    A.tab_q = h->tab_q;
+    A.z = (const float *)h->z;
+    A.n = (const float *)h->n;
+    A.inflow_q = (float *)h->inflow_q;
+    A.n_slots = h->n_slots;
+    A.inflow_Q = h->inflow_Q;
+    A.inflow_W = h->inflow_W;
+    return A;
 }
 
 // Rows per work item of the temporal-blocking kernel for a member grid: the
@@ -153,6 +177,21 @@ flood_status build_tables(flood_ensemble *e)
             }
             c = cudaMemcpyAsync(e->gtbase[g], gb.data(), (ng + 1) * sizeof(int), cudaMemcpyHostToDevice, e->stream);
             if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+            // the group's own epoch starts (dt, Eq. 6), on its stream
+            std::vector<EpochArgs<float>> et(ng);
+            std::vector<int2> tk;
+            for (int i = 0; i < ng; i++) {
+                const flood_handle *h = e->members[members[g][i]];
+                et[i] = epoch_args(h);
+                for (int sct = 0; sct < h->n_in; sct++) tk.push_back(make_int2(i, sct));
+            }
+            e->gntasks[g] = (int)tk.size();
+            if (ng && (c = cudaMemcpyAsync(e->getab[g], et.data(), ng * sizeof(EpochArgs<float>), cudaMemcpyHostToDevice,
+                                           e->stream)) != cudaSuccess)
+                return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+            if (tk.size() && (c = cudaMemcpyAsync(e->gtasks[g], tk.data(), tk.size() * sizeof(int2),
+                                                  cudaMemcpyHostToDevice, e->stream)) != cudaSuccess)
+                return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
         }
     }
     c = cudaStreamSynchronize(e->stream);
@@ -192,8 +231,18 @@ flood_status ensemble_step(flood_ensemble *e, int64_t limit, cudaStream_t st, in
 {
     const int E = e->E;
     const int s = (int)(e->step % E);
-    if (s == 0) {
-        flood_status fs = join_groups(e, st);   // every member's epoch end, then all epoch starts at once
+    const bool grouped = e->kernel == FLOOD_KERNEL_TILED && !(e->k_steps == 8 && (int)std::min<int64_t>(E - s, limit) < 8);
+    if (s == 0 && grouped) {
+        // each group starts its members' epoch on its own stream
+        flood_status fs = fork_groups(e, st);
+        if (fs) return fs;
+        for (int g = 0; g < flood_ensemble::kGroups; g++) {
+            if (e->gn[g] == 0) continue;
+            cudaError_t c = launch_epoch_batched<float>(e->getab[g], e->gn[g], e->gtasks[g], e->gntasks[g], E, e->lane[g]);
+            if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
+        }
+    } else if (s == 0) {
+        flood_status fs = join_groups(e, st);
         if (fs) return fs;
         cudaError_t c = launch_epoch_batched<float>(e->etab, (int)e->members.size(), e->tasks, e->n_tasks, E, st);
         if (c != cudaSuccess) return efail(e, FLOOD_ERR_CUDA, cudaGetErrorString(c));
@@ -342,7 +391,11 @@ extern "C" flood_status flood_ensemble_create(int32_t n, const flood_grid *grids
         for (int p = 0; p < 2; p++) e->gtable[g][p] = (StepArgs<float> *)dev_alloc(e->owner, n * sizeof(StepArgs<float>));
         e->gtbase[g] = (int *)dev_alloc(e->owner, (n + 1) * sizeof(int));
         e->gnext[g] = (int *)dev_alloc(e->owner, sizeof(int));
-        if (!e->gtable[g][0] || !e->gtable[g][1] || !e->gtbase[g] || !e->gnext[g] ||
+        e->getab[g] = (EpochArgs<float> *)dev_alloc(e->owner, n * sizeof(EpochArgs<float>));
+        int n_sec_all = 0;
+        for (flood_handle *h : e->members) n_sec_all += h->n_in;
+        e->gtasks[g] = (int2 *)dev_alloc(e->owner, std::max(n_sec_all, 1) * sizeof(int2));
+        if (!e->gtable[g][0] || !e->gtable[g][1] || !e->gtbase[g] || !e->gnext[g] || !e->getab[g] || !e->gtasks[g] ||
             cudaStreamCreateWithFlags(&e->lane[g], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&e->lane_ev[g], cudaEventDisableTiming) != cudaSuccess) {
             flood_ensemble_destroy(e);
@@ -480,6 +533,8 @@ extern "C" flood_status flood_ensemble_destroy(flood_ensemble *e)
                 if (e->gtable[g][p]) dev_free(e->owner, e->gtable[g][p]);
             if (e->gtbase[g]) dev_free(e->owner, e->gtbase[g]);
             if (e->gnext[g]) dev_free(e->owner, e->gnext[g]);
+            if (e->getab[g]) dev_free(e->owner, e->getab[g]);
+            if (e->gtasks[g]) dev_free(e->owner, e->gtasks[g]);
         }
         if (e->etab) dev_free(e->owner, e->etab);
         if (e->tasks) dev_free(e->owner, e->tasks);
