@@ -49,12 +49,12 @@ def _save(path: str, data: dict) -> None:
 
 def ensemble_key(ens) -> str:
     shapes = ",".join(f"{p.nx}x{p.ny}" for p in ens.problems)
-    return f"v3|{torch.cuda.get_device_name()}|E{ens.problems[0].opts.epoch_steps}|{shapes}"
+    return f"v4|{torch.cuda.get_device_name()}|E{ens.problems[0].opts.epoch_steps}|{shapes}"
 
 
 def default_candidates(E: int) -> Sequence[Shape]:
     stream = [(0, w, r, g) for w in (2, 4) for r in (32, 64, 128) for g in (E, 4 * E)]
-    tiled = [(k, 2, r, g) for k in (2, 4) if E % k == 0 for r in (64, 96, 128, 192, 256) for g in (E, 4 * E)]
+    tiled = [(k, 2, r, g) for k in (2, 4) if E % k == 0 for r in (96, 128, 192, 256, 320) for g in (E, 4 * E)]
     return stream + tiled
 
 
