@@ -280,15 +280,17 @@ const char *flood_last_error(const flood_handle *h);
  * release policies and climate scenarios are the use): n independent FP32
  * scenarios, each with its own grid, DEM, Manning field and boundary
  * sections (arguments as for flood_create, element k of each array), advanced
- * together.  Every launch covers all scenarios, largest grid first: one step
- * of the stream kernel over their blocks (default), or, after
- * flood_ensemble_set_kernel(TILED, K), K steps of the temporal-blocking kernel
- * over their (chunk, strip) items.  Each scenario keeps its own CFL time
- * step, Eq. 6 inflow and ledger.  Whole epochs are captured once into a CUDA
- * graph (steps_per_graph steps, a multiple of epoch_steps) and replayed.
- * opts applies to every scenario (kernel and use_graph are set by the
- * ensemble; theta and friction apply to every scenario); all scenarios share
- * its stream.  flood_ensemble_member returns
+ * together: one step of the stream kernel over all their blocks per launch,
+ * largest grid first (default), or, after flood_ensemble_set_kernel(TILED, K),
+ * K steps of the temporal-blocking kernel over their (chunk, strip) items, the
+ * scenarios in two groups of about equal cells, each group launching (and
+ * starting its scenarios' epochs) on a stream of its own created here.  Each
+ * scenario keeps its own CFL time step, Eq. 6 inflow and ledger.  Whole epochs
+ * are captured once into a CUDA graph (steps_per_graph steps, a multiple of
+ * epoch_steps) and replayed.  opts applies to every scenario (kernel and
+ * use_graph are set by the ensemble; theta and friction apply to every
+ * scenario); the scenarios share its stream, and flood_ensemble_step returns
+ * with that stream waiting for both groups.  flood_ensemble_member returns
  * scenario k's handle for flood_read / flood_write_state / flood_set_clock
  * (do not destroy it or step it alone).  Errors: flood_ensemble_last_error.
  */
