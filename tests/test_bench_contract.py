@@ -54,3 +54,5 @@ def test_gpu_arm_line():
     assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert d["config"]["kernel"] == "tiled" and d["config"]["steps_per_launch"] == 4
     assert d["one_step"]["kernel"] == "stream" and d["one_step"]["value"] > 0
+    runs = d["decomposition"]["runs"]                 # 1 x 2 and 1 x 4 strips of the same workload
+    assert [r["parts"] for r in runs] == [2, 4] and all(r["value"] > 0 and r["halo"] == 4 for r in runs)
