@@ -241,7 +241,10 @@ flood_status flood_run_gauges(flood_handle *h, int64_t n_steps, const int64_t *g
  * held fixed (chosen by the forward sweep).  Binomial checkpointing keeps at
  * most n_checkpoints states on the device (>= 1; 0: as many as half the free
  * device memory holds, up to n_steps, where every state is kept and no step is
- * replayed twice).  dLdh: host doubles.
+ * replayed twice; the count is halved while that allocation fails).  The
+ * snapshots and scratch return to the PyTorch caching allocator when the call
+ * ends, which keeps them reserved for later allocations of the process
+ * (torch.cuda.empty_cache() hands them back to the driver).  dLdh: host doubles.
  * dLdn_out: ny*nx elements of the grid's precision, host (out_on_device = 0)
  * or device.  dLdh0_out: optional (NULL) gradient with respect to the
  * starting depth.  The handle's state, clock and ledger are unchanged.
