@@ -141,10 +141,11 @@ __host__ __device__ constexpr int hand_fields(int mode) { return mode ? 4 : 3; }
 // level 1 reads it from the ring one row ahead (or from global memory past the
 // staged rows), level s > 1 from the hand-off, where level s - 1 leaves the qy
 // it computed for that row; and the old qy / qx of the row below, kept in
-// registers.  Their faces are evaluated one at a time (the paired form serves
-// Eq. 3 as printed).  The lanes at the strip's edges take their missing
-// neighbour columns as garbage, like the plain arithmetic's edge lanes: the
-// stencil still reaches one column per level, inside the halo.
+// registers.  Their faces are evaluated two per paired instruction, like
+// Eq. 3 as printed, in the scalar option arithmetic's order.  The lanes at
+// the strip's edges take their missing neighbour columns as garbage, like the
+// plain arithmetic's edge lanes: the stencil still reaches one column per
+// level, inside the halo.
 template <int K, int kPF, int kMode = 0>
 __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s0, const FastConst &Kc,
                                            const int strip, const int y0, const int y1,
@@ -281,7 +282,7 @@ __device__ __forceinline__ bool tiled_item(const StepArgs<float> &a, const int s
                     // rows, uniform over the warp, take the Eq. 5-6 path)
                     float4 qys;
                     if (r > 0 && r < ny && kOpt) {
-                        // one face at a time with the options (the stream kernel's arithmetic)
+                        // with the options (the stream kernel's arithmetic)
                         float xs4 = 0.0f, xn4 = 0.0f;  // old qx right of the lane's last column, rows r-1, r
                         if constexpr (kVec) {
                             xs4 = __shfl_down_sync(0xffffffffu, qxo_p.x, 1);
