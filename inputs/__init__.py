@@ -348,6 +348,19 @@ def normal_depth_channel(nx: int = 96, ny: int = 8, dx: float = 10.0, S0: float 
                    Options(dt_mode=1, dt_const=1.0), h0=np.full((ny, nx), h_n))
 
 
+def standing_wave(nx: int, ny: int, mx: int, my: int, H: float = 2.0, eps: float = 1e-7, dx: float = 1.5,
+                  dt: float = 0.05, theta: float = 1.0) -> Problem:
+    """Closed basin, flat bed, no friction, at rest: depth H + eps cos(kx x) cos(ky y)
+    at the cell centres, kx = pi mx / (nx dx), ky = pi my / (ny dx) (the cosine
+    modes that the walls admit), constant time step dt."""
+    xc = (np.arange(nx) + 0.5) * dx
+    yc = (np.arange(ny) + 0.5) * dx
+    mode = np.outer(np.cos(np.pi * my / (ny * dx) * yc), np.cos(np.pi * mx / (nx * dx) * xc))
+    return Problem(f"standing_wave_{nx}x{ny}_{mx}_{my}", nx, ny, dx, np.zeros((ny, nx)), np.zeros((ny, nx)), [],
+                   Options(dt_mode=1, dt_const=dt, theta=theta), h0=H + eps * mode,
+                   qx0=np.zeros((ny, nx + 1)), qy0=np.zeros((ny + 1, nx)))
+
+
 def random_small(nx: int, ny: int, seed: int, wet: float = 0.5, inflow: float = 5.0,
                  bc_form: int = 0, dt_mode: int = 0) -> Problem:
     """Small seeded case with rough terrain, partial wetting and every boundary kind.
