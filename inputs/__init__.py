@@ -349,14 +349,15 @@ def normal_depth_channel(nx: int = 96, ny: int = 8, dx: float = 10.0, S0: float 
 
 
 def standing_wave(nx: int, ny: int, mx: int, my: int, H: float = 2.0, eps: float = 1e-7, dx: float = 1.5,
-                  dt: float = 0.05, theta: float = 1.0) -> Problem:
-    """Closed basin, flat bed, no friction, at rest: depth H + eps cos(kx x) cos(ky y)
-    at the cell centres, kx = pi mx / (nx dx), ky = pi my / (ny dx) (the cosine
-    modes that the walls admit), constant time step dt."""
+                  dt: float = 0.05, theta: float = 1.0, n: float = 0.0) -> Problem:
+    """Closed basin, flat bed, Manning n (0: no friction), at rest: depth
+    H + eps cos(kx x) cos(ky y) at the cell centres, kx = pi mx / (nx dx),
+    ky = pi my / (ny dx) (the cosine modes that the walls admit), constant time
+    step dt."""
     xc = (np.arange(nx) + 0.5) * dx
     yc = (np.arange(ny) + 0.5) * dx
     mode = np.outer(np.cos(np.pi * my / (ny * dx) * yc), np.cos(np.pi * mx / (nx * dx) * xc))
-    return Problem(f"standing_wave_{nx}x{ny}_{mx}_{my}", nx, ny, dx, np.zeros((ny, nx)), np.zeros((ny, nx)), [],
+    return Problem(f"standing_wave_{nx}x{ny}_{mx}_{my}", nx, ny, dx, np.zeros((ny, nx)), np.full((ny, nx), n), [],
                    Options(dt_mode=1, dt_const=dt, theta=theta), h0=H + eps * mode,
                    qx0=np.zeros((ny, nx + 1)), qy0=np.zeros((ny + 1, nx)))
 

@@ -12,7 +12,9 @@ on this grid they reach 1.1e-3 eps at eps = 3 mm and 5e-8 eps at eps = 0.1 um
 (4e-5 eps per rounding); the depth update rounds once per cell and step, which
 over 128 steps adds about 5e-4 eps.  Bounds: 1e-2 eps (FP32, eps = 3 mm) and
 1e-5 eps (FP64, eps = 0.1 um).  A wrong factor, sign or index moves the result
-by order eps.
+by order eps.  The library takes Manning n > 0 only, so the lake has
+n = 1e-4: the friction term is of second order in eps (|q| q), here below
+1e-10 of the discharges per step.
 """
 import numpy as np
 import pytest
@@ -28,7 +30,7 @@ H, DX, DT = 2.0, 1.5, 0.05
 
 def run_wave(precision, kernel, k, theta, eps):
     import paper_2204_10323_gb300 as F
-    p = inputs.standing_wave(NX, NY, MX, MY, H=H, eps=eps, dx=DX, dt=DT, theta=theta)
+    p = inputs.standing_wave(NX, NY, MX, MY, H=H, eps=eps, dx=DX, dt=DT, theta=theta, n=1e-4)
     mode = (p.h0 - H) / eps
     amp = standing_wave_amplitudes(NX, NY, MX, MY, H, DX, DT, theta, 128)
     s = F.Sim(p, precision=precision, kernel=kernel, steps_per_launch=k)
