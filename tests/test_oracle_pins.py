@@ -402,6 +402,33 @@ def test_friction_norm_closed_form(friction):
     np.testing.assert_allclose(o.qy[1:ny, :], 0.4 / (1 + c * my), rtol=1e-14)
 
 
+def test_friction_vector_norm_takes_the_four_faces_around():
+    """Flat water 1 m deep (h_f = 1, no slope term), n = 0.05, dt = 0.1 s.  Old
+    x-face discharges 0.3 + 0.1 j (rising with the row), y-face discharges
+    0.4 + 0.2 i (rising with the column).  The four y-faces around x-face (j, i)
+    (between cells i - 1 and i) sit in columns i - 1 and i, mean
+    0.4 + 0.2 (i - 1/2); the four x-faces around y-face (j, i) sit in rows j - 1
+    and j, mean 0.3 + 0.1 (j - 1/2).  A face keeps q / (1 + g dt n^2 sqrt(q^2 + mean^2));
+    a mean taken one column or row off moves it by about 1e-4 of q."""
+    nx, ny = 6, 5
+    p = closed_box(np.zeros((ny, nx)), np.ones((ny, nx)), n=0.05, friction=1)
+    jj, ii = np.mgrid[0:ny, 0:nx + 1]
+    p.qx0 = 0.3 + 0.1 * jj
+    jj, ii = np.mgrid[0:ny + 1, 0:nx]
+    p.qy0 = 0.4 + 0.2 * ii
+    o = oracle.Oracle(p)
+    o.step_dt(0.1)
+    c = 9.81 * 0.1 * 0.05 ** 2
+    for j in range(ny):
+        for i in range(1, nx):
+            q, m = 0.3 + 0.1 * j, 0.4 + 0.2 * (i - 0.5)
+            assert o.qx[j, i] == pytest.approx(q / (1 + c * math.sqrt(q * q + m * m)), rel=1e-14), (j, i)
+    for j in range(1, ny):
+        for i in range(nx):
+            q, m = 0.4 + 0.2 * i, 0.3 + 0.1 * (j - 0.5)
+            assert o.qy[j, i] == pytest.approx(q / (1 + c * math.sqrt(q * q + m * m)), rel=1e-14), (j, i)
+
+
 # ---------------------------------------------------------------- boundary conditions
 def test_section_fraction_rule():
     p = inputs.random_small(20, 12, 0)
