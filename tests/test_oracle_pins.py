@@ -579,6 +579,62 @@ def test_adjoint_dh0_matches_central_differences(theta, friction):
         assert lqy[j, i] == pytest.approx(fd("qy0", j, i), rel=2e-5, abs=1e-8)
 
 
+def _dot_case(theta, friction, bc_form, inflow):
+    """10 x 7 wet basin with moving water (|q| and the vector norm smooth),
+    outflow on three sides and optionally a Manning inflow section."""
+    rng = np.random.default_rng(900)
+    nx, ny, dx = 10, 7, 4.0
+    xm = (np.arange(nx) + 0.5) * dx
+    z = 1.0 - 2e-3 * xm[None, :] + rng.uniform(-0.05, 0.05, (ny, nx))
+    h0 = 0.6 + rng.uniform(0.0, 0.2, (ny, nx))
+    n = rng.uniform(0.03, 0.06, (ny, nx))
+    so = 2e-3 if bc_form == 0 else 2e-5
+    secs = [Section.cells(XMAX, 0, ny, OUTFLOW, so, nx, ny), Section.cells(YMAX, 3, 8, OUTFLOW, so / 2, nx, ny),
+            Section.cells(YMIN, 0, 4, OUTFLOW, so, nx, ny)]
+    if inflow:
+        secs.append(Section.cells(XMIN, 2, 6, INFLOW, 2e-3, nx, ny, [0.0, 30.0], [1.0, 3.0]))
+    return Problem("dot", nx, ny, dx, z, n, secs,
+                   Options(dt_mode=1, dt_const=0.4, bc_form=bc_form, theta=theta, friction=friction), h0=h0,
+                   qx0=rng.uniform(-0.05, 0.05, (ny, nx + 1)), qy0=rng.uniform(-0.05, 0.05, (ny + 1, nx)))
+
+
+@pytest.mark.parametrize("theta,friction,bc_form,inflow", [(1.0, 0, 0, False), (0.8, 0, 0, False),
+                                                           (1.0, 1, 0, False), (0.85, 1, 1, False),
+                                                           (1.0, 0, 0, True)])
+def test_adjoint_dot_product_one_step(theta, friction, bc_form, inflow):
+    """The transpose test on one step y = S(x), x = (h, qx, qy, n): for a random
+    seed lam on the depths after the step and a random direction v,
+    <lam, J v> = <J^T lam, v>.  J^T lam is the reverse sweep's (dL/dh0, dL/dqx0,
+    dL/dqy0, dL/dn) with L = <lam, h(after the step)>; J v is the fourth-order
+    central difference of L along v (step 5e-3 of v: truncation and rounding
+    both near 1e-12 of the product, masks fixed on this range).  Agreement to
+    1e-10 relative, for each input separately, checks every term of the
+    reverse step far below the per-cell finite differences' 1e-5."""
+    p = _dot_case(theta, friction, bc_form, inflow)
+    rng = np.random.default_rng(5)
+    lam = rng.standard_normal((p.ny, p.nx))
+    jj, ii = np.mgrid[0:p.ny, 0:p.nx]
+    gauges = np.stack([ii.ravel(), jj.ravel()], 1)
+    gn, lh, lqx, lqy = oracle.Oracle(p).adjoint(1, gauges, lam.reshape(1, -1), want_state=True)
+    full = (0.01 * rng.standard_normal(p.h0.shape), 0.01 * rng.standard_normal(p.qx0.shape),
+            0.01 * rng.standard_normal(p.qy0.shape), 0.001 * rng.standard_normal(p.n.shape))
+    grads = (lh, lqx, lqy, gn)
+
+    def L(v, e):
+        q = Problem(p.name, p.nx, p.ny, p.dx, p.z, p.n + e * v[3], p.sections, p.opts, h0=p.h0 + e * v[0],
+                    qx0=p.qx0 + e * v[1], qy0=p.qy0 + e * v[2])
+        o = oracle.Oracle(q)
+        o.run(1)
+        return float(np.sum(lam * o.h))
+    e = 5e-3
+    for k in range(4):                  # one input at a time (h, qx, qy, n), each to its own 1e-10
+        v = tuple(full[m] if m == k else np.zeros_like(full[m]) for m in range(4))
+        transposed = float(np.sum(grads[k] * v[k]))
+        tangent = (8.0 * (L(v, e) - L(v, -e)) - (L(v, 2 * e) - L(v, -2 * e))) / (12.0 * e)
+        assert abs(transposed) > 1e-6, k
+        assert transposed == pytest.approx(tangent, rel=1e-10), k
+
+
 def test_adjoint_zero_seed_gives_zero():
     p = wet_case()
     o = oracle.Oracle(p)
