@@ -156,6 +156,26 @@ def test_automatic_checkpoints_keep_every_state(prec):
     assert np.array_equal(s.adjoint(steps, GAUGES, w, n_checkpoints=3), ref)
 
 
+def test_automatic_checkpoints_halve_when_the_snapshot_block_fails():
+    # n_checkpoints = 0 asks for one snapshot per step (45 here); the sweep's first
+    # allocation, the snapshot block, is made to fail once, so the count halves to
+    # 22 and the sweep goes on with the binomial schedule of 22 snapshots
+    Fm = F()
+    p = wet_case(seed=3)
+    steps = 45
+    w = np.random.default_rng(9).standard_normal((steps, len(GAUGES)))
+    s = Fm.Sim(p, precision=Fm.F32)
+    ref = s.adjoint(steps, GAUGES, w, n_checkpoints=steps)
+    Fm.flood_debug_fail_alloc_after(0)
+    try:
+        gn = s.adjoint(steps, GAUGES, w, n_checkpoints=0)
+    finally:
+        Fm.flood_debug_fail_alloc_after(-1)
+    assert s.adjoint_forward_steps() == closed_cost(steps, steps // 2)
+    assert np.array_equal(gn, ref)
+    s.close()
+
+
 def test_adjoint_leaves_the_handle_unchanged():
     Fm = F()
     p = wet_case(seed=4, dt_mode=0)
