@@ -81,6 +81,27 @@ def test_tiled_ensemble_equals_members_alone(K, rows, spg, graph):
     ens.close()
 
 
+@pytest.mark.parametrize("K,graph", [(4, True), (8, False)])
+def test_tiled_ensemble_of_one_member_equals_it_alone(K, graph):
+    """A single member: the members are launched in two groups of about equal
+    cells, so the second group is empty and only the first one steps."""
+    Fm = F()
+    p = scenarios()[1]
+    p.opts.epoch_steps = max(4, K)
+    ens = Fm.Ensemble([p])
+    ens.set_launch(2, 16, 8, use_graph=graph)
+    ens.set_kernel(Fm.KERNEL_TILED, K)
+    for n in (3, 16, 5):
+        ens.step(n)
+    s = Fm.Sim(p, kernel=Fm.KERNEL_STREAM)
+    s.step(24)
+    for f in (Fm.FIELD_H, Fm.FIELD_QX, Fm.FIELD_QY):
+        assert np.array_equal(ens.members[0].read(f), s.read(f)), f
+    assert ens.members[0].ledger()["step"] == 24
+    s.close()
+    ens.close()
+
+
 def test_ensemble_set_kernel_rejects_bad_values():
     Fm = F()
     probs = scenarios()[:2]
