@@ -244,7 +244,7 @@ flood_status flood_run_gauges(flood_handle *h, int64_t n_steps, const int64_t *g
  * replayed twice; the count is halved while that allocation fails).  The
  * snapshots and scratch return to the PyTorch caching allocator when the call
  * ends, which keeps them reserved for later allocations of the process
- * (torch.cuda.empty_cache() hands them back to the driver).  dLdh: host doubles.
+ * (torch.cuda.empty_cache() hands them back to the CUDA driver).  dLdh: host doubles.
  * dLdn_out: ny*nx elements of the grid's precision, host (out_on_device = 0)
  * or device.  dLdh0_out: optional (NULL) gradient with respect to the
  * starting depth.  The handle's state, clock and ledger are unchanged.

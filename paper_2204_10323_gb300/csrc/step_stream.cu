@@ -633,8 +633,8 @@ cudaError_t launch_step_stream(const StepArgs<float> &a, cudaStream_t st)
     return cudaSuccess;
 }
 
-// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point
-// query, so the library needs no link against the driver library).
+// cuTensorMapEncodeTiled from the CUDA driver (through the runtime's entry-point
+// query, so the library needs no link against the CUDA driver library).
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
