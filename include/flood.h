@@ -263,6 +263,26 @@ flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const int64_t *gaug
 /* Number of forward steps the last flood_adjoint call recomputed (revolve cost). */
 int64_t flood_adjoint_forward_steps(const flood_handle *h);
 
+/*
+ * The checkpoint schedule of flood_adjoint without a grid or a device (not in
+ * the paper; host only, runs without a GPU): the same binomial (revolve)
+ * recursion reverses n_steps steps (1 .. 10^6) with min(n_checkpoints,
+ * n_steps) snapshot slots (n_checkpoints >= 1; slot 0 holds the start
+ * state), starting at global step start_step >= 0 of epochs of epoch_steps
+ * steps, with replay launches of up to steps_per_replay steps that never
+ * cross an epoch end (flood_adjoint uses 4 for FP32 grids with Eq. 3 as
+ * printed, else 1).  Outputs: *forward_steps the steps replayed (what
+ * flood_adjoint_forward_steps reports after the same sweep), *replay_launches
+ * the launches they take, *in_order 1 if the steps were reversed exactly
+ * from n_steps - 1 down to 0 with every snapshot slot free again at the end,
+ * else 0.  A restore that would read a snapshot holding another step returns
+ * FLOOD_ERR_STATE (flood_adjoint makes the same check).  FLOOD_ERR_ARG for
+ * arguments out of range or NULL outputs.
+ */
+flood_status flood_revolve_plan(int64_t n_steps, int32_t n_checkpoints, int32_t epoch_steps,
+                                int64_t start_step, int32_t steps_per_replay, int64_t *forward_steps,
+                                int64_t *replay_launches, int32_t *in_order);
+
 /* Profiling of flood_adjoint (off by default): when enabled, the next calls
  * bracket every reverse step and every forward replay with CUDA events, and
  * flood_adjoint_times reports their summed device time (ms) and counts. */

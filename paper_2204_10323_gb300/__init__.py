@@ -92,6 +92,8 @@ def _load():
     L.flood_adjoint.argtypes = [H, i64, C.POINTER(C.c_int64), i32, C.POINTER(C.c_double), i32, vp, vp, i32]
     L.flood_adjoint_forward_steps.argtypes = [H]
     L.flood_adjoint_forward_steps.restype = i64
+    L.flood_revolve_plan.argtypes = [i64, i32, i32, i64, i32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_int32)]
     L.flood_destroy.argtypes = [H]
     L.flood_last_error.argtypes = [H]
     L.flood_last_error.restype = C.c_char_p
@@ -229,6 +231,16 @@ def flood_volume_noalloc(depth_ptr, nx: int, ny: int, row_pitch: int, precision:
     """Stored volume of a device depth array without any allocation (see include/flood.h)."""
     _check(lib().flood_volume_noalloc(depth_ptr, int(nx), int(ny), int(row_pitch), int(precision), float(dx),
                                       out_ptr, stream_ptr), None)
+
+
+def revolve_plan(n_steps: int, n_checkpoints: int, epoch_steps: int = 16, start_step: int = 0,
+                 steps_per_replay: int = 1) -> dict:
+    """flood_revolve_plan: the adjoint's checkpoint schedule run on the host alone
+    (see include/flood.h): steps replayed, replay launches, reversal in order."""
+    f, n, ok = C.c_int64(), C.c_int64(), C.c_int32()
+    _check(lib().flood_revolve_plan(int(n_steps), int(n_checkpoints), int(epoch_steps), int(start_step),
+                                    int(steps_per_replay), C.byref(f), C.byref(n), C.byref(ok)), None)
+    return {"forward_steps": f.value, "replay_launches": n.value, "in_order": bool(ok.value)}
 
 
 def flood_debug_fail_alloc_after(n: int) -> None:

@@ -101,6 +101,11 @@ struct Sweep {
     const double *seed = nullptr;    // device, N x G
     int64_t fwd_steps = 0;
     int64_t prof_fwd_steps = 0;      // forward steps inside the profiled launches
+    int64_t launches = 0;            // forward replay launches
+    int max_k = 1;                   // steps a replay launch may take at most
+    std::vector<int64_t> slot_step;  // the step whose state each snapshot slot holds (-1: none)
+    bool dry = false;                // the schedule alone, no device work (flood_revolve_plan)
+    std::vector<int64_t> reversed;   // dry runs: the steps reversed, in order
 };
 
 flood_status copy_planes(flood_handle *h, const Planes &dst, const Planes &src, size_t plane, size_t plane_y)
@@ -179,15 +184,14 @@ flood_status ensure_epoch(Sweep &S, int64_t e)
 
 bool same(const Planes &a, const Planes &b) { return a.h == b.h; }
 
-// Steps the next replay launch may take towards `step`: up to 4 for FP32 grids
-// running Eq. 3 as printed (their temporal-blocking kernel gives the single steps'
-// bits), never past the end of the epoch; one otherwise.
+// Steps the next replay launch may take towards `step`: up to S.max_k (4 for FP32
+// grids running Eq. 3 as printed, whose temporal-blocking kernel gives the single
+// steps' bits; 1 otherwise), never past the end of the epoch.
 int replay_steps(const Sweep &S, int64_t step)
 {
-    const flood_handle *h = S.h;
-    if (h->prec != FLOOD_F32 || h->geo.theta != 1.0 || h->geo.friction != 0) return 1;
+    if (S.max_k <= 1) return 1;
     const int s = (int)((S.g0 + S.work_step) % S.E);
-    return (int)std::min<int64_t>(std::min<int64_t>(step - S.work_step, 4), S.E - s);
+    return (int)std::min<int64_t>(std::min<int64_t>(step - S.work_step, S.max_k), S.E - s);
 }
 
 // One forward replay launch of k steps (replay_steps) from S.src into `dst` (a
@@ -199,18 +203,22 @@ flood_status forward_step(Sweep &S, const Planes *dst = nullptr, int k = 1)
     const int64_t g = S.g0 + S.work_step;
     const int64_t e = g / S.E;
     const int s = (int)(g % S.E);
-    if (s == 0 && !S.logged[e - S.e0]) S.loaded = -1;
-    flood_status st = ensure_epoch(S, e);
-    if (st) return st;
     const Planes out = dst ? *dst : same(S.src, S.work[0]) ? S.work[1] : S.work[0];
-    const void *in[3] = {S.src.h, S.src.qx, S.src.qy};
-    void *o[3] = {out.h, out.qx, out.qy};
-    if (S.profile) st = timed(S, S.ev_fwd, [&] { return launch_step_planes(h, s, k, in, o); });
-    else st = launch_step_planes(h, s, k, in, o);
-    if (st) return st;
+    if (!S.dry) {
+        if (s == 0 && !S.logged[e - S.e0]) S.loaded = -1;
+        flood_status st = ensure_epoch(S, e);
+        if (st) return st;
+        const void *in[3] = {S.src.h, S.src.qx, S.src.qy};
+        void *o[3] = {out.h, out.qx, out.qy};
+        if (S.profile) st = timed(S, S.ev_fwd, [&] { return launch_step_planes(h, s, k, in, o); });
+        else st = launch_step_planes(h, s, k, in, o);
+        if (st) return st;
+    }
     S.src = out;
     S.work_step += k;
     S.fwd_steps += k;
+    S.launches++;
+    if (dst) S.slot_step[dst - S.slots.data()] = S.work_step;
     if (S.profile) S.prof_fwd_steps += k;
     return FLOOD_OK;
 }
@@ -219,6 +227,7 @@ flood_status forward_step(Sweep &S, const Planes *dst = nullptr, int k = 1)
 flood_status restore(Sweep &S, int slot, int64_t step)
 {
     if (S.work_step == step) return FLOOD_OK;
+    if (S.slot_step[slot] != step) return fail(S.h, FLOOD_ERR_STATE, "revolve: a snapshot holds another step");
     S.src = S.slots[slot];
     S.work_step = step;
     return FLOOD_OK;
@@ -300,6 +309,10 @@ flood_status reverse_step_t(Sweep &S)
 
 flood_status reverse_step(Sweep &S)
 {
+    if (S.dry) {
+        S.reversed.push_back(S.work_step);
+        return FLOOD_OK;
+    }
     return S.h->prec == FLOOD_F32 ? reverse_step_t<float>(S) : reverse_step_t<double>(S);
 }
 
@@ -338,8 +351,9 @@ flood_status reverse_range(Sweep &S, int64_t a, int64_t b, int sa)
     const int sm = S.free_slots.back();
     S.free_slots.pop_back();
     if (S.work_step == m) {
-        if ((st = copy_planes(S.h, S.slots[sm], S.src, S.plane, S.plane_y))) return st;
+        if (!S.dry && (st = copy_planes(S.h, S.slots[sm], S.src, S.plane, S.plane_y))) return st;
         S.src = S.slots[sm];
+        S.slot_step[sm] = m;
     } else if ((st = advance_to(S, m, &S.slots[sm]))) {
         return st;
     }
@@ -436,6 +450,9 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
         }
     }
     for (int c = C - 1; c >= 1; c--) S.free_slots.push_back(c);
+    S.slot_step.assign(C, -1);
+    S.slot_step[0] = 0;                   // the start state, copied in before the sweep
+    S.max_k = (h->prec == FLOOD_F32 && h->geo.theta == 1.0 && h->geo.friction == 0) ? 4 : 1;
     S.e0 = S.g0 / S.E;
     const int64_t n_ep = (S.g0 + n_steps - 1) / S.E - S.e0 + 1;
     S.logged.assign(n_ep, 0);
@@ -527,9 +544,10 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     S.cells = cells_dev;
     S.G = n_gauges;
     S.seed = seed_dev;
-    // FP32 forward replays run one step at a time with the arithmetic the adjoint
-    // linearises: the tensor-tile kernel below 2^27 cells, the stream kernel above
-    // (bitwise equal to each other and to the temporal-blocking kernel)
+    // FP32 forward replays run the arithmetic the adjoint linearises: launches of
+    // one step the tensor-tile kernel below 2^27 cells, the stream kernel above;
+    // launches of up to four steps (replay_steps) the temporal-blocking kernel (all
+    // bitwise equal)
     if (h->prec == FLOOD_F32)
         h->kernel = (int64_t)h->geo.nx * h->geo.ny < ((int64_t)1 << 27) ? FLOOD_KERNEL_TMA : FLOOD_KERNEL_STREAM;
     for (int b = 0; b < 2; b++) {
@@ -580,4 +598,33 @@ extern "C" flood_status flood_adjoint(flood_handle *h, int64_t n_steps, const in
     CKF(cudaStreamSynchronize(h->stream));
 #undef CKF
     return finish(FLOOD_OK);
+}
+
+extern "C" flood_status flood_revolve_plan(int64_t n_steps, int32_t n_checkpoints, int32_t epoch_steps,
+                                           int64_t start_step, int32_t steps_per_replay, int64_t *forward_steps,
+                                           int64_t *replay_launches, int32_t *in_order)
+{
+    if (n_steps < 1 || n_steps > 1000000 || n_checkpoints < 1 || epoch_steps < 1 || start_step < 0 ||
+        steps_per_replay < 1 || !forward_steps || !replay_launches || !in_order)
+        return fail(nullptr, FLOOD_ERR_ARG, "bad revolve plan arguments");
+    Sweep S;
+    S.dry = true;
+    S.g0 = start_step;
+    S.N = n_steps;
+    S.E = epoch_steps;
+    S.max_k = steps_per_replay;
+    const int C = (int)std::min<int64_t>(n_checkpoints, n_steps);
+    S.slots.resize(C);
+    S.slot_step.assign(C, -1);
+    S.slot_step[0] = 0;
+    for (int c = C - 1; c >= 1; c--) S.free_slots.push_back(c);
+    S.work_step = 0;
+    flood_status st = reverse_range(S, 0, n_steps, 0);
+    if (st) return st;
+    bool ok = (int64_t)S.reversed.size() == n_steps && (int)S.free_slots.size() == C - 1;
+    for (int64_t k = 0; ok && k < n_steps; k++) ok = S.reversed[k] == n_steps - 1 - k;
+    *forward_steps = S.fwd_steps;
+    *replay_launches = S.launches;
+    *in_order = ok ? 1 : 0;
+    return FLOOD_OK;
 }
