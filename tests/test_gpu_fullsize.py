@@ -223,8 +223,9 @@ def test_ensemble_96_sampled_members_match_oracle():
 
 
 def test_ensemble_96_one_member_of_each_shape_matches_oracle_1024_steps():
-    """One member of each of the five grid shapes, 1024 steps (64 epochs) in the
-    benchmark's launch shape, element by element against the oracle run alone."""
+    """One member of each of the five grid shapes, 1024 steps (64 epochs) on the
+    benchmark's kernel (temporal blocking, K = 4, two launch groups; the rows
+    per item change no bit), element by element against the oracle run alone."""
     Fm = F()
     probs = []
     for s in range(96):
