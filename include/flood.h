@@ -35,7 +35,11 @@
  * PyTorch CUDA caching allocator) and issues all work on the stream given in
  * flood_opts (or the current PyTorch stream of the current device at
  * creation).  Input arrays are copied at the call; output arrays are
- * caller-owned.  A handle must not be used by two threads at once.
+ * caller-owned.  A handle must not be used by two threads at once; different
+ * handles may be used from different threads.  The kernels' shared-memory
+ * limits and occupancy figures are set up once per process, on the device of
+ * the first launch: a process drives one GPU (one process per GPU, as under
+ * torchrun).
  */
 #ifndef FLOOD_H
 #define FLOOD_H

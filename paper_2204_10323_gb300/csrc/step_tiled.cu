@@ -12,7 +12,7 @@ namespace flood {
 // which level K lags level 1.
 void tiled_split(int n_strips, int ny, int resident, int K, int *chunk_rows, int *blocks)
 {
-    static int memo[4] = {-1, -1, -1, -1}, memo_rows = 0;
+    static thread_local int memo[4] = {-1, -1, -1, -1}, memo_rows = 0;   // per thread: no race between handles
     if (memo[0] == n_strips && memo[1] == ny && memo[2] == resident && memo[3] == K) {
         const long long items = (long long)n_strips * ((ny + memo_rows - 1) / memo_rows);
         *chunk_rows = memo_rows;
