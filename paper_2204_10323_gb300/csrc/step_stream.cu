@@ -15,6 +15,7 @@
 // leaves without storing.
 #include <cuda.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "fast_face.cuh"
@@ -558,8 +559,8 @@ int kernel_mode(const Geom &g) { return (g.theta != 1.0 ? 1 : 0) | (g.friction !
 
 cudaError_t configure(int warps)
 {
-    static bool configured = false;
-    if (configured) return cudaSuccess;
+    static std::atomic<bool> configured{false};
+    if (configured.load(std::memory_order_acquire)) return cudaSuccess;
     for (auto k : {step_stream_kernel<0>, step_stream_kernel<1>, step_stream_kernel<2>, step_stream_kernel<3>}) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(sizeof(WarpRing) * kMaxWarps));
@@ -571,7 +572,7 @@ cudaError_t configure(int warps)
                                              (int)(sizeof(WarpRing) * kMaxWarps));
         if (e != cudaSuccess) return e;
     }
-    configured = true;
+    configured.store(true, std::memory_order_release);
     (void)warps;
     return cudaSuccess;
 }
@@ -641,15 +642,16 @@ using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
 
 static EncodeTiled encode_tiled()
 {
-    static EncodeTiled fn = nullptr;
-    if (!fn) {
+    // looked up once per process (a function-local static: thread-safe initialisation)
+    static const EncodeTiled fn = [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-    }
+            return reinterpret_cast<EncodeTiled>(p);
+        return (EncodeTiled) nullptr;
+    }();
     return fn;
 }
 
@@ -688,14 +690,14 @@ cudaError_t launch_step_tma(const StepArgs<float> &a, cudaStream_t st)
     int warps, rows;
     stream_launch_shape(a.geo, a.tile_x, a.tile_y, &warps, &rows);
     const size_t smem = sizeof(WarpRingT) * warps + 128;
-    static bool configured = false;
-    if (!configured) {
+    static std::atomic<bool> configured{false};
+    if (!configured.load(std::memory_order_acquire)) {
         for (auto k : {step_tma_kernel<0>, step_tma_kernel<1>, step_tma_kernel<2>, step_tma_kernel<3>}) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)(sizeof(WarpRingT) * kMaxWarps + 128));
             if (e != cudaSuccess) return e;
         }
-        configured = true;
+        configured.store(true, std::memory_order_release);
     }
     const int P = a.geo.pitch, ny = a.geo.ny;
     TmaMaps maps;

@@ -27,6 +27,8 @@
 // which the status word gets the timeout bit and the pipeline stops storing.
 #pragma once
 
+#include <atomic>
+
 #include "fast_face.cuh"
 #include "tma_util.cuh"
 
@@ -682,11 +684,14 @@ __global__ void __launch_bounds__(K * 32, K == 4 ? (kMode ? 4 : 6) : K == 8 ? 2 
 }
 
 
-// Blocks of `kernel` (K warps, `smem` bytes) resident on the GPU at once.
+// Blocks of `kernel` (K warps, `smem` bytes) resident on the GPU at once; the
+// first call of a kernel sets its shared-memory limit and fills `cache` (threads
+// that race here do the same work and store the same value).
 template <typename Kern>
-cudaError_t resident_blocks(Kern kernel, int threads, size_t smem, int *cache, int *out)
+cudaError_t resident_blocks(Kern kernel, int threads, size_t smem, std::atomic<int> *cache, int *out)
 {
-    if (!*cache) {
+    int v = cache->load(std::memory_order_acquire);
+    if (!v) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per_sm = 0;
@@ -694,9 +699,10 @@ cudaError_t resident_blocks(Kern kernel, int threads, size_t smem, int *cache, i
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
         if (e != cudaSuccess) return e;
-        *cache = (per_sm < 1 ? 1 : per_sm) * sms;
+        v = (per_sm < 1 ? 1 : per_sm) * sms;
+        cache->store(v, std::memory_order_release);
     }
-    *out = *cache;
+    *out = v;
     return cudaSuccess;
 }
 
@@ -704,7 +710,7 @@ template <int K, int kMode>
 cudaError_t launch_k(const StepArgs<float> &a0, cudaStream_t st)
 {
     using Smem = PipeSmem<K, kPF1, hand_fields(kMode)>;
-    static int cache = 0;
+    static std::atomic<int> cache{0};
     int resident = 0;
     cudaError_t e = resident_blocks(step_tiled_kernel<K, kMode>, K * 32, sizeof(Smem), &cache, &resident);
     if (e != cudaSuccess) return e;
@@ -733,7 +739,7 @@ cudaError_t launch_ens_k(const StepArgs<float> *table, const int *base, int n, i
                          int want_hmax, int *next_item, cudaStream_t st)
 {
     using Smem = PipeSmem<K, kPFE, hand_fields(kMode)>;
-    static int cache = 0;
+    static std::atomic<int> cache{0};
     int resident = 0;
     cudaError_t e = resident_blocks(step_tiled_ensemble_kernel<K, kMode>, K * 32, sizeof(Smem), &cache, &resident);
     if (e != cudaSuccess) return e;
