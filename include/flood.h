@@ -451,6 +451,19 @@ void flood_debug_fail_alloc_after(int64_t n);
 int64_t flood_debug_alloc_count(void);
 flood_status flood_debug_padding(flood_handle *h, int32_t fill, int64_t *bad);
 
+/*
+ * flood_debug_tiled_split: the work items the temporal-blocking kernel would
+ * split an nx x ny grid into (host only, no device): k_steps 1..4 or 8, mode
+ * bit 0 theta weighting and bit 1 vector-norm friction (they narrow the
+ * strips), resident >= 1 the pipelines the GPU holds at once (912 on a GB300
+ * for K = 4 as printed).  *chunk_rows the rows per item, *blocks the
+ * pipelines launched, *n_items the (chunk, strip) items.  FLOOD_ERR_ARG (no
+ * message) for arguments out of range, NULL outputs or more than 2^31 - 1
+ * items.
+ */
+flood_status flood_debug_tiled_split(int32_t nx, int32_t ny, int32_t k_steps, int32_t mode, int32_t resident,
+                                     int32_t *chunk_rows, int32_t *blocks, int32_t *n_items);
+
 /* Library version string. */
 const char *flood_version(void);
 

@@ -136,6 +136,8 @@ def _load():
     L.flood_debug_alloc_count.restype = i64
     L.flood_debug_padding.argtypes = [H, i32, C.POINTER(i64)]
     L.flood_debug_padding.restype = C.c_int
+    L.flood_debug_tiled_split.argtypes = [i32, i32, i32, i32, i32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_int32)]
     for name in ("flood_decomp_plan", "flood_decomp_combine_ledgers", "flood_decomp_create", "flood_decomp_step",
                  "flood_decomp_read", "flood_decomp_write_state", "flood_decomp_sync", "flood_decomp_destroy"):
         getattr(L, name).restype = C.c_int
@@ -246,6 +248,14 @@ def revolve_plan(n_steps: int, n_checkpoints: int, epoch_steps: int = 16, start_
 def flood_debug_fail_alloc_after(n: int) -> None:
     """Make the library's device allocation after n more successful ones fail (n < 0: off)."""
     lib().flood_debug_fail_alloc_after(int(n))
+
+
+def flood_debug_tiled_split(nx: int, ny: int, k_steps: int = 4, mode: int = 0, resident: int = 912) -> dict:
+    """The temporal-blocking kernel's work items for an nx x ny grid (host only)."""
+    rows, blocks, items = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().flood_debug_tiled_split(int(nx), int(ny), int(k_steps), int(mode), int(resident), C.byref(rows),
+                                         C.byref(blocks), C.byref(items)), None)
+    return {"chunk_rows": rows.value, "blocks": blocks.value, "items": items.value}
 
 
 def flood_debug_alloc_count() -> int:

@@ -103,3 +103,25 @@ cudaError_t launch_step_tiled(const StepArgs<float> &a, cudaStream_t st)
 }
 
 }  // namespace flood
+
+#include "flood.h"
+
+extern "C" flood_status flood_debug_tiled_split(int32_t nx, int32_t ny, int32_t k_steps, int32_t mode,
+                                                int32_t resident, int32_t *chunk_rows, int32_t *blocks,
+                                                int32_t *n_items)
+{
+    using namespace flood;
+    if (nx < 1 || ny < 1 || !(k_steps >= 1 && (k_steps <= 4 || k_steps == 8)) || mode < 0 || mode > 3 ||
+        resident < 1 || !chunk_rows || !blocks || !n_items)
+        return FLOOD_ERR_ARG;
+    const int out = out_cols(k_steps, mode);
+    const int n_strips = (nx + out - 1) / out;
+    int rows = 0, b = 0;
+    tiled_split_dynamic(n_strips, ny, resident, k_steps, &rows, &b);
+    const long long items = (long long)n_strips * ((ny + rows - 1) / rows);
+    if (items > 0x7fffffffLL) return FLOOD_ERR_ARG;
+    *chunk_rows = rows;
+    *blocks = b;
+    *n_items = (int32_t)items;
+    return FLOOD_OK;
+}
