@@ -516,7 +516,9 @@ def test_vector_friction_tma_tiles_equal_row_staging_bitwise(theta, tile):
         assert np.array_equal(a.read(f), b.read(f)), f
 
 
-def test_vector_friction_auto_runs_the_tensor_tile_kernel():
+def test_vector_friction_auto_equals_the_tensor_tile_kernel():
+    """AUTO runs the options on the temporal-blocking kernel (E = 16 is a multiple
+    of 4); its bits are the TMA-tile kernel's."""
     Fm = F()
     p = as_f32_problem(with_friction(inputs.random_small(257, 129, 6), 1))
     a = Fm.Sim(p, kernel=Fm.KERNEL_AUTO)

@@ -8,9 +8,10 @@ benchmark times.
   oracle run on a window of radius N + 2 around a cell, with the GPU's time
   step and closed window edges, gives that cell's exact FP64 value: the edge
   faces reach only N + 1 cells inward in N steps.
-* 96-scenario ensemble (256^2 .. 2048^2) with the launch shape the benchmark's
-  autotuner picks (temporal blocking, 4 steps per launch, 128-row items):
-  sampled members element by element against the oracle run on each alone.
+* 96-scenario ensemble (256^2 .. 2048^2) on the benchmark's kernel (temporal
+  blocking, 4 steps per launch, two launch groups; 128-row base items here,
+  the rows per item change no bit): sampled members element by element against
+  the oracle run on each alone.
 
 FP32 tolerance: the FP32 path rounds about 6e-8 relative per operation on water
 levels of 10-100 m; over these 16-100 steps that stays below 1e-4 m (the
