@@ -35,11 +35,25 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
+
+/* Work arrays inside a step: an allocation failure ends the process with a
+ * message (this is a test oracle; the entry points that allocate whole grids
+ * report failure by their return value instead). */
+static double *work_alloc(size_t n, int zeroed)
+{
+    double *p = zeroed ? (double *)calloc(n ? n : 1, sizeof(double)) : (double *)malloc(sizeof(double) * (n ? n : 1));
+    if (!p) {
+        fprintf(stderr, "flood oracle: out of host memory (%zu doubles)\n", n);
+        abort();
+    }
+    return p;
+}
 
 typedef struct {
     int32_t nx, ny;
@@ -237,7 +251,7 @@ static void boundary_faces(const orc_params *p, const orc_section *secs, int32_t
         int32_t i0, i1;
         orc_section_range(p, sec, &i0, &i1);
         if (i1 <= i0) continue;
-        double *qb = (double *)malloc(sizeof(double) * (size_t)(i1 - i0));
+        double *qb = work_alloc((size_t)(i1 - i0), 0);
         /* inward sign: +1 on xmin/ymin, -1 on xmax/ymax */
         double inward = (sec->side == 0 || sec->side == 2) ? 1.0 : -1.0;
         if (sec->kind == 0) {
@@ -536,12 +550,12 @@ static void orc_step_reverse(const orc_params *p, const orc_section *secs, int32
 {
     int32_t nx = p->nx, ny = p->ny;
     size_t NC = (size_t)nx * ny, NX = (size_t)ny * (nx + 1), NY = (size_t)(ny + 1) * nx;
-    double *qxn = (double *)malloc(sizeof(double) * NX);
-    double *qyn = (double *)malloc(sizeof(double) * NY);
-    double *lhu = (double *)malloc(sizeof(double) * NC);   /* adjoint of unclipped h' */
-    double *lh_out = (double *)calloc(NC, sizeof(double));
-    double *lqx_out = (double *)calloc(NX, sizeof(double));
-    double *lqy_out = (double *)calloc(NY, sizeof(double));
+    double *qxn = work_alloc(NX, 0);
+    double *qyn = work_alloc(NY, 0);
+    double *lhu = work_alloc(NC, 0);   /* adjoint of unclipped h' */
+    double *lh_out = work_alloc(NC, 1);
+    double *lqx_out = work_alloc(NX, 1);
+    double *lqy_out = work_alloc(NY, 1);
     orc_ledger dummy = {0};
 
     /* forward recompute of the new face fluxes (as in the step) */
@@ -643,7 +657,7 @@ static void orc_step_reverse(const orc_params *p, const orc_section *secs, int32
         if (i1 <= i0) continue;
         double inward = (sec->side == 0 || sec->side == 2) ? 1.0 : -1.0;
         int32_t m = i1 - i0;
-        double *mu = (double *)malloc(sizeof(double) * (size_t)m);
+        double *mu = work_alloc((size_t)m, 0);
         for (int32_t k = i0; k < i1; k++) {
             switch (sec->side) {
             case 0: mu[k - i0] = QX(lqx, k, 0); break;
@@ -669,7 +683,7 @@ static void orc_step_reverse(const orc_params *p, const orc_section *secs, int32
                dw_c/dn_j = -delta_cj w_c/n_c + (pe w_c / hhat_c) dW/dn_j,
                dW/dn_j = (w_j / n_j) / sum_c (pe w_c / hhat_c). */
             double Q = orc_hydrograph(sec, t);
-            double *qb = (double *)malloc(sizeof(double) * (size_t)m);
+            double *qb = work_alloc((size_t)m, 0);
             double W = orc_inflow_faces(p, sec, z, n, Q, qb);
             if (Q > 0.0) {
                 double D = 0.0, Nnu = 0.0;
