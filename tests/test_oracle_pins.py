@@ -14,7 +14,7 @@ import pytest
 import inputs
 from inputs import INFLOW, OUTFLOW, XMAX, XMIN, YMAX, YMIN, Options, Problem, Section
 import oracle
-from closed_forms import standing_wave_amplitudes
+from closed_forms import standing_wave_amplitudes, standing_wave_gradient
 
 
 def closed_box(z, h0, dx=1.0, n=0.03, sections=(), **opt):
@@ -633,6 +633,30 @@ def test_adjoint_dot_product_one_step(theta, friction, bc_form, inflow):
         tangent = (8.0 * (L(v, e) - L(v, -e)) - (L(v, 2 * e) - L(v, -2 * e))) / (12.0 * e)
         assert abs(transposed) > 1e-6, k
         assert transposed == pytest.approx(tangent, rel=1e-10), k
+
+
+@pytest.mark.parametrize("nx,ny,mx,my,theta", [(16, 1, 3, 0, 1.0), (12, 10, 2, 3, 1.0), (12, 10, 1, 2, 0.9),
+                                               (1, 12, 0, 2, 0.8), (16, 1, 3, 0, 0.7)])
+def test_adjoint_at_rest_is_the_transposed_mode_dynamics(nx, ny, mx, my, theta):
+    """A 2 m lake at rest (n = 0.03, walls): there the reverse sweep's Jacobian is
+    the linear staggered scheme's (no discharge, so neither friction nor the
+    h_f factor of the slope term has a derivative), and the gradient of
+    L = <cosine mode, depths after 40 steps> has the closed form of
+    closed_forms.standing_wave_gradient: the mode dynamics transposed, plus the
+    wall faces' theta terms.  dL/dn is zero.  Bound 1e-12 (measured 1e-15)."""
+    H, dx, dt, steps = 2.0, 1.5, 0.05, 40
+    p = inputs.standing_wave(nx, ny, mx, my, H=H, eps=0.0, dx=dx, dt=dt, theta=theta, n=0.03)
+    mh, gh, gx, gy = standing_wave_gradient(nx, ny, mx, my, H, dx, dt, theta, steps)
+    jj, ii = np.mgrid[0:ny, 0:nx]
+    gauges = np.stack([ii.ravel(), jj.ravel()], 1)
+    seed = np.zeros((steps, nx * ny))
+    seed[-1] = mh.ravel()
+    gn, lh, lqx, lqy = oracle.Oracle(p).adjoint(steps, gauges, seed, want_state=True)
+    assert np.abs(gh).max() > 0.1
+    np.testing.assert_allclose(lh, gh, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(lqx, gx, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(lqy, gy, rtol=0, atol=1e-12)
+    assert not gn.any()
 
 
 def test_adjoint_zero_seed_gives_zero():
