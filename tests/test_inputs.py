@@ -87,3 +87,20 @@ def test_c5_calibration_recipe():
         ring = z[max(j - 30, 0):j + 31, i]
         assert z[j, i] <= np.median(ring)
     assert p.opts.dt_mode == 1                        # a fixed dt for the gradient
+
+
+def test_standing_wave_recipe():
+    """Flat closed basin at rest, depth H + eps cos(kx x) cos(ky y) at the cell
+    centres: the mode is even about both walls (the cells next to a wall mirror
+    the ones at the opposite wall up to the mode's parity) and has zero mean for
+    a mode number above 0."""
+    p = inputs.standing_wave(12, 10, 2, 3, H=2.0, eps=1e-3, dx=1.5, n=0.03)
+    assert (p.nx, p.ny, p.dx) == (12, 10, 1.5) and p.sections == []
+    assert not p.z.any() and np.all(p.n == 0.03)
+    assert not p.qx0.any() and not p.qy0.any()
+    m = (p.h0 - 2.0) / 1e-3
+    assert abs(m.max() - 1.0) < 0.1 and abs(m.min() + 1.0) < 0.2
+    np.testing.assert_allclose(m[:, ::-1], m, atol=1e-12)          # mx = 2: even under x -> L - x
+    np.testing.assert_allclose(m[::-1, :], -m, atol=1e-12)         # my = 3: odd under y -> L - y
+    assert abs(m.sum()) < 1e-9
+    assert p.opts.dt_mode == 1 and p.opts.dt_const == 0.05
