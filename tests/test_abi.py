@@ -207,3 +207,18 @@ def test_create_rejects_theta_out_of_range_and_unsupported_kernels():
         o.kernel = kernel
         st, _ = _create(_grid(8, 8), np.zeros(64, np.float32), opts=o)
         assert st == F.ERR_UNSUPPORTED and "theta" in F.flood_last_error(None)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/flood.h compiles as ISO C99 with warnings as errors (no C++ or
+    torch types in the boundary), and as C++17."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    for compiler, std, name in (("gcc", "-std=c99", "t.c"), ("g++", "-std=c++17", "t.cpp")):
+        src = tmp_path / name
+        src.write_text('#include "flood.h"\nint main(void) { return (int)sizeof(flood_opts) > 0 ? 0 : 1; }\n')
+        r = subprocess.run([compiler, std, "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only", "-I",
+                            os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
