@@ -222,3 +222,38 @@ def test_header_is_plain_c(tmp_path):
         r = subprocess.run([compiler, std, "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only", "-I",
                             os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_plain_c_program_links_and_calls_the_library(tmp_path):
+    """A C program (no Python, no torch headers) links libflood_gb300.so and calls
+    entry points that need no device: the version string, the default options
+    and the adjoint's checkpoint plan (2000 steps, 40 snapshots: 5097 replays)."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    import paper_2204_10323_gb300 as F
+    so = F.lib()._name
+    src = tmp_path / "use.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "flood.h"
+int main(void)
+{
+    flood_opts o;
+    int64_t fwd = 0, launches = 0;
+    int32_t in_order = 0;
+    flood_default_opts(&o);
+    if (flood_revolve_plan(2000, 40, o.epoch_steps, 0, 4, &fwd, &launches, &in_order) != FLOOD_OK) return 1;
+    printf("%s|%d|%lld|%d\n", flood_version(), o.epoch_steps, (long long)fwd, (int)in_order);
+    return 0;
+}
+''')
+    exe = tmp_path / "use"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), so,
+                        "-Wl,-rpath," + os.path.dirname(so), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    version, E, fwd, in_order = r.stdout.strip().split("|")
+    assert "sm_103a" in version and E == "16" and fwd == "5097" and in_order == "1"
